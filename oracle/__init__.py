@@ -1,0 +1,196 @@
+"""FP64 CPU reference for the recommendation path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  The CUDA library never loads it and shares no code with it.
+
+``build()`` compiles ``rs_oracle.c`` (plain C, double precision, ``-ffp-contract=off`` so
+the host results are the same on x86-64 and AArch64) into ``oracle/_build``.  The Python
+functions below only marshal numpy arrays into the C functions; the MLP reference used
+for the surrogate lives in ``mlp.py`` (numpy, float64).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "librs_oracle.so")
+_lib = None
+
+N_OPT = 6
+N_COUNTERS = 16
+EPS = 1e-30
+COUNTER_NAMES = [
+    "n_rows", "n_pred", "n_scored", "sign_hits", "n_rec", "rec_known", "rec_hits",
+    "top1_rows", "top1_hits", "fit_ok", "fit_empty", "fit_notpd", "fit_nonfinite",
+    "unscored_invalid", "reserved14", "reserved15",
+]
+FIT_OK, FIT_EMPTY, FIT_NOTPD, FIT_NONFINITE = 0, 1, 2, 3
+RANK_ALL = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the C reference with gcc (OpenMP over splits, IEEE double, no FP contraction)."""
+    src = os.path.join(_HERE, "rs_oracle.c")
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        P = C.c_void_p
+        L.orc_standardize.argtypes = [C.c_int, C.c_int, P, P, C.c_double, P, P, P]
+        L.orc_pairs.argtypes = [C.c_int, P, C.c_int, P, P]
+        L.orc_pairs.restype = C.c_int
+        L.orc_cholesky.argtypes = [C.c_int, P]
+        L.orc_cholesky.restype = C.c_int
+        L.orc_cholesky_solve.argtypes = [C.c_int, P, P]
+        L.orc_ridge_fit.argtypes = [C.c_int, C.c_int, P, P, C.c_double, P, P, P]
+        L.orc_ridge_fit.restype = C.c_int
+        L.orc_rank.argtypes = [P, P, C.c_int, C.c_double, P]
+        L.orc_rank.restype = C.c_int
+        L.orc_rec_offsets.argtypes = [C.c_int, P, P, P, P]
+        L.orc_cv_batch.argtypes = [C.c_int, P, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double,
+                                   C.c_int, C.c_double, C.c_int, C.c_double, P, P, P, P, P, P,
+                                   P, P, P, C.c_int]
+        L.orc_num_threads_available.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def standardize(X: np.ndarray, cycles: Optional[np.ndarray] = None, eps: float = EPS):
+    """Sec. 2 feature vectors (counters / cycles), log, per-feature z-score over the rows."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    V, F = X.shape
+    cyc = None if cycles is None else np.ascontiguousarray(cycles, dtype=np.float64)
+    Z = np.empty_like(X)
+    mu = np.empty(F)
+    sg = np.empty(F)
+    lib().orc_standardize(V, F, _p(X), _p(cyc), eps, _p(Z), _p(mu), _p(sg))
+    return Z, mu, sg
+
+
+def pairs(masks: np.ndarray, j: int):
+    """Sec. 3.3 before/after version pairs of optimization j (brute force)."""
+    m = np.ascontiguousarray(masks, dtype=np.uint8)
+    b = np.zeros(64, dtype=np.int32)
+    a = np.zeros(64, dtype=np.int32)
+    n = lib().orc_pairs(int(m.shape[0]), _p(m), int(j), _p(b), _p(a))
+    return b[:n].copy(), a[:n].copy()
+
+
+def cholesky(A: np.ndarray):
+    A = np.ascontiguousarray(A, dtype=np.float64).copy()
+    st = lib().orc_cholesky(A.shape[0], _p(A))
+    return st, np.tril(A)
+
+
+def ridge_fit(Z: np.ndarray, y: np.ndarray, lam: float):
+    """Ridge with unpenalised intercept by the primal normal equations (Sec. 3.4 family)."""
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n, F = Z.shape if Z.ndim == 2 else (0, Z.shape[-1])
+    beta = np.zeros(F)
+    b = C.c_double(0.0)
+    work = np.zeros(F * F + 2 * F)
+    st = lib().orc_ridge_fit(n, F, _p(Z), _p(y), lam, _p(beta), C.byref(b), _p(work))
+    return st, beta, b.value
+
+
+def rank(pred: np.ndarray, valid: np.ndarray, k: int, log_tau: float):
+    """Sec. 2 Tier 3: sort descending (ties: lower index), threshold, top k."""
+    p = np.ascontiguousarray(pred, dtype=np.float64)
+    v = np.ascontiguousarray(valid, dtype=np.int32)
+    idx = np.zeros(N_OPT, dtype=np.int32)
+    c = lib().orc_rank(_p(p), _p(v), int(k), float(log_tau), _p(idx))
+    return idx[:c].copy()
+
+
+@dataclass
+class CVResult:
+    Z: np.ndarray
+    mu: np.ndarray
+    sigma: np.ndarray
+    fit_status: np.ndarray
+    rec_offsets: np.ndarray
+    rec_code: np.ndarray
+    rec_pred: np.ndarray
+    pred_all: np.ndarray
+    counters: np.ndarray
+
+    def counter(self, name: str) -> int:
+        return int(self.counters[COUNTER_NAMES.index(name)])
+
+
+def rec_offsets(batch, splits) -> np.ndarray:
+    out = np.zeros(splits.n_splits + 1, dtype=np.int64)
+    lib().orc_rec_offsets(batch.n_programs, _p(np.ascontiguousarray(batch.row_offsets)),
+                          _p(np.ascontiguousarray(splits.split_offsets)),
+                          _p(np.ascontiguousarray(splits.train_masks)), _p(out))
+    return out
+
+
+def cv_batch(batch, splits, lam: float = 1e-3, k: int = 3, tau: float = 1.05, flags: int = 0,
+             nthreads: int = 1, want_Z: bool = True) -> CVResult:
+    """Whole pass (standardize, pairs, fits, predictions, ranking, counters) for a batch."""
+    L = lib()
+    P = batch.n_programs
+    fo = np.zeros(P + 1, dtype=np.int64)
+    fo[1:] = np.cumsum(batch.feat_width.astype(np.int64))
+    x_is_f32 = 1 if batch.X.dtype == np.float32 else 0
+    X = np.ascontiguousarray(batch.X)
+    S = splits.n_splits
+    ro = rec_offsets(batch, splits)
+    R = int(ro[-1])
+    Z = np.empty(X.shape[0], dtype=np.float64) if want_Z else None
+    mu = np.empty(int(fo[-1]))
+    sg = np.empty(int(fo[-1]))
+    fs = np.zeros(S * N_OPT, dtype=np.uint8)
+    code = np.zeros(R, dtype=np.uint32)
+    rp = np.zeros(R * k, dtype=np.float64)
+    pa = np.zeros(R * N_OPT, dtype=np.float64)
+    cnt = np.zeros(N_COUNTERS, dtype=np.uint64)
+    cyc = None if batch.cycles is None else np.ascontiguousarray(batch.cycles, dtype=np.float64)
+    L.orc_cv_batch(P, _p(np.ascontiguousarray(batch.row_offsets)),
+                   _p(np.ascontiguousarray(batch.feat_width, dtype=np.int32)),
+                   _p(np.ascontiguousarray(batch.x_offsets)), _p(fo), _p(X), x_is_f32,
+                   _p(np.ascontiguousarray(batch.masks)),
+                   _p(np.ascontiguousarray(batch.log_time)), _p(cyc),
+                   _p(np.ascontiguousarray(splits.split_offsets)),
+                   _p(np.ascontiguousarray(splits.train_masks)), float(lam), int(k),
+                   float(np.log(tau)), int(flags), EPS, _p(Z), _p(mu), _p(sg), _p(fs), _p(ro),
+                   _p(code), _p(rp), _p(pa), _p(cnt), int(nthreads))
+    return CVResult(Z=Z, mu=mu, sigma=sg, fit_status=fs.reshape(S, N_OPT), rec_offsets=ro,
+                    rec_code=code, rec_pred=rp.reshape(R, k), pred_all=pa.reshape(R, N_OPT),
+                    counters=cnt)
+
+
+def decode_rec(code: np.ndarray):
+    """Unpack rec_code words into (count, [idx...]) lists."""
+    out = []
+    for c in np.asarray(code, dtype=np.uint64):
+        c = int(c)
+        n = c & 0xF
+        out.append([(c >> (4 + 4 * a)) & 0xF for a in range(n)])
+    return out
+
+
+def threads_available() -> int:
+    return int(lib().orc_num_threads_available())

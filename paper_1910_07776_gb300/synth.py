@@ -1,0 +1,265 @@
+"""Seeded synthetic inputs shaped like the paper's profiling data (generator "gen/v1").
+
+The paper profiles 64 versions of each subject program, one per combination of six
+source-code optimizations (Sec. 3.3), and normalises hardware-counter readings by the
+cycle count to form feature vectors (Sec. 2).  Its profiles are not available, so this
+module draws stand-ins with the same structure:
+
+* a version is a 6-bit optimization mask; a program owns a set of distinct masks;
+* every version has F positive counter readings, a cycle count and a run time;
+* adding optimization ``j`` to version ``v`` changes the run time by a program- and
+  mask-dependent factor (per-optimization main effects plus pairwise interactions).
+
+This module holds input generation only.  It computes no log/z-score, no pair, no fit,
+no prediction and no ranking: those belong to the method and live on each side of the
+parity check (the CPU reference and the CUDA library) separately.
+
+Recipe (all draws from one numpy PCG64 stream per call, so a seed fixes every byte):
+
+* latent program state ``h_p ~ N(0, I_8)``;
+* main effect of optimization j: ``a_pj = 0.3 * w_j.h_p / |w_j|`` (marginally N(0, 0.3^2));
+* pairwise interaction: ``b_pjk = 0.1 * u_jk.h_p / |u_jk|`` (marginally N(0, 0.1^2));
+* log speedup of mask m: ``LS(m) = sum_{j in m} a_j + sum_{j<k in m} b_jk + N(0, 0.05^2)``;
+  ``log t(m) = t0_p - LS(m)``;
+* log counter rate: ``log x_{m,f} = (M h_p)_f + sum_{k in m} s_{p,k,f} + N(0, 0.3^2)`` with
+  per-optimization shifts ``s_{p,k,f} = U_{k,f} + 0.3 (C_k h_p)_f / sqrt(8)``,
+  ``U ~ N(0, 0.5^2)``; ``M`` is scaled so the marginal of ``log x`` is about N(0, 1.5^2)
+  (the "log-normal(0, 1.5) with a per-mask additive shift" of the workloads);
+* raw counters ``X = x * cycles`` with ``cycles = exp(log t + 20 + N(0, 0.02^2))`` when a
+  cycle column is requested, else ``X = x``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional, Sequence, Union
+
+import numpy as np
+
+GEN_VERSION = "gen/v1"
+N_OPT = 6
+N_MASK = 1 << N_OPT
+LATENT = 8
+
+IntOrRange = Union[int, Sequence[int]]
+
+
+@dataclass
+class ProgramBatch:
+    """A ragged batch of programs.
+
+    Program ``p`` owns rows ``row_offsets[p] .. row_offsets[p+1]-1`` (its versions, at most
+    64); its counter block starts at element ``x_offsets[p]`` of ``X`` and is row-major
+    ``[V_p, F_p]`` with ``F_p = feat_width[p]``.
+    """
+
+    X: np.ndarray              # flat float32/float64 raw counters
+    x_offsets: np.ndarray      # int64 [P]
+    row_offsets: np.ndarray    # int64 [P+1]
+    feat_width: np.ndarray     # int32 [P]
+    masks: np.ndarray          # uint8 [R] 6-bit optimization mask per version
+    log_time: np.ndarray       # float64 [R]
+    cycles: Optional[np.ndarray]  # float64 [R] or None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_programs(self) -> int:
+        return int(self.feat_width.shape[0])
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.row_offsets[-1])
+
+    def versions(self, p: int) -> int:
+        return int(self.row_offsets[p + 1] - self.row_offsets[p])
+
+    def program_X(self, p: int) -> np.ndarray:
+        V, F = self.versions(p), int(self.feat_width[p])
+        o = int(self.x_offsets[p])
+        return self.X[o:o + V * F].reshape(V, F)
+
+    def program_rows(self, p: int) -> slice:
+        return slice(int(self.row_offsets[p]), int(self.row_offsets[p + 1]))
+
+
+def _pick(rng: np.random.Generator, spec: IntOrRange, n: int) -> np.ndarray:
+    """Integers: a fixed value, a (lo, hi) inclusive uniform range, or a set to choose from."""
+    if isinstance(spec, (int, np.integer)):
+        return np.full(n, int(spec), dtype=np.int64)
+    spec = list(spec)
+    if len(spec) == 2 and spec[0] <= spec[1] and not isinstance(spec, set):
+        return rng.integers(spec[0], spec[1] + 1, size=n).astype(np.int64)
+    raise ValueError("use an int or a (lo, hi) pair; for a choice set call with choices=")
+
+
+def make_batch(n_programs: int,
+               versions: IntOrRange = 64,
+               feat: IntOrRange = 96,
+               feat_choices: Optional[Sequence[int]] = None,
+               dtype=np.float64,
+               seed: int = 0,
+               with_cycles: bool = True,
+               label_noise: float = 0.05,
+               feat_noise: float = 0.3,
+               mixing_kappa: Optional[float] = None) -> ProgramBatch:
+    """Draw ``n_programs`` programs (recipe in the module docstring).
+
+    ``versions``: versions per program (int, or inclusive (lo, hi) range; subsets of the
+    64 masks drawn without replacement, all 64 when V=64).  ``feat`` / ``feat_choices``:
+    feature width per program.  ``mixing_kappa``: if given, each program's log-features
+    are mixed by ``Q diag(s) Q^T`` (one random orthogonal ``Q`` per width, ``s`` log-spaced
+    from 1 down to ``1/sqrt(kappa)`` over the leading directions) to make counters
+    correlated and the Gram matrices ill-conditioned.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    P = int(n_programs)
+    Vs = _pick(rng, versions, P)
+    if np.any(Vs < 1) or np.any(Vs > N_MASK):
+        raise ValueError("versions per program must lie in 1..64")
+    if feat_choices is not None:
+        Fs = rng.choice(np.asarray(feat_choices, dtype=np.int64), size=P)
+    else:
+        Fs = _pick(rng, feat, P)
+
+    # Global (workload-level) structure shared by all programs.
+    w = rng.standard_normal((N_OPT, LATENT))
+    u = rng.standard_normal((N_OPT, N_OPT, LATENT))
+    Fmax = int(Fs.max())
+    U = 0.5 * rng.standard_normal((N_OPT, Fmax))
+    C = rng.standard_normal((N_OPT, Fmax, LATENT))
+    sM = np.sqrt(max(2.25 - 3.0 * (0.25 + 0.09 * 1.0) - feat_noise ** 2, 0.1) / LATENT)
+    M = sM * rng.standard_normal((Fmax, LATENT))
+    mixers = {}
+
+    X_parts, masks_parts, lt_parts, cyc_parts = [], [], [], []
+    x_off = np.zeros(P, dtype=np.int64)
+    row_off = np.zeros(P + 1, dtype=np.int64)
+    pos = 0
+    all_masks = np.arange(N_MASK, dtype=np.int64)
+    pop = np.array([bin(m).count("1") for m in range(N_MASK)])
+    bits = ((all_masks[:, None] >> np.arange(N_OPT)[None, :]) & 1).astype(np.float64)  # [64,6]
+    for p in range(P):
+        V, F = int(Vs[p]), int(Fs[p])
+        h = rng.standard_normal(LATENT)
+        a = 0.3 * (w @ h) / np.linalg.norm(w, axis=1)
+        b = 0.1 * (u @ h) / np.linalg.norm(u, axis=2)
+        b = np.triu(b, 1)
+        if V == N_MASK:
+            ms = all_masks.copy()
+        else:
+            ms = np.sort(rng.choice(N_MASK, size=V, replace=False)).astype(np.int64)
+        mb = bits[ms]                                           # [V,6]
+        ls = mb @ a + np.einsum("vj,jk,vk->v", mb, b, mb)
+        ls = ls + label_noise * rng.standard_normal(V)
+        t0 = rng.standard_normal()
+        log_t = t0 - ls
+        shift = U[:, :F] + 0.3 * np.einsum("kfl,l->kf", C[:, :F, :], h) / np.sqrt(LATENT)
+        logx = (M[:F] @ h)[None, :] + mb @ shift + feat_noise * rng.standard_normal((V, F))
+        if mixing_kappa is not None:
+            key = F
+            if key not in mixers:
+                Q, _ = np.linalg.qr(rng.standard_normal((F, F)))
+                r = min(F, 64)
+                s = np.full(F, 1.0 / np.sqrt(mixing_kappa))
+                s[:r] = np.logspace(0.0, -0.5 * np.log10(mixing_kappa), r)
+                mixers[key] = (Q * s[None, :]) @ Q.T
+            logx = logx @ mixers[key]
+        x = np.exp(logx)
+        if with_cycles:
+            cyc = np.exp(log_t + 20.0 + 0.02 * rng.standard_normal(V))
+            Xp = x * cyc[:, None]
+            cyc_parts.append(cyc)
+        else:
+            Xp = x
+        x_off[p] = pos
+        pos += V * F
+        row_off[p + 1] = row_off[p] + V
+        X_parts.append(Xp.reshape(-1))
+        masks_parts.append(ms.astype(np.uint8))
+        lt_parts.append(log_t)
+    del pop
+    X = np.concatenate(X_parts).astype(dtype)
+    return ProgramBatch(
+        X=X, x_offsets=x_off, row_offsets=row_off, feat_width=Fs.astype(np.int32),
+        masks=np.concatenate(masks_parts), log_time=np.concatenate(lt_parts).astype(np.float64),
+        cycles=(np.concatenate(cyc_parts).astype(np.float64) if with_cycles else None),
+        meta=dict(gen=GEN_VERSION, seed=seed, n_programs=P, mixing_kappa=mixing_kappa),
+    )
+
+
+@dataclass
+class Splits:
+    """Train/test splits: program ``p`` owns splits ``split_offsets[p] .. split_offsets[p+1]-1``;
+    split ``i`` trains on the version slots whose bit is set in ``train_masks[i]`` (bit ``r``
+    = the program's ``r``-th row) and tests on the others."""
+
+    split_offsets: np.ndarray  # int64 [P+1]
+    train_masks: np.ndarray    # uint64 [S]
+
+    @property
+    def n_splits(self) -> int:
+        return int(self.train_masks.shape[0])
+
+
+def make_splits(batch: ProgramBatch, kind: str = "half", n_splits: int = 16,
+                seed: int = 0) -> Splits:
+    """``kind``: ``"half"`` (random train subsets of exactly floor(V/2) versions, ``n_splits``
+    per program), ``"lovo"`` (leave one version out: V splits per program), ``"all"`` (one
+    split that trains on every version), or ``"frac"`` (each version in train with prob. 1/2)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5EED))
+    P = batch.n_programs
+    offs = np.zeros(P + 1, dtype=np.int64)
+    out = []
+    for p in range(P):
+        V = batch.versions(p)
+        full = (1 << V) - 1 if V < 64 else (1 << 64) - 1
+        if kind == "lovo":
+            ms = [full & ~(1 << r) for r in range(V)]
+        elif kind == "all":
+            ms = [full]
+        elif kind == "half":
+            k = V // 2
+            ms = []
+            for _ in range(n_splits):
+                sel = rng.choice(V, size=k, replace=False)
+                m = 0
+                for r in sel:
+                    m |= 1 << int(r)
+                ms.append(m)
+        elif kind == "frac":
+            ms = []
+            for _ in range(n_splits):
+                sel = np.nonzero(rng.random(V) < 0.5)[0]
+                m = 0
+                for r in sel:
+                    m |= 1 << int(r)
+                ms.append(m)
+        else:
+            raise ValueError(kind)
+        offs[p + 1] = offs[p] + len(ms)
+        out.extend(ms)
+    return Splits(split_offsets=offs, train_masks=np.array(out, dtype=np.uint64))
+
+
+def make_half_splits_fast(batch: ProgramBatch, n_splits: int, seed: int = 0) -> Splits:
+    """Vectorised ``kind="half"`` for large workloads (same distribution, different stream)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0xBA7C4))
+    P = batch.n_programs
+    offs = np.arange(P + 1, dtype=np.int64) * n_splits
+    tm = np.zeros(P * n_splits, dtype=np.uint64)
+    for p in range(P):
+        V = batch.versions(p)
+        k = V // 2
+        keys = rng.random((n_splits, V))
+        sel = np.argsort(keys, axis=1)[:, :k]
+        bitsv = np.zeros((n_splits, V), dtype=bool)
+        np.put_along_axis(bitsv, sel, True, axis=1)
+        weights = (np.uint64(1) << np.arange(V, dtype=np.uint64))
+        tm[p * n_splits:(p + 1) * n_splits] = (bitsv.astype(np.uint64) * weights[None, :]).sum(
+            axis=1, dtype=np.uint64)
+    return Splits(split_offsets=offs, train_masks=tm)
+
+
+def make_vectors(n: int, F: int = 256, seed: int = 0, dtype=np.float32) -> np.ndarray:
+    """Standard-normal stand-ins for standardized feature vectors (surrogate inputs)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x7EC7))
+    return rng.standard_normal((n, F)).astype(dtype)
