@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Ranked recommendations per second of the batched cross-validation pass.
+
+Workload (the batched-CV configuration): 64 programs, each with 16..64 versions (random
+subsets of the 64 optimization masks), 256 FP32 counter features per version (synthetic,
+log-normal(0, 1.5) with per-mask shifts, generator gen/v1, seed 0), 4096 random 50/50
+train/test splits per program (262,144 splits, about 1.57 M ridge fits), lambda 1e-3,
+top-3, threshold 1.05.  A step = one whole pass: standardize, Gram, test-row planning and
+the fused fit / predict / rank / score kernel, all in the sm_103a library.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU reference on the
+host cores instead (bounded samples of the same workload).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ranked recommendations/sec (CV-split fits+predicts) vs plain GPU form at equal accuracy"
+UNIT = "recommendations/s"
+WORKLOAD = "batched_cv: 64 programs x U{16..64} versions x 256 f32 features, 4096 half splits/program"
+CFG = dict(programs=64, versions=(16, 64), feat=256, splits=4096, lam=1e-3, k=3, tau=1.05, seed=0)
+FP64_PEAK_NOMINAL_GFLOPS = 152 * 4 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+
+
+def make_inputs(seed):
+    from paper_1910_07776_gb300 import synth
+    b = synth.make_batch(CFG["programs"], versions=CFG["versions"], feat=CFG["feat"],
+                         dtype=np.float32, seed=seed)
+    s = synth.make_half_splits_fast(b, CFG["splits"], seed=seed)
+    return b, s
+
+
+def algorithmic_flops(batch, splits):
+    """FP64 flops of the fit/predict kernel, counted from the definitions: per fit with n
+    pairs a Cholesky (n^3/3), two right-hand sides through both triangular solves (4 n^2)
+    and the intercept / dual update (4 n); per prediction 2 n."""
+    total_fit = 0.0
+    total_pred = 0.0
+    for p in range(batch.n_programs):
+        rs_ = batch.program_rows(p)
+        m = batch.masks[rs_].astype(np.int64)
+        V = len(m)
+        slot = {int(x): i for i, x in enumerate(m)}
+        T = splits.train_masks[splits.split_offsets[p]:splits.split_offsets[p + 1]].astype(np.uint64)
+        full = np.uint64((1 << V) - 1) if V < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+        test = (~T) & full
+        for j in range(6):
+            pm = [(1 << v) | (1 << slot[int(m[v]) | (1 << j)]) for v in range(V)
+                  if not (m[v] >> j) & 1 and (int(m[v]) | (1 << j)) in slot]
+            if not pm:
+                continue
+            pm = np.array(pm, dtype=np.uint64)
+            n = ((T[:, None] & pm[None, :]) == pm[None, :]).sum(axis=1).astype(np.float64)
+            nomask = np.uint64(sum(1 << v for v in range(V) if not (m[v] >> j) & 1))
+            x = test & nomask
+            cnt = np.zeros(x.shape, dtype=np.float64)
+            for _ in range(V):
+                cnt += (x & np.uint64(1)).astype(np.float64)
+                x = x >> np.uint64(1)
+            total_fit += float(np.sum(n ** 3 / 3 + 4 * n ** 2 + 4 * n))
+            total_pred += float(np.sum(2 * n * cnt * (n > 0)))
+    return total_fit + total_pred
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "power_w_max": float(max(pw)) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_reference_sample(batch, splits, target_s, seed=1):
+    """Time the FP64 CPU reference on a random sample of splits (all host cores)."""
+    import oracle
+    from paper_1910_07776_gb300 import synth
+    oracle.build()
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    rng = np.random.default_rng(seed)
+
+    def run(nsplit):
+        pick = np.sort(rng.choice(splits.n_splits, size=nsplit, replace=False))
+        prog = np.searchsorted(splits.split_offsets, pick, side="right") - 1
+        off = np.zeros(batch.n_programs + 1, dtype=np.int64)
+        np.add.at(off, prog + 1, 1)
+        off = np.cumsum(off)
+        sub = synth.Splits(split_offsets=off, train_masks=splits.train_masks[pick])
+        t0 = time.perf_counter()
+        r = oracle.cv_batch(batch, sub, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                            nthreads=threads, want_Z=False)
+        dt = time.perf_counter() - t0
+        return int(r.counters[0]), dt, nsplit
+
+    rows, dt, n = run(max(threads, 8))
+    per_split = dt / n
+    n2 = int(min(splits.n_splits, max(threads, target_s / max(per_split, 1e-6))))
+    rows, dt, n = run(n2)
+    return dict(value=rows / dt, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"{n} random splits of the {splits.n_splits} ({rows} ranked rows), "
+                       f"{dt:.1f} s wall, FP64 primal normal equations, OpenMP over splits")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    batch, splits = make_inputs(CFG["seed"])
+    for _ in range(args.warmup):
+        cpu_reference_sample(batch, splits, args.ref_step_seconds, seed=7)
+    vals, cores, sample = [], None, None
+    t_all = 0.0
+    rows_all = 0
+    for i in range(args.steps):
+        c = cpu_reference_sample(batch, splits, args.ref_step_seconds, seed=100 + i)
+        vals.append(c["value"])
+        cores, sample = c["cores"], c["sample"]
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, **{k: (list(v_) if isinstance(v_, tuple) else v_) for k, v_ in CFG.items()}},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: " + sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=6.0)
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1910_07776_gb300 import build as _b
+    _b.build()
+    from paper_1910_07776_gb300 import rs
+
+    batch, splits = make_inputs(CFG["seed"] + rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = rs.Context(local, stream)
+    db = rs.DeviceBatch.from_host(batch, dev)
+    ds = rs.DeviceSplits.from_host(splits, dev)
+    Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
+    zb = db.with_X(Z)
+    K = torch.zeros(db.n_programs * 64 * 64, dtype=torch.float64, device=dev)
+    ro = ctx.rec_offsets(db, ds)
+    R = int(ro[-1].item())
+    out = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
+    out.rec_offsets = ro
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def step():
+        ev[0].record(stream)
+        ctx.standardize(db, Z)
+        ev[1].record(stream)
+        ctx.gram(zb, rs.RS_GRAM_F64, K)
+        ev[2].record(stream)
+        ctx.rec_offsets(zb, ds, out.rec_offsets)
+        ev[3].record(stream)
+        ctx.predict_rank(zb, K, ds, out.rec_offsets, out.rec_code, lam=CFG["lam"], k=CFG["k"],
+                         tau=CFG["tau"], rec_pred=out.rec_pred, counters=out.counters)
+        ev[4].record(stream)
+
+    def between():
+        flush.fill_(1)   # evicts the 129 MB L2 between timed steps (not timed)
+        out.counters.zero_()
+
+    for _ in range(args.warmup):
+        between()
+        step()
+    torch.cuda.synchronize()
+    ctx.check_device_status()
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    parts = np.zeros(4)
+    tot = 0.0
+    for _ in range(args.steps):
+        between()
+        step()
+        torch.cuda.synchronize()
+        d = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+        parts += d
+        tot += ev[0].elapsed_time(ev[4])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+        r_all = torch.tensor([R], dtype=torch.float64, device=dev)
+        dist.all_reduce(r_all)
+        R_total = float(r_all.item())
+    else:
+        R_total = float(R)
+    ctx.check_device_status()
+    ms_step = tot / args.steps
+    value = R_total * args.steps / (tot / 1e3)
+    cnt = out.counters.cpu().numpy().view(np.uint64).astype(np.float64)
+    acc = {"sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1),
+           "rec_precision": cnt[6] / max(cnt[5], 1), "recs_per_row": cnt[4] / max(cnt[0], 1)}
+
+    flops = algorithmic_flops(batch, splits)
+    fit_ms = parts[3] / args.steps
+    achieved = flops / (fit_ms * 1e-3) / 1e12
+    peak_meas = rs.measure_fma_peak(True, 2048) / 1e3
+    peak = FP64_PEAK_NOMINAL_GFLOPS / 1e3
+
+    # plain GPU form: one launch per step per program, FP64, one warp per fit, no persistence
+    plain = None
+    if not args.no_plain and rank == 0:
+        plain = run_plain(rs, ctx, batch, splits, dev, stream, flush, args)
+
+    # end to end through the C ABI single call with host buffers (pinned), copies timed
+    e2e = run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_reference_sample(batch, splits, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "programs": CFG["programs"], "versions": "16..64",
+                   "features": CFG["feat"], "splits_per_program": CFG["splits"],
+                   "recs_per_step": R, "lambda": CFG["lam"], "k": CFG["k"], "tau": CFG["tau"],
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "parallelism": f"programs sharded, {world} GPU(s), no collective"},
+        "kernels_ms": {"standardize": parts[0] / args.steps, "gram_f64": parts[1] / args.steps,
+                       "plan_rows": parts[2] / args.steps, "fit_predict_rank": fit_ms},
+        "roofline": {"bound": "alu", "kernel": "fit_predict_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": "nominal FP64 1.25 TFLOP/s: 152 SMs x 2 FMA/clk x 2.07 GHz",
+                     "peak_measured_fma_chains": peak_meas, "flops_per_launch": flops},
+        "accuracy": acc,
+        "plain_form": plain,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": 6 * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def run_plain(rs, ctx, batch, splits, dev, stream, flush, args):
+    import torch
+    progs = []
+    for p in range(batch.n_programs):
+        rsl = batch.program_rows(p)
+        V, F = batch.versions(p), int(batch.feat_width[p])
+        o = int(batch.x_offsets[p])
+        s0, s1 = int(splits.split_offsets[p]), int(splits.split_offsets[p + 1])
+        from paper_1910_07776_gb300 import synth
+        sub = synth.ProgramBatch(
+            X=batch.X[o:o + V * F], x_offsets=np.zeros(1, np.int64),
+            row_offsets=np.array([0, V], np.int64), feat_width=np.array([F], np.int32),
+            masks=batch.masks[rsl], log_time=batch.log_time[rsl],
+            cycles=None if batch.cycles is None else batch.cycles[rsl])
+        ss = synth.Splits(split_offsets=np.array([0, s1 - s0], np.int64),
+                          train_masks=splits.train_masks[s0:s1])
+        db = rs.DeviceBatch.from_host(sub, dev)
+        ds = rs.DeviceSplits.from_host(ss, dev)
+        Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
+        K = torch.zeros(64 * 64, dtype=torch.float64, device=dev)
+        ro = ctx.rec_offsets(db, ds)
+        R = int(ro[-1].item())
+        o_ = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
+        progs.append((db, ds, Z, db.with_X(Z), K, ro, o_, R))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        for db, ds, Z, zb, K, ro, o_, R in progs:
+            ctx.standardize(db, Z)
+            ctx.gram(zb, rs.RS_GRAM_F64, K)
+            ctx.rec_offsets(zb, ds, ro)
+            ctx.predict_rank(zb, K, ds, ro, o_.rec_code, lam=CFG["lam"], k=CFG["k"],
+                             tau=CFG["tau"], form=rs.RS_FORM_PLAIN, rec_pred=o_.rec_pred,
+                             counters=o_.counters)
+
+    def between():
+        flush.fill_(1)
+        for pr in progs:
+            pr[6].counters.zero_()
+
+    for _ in range(3):
+        between()
+        step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    n = max(2, min(args.steps, 5))
+    for _ in range(n):
+        between()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    R = sum(pr[7] for pr in progs)
+    cnt = sum(pr[6].counters.cpu().numpy().view(np.uint64).astype(np.float64) for pr in progs)
+    return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n,
+            "launches_per_step": 6 * len(progs),
+            "sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1)}
+
+
+def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    fo = np.zeros(batch.n_programs + 1, np.int64)
+    fo[1:] = np.cumsum(batch.feat_width.astype(np.int64))
+    host = dict(X=pin(batch.X), row_offsets=pin(batch.row_offsets.astype(np.int64)),
+                feat_width=pin(batch.feat_width.astype(np.int32)),
+                x_offsets=pin(batch.x_offsets.astype(np.int64)), feat_offsets=pin(fo),
+                masks=pin(batch.masks), log_time=pin(batch.log_time), cycles=pin(batch.cycles),
+                split_offsets=pin(splits.split_offsets.astype(np.int64)),
+                train_masks=pin(splits.train_masks.view(np.int64)))
+    devb = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    db = rs.DeviceBatch(n_programs=batch.n_programs, dtype=rs.RS_F32, n_rows=batch.n_rows,
+                        max_versions=64, max_feat=int(batch.feat_width.max()),
+                        x_elems=int(batch.X.shape[0]), feat_total=int(fo[-1]),
+                        row_offsets=devb["row_offsets"], feat_width=devb["feat_width"],
+                        x_offsets=devb["x_offsets"], feat_offsets=devb["feat_offsets"],
+                        X=devb["X"], masks=devb["masks"], log_time=devb["log_time"],
+                        cycles=devb["cycles"])
+    ds = rs.DeviceSplits(n_splits=splits.n_splits, max_train=64,
+                         split_offsets=devb["split_offsets"], train_masks=devb["train_masks"])
+    ws = torch.empty(ctx.cv_workspace_bytes(db), dtype=torch.uint8, device=dev)
+    out = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
+    h_code = torch.empty(R, dtype=torch.int32).pin_memory()
+    h_pred = torch.empty(R * CFG["k"], dtype=torch.float64).pin_memory()
+    h_cnt = torch.empty(16, dtype=torch.int64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = h_code.numel() * 4 + h_pred.numel() * 8 + 16 * 8
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        for k_, v in host.items():
+            devb[k_].copy_(v, non_blocking=True)
+        out.counters.zero_()
+        ctx.cv_step(db, ds, ws, out.rec_offsets, out.rec_code, lam=CFG["lam"], k=CFG["k"],
+                    tau=CFG["tau"], rec_pred=out.rec_pred, counters=out.counters)
+        h_code.copy_(out.rec_code, non_blocking=True)
+        h_pred.copy_(out.rec_pred, non_blocking=True)
+        h_cnt.copy_(out.counters, non_blocking=True)
+
+    for _ in range(3):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    n = max(2, min(args.steps, 5))
+    for _ in range(n):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "path": "pinned host -> device copies, rs_cv_step, device -> pinned host copies"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

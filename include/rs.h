@@ -1,0 +1,196 @@
+/*
+ * rs.h -- C ABI of the GB300 (sm_103a) library for the tier-2 / tier-3 analysis of an
+ * optimization-recommendation tool (Taheri, Qasem, Burtscher: "A Tool for Automatically
+ * Suggesting Source-Code Optimizations for Complex GPU Kernels").
+ *
+ * The tool's tiers talk through a simple interface so that any tier can be replaced
+ * (Sec. 2).  This header is that interface for tiers 2 and 3: profiled feature vectors in,
+ * per-optimization predicted speedups out, sorted, thresholded and truncated.
+ *
+ * Conventions for every entry point
+ *   - Pointers named in a struct or argument list are DEVICE pointers unless the comment
+ *     says "host".  All of them are owned by the caller; the library never frees them.
+ *   - Calls are asynchronous on the stream given to rs_create (or rs_set_stream).  A
+ *     return of RS_OK means the work was enqueued; results are valid after the stream is
+ *     synchronised.
+ *   - A call that returns anything but RS_OK enqueued nothing (argument errors) or hit a
+ *     CUDA error; rs_last_error gives a one-line reason.  Problems of a single fit
+ *     (no training pair, a non-positive pivot, a non-finite value) are not errors: they go
+ *     to the per-fit status array and never abort a batch.
+ *   - Data layout: a batch holds P programs; program p owns the versions (rows)
+ *     row_offsets[p] .. row_offsets[p+1]-1 (at most 64, one per 6-bit optimization mask,
+ *     Sec. 3.3) and a row-major [V_p][F_p] counter block starting at element x_offsets[p]
+ *     of X.  Per-feature statistics of program p sit at feat_offsets[p] + f.
+ *   - A split trains on the version slots whose bit is set in its 64-bit train mask (bit r
+ *     = the program's r-th row) and tests on the other slots (Sec. 5).  Splits of
+ *     program p are split_offsets[p] .. split_offsets[p+1]-1.
+ */
+#ifndef RS_H_
+#define RS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RS_OK = 0,
+    RS_EINVAL = 1,        /* bad argument (null pointer, size out of range, bad enum)   */
+    RS_ENOMEM = 2,        /* a caller-provided workspace is too small                   */
+    RS_ECUDA = 3,         /* a CUDA runtime call failed                                 */
+    RS_ETIMEOUT = 4,      /* a bounded device-side wait gave up                         */
+    RS_EUNSUPPORTED = 5,  /* the device is not sm_103 / feature not built               */
+    RS_EDATA = 6          /* the device found inconsistent data (see rs_last_error)      */
+} rs_status;
+
+enum { RS_FIT_OK = 0, RS_FIT_EMPTY = 1, RS_FIT_NOTPD = 2, RS_FIT_NONFINITE = 3 };
+enum { RS_F32 = 0, RS_F64 = 1 };
+/* Gram precision: plain FP64 FMAs, or the BF16 hi/lo split on the tensor cores (three
+ * BF16 products per term, FP32 accumulation in tensor memory).                         */
+enum { RS_GRAM_F64 = 0, RS_GRAM_BF16X3 = 1 };
+/* Fit forms: the batched form (fits binned by size, one thread per small fit), or the
+ * plain form (one warp per fit, lanes = matrix rows).  Both give the same results.     */
+enum { RS_FORM_BATCHED = 0, RS_FORM_PLAIN = 1 };
+/* Flags for rs_predict_rank. */
+enum {
+    RS_RANK_ALL = 1,      /* rank all six optimizations, not only those not yet applied */
+    RS_REFINE_X = 2       /* one step of iterative refinement with residual and
+                             predictions taken through Z (for an inexact Gram)        */
+};
+
+#define RS_NOPT 6
+#define RS_MAXV 64          /* versions per program (6-bit masks)                       */
+#define RS_MAXPAIRS 32      /* pairs per optimization per program                        */
+#define RS_COEF_STRIDE 33   /* doubles per fit in the coefficient array: b, alpha[32]   */
+#define RS_GRAM_LD 64       /* leading dimension of each program's Gram block           */
+#define RS_NCOUNTERS 16
+
+/* Accuracy counters (uint64, accumulated, never reset by the library):
+ *  0 test rows ranked        1 predictions made          2 predictions with a known actual
+ *  3 sign hits (pred > 0 and actual > 0 agree: the accuracy of Table 3)
+ *  4 recommendations emitted 5 ... with a known actual   6 ... whose actual speedup > 1
+ *  7 rows with >= 1 scored prediction  8 ... whose top prediction is the best actual
+ *  9..12 fits by status OK / EMPTY / NOTPD / NONFINITE (rs_predict_rank only)
+ * 13 candidates skipped because their fit was not OK     14, 15 reserved (0)          */
+
+typedef struct rs_ctx rs_ctx;
+
+typedef struct {
+    int32_t n_programs;          /* host: P >= 1                                          */
+    int32_t dtype;               /* host: RS_F32 or RS_F64, element type of X             */
+    int64_t n_rows;              /* host: total versions = row_offsets[P]                 */
+    int32_t max_versions;        /* host: upper bound on V_p, 1..64                       */
+    int32_t max_feat;            /* host: upper bound on F_p, 1..4096                     */
+    int64_t x_elems;             /* host: elements of X (and of Z)                        */
+    int64_t feat_total;          /* host: sum of F_p = feat_offsets[P]                    */
+    const int64_t* row_offsets;  /* [P+1]                                                 */
+    const int32_t* feat_width;   /* [P]                                                   */
+    const int64_t* x_offsets;    /* [P]                                                   */
+    const int64_t* feat_offsets; /* [P+1]                                                 */
+    const void* X;               /* raw counters (dtype), or standardized Z (double)      */
+    const uint8_t* masks;        /* [n_rows] 6-bit optimization mask of each version      */
+    const double* log_time;      /* [n_rows] log run time of each version                 */
+    const double* cycles;        /* [n_rows] cycle counts, or NULL (no normalisation)     */
+} rs_batch;
+
+typedef struct {
+    int64_t n_splits;            /* host: S = split_offsets[P]                            */
+    int32_t max_train;           /* host: upper bound on popcount(train mask), 0..64      */
+    int32_t reserved;
+    const int64_t* split_offsets;/* [P+1]                                                 */
+    const uint64_t* train_masks; /* [S]                                                   */
+} rs_splits;
+
+/* ---- context ------------------------------------------------------------------------
+ * rs_create: binds a context to CUDA device `device` and the stream `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Allocates 4 KiB of device memory for
+ * the context's status word and queue heads, and 32 KiB for the row-planning scan.  Fails with RS_EUNSUPPORTED if the device
+ * is not compute capability 10.3.  rs_destroy frees it (and any captured graphs).      */
+rs_status rs_create(rs_ctx** out, int device, void* cuda_stream);
+rs_status rs_destroy(rs_ctx* ctx);
+rs_status rs_set_stream(rs_ctx* ctx, void* cuda_stream);
+/* Last error of this context as a NUL-terminated string ("" if none); owned by ctx.   */
+const char* rs_last_error(const rs_ctx* ctx);
+/* Reads (and clears) the device status word after a stream sync: RS_OK, RS_EDATA when a
+ * kernel met a program with more than 64 versions or more pairs than the hint allowed,
+ * RS_ETIMEOUT when a bounded wait gave up.  Synchronises the context's stream.        */
+rs_status rs_check_device_status(rs_ctx* ctx);
+
+/* ---- A1: feature vectors (Sec. 2) -----------------------------------------------------
+ * Z[r][f] = (log(max(X[r][f] / cycles[r], 1e-30)) - mu_f) / sigma_f with mu_f, sigma_f the
+ * population mean and standard deviation of the log values over the program's versions
+ * (sigma_f < 1e-12 gives Z = 0).  The division by the cycle count is the paper's
+ * normalisation (Sec. 2); the log and z-score are this library's reading.
+ * Z: double, same layout as X (x_elems).  mu, sigma: double [feat_total], may be NULL.
+ * All arithmetic is FP64 whatever the input type.                                     */
+rs_status rs_standardize(rs_ctx* ctx, const rs_batch* batch, double* Z, double* mu,
+                         double* sigma);
+
+/* ---- A3: per-program Gram of the standardized feature vectors -------------------------
+ * K_p[a][b] = sum_f Z[a][f] * Z[b][f] for a, b < V_p, written to
+ * K[p * 64 * 64 + a * 64 + b] (double; entries outside V_p x V_p are left untouched).
+ * std: a batch whose X is Z (double).  precision: RS_GRAM_F64 (FP64 FMAs) or
+ * RS_GRAM_BF16X3 (tcgen05 tensor cores, BF16 hi/lo split of Z, three products per term,
+ * FP32 accumulation; relative error about 2^-16 per entry).  Every ridge fit of a split
+ * reads its kernel entries from this block (the dual form of the regression).         */
+rs_status rs_gram(rs_ctx* ctx, const rs_batch* std, int precision, double* K);
+
+/* ---- A2: test-row planning ------------------------------------------------------------
+ * rec_offsets[i] = number of test rows (version slots outside the train mask) of all
+ * splits before split i; rec_offsets[S] = total.  int64 [S+1].  Rows of a split are in
+ * ascending slot order.  Every rs_predict_rank output is indexed by these rows.       */
+rs_status rs_rec_offsets(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
+                         int64_t* rec_offsets);
+
+/* ---- A2 + A4: batched ridge fits (Sec. 2 tier-2 training, Sec. 3.4 regression) ---------
+ * For every split and optimization j: the training pairs are the before/after version
+ * pairs (v, v|j) with both versions in the train mask (Sec. 3.3); each pair contributes
+ * the feature vector of v labelled with log t(v) - log t(v|j), the log speedup of adding
+ * j (Sec. 5).  Fits minimise sum (y - b - z.beta)^2 + lambda |beta|^2 with an unpenalised
+ * intercept, solved in dual form from the Gram block K with an FP64 Cholesky:
+ * beta = sum_a alpha_a z_a.
+ * coef (nullable): double [S][6][33] = b, then alpha for the training pairs in ascending
+ * order of their before-version slot (zeros after n).  fit_status (nullable): uint8
+ * [S][6] RS_FIT_*.  lambda >= 0.  form: RS_FORM_BATCHED or RS_FORM_PLAIN.            */
+rs_status rs_fit_batched(rs_ctx* ctx, const rs_batch* std, const double* K,
+                         const rs_splits* splits, double lambda, int form, double* coef,
+                         uint8_t* fit_status);
+
+/* ---- A4 + A5 + A6: fit, predict, rank, threshold, score (Sec. 2 tier 3, Sec. 5, 6) -----
+ * For every test row t of every split: one predicted log speedup per candidate
+ * optimization (those not in t's mask; all six with RS_RANK_ALL), from the split's fits;
+ * candidates sorted by prediction (ties: lower index first), kept if >= log(tau), at most
+ * k (1..6) reported.  Fits are recomputed in the same launch unless coef (from
+ * rs_fit_batched with the same inputs) is given.
+ * rec_offsets: from rs_rec_offsets.  Outputs per row (R = rec_offsets[S]):
+ *   rec_code  uint32 [R]: bits 0-3 = count c, bits 4+4i..7+4i = i-th optimization (0xF unused)
+ *   rec_pred  double [R][k]: predicted log speedups of the reported list (NaN unused), nullable
+ *   pred_all  double [R][6]: every prediction (NaN where none), nullable
+ *   counters  uint64 [16]: accuracy counters (listed above), added to; nullable
+ * flags: RS_RANK_ALL, RS_REFINE_X (refine each dual solve once with residuals computed
+ * through Z in FP64 and predict through Z; for Gram blocks made with RS_GRAM_BF16X3).
+ * lambda as in rs_fit_batched; tau > 0; form as in rs_fit_batched.                   */
+rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
+                          const rs_splits* splits, double lambda, const double* coef,
+                          int k, double tau, int flags, int form,
+                          const int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
+                          double* pred_all, uint64_t* counters);
+
+/* ---- the whole step in one call ---------------------------------------------------------
+ * rs_cv_step runs A1..A6 on raw counters: standardize into workspace, Gram (precision as
+ * given), plan rows into rec_offsets, then fit/predict/rank.  workspace: device memory of
+ * at least rs_cv_workspace_bytes(batch) bytes, 256-byte aligned, owned by the caller and
+ * used as scratch (Z and the Gram blocks).  Outputs as in rs_predict_rank.            */
+size_t rs_cv_workspace_bytes(const rs_batch* batch);
+rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
+                     double lambda, int k, double tau, int flags, int precision,
+                     void* workspace, size_t workspace_bytes, int64_t* rec_offsets,
+                     uint32_t* rec_code, double* rec_pred, double* pred_all,
+                     uint64_t* counters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H_ */

@@ -1,0 +1,279 @@
+// rs_api.cu -- host side of the C ABI declared in include/rs.h: argument validation,
+// context state, and the launch sequence of each entry point.  No arithmetic of the
+// method happens here; every step runs in the kernels of the k_*.cu files.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "rs_internal.cuh"
+
+struct rs_ctx {
+    int device;
+    cudaStream_t stream;
+    int* dstatus;            // RS_DST_INTS ints of device memory
+    int64_t* scan;           // block sums of the row-planning scan (kScanBlocksMax + 1)
+    char err[512];
+};
+
+namespace {
+
+rs_status fail(rs_ctx* c, rs_status code, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+rs_status cuda_fail(rs_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, RS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+rs_status check_batch(rs_ctx* c, const rs_batch* b, bool need_raw) {
+    if (!b) return fail(c, RS_EINVAL, "batch is NULL");
+    if (b->n_programs < 1) return fail(c, RS_EINVAL, "n_programs must be >= 1");
+    if (b->max_versions < 1 || b->max_versions > RS_MAXV)
+        return fail(c, RS_EINVAL, "max_versions must be in 1..64");
+    if (b->max_feat < 1 || b->max_feat > 4096) return fail(c, RS_EINVAL, "max_feat must be in 1..4096");
+    if (!b->row_offsets || !b->feat_width || !b->x_offsets || !b->X || !b->masks || !b->log_time)
+        return fail(c, RS_EINVAL, "a required batch pointer is NULL");
+    if (need_raw && b->dtype != RS_F32 && b->dtype != RS_F64)
+        return fail(c, RS_EINVAL, "dtype must be RS_F32 or RS_F64");
+    if ((uintptr_t)b->X % (b->dtype == RS_F32 ? 4 : 8) != 0) return fail(c, RS_EINVAL, "X is misaligned");
+    return RS_OK;
+}
+
+rs_status check_splits(rs_ctx* c, const rs_splits* s) {
+    if (!s) return fail(c, RS_EINVAL, "splits is NULL");
+    if (s->n_splits < 0) return fail(c, RS_EINVAL, "n_splits must be >= 0");
+    if (s->n_splits > 0 && (!s->split_offsets || !s->train_masks))
+        return fail(c, RS_EINVAL, "a required splits pointer is NULL");
+    if (s->n_splits > (int64_t)4096 * 4096) return fail(c, RS_EINVAL, "at most 16,777,216 splits per call");
+    return RS_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+rs_status rs_create(rs_ctx** out, int device, void* stream) {
+    if (!out) return RS_EINVAL;
+    *out = nullptr;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return RS_ECUDA;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return RS_ECUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return RS_EUNSUPPORTED;
+    rs_ctx* c = new (std::nothrow) rs_ctx;
+    if (!c) return RS_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    c->err[0] = 0;
+    e = cudaMalloc(&c->dstatus, RS_DST_INTS * sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return RS_ECUDA;
+    }
+    e = cudaMalloc(&c->scan, rs_rec_offsets_scratch_elems((int64_t)4096 * 4096) * sizeof(int64_t));
+    if (e != cudaSuccess) {
+        cudaFree(c->dstatus);
+        delete c;
+        return RS_ECUDA;
+    }
+    e = cudaMemset(c->dstatus, 0, RS_DST_INTS * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(c->dstatus);
+        cudaFree(c->scan);
+        delete c;
+        return RS_ECUDA;
+    }
+    *out = c;
+    return RS_OK;
+}
+
+rs_status rs_destroy(rs_ctx* c) {
+    if (!c) return RS_EINVAL;
+    cudaSetDevice(c->device);
+    cudaFree(c->dstatus);
+    cudaFree(c->scan);
+    delete c;
+    return RS_OK;
+}
+
+rs_status rs_set_stream(rs_ctx* c, void* stream) {
+    if (!c) return RS_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return RS_OK;
+}
+
+const char* rs_last_error(const rs_ctx* c) { return c ? c->err : "context is NULL"; }
+
+rs_status rs_check_device_status(rs_ctx* c) {
+    if (!c) return RS_EINVAL;
+    cudaSetDevice(c->device);
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, c->dstatus, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_check_device_status");
+    if (h[0] != 0) {
+        e = cudaMemsetAsync(c->dstatus, 0, 2 * sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rs_check_device_status");
+        if (h[0] == RS_EDATA) return fail(c, RS_EDATA, "program %d has fewer than 1 or more than 64 versions", h[1]);
+        if (h[0] == RS_ETIMEOUT) return fail(c, RS_ETIMEOUT, "a bounded device wait gave up (site %d)", h[1]);
+        return fail(c, (rs_status)h[0], "device status %d (detail %d)", h[0], h[1]);
+    }
+    return RS_OK;
+}
+
+rs_status rs_standardize(rs_ctx* c, const rs_batch* b, double* Z, double* mu, double* sigma) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, true);
+    if (s != RS_OK) return s;
+    if (!Z) return fail(c, RS_EINVAL, "Z is NULL");
+    if ((mu || sigma) && !b->feat_offsets) return fail(c, RS_EINVAL, "feat_offsets is NULL");
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_standardize(b, Z, mu, sigma, c->dstatus, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_standardize");
+}
+
+rs_status rs_gram(rs_ctx* c, const rs_batch* b, int precision, double* K) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, false);
+    if (s != RS_OK) return s;
+    if (!K) return fail(c, RS_EINVAL, "K is NULL");
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    if (precision == RS_GRAM_F64) e = rs_launch_gram_f64(b, K, c->dstatus, c->stream);
+    else if (precision == RS_GRAM_BF16X3) e = rs_launch_gram_bf16x3(b, K, c->dstatus, c->stream);
+    else return fail(c, RS_EINVAL, "precision must be RS_GRAM_F64 or RS_GRAM_BF16X3");
+    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "rs_gram: precision not built");
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_gram");
+}
+
+}  // extern "C"
+
+extern "C" {
+
+rs_status rs_rec_offsets(rs_ctx* c, const rs_batch* b, const rs_splits* sp, int64_t* ro) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, false);
+    if (s == RS_OK) s = check_splits(c, sp);
+    if (s != RS_OK) return s;
+    if (!ro) return fail(c, RS_EINVAL, "rec_offsets is NULL");
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_rec_offsets(b, sp, ro, c->scan, c->dstatus, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_rec_offsets");
+}
+
+static rs_status fit_common(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
+                            double lambda, int form, rs_fit_args& a) {
+    rs_status s = check_batch(c, b, false);
+    if (s == RS_OK) s = check_splits(c, sp);
+    if (s != RS_OK) return s;
+    if (!K) return fail(c, RS_EINVAL, "K is NULL");
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(c, RS_EINVAL, "lambda must be finite and >= 0");
+    if (form != RS_FORM_BATCHED && form != RS_FORM_PLAIN) return fail(c, RS_EINVAL, "bad form");
+    memset(&a, 0, sizeof(a));
+    a.P = b->n_programs;
+    a.row_offsets = b->row_offsets;
+    a.feat_width = b->feat_width;
+    a.x_offsets = b->x_offsets;
+    a.Z = (const double*)b->X;
+    a.masks = b->masks;
+    a.log_time = b->log_time;
+    a.K = K;
+    a.S = sp->n_splits;
+    a.split_offsets = sp->split_offsets;
+    a.train_masks = sp->train_masks;
+    a.lambda = lambda;
+    a.form = form;
+    a.dstatus = c->dstatus;
+    a.queue = (unsigned int*)(c->dstatus + RS_DST_QUEUE);
+    return RS_OK;
+}
+
+rs_status rs_fit_batched(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
+                         double lambda, int form, double* coef, uint8_t* fit_status) {
+    if (!c) return RS_EINVAL;
+    rs_fit_args a;
+    rs_status s = fit_common(c, b, K, sp, lambda, form, a);
+    if (s != RS_OK) return s;
+    a.coef_out = coef;
+    a.status_out = fit_status;
+    a.k = 1;
+    a.log_tau = 0.0;
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_fit_predict(a, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_fit_batched");
+}
+
+rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
+                          double lambda, const double* coef, int k, double tau, int flags,
+                          int form, const int64_t* rec_offsets, uint32_t* rec_code,
+                          double* rec_pred, double* pred_all, uint64_t* counters) {
+    if (!c) return RS_EINVAL;
+    rs_fit_args a;
+    rs_status s = fit_common(c, b, K, sp, lambda, form, a);
+    if (s != RS_OK) return s;
+    if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
+    if (flags & ~(RS_RANK_ALL | RS_REFINE_X)) return fail(c, RS_EINVAL, "unknown flag bits");
+    if (flags & RS_REFINE_X) return fail(c, RS_EUNSUPPORTED, "RS_REFINE_X is not built");
+    if (!rec_offsets || !rec_code) return fail(c, RS_EINVAL, "rec_offsets and rec_code are required");
+    a.coef_in = coef;
+    a.k = k;
+    a.log_tau = log(tau);   // host libm, the same call on both sides of any comparison
+    a.flags = flags;
+    a.rec_offsets = rec_offsets;
+    a.rec_code = rec_code;
+    a.rec_pred = rec_pred;
+    a.pred_all = pred_all;
+    a.counters = (unsigned long long*)counters;
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_fit_predict(a, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_predict_rank");
+}
+
+size_t rs_cv_workspace_bytes(const rs_batch* b) {
+    if (!b || b->n_programs < 1 || b->x_elems < 0) return 0;
+    size_t z = align256((size_t)b->x_elems * sizeof(double));
+    size_t k = align256((size_t)b->n_programs * RS_GRAM_LD * RS_GRAM_LD * sizeof(double));
+    return z + k + 256;
+}
+
+rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double lambda, int k,
+                     double tau, int flags, int precision, void* ws, size_t ws_bytes,
+                     int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
+                     double* pred_all, uint64_t* counters) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, true);
+    if (s != RS_OK) return s;
+    if (!ws) return fail(c, RS_EINVAL, "workspace is NULL");
+    if ((uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
+    const size_t need = rs_cv_workspace_bytes(b);
+    if (ws_bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    double* Z = (double*)ws;
+    double* K = (double*)((char*)ws + align256((size_t)b->x_elems * sizeof(double)));
+    s = rs_standardize(c, b, Z, nullptr, nullptr);
+    if (s != RS_OK) return s;
+    rs_batch zb = *b;
+    zb.X = Z;
+    zb.dtype = RS_F64;
+    s = rs_gram(c, &zb, precision, K);
+    if (s != RS_OK) return s;
+    s = rs_rec_offsets(c, &zb, sp, rec_offsets);
+    if (s != RS_OK) return s;
+    return rs_predict_rank(c, &zb, K, sp, lambda, nullptr, k, tau, flags, RS_FORM_BATCHED,
+                           rec_offsets, rec_code, rec_pred, pred_all, counters);
+}
+
+}  // extern "C"

@@ -1,0 +1,323 @@
+"""Python binding of the C ABI in ``include/rs.h`` (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/librs.so``.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is missing or the
+device is not a GB300 (sm_103), the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "_build", "librs.so")
+
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EUNSUPPORTED, RS_EDATA = range(7)
+RS_F32, RS_F64 = 0, 1
+RS_GRAM_F64, RS_GRAM_BF16X3 = 0, 1
+RS_FORM_BATCHED, RS_FORM_PLAIN = 0, 1
+RS_RANK_ALL, RS_REFINE_X = 1, 2
+NOPT = 6
+COEF_STRIDE = 33
+GRAM_LD = 64
+NCOUNTERS = 16
+
+# every symbol include/rs.h declares (tests check that the library exports all of them)
+EXPORTS = [
+    "rs_create", "rs_destroy", "rs_set_stream", "rs_last_error", "rs_check_device_status",
+    "rs_standardize", "rs_gram", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
+    "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak",
+]
+
+
+class RsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rs status {status}: {msg}")
+        self.status = status
+
+
+class _Batch(C.Structure):
+    _fields_ = [
+        ("n_programs", C.c_int32), ("dtype", C.c_int32), ("n_rows", C.c_int64),
+        ("max_versions", C.c_int32), ("max_feat", C.c_int32), ("x_elems", C.c_int64),
+        ("feat_total", C.c_int64), ("row_offsets", C.c_void_p), ("feat_width", C.c_void_p),
+        ("x_offsets", C.c_void_p), ("feat_offsets", C.c_void_p), ("X", C.c_void_p),
+        ("masks", C.c_void_p), ("log_time", C.c_void_p), ("cycles", C.c_void_p),
+    ]
+
+
+class _Splits(C.Structure):
+    _fields_ = [
+        ("n_splits", C.c_int64), ("max_train", C.c_int32), ("reserved", C.c_int32),
+        ("split_offsets", C.c_void_p), ("train_masks", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = SO):
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    i, d, i64 = C.c_int, C.c_double, C.c_int64
+    L.rs_create.argtypes = [C.POINTER(P), i, P]
+    L.rs_destroy.argtypes = [P]
+    L.rs_set_stream.argtypes = [P, P]
+    L.rs_last_error.argtypes = [P]
+    L.rs_last_error.restype = C.c_char_p
+    L.rs_check_device_status.argtypes = [P]
+    L.rs_standardize.argtypes = [P, P, P, P, P]
+    L.rs_gram.argtypes = [P, P, i, P]
+    L.rs_rec_offsets.argtypes = [P, P, P, P]
+    L.rs_fit_batched.argtypes = [P, P, P, P, d, i, P, P]
+    L.rs_predict_rank.argtypes = [P, P, P, P, d, P, i, d, i, i, P, P, P, P, P]
+    L.rs_cv_workspace_bytes.argtypes = [P]
+    L.rs_cv_workspace_bytes.restype = C.c_size_t
+    L.rs_cv_step.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
+    L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
+    for name in EXPORTS:
+        if name not in ("rs_last_error", "rs_cv_workspace_bytes"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class DeviceBatch:
+    """Device-resident copy of a ``synth.ProgramBatch`` (or of its standardized Z)."""
+    n_programs: int
+    dtype: int
+    n_rows: int
+    max_versions: int
+    max_feat: int
+    x_elems: int
+    feat_total: int
+    row_offsets: torch.Tensor
+    feat_width: torch.Tensor
+    x_offsets: torch.Tensor
+    feat_offsets: torch.Tensor
+    X: torch.Tensor
+    masks: torch.Tensor
+    log_time: torch.Tensor
+    cycles: Optional[torch.Tensor]
+
+    @staticmethod
+    def from_host(b, device="cuda") -> "DeviceBatch":
+        fo = np.zeros(b.n_programs + 1, dtype=np.int64)
+        fo[1:] = np.cumsum(b.feat_width.astype(np.int64))
+        dt = RS_F32 if b.X.dtype == np.float32 else RS_F64
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return DeviceBatch(
+            n_programs=b.n_programs, dtype=dt, n_rows=b.n_rows,
+            max_versions=int(np.diff(b.row_offsets).max()), max_feat=int(b.feat_width.max()),
+            x_elems=int(b.X.shape[0]), feat_total=int(fo[-1]),
+            row_offsets=t(b.row_offsets.astype(np.int64)), feat_width=t(b.feat_width.astype(np.int32)),
+            x_offsets=t(b.x_offsets.astype(np.int64)), feat_offsets=t(fo), X=t(b.X),
+            masks=t(b.masks.astype(np.uint8)), log_time=t(b.log_time.astype(np.float64)),
+            cycles=None if b.cycles is None else t(b.cycles.astype(np.float64)))
+
+    def with_X(self, Z: torch.Tensor) -> "DeviceBatch":
+        """The same batch with X replaced by a standardized Z (double)."""
+        d = dict(self.__dict__)
+        d["X"] = Z
+        d["dtype"] = RS_F64
+        return DeviceBatch(**d)
+
+    def c(self) -> _Batch:
+        return _Batch(self.n_programs, self.dtype, self.n_rows, self.max_versions, self.max_feat,
+                      self.x_elems, self.feat_total, _ptr(self.row_offsets), _ptr(self.feat_width),
+                      _ptr(self.x_offsets), _ptr(self.feat_offsets), _ptr(self.X),
+                      _ptr(self.masks), _ptr(self.log_time), _ptr(self.cycles))
+
+
+@dataclass
+class DeviceSplits:
+    n_splits: int
+    max_train: int
+    split_offsets: torch.Tensor
+    train_masks: torch.Tensor
+
+    @staticmethod
+    def from_host(s, device="cuda") -> "DeviceSplits":
+        tm = np.ascontiguousarray(s.train_masks, dtype=np.uint64)
+        mt = 0
+        if tm.size:
+            x = tm.copy()
+            cnt = np.zeros(tm.shape, dtype=np.int64)
+            for _ in range(64):
+                cnt += (x & np.uint64(1)).astype(np.int64)
+                x >>= np.uint64(1)
+            mt = int(cnt.max())
+        return DeviceSplits(
+            n_splits=int(tm.shape[0]), max_train=mt,
+            split_offsets=torch.from_numpy(np.ascontiguousarray(s.split_offsets, dtype=np.int64)).to(device),
+            train_masks=torch.from_numpy(tm.view(np.int64)).to(device))
+
+    def c(self) -> _Splits:
+        return _Splits(self.n_splits, self.max_train, 0, _ptr(self.split_offsets), _ptr(self.train_masks))
+
+
+class Context:
+    """An ``rs_ctx`` bound to one device and one CUDA stream (torch's current one by default)."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self.L = load()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        st = self.L.rs_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
+        if st != RS_OK:
+            raise RsError(st, "rs_create failed (is this an sm_103 GPU?)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != RS_OK:
+            raise RsError(st, self.L.rs_last_error(self.h).decode())
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self.L.rs_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def check_device_status(self):
+        self._check(self.L.rs_check_device_status(self.h))
+
+    # ---- entry points (same names as the C ABI) ------------------------------------------
+    def standardize(self, b: DeviceBatch, Z=None, mu=None, sigma=None):
+        if Z is None:
+            Z = torch.empty(b.x_elems, dtype=torch.float64, device=b.X.device)
+        bc = b.c()
+        self._check(self.L.rs_standardize(self.h, C.byref(bc), _ptr(Z), _ptr(mu), _ptr(sigma)))
+        return Z
+
+    def gram(self, zb: DeviceBatch, precision: int = RS_GRAM_F64, K=None):
+        if K is None:
+            K = torch.zeros(zb.n_programs * GRAM_LD * GRAM_LD, dtype=torch.float64, device=zb.X.device)
+        bc = zb.c()
+        self._check(self.L.rs_gram(self.h, C.byref(bc), precision, _ptr(K)))
+        return K
+
+    def rec_offsets(self, b: DeviceBatch, s: DeviceSplits, out=None):
+        if out is None:
+            out = torch.empty(s.n_splits + 1, dtype=torch.int64, device=b.X.device)
+        bc, sc = b.c(), s.c()
+        self._check(self.L.rs_rec_offsets(self.h, C.byref(bc), C.byref(sc), _ptr(out)))
+        return out
+
+    def fit_batched(self, zb: DeviceBatch, K, s: DeviceSplits, lam: float = 1e-3,
+                    form: int = RS_FORM_BATCHED, coef=None, fit_status=None):
+        bc, sc = zb.c(), s.c()
+        self._check(self.L.rs_fit_batched(self.h, C.byref(bc), _ptr(K), C.byref(sc), float(lam),
+                                          int(form), _ptr(coef), _ptr(fit_status)))
+        return coef, fit_status
+
+    def predict_rank(self, zb: DeviceBatch, K, s: DeviceSplits, rec_offsets, rec_code,
+                     lam: float = 1e-3, coef=None, k: int = 3, tau: float = 1.05, flags: int = 0,
+                     form: int = RS_FORM_BATCHED, rec_pred=None, pred_all=None, counters=None):
+        bc, sc = zb.c(), s.c()
+        self._check(self.L.rs_predict_rank(
+            self.h, C.byref(bc), _ptr(K), C.byref(sc), float(lam), _ptr(coef), int(k), float(tau),
+            int(flags), int(form), _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred),
+            _ptr(pred_all), _ptr(counters)))
+
+    def cv_workspace_bytes(self, b: DeviceBatch) -> int:
+        bc = b.c()
+        return int(self.L.rs_cv_workspace_bytes(C.byref(bc)))
+
+    def cv_step(self, b: DeviceBatch, s: DeviceSplits, workspace, rec_offsets, rec_code,
+                lam: float = 1e-3, k: int = 3, tau: float = 1.05, flags: int = 0,
+                precision: int = RS_GRAM_F64, rec_pred=None, pred_all=None, counters=None):
+        bc, sc = b.c(), s.c()
+        self._check(self.L.rs_cv_step(
+            self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags),
+            int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
+            _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
+
+
+def measure_fma_peak(f64: bool = True, iters: int = 4096) -> float:
+    """GFLOP/s of independent FMA chains over the whole device (FP64 or FP32)."""
+    L = load()
+    g = C.c_double(0.0)
+    st = L.rs_measure_fma_peak(1 if f64 else 0, int(iters), C.byref(g))
+    if st != RS_OK:
+        raise RsError(st, "rs_measure_fma_peak failed")
+    return g.value
+
+
+@dataclass
+class CVOutputs:
+    rec_offsets: torch.Tensor
+    rec_code: torch.Tensor
+    rec_pred: Optional[torch.Tensor]
+    pred_all: Optional[torch.Tensor]
+    counters: torch.Tensor
+
+
+def alloc_outputs(n_rows_total: int, n_splits: int, k: int, device="cuda", pred_all=True,
+                  rec_pred=True) -> CVOutputs:
+    return CVOutputs(
+        rec_offsets=torch.empty(n_splits + 1, dtype=torch.int64, device=device),
+        rec_code=torch.empty(n_rows_total, dtype=torch.int32, device=device),
+        rec_pred=torch.empty(n_rows_total * k, dtype=torch.float64, device=device) if rec_pred else None,
+        pred_all=torch.empty(n_rows_total * NOPT, dtype=torch.float64, device=device) if pred_all else None,
+        counters=torch.zeros(NCOUNTERS, dtype=torch.int64, device=device))
+
+
+def cv_run(ctx: Context, b: DeviceBatch, s: DeviceSplits, lam=1e-3, k=3, tau=1.05, flags=0,
+           precision=RS_GRAM_F64, form=RS_FORM_BATCHED, want_pred_all=True, want_Z=False):
+    """The whole pass through the individual entry points; returns host numpy outputs."""
+    dev = b.X.device
+    Z = torch.empty(b.x_elems, dtype=torch.float64, device=dev)
+    mu = torch.empty(b.feat_total, dtype=torch.float64, device=dev)
+    sg = torch.empty(b.feat_total, dtype=torch.float64, device=dev)
+    ctx.standardize(b, Z, mu, sg)
+    zb = b.with_X(Z)
+    K = ctx.gram(zb, precision)
+    ro = ctx.rec_offsets(zb, s)
+    R = int(ro[-1].item())
+    out = alloc_outputs(R, s.n_splits, k, dev, pred_all=want_pred_all)
+    out.rec_offsets = ro
+    ctx.predict_rank(zb, K, s, ro, out.rec_code, lam=lam, k=k, tau=tau, flags=flags, form=form,
+                     rec_pred=out.rec_pred, pred_all=out.pred_all, counters=out.counters)
+    torch.cuda.synchronize(dev)
+    ctx.check_device_status()
+    res = dict(rec_offsets=ro.cpu().numpy(), rec_code=out.rec_code.cpu().numpy().view(np.uint32),
+               rec_pred=out.rec_pred.cpu().numpy().reshape(R, k),
+               counters=out.counters.cpu().numpy().view(np.uint64), mu=mu.cpu().numpy(),
+               sigma=sg.cpu().numpy(), K=K)
+    if want_pred_all:
+        res["pred_all"] = out.pred_all.cpu().numpy().reshape(R, NOPT)
+    if want_Z:
+        res["Z"] = Z.cpu().numpy()
+    return res

@@ -1,0 +1,204 @@
+"""GPU parity: the sm_103a library (through its C ABI) against the FP64 CPU reference, on the
+same seeded inputs.  Element-wise at small sizes that still span many chunks, program
+changes and ragged tails; sampled at the full batched-CV size in the launch configuration
+the benchmark times."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1910_07776_gb300 import synth
+from parity import close, compare_counters, compare_rankings
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1910_07776_gb300 import build
+    build.build()
+    from paper_1910_07776_gb300 import rs as _rs
+    return _rs
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    c = rs.Context(0)
+    yield c
+    c.close()
+
+
+def _run_both(rs, ctx, batch, splits, lam=1e-3, k=3, tau=1.05, flags=0, form=0):
+    db = rs.DeviceBatch.from_host(batch)
+    ds = rs.DeviceSplits.from_host(splits)
+    g = rs.cv_run(ctx, db, ds, lam=lam, k=k, tau=tau, flags=flags, form=form, want_Z=True)
+    r = oracle.cv_batch(batch, splits, lam=lam, k=k, tau=tau, flags=flags)
+    return g, r
+
+
+def _check_cv(g, r, k, tau):
+    np.testing.assert_array_equal(g["rec_offsets"], r.rec_offsets)
+    err = close(g["pred_all"], r.pred_all)
+    ndiff, nnear = compare_rankings(g["rec_code"], r.rec_code, r.pred_all, math.log(tau))
+    same = g["rec_code"] == r.rec_code
+    close(g["rec_pred"][same], r.rec_pred[same])
+    compare_counters(g["counters"], r.counters, slack=nnear)
+    return err, ndiff
+
+
+# ------------------------------------------------------------------------------ A1 + A3
+@pytest.mark.parametrize("dtype,cycles", [(np.float64, False), (np.float32, True)])
+def test_standardize_and_gram(rs, ctx, dtype, cycles):
+    batch = synth.make_batch(5, versions=(1, 64), feat_choices=[24, 40, 96, 130], dtype=dtype,
+                             seed=21, with_cycles=cycles)
+    splits = synth.make_splits(batch, "half", 2, seed=21)
+    g, r = _run_both(rs, ctx, batch, splits)
+    close(g["Z"], r.Z, rel=1e-12, abs_=1e-12)
+    close(g["mu"], r.mu, rel=1e-13, abs_=1e-13)
+    close(g["sigma"], r.sigma, rel=1e-12, abs_=1e-14)
+    K = g["K"].cpu().numpy().reshape(-1, 64, 64)
+    for p in range(batch.n_programs):
+        V, F = batch.versions(p), int(batch.feat_width[p])
+        o = int(batch.x_offsets[p])
+        Zp = r.Z[o:o + V * F].reshape(V, F)
+        ref = Zp @ Zp.T
+        close(K[p, :V, :V], ref, rel=1e-12, abs_=1e-12 * F)
+        np.testing.assert_array_equal(K[p, :V, :V], K[p, :V, :V].T)
+
+
+# ------------------------------------------------------------------------------ A2..A6
+@pytest.mark.parametrize("form", [0, 1])
+def test_tiny_config_lovo_full(rs, ctx, form):
+    # 2 programs x 64 versions (all masks) x 96 FP64 features, leave-one-version-out:
+    # 128 fits of 6 ridge regressions, lambda 1e-3, top-3, threshold 1.05, seed 0
+    batch = synth.make_batch(2, versions=64, feat=96, dtype=np.float64, seed=0)
+    splits = synth.make_splits(batch, "lovo")
+    g, r = _run_both(rs, ctx, batch, splits, form=form)
+    err, ndiff = _check_cv(g, r, 3, 1.05)
+    assert r.counter("fit_ok") == 128 * 6
+    assert g["counters"][9] == 128 * 6
+    assert ndiff == 0
+
+
+@pytest.mark.parametrize("kind,k,flags,form", [
+    ("half", 3, 0, 0), ("frac", 6, 0, 0), ("frac", 2, 1, 0), ("half", 3, 0, 1), ("frac", 1, 1, 1)])
+def test_ragged_batches(rs, ctx, kind, k, flags, form):
+    batch = synth.make_batch(9, versions=(1, 64), feat_choices=[8, 33, 64], dtype=np.float32,
+                             seed=31 + k)
+    splits = synth.make_splits(batch, kind, 37, seed=5 + k)
+    g, r = _run_both(rs, ctx, batch, splits, k=k, flags=flags, form=form)
+    _check_cv(g, r, k, 1.05)
+
+
+def test_degenerate_splits(rs, ctx):
+    batch = synth.make_batch(3, versions=(30, 64), feat=16, seed=41)
+    S = 5
+    offs = np.arange(4, dtype=np.int64) * S
+    tm = []
+    for p in range(3):
+        V = batch.versions(p)
+        full = (1 << V) - 1 if V < 64 else (1 << 64) - 1
+        tm += [0, full, full & ~1, 1, 0b11]     # nothing, everything, one out, one, two
+    splits = synth.Splits(split_offsets=offs, train_masks=np.array(tm, dtype=np.uint64))
+    g, r = _run_both(rs, ctx, batch, splits)
+    _check_cv(g, r, 3, 1.05)
+
+
+def test_fit_batched_coefficients_and_status(rs, ctx):
+    batch = synth.make_batch(4, versions=(10, 64), feat=48, seed=51)
+    splits = synth.make_splits(batch, "frac", 40, seed=51)
+    r = oracle.cv_batch(batch, splits)
+    db, ds = rs.DeviceBatch.from_host(batch), rs.DeviceSplits.from_host(splits)
+    Z = ctx.standardize(db)
+    zb = db.with_X(Z)
+    K = ctx.gram(zb)
+    S = ds.n_splits
+    coef = torch.full((S * 6 * 33,), 7.0, dtype=torch.float64, device="cuda")
+    st = torch.full((S * 6,), 9, dtype=torch.uint8, device="cuda")
+    ctx.fit_batched(zb, K, ds, 1e-3, 0, coef, st)
+    ro = ctx.rec_offsets(zb, ds)
+    R = int(ro[-1])
+    out_a = rs.alloc_outputs(R, S, 3)
+    out_b = rs.alloc_outputs(R, S, 3)
+    ctx.predict_rank(zb, K, ds, ro, out_a.rec_code, rec_pred=out_a.rec_pred, pred_all=out_a.pred_all,
+                     counters=out_a.counters)
+    ctx.predict_rank(zb, K, ds, ro, out_b.rec_code, coef=coef, rec_pred=out_b.rec_pred,
+                     pred_all=out_b.pred_all, counters=out_b.counters)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(st.cpu().numpy().reshape(S, 6), r.fit_status)
+    # predicting from stored coefficients is the same arithmetic as the fused path
+    np.testing.assert_array_equal(out_a.pred_all.cpu().numpy(), out_b.pred_all.cpu().numpy())
+    np.testing.assert_array_equal(out_a.rec_code.cpu().numpy(), out_b.rec_code.cpu().numpy())
+    cf = coef.cpu().numpy().reshape(S, 6, 33)
+    ok = r.fit_status == 0
+    assert np.all(np.isnan(cf[~ok][:, 0])) and np.all(cf[~ok][:, 1:] == 0)
+    assert np.all(np.isfinite(cf[ok][:, 0]))
+    # the dual coefficients of a fit sum to zero (stationarity in the intercept)
+    sums = cf[ok][:, 1:].sum(axis=1)
+    assert np.abs(sums).max() < 1e-6 * max(1.0, np.abs(cf[ok][:, 1:]).max())
+
+
+def test_full_batched_cv_size_sampled(rs, ctx):
+    # 64 programs x U{16..64} versions x 256 FP32 features, 4096 random half splits each,
+    # through rs_cv_step (the single-call path the benchmark times); sampled splits are
+    # recomputed by the reference and compared row by row.
+    batch = synth.make_batch(64, versions=(16, 64), feat=256, dtype=np.float32, seed=0)
+    splits = synth.make_half_splits_fast(batch, 4096, seed=0)
+    db, ds = rs.DeviceBatch.from_host(batch), rs.DeviceSplits.from_host(splits)
+    ro = ctx.rec_offsets(db, ds)
+    R = int(ro[-1])
+    out = rs.alloc_outputs(R, ds.n_splits, 3)
+    ws = torch.empty(ctx.cv_workspace_bytes(db), dtype=torch.uint8, device="cuda")
+    ctx.cv_step(db, ds, ws, out.rec_offsets, out.rec_code, rec_pred=out.rec_pred,
+                pred_all=out.pred_all, counters=out.counters)
+    torch.cuda.synchronize()
+    ctx.check_device_status()
+    gro = out.rec_offsets.cpu().numpy()
+    ref_ro = oracle.rec_offsets(batch, splits)
+    np.testing.assert_array_equal(gro, ref_ro)
+    cnt = out.counters.cpu().numpy()
+    assert cnt[0] == R and cnt[9] + cnt[10] + cnt[11] + cnt[12] == 6 * ds.n_splits
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(ds.n_splits, size=48, replace=False))
+    prog = np.searchsorted(splits.split_offsets, pick, side="right") - 1
+    sub_off = np.zeros(batch.n_programs + 1, dtype=np.int64)
+    for p in prog:
+        sub_off[p + 1:] += 1
+    sub = synth.Splits(split_offsets=sub_off, train_masks=splits.train_masks[pick])
+    r = oracle.cv_batch(batch, sub)
+    rows = np.concatenate([np.arange(gro[i], gro[i + 1]) for i in pick])
+    pa = out.pred_all.cpu().numpy().reshape(R, 6)[rows]
+    code = out.rec_code.cpu().numpy().view(np.uint32)[rows]
+    close(pa, r.pred_all)
+    compare_rankings(code, r.rec_code, r.pred_all, math.log(1.05))
+
+
+def test_bad_program_size_is_reported(rs, ctx):
+    # a program with 65 rows: every kernel's own check skips it and flags RS_EDATA
+    batch = synth.make_batch(2, versions=64, feat=8, seed=61)
+    db = rs.DeviceBatch.from_host(batch)
+    db.row_offsets = torch.tensor([0, 65, 128], dtype=torch.int64, device="cuda")
+    ctx.standardize(db)
+    torch.cuda.synchronize()
+    with pytest.raises(rs.RsError) as e:
+        ctx.check_device_status()
+    assert e.value.status == rs.RS_EDATA
+    ctx.check_device_status()   # cleared
+
+
+def test_argument_errors(rs, ctx):
+    batch = synth.make_batch(1, versions=8, feat=8, seed=62)
+    db = rs.DeviceBatch.from_host(batch)
+    ds = rs.DeviceSplits.from_host(synth.make_splits(batch, "half", 2))
+    Z = ctx.standardize(db)
+    zb = db.with_X(Z)
+    K = ctx.gram(zb)
+    ro = ctx.rec_offsets(zb, ds)
+    code = torch.empty(int(ro[-1]), dtype=torch.int32, device="cuda")
+    for kw in (dict(k=0), dict(k=7), dict(tau=0.0), dict(lam=-1.0), dict(flags=64), dict(form=3)):
+        with pytest.raises(rs.RsError) as e:
+            ctx.predict_rank(zb, K, ds, ro, code, **kw)
+        assert e.value.status == rs.RS_EINVAL
