@@ -40,11 +40,13 @@ def make_inputs(seed):
     return b, s
 
 
-def algorithmic_flops(batch, splits):
-    """FP64 flops of the fit/predict kernel, counted from the definitions: per fit with n
+def algorithmic_flops(batch, splits, nreg=10):
+    """FP64 flops of the fit/predict path, counted from the definitions: per fit with n
     pairs a Cholesky (n^3/3), two right-hand sides through both triangular solves (4 n^2)
-    and the intercept / dual update (4 n); per prediction 2 n."""
+    and the intercept / dual update (4 n); per prediction 2 n.  Split into fits solved one
+    per thread (n <= nreg), fits solved one per warp (n > nreg) and predictions."""
     total_fit = 0.0
+    total_big = 0.0
     total_pred = 0.0
     for p in range(batch.n_programs):
         rs_ = batch.program_rows(p)
@@ -67,9 +69,11 @@ def algorithmic_flops(batch, splits):
             for _ in range(V):
                 cnt += (x & np.uint64(1)).astype(np.float64)
                 x = x >> np.uint64(1)
-            total_fit += float(np.sum(n ** 3 / 3 + 4 * n ** 2 + 4 * n))
+            fl = n ** 3 / 3 + 4 * n ** 2 + 4 * n
+            total_fit += float(np.sum(fl * (n <= nreg)))
+            total_big += float(np.sum(fl * (n > nreg)))
             total_pred += float(np.sum(2 * n * cnt * (n > 0)))
-    return total_fit + total_pred
+    return {"solve_small": total_fit, "solve_large": total_big, "rank": total_pred}
 
 
 class ClockSampler:
@@ -222,7 +226,9 @@ def main():
     out = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
     out.rec_offsets = ro
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    fws = ctx.workspace(ctx.fit_workspace_bytes(zb, ds))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ctx.profile_enable(True)
 
     def step():
         ev[0].record(stream)
@@ -233,7 +239,8 @@ def main():
         ctx.rec_offsets(zb, ds, out.rec_offsets)
         ev[3].record(stream)
         ctx.predict_rank(zb, K, ds, out.rec_offsets, out.rec_code, lam=CFG["lam"], k=CFG["k"],
-                         tau=CFG["tau"], rec_pred=out.rec_pred, counters=out.counters)
+                         tau=CFG["tau"], rec_pred=out.rec_pred, counters=out.counters,
+                         workspace=fws)
         ev[4].record(stream)
 
     def between():
@@ -251,6 +258,7 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     parts = np.zeros(4)
+    stages = {}
     tot = 0.0
     for _ in range(args.steps):
         between()
@@ -259,6 +267,8 @@ def main():
         d = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
         parts += d
         tot += ev[0].elapsed_time(ev[4])
+        for k_, v_ in ctx.profile_read().items():
+            stages[k_] = stages.get(k_, 0.0) + v_
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
@@ -280,7 +290,10 @@ def main():
 
     flops = algorithmic_flops(batch, splits)
     fit_ms = parts[3] / args.steps
-    achieved = flops / (fit_ms * 1e-3) / 1e12
+    stage_ms = {k_: v_ / args.steps for k_, v_ in stages.items()}
+    top = max(("solve_small", "solve_large", "rank"), key=lambda k_: stage_ms.get(k_, 0.0))
+    achieved = flops[top] / (stage_ms[top] * 1e-3) / 1e12
+    path_achieved = sum(flops.values()) / (fit_ms * 1e-3) / 1e12
     peak_meas = rs.measure_fma_peak(True, 2048) / 1e3
     peak = FP64_PEAK_NOMINAL_GFLOPS / 1e3
 
@@ -306,18 +319,21 @@ def main():
                    "l2": "flushed between timed steps (256 MB write, untimed)",
                    "parallelism": f"programs sharded, {world} GPU(s), no collective"},
         "kernels_ms": {"standardize": parts[0] / args.steps, "gram_f64": parts[1] / args.steps,
-                       "plan_rows": parts[2] / args.steps, "fit_predict_rank": fit_ms},
-        "roofline": {"bound": "alu", "kernel": "fit_predict_kernel", "achieved": achieved,
+                       "plan_rows": parts[2] / args.steps, "fit_predict_rank": fit_ms,
+                       **{"fit." + k_: v_ for k_, v_ in stage_ms.items()}},
+        "roofline": {"bound": "alu", "kernel": top, "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None,
-                     "peak_source": "nominal FP64 1.25 TFLOP/s: 152 SMs x 2 FMA/clk x 2.07 GHz",
-                     "peak_measured_fma_chains": peak_meas, "flops_per_launch": flops},
+                     "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                     "peak_measured_fma_chains": peak_meas, "flops_per_launch": flops[top],
+                     "fit_predict_path": {"flops": sum(flops.values()), "ms": fit_ms,
+                                          "achieved": path_achieved, "frac": path_achieved / peak}},
         "accuracy": acc,
         "plain_form": plain,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 11 * args.steps,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -408,7 +424,7 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
                         cycles=devb["cycles"])
     ds = rs.DeviceSplits(n_splits=splits.n_splits, max_train=64,
                          split_offsets=devb["split_offsets"], train_masks=devb["train_masks"])
-    ws = torch.empty(ctx.cv_workspace_bytes(db), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ctx.cv_workspace_bytes(db, ds), dtype=torch.uint8, device=dev)
     out = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
     h_code = torch.empty(R, dtype=torch.int32).pin_memory()
     h_pred = torch.empty(R * CFG["k"], dtype=torch.float64).pin_memory()

@@ -106,8 +106,9 @@ typedef struct {
 /* ---- context ------------------------------------------------------------------------
  * rs_create: binds a context to CUDA device `device` and the stream `cuda_stream`
  * (a cudaStream_t, NULL = legacy default stream).  Allocates 4 KiB of device memory for
- * the context's status word and queue heads, and 32 KiB for the row-planning scan.  Fails with RS_EUNSUPPORTED if the device
- * is not compute capability 10.3.  rs_destroy frees it (and any captured graphs).      */
+ * the context's status word and queue heads and 32 KiB for the row-planning scan.
+ * Fails with RS_EUNSUPPORTED if the device is not compute capability 10.3.
+ * rs_destroy frees them.                                                              */
 rs_status rs_create(rs_ctx** out, int device, void* cuda_stream);
 rs_status rs_destroy(rs_ctx* ctx);
 rs_status rs_set_stream(rs_ctx* ctx, void* cuda_stream);
@@ -117,6 +118,14 @@ const char* rs_last_error(const rs_ctx* ctx);
  * kernel met a program with more than 64 versions or more pairs than the hint allowed,
  * RS_ETIMEOUT when a bounded wait gave up.  Synchronises the context's stream.        */
 rs_status rs_check_device_status(rs_ctx* ctx);
+/* Stage timing (a tracing aid, not part of the method).  rs_profile_enable(ctx, 1) makes
+ * the batched fit/predict path record CUDA events on the context's stream around each of
+ * its six internal launches (pair tables, fit planning, bucketing, small solves, large
+ * solves, rank); rs_profile_read waits for the last event and writes the six stage
+ * durations in milliseconds of the most recent batched call into ms (at most max_stages;
+ * *n_stages = count).  RS_EINVAL if profiling is off.                                */
+rs_status rs_profile_enable(rs_ctx* ctx, int on);
+rs_status rs_profile_read(rs_ctx* ctx, float* ms, int max_stages, int* n_stages);
 
 /* ---- A1: feature vectors (Sec. 2) -----------------------------------------------------
  * Z[r][f] = (log(max(X[r][f] / cycles[r], 1e-30)) - mu_f) / sigma_f with mu_f, sigma_f the
@@ -152,38 +161,48 @@ rs_status rs_rec_offsets(rs_ctx* ctx, const rs_batch* batch, const rs_splits* sp
  * intercept, solved in dual form from the Gram block K with an FP64 Cholesky:
  * beta = sum_a alpha_a z_a.
  * coef (nullable): double [S][6][33] = b, then alpha for the training pairs in ascending
- * order of their before-version slot (zeros after n).  fit_status (nullable): uint8
- * [S][6] RS_FIT_*.  lambda >= 0.  form: RS_FORM_BATCHED or RS_FORM_PLAIN.            */
+ * order of their before-version slot (zeros after n); b is NaN when the fit is not OK.
+ * fit_status (nullable): uint8 [S][6] RS_FIT_*.  lambda >= 0 (at lambda = 0 the dual
+ * system is the minimum-norm interpolant when n <= F).
+ * form: RS_FORM_BATCHED (fits of the whole batch sorted by size, one thread per fit up to
+ * 10 pairs, one warp per larger fit) or RS_FORM_PLAIN (one warp per fit, per chunk).
+ * workspace: caller-owned device scratch of at least rs_fit_workspace_bytes(std, splits)
+ * bytes, 256-byte aligned, required by the batched form (may be NULL for the plain form);
+ * its contents are undefined after the call.  RS_ENOMEM if it is too small.  A fit with
+ * more pairs than splits->max_train / 2 (a wrong hint) is treated as empty and the device
+ * status reports RS_EDATA.                                                            */
+size_t rs_fit_workspace_bytes(const rs_batch* std, const rs_splits* splits);
 rs_status rs_fit_batched(rs_ctx* ctx, const rs_batch* std, const double* K,
-                         const rs_splits* splits, double lambda, int form, double* coef,
-                         uint8_t* fit_status);
+                         const rs_splits* splits, double lambda, int form, void* workspace,
+                         size_t workspace_bytes, double* coef, uint8_t* fit_status);
 
 /* ---- A4 + A5 + A6: fit, predict, rank, threshold, score (Sec. 2 tier 3, Sec. 5, 6) -----
  * For every test row t of every split: one predicted log speedup per candidate
- * optimization (those not in t's mask; all six with RS_RANK_ALL), from the split's fits;
- * candidates sorted by prediction (ties: lower index first), kept if >= log(tau), at most
- * k (1..6) reported.  Fits are recomputed in the same launch unless coef (from
- * rs_fit_batched with the same inputs) is given.
+ * optimization (those not in t's mask; all six with RS_RANK_ALL), b + sum_a alpha_a
+ * K[t][v_a] from the split's fit; candidates sorted by prediction (ties: lower index
+ * first), kept if >= log(tau), at most k (1..6) reported.  The fits are computed in the
+ * same call (as rs_fit_batched with the same form and workspace rules) unless coef, from
+ * rs_fit_batched with the same inputs, is given; then no workspace is needed.
  * rec_offsets: from rs_rec_offsets.  Outputs per row (R = rec_offsets[S]):
  *   rec_code  uint32 [R]: bits 0-3 = count c, bits 4+4i..7+4i = i-th optimization (0xF unused)
  *   rec_pred  double [R][k]: predicted log speedups of the reported list (NaN unused), nullable
  *   pred_all  double [R][6]: every prediction (NaN where none), nullable
  *   counters  uint64 [16]: accuracy counters (listed above), added to; nullable
- * flags: RS_RANK_ALL, RS_REFINE_X (refine each dual solve once with residuals computed
- * through Z in FP64 and predict through Z; for Gram blocks made with RS_GRAM_BF16X3).
- * lambda as in rs_fit_batched; tau > 0; form as in rs_fit_batched.                   */
+ * flags: RS_RANK_ALL; RS_REFINE_X is reserved (RS_EUNSUPPORTED).  tau > 0.             */
 rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
                           const rs_splits* splits, double lambda, const double* coef,
-                          int k, double tau, int flags, int form,
-                          const int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
-                          double* pred_all, uint64_t* counters);
+                          int k, double tau, int flags, int form, void* workspace,
+                          size_t workspace_bytes, const int64_t* rec_offsets,
+                          uint32_t* rec_code, double* rec_pred, double* pred_all,
+                          uint64_t* counters);
 
 /* ---- the whole step in one call ---------------------------------------------------------
  * rs_cv_step runs A1..A6 on raw counters: standardize into workspace, Gram (precision as
- * given), plan rows into rec_offsets, then fit/predict/rank.  workspace: device memory of
- * at least rs_cv_workspace_bytes(batch) bytes, 256-byte aligned, owned by the caller and
- * used as scratch (Z and the Gram blocks).  Outputs as in rs_predict_rank.            */
-size_t rs_cv_workspace_bytes(const rs_batch* batch);
+ * given), plan rows into rec_offsets, then the batched fit/predict/rank.  workspace:
+ * device memory of at least rs_cv_workspace_bytes(batch, splits) bytes, 256-byte
+ * aligned, owned by the caller and used as scratch (Z, the Gram blocks and the fit
+ * workspace).  Outputs as in rs_predict_rank.                                          */
+size_t rs_cv_workspace_bytes(const rs_batch* batch, const rs_splits* splits);
 rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
                      double lambda, int k, double tau, int flags, int precision,
                      void* workspace, size_t workspace_bytes, int64_t* rec_offsets,

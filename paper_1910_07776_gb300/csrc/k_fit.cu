@@ -1,64 +1,70 @@
 // K3 + K4: batched ridge fits, predictions, ranking and scoring (Sec. 2 tiers 2 and 3,
 // Sec. 3.3 pairs, Sec. 3.4 regression family, Sec. 5 protocol, Sec. 6 / Table 3 metric).
 //
-// Work unit: a chunk of up to kChunk consecutive splits of one program.  A persistent grid
-// pulls chunks from an atomic queue; the program's Gram block, masks, log times and pair
-// lists are staged in shared memory once per program change.
-//
 // Fit (per split s and optimization j): the n training pairs are the pairs (v, v|j) with
-// both versions in the train mask.  With the Gram block K (uncentred), the ridge problem
-// with an unpenalised intercept is the bordered system
-//       (K_TT + lambda I) alpha + b 1 = y,      1^T alpha = 0,
+// both versions in the train mask (Sec. 3.3); a pair carries the feature vector of v and
+// the label log t(v) - log t(v|j) (Sec. 5).  With the per-program Gram block K
+// (uncentred), ridge with an unpenalised intercept is the bordered system
+//       (K_TT + lambda I) alpha + b 1 = y,      1^T alpha = 0
 // (stationarity in beta = sum_a alpha_a z_a and in b).  With M = K_TT + lambda I = L L^T
-// (FP64 Cholesky): u = M^-1 y, w = M^-1 1, b = 1^T u / 1^T w, alpha = u - b w; the
-// prediction for a test version t is b + sum_a alpha_a K[t][v_a] = b + z_t . beta.
+// (FP64 Cholesky): u = M^-1 y, w = M^-1 1, b = 1^T u / 1^T w, alpha = u - b w.  The
+// prediction for a test version t is b + sum_a alpha_a K[t][v_a] (= b + z_t . beta).
 //
-// The FP64 pipe of this part is narrow, so the kernel keeps its FP64 lanes busy:
-//   - batched form: fits with n <= SMALL are solved one per thread; fits are sorted by n
-//     (descending) so a warp's 32 fits have nearly the same size; each lane's packed
-//     triangle lives in shared memory interleaved across lanes (conflict-free);
-//   - larger fits (and every fit in the plain form) are solved one per warp, lanes = rows.
-// Predict/rank: one thread per (split, test row): six dot products over the fit's pairs,
-// an insertion sort of at most six keys, threshold, top-k, counters.
+// This part's FP64 pipe is narrow: one FP64 warp instruction holds an SM sub-partition's
+// FP64 unit for many cycles whatever the number of active lanes.  So the batched form
+// never lets fits of different sizes share a warp:
+//   pairs  -> per program and optimization, the before/after version pairs and labels;
+//   plan   -> per fit, the mask of its training pairs and its size n; histogram of n;
+//   bucket -> a counting sort of all fits of the batch by n;
+//   solve  -> n <= kNReg: one fit per thread, fully unrolled for that n, registers only;
+//             n >  kNReg: one fit per warp, lanes = matrix rows;
+//   rank   -> per chunk of splits of one program: predictions, sort, threshold, top-k,
+//             scores; comparisons on order-preserving integer keys (no FP64 compares).
+// Reciprocal square roots of the pivots come from an FP32 seed refined by two Newton
+// steps in FP64 (fewer FP64 instructions than a division and a square root).
+// The plain form solves every fit with one warp inside the rank kernel (no bucketing).
 #include <math.h>
 
 #include "rs_internal.cuh"
 
 namespace {
 
-constexpr int kChunk = 16;
+constexpr int kChunk = 16;                  // splits per work item of the rank kernel
 constexpr int kFits = kChunk * RS_NOPT;
-constexpr int kKld = RS_MAXV + 1;   // padded row stride of the Gram block in shared memory
+constexpr int kKld = RS_MAXV + 1;           // padded row stride of K in shared memory
+constexpr int kNReg = 10;                   // largest n solved by one thread in registers
+constexpr int kHist = RS_MAXPAIRS + 2;      // n = 0..32, plus one end slot
+constexpr long long kNaNBits = 0x7ff8000000000000ll;
 
 __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
 
-template <int WARPS, int SMALL>
-struct FitSmem {
-    static constexpr int kLaneNeed = tri(SMALL) + 2 * SMALL;         // L, 1/diag, w
-    static constexpr int kPoolSmall = kLaneNeed * 32;
-    static constexpr int kPoolLarge = 32 * 33;
-    static constexpr int kPool = kPoolSmall > kPoolLarge ? kPoolSmall : kPoolLarge;
-    double K[RS_MAXV * kKld];
-    double lt[RS_MAXV];
-    double ylab[RS_NOPT][RS_MAXPAIRS];
-    double coef[kFits][RS_COEF_STRIDE];
-    double pool[WARPS][kPool];
-    uint64_t tmask[kChunk];
-    uint32_t pmask[kFits];
-    int row_base[kChunk + 1];
-    int npair[RS_NOPT];
-    int16_t small_list[kFits];
-    int16_t large_list[kFits];
-    uint8_t nfit[kFits];
-    uint8_t status[kFits];
-    uint8_t pair_b[RS_NOPT][RS_MAXPAIRS];
-    uint8_t pair_a[RS_NOPT][RS_MAXPAIRS];
-    uint8_t vidx[WARPS][32][RS_MAXPAIRS];
-    uint8_t msk[RS_MAXV];
-    int8_t slot_of[RS_MAXV];
-    int n_small, n_large;
-    int cur_prog, V, item, prog_ok;
-};
+__device__ __forceinline__ double nan_d() { return __longlong_as_double(kNaNBits); }
+
+// x > 0 and finite, decided on the bit pattern (no FP64 instruction).
+__device__ __forceinline__ bool pos_finite(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+// Order-preserving integer key of a non-NaN double; -0.0 and +0.0 share key 0.
+__device__ __forceinline__ long long okey(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// 1/sqrt(d) for a positive finite d: FP32 seed, then two Newton steps of r <- r (3 - d r^2) / 2
+// (Newton's method on f(r) = r^-2 - d).  Outside the float range: plain division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);
+    const double hd = 0.5 * d;
+    double r = (double)rsqrtf((float)d);
+    r = r * fma(-hd, r * r, 1.5);
+    r = r * fma(-hd, r * r, 1.5);
+    return r;
+}
 
 // The a-th set bit (0-based) of x; x must have more than a set bits.
 __device__ __forceinline__ int select_bit(uint64_t x, int a) {
@@ -66,75 +72,294 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
     return __ffsll((long long)x) - 1;
 }
 
-// ------------------------------------------------------------------ one fit per thread
-// Packed lower triangle L (row-major), reciprocal diagonal and w live at reg[e * 32].
-// u (then alpha) lives in coef[1..n]; coef[0] receives b.
-template <int SMALL>
-__device__ int fit_thread(int n, const uint8_t* vlist, const double* K, double lambda,
-                          double* reg, double* coef) {
-    double* L = reg;
-    double* rinv = reg + tri(SMALL) * 32;
-    double* w = rinv + SMALL * 32;
-    for (int i = 0; i < n; ++i) {
-        const int vi = vlist[i];
-        const int ti = tri(i);
+// ====================================================================== pair tables
+// One block per program: the before/after pairs of each optimization in ascending order of
+// the before slot, and their labels.  Tables: [P][6][32] (u8, u8, double), counts [P][6].
+__global__ void __launch_bounds__(64)
+pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restrict__ masks,
+             const double* __restrict__ log_time, uint8_t* pb, uint8_t* pa, double* ylab,
+             int* npair, int* dstatus) {
+    __shared__ int8_t slot_of[RS_MAXV];
+    __shared__ uint8_t msk[RS_MAXV];
+    __shared__ double lt[RS_MAXV];
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const int64_t r0 = row_off[p];
+    const int V = (int)(row_off[p + 1] - r0);
+    if (V < 1 || V > RS_MAXV) {
+        if (tid < RS_NOPT) npair[p * RS_NOPT + tid] = 0;
+        if (tid == 0) rs_dev_flag(dstatus, RS_EDATA, p);
+        return;
+    }
+    slot_of[tid] = -1;
+    if (tid < V) {
+        msk[tid] = masks[r0 + tid] & 63;
+        lt[tid] = log_time[r0 + tid];
+    }
+    __syncthreads();
+    if (tid < V) slot_of[msk[tid]] = (int8_t)tid;
+    __syncthreads();
+    if (tid < RS_NOPT) {
+        const int j = tid;
+        const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+        int np = 0;
+        for (int v = 0; v < V; ++v) {
+            const int m = msk[v];
+            if ((m >> j) & 1) continue;
+            const int w = slot_of[m | (1 << j)];
+            if (w < 0) continue;
+            if (np == RS_MAXPAIRS) {      // only possible with repeated masks
+                rs_dev_flag(dstatus, RS_EDATA, p);
+                break;
+            }
+            pb[base + np] = (uint8_t)v;
+            pa[base + np] = (uint8_t)w;
+            ylab[base + np] = lt[v] - lt[w];
+            ++np;
+        }
+        npair[p * RS_NOPT + j] = np;
+    }
+}
+
+// ====================================================================== plan
+__global__ void __launch_bounds__(256)
+plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __restrict__ split_off,
+                 const uint64_t* __restrict__ tm, int64_t S, const uint8_t* __restrict__ pb,
+                 const uint8_t* __restrict__ pa, const int* __restrict__ npair, uint32_t* fit_pm,
+                 uint8_t* fit_n, unsigned* hist, int nmax, int* dstatus) {
+    __shared__ unsigned h[kHist];
+    if (threadIdx.x < kHist) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < S * RS_NOPT) {
+        const int64_t s = f / RS_NOPT;
+        const int j = (int)(f - s * RS_NOPT);
+        const int p = rs_find_segment(split_off, P, s);
+        const int V = (int)(row_off[p + 1] - row_off[p]);
+        uint32_t pm = 0;
+        if (V >= 1 && V <= RS_MAXV) {
+            const uint64_t T = tm[s] & rs_full_mask(V);
+            const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+            const int np = npair[p * RS_NOPT + j];
+            for (int q = 0; q < np; ++q)
+                if (((T >> pb[base + q]) & 1) && ((T >> pa[base + q]) & 1)) pm |= 1u << q;
+        }
+        int n = __popc(pm);
+        if (n > nmax) {            // more pairs than the workspace was sized for
+            rs_dev_flag(dstatus, RS_EDATA, -2);
+            pm = 0;
+            n = 0;
+        }
+        fit_pm[f] = pm;
+        fit_n[f] = (uint8_t)n;
+        atomicAdd(&h[n], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kHist && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// Bucket starts from the histogram: positions of fits with n >= 1 ordered by n, and the
+// offsets of their compact coefficient records (n + 1 doubles each).
+__device__ __forceinline__ void bucket_tables(const unsigned* hist, long long* start, long long* cstart) {
+    long long acc = 0, cacc = 0;
+    start[0] = 0;
+    cstart[0] = 0;
+    for (int n = 1; n <= RS_MAXPAIRS; ++n) {
+        start[n] = acc;
+        cstart[n] = cacc;
+        acc += hist[n];
+        cacc += (long long)hist[n] * (n + 1);
+    }
+    start[RS_MAXPAIRS + 1] = acc;
+    cstart[RS_MAXPAIRS + 1] = cacc;
+}
+
+// ====================================================================== bucket
+__global__ void __launch_bounds__(256)
+bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
+                   unsigned* cursor, int* order, int64_t* fit_off, uint8_t* status, double* coef_user,
+                   unsigned long long* counters) {
+    __shared__ long long start[kHist], cstart[kHist];
+    if (threadIdx.x == 0) bucket_tables(hist, start, cstart);
+    __syncthreads();
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned empty = 0;
+    if (f < S6) {
+        const int n = fit_n[f];
+        if (n == 0) {
+            fit_off[f] = -1;
+            status[f] = RS_FIT_EMPTY;
+            empty = 1;
+            if (coef_user) {
+                double* o = coef_user + f * RS_COEF_STRIDE;
+                o[0] = nan_d();
+                for (int e = 1; e < RS_COEF_STRIDE; ++e) o[e] = 0.0;
+            }
+        } else {
+            const long long pos = start[n] + atomicAdd(&cursor[n], 1u);
+            order[pos] = (int)f;
+            fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
+        }
+    }
+    if (counters) {
+        const unsigned e = __reduce_add_sync(0xffffffffu, empty);
+        if ((threadIdx.x & 31) == 0 && e) atomicAdd(counters + 10, (unsigned long long)e);
+    }
+}
+
+// ====================================================================== solve, n <= kNReg
+template <int N>
+__device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
+                                           const double* __restrict__ yl, uint32_t pm, double lambda,
+                                           double* out) {
+    int vb[N];
+    double u[N], w[N], L[tri(N)], ri[N];
+    uint32_t x = pm;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        const int q = __ffs(x) - 1;
+        x &= x - 1;
+        vb[a] = pb[q];
+        u[a] = yl[q];
+        w[a] = 1.0;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
         for (int k = 0; k <= i; ++k) {
-            double s = K[vi * kKld + vlist[k]];
+            double s = __ldg(Kp + vb[i] * RS_GRAM_LD + vb[k]);
             if (k == i) s += lambda;
-            const int tk = tri(k);
-            for (int m = 0; m < k; ++m) s = fma(-L[(ti + m) * 32], L[(tk + m) * 32], s);
+#pragma unroll
+            for (int m = 0; m < k; ++m) s = fma(-L[tri(i) + m], L[tri(k) + m], s);
             if (k < i) {
-                L[(ti + k) * 32] = s * rinv[k * 32];
+                L[tri(i) + k] = s * ri[k];
             } else {
-                if (!(s > 0.0)) return RS_FIT_NOTPD;
-                const double d = sqrt(s);
-                L[(ti + i) * 32] = d;
-                rinv[i * 32] = 1.0 / d;
+                if (!pos_finite(s)) return RS_FIT_NOTPD;
+                ri[i] = rsqrt_newton(s);
             }
         }
     }
-    double* u = coef + 1;   // holds y on entry
-    for (int i = 0; i < n; ++i) {
-        const int ti = tri(i);
-        double su = u[i], sw = 1.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {          // L t = rhs (two right-hand sides)
+#pragma unroll
         for (int k = 0; k < i; ++k) {
-            const double l = L[(ti + k) * 32];
-            su = fma(-l, u[k], su);
-            sw = fma(-l, w[k * 32], sw);
+            u[i] = fma(-L[tri(i) + k], u[k], u[i]);
+            w[i] = fma(-L[tri(i) + k], w[k], w[i]);
         }
-        u[i] = su * rinv[i * 32];
-        w[i * 32] = sw * rinv[i * 32];
+        u[i] *= ri[i];
+        w[i] *= ri[i];
     }
-    for (int i = n - 1; i >= 0; --i) {
-        double su = u[i], sw = w[i * 32];
-        for (int k = i + 1; k < n; ++k) {
-            const double l = L[(tri(k) + i) * 32];
-            su = fma(-l, u[k], su);
-            sw = fma(-l, w[k * 32], sw);
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {     // L^T x = t
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) {
+            u[i] = fma(-L[tri(k) + i], u[k], u[i]);
+            w[i] = fma(-L[tri(k) + i], w[k], w[i]);
         }
-        u[i] = su * rinv[i * 32];
-        w[i * 32] = sw * rinv[i * 32];
+        u[i] *= ri[i];
+        w[i] *= ri[i];
     }
     double su = 0.0, sw = 0.0;
-    for (int i = 0; i < n; ++i) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
         su += u[i];
-        sw += w[i * 32];
+        sw += w[i];
     }
     const double b = su / sw;
-    bool finite = isfinite(b);
-    for (int i = 0; i < n; ++i) {
-        const double a = fma(-b, w[i * 32], u[i]);
-        u[i] = a;
-        finite = finite && isfinite(a);
+    bool fin = finite_bits(b);
+    out[0] = b;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double al = fma(-b, w[i], u[i]);
+        fin = fin && finite_bits(al);
+        out[1 + i] = al;
     }
-    coef[0] = b;
-    return finite ? RS_FIT_OK : RS_FIT_NONFINITE;
+    return fin ? RS_FIT_OK : RS_FIT_NONFINITE;
 }
 
-// ------------------------------------------------------------------ one fit per warp
-// Lane a owns row a (a < n <= 32).  Lsh: [32][33] doubles.  Returns a warp-uniform status.
+struct SolveArgs {
+    int P;
+    const int64_t* split_off;
+    const double* K;
+    const uint8_t* pb;
+    const double* ylab;
+    const uint32_t* fit_pm;
+    const uint8_t* fit_n;
+    const int* order;
+    const unsigned* hist;
+    const int64_t* fit_off;
+    double* coef;         // compact records, or the caller's [S][6][33] array
+    int coef_user;
+    uint8_t* status;
+    double lambda;
+    unsigned long long* counters;
+};
+
+__device__ __forceinline__ void finish_record(const SolveArgs& a, int64_t f, int n, int st, double* out) {
+    if (st != RS_FIT_OK) {
+        out[0] = nan_d();
+        for (int e = 1; e <= n; ++e) out[e] = 0.0;
+    }
+    if (a.coef_user)
+        for (int e = n + 1; e < RS_COEF_STRIDE; ++e) out[e] = 0.0;
+    a.status[f] = (uint8_t)st;
+}
+
+__device__ __forceinline__ void count_status(const SolveArgs& a, int st, bool active) {
+    if (!a.counters) return;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned ok = __reduce_add_sync(0xffffffffu, active && st == RS_FIT_OK);
+    const unsigned np = __reduce_add_sync(0xffffffffu, active && st == RS_FIT_NOTPD);
+    const unsigned nf = __reduce_add_sync(0xffffffffu, active && st == RS_FIT_NONFINITE);
+    if (lane == 0) {
+        if (ok) atomicAdd(a.counters + 9, (unsigned long long)ok);
+        if (np) atomicAdd(a.counters + 11, (unsigned long long)np);
+        if (nf) atomicAdd(a.counters + 12, (unsigned long long)nf);
+    }
+}
+
+__global__ void __launch_bounds__(128)
+solve_small_kernel(const SolveArgs a) {
+    __shared__ long long start[kHist], cstart[kHist];
+    if (threadIdx.x == 0) bucket_tables(a.hist, start, cstart);
+    __syncthreads();
+    const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = pos < start[kNReg + 1];
+    int st = RS_FIT_OK;
+    if (active) {
+        int n = 1;
+        while (start[n + 1] <= pos) ++n;
+        const int64_t f = a.order[pos];
+        const int64_t s = f / RS_NOPT;
+        const int j = (int)(f - s * RS_NOPT);
+        const int p = rs_find_segment(a.split_off, a.P, s);
+        const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+        const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+        const uint32_t pm = a.fit_pm[f];
+        double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
+        const uint8_t* pb = a.pb + base;
+        const double* yl = a.ylab + base;
+        switch (n) {
+            case 1: st = solve_fixed<1>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 2: st = solve_fixed<2>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 3: st = solve_fixed<3>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 4: st = solve_fixed<4>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 5: st = solve_fixed<5>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 6: st = solve_fixed<6>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 7: st = solve_fixed<7>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 8: st = solve_fixed<8>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 9: st = solve_fixed<9>(Kp, pb, yl, pm, a.lambda, out); break;
+            default: st = solve_fixed<10>(Kp, pb, yl, pm, a.lambda, out); break;
+        }
+        finish_record(a, f, n, st, out);
+    }
+    count_status(a, st, active);
+}
+
+// ====================================================================== solve, one fit per warp
+// Lane a owns row a (a < n <= 32).  K is read with leading dimension ld.  Lsh: [32][33].
+// Writes b to coef[0] and alpha to coef[1..n]; returns a warp-uniform status.
 __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double* ylab,
-                        const double* K, double lambda, double* Lsh, double* coef) {
+                        const double* K, int ld, double lambda, double* Lsh, double* coef) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < n;
     int v = 0;
@@ -149,20 +374,15 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
         const int vj = __shfl_sync(0xffffffffu, v, jj);
         double s = 0.0;
         if (act && lane >= jj) {
-            s = K[v * kKld + vj];
+            s = K[v * ld + vj];
             if (lane == jj) s += lambda;
             for (int m = 0; m < jj; ++m) s = fma(-Lsh[lane * 33 + m], Lsh[jj * 33 + m], s);
         }
         const double d = __shfl_sync(0xffffffffu, s, jj);
-        if (!(d > 0.0)) return RS_FIT_NOTPD;
-        const double ljj = sqrt(d);
-        const double r = 1.0 / ljj;
-        if (lane == jj) {
-            Lsh[jj * 33 + jj] = ljj;
-            rinv = r;
-        } else if (act && lane > jj) {
-            Lsh[lane * 33 + jj] = s * r;
-        }
+        if (!pos_finite(d)) return RS_FIT_NOTPD;
+        const double r = rsqrt_newton(d);
+        if (lane == jj) rinv = r;
+        else if (act && lane > jj) Lsh[lane * 33 + jj] = s * r;
         __syncwarp();
     }
     double u = y, w = act ? 1.0 : 0.0;
@@ -199,18 +419,74 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
         sw += __shfl_xor_sync(0xffffffffu, sw, o);
     }
     const double b = su / sw;
-    const double a = fma(-b, w, u);
-    const int fin = __all_sync(0xffffffffu, !act || isfinite(a)) && isfinite(b);
-    if (act) coef[1 + lane] = a;
+    const double al = fma(-b, w, u);
+    const int fin = __all_sync(0xffffffffu, !act || finite_bits(al)) && finite_bits(b);
+    if (act) coef[1 + lane] = al;
     if (lane == 0) coef[0] = b;
     __syncwarp();
     return fin ? RS_FIT_OK : RS_FIT_NONFINITE;
 }
 
-template <int WARPS, int SMALL>
-__global__ void __launch_bounds__(WARPS * 32, 1)
-fit_predict_kernel(const rs_fit_args a) {
-    using Sm = FitSmem<WARPS, SMALL>;
+constexpr int kLargeWarps = 4;
+
+__global__ void __launch_bounds__(kLargeWarps * 32)
+solve_large_kernel(const SolveArgs a) {
+    __shared__ long long start[kHist], cstart[kHist];
+    __shared__ double Lsh[kLargeWarps][32 * 33];
+    if (threadIdx.x == 0) bucket_tables(a.hist, start, cstart);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long first = start[kNReg + 1], end = start[RS_MAXPAIRS + 1];
+    for (long long pos = first + (long long)blockIdx.x * kLargeWarps + warp; pos < end;
+         pos += (long long)gridDim.x * kLargeWarps) {
+        int n = kNReg + 1;
+        while (start[n + 1] <= pos) ++n;
+        const int64_t f = a.order[pos];
+        const int64_t s = f / RS_NOPT;
+        const int j = (int)(f - s * RS_NOPT);
+        const int p = rs_find_segment(a.split_off, a.P, s);
+        const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+        const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+        double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
+        const int st = fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
+                                a.lambda, Lsh[warp], out);
+        if (lane == 0) finish_record(a, f, n, st, out);
+        if (a.counters && lane == 0) atomicAdd(a.counters + (st == RS_FIT_OK ? 9 : st == RS_FIT_NOTPD ? 11 : 12), 1ull);
+        __syncwarp();
+    }
+}
+
+// ====================================================================== predict / rank
+template <int WARPS, bool FIT>
+struct RankSmem {
+    static constexpr int kPool = FIT ? 32 * 33 : 1;
+    double K[RS_MAXV * kKld];
+    double lt[RS_MAXV];
+    double ylab[RS_NOPT][RS_MAXPAIRS];
+    double coef[kFits][RS_COEF_STRIDE];
+    double pool[WARPS][kPool];
+    long long act_key[RS_MAXV][RS_NOPT];
+    uint64_t tmask[kChunk];
+    uint32_t pmask[kFits];
+    int row_base[kChunk + 1];
+    int npair[RS_NOPT];
+    uint8_t nfit[kFits];
+    uint8_t status[kFits];
+    uint8_t known[RS_MAXV];
+    uint8_t pair_b[RS_NOPT][RS_MAXPAIRS];
+    uint8_t msk[RS_MAXV];
+    int8_t slot_of[RS_MAXV];
+    int cur_prog, V, item, prog_ok;
+};
+
+// FIT = true: the plain form, every fit solved here by one warp.  FIT = false: the
+// coefficients come from coef_in (compact records at coef_off, or the caller's
+// [S][6][33] layout) and the statuses from status_in (or from whether b is finite).
+template <int WARPS, bool FIT>
+__global__ void __launch_bounds__(WARPS * 32, FIT ? 1 : 2)
+rank_kernel(const rs_fit_args a, const int64_t* __restrict__ coef_off,
+            const uint8_t* __restrict__ status_in) {
+    using Sm = RankSmem<WARPS, FIT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
@@ -220,8 +496,7 @@ fit_predict_kernel(const rs_fit_args a) {
     uint32_t cnt[RS_NCOUNTERS];
 #pragma unroll
     for (int c = 0; c < RS_NCOUNTERS; ++c) cnt[c] = 0;
-    const bool fit_in_launch = (a.coef_in == nullptr);
-    const int NPLUS = RS_COEF_STRIDE;
+    const long long ktau = okey(a.log_tau);
 
     if (tid == 0) sm.cur_prog = -1;
     for (;;) {
@@ -268,12 +543,30 @@ fit_predict_kernel(const rs_fit_args a) {
                         if ((m >> j) & 1) continue;
                         const int w = sm.slot_of[m | (1 << j)];
                         if (w < 0) continue;
+                        if (np == RS_MAXPAIRS) {      // only possible with repeated masks
+                            rs_dev_flag(a.dstatus, RS_EDATA, p);
+                            break;
+                        }
                         sm.pair_b[j][np] = (uint8_t)v;
-                        sm.pair_a[j][np] = (uint8_t)w;
                         sm.ylab[j][np] = sm.lt[v] - sm.lt[w];
                         ++np;
                     }
                     sm.npair[j] = np;
+                }
+                // actual log speedups of adding j to each version, as order keys
+                if (ok && tid < V) {
+                    const int m = sm.msk[tid];
+                    uint8_t kn = 0;
+                    for (int j = 0; j < RS_NOPT; ++j) {
+                        const int w = ((m >> j) & 1) ? -1 : sm.slot_of[m | (1 << j)];
+                        long long key = 0;
+                        if (w >= 0) {
+                            key = okey(sm.lt[tid] - sm.lt[w]);
+                            kn |= (uint8_t)(1u << j);
+                        }
+                        sm.act_key[tid][j] = key;
+                    }
+                    sm.known[tid] = kn;
                 }
                 if (tid == 0) {
                     sm.cur_prog = p;
@@ -288,87 +581,41 @@ fit_predict_kernel(const rs_fit_args a) {
                 continue;
             }
             const uint64_t full = rs_full_mask(V);
-            // ---------------------------------------------------------- per-fit pair masks
+            // ---------------------------------------------------------- fits of the chunk
             for (int i = tid; i < ns; i += NT) sm.tmask[i] = a.train_masks[s0 + i] & full;
             __syncthreads();
             for (int f = tid; f < ns * RS_NOPT; f += NT) {
                 const int i = f / RS_NOPT, j = f % RS_NOPT;
                 const uint64_t T = sm.tmask[i];
                 uint32_t pm = 0;
-                for (int q = 0; q < sm.npair[j]; ++q)
-                    if (((T >> sm.pair_b[j][q]) & 1) && ((T >> sm.pair_a[j][q]) & 1)) pm |= 1u << q;
+                for (int q = 0; q < sm.npair[j]; ++q) {
+                    const int v = sm.pair_b[j][q];
+                    const int w = sm.slot_of[sm.msk[v] | (1 << j)];
+                    if (((T >> v) & 1) && ((T >> w) & 1)) pm |= 1u << q;
+                }
                 sm.pmask[f] = pm;
-                sm.nfit[f] = (uint8_t)__popc(pm);
-                if (fit_in_launch) {
-                    // place the labels where the solver expects u
-                    int aa = 0;
-                    for (uint32_t x = pm; x; x &= x - 1) sm.coef[f][1 + aa++] = sm.ylab[j][__ffs(x) - 1];
-                } else {
-                    const double* src = a.coef_in + (s0 * RS_NOPT + f) * (int64_t)NPLUS;
-                    for (int e = 0; e < NPLUS; ++e) sm.coef[f][e] = src[e];
-                    sm.status[f] = isfinite(sm.coef[f][0]) ? RS_FIT_OK : RS_FIT_EMPTY;
+                const int n = __popc(pm);
+                sm.nfit[f] = (uint8_t)n;
+                if (!FIT) {
+                    const int64_t gf = s0 * RS_NOPT + f;
+                    const double* src = a.coef_in + (coef_off ? coef_off[gf] : gf * RS_COEF_STRIDE);
+                    int st;
+                    if (status_in) st = status_in[gf];
+                    else st = (n > 0 && finite_bits(src[0])) ? RS_FIT_OK : RS_FIT_EMPTY;
+                    sm.status[f] = (uint8_t)st;
+                    if (st == RS_FIT_OK)
+                        for (int e = 0; e <= n; ++e) sm.coef[f][e] = src[e];
+                } else if (n == 0) {
+                    sm.status[f] = RS_FIT_EMPTY;
                 }
             }
             __syncthreads();
-            if (fit_in_launch) {
-                // ------------------------------------------------------ bin fits by size
-                // Each fit computes its own position: small fits sorted by n descending
-                // (ties by fit index), large fits in fit order.  Integer work only.
-                {
-                    const int nf = ns * RS_NOPT;
-                    const bool plain = (a.form == RS_FORM_PLAIN);
-                    int my_small = 0, my_large = 0;
-                    for (int f = tid; f < kFits; f += NT) {
-                        if (f >= nf) continue;
-                        const int n = sm.nfit[f];
-                        const bool is_large = n > 0 && (plain || n > SMALL);
-                        const bool is_small = n > 0 && !is_large;
-                        if (n == 0) {
-                            sm.status[f] = RS_FIT_EMPTY;
-                            sm.coef[f][0] = __longlong_as_double(0x7ff8000000000000ll);
-                        }
-                        int pos = 0;
-                        for (int g = 0; g < nf; ++g) {
-                            const int m = sm.nfit[g];
-                            const bool gl = m > 0 && (plain || m > SMALL);
-                            const bool gs = m > 0 && !gl;
-                            if (is_small && gs && (m > n || (m == n && g < f))) ++pos;
-                            if (is_large && gl && g < f) ++pos;
-                        }
-                        if (is_small) sm.small_list[pos] = (int16_t)f;
-                        if (is_large) sm.large_list[pos] = (int16_t)f;
-                        my_small += is_small;
-                        my_large += is_large;
-                    }
-                    const int tot_small = __syncthreads_count(my_small);
-                    const int tot_large = __syncthreads_count(my_large);
-                    if (tid == 0) {
-                        sm.n_small = tot_small;
-                        sm.n_large = tot_large;
-                    }
-                }
-                __syncthreads();
-                // ------------------------------------------------------ small fits: one per lane
-                const int groups = (sm.n_small + 31) / 32;
-                for (int g = warp; g < groups; g += WARPS) {
-                    const int e = g * 32 + lane;
-                    if (e < sm.n_small) {
-                        const int f = sm.small_list[e];
-                        const int j = f % RS_NOPT;
-                        const int n = sm.nfit[f];
-                        uint8_t* vl = sm.vidx[warp][lane];
-                        int aa = 0;
-                        for (uint32_t x = sm.pmask[f]; x; x &= x - 1) vl[aa++] = sm.pair_b[j][__ffs(x) - 1];
-                        sm.status[f] = (uint8_t)fit_thread<SMALL>(n, vl, sm.K, a.lambda,
-                                                                 sm.pool[warp] + lane, sm.coef[f]);
-                    }
-                    __syncwarp();
-                }
-                // ------------------------------------------------------ large fits: one per warp
-                for (int e = warp; e < sm.n_large; e += WARPS) {
-                    const int f = sm.large_list[e];
+            if (FIT) {
+                for (int f = warp; f < ns * RS_NOPT; f += WARPS) {
+                    const int n = sm.nfit[f];
+                    if (n == 0) continue;
                     const int j = f % RS_NOPT;
-                    const int st = fit_warp(sm.nfit[f], sm.pmask[f], sm.pair_b[j], sm.ylab[j], sm.K,
+                    const int st = fit_warp(n, sm.pmask[f], sm.pair_b[j], sm.ylab[j], sm.K, kKld,
                                             a.lambda, sm.pool[warp], sm.coef[f]);
                     if (lane == 0) sm.status[f] = (uint8_t)st;
                     __syncwarp();
@@ -380,23 +627,20 @@ fit_predict_kernel(const rs_fit_args a) {
                     cnt[10] += st == RS_FIT_EMPTY;
                     cnt[11] += st == RS_FIT_NOTPD;
                     cnt[12] += st == RS_FIT_NONFINITE;
-                    if (st != RS_FIT_OK) sm.coef[f][0] = __longlong_as_double(0x7ff8000000000000ll);
                 }
-                __syncthreads();
-            }
-            // ---------------------------------------------------------- fit outputs
-            if (a.coef_out) {
-                double* dst = a.coef_out + s0 * RS_NOPT * (int64_t)NPLUS;
-                for (int e = tid; e < ns * RS_NOPT * NPLUS; e += NT) {
-                    const int f = e / NPLUS, c = e % NPLUS;
-                    const bool ok = sm.status[f] == RS_FIT_OK;
-                    double v = sm.coef[f][c];
-                    if (c > 0 && (!ok || c > sm.nfit[f])) v = 0.0;
-                    dst[e] = v;
+                if (a.coef_out) {
+                    double* dst = a.coef_out + s0 * RS_NOPT * (int64_t)RS_COEF_STRIDE;
+                    for (int e = tid; e < ns * RS_NOPT * RS_COEF_STRIDE; e += NT) {
+                        const int f = e / RS_COEF_STRIDE, c = e % RS_COEF_STRIDE;
+                        const bool ok = sm.status[f] == RS_FIT_OK;
+                        double v = ok ? sm.coef[f][c] : (c == 0 ? nan_d() : 0.0);
+                        if (c > sm.nfit[f]) v = 0.0;
+                        dst[e] = v;
+                    }
                 }
+                if (a.status_out)
+                    for (int f = tid; f < ns * RS_NOPT; f += NT) a.status_out[s0 * RS_NOPT + f] = sm.status[f];
             }
-            if (a.status_out)
-                for (int f = tid; f < ns * RS_NOPT; f += NT) a.status_out[s0 * RS_NOPT + f] = sm.status[f];
             // ---------------------------------------------------------- predict, rank, score
             if (a.rec_code) {
                 if (tid == 0) {
@@ -416,12 +660,14 @@ fit_predict_kernel(const rs_fit_args a) {
                     const int t = select_bit(~sm.tmask[i] & full, kth);
                     const int64_t grow = a.rec_offsets[s0 + i] + kth;
                     const int mt = sm.msk[t];
-                    double pred[RS_NOPT], act[RS_NOPT];
-                    bool valid[RS_NOPT], known[RS_NOPT];
+                    const int kn = sm.known[t];
+                    double pred[RS_NOPT];
+                    long long key[RS_NOPT];
+                    int validm = 0;
 #pragma unroll
                     for (int j = 0; j < RS_NOPT; ++j) {
-                        valid[j] = known[j] = false;
-                        pred[j] = act[j] = __longlong_as_double(0x7ff8000000000000ll);
+                        pred[j] = nan_d();
+                        key[j] = 0;
                         const bool has = (mt >> j) & 1;
                         if (has && !(a.flags & RS_RANK_ALL)) continue;
                         const int f = i * RS_NOPT + j;
@@ -435,59 +681,62 @@ fit_predict_kernel(const rs_fit_args a) {
                         for (uint32_t x = sm.pmask[f]; x; x &= x - 1)
                             yh = fma(cf[aa++], sm.K[t * kKld + sm.pair_b[j][__ffs(x) - 1]], yh);
                         pred[j] = yh;
-                        valid[j] = true;
-                        cnt[1] += 1;
-                        if (!has) {
-                            const int w = sm.slot_of[mt | (1 << j)];
-                            if (w >= 0) {
-                                act[j] = sm.lt[t] - sm.lt[w];
-                                known[j] = true;
-                                cnt[2] += 1;
-                                if ((yh > 0.0) == (act[j] > 0.0)) cnt[3] += 1;
-                            }
-                        }
+                        key[j] = okey(yh);
+                        validm |= 1 << j;
                     }
-                    // insertion sort, descending; a later entry passes only if strictly larger
+                    const int scored = validm & kn;
+                    cnt[1] += __popc(validm);
+                    cnt[2] += __popc(scored);
+                    // insertion sort of the valid candidates by key, descending; a later
+                    // entry passes an earlier one only if strictly larger (ties: lower index)
                     int order[RS_NOPT];
                     int m = 0;
 #pragma unroll
                     for (int j = 0; j < RS_NOPT; ++j)
-                        if (valid[j]) order[m++] = j;
+                        if ((validm >> j) & 1) order[m++] = j;
                     for (int x = 1; x < m; ++x) {
                         const int cur = order[x];
                         int y = x - 1;
-                        while (y >= 0 && pred[order[y]] < pred[cur]) {
+                        while (y >= 0 && key[order[y]] < key[cur]) {
                             order[y + 1] = order[y];
                             --y;
                         }
                         order[y + 1] = cur;
                     }
                     int c = 0;
-                    int idx[RS_NOPT];
-                    for (int x = 0; x < m && c < a.k; ++x)
-                        if (pred[order[x]] >= a.log_tau) idx[c++] = order[x];
-                    uint32_t code = (uint32_t)c;
-                    for (int x = 0; x < RS_NOPT; ++x) code |= (uint32_t)(x < c ? idx[x] : 0xF) << (4 + 4 * x);
+                    uint32_t code = 0x0FFFFFF0u;
+                    for (int x = 0; x < m && c < a.k; ++x) {
+                        const int j = order[x];
+                        if (key[j] >= ktau) {
+                            code = (code & ~(0xFu << (4 + 4 * c))) | ((uint32_t)j << (4 + 4 * c));
+                            if (a.rec_pred) a.rec_pred[grow * a.k + c] = pred[j];
+                            ++c;
+                        }
+                    }
+                    code = (code & ~0xFu) | (uint32_t)c;
                     a.rec_code[grow] = code;
                     if (a.rec_pred)
-                        for (int x = 0; x < a.k; ++x)
-                            a.rec_pred[grow * a.k + x] = x < c ? pred[idx[x]] : __longlong_as_double(0x7ff8000000000000ll);
+                        for (int x = c; x < a.k; ++x) a.rec_pred[grow * a.k + x] = nan_d();
                     if (a.pred_all)
 #pragma unroll
                         for (int j = 0; j < RS_NOPT; ++j) a.pred_all[grow * RS_NOPT + j] = pred[j];
                     cnt[0] += 1;
                     cnt[4] += c;
-                    for (int x = 0; x < c; ++x)
-                        if (known[idx[x]]) {
-                            cnt[5] += 1;
-                            if (act[idx[x]] > 0.0) cnt[6] += 1;
-                        }
                     int bp = -1, ba = -1;
 #pragma unroll
                     for (int j = 0; j < RS_NOPT; ++j) {
-                        if (!(valid[j] && known[j])) continue;
-                        if (bp < 0 || pred[j] > pred[bp]) bp = j;
-                        if (ba < 0 || act[j] > act[ba]) ba = j;
+                        if (!((scored >> j) & 1)) continue;
+                        const long long ak = sm.act_key[t][j];
+                        if ((key[j] > 0) == (ak > 0)) cnt[3] += 1;
+                        if (bp < 0 || key[j] > key[bp]) bp = j;
+                        if (ba < 0 || ak > sm.act_key[t][ba]) ba = j;
+                    }
+                    for (int x = 0; x < c; ++x) {
+                        const int j = (code >> (4 + 4 * x)) & 0xF;
+                        if ((scored >> j) & 1) {
+                            cnt[5] += 1;
+                            if (sm.act_key[t][j] > 0) cnt[6] += 1;
+                        }
                     }
                     if (bp >= 0) {
                         cnt[7] += 1;
@@ -508,10 +757,11 @@ fit_predict_kernel(const rs_fit_args a) {
     }
 }
 
-template <int WARPS, int SMALL>
-cudaError_t launch_fp(const rs_fit_args& a, cudaStream_t st) {
-    using Sm = FitSmem<WARPS, SMALL>;
-    auto kern = fit_predict_kernel<WARPS, SMALL>;
+template <int WARPS, bool FIT>
+cudaError_t launch_rank(const rs_fit_args& a, const int64_t* coef_off, const uint8_t* status_in,
+                        cudaStream_t st) {
+    using Sm = RankSmem<WARPS, FIT>;
+    auto kern = rank_kernel<WARPS, FIT>;
     const size_t smem = sizeof(Sm);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -527,13 +777,107 @@ cudaError_t launch_fp(const rs_fit_args& a, cudaStream_t st) {
     if (grid < 1) grid = 1;
     e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, WARPS * 32, smem, st>>>(a);
+    kern<<<(unsigned)grid, WARPS * 32, smem, st>>>(a, coef_off, status_in);
     return cudaGetLastError();
+}
+
+// Workspace carve-up for the batched form.
+struct FitWs {
+    unsigned* hist;      // [kHist]
+    unsigned* cursor;    // [kHist]
+    uint8_t* pb;         // [P][6][32]
+    uint8_t* pa;         // [P][6][32]
+    double* ylab;        // [P][6][32]
+    int* npair;          // [P][6]
+    uint32_t* fit_pm;    // [S*6]
+    uint8_t* fit_n;      // [S*6]
+    int* order;          // [S*6]
+    int64_t* fit_off;    // [S*6]
+    uint8_t* status;     // [S*6]
+    double* coef;        // compact records
+    size_t bytes;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+FitWs carve(void* base, int64_t P, int64_t S, int nmax) {
+    FitWs w{};
+    char* c = (char*)base;
+    size_t o = 0;
+    auto take = [&](size_t b) { char* p = c ? c + o : nullptr; o += a256(b); return p; };
+    const int64_t S6 = S * RS_NOPT;
+    w.hist = (unsigned*)take(2 * kHist * sizeof(unsigned));
+    w.cursor = w.hist ? w.hist + kHist : nullptr;
+    w.pb = (uint8_t*)take(P * RS_NOPT * RS_MAXPAIRS);
+    w.pa = (uint8_t*)take(P * RS_NOPT * RS_MAXPAIRS);
+    w.ylab = (double*)take(P * RS_NOPT * RS_MAXPAIRS * sizeof(double));
+    w.npair = (int*)take(P * RS_NOPT * sizeof(int));
+    w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
+    w.fit_n = (uint8_t*)take(S6);
+    w.order = (int*)take(S6 * sizeof(int));
+    w.fit_off = (int64_t*)take(S6 * sizeof(int64_t));
+    w.status = (uint8_t*)take(S6);
+    w.coef = (double*)take(S6 * (size_t)(nmax + 1) * sizeof(double));
+    w.bytes = o;
+    return w;
+}
+
+int nmax_of(int max_train) {
+    int n = max_train / 2;   // pairs are disjoint in versions: at most half the train set
+    if (n > RS_MAXPAIRS) n = RS_MAXPAIRS;
+    if (n < 1) n = 1;
+    return n;
 }
 
 }  // namespace
 
+size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train) {
+    return carve(nullptr, P, S, nmax_of(max_train)).bytes;
+}
+
 cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (a.S == 0) return cudaSuccess;
-    return launch_fp<4, 15>(a, st);
+    if (a.form == RS_FORM_PLAIN) return launch_rank<8, true>(a, nullptr, nullptr, st);
+    if (a.coef_in) return launch_rank<8, false>(a, nullptr, nullptr, st);
+    // batched form: pairs -> plan -> bucket -> solve -> rank
+    if (!a.workspace) return cudaErrorInvalidValue;
+    const int nmax = nmax_of(a.max_train);
+    FitWs w = carve(a.workspace, a.P, a.S, nmax);
+    if (w.bytes > a.workspace_bytes) return cudaErrorInvalidValue;
+    const int64_t S6 = a.S * RS_NOPT;
+    auto mark = [&](int i) { if (a.ev) cudaEventRecord(a.ev[i], st); };
+    cudaError_t e = cudaMemsetAsync(w.hist, 0, 2 * kHist * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    mark(0);
+    pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
+                                     w.npair, a.dstatus);
+    mark(1);
+    const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
+    plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
+                                                a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
+                                                nmax, a.dstatus);
+    mark(2);
+    const bool user = a.coef_out != nullptr;
+    uint8_t* status = a.status_out ? a.status_out : w.status;
+    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order, w.fit_off,
+                                                  status, user ? a.coef_out : nullptr, a.counters);
+    mark(3);
+    SolveArgs sa{a.P, a.split_offsets, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
+                 w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, a.counters};
+    solve_small_kernel<<<(unsigned)((S6 + 127) / 128), 128, 0, st>>>(sa);
+    mark(4);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, 0, st>>>(sa);
+    mark(5);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!a.rec_code) return cudaSuccess;
+    rs_fit_args b = a;
+    b.coef_in = user ? a.coef_out : w.coef;
+    b.counters = a.counters;
+    e = launch_rank<8, false>(b, user ? nullptr : w.fit_off, status, st);
+    mark(6);
+    return e;
 }

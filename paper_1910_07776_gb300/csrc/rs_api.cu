@@ -15,6 +15,8 @@ struct rs_ctx {
     cudaStream_t stream;
     int* dstatus;            // RS_DST_INTS ints of device memory
     int64_t* scan;           // block sums of the row-planning scan (kScanBlocksMax + 1)
+    int profiling;           // record stage events in the batched fit/predict path
+    cudaEvent_t ev[RS_NSTAGE_EVENTS];
     char err[512];
 };
 
@@ -77,6 +79,8 @@ rs_status rs_create(rs_ctx** out, int device, void* stream) {
     c->device = device;
     c->stream = (cudaStream_t)stream;
     c->err[0] = 0;
+    c->profiling = 0;
+    for (int i = 0; i < RS_NSTAGE_EVENTS; ++i) c->ev[i] = nullptr;
     e = cudaMalloc(&c->dstatus, RS_DST_INTS * sizeof(int));
     if (e != cudaSuccess) {
         delete c;
@@ -104,7 +108,37 @@ rs_status rs_destroy(rs_ctx* c) {
     cudaSetDevice(c->device);
     cudaFree(c->dstatus);
     cudaFree(c->scan);
+    for (int i = 0; i < RS_NSTAGE_EVENTS; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;
+    return RS_OK;
+}
+
+rs_status rs_profile_enable(rs_ctx* c, int on) {
+    if (!c) return RS_EINVAL;
+    cudaSetDevice(c->device);
+    if (on && !c->ev[0])
+        for (int i = 0; i < RS_NSTAGE_EVENTS; ++i) {
+            cudaError_t e = cudaEventCreate(&c->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "rs_profile_enable");
+        }
+    c->profiling = on ? 1 : 0;
+    return RS_OK;
+}
+
+rs_status rs_profile_read(rs_ctx* c, float* ms, int max_stages, int* n_stages) {
+    if (!c || !ms || !n_stages) return RS_EINVAL;
+    *n_stages = 0;
+    if (!c->profiling) return fail(c, RS_EINVAL, "profiling is off");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaEventSynchronize(c->ev[RS_NSTAGE_EVENTS - 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_profile_read");
+    int n = 0;
+    for (int i = 0; i + 1 < RS_NSTAGE_EVENTS && n < max_stages; ++i, ++n) {
+        e = cudaEventElapsedTime(&ms[n], c->ev[i], c->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rs_profile_read");
+    }
+    *n_stages = n;
     return RS_OK;
 }
 
@@ -198,15 +232,39 @@ static rs_status fit_common(rs_ctx* c, const rs_batch* b, const double* K, const
     a.form = form;
     a.dstatus = c->dstatus;
     a.queue = (unsigned int*)(c->dstatus + RS_DST_QUEUE);
+    a.ev = c->profiling ? c->ev : nullptr;
+    return RS_OK;
+}
+
+size_t rs_fit_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
+    if (!b || !sp || b->n_programs < 1 || sp->n_splits < 0) return 0;
+    return rs_fit_workspace_bytes_impl(b->n_programs, sp->n_splits, sp->max_train);
+}
+
+static rs_status check_ws(rs_ctx* c, const rs_batch* b, const rs_splits* sp, void* ws, size_t bytes,
+                          rs_fit_args& a) {
+    const size_t need = rs_fit_workspace_bytes(b, sp);
+    if (!ws) return fail(c, RS_EINVAL, "the batched form needs a workspace of %zu bytes", need);
+    if ((uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, need);
+    if (sp->max_train < 0 || sp->max_train > 64) return fail(c, RS_EINVAL, "max_train must be in 0..64");
+    a.workspace = ws;
+    a.workspace_bytes = bytes;
+    a.max_train = sp->max_train;
     return RS_OK;
 }
 
 rs_status rs_fit_batched(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
-                         double lambda, int form, double* coef, uint8_t* fit_status) {
+                         double lambda, int form, void* workspace, size_t workspace_bytes,
+                         double* coef, uint8_t* fit_status) {
     if (!c) return RS_EINVAL;
     rs_fit_args a;
     rs_status s = fit_common(c, b, K, sp, lambda, form, a);
     if (s != RS_OK) return s;
+    if (form == RS_FORM_BATCHED) {
+        s = check_ws(c, b, sp, workspace, workspace_bytes, a);
+        if (s != RS_OK) return s;
+    }
     a.coef_out = coef;
     a.status_out = fit_status;
     a.k = 1;
@@ -218,12 +276,17 @@ rs_status rs_fit_batched(rs_ctx* c, const rs_batch* b, const double* K, const rs
 
 rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
                           double lambda, const double* coef, int k, double tau, int flags,
-                          int form, const int64_t* rec_offsets, uint32_t* rec_code,
-                          double* rec_pred, double* pred_all, uint64_t* counters) {
+                          int form, void* workspace, size_t workspace_bytes,
+                          const int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
+                          double* pred_all, uint64_t* counters) {
     if (!c) return RS_EINVAL;
     rs_fit_args a;
     rs_status s = fit_common(c, b, K, sp, lambda, form, a);
     if (s != RS_OK) return s;
+    if (form == RS_FORM_BATCHED && !coef) {
+        s = check_ws(c, b, sp, workspace, workspace_bytes, a);
+        if (s != RS_OK) return s;
+    }
     if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
     if (flags & ~(RS_RANK_ALL | RS_REFINE_X)) return fail(c, RS_EINVAL, "unknown flag bits");
@@ -243,11 +306,11 @@ rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const r
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_predict_rank");
 }
 
-size_t rs_cv_workspace_bytes(const rs_batch* b) {
-    if (!b || b->n_programs < 1 || b->x_elems < 0) return 0;
+size_t rs_cv_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
+    if (!b || !sp || b->n_programs < 1 || b->x_elems < 0) return 0;
     size_t z = align256((size_t)b->x_elems * sizeof(double));
     size_t k = align256((size_t)b->n_programs * RS_GRAM_LD * RS_GRAM_LD * sizeof(double));
-    return z + k + 256;
+    return z + k + align256(rs_fit_workspace_bytes(b, sp));
 }
 
 rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double lambda, int k,
@@ -259,10 +322,15 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
     if (s != RS_OK) return s;
     if (!ws) return fail(c, RS_EINVAL, "workspace is NULL");
     if ((uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
-    const size_t need = rs_cv_workspace_bytes(b);
+    s = check_splits(c, sp);
+    if (s != RS_OK) return s;
+    const size_t need = rs_cv_workspace_bytes(b, sp);
     if (ws_bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
     double* Z = (double*)ws;
-    double* K = (double*)((char*)ws + align256((size_t)b->x_elems * sizeof(double)));
+    const size_t zbytes = align256((size_t)b->x_elems * sizeof(double));
+    const size_t kbytes = align256((size_t)b->n_programs * RS_GRAM_LD * RS_GRAM_LD * sizeof(double));
+    double* K = (double*)((char*)ws + zbytes);
+    void* fws = (char*)ws + zbytes + kbytes;
     s = rs_standardize(c, b, Z, nullptr, nullptr);
     if (s != RS_OK) return s;
     rs_batch zb = *b;
@@ -272,8 +340,9 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
     if (s != RS_OK) return s;
     s = rs_rec_offsets(c, &zb, sp, rec_offsets);
     if (s != RS_OK) return s;
-    return rs_predict_rank(c, &zb, K, sp, lambda, nullptr, k, tau, flags, RS_FORM_BATCHED,
-                           rec_offsets, rec_code, rec_pred, pred_all, counters);
+    return rs_predict_rank(c, &zb, K, sp, lambda, nullptr, k, tau, flags, RS_FORM_BATCHED, fws,
+                           ws_bytes - zbytes - kbytes, rec_offsets, rec_code, rec_pred, pred_all,
+                           counters);
 }
 
 }  // extern "C"

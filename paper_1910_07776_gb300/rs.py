@@ -31,7 +31,8 @@ NCOUNTERS = 16
 EXPORTS = [
     "rs_create", "rs_destroy", "rs_set_stream", "rs_last_error", "rs_check_device_status",
     "rs_standardize", "rs_gram", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
-    "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak",
+    "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak", "rs_fit_workspace_bytes",
+    "rs_profile_enable", "rs_profile_read",
 ]
 
 
@@ -80,14 +81,18 @@ def load(path: str = SO):
     L.rs_standardize.argtypes = [P, P, P, P, P]
     L.rs_gram.argtypes = [P, P, i, P]
     L.rs_rec_offsets.argtypes = [P, P, P, P]
-    L.rs_fit_batched.argtypes = [P, P, P, P, d, i, P, P]
-    L.rs_predict_rank.argtypes = [P, P, P, P, d, P, i, d, i, i, P, P, P, P, P]
-    L.rs_cv_workspace_bytes.argtypes = [P]
+    L.rs_fit_batched.argtypes = [P, P, P, P, d, i, P, C.c_size_t, P, P]
+    L.rs_predict_rank.argtypes = [P, P, P, P, d, P, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
+    L.rs_fit_workspace_bytes.argtypes = [P, P]
+    L.rs_fit_workspace_bytes.restype = C.c_size_t
+    L.rs_cv_workspace_bytes.argtypes = [P, P]
     L.rs_cv_workspace_bytes.restype = C.c_size_t
     L.rs_cv_step.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
+    L.rs_profile_enable.argtypes = [P, i]
+    L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     for name in EXPORTS:
-        if name not in ("rs_last_error", "rs_cv_workspace_bytes"):
+        if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -210,6 +215,17 @@ class Context:
         self.stream = stream
         self._check(self.L.rs_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
 
+    STAGES = ["pairs", "plan_fits", "bucket_fits", "solve_small", "solve_large", "rank"]
+
+    def profile_enable(self, on: bool = True):
+        self._check(self.L.rs_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        ms = (C.c_float * 8)()
+        n = C.c_int(0)
+        self._check(self.L.rs_profile_read(self.h, ms, 8, C.byref(n)))
+        return {self.STAGES[i]: float(ms[i]) for i in range(n.value)}
+
     def check_device_status(self):
         self._check(self.L.rs_check_device_status(self.h))
 
@@ -235,25 +251,41 @@ class Context:
         self._check(self.L.rs_rec_offsets(self.h, C.byref(bc), C.byref(sc), _ptr(out)))
         return out
 
+    def fit_workspace_bytes(self, b: DeviceBatch, s: DeviceSplits) -> int:
+        bc, sc = b.c(), s.c()
+        return int(self.L.rs_fit_workspace_bytes(C.byref(bc), C.byref(sc)))
+
+    def workspace(self, nbytes: int) -> torch.Tensor:
+        """A device scratch buffer (256-byte aligned by the caching allocator)."""
+        return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=f"cuda:{self.device}")
+
     def fit_batched(self, zb: DeviceBatch, K, s: DeviceSplits, lam: float = 1e-3,
-                    form: int = RS_FORM_BATCHED, coef=None, fit_status=None):
+                    form: int = RS_FORM_BATCHED, coef=None, fit_status=None, workspace=None):
+        if workspace is None and form == RS_FORM_BATCHED:
+            workspace = self.workspace(self.fit_workspace_bytes(zb, s))
         bc, sc = zb.c(), s.c()
+        wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
         self._check(self.L.rs_fit_batched(self.h, C.byref(bc), _ptr(K), C.byref(sc), float(lam),
-                                          int(form), _ptr(coef), _ptr(fit_status)))
+                                          int(form), _ptr(workspace), wsb, _ptr(coef),
+                                          _ptr(fit_status)))
         return coef, fit_status
 
     def predict_rank(self, zb: DeviceBatch, K, s: DeviceSplits, rec_offsets, rec_code,
                      lam: float = 1e-3, coef=None, k: int = 3, tau: float = 1.05, flags: int = 0,
-                     form: int = RS_FORM_BATCHED, rec_pred=None, pred_all=None, counters=None):
+                     form: int = RS_FORM_BATCHED, rec_pred=None, pred_all=None, counters=None,
+                     workspace=None):
+        if workspace is None and form == RS_FORM_BATCHED and coef is None:
+            workspace = self.workspace(self.fit_workspace_bytes(zb, s))
         bc, sc = zb.c(), s.c()
+        wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
         self._check(self.L.rs_predict_rank(
             self.h, C.byref(bc), _ptr(K), C.byref(sc), float(lam), _ptr(coef), int(k), float(tau),
-            int(flags), int(form), _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred),
-            _ptr(pred_all), _ptr(counters)))
+            int(flags), int(form), _ptr(workspace), wsb, _ptr(rec_offsets), _ptr(rec_code),
+            _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
 
-    def cv_workspace_bytes(self, b: DeviceBatch) -> int:
-        bc = b.c()
-        return int(self.L.rs_cv_workspace_bytes(C.byref(bc)))
+    def cv_workspace_bytes(self, b: DeviceBatch, s: DeviceSplits) -> int:
+        bc, sc = b.c(), s.c()
+        return int(self.L.rs_cv_workspace_bytes(C.byref(bc), C.byref(sc)))
 
     def cv_step(self, b: DeviceBatch, s: DeviceSplits, workspace, rec_offsets, rec_code,
                 lam: float = 1e-3, k: int = 3, tau: float = 1.05, flags: int = 0,
@@ -263,16 +295,6 @@ class Context:
             self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags),
             int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
-
-
-def measure_fma_peak(f64: bool = True, iters: int = 4096) -> float:
-    """GFLOP/s of independent FMA chains over the whole device (FP64 or FP32)."""
-    L = load()
-    g = C.c_double(0.0)
-    st = L.rs_measure_fma_peak(1 if f64 else 0, int(iters), C.byref(g))
-    if st != RS_OK:
-        raise RsError(st, "rs_measure_fma_peak failed")
-    return g.value
 
 
 @dataclass

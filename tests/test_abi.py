@@ -39,10 +39,16 @@ def test_workspace_query_needs_no_gpu():
     b = synth.make_batch(3, versions=(5, 64), feat=20, seed=0)
     cb = rs._Batch(b.n_programs, 0, b.n_rows, 64, 20, b.X.shape[0], int(b.feat_width.sum()),
                    None, None, None, None, None, None, None, None)
-    nbytes = lib.rs_cv_workspace_bytes(ctypes.byref(cb))
-    need = b.X.shape[0] * 8 + 3 * 64 * 64 * 8
+    S = 100
+    cs = rs._Splits(S, 32, 0, None, None)
+    fit = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
+    # per fit: pair mask, size, order, offset, status, and up to 17 coefficient doubles
+    assert S * 6 * (4 + 1 + 4 + 8 + 1 + 17 * 8) <= fit <= S * 6 * (4 + 1 + 4 + 8 + 1 + 17 * 8) + 64 * 1024
+    nbytes = lib.rs_cv_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
+    need = b.X.shape[0] * 8 + 3 * 64 * 64 * 8 + fit
     assert need <= nbytes <= need + 1024
-    assert lib.rs_cv_workspace_bytes(None) == 0
+    assert lib.rs_cv_workspace_bytes(None, None) == 0
+    assert lib.rs_fit_workspace_bytes(None, None) == 0
 
 
 def test_invalid_arguments_are_rejected_before_any_launch():

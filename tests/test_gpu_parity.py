@@ -151,7 +151,7 @@ def test_full_batched_cv_size_sampled(rs, ctx):
     ro = ctx.rec_offsets(db, ds)
     R = int(ro[-1])
     out = rs.alloc_outputs(R, ds.n_splits, 3)
-    ws = torch.empty(ctx.cv_workspace_bytes(db), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(ctx.cv_workspace_bytes(db, ds), dtype=torch.uint8, device="cuda")
     ctx.cv_step(db, ds, ws, out.rec_offsets, out.rec_code, rec_pred=out.rec_pred,
                 pred_all=out.pred_all, counters=out.counters)
     torch.cuda.synchronize()
