@@ -297,6 +297,16 @@ class Context:
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
 
 
+def measure_fma_peak(f64: bool = True, iters: int = 4096) -> float:
+    """GFLOP/s of independent FMA chains over the whole device (FP64 or FP32)."""
+    L = load()
+    g = C.c_double(0.0)
+    st = L.rs_measure_fma_peak(1 if f64 else 0, int(iters), C.byref(g))
+    if st != RS_OK:
+        raise RsError(st, "rs_measure_fma_peak failed")
+    return g.value
+
+
 @dataclass
 class CVOutputs:
     rec_offsets: torch.Tensor
