@@ -217,7 +217,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ctx = rs.Context(local, stream)
     db = rs.DeviceBatch.from_host(batch, dev)
-    ds = rs.DeviceSplits.from_host(splits, dev)
+    ds = rs.DeviceSplits.from_host(splits, dev, batch)
     Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
     zb = db.with_X(Z)
     K = torch.zeros(db.n_programs * 64 * 64, dtype=torch.float64, device=dev)
@@ -360,7 +360,7 @@ def run_plain(rs, ctx, batch, splits, dev, stream, flush, args):
         ss = synth.Splits(split_offsets=np.array([0, s1 - s0], np.int64),
                           train_masks=splits.train_masks[s0:s1])
         db = rs.DeviceBatch.from_host(sub, dev)
-        ds = rs.DeviceSplits.from_host(ss, dev)
+        ds = rs.DeviceSplits.from_host(ss, dev, sub)
         Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
         K = torch.zeros(64 * 64, dtype=torch.float64, device=dev)
         ro = ctx.rec_offsets(db, ds)
@@ -422,8 +422,9 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
                         x_offsets=devb["x_offsets"], feat_offsets=devb["feat_offsets"],
                         X=devb["X"], masks=devb["masks"], log_time=devb["log_time"],
                         cycles=devb["cycles"])
-    ds = rs.DeviceSplits(n_splits=splits.n_splits, max_train=64,
-                         split_offsets=devb["split_offsets"], train_masks=devb["train_masks"])
+    ds = rs.DeviceSplits(n_splits=splits.n_splits, max_train=int(CFG["versions"][1]) // 2 + 1,
+                         split_offsets=devb["split_offsets"], train_masks=devb["train_masks"],
+                         n_test_rows=R)
     ws = torch.empty(ctx.cv_workspace_bytes(db, ds), dtype=torch.uint8, device=dev)
     out = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
     h_code = torch.empty(R, dtype=torch.int32).pin_memory()

@@ -97,6 +97,8 @@ typedef struct {
 
 typedef struct {
     int64_t n_splits;            /* host: S = split_offsets[P]                            */
+    int64_t n_test_rows;         /* host: rec_offsets[S] if known, else 0 (then the bound
+                                    S * max_versions sizes the prediction buffer)         */
     int32_t max_train;           /* host: upper bound on popcount(train mask), 0..64      */
     int32_t reserved;
     const int64_t* split_offsets;/* [P+1]                                                 */

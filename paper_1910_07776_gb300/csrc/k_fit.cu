@@ -24,6 +24,7 @@
 // steps in FP64 (fewer FP64 instructions than a division and a square root).
 // The plain form solves every fit with one warp inside the rank kernel (no bucketing).
 #include <math.h>
+#include <string.h>
 
 #include "rs_internal.cuh"
 
@@ -66,6 +67,13 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
     return r;
 }
 
+long long okey_host(double x) {
+    long long b;
+    memcpy(&b, &x, sizeof(b));
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
 // The a-th set bit (0-based) of x; x must have more than a set bits.
 __device__ __forceinline__ int select_bit(uint64_t x, int a) {
     for (int i = 0; i < a; ++i) x &= x - 1;
@@ -75,10 +83,13 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
 // ====================================================================== pair tables
 // One block per program: the before/after pairs of each optimization in ascending order of
 // the before slot, and their labels.  Tables: [P][6][32] (u8, u8, double), counts [P][6].
+// Also, per program: cand[p][j] = slots whose mask lacks j (uint64), and for every slot t
+// and optimization j the actual log speedup of adding j, as an order key, with a bit in
+// known[p][t] when the version t|j exists (Sec. 5: the measured speedup of the pair).
 __global__ void __launch_bounds__(64)
 pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restrict__ masks,
              const double* __restrict__ log_time, uint8_t* pb, uint8_t* pa, double* ylab,
-             int* npair, int* dstatus) {
+             int* npair, uint64_t* cand, long long* act_key, uint8_t* known, int* dstatus) {
     __shared__ int8_t slot_of[RS_MAXV];
     __shared__ uint8_t msk[RS_MAXV];
     __shared__ double lt[RS_MAXV];
@@ -86,7 +97,10 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
     const int64_t r0 = row_off[p];
     const int V = (int)(row_off[p + 1] - r0);
     if (V < 1 || V > RS_MAXV) {
-        if (tid < RS_NOPT) npair[p * RS_NOPT + tid] = 0;
+        if (tid < RS_NOPT) {
+            npair[p * RS_NOPT + tid] = 0;
+            cand[p * RS_NOPT + tid] = 0;
+        }
         if (tid == 0) rs_dev_flag(dstatus, RS_EDATA, p);
         return;
     }
@@ -102,14 +116,16 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
         const int j = tid;
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
         int np = 0;
+        uint64_t cm = 0;
         for (int v = 0; v < V; ++v) {
             const int m = msk[v];
             if ((m >> j) & 1) continue;
+            cm |= 1ull << v;
             const int w = slot_of[m | (1 << j)];
             if (w < 0) continue;
             if (np == RS_MAXPAIRS) {      // only possible with repeated masks
                 rs_dev_flag(dstatus, RS_EDATA, p);
-                break;
+                continue;
             }
             pb[base + np] = (uint8_t)v;
             pa[base + np] = (uint8_t)w;
@@ -117,6 +133,24 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
             ++np;
         }
         npair[p * RS_NOPT + j] = np;
+        cand[p * RS_NOPT + j] = cm;
+    }
+    {
+        const int t = tid;
+        uint8_t kn = 0;
+        long long* ak = act_key + ((int64_t)p * RS_MAXV + t) * RS_NOPT;
+        for (int j = 0; j < RS_NOPT; ++j) {
+            long long key = 0;
+            if (t < V && !((msk[t] >> j) & 1)) {
+                const int w = slot_of[msk[t] | (1 << j)];
+                if (w >= 0) {
+                    key = okey(lt[t] - lt[w]);
+                    kn |= (uint8_t)(1u << j);
+                }
+            }
+            ak[j] = key;
+        }
+        known[(int64_t)p * RS_MAXV + t] = kn;
     }
 }
 
@@ -174,17 +208,27 @@ __device__ __forceinline__ void bucket_tables(const unsigned* hist, long long* s
 }
 
 // ====================================================================== bucket
+// Counting sort of the fits by n.  Each block counts its fits per n in shared memory,
+// reserves one range per n with a single global atomic, and places its fits inside it.
 __global__ void __launch_bounds__(256)
 bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
                    unsigned* cursor, int* order, int64_t* fit_off, uint8_t* status, double* coef_user,
                    unsigned long long* counters) {
     __shared__ long long start[kHist], cstart[kHist];
+    __shared__ unsigned lcount[kHist], lbase[kHist];
     if (threadIdx.x == 0) bucket_tables(hist, start, cstart);
+    if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
     __syncthreads();
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = f < S6 ? fit_n[f] : 0;
+    unsigned local = 0;
+    if (f < S6 && n > 0) local = atomicAdd(&lcount[n], 1u);
+    __syncthreads();
+    if (threadIdx.x < kHist && lcount[threadIdx.x])
+        lbase[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], lcount[threadIdx.x]);
+    __syncthreads();
     unsigned empty = 0;
     if (f < S6) {
-        const int n = fit_n[f];
         if (n == 0) {
             fit_off[f] = -1;
             status[f] = RS_FIT_EMPTY;
@@ -195,7 +239,7 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
                 for (int e = 1; e < RS_COEF_STRIDE; ++e) o[e] = 0.0;
             }
         } else {
-            const long long pos = start[n] + atomicAdd(&cursor[n], 1u);
+            const long long pos = start[n] + lbase[n] + local;
             order[pos] = (int)f;
             fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
         }
@@ -207,10 +251,19 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
 }
 
 // ====================================================================== solve, n <= kNReg
+// Where the predictions of one fit go: the test rows of its split that are candidates for
+// its optimization; row r of the split (r-th test slot in ascending order) is dst[r].
+struct PredTarget {
+    double* dst;          // prediction buffer row of this optimization + the split's first row
+    uint64_t test;        // test slots of the split
+    uint64_t cand;        // test slots to predict (candidates)
+    int64_t room;         // rows left in the buffer from dst (guards a wrong size hint)
+};
+
 template <int N>
 __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
                                            const double* __restrict__ yl, uint32_t pm, double lambda,
-                                           double* out) {
+                                           double* out, const PredTarget* pt) {
     int vb[N];
     double u[N], w[N], L[tri(N)], ri[N];
     uint32_t x = pm;
@@ -269,11 +322,23 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
     out[0] = b;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const double al = fma(-b, w[i], u[i]);
-        fin = fin && finite_bits(al);
-        out[1 + i] = al;
+        u[i] = fma(-b, w[i], u[i]);        // alpha
+        fin = fin && finite_bits(u[i]);
+        out[1 + i] = u[i];
     }
-    return fin ? RS_FIT_OK : RS_FIT_NONFINITE;
+    if (!fin) return RS_FIT_NONFINITE;
+    if (pt) {                              // predictions b + sum_a alpha_a K[t][v_a]
+        for (uint64_t c = pt->cand; c; c &= c - 1) {
+            const int t = __ffsll((long long)c) - 1;
+            const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+            const double* Kt = Kp + t * RS_GRAM_LD;
+            double yh = b;
+#pragma unroll
+            for (int a = 0; a < N; ++a) yh = fma(u[a], __ldg(Kt + vb[a]), yh);
+            if (r < pt->room) pt->dst[r] = yh;
+        }
+    }
+    return RS_FIT_OK;
 }
 
 struct SolveArgs {
@@ -292,7 +357,29 @@ struct SolveArgs {
     uint8_t* status;
     double lambda;
     unsigned long long* counters;
+    // predictions (batched predict/rank only; predbuf == nullptr for fits alone)
+    const int64_t* row_off;
+    const uint64_t* train_masks;
+    const int64_t* rec_offsets;
+    const uint64_t* cand;
+    double* predbuf;      // [6][R]
+    int64_t R;
+    int flags;
+    int* dstatus;
 };
+
+__device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j, int p, PredTarget& pt) {
+    if (!a.predbuf) return false;
+    const int V = (int)(a.row_off[p + 1] - a.row_off[p]);
+    const uint64_t full = rs_full_mask(V);
+    pt.test = ~a.train_masks[s] & full;
+    pt.cand = pt.test & ((a.flags & RS_RANK_ALL) ? full : a.cand[p * RS_NOPT + j]);
+    const int64_t r0 = a.rec_offsets[s];
+    pt.dst = a.predbuf + (int64_t)j * a.R + r0;
+    pt.room = a.R - r0;
+    if (r0 + __popcll(pt.test) > a.R) rs_dev_flag(a.dstatus, RS_EDATA, -3);
+    return true;
+}
 
 __device__ __forceinline__ void finish_record(const SolveArgs& a, int64_t f, int n, int st, double* out) {
     if (st != RS_FIT_OK) {
@@ -338,17 +425,19 @@ solve_small_kernel(const SolveArgs a) {
         double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
         const uint8_t* pb = a.pb + base;
         const double* yl = a.ylab + base;
+        PredTarget ptv;
+        const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
         switch (n) {
-            case 1: st = solve_fixed<1>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 2: st = solve_fixed<2>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 3: st = solve_fixed<3>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 4: st = solve_fixed<4>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 5: st = solve_fixed<5>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 6: st = solve_fixed<6>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 7: st = solve_fixed<7>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 8: st = solve_fixed<8>(Kp, pb, yl, pm, a.lambda, out); break;
-            case 9: st = solve_fixed<9>(Kp, pb, yl, pm, a.lambda, out); break;
-            default: st = solve_fixed<10>(Kp, pb, yl, pm, a.lambda, out); break;
+            case 1: st = solve_fixed<1>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 2: st = solve_fixed<2>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 3: st = solve_fixed<3>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 4: st = solve_fixed<4>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 5: st = solve_fixed<5>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 6: st = solve_fixed<6>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 7: st = solve_fixed<7>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 8: st = solve_fixed<8>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            case 9: st = solve_fixed<9>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+            default: st = solve_fixed<10>(Kp, pb, yl, pm, a.lambda, out, pt); break;
         }
         finish_record(a, f, n, st, out);
     }
@@ -359,7 +448,8 @@ solve_small_kernel(const SolveArgs a) {
 // Lane a owns row a (a < n <= 32).  K is read with leading dimension ld.  Lsh: [32][33].
 // Writes b to coef[0] and alpha to coef[1..n]; returns a warp-uniform status.
 __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double* ylab,
-                        const double* K, int ld, double lambda, double* Lsh, double* coef) {
+                        const double* K, int ld, double lambda, double* Lsh, double* coef,
+                        const PredTarget* pt = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < n;
     int v = 0;
@@ -424,7 +514,26 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
     if (act) coef[1 + lane] = al;
     if (lane == 0) coef[0] = b;
     __syncwarp();
-    return fin ? RS_FIT_OK : RS_FIT_NONFINITE;
+    if (!fin) return RS_FIT_NONFINITE;
+    if (pt) {                                 // predictions, one candidate row per lane
+        const int nc = __popcll(pt->cand);
+        for (int r0 = 0; r0 < nc; r0 += 32) {
+            const bool mine = r0 + lane < nc;
+            int t = 0;
+            if (mine) t = select_bit(pt->cand, r0 + lane);
+            double yh = b;
+            for (int q = 0; q < n; ++q) {
+                const double aq = __shfl_sync(0xffffffffu, al, q);
+                const int vq = __shfl_sync(0xffffffffu, v, q);
+                if (mine) yh = fma(aq, K[t * ld + vq], yh);
+            }
+            if (mine) {
+                const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+                if (r < pt->room) pt->dst[r] = yh;
+            }
+        }
+    }
+    return RS_FIT_OK;
 }
 
 constexpr int kLargeWarps = 4;
@@ -448,15 +557,162 @@ solve_large_kernel(const SolveArgs a) {
         const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
         double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
+        PredTarget ptv;
+        const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
         const int st = fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
-                                a.lambda, Lsh[warp], out);
+                                a.lambda, Lsh[warp], out, pt);
         if (lane == 0) finish_record(a, f, n, st, out);
         if (a.counters && lane == 0) atomicAdd(a.counters + (st == RS_FIT_OK ? 9 : st == RS_FIT_NOTPD ? 11 : 12), 1ull);
         __syncwarp();
     }
 }
 
-// ====================================================================== predict / rank
+// ====================================================================== rank pass
+// One warp per split, one lane per test row.  No FP64 arithmetic: predictions (written by
+// the solve kernels) are compared as order keys; each candidate's place in the sorted
+// list is counted directly (ties: lower index first), so every array index is static.
+struct RankPassArgs {
+    int P;
+    const int64_t* row_off;
+    const uint8_t* masks;
+    const int64_t* split_off;
+    const uint64_t* tm;
+    int64_t S;
+    const int64_t* rec_offsets;
+    const uint8_t* status;
+    const double* predbuf;       // [6][R]
+    int64_t R;
+    const long long* act_key;    // [P][64][6]
+    const uint8_t* known;        // [P][64]
+    int k;
+    long long ktau;
+    int flags;
+    uint32_t* rec_code;
+    double* rec_pred;
+    double* pred_all;
+    unsigned long long* counters;
+};
+
+__device__ __forceinline__ bool before(long long ka, int ja, long long kb, int jb) {
+    return ka > kb || (ka == kb && ja < jb);
+}
+
+__global__ void __launch_bounds__(256)
+rank_pass_kernel(const RankPassArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t cnt[14];
+#pragma unroll
+    for (int c = 0; c < 14; ++c) cnt[c] = 0;
+    for (int64_t s = wg; s < a.S; s += nw) {
+        const int p = rs_find_segment(a.split_off, a.P, s);
+        const int64_t rv = a.row_off[p];
+        const int V = (int)(a.row_off[p + 1] - rv);
+        if (V < 1 || V > RS_MAXV) continue;
+        const uint64_t test = ~a.tm[s] & rs_full_mask(V);
+        const int nt = __popcll(test);
+        const int64_t base = a.rec_offsets[s];
+        if (base + nt > a.R) continue;
+        int okm = 0;
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j) okm |= (a.status[s * RS_NOPT + j] == RS_FIT_OK) << j;
+        const uint32_t lo = (uint32_t)test, hi = (uint32_t)(test >> 32);
+        const int clo = __popc(lo);
+        for (int r = lane; r < nt; r += 32) {
+            const int t = r < clo ? (int)__fns(lo, 0, r + 1) : 32 + (int)__fns(hi, 0, r - clo + 1);
+            const int64_t row = base + r;
+            const int mt = a.masks[rv + t] & 63;
+            const int kn = a.known[(int64_t)p * RS_MAXV + t];
+            const long long* ak = a.act_key + ((int64_t)p * RS_MAXV + t) * RS_NOPT;
+            double pred[RS_NOPT];
+            long long key[RS_NOPT];
+            int validm = 0;
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j) {
+                pred[j] = nan_d();
+                key[j] = 0;
+                const bool cand = (a.flags & RS_RANK_ALL) || !((mt >> j) & 1);
+                if (!cand) continue;
+                if (!((okm >> j) & 1)) {
+                    cnt[13] += 1;
+                    continue;
+                }
+                pred[j] = a.predbuf[(int64_t)j * a.R + row];
+                key[j] = okey(pred[j]);
+                validm |= 1 << j;
+            }
+            int above = 0;
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j)
+                if (((validm >> j) & 1) && key[j] >= a.ktau) above |= 1 << j;
+            uint32_t code = 0x0FFFFFF0u;
+            int c = 0;
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j) {
+                if (!((above >> j) & 1)) continue;
+                int pos = 0;
+#pragma unroll
+                for (int i = 0; i < RS_NOPT; ++i)
+                    if (i != j && ((above >> i) & 1) && before(key[i], i, key[j], j)) ++pos;
+                if (pos < a.k) {
+                    code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
+                    if (a.rec_pred) a.rec_pred[row * a.k + pos] = pred[j];
+                    ++c;
+                }
+            }
+            code = (code & ~0xFu) | (uint32_t)c;
+            a.rec_code[row] = code;
+            if (a.rec_pred)
+                for (int x = c; x < a.k; ++x) a.rec_pred[row * a.k + x] = nan_d();
+            if (a.pred_all)
+#pragma unroll
+                for (int j = 0; j < RS_NOPT; ++j) a.pred_all[row * RS_NOPT + j] = pred[j];
+            const int scored = validm & kn;
+            cnt[0] += 1;
+            cnt[1] += __popc(validm);
+            cnt[2] += __popc(scored);
+            cnt[4] += c;
+            int bp = -1, ba = -1;
+            long long kbp = 0, kba = 0;
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j) {
+                if (!((scored >> j) & 1)) continue;
+                const long long akj = ak[j];
+                if ((key[j] > 0) == (akj > 0)) cnt[3] += 1;
+                if (bp < 0 || key[j] > kbp) {
+                    bp = j;
+                    kbp = key[j];
+                }
+                if (ba < 0 || akj > kba) {
+                    ba = j;
+                    kba = akj;
+                }
+            }
+            for (int x = 0; x < c; ++x) {
+                const int j = (code >> (4 + 4 * x)) & 0xF;
+                if ((scored >> j) & 1) {
+                    cnt[5] += 1;
+                    if (ak[j] > 0) cnt[6] += 1;
+                }
+            }
+            if (bp >= 0) {
+                cnt[7] += 1;
+                if (bp == ba) cnt[8] += 1;
+            }
+        }
+    }
+    if (a.counters) {
+#pragma unroll
+        for (int c = 0; c < 14; ++c) {
+            if (c >= 9 && c <= 12) continue;   // fit statuses are counted by the solvers
+            const uint32_t v = __reduce_add_sync(0xffffffffu, cnt[c]);
+            if (lane == 0 && v) atomicAdd(a.counters + c, (unsigned long long)v);
+        }
+    }
+}
+
+// ====================================================================== predict / rank (chunked)
 template <int WARPS, bool FIT>
 struct RankSmem {
     static constexpr int kPool = FIT ? 32 * 33 : 1;
@@ -789,18 +1045,22 @@ struct FitWs {
     uint8_t* pa;         // [P][6][32]
     double* ylab;        // [P][6][32]
     int* npair;          // [P][6]
+    uint64_t* cand;      // [P][6]
+    long long* act_key;  // [P][64][6]
+    uint8_t* known;      // [P][64]
     uint32_t* fit_pm;    // [S*6]
     uint8_t* fit_n;      // [S*6]
     int* order;          // [S*6]
     int64_t* fit_off;    // [S*6]
     uint8_t* status;     // [S*6]
     double* coef;        // compact records
+    double* predbuf;     // [6][Rcap]
     size_t bytes;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-FitWs carve(void* base, int64_t P, int64_t S, int nmax) {
+FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     FitWs w{};
     char* c = (char*)base;
     size_t o = 0;
@@ -812,12 +1072,16 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax) {
     w.pa = (uint8_t*)take(P * RS_NOPT * RS_MAXPAIRS);
     w.ylab = (double*)take(P * RS_NOPT * RS_MAXPAIRS * sizeof(double));
     w.npair = (int*)take(P * RS_NOPT * sizeof(int));
+    w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
+    w.act_key = (long long*)take(P * RS_MAXV * RS_NOPT * sizeof(long long));
+    w.known = (uint8_t*)take(P * RS_MAXV);
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
     w.fit_n = (uint8_t*)take(S6);
     w.order = (int*)take(S6 * sizeof(int));
     w.fit_off = (int64_t*)take(S6 * sizeof(int64_t));
     w.status = (uint8_t*)take(S6);
     w.coef = (double*)take(S6 * (size_t)(nmax + 1) * sizeof(double));
+    w.predbuf = (double*)take((size_t)RS_NOPT * Rcap * sizeof(double));
     w.bytes = o;
     return w;
 }
@@ -831,18 +1095,18 @@ int nmax_of(int max_train) {
 
 }  // namespace
 
-size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train) {
-    return carve(nullptr, P, S, nmax_of(max_train)).bytes;
+size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t Rcap) {
+    return carve(nullptr, P, S, nmax_of(max_train), Rcap).bytes;
 }
 
 cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (a.S == 0) return cudaSuccess;
     if (a.form == RS_FORM_PLAIN) return launch_rank<8, true>(a, nullptr, nullptr, st);
     if (a.coef_in) return launch_rank<8, false>(a, nullptr, nullptr, st);
-    // batched form: pairs -> plan -> bucket -> solve -> rank
+    // batched form: pairs -> plan -> bucket -> solve (+ predictions) -> rank pass
     if (!a.workspace) return cudaErrorInvalidValue;
     const int nmax = nmax_of(a.max_train);
-    FitWs w = carve(a.workspace, a.P, a.S, nmax);
+    FitWs w = carve(a.workspace, a.P, a.S, nmax, a.rows_cap);
     if (w.bytes > a.workspace_bytes) return cudaErrorInvalidValue;
     const int64_t S6 = a.S * RS_NOPT;
     auto mark = [&](int i) { if (a.ev) cudaEventRecord(a.ev[i], st); };
@@ -850,7 +1114,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     mark(0);
     pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
-                                     w.npair, a.dstatus);
+                                     w.npair, w.cand, w.act_key, w.known, a.dstatus);
     mark(1);
     const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
     plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
@@ -862,8 +1126,11 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order, w.fit_off,
                                                   status, user ? a.coef_out : nullptr, a.counters);
     mark(3);
+    const bool rank = a.rec_code != nullptr;
     SolveArgs sa{a.P, a.split_offsets, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
-                 w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, a.counters};
+                 w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, a.counters,
+                 a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
+                 a.rows_cap, a.flags, a.dstatus};
     solve_small_kernel<<<(unsigned)((S6 + 127) / 128), 128, 0, st>>>(sa);
     mark(4);
     int dev = 0, sms = 0;
@@ -871,13 +1138,15 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, 0, st>>>(sa);
     mark(5);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (!a.rec_code) return cudaSuccess;
-    rs_fit_args b = a;
-    b.coef_in = user ? a.coef_out : w.coef;
-    b.counters = a.counters;
-    e = launch_rank<8, false>(b, user ? nullptr : w.fit_off, status, st);
+    if (rank) {
+        RankPassArgs ra{a.P, a.row_offsets, a.masks, a.split_offsets, a.train_masks, a.S,
+                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.act_key, w.known, a.k,
+                        0, a.flags, a.rec_code, a.rec_pred, a.pred_all, a.counters};
+        ra.ktau = okey_host(a.log_tau);
+        int64_t blocks = (a.S + 7) / 8;
+        if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
+        rank_pass_kernel<<<(unsigned)blocks, 256, 0, st>>>(ra);
+    }
     mark(6);
-    return e;
+    return cudaGetLastError();
 }

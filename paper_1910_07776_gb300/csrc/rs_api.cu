@@ -236,9 +236,13 @@ static rs_status fit_common(rs_ctx* c, const rs_batch* b, const double* K, const
     return RS_OK;
 }
 
+static int64_t rows_cap(const rs_batch* b, const rs_splits* sp) {
+    return sp->n_test_rows > 0 ? sp->n_test_rows : sp->n_splits * (int64_t)b->max_versions;
+}
+
 size_t rs_fit_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
     if (!b || !sp || b->n_programs < 1 || sp->n_splits < 0) return 0;
-    return rs_fit_workspace_bytes_impl(b->n_programs, sp->n_splits, sp->max_train);
+    return rs_fit_workspace_bytes_impl(b->n_programs, sp->n_splits, sp->max_train, rows_cap(b, sp));
 }
 
 static rs_status check_ws(rs_ctx* c, const rs_batch* b, const rs_splits* sp, void* ws, size_t bytes,
@@ -251,6 +255,7 @@ static rs_status check_ws(rs_ctx* c, const rs_batch* b, const rs_splits* sp, voi
     a.workspace = ws;
     a.workspace_bytes = bytes;
     a.max_train = sp->max_train;
+    a.rows_cap = rows_cap(b, sp);
     return RS_OK;
 }
 

@@ -77,11 +77,12 @@ struct rs_fit_args {
     unsigned int* queue;          // persistent work queue head (zeroed before launch)
     // batched form only
     int max_train;                // host bound on popcount(train mask)
+    int64_t rows_cap;             // rows of the prediction buffer (>= rec_offsets[S])
     void* workspace;
     size_t workspace_bytes;
     // optional stage events (recorded on the stream before and after each internal launch)
     cudaEvent_t* ev;
 };
 #define RS_NSTAGE_EVENTS 7   // before pairs, after pairs / plan / bucket / solve / solve-large / rank
-size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train);
+size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t rows_cap);
 cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st);

@@ -54,7 +54,8 @@ class _Batch(C.Structure):
 
 class _Splits(C.Structure):
     _fields_ = [
-        ("n_splits", C.c_int64), ("max_train", C.c_int32), ("reserved", C.c_int32),
+        ("n_splits", C.c_int64), ("n_test_rows", C.c_int64), ("max_train", C.c_int32),
+        ("reserved", C.c_int32),
         ("split_offsets", C.c_void_p), ("train_masks", C.c_void_p),
     ]
 
@@ -162,25 +163,38 @@ class DeviceSplits:
     max_train: int
     split_offsets: torch.Tensor
     train_masks: torch.Tensor
+    n_test_rows: int = 0
 
     @staticmethod
-    def from_host(s, device="cuda") -> "DeviceSplits":
+    def from_host(s, device="cuda", batch=None) -> "DeviceSplits":
+        """Host hints: the largest train-set size and, when the batch is given, the exact
+        number of test rows (otherwise the library sizes buffers by an upper bound)."""
         tm = np.ascontiguousarray(s.train_masks, dtype=np.uint64)
-        mt = 0
-        if tm.size:
-            x = tm.copy()
-            cnt = np.zeros(tm.shape, dtype=np.int64)
+        pc = np.zeros(tm.shape, dtype=np.int64)
+        x = tm.copy()
+        for _ in range(64):
+            pc += (x & np.uint64(1)).astype(np.int64)
+            x >>= np.uint64(1)
+        rows = 0
+        if batch is not None and tm.size:
+            V = np.diff(batch.row_offsets).astype(np.int64)
+            per = np.repeat(V, np.diff(s.split_offsets))
+            full = np.where(per >= 64, np.uint64(0xFFFFFFFFFFFFFFFF),
+                            (np.uint64(1) << np.minimum(per, 63).astype(np.uint64)) - np.uint64(1))
+            y = tm & full
+            pin = np.zeros(tm.shape, dtype=np.int64)
             for _ in range(64):
-                cnt += (x & np.uint64(1)).astype(np.int64)
-                x >>= np.uint64(1)
-            mt = int(cnt.max())
+                pin += (y & np.uint64(1)).astype(np.int64)
+                y >>= np.uint64(1)
+            rows = int((per - pin).sum())
         return DeviceSplits(
-            n_splits=int(tm.shape[0]), max_train=mt,
+            n_splits=int(tm.shape[0]), max_train=int(pc.max()) if tm.size else 0,
             split_offsets=torch.from_numpy(np.ascontiguousarray(s.split_offsets, dtype=np.int64)).to(device),
-            train_masks=torch.from_numpy(tm.view(np.int64)).to(device))
+            train_masks=torch.from_numpy(tm.view(np.int64)).to(device), n_test_rows=rows)
 
     def c(self) -> _Splits:
-        return _Splits(self.n_splits, self.max_train, 0, _ptr(self.split_offsets), _ptr(self.train_masks))
+        return _Splits(self.n_splits, self.n_test_rows, self.max_train, 0, _ptr(self.split_offsets),
+                       _ptr(self.train_masks))
 
 
 class Context:

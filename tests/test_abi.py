@@ -40,10 +40,16 @@ def test_workspace_query_needs_no_gpu():
     cb = rs._Batch(b.n_programs, 0, b.n_rows, 64, 20, b.X.shape[0], int(b.feat_width.sum()),
                    None, None, None, None, None, None, None, None)
     S = 100
-    cs = rs._Splits(S, 32, 0, None, None)
+    cs = rs._Splits(S, 0, 32, 0, None, None)
     fit = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
-    # per fit: pair mask, size, order, offset, status, and up to 17 coefficient doubles
-    assert S * 6 * (4 + 1 + 4 + 8 + 1 + 17 * 8) <= fit <= S * 6 * (4 + 1 + 4 + 8 + 1 + 17 * 8) + 64 * 1024
+    # per fit: pair mask, size, order, offset, status, and up to 17 coefficient doubles;
+    # per test row (bound: S x max_versions when no row count is given): six predictions
+    need_fit = S * 6 * (4 + 1 + 4 + 8 + 1 + 17 * 8) + S * 64 * 6 * 8
+    assert need_fit <= fit <= need_fit + 64 * 1024
+    cs.n_test_rows = 1000
+    fit2 = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
+    assert fit2 - fit == (1000 - S * 64) * 6 * 8 or abs(fit2 - fit - (1000 - S * 64) * 48) < 512
+    cs.n_test_rows = 0
     nbytes = lib.rs_cv_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
     need = b.X.shape[0] * 8 + 3 * 64 * 64 * 8 + fit
     assert need <= nbytes <= need + 1024

@@ -31,9 +31,9 @@ def ctx(rs):
     c.close()
 
 
-def _run_both(rs, ctx, batch, splits, lam=1e-3, k=3, tau=1.05, flags=0, form=0):
+def _run_both(rs, ctx, batch, splits, lam=1e-3, k=3, tau=1.05, flags=0, form=0, exact_rows=True):
     db = rs.DeviceBatch.from_host(batch)
-    ds = rs.DeviceSplits.from_host(splits)
+    ds = rs.DeviceSplits.from_host(splits, batch=batch if exact_rows else None)
     g = rs.cv_run(ctx, db, ds, lam=lam, k=k, tau=tau, flags=flags, form=form, want_Z=True)
     r = oracle.cv_batch(batch, splits, lam=lam, k=k, tau=tau, flags=flags)
     return g, r
@@ -83,14 +83,39 @@ def test_tiny_config_lovo_full(rs, ctx, form):
     assert ndiff == 0
 
 
-@pytest.mark.parametrize("kind,k,flags,form", [
-    ("half", 3, 0, 0), ("frac", 6, 0, 0), ("frac", 2, 1, 0), ("half", 3, 0, 1), ("frac", 1, 1, 1)])
-def test_ragged_batches(rs, ctx, kind, k, flags, form):
+@pytest.mark.parametrize("kind,k,flags,form,exact", [
+    ("half", 3, 0, 0, True), ("frac", 6, 0, 0, False), ("frac", 2, 1, 0, True),
+    ("half", 3, 0, 1, True), ("frac", 1, 1, 1, False)])
+def test_ragged_batches(rs, ctx, kind, k, flags, form, exact):
     batch = synth.make_batch(9, versions=(1, 64), feat_choices=[8, 33, 64], dtype=np.float32,
                              seed=31 + k)
     splits = synth.make_splits(batch, kind, 37, seed=5 + k)
-    g, r = _run_both(rs, ctx, batch, splits, k=k, flags=flags, form=form)
+    g, r = _run_both(rs, ctx, batch, splits, k=k, flags=flags, form=form, exact_rows=exact)
     _check_cv(g, r, k, 1.05)
+
+
+def test_wrong_size_hints_are_caught(rs, ctx):
+    # hints smaller than the data: the kernels' own checks skip the excess and flag RS_EDATA
+    batch = synth.make_batch(3, versions=64, feat=16, seed=71)
+    splits = synth.make_splits(batch, "half", 9, seed=71)
+    db = rs.DeviceBatch.from_host(batch)
+    for bad in ("rows", "train"):
+        ds = rs.DeviceSplits.from_host(splits, batch=batch)
+        if bad == "rows":
+            ds.n_test_rows = ds.n_test_rows // 2
+        else:
+            ds.max_train = 8
+        Z = ctx.standardize(db)
+        zb = db.with_X(Z)
+        K = ctx.gram(zb)
+        ro = ctx.rec_offsets(zb, ds)
+        R = int(ro[-1])
+        out = rs.alloc_outputs(R, ds.n_splits, 3)
+        ctx.predict_rank(zb, K, ds, ro, out.rec_code, rec_pred=out.rec_pred, counters=out.counters)
+        torch.cuda.synchronize()
+        with pytest.raises(rs.RsError) as e:
+            ctx.check_device_status()
+        assert e.value.status == rs.RS_EDATA
 
 
 def test_degenerate_splits(rs, ctx):
@@ -147,7 +172,7 @@ def test_full_batched_cv_size_sampled(rs, ctx):
     # recomputed by the reference and compared row by row.
     batch = synth.make_batch(64, versions=(16, 64), feat=256, dtype=np.float32, seed=0)
     splits = synth.make_half_splits_fast(batch, 4096, seed=0)
-    db, ds = rs.DeviceBatch.from_host(batch), rs.DeviceSplits.from_host(splits)
+    db, ds = rs.DeviceBatch.from_host(batch), rs.DeviceSplits.from_host(splits, batch=batch)
     ro = ctx.rec_offsets(db, ds)
     R = int(ro[-1])
     out = rs.alloc_outputs(R, ds.n_splits, 3)
