@@ -194,6 +194,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
+                         "used for profiler captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -294,19 +297,19 @@ def main():
     top = max(("solve_small", "solve_large", "rank"), key=lambda k_: stage_ms.get(k_, 0.0))
     achieved = flops[top] / (stage_ms[top] * 1e-3) / 1e12
     path_achieved = sum(flops.values()) / (fit_ms * 1e-3) / 1e12
-    peak_meas = rs.measure_fma_peak(True, 2048) / 1e3
+    peak_meas = None if args.only_step else rs.measure_fma_peak(True, 2048) / 1e3
     peak = FP64_PEAK_NOMINAL_GFLOPS / 1e3
 
     # plain GPU form: one launch per step per program, FP64, one warp per fit, no persistence
     plain = None
-    if not args.no_plain and rank == 0:
+    if not args.no_plain and not args.only_step and rank == 0:
         plain = run_plain(rs, ctx, batch, splits, dev, stream, flush, args)
 
     # end to end through the C ABI single call with host buffers (pinned), copies timed
-    e2e = run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
+    e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.only_step:
         cpu = cpu_reference_sample(batch, splits, args.cpu_seconds)
 
     line = {
