@@ -74,6 +74,18 @@ long long okey_host(double x) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
+// 1/d for a positive finite d: FP32 seed, then two Newton steps r <- r + r (1 - d r)
+// (Newton's method on f(r) = 1/r - d).  Outside the float range: plain division.
+__device__ __forceinline__ double rcp_newton(double d) {
+    if (d < 1e-30 || d > 1e30) return 1.0 / d;
+    double r = (double)__frcp_rn((float)d);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    return r;
+}
+
 // The a-th set bit (0-based) of x; x must have more than a set bits.
 __device__ __forceinline__ int select_bit(uint64_t x, int a) {
     for (int i = 0; i < a; ++i) x &= x - 1;
@@ -159,7 +171,7 @@ __global__ void __launch_bounds__(256)
 plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __restrict__ split_off,
                  const uint64_t* __restrict__ tm, int64_t S, const uint8_t* __restrict__ pb,
                  const uint8_t* __restrict__ pa, const int* __restrict__ npair, uint32_t* fit_pm,
-                 uint8_t* fit_n, unsigned* hist, int nmax, int* dstatus) {
+                 uint8_t* fit_n, unsigned* hist, int nmax, int* split_prog, int* dstatus) {
     __shared__ unsigned h[kHist];
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
     __syncthreads();
@@ -168,6 +180,7 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         const int64_t s = f / RS_NOPT;
         const int j = (int)(f - s * RS_NOPT);
         const int p = rs_find_segment(split_off, P, s);
+        if (j == 0) split_prog[s] = p;
         const int V = (int)(row_off[p + 1] - row_off[p]);
         uint32_t pm = 0;
         if (V >= 1 && V <= RS_MAXV) {
@@ -260,90 +273,101 @@ struct PredTarget {
     int64_t room;         // rows left in the buffer from dst (guards a wrong size hint)
 };
 
+// One fit of n = N pairs in registers.  M = K_TT + lambda I = L D L^T (unit lower L, no
+// square roots; reciprocal pivots by rcp_newton).  With t_y = L^-1 y and t_1 = L^-1 1:
+//   1^T M^-1 y = t_1^T D^-1 t_y,  1^T M^-1 1 = t_1^T D^-1 t_1,  b = their ratio,
+//   alpha = L^-T D^-1 (t_y - b t_1)   (one backward solve).
 template <int N>
 __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
                                            const double* __restrict__ yl, uint32_t pm, double lambda,
                                            double* out, const PredTarget* pt) {
     int vb[N];
-    double u[N], w[N], L[tri(N)], ri[N];
+    double ty[N], t1[N], L[tri(N)], dinv[N];
     uint32_t x = pm;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
         const int q = __ffs(x) - 1;
         x &= x - 1;
         vb[a] = pb[q];
-        u[a] = yl[q];
-        w[a] = 1.0;
+        ty[a] = yl[q];
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int k = 0; k <= i; ++k) {
-            double s = __ldg(Kp + vb[i] * RS_GRAM_LD + vb[k]);
-            if (k == i) s += lambda;
-#pragma unroll
-            for (int m = 0; m < k; ++m) s = fma(-L[tri(i) + m], L[tri(k) + m], s);
-            if (k < i) {
-                L[tri(i) + k] = s * ri[k];
-            } else {
-                if (!pos_finite(s)) return RS_FIT_NOTPD;
-                ri[i] = rsqrt_newton(s);
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {          // L t = rhs (two right-hand sides)
+        double c[N];                       // c_m = L_im d_m of the current row
 #pragma unroll
         for (int k = 0; k < i; ++k) {
-            u[i] = fma(-L[tri(i) + k], u[k], u[i]);
-            w[i] = fma(-L[tri(i) + k], w[k], w[i]);
+            double s = __ldg(Kp + vb[i] * RS_GRAM_LD + vb[k]);
+#pragma unroll
+            for (int m = 0; m < k; ++m) s = fma(-c[m], L[tri(k) + m], s);
+            c[k] = s;
+            L[tri(i) + k] = s * dinv[k];
         }
-        u[i] *= ri[i];
-        w[i] *= ri[i];
+        double d = __ldg(Kp + vb[i] * RS_GRAM_LD + vb[i]) + lambda;
+#pragma unroll
+        for (int m = 0; m < i; ++m) d = fma(-c[m], L[tri(i) + m], d);
+        if (!pos_finite(d)) return RS_FIT_NOTPD;
+        dinv[i] = rcp_newton(d);
     }
 #pragma unroll
-    for (int i = N - 1; i >= 0; --i) {     // L^T x = t
+    for (int i = 0; i < N; ++i) {          // L t = rhs, unit diagonal, two right-hand sides
+        t1[i] = 1.0;
 #pragma unroll
-        for (int k = i + 1; k < N; ++k) {
-            u[i] = fma(-L[tri(k) + i], u[k], u[i]);
-            w[i] = fma(-L[tri(k) + i], w[k], w[i]);
+        for (int k = 0; k < i; ++k) {
+            ty[i] = fma(-L[tri(i) + k], ty[k], ty[i]);
+            t1[i] = fma(-L[tri(i) + k], t1[k], t1[i]);
         }
-        u[i] *= ri[i];
-        w[i] *= ri[i];
     }
-    double su = 0.0, sw = 0.0;
+    double num = 0.0, den = 0.0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        su += u[i];
-        sw += w[i];
+        const double sc = t1[i] * dinv[i];
+        num = fma(sc, ty[i], num);
+        den = fma(sc, t1[i], den);
     }
-    const double b = su / sw;
+    const double b = num * rcp_newton(den);
+#pragma unroll
+    for (int i = 0; i < N; ++i) ty[i] = fma(-b, t1[i], ty[i]) * dinv[i];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i)       // L^T alpha = D^-1 (t_y - b t_1)
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) ty[i] = fma(-L[tri(k) + i], ty[k], ty[i]);
     bool fin = finite_bits(b);
     out[0] = b;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        u[i] = fma(-b, w[i], u[i]);        // alpha
-        fin = fin && finite_bits(u[i]);
-        out[1 + i] = u[i];
+        fin = fin && finite_bits(ty[i]);
+        out[1 + i] = ty[i];
     }
     if (!fin) return RS_FIT_NONFINITE;
     if (pt) {                              // predictions b + sum_a alpha_a K[t][v_a]
-        for (uint64_t c = pt->cand; c; c &= c - 1) {
-            const int t = __ffsll((long long)c) - 1;
+        for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
+            const int t = __ffsll((long long)cm) - 1;
             const int r = __popcll(pt->test & ((1ull << t) - 1ull));
             const double* Kt = Kp + t * RS_GRAM_LD;
             double yh = b;
 #pragma unroll
-            for (int a = 0; a < N; ++a) yh = fma(u[a], __ldg(Kt + vb[a]), yh);
+            for (int a = 0; a < N; ++a) yh = fma(ty[a], __ldg(Kt + vb[a]), yh);
             if (r < pt->room) pt->dst[r] = yh;
         }
     }
     return RS_FIT_OK;
 }
 
+template <int N, int NHI>
+__device__ __forceinline__ int solve_dispatch(int n, const double* Kp, const uint8_t* pb, const double* yl,
+                                              uint32_t pm, double lambda, double* out, const PredTarget* pt) {
+    if constexpr (N >= NHI) {
+        return solve_fixed<N>(Kp, pb, yl, pm, lambda, out, pt);
+    } else {
+        if (n == N) return solve_fixed<N>(Kp, pb, yl, pm, lambda, out, pt);
+        return solve_dispatch<N + 1, NHI>(n, Kp, pb, yl, pm, lambda, out, pt);
+    }
+}
+
 struct SolveArgs {
     int P;
     const int64_t* split_off;
+    const int* split_prog;
     const double* K;
     const uint8_t* pb;
     const double* ylab;
@@ -404,44 +428,38 @@ __device__ __forceinline__ void count_status(const SolveArgs& a, int st, bool ac
     }
 }
 
-__global__ void __launch_bounds__(128)
+// Fits with NLO <= n <= NHI, one per thread, in bucket order (n is warp-uniform except at
+// bucket boundaries).  Grid-stride over the bucket positions of that range.
+template <int NLO, int NHI, int MINB>
+__global__ void __launch_bounds__(128, MINB)
 solve_small_kernel(const SolveArgs a) {
     __shared__ long long start[kHist], cstart[kHist];
     if (threadIdx.x == 0) bucket_tables(a.hist, start, cstart);
     __syncthreads();
-    const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = pos < start[kNReg + 1];
-    int st = RS_FIT_OK;
-    if (active) {
-        int n = 1;
-        while (start[n + 1] <= pos) ++n;
-        const int64_t f = a.order[pos];
-        const int64_t s = f / RS_NOPT;
-        const int j = (int)(f - s * RS_NOPT);
-        const int p = rs_find_segment(a.split_off, a.P, s);
-        const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
-        const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-        const uint32_t pm = a.fit_pm[f];
-        double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
-        const uint8_t* pb = a.pb + base;
-        const double* yl = a.ylab + base;
-        PredTarget ptv;
-        const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
-        switch (n) {
-            case 1: st = solve_fixed<1>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 2: st = solve_fixed<2>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 3: st = solve_fixed<3>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 4: st = solve_fixed<4>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 5: st = solve_fixed<5>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 6: st = solve_fixed<6>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 7: st = solve_fixed<7>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 8: st = solve_fixed<8>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            case 9: st = solve_fixed<9>(Kp, pb, yl, pm, a.lambda, out, pt); break;
-            default: st = solve_fixed<10>(Kp, pb, yl, pm, a.lambda, out, pt); break;
+    const long long lo = start[NLO], hi = start[NHI + 1];
+    for (long long base = lo + (long long)blockIdx.x * blockDim.x; base < hi;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long pos = base + threadIdx.x;
+        const bool active = pos < hi;
+        int st = RS_FIT_OK;
+        if (active) {
+            int n = NLO;
+            while (start[n + 1] <= pos) ++n;
+            const int64_t f = a.order[pos];
+            const int64_t s = f / RS_NOPT;
+            const int j = (int)(f - s * RS_NOPT);
+            const int p = a.split_prog[s];
+            const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+            const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+            double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
+            PredTarget ptv;
+            const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
+            st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f], a.lambda,
+                                          out, pt);
+            finish_record(a, f, n, st, out);
         }
-        finish_record(a, f, n, st, out);
+        count_status(a, st, active);
     }
-    count_status(a, st, active);
 }
 
 // ====================================================================== solve, one fit per warp
@@ -553,7 +571,7 @@ solve_large_kernel(const SolveArgs a) {
         const int64_t f = a.order[pos];
         const int64_t s = f / RS_NOPT;
         const int j = (int)(f - s * RS_NOPT);
-        const int p = rs_find_segment(a.split_off, a.P, s);
+        const int p = a.split_prog[s];
         const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
         double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
@@ -573,6 +591,7 @@ solve_large_kernel(const SolveArgs a) {
 // list is counted directly (ties: lower index first), so every array index is static.
 struct RankPassArgs {
     int P;
+    const int* split_prog;
     const int64_t* row_off;
     const uint8_t* masks;
     const int64_t* split_off;
@@ -593,8 +612,13 @@ struct RankPassArgs {
     unsigned long long* counters;
 };
 
-__device__ __forceinline__ bool before(long long ka, int ja, long long kb, int jb) {
-    return ka > kb || (ka == kb && ja < jb);
+// The 12-comparator sorting network for six inputs (depth 5).  Each comparator leaves the
+// element that ranks first (larger key; on equal keys the lower optimization index) in its
+// first slot, so the network sorts by (prediction descending, index ascending).
+__host__ __device__ constexpr int net6(int c, int side) {
+    constexpr int a[12] = {0, 1, 2, 1, 3, 0, 2, 0, 2, 4, 1, 3};
+    constexpr int b[12] = {5, 3, 4, 2, 4, 3, 5, 1, 3, 5, 2, 4};
+    return side == 0 ? a[c] : b[c];
 }
 
 __global__ void __launch_bounds__(256)
@@ -605,60 +629,83 @@ rank_pass_kernel(const RankPassArgs a) {
     uint32_t cnt[14];
 #pragma unroll
     for (int c = 0; c < 14; ++c) cnt[c] = 0;
+    const long long kNone = (long long)0x8000000000000000ull;   // below every valid key
     for (int64_t s = wg; s < a.S; s += nw) {
-        const int p = rs_find_segment(a.split_off, a.P, s);
+        const int p = a.split_prog[s];
         const int64_t rv = a.row_off[p];
         const int V = (int)(a.row_off[p + 1] - rv);
         if (V < 1 || V > RS_MAXV) continue;
         const uint64_t test = ~a.tm[s] & rs_full_mask(V);
-        const int nt = __popcll(test);
         const int64_t base = a.rec_offsets[s];
-        if (base + nt > a.R) continue;
-        int okm = 0;
+        if (base + __popcll(test) > a.R) continue;
+        const int okm = __ballot_sync(0xffffffffu, lane < RS_NOPT && a.status[s * RS_NOPT + (lane < RS_NOPT ? lane : 0)] == RS_FIT_OK) & 63;
 #pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) okm |= (a.status[s * RS_NOPT + j] == RS_FIT_OK) << j;
-        const uint32_t lo = (uint32_t)test, hi = (uint32_t)(test >> 32);
-        const int clo = __popc(lo);
-        for (int r = lane; r < nt; r += 32) {
-            const int t = r < clo ? (int)__fns(lo, 0, r + 1) : 32 + (int)__fns(hi, 0, r - clo + 1);
-            const int64_t row = base + r;
+        for (int half = 0; half < 2; ++half) {
+            const int t = lane + 32 * half;         // one version slot per lane
+            if (t >= V || !((test >> t) & 1)) continue;
+            const int64_t row = base + __popcll(test & ((1ull << t) - 1ull));
             const int mt = a.masks[rv + t] & 63;
             const int kn = a.known[(int64_t)p * RS_MAXV + t];
             const long long* ak = a.act_key + ((int64_t)p * RS_MAXV + t) * RS_NOPT;
+            const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
+            const int validm = candm & okm;
+            cnt[13] += __popc(candm & ~okm);
             double pred[RS_NOPT];
-            long long key[RS_NOPT];
-            int validm = 0;
+            long long key[RS_NOPT], akv[RS_NOPT];
+            int idx[RS_NOPT];
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j) {    // independent loads, all issued up front
+                pred[j] = a.predbuf[(int64_t)j * a.R + row];
+                akv[j] = ak[j];
+            }
+            int apos = 0;
 #pragma unroll
             for (int j = 0; j < RS_NOPT; ++j) {
-                pred[j] = nan_d();
-                key[j] = 0;
-                const bool cand = (a.flags & RS_RANK_ALL) || !((mt >> j) & 1);
-                if (!cand) continue;
-                if (!((okm >> j) & 1)) {
-                    cnt[13] += 1;
-                    continue;
-                }
-                pred[j] = a.predbuf[(int64_t)j * a.R + row];
-                key[j] = okey(pred[j]);
-                validm |= 1 << j;
+                const bool v = (validm >> j) & 1;
+                if (!v) pred[j] = nan_d();
+                key[j] = v ? okey(pred[j]) : kNone;
+                idx[j] = j;
+                apos |= (akv[j] > 0) << j;
             }
-            int above = 0;
+            const int scored = validm & kn;
+            // top-1 agreement: best prediction and best actual among scored candidates
+            int bp = -1, ba = -1;
+            long long kbp = 0, kba = 0;
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j)
-                if (((validm >> j) & 1) && key[j] >= a.ktau) above |= 1 << j;
+            for (int j = 0; j < RS_NOPT; ++j) {
+                if (!((scored >> j) & 1)) continue;
+                if ((key[j] > 0) == (akv[j] > 0)) cnt[3] += 1;
+                if (bp < 0 || key[j] > kbp) { bp = j; kbp = key[j]; }
+                if (ba < 0 || akv[j] > kba) { ba = j; kba = akv[j]; }
+            }
+            double sp[RS_NOPT];
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j) sp[j] = pred[j];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                const int x = net6(c, 0), y = net6(c, 1);
+                const bool sw = key[y] > key[x] || (key[y] == key[x] && idx[y] < idx[x]);
+                const long long tk = sw ? key[y] : key[x];
+                key[y] = sw ? key[x] : key[y];
+                key[x] = tk;
+                const int ti = sw ? idx[y] : idx[x];
+                idx[y] = sw ? idx[x] : idx[y];
+                idx[x] = ti;
+                const double tp = sw ? sp[y] : sp[x];
+                sp[y] = sw ? sp[x] : sp[y];
+                sp[x] = tp;
+            }
             uint32_t code = 0x0FFFFFF0u;
             int c = 0;
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) {
-                if (!((above >> j) & 1)) continue;
-                int pos = 0;
-#pragma unroll
-                for (int i = 0; i < RS_NOPT; ++i)
-                    if (i != j && ((above >> i) & 1) && before(key[i], i, key[j], j)) ++pos;
-                if (pos < a.k) {
-                    code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
-                    if (a.rec_pred) a.rec_pred[row * a.k + pos] = pred[j];
-                    ++c;
+            for (int x = 0; x < RS_NOPT; ++x) {
+                if (x < a.k && key[x] != kNone && key[x] >= a.ktau) {
+                    code = (code & ~(0xFu << (4 + 4 * x))) | ((uint32_t)idx[x] << (4 + 4 * x));
+                    if (a.rec_pred) a.rec_pred[row * a.k + x] = sp[x];
+                    const int j = idx[x];
+                    cnt[5] += (scored >> j) & 1;
+                    cnt[6] += ((scored & apos) >> j) & 1;
+                    c = x + 1;
                 }
             }
             code = (code & ~0xFu) | (uint32_t)c;
@@ -668,34 +715,10 @@ rank_pass_kernel(const RankPassArgs a) {
             if (a.pred_all)
 #pragma unroll
                 for (int j = 0; j < RS_NOPT; ++j) a.pred_all[row * RS_NOPT + j] = pred[j];
-            const int scored = validm & kn;
             cnt[0] += 1;
             cnt[1] += __popc(validm);
             cnt[2] += __popc(scored);
             cnt[4] += c;
-            int bp = -1, ba = -1;
-            long long kbp = 0, kba = 0;
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) {
-                if (!((scored >> j) & 1)) continue;
-                const long long akj = ak[j];
-                if ((key[j] > 0) == (akj > 0)) cnt[3] += 1;
-                if (bp < 0 || key[j] > kbp) {
-                    bp = j;
-                    kbp = key[j];
-                }
-                if (ba < 0 || akj > kba) {
-                    ba = j;
-                    kba = akj;
-                }
-            }
-            for (int x = 0; x < c; ++x) {
-                const int j = (code >> (4 + 4 * x)) & 0xF;
-                if ((scored >> j) & 1) {
-                    cnt[5] += 1;
-                    if (ak[j] > 0) cnt[6] += 1;
-                }
-            }
             if (bp >= 0) {
                 cnt[7] += 1;
                 if (bp == ba) cnt[8] += 1;
@@ -1048,6 +1071,7 @@ struct FitWs {
     uint64_t* cand;      // [P][6]
     long long* act_key;  // [P][64][6]
     uint8_t* known;      // [P][64]
+    int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
     uint8_t* fit_n;      // [S*6]
     int* order;          // [S*6]
@@ -1075,6 +1099,7 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
     w.act_key = (long long*)take(P * RS_MAXV * RS_NOPT * sizeof(long long));
     w.known = (uint8_t*)take(P * RS_MAXV);
+    w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
     w.fit_n = (uint8_t*)take(S6);
     w.order = (int*)take(S6 * sizeof(int));
@@ -1084,6 +1109,20 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.predbuf = (double*)take((size_t)RS_NOPT * Rcap * sizeof(double));
     w.bytes = o;
     return w;
+}
+
+template <int NLO, int NHI, int MINB>
+cudaError_t launch_small(const SolveArgs& sa, int sms, int64_t S6, cudaStream_t st) {
+    auto kern = solve_small_kernel<NLO, NHI, MINB>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (S6 + 127) / 128;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, 128, 0, st>>>(sa);
+    return cudaGetLastError();
 }
 
 int nmax_of(int max_train) {
@@ -1119,7 +1158,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
     plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
                                                 a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
-                                                nmax, a.dstatus);
+                                                nmax, w.split_prog, a.dstatus);
     mark(2);
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
@@ -1127,19 +1166,21 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                                                   status, user ? a.coef_out : nullptr, a.counters);
     mark(3);
     const bool rank = a.rec_code != nullptr;
-    SolveArgs sa{a.P, a.split_offsets, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
+    SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
                  a.rows_cap, a.flags, a.dstatus};
-    solve_small_kernel<<<(unsigned)((S6 + 127) / 128), 128, 0, st>>>(sa);
-    mark(4);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = launch_small<1, 6, 4>(sa, sms, S6, st);
+    if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, st);
+    if (e != cudaSuccess) return e;
+    mark(4);
     solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, 0, st>>>(sa);
     mark(5);
     if (rank) {
-        RankPassArgs ra{a.P, a.row_offsets, a.masks, a.split_offsets, a.train_masks, a.S,
+        RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.split_offsets, a.train_masks, a.S,
                         a.rec_offsets, status, w.predbuf, a.rows_cap, w.act_key, w.known, a.k,
                         0, a.flags, a.rec_code, a.rec_pred, a.pred_all, a.counters};
         ra.ktau = okey_host(a.log_tau);
