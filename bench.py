@@ -32,6 +32,15 @@ CFG = dict(programs=64, versions=(16, 64), feat=256, splits=4096, lam=1e-3, k=3,
 FP64_PEAK_NOMINAL_GFLOPS = 152 * 4 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 
 
+def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the machine's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def make_inputs(seed):
     from paper_1910_07776_gb300 import synth
     b = synth.make_batch(CFG["programs"], versions=CFG["versions"], feat=CFG["feat"],
@@ -40,14 +49,15 @@ def make_inputs(seed):
     return b, s
 
 
-def algorithmic_flops(batch, splits, nreg=10):
-    """FP64 flops of the fit/predict path, counted from the definitions: per fit with n
-    pairs a Cholesky (n^3/3), two right-hand sides through both triangular solves (4 n^2)
-    and the intercept / dual update (4 n); per prediction 2 n.  Split into fits solved one
-    per thread (n <= nreg), fits solved one per warp (n > nreg) and predictions."""
-    total_fit = 0.0
-    total_big = 0.0
-    total_pred = 0.0
+def algorithmic_work(batch, splits, k=3, nreg=10):
+    """Algorithmic work of the fit/predict stages, counted from the definitions.
+    FP64 flops: per fit with n pairs a factorisation (n^3/3), two right-hand sides through
+    both triangular solves (4 n^2) and the intercept / dual update (4 n); per prediction
+    2 n.  Fits with n <= nreg (and their predictions) belong to the one-thread-per-fit
+    solver, larger ones to the one-warp-per-fit solver.  Rank stage bytes: per test row the
+    version mask (1 B), its scoring summary (4 B), the code word (4 B) and k reported
+    values (8 B each), plus 8 B per prediction read."""
+    out = {"solve_small": 0.0, "solve_large": 0.0, "rows": 0, "preds": 0}
     for p in range(batch.n_programs):
         rs_ = batch.program_rows(p)
         m = batch.masks[rs_].astype(np.int64)
@@ -56,6 +66,12 @@ def algorithmic_flops(batch, splits, nreg=10):
         T = splits.train_masks[splits.split_offsets[p]:splits.split_offsets[p + 1]].astype(np.uint64)
         full = np.uint64((1 << V) - 1) if V < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
         test = (~T) & full
+        x = test.copy()
+        rows = np.zeros(x.shape, dtype=np.int64)
+        for _ in range(V):
+            rows += (x & np.uint64(1)).astype(np.int64)
+            x = x >> np.uint64(1)
+        out["rows"] += int(rows.sum())
         for j in range(6):
             pm = [(1 << v) | (1 << slot[int(m[v]) | (1 << j)]) for v in range(V)
                   if not (m[v] >> j) & 1 and (int(m[v]) | (1 << j)) in slot]
@@ -69,11 +85,12 @@ def algorithmic_flops(batch, splits, nreg=10):
             for _ in range(V):
                 cnt += (x & np.uint64(1)).astype(np.float64)
                 x = x >> np.uint64(1)
-            fl = n ** 3 / 3 + 4 * n ** 2 + 4 * n
-            total_fit += float(np.sum(fl * (n <= nreg)))
-            total_big += float(np.sum(fl * (n > nreg)))
-            total_pred += float(np.sum(2 * n * cnt * (n > 0)))
-    return {"solve_small": total_fit, "solve_large": total_big, "rank": total_pred}
+            fl = n ** 3 / 3 + 4 * n ** 2 + 4 * n + 2 * n * cnt
+            out["solve_small"] += float(np.sum(fl * (n >= 1) * (n <= nreg)))
+            out["solve_large"] += float(np.sum(fl * (n > nreg)))
+            out["preds"] += int(np.sum(cnt * (n > 0)))
+    out["rank_bytes"] = float(out["rows"] * (1 + 4 + 4 + 8 * k) + 8 * out["preds"])
+    return out
 
 
 class ClockSampler:
@@ -291,14 +308,36 @@ def main():
     acc = {"sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1),
            "rec_precision": cnt[6] / max(cnt[5], 1), "recs_per_row": cnt[4] / max(cnt[0], 1)}
 
-    flops = algorithmic_flops(batch, splits)
+    work = algorithmic_work(batch, splits, CFG["k"])
     fit_ms = parts[3] / args.steps
     stage_ms = {k_: v_ / args.steps for k_, v_ in stages.items()}
     top = max(("solve_small", "solve_large", "rank"), key=lambda k_: stage_ms.get(k_, 0.0))
-    achieved = flops[top] / (stage_ms[top] * 1e-3) / 1e12
-    path_achieved = sum(flops.values()) / (fit_ms * 1e-3) / 1e12
     peak_meas = None if args.only_step else rs.measure_fma_peak(True, 2048) / 1e3
-    peak = FP64_PEAK_NOMINAL_GFLOPS / 1e3
+    fp64_peak = FP64_PEAK_NOMINAL_GFLOPS / 1e3
+    hbm_peak = measured_hbm_peak()
+    if top == "rank":
+        achieved = work["rank_bytes"] / (stage_ms[top] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "rank_pass_kernel", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+                "bytes_per_launch": work["rank_bytes"]}
+    else:
+        achieved = work[top] / (stage_ms[top] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "solve_" + top.split("_")[1] + "_kernel", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "flops_per_launch": work[top]}
+    path_flops = work["solve_small"] + work["solve_large"]
+    roof["peak_measured_fp64_fma_chains"] = peak_meas
+    roof["stages"] = {
+        "solve_small": {"ms": stage_ms.get("solve_small"), "flops": work["solve_small"],
+                        "frac_fp64": work["solve_small"] / (stage_ms["solve_small"] * 1e-3) / 1e12 / fp64_peak},
+        "solve_large": {"ms": stage_ms.get("solve_large"), "flops": work["solve_large"],
+                        "frac_fp64": work["solve_large"] / (stage_ms["solve_large"] * 1e-3) / 1e12 / fp64_peak},
+        "rank": {"ms": stage_ms.get("rank"), "bytes": work["rank_bytes"],
+                 "frac_hbm": work["rank_bytes"] / (stage_ms["rank"] * 1e-3) / 1e9 / hbm_peak},
+        "fit_predict_path": {"ms": fit_ms, "fp64_flops": path_flops,
+                             "frac_fp64": path_flops / (fit_ms * 1e-3) / 1e12 / fp64_peak}}
 
     # plain GPU form: one launch per step per program, FP64, one warp per fit, no persistence
     plain = None
@@ -324,19 +363,13 @@ def main():
         "kernels_ms": {"standardize": parts[0] / args.steps, "gram_f64": parts[1] / args.steps,
                        "plan_rows": parts[2] / args.steps, "fit_predict_rank": fit_ms,
                        **{"fit." + k_: v_ for k_, v_ in stage_ms.items()}},
-        "roofline": {"bound": "alu", "kernel": top, "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None,
-                     "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
-                     "peak_measured_fma_chains": peak_meas, "flops_per_launch": flops[top],
-                     "fit_predict_path": {"flops": sum(flops.values()), "ms": fit_ms,
-                                          "achieved": path_achieved, "frac": path_achieved / peak}},
+        "roofline": roof,
         "accuracy": acc,
         "plain_form": plain,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
-        "gpu_launches": 11 * args.steps,
+        "gpu_launches": 12 * args.steps,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

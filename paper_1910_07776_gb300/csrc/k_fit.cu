@@ -95,13 +95,13 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
 // ====================================================================== pair tables
 // One block per program: the before/after pairs of each optimization in ascending order of
 // the before slot, and their labels.  Tables: [P][6][32] (u8, u8, double), counts [P][6].
-// Also, per program: cand[p][j] = slots whose mask lacks j (uint64), and for every slot t
-// and optimization j the actual log speedup of adding j, as an order key, with a bit in
-// known[p][t] when the version t|j exists (Sec. 5: the measured speedup of the pair).
+// Also, per program: cand[p][j] = slots whose mask lacks j (uint64), and for every slot t a
+// summary of the actual log speedups of adding each j (Sec. 5: the measured speedup of the
+// pair, used only for scoring).
 __global__ void __launch_bounds__(64)
 pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restrict__ masks,
              const double* __restrict__ log_time, uint8_t* pb, uint8_t* pa, double* ylab,
-             int* npair, uint64_t* cand, long long* act_key, uint8_t* known, int* dstatus) {
+             int* npair, uint64_t* cand, uint32_t* rowinfo, int* dstatus) {
     __shared__ int8_t slot_of[RS_MAXV];
     __shared__ uint8_t msk[RS_MAXV];
     __shared__ double lt[RS_MAXV];
@@ -148,21 +148,33 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
         cand[p * RS_NOPT + j] = cm;
     }
     {
+        // rowinfo[p][t]: bits 0-5 known (version t|j exists), bits 6-11 actual speedup > 1,
+        // bits 12-29 the six optimizations ordered by actual log speedup (descending, lower
+        // index first on ties, unknown last), 3 bits each.
         const int t = tid;
-        uint8_t kn = 0;
-        long long* ak = act_key + ((int64_t)p * RS_MAXV + t) * RS_NOPT;
+        long long key[RS_NOPT];
+        int kn = 0, apos = 0;
         for (int j = 0; j < RS_NOPT; ++j) {
-            long long key = 0;
+            key[j] = (long long)0x8000000000000000ull;
             if (t < V && !((msk[t] >> j) & 1)) {
                 const int w = slot_of[msk[t] | (1 << j)];
                 if (w >= 0) {
-                    key = okey(lt[t] - lt[w]);
-                    kn |= (uint8_t)(1u << j);
+                    key[j] = okey(lt[t] - lt[w]);
+                    kn |= 1 << j;
+                    apos |= (key[j] > 0) << j;
                 }
             }
-            ak[j] = key;
         }
-        known[(int64_t)p * RS_MAXV + t] = kn;
+        uint32_t ord = 0;
+        int used = 0;
+        for (int x = 0; x < RS_NOPT; ++x) {
+            int best = -1;
+            for (int j = 0; j < RS_NOPT; ++j)
+                if (!((used >> j) & 1) && (best < 0 || key[j] > key[best])) best = j;
+            used |= 1 << best;
+            ord |= (uint32_t)best << (3 * x);
+        }
+        rowinfo[(int64_t)p * RS_MAXV + t] = (uint32_t)kn | ((uint32_t)apos << 6) | (ord << 12);
     }
 }
 
@@ -586,23 +598,23 @@ solve_large_kernel(const SolveArgs a) {
 }
 
 // ====================================================================== rank pass
-// One warp per split, one lane per test row.  No FP64 arithmetic: predictions (written by
-// the solve kernels) are compared as order keys; each candidate's place in the sorted
-// list is counted directly (ties: lower index first), so every array index is static.
+// One warp per split; its test rows are compacted onto the lanes (one row per lane).  No
+// FP64 arithmetic: predictions (written by the solve kernels) are compared as order keys.
+// Ranking: 15 comparisons give, for each candidate j, the set of candidates that rank
+// before it (larger key; on equal keys the lower index); its place is the popcount of
+// that set restricted to the candidates at or above the threshold.
 struct RankPassArgs {
     int P;
     const int* split_prog;
     const int64_t* row_off;
     const uint8_t* masks;
-    const int64_t* split_off;
     const uint64_t* tm;
     int64_t S;
     const int64_t* rec_offsets;
     const uint8_t* status;
     const double* predbuf;       // [6][R]
     int64_t R;
-    const long long* act_key;    // [P][64][6]
-    const uint8_t* known;        // [P][64]
+    const uint32_t* rowinfo;     // [P][64]
     int k;
     long long ktau;
     int flags;
@@ -612,125 +624,119 @@ struct RankPassArgs {
     unsigned long long* counters;
 };
 
-// The 12-comparator sorting network for six inputs (depth 5).  Each comparator leaves the
-// element that ranks first (larger key; on equal keys the lower optimization index) in its
-// first slot, so the network sorts by (prediction descending, index ascending).
-__host__ __device__ constexpr int net6(int c, int side) {
-    constexpr int a[12] = {0, 1, 2, 1, 3, 0, 2, 0, 2, 4, 1, 3};
-    constexpr int b[12] = {5, 3, 4, 2, 4, 3, 5, 1, 3, 5, 2, 4};
-    return side == 0 ? a[c] : b[c];
-}
+constexpr int kRankWarps = 8;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kRankWarps * 32)
 rank_pass_kernel(const RankPassArgs a) {
-    const int lane = threadIdx.x & 31;
+    __shared__ uint8_t slots[kRankWarps][RS_MAXV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    uint32_t cnt[14];
+    const double* pbj[RS_NOPT];
 #pragma unroll
-    for (int c = 0; c < 14; ++c) cnt[c] = 0;
-    const long long kNone = (long long)0x8000000000000000ull;   // below every valid key
+    for (int j = 0; j < RS_NOPT; ++j) pbj[j] = a.predbuf + (int64_t)j * a.R;
+    uint32_t c_rows = 0, c_pred = 0, c_scored = 0, c_sign = 0, c_rec = 0, c_reck = 0, c_rech = 0;
+    uint32_t c_t1 = 0, c_t1h = 0, c_inv = 0;
     for (int64_t s = wg; s < a.S; s += nw) {
         const int p = a.split_prog[s];
         const int64_t rv = a.row_off[p];
         const int V = (int)(a.row_off[p + 1] - rv);
         if (V < 1 || V > RS_MAXV) continue;
         const uint64_t test = ~a.tm[s] & rs_full_mask(V);
+        const int nt = __popcll(test);
         const int64_t base = a.rec_offsets[s];
-        if (base + __popcll(test) > a.R) continue;
-        const int okm = __ballot_sync(0xffffffffu, lane < RS_NOPT && a.status[s * RS_NOPT + (lane < RS_NOPT ? lane : 0)] == RS_FIT_OK) & 63;
+        if (base + nt > a.R) continue;
+        const int okm = __ballot_sync(0xffffffffu, lane < RS_NOPT &&
+                                      a.status[s * RS_NOPT + (lane < RS_NOPT ? lane : 0)] == RS_FIT_OK) & 63;
+        __syncwarp();
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int t = lane + 32 * half;         // one version slot per lane
-            if (t >= V || !((test >> t) & 1)) continue;
-            const int64_t row = base + __popcll(test & ((1ull << t) - 1ull));
+        for (int h = 0; h < 2; ++h) {
+            const int t = lane + 32 * h;
+            if (t < V && ((test >> t) & 1)) slots[warp][__popcll(test & ((1ull << t) - 1ull))] = (uint8_t)t;
+        }
+        __syncwarp();
+        for (int r = lane; r < nt; r += 32) {
+            const int t = slots[warp][r];
+            const int64_t row = base + r;
             const int mt = a.masks[rv + t] & 63;
-            const int kn = a.known[(int64_t)p * RS_MAXV + t];
-            const long long* ak = a.act_key + ((int64_t)p * RS_MAXV + t) * RS_NOPT;
+            const uint32_t info = a.rowinfo[(int64_t)p * RS_MAXV + t];
+            double pred[RS_NOPT];
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j) pred[j] = pbj[j][row];
             const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
             const int validm = candm & okm;
-            cnt[13] += __popc(candm & ~okm);
-            double pred[RS_NOPT];
-            long long key[RS_NOPT], akv[RS_NOPT];
-            int idx[RS_NOPT];
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) {    // independent loads, all issued up front
-                pred[j] = a.predbuf[(int64_t)j * a.R + row];
-                akv[j] = ak[j];
-            }
-            int apos = 0;
+            long long key[RS_NOPT];
+            int above = 0, spos = 0;
 #pragma unroll
             for (int j = 0; j < RS_NOPT; ++j) {
-                const bool v = (validm >> j) & 1;
-                if (!v) pred[j] = nan_d();
-                key[j] = v ? okey(pred[j]) : kNone;
-                idx[j] = j;
-                apos |= (akv[j] > 0) << j;
+                key[j] = okey(pred[j]);
+                above |= (key[j] >= a.ktau) << j;
+                spos |= (key[j] > 0) << j;
             }
-            const int scored = validm & kn;
-            // top-1 agreement: best prediction and best actual among scored candidates
-            int bp = -1, ba = -1;
-            long long kbp = 0, kba = 0;
+            above &= validm;
+            int bm[RS_NOPT];                       // bm[j]: candidates ranking before j
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) {
-                if (!((scored >> j) & 1)) continue;
-                if ((key[j] > 0) == (akv[j] > 0)) cnt[3] += 1;
-                if (bp < 0 || key[j] > kbp) { bp = j; kbp = key[j]; }
-                if (ba < 0 || akv[j] > kba) { ba = j; kba = akv[j]; }
-            }
-            double sp[RS_NOPT];
+            for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) sp[j] = pred[j];
+            for (int i = 0; i < RS_NOPT; ++i)
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                const int x = net6(c, 0), y = net6(c, 1);
-                const bool sw = key[y] > key[x] || (key[y] == key[x] && idx[y] < idx[x]);
-                const long long tk = sw ? key[y] : key[x];
-                key[y] = sw ? key[x] : key[y];
-                key[x] = tk;
-                const int ti = sw ? idx[y] : idx[x];
-                idx[y] = sw ? idx[x] : idx[y];
-                idx[x] = ti;
-                const double tp = sw ? sp[y] : sp[x];
-                sp[y] = sw ? sp[x] : sp[y];
-                sp[x] = tp;
-            }
+                for (int j = i + 1; j < RS_NOPT; ++j) {
+                    if (key[i] >= key[j]) bm[j] |= 1 << i;
+                    else bm[i] |= 1 << j;
+                }
             uint32_t code = 0x0FFFFFF0u;
-            int c = 0;
+            int rk = 0;
 #pragma unroll
-            for (int x = 0; x < RS_NOPT; ++x) {
-                if (x < a.k && key[x] != kNone && key[x] >= a.ktau) {
-                    code = (code & ~(0xFu << (4 + 4 * x))) | ((uint32_t)idx[x] << (4 + 4 * x));
-                    if (a.rec_pred) a.rec_pred[row * a.k + x] = sp[x];
-                    const int j = idx[x];
-                    cnt[5] += (scored >> j) & 1;
-                    cnt[6] += ((scored & apos) >> j) & 1;
-                    c = x + 1;
+            for (int j = 0; j < RS_NOPT; ++j) {
+                const int pos = __popc(bm[j] & above);
+                if (((above >> j) & 1) && pos < a.k) {
+                    code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
+                    if (a.rec_pred) a.rec_pred[row * a.k + pos] = pred[j];
+                    rk |= 1 << j;
                 }
             }
+            const int c = __popc(rk);
             code = (code & ~0xFu) | (uint32_t)c;
             a.rec_code[row] = code;
             if (a.rec_pred)
                 for (int x = c; x < a.k; ++x) a.rec_pred[row * a.k + x] = nan_d();
             if (a.pred_all)
 #pragma unroll
-                for (int j = 0; j < RS_NOPT; ++j) a.pred_all[row * RS_NOPT + j] = pred[j];
-            cnt[0] += 1;
-            cnt[1] += __popc(validm);
-            cnt[2] += __popc(scored);
-            cnt[4] += c;
-            if (bp >= 0) {
-                cnt[7] += 1;
-                if (bp == ba) cnt[8] += 1;
+                for (int j = 0; j < RS_NOPT; ++j)
+                    a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
+            const int known = info & 63, apos = (info >> 6) & 63;
+            const int scored = validm & known;
+            c_rows += 1;
+            c_pred += __popc(validm);
+            c_scored += __popc(scored);
+            c_sign += __popc(scored & ~(spos ^ apos));
+            c_rec += c;
+            c_reck += __popc(rk & scored);
+            c_rech += __popc(rk & scored & apos);
+            c_inv += __popc(candm & ~okm);
+            if (scored) {
+                int bp = 0;
+#pragma unroll
+                for (int j = 0; j < RS_NOPT; ++j)
+                    if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
+                int ba = -1;
+#pragma unroll
+                for (int x = 0; x < RS_NOPT; ++x) {
+                    const int j = (info >> (12 + 3 * x)) & 7;
+                    if (ba < 0 && ((scored >> j) & 1)) ba = j;
+                }
+                c_t1 += 1;
+                c_t1h += (bp == ba);
             }
         }
     }
     if (a.counters) {
+        const uint32_t vals[10] = {c_rows, c_pred, c_scored, c_sign, c_rec, c_reck, c_rech, c_t1, c_t1h, c_inv};
+        const int slot[10] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 13};
 #pragma unroll
-        for (int c = 0; c < 14; ++c) {
-            if (c >= 9 && c <= 12) continue;   // fit statuses are counted by the solvers
-            const uint32_t v = __reduce_add_sync(0xffffffffu, cnt[c]);
-            if (lane == 0 && v) atomicAdd(a.counters + c, (unsigned long long)v);
+        for (int c = 0; c < 10; ++c) {
+            const uint32_t v = __reduce_add_sync(0xffffffffu, vals[c]);
+            if (lane == 0 && v) atomicAdd(a.counters + slot[c], (unsigned long long)v);
         }
     }
 }
@@ -1069,8 +1075,7 @@ struct FitWs {
     double* ylab;        // [P][6][32]
     int* npair;          // [P][6]
     uint64_t* cand;      // [P][6]
-    long long* act_key;  // [P][64][6]
-    uint8_t* known;      // [P][64]
+    uint32_t* rowinfo;   // [P][64]
     int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
     uint8_t* fit_n;      // [S*6]
@@ -1097,8 +1102,7 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.ylab = (double*)take(P * RS_NOPT * RS_MAXPAIRS * sizeof(double));
     w.npair = (int*)take(P * RS_NOPT * sizeof(int));
     w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
-    w.act_key = (long long*)take(P * RS_MAXV * RS_NOPT * sizeof(long long));
-    w.known = (uint8_t*)take(P * RS_MAXV);
+    w.rowinfo = (uint32_t*)take(P * RS_MAXV * sizeof(uint32_t));
     w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
     w.fit_n = (uint8_t*)take(S6);
@@ -1153,7 +1157,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     mark(0);
     pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
-                                     w.npair, w.cand, w.act_key, w.known, a.dstatus);
+                                     w.npair, w.cand, w.rowinfo, a.dstatus);
     mark(1);
     const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
     plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
@@ -1180,13 +1184,13 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, 0, st>>>(sa);
     mark(5);
     if (rank) {
-        RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.split_offsets, a.train_masks, a.S,
-                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.act_key, w.known, a.k,
+        RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.train_masks, a.S,
+                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo, a.k,
                         0, a.flags, a.rec_code, a.rec_pred, a.pred_all, a.counters};
         ra.ktau = okey_host(a.log_tau);
-        int64_t blocks = (a.S + 7) / 8;
+        int64_t blocks = (a.S + kRankWarps - 1) / kRankWarps;
         if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
-        rank_pass_kernel<<<(unsigned)blocks, 256, 0, st>>>(ra);
+        rank_pass_kernel<<<(unsigned)blocks, kRankWarps * 32, 0, st>>>(ra);
     }
     mark(6);
     return cudaGetLastError();
