@@ -183,7 +183,9 @@ __global__ void __launch_bounds__(256)
 plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __restrict__ split_off,
                  const uint64_t* __restrict__ tm, int64_t S, const uint8_t* __restrict__ pb,
                  const uint8_t* __restrict__ pa, const int* __restrict__ npair, uint32_t* fit_pm,
-                 uint8_t* fit_n, unsigned* hist, int nmax, int* split_prog, int* dstatus) {
+                 uint8_t* fit_n, unsigned* hist, int nmax, int* split_prog,
+                 const int64_t* __restrict__ rec_offsets, int64_t rows_cap, int* row_split,
+                 uint8_t* row_slot, int* dstatus) {
     __shared__ unsigned h[kHist];
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
     __syncthreads();
@@ -192,8 +194,17 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         const int64_t s = f / RS_NOPT;
         const int j = (int)(f - s * RS_NOPT);
         const int p = rs_find_segment(split_off, P, s);
-        if (j == 0) split_prog[s] = p;
         const int V = (int)(row_off[p + 1] - row_off[p]);
+        if (j == 0) {
+            split_prog[s] = p;
+            if (row_split && V >= 1 && V <= RS_MAXV) {   // the split's test rows, in slot order
+                int64_t r = rec_offsets[s];
+                for (uint64_t x = ~tm[s] & rs_full_mask(V); x && r < rows_cap; x &= x - 1, ++r) {
+                    row_split[r] = (int)s;
+                    row_slot[r] = (uint8_t)(__ffsll((long long)x) - 1);
+                }
+            }
+        }
         uint32_t pm = 0;
         if (V >= 1 && V <= RS_MAXV) {
             const uint64_t T = tm[s] & rs_full_mask(V);
@@ -615,6 +626,9 @@ struct RankPassArgs {
     const double* predbuf;       // [6][R]
     int64_t R;
     const uint32_t* rowinfo;     // [P][64]
+    const int* row_split;        // [R] split of each test row
+    const uint8_t* row_slot;     // [R] version slot of each test row
+    int* dstatus;
     int k;
     long long ktau;
     int flags;
@@ -624,110 +638,109 @@ struct RankPassArgs {
     unsigned long long* counters;
 };
 
-constexpr int kRankWarps = 8;
+constexpr int kRankThreads = 256;
 
-__global__ void __launch_bounds__(kRankWarps * 32)
+__global__ void __launch_bounds__(kRankThreads)
 rank_pass_kernel(const RankPassArgs a) {
-    __shared__ uint8_t slots[kRankWarps][RS_MAXV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double* pbj[RS_NOPT];
-#pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) pbj[j] = a.predbuf + (int64_t)j * a.R;
+    const int lane = threadIdx.x & 31;
     uint32_t c_rows = 0, c_pred = 0, c_scored = 0, c_sign = 0, c_rec = 0, c_reck = 0, c_rech = 0;
     uint32_t c_t1 = 0, c_t1h = 0, c_inv = 0;
-    for (int64_t s = wg; s < a.S; s += nw) {
+    const int64_t total = a.rec_offsets[a.S];
+    const int64_t nrows = total < a.R ? total : a.R;
+    if (total > a.R && blockIdx.x == 0 && threadIdx.x == 0) rs_dev_flag(a.dstatus, RS_EDATA, -3);
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nrows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = a.row_split[row];
+        const int t = a.row_slot[row];
+        double pred[RS_NOPT];
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j) pred[j] = a.predbuf[(int64_t)j * a.R + row];
         const int p = a.split_prog[s];
-        const int64_t rv = a.row_off[p];
-        const int V = (int)(a.row_off[p + 1] - rv);
-        if (V < 1 || V > RS_MAXV) continue;
-        const uint64_t test = ~a.tm[s] & rs_full_mask(V);
-        const int nt = __popcll(test);
-        const int64_t base = a.rec_offsets[s];
-        if (base + nt > a.R) continue;
-        const int okm = __ballot_sync(0xffffffffu, lane < RS_NOPT &&
-                                      a.status[s * RS_NOPT + (lane < RS_NOPT ? lane : 0)] == RS_FIT_OK) & 63;
-        __syncwarp();
+        const uint8_t* stp = a.status + s * RS_NOPT;
+        int okm = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if (t < V && ((test >> t) & 1)) slots[warp][__popcll(test & ((1ull << t) - 1ull))] = (uint8_t)t;
+        for (int j = 0; j < RS_NOPT; ++j) okm |= (stp[j] == RS_FIT_OK) << j;
+        const int mt = a.masks[a.row_off[p] + t] & 63;
+        const uint32_t info = a.rowinfo[(int64_t)p * RS_MAXV + t];
+        const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
+        const int validm = candm & okm;
+        long long key[RS_NOPT];
+        int above = 0, spos = 0;
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j) {
+            key[j] = okey(pred[j]);
+            above |= (key[j] >= a.ktau) << j;
+            spos |= (key[j] > 0) << j;
         }
-        __syncwarp();
-        for (int r = lane; r < nt; r += 32) {
-            const int t = slots[warp][r];
-            const int64_t row = base + r;
-            const int mt = a.masks[rv + t] & 63;
-            const uint32_t info = a.rowinfo[(int64_t)p * RS_MAXV + t];
-            double pred[RS_NOPT];
+        above &= validm;
+        int bm[RS_NOPT];                       // bm[j]: candidates ranking before j
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) pred[j] = pbj[j][row];
-            const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
-            const int validm = candm & okm;
-            long long key[RS_NOPT];
-            int above = 0, spos = 0;
+        for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) {
-                key[j] = okey(pred[j]);
-                above |= (key[j] >= a.ktau) << j;
-                spos |= (key[j] > 0) << j;
+        for (int i = 0; i < RS_NOPT; ++i)
+#pragma unroll
+            for (int j = i + 1; j < RS_NOPT; ++j) {
+                if (key[i] >= key[j]) bm[j] |= 1 << i;
+                else bm[i] |= 1 << j;
             }
-            above &= validm;
-            int bm[RS_NOPT];                       // bm[j]: candidates ranking before j
+        uint32_t code = 0x0FFFFFF0u;
+        int rk = 0;
+        double rp[RS_NOPT];
 #pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
+        for (int x = 0; x < RS_NOPT; ++x) rp[x] = nan_d();
 #pragma unroll
-            for (int i = 0; i < RS_NOPT; ++i)
+        for (int j = 0; j < RS_NOPT; ++j) {
+            const int pos = __popc(bm[j] & above);
+            if (((above >> j) & 1) && pos < a.k) {
+                code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
 #pragma unroll
-                for (int j = i + 1; j < RS_NOPT; ++j) {
-                    if (key[i] >= key[j]) bm[j] |= 1 << i;
-                    else bm[i] |= 1 << j;
-                }
-            uint32_t code = 0x0FFFFFF0u;
-            int rk = 0;
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j) {
-                const int pos = __popc(bm[j] & above);
-                if (((above >> j) & 1) && pos < a.k) {
-                    code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
-                    if (a.rec_pred) a.rec_pred[row * a.k + pos] = pred[j];
-                    rk |= 1 << j;
-                }
+                for (int x = 0; x < RS_NOPT; ++x)
+                    if (x == pos) rp[x] = pred[j];
+                rk |= 1 << j;
             }
-            const int c = __popc(rk);
-            code = (code & ~0xFu) | (uint32_t)c;
-            a.rec_code[row] = code;
-            if (a.rec_pred)
-                for (int x = c; x < a.k; ++x) a.rec_pred[row * a.k + x] = nan_d();
-            if (a.pred_all)
+        }
+        const int c = __popc(rk);
+        code = (code & ~0xFu) | (uint32_t)c;
+        a.rec_code[row] = code;
+        if (a.rec_pred) {
+            if (a.k == 3) {
+                double* o = a.rec_pred + row * 3;
+                o[0] = rp[0];
+                o[1] = rp[1];
+                o[2] = rp[2];
+            } else {
 #pragma unroll
-                for (int j = 0; j < RS_NOPT; ++j)
-                    a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
-            const int known = info & 63, apos = (info >> 6) & 63;
-            const int scored = validm & known;
-            c_rows += 1;
-            c_pred += __popc(validm);
-            c_scored += __popc(scored);
-            c_sign += __popc(scored & ~(spos ^ apos));
-            c_rec += c;
-            c_reck += __popc(rk & scored);
-            c_rech += __popc(rk & scored & apos);
-            c_inv += __popc(candm & ~okm);
-            if (scored) {
-                int bp = 0;
-#pragma unroll
-                for (int j = 0; j < RS_NOPT; ++j)
-                    if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
-                int ba = -1;
-#pragma unroll
-                for (int x = 0; x < RS_NOPT; ++x) {
-                    const int j = (info >> (12 + 3 * x)) & 7;
-                    if (ba < 0 && ((scored >> j) & 1)) ba = j;
-                }
-                c_t1 += 1;
-                c_t1h += (bp == ba);
+                for (int x = 0; x < RS_NOPT; ++x)
+                    if (x < a.k) a.rec_pred[row * a.k + x] = rp[x];
             }
+        }
+        if (a.pred_all)
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j)
+                a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
+        const int known = info & 63, apos = (info >> 6) & 63;
+        const int scored = validm & known;
+        c_rows += 1;
+        c_pred += __popc(validm);
+        c_scored += __popc(scored);
+        c_sign += __popc(scored & ~(spos ^ apos));
+        c_rec += c;
+        c_reck += __popc(rk & scored);
+        c_rech += __popc(rk & scored & apos);
+        c_inv += __popc(candm & ~okm);
+        if (scored) {
+            int bp = 0;
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j)
+                if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
+            int ba = -1;
+#pragma unroll
+            for (int x = 0; x < RS_NOPT; ++x) {
+                const int j = (info >> (12 + 3 * x)) & 7;
+                if (ba < 0 && ((scored >> j) & 1)) ba = j;
+            }
+            c_t1 += 1;
+            c_t1h += (bp == ba);
         }
     }
     if (a.counters) {
@@ -1076,6 +1089,8 @@ struct FitWs {
     int* npair;          // [P][6]
     uint64_t* cand;      // [P][6]
     uint32_t* rowinfo;   // [P][64]
+    int* row_split;      // [Rcap]
+    uint8_t* row_slot;   // [Rcap]
     int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
     uint8_t* fit_n;      // [S*6]
@@ -1103,6 +1118,8 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.npair = (int*)take(P * RS_NOPT * sizeof(int));
     w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
     w.rowinfo = (uint32_t*)take(P * RS_MAXV * sizeof(uint32_t));
+    w.row_split = (int*)take((size_t)Rcap * sizeof(int));
+    w.row_slot = (uint8_t*)take((size_t)Rcap);
     w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
     w.fit_n = (uint8_t*)take(S6);
@@ -1162,7 +1179,10 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
     plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
                                                 a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
-                                                nmax, w.split_prog, a.dstatus);
+                                                nmax, w.split_prog, a.rec_offsets,
+                                                a.rec_code ? a.rows_cap : 0,
+                                                a.rec_code ? w.row_split : nullptr, w.row_slot,
+                                                a.dstatus);
     mark(2);
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
@@ -1185,12 +1205,14 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     mark(5);
     if (rank) {
         RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.train_masks, a.S,
-                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo, a.k,
-                        0, a.flags, a.rec_code, a.rec_pred, a.pred_all, a.counters};
+                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo, w.row_split,
+                        w.row_slot, a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all,
+                        a.counters};
         ra.ktau = okey_host(a.log_tau);
-        int64_t blocks = (a.S + kRankWarps - 1) / kRankWarps;
-        if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
-        rank_pass_kernel<<<(unsigned)blocks, kRankWarps * 32, 0, st>>>(ra);
+        int64_t blocks = (a.rows_cap + kRankThreads - 1) / kRankThreads;
+        if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
+        if (blocks < 1) blocks = 1;
+        rank_pass_kernel<<<(unsigned)blocks, kRankThreads, 0, st>>>(ra);
     }
     mark(6);
     return cudaGetLastError();
