@@ -228,19 +228,36 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
 }
 
 // Bucket starts from the histogram: positions of fits with n >= 1 ordered by n, and the
-// offsets of their compact coefficient records (n + 1 doubles each).
+// offsets of their compact coefficient records (n + 1 doubles each).  Called by every
+// thread of the block; warp 0 scans the 32 counts with shuffles.  Ends with a barrier.
 __device__ __forceinline__ void bucket_tables(const unsigned* hist, long long* start, long long* cstart) {
-    long long acc = 0, cacc = 0;
-    start[0] = 0;
-    cstart[0] = 0;
-    for (int n = 1; n <= RS_MAXPAIRS; ++n) {
-        start[n] = acc;
-        cstart[n] = cacc;
-        acc += hist[n];
-        cacc += (long long)hist[n] * (n + 1);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int n = lane + 1;
+        const long long v = hist[n];
+        const long long w = v * (n + 1);
+        long long iv = v, iw = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long yv = __shfl_up_sync(0xffffffffu, iv, o);
+            const long long yw = __shfl_up_sync(0xffffffffu, iw, o);
+            if (lane >= o) {
+                iv += yv;
+                iw += yw;
+            }
+        }
+        start[n] = iv - v;
+        cstart[n] = iw - w;
+        if (lane == 31) {
+            start[RS_MAXPAIRS + 1] = iv;
+            cstart[RS_MAXPAIRS + 1] = iw;
+        }
+        if (lane == 0) {
+            start[0] = 0;
+            cstart[0] = 0;
+        }
     }
-    start[RS_MAXPAIRS + 1] = acc;
-    cstart[RS_MAXPAIRS + 1] = cacc;
+    __syncthreads();
 }
 
 // ====================================================================== bucket
@@ -252,9 +269,8 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
                    unsigned long long* counters) {
     __shared__ long long start[kHist], cstart[kHist];
     __shared__ unsigned lcount[kHist], lbase[kHist];
-    if (threadIdx.x == 0) bucket_tables(hist, start, cstart);
     if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
-    __syncthreads();
+    bucket_tables(hist, start, cstart);
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = f < S6 ? fit_n[f] : 0;
     unsigned local = 0;
@@ -457,8 +473,7 @@ template <int NLO, int NHI, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 solve_small_kernel(const SolveArgs a) {
     __shared__ long long start[kHist], cstart[kHist];
-    if (threadIdx.x == 0) bucket_tables(a.hist, start, cstart);
-    __syncthreads();
+    bucket_tables(a.hist, start, cstart);
     const long long lo = start[NLO], hi = start[NHI + 1];
     for (long long base = lo + (long long)blockIdx.x * blockDim.x; base < hi;
          base += (long long)gridDim.x * blockDim.x) {
@@ -500,13 +515,17 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
         v = pair_b[q];
         y = ylab[q];
     }
+    // stage row a of M = K_TT + lambda I (lower triangle) in Lsh: independent loads
+    for (int b = 0; b < n; ++b) {
+        const int vb = __shfl_sync(0xffffffffu, v, b);
+        if (act && b <= lane) Lsh[lane * 33 + b] = K[v * ld + vb] + (b == lane ? lambda : 0.0);
+    }
+    __syncwarp();
     double rinv = 0.0;
-    for (int jj = 0; jj < n; ++jj) {
-        const int vj = __shfl_sync(0xffffffffu, v, jj);
+    for (int jj = 0; jj < n; ++jj) {           // left-looking, in place
         double s = 0.0;
         if (act && lane >= jj) {
-            s = K[v * ld + vj];
-            if (lane == jj) s += lambda;
+            s = Lsh[lane * 33 + jj];
             for (int m = 0; m < jj; ++m) s = fma(-Lsh[lane * 33 + m], Lsh[jj * 33 + m], s);
         }
         const double d = __shfl_sync(0xffffffffu, s, jj);
@@ -583,8 +602,7 @@ __global__ void __launch_bounds__(kLargeWarps * 32)
 solve_large_kernel(const SolveArgs a) {
     __shared__ long long start[kHist], cstart[kHist];
     __shared__ double Lsh[kLargeWarps][32 * 33];
-    if (threadIdx.x == 0) bucket_tables(a.hist, start, cstart);
-    __syncthreads();
+    bucket_tables(a.hist, start, cstart);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long first = start[kNReg + 1], end = start[RS_MAXPAIRS + 1];
     for (long long pos = first + (long long)blockIdx.x * kLargeWarps + warp; pos < end;
