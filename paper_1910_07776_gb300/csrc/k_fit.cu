@@ -56,14 +56,42 @@ __device__ __forceinline__ long long okey(double x) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
+// float <-> double for values inside the float normal range, by re-packing the IEEE-754
+// fields with integer operations (the mantissa is truncated).  Used only to seed Newton
+// iterations, so no FP64 instruction is spent on the conversion.
+__device__ __forceinline__ float f32_of(double d) {
+    const long long b = __double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    const unsigned m = (unsigned)((b >> 29) & 0x7fffff);
+    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | m);
+}
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned u = __float_as_uint(f);
+    const long long e = (long long)((u >> 23) & 0xff) - 127 + 1023;
+    return __longlong_as_double(((long long)(u & 0x80000000u) << 32) | (e << 52) |
+                                ((long long)(u & 0x7fffff) << 29));
+}
+
 // 1/sqrt(d) for a positive finite d: FP32 seed, then two Newton steps of r <- r (3 - d r^2) / 2
-// (Newton's method on f(r) = r^-2 - d).  Outside the float range: plain division.
+// (Newton's method on f(r) = r^-2 - d).  Outside [1e-30, 1e30]: plain division.
 __device__ __forceinline__ double rsqrt_newton(double d) {
     if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);
     const double hd = 0.5 * d;
-    double r = (double)rsqrtf((float)d);
+    double r = f64_of(rsqrtf(f32_of(d)));
     r = r * fma(-hd, r * r, 1.5);
     r = r * fma(-hd, r * r, 1.5);
+    return r;
+}
+
+// 1/d for a positive finite d: FP32 seed, then two Newton steps r <- r + r (1 - d r)
+// (Newton's method on f(r) = 1/r - d).  Outside [1e-30, 1e30]: plain division.
+__device__ __forceinline__ double rcp_newton(double d) {
+    if (d < 1e-30 || d > 1e30) return 1.0 / d;
+    double r = f64_of(__frcp_rn(f32_of(d)));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
     return r;
 }
 
@@ -72,18 +100,6 @@ long long okey_host(double x) {
     memcpy(&b, &x, sizeof(b));
     if (b == (long long)0x8000000000000000ull) b = 0;
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-
-// 1/d for a positive finite d: FP32 seed, then two Newton steps r <- r + r (1 - d r)
-// (Newton's method on f(r) = 1/r - d).  Outside the float range: plain division.
-__device__ __forceinline__ double rcp_newton(double d) {
-    if (d < 1e-30 || d > 1e30) return 1.0 / d;
-    double r = (double)__frcp_rn((float)d);
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    return r;
 }
 
 // The a-th set bit (0-based) of x; x must have more than a set bits.
@@ -101,7 +117,8 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
 __global__ void __launch_bounds__(64)
 pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restrict__ masks,
              const double* __restrict__ log_time, uint8_t* pb, uint8_t* pa, double* ylab,
-             int* npair, uint64_t* cand, uint32_t* rowinfo, int* dstatus) {
+             int* npair, uint64_t* cand, uint32_t* rowinfo, const double* __restrict__ K,
+             double lambda, double* dlam, int* dstatus) {
     __shared__ int8_t slot_of[RS_MAXV];
     __shared__ uint8_t msk[RS_MAXV];
     __shared__ double lt[RS_MAXV];
@@ -175,6 +192,8 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
             ord |= (uint32_t)best << (3 * x);
         }
         rowinfo[(int64_t)p * RS_MAXV + t] = (uint32_t)kn | ((uint32_t)apos << 6) | (ord << 12);
+        if (t < V) dlam[(int64_t)p * RS_MAXV + t] =
+            K[(int64_t)p * RS_GRAM_LD * RS_GRAM_LD + t * RS_GRAM_LD + t] + lambda;
     }
 }
 
@@ -185,7 +204,8 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                  const uint8_t* __restrict__ pa, const int* __restrict__ npair, uint32_t* fit_pm,
                  uint8_t* fit_n, unsigned* hist, int nmax, int* split_prog,
                  const int64_t* __restrict__ rec_offsets, int64_t rows_cap, int* row_split,
-                 uint8_t* row_slot, int* dstatus) {
+                 unsigned long long* row_info, const uint8_t* __restrict__ masks,
+                 const uint32_t* __restrict__ rowinfo, int* dstatus) {
     __shared__ unsigned h[kHist];
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
     __syncthreads();
@@ -199,9 +219,12 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
             split_prog[s] = p;
             if (row_split && V >= 1 && V <= RS_MAXV) {   // the split's test rows, in slot order
                 int64_t r = rec_offsets[s];
+                const int64_t rv = row_off[p];
                 for (uint64_t x = ~tm[s] & rs_full_mask(V); x && r < rows_cap; x &= x - 1, ++r) {
+                    const int t = __ffsll((long long)x) - 1;
                     row_split[r] = (int)s;
-                    row_slot[r] = (uint8_t)(__ffsll((long long)x) - 1);
+                    row_info[r] = (unsigned long long)rowinfo[(int64_t)p * RS_MAXV + t] |
+                                  ((unsigned long long)(masks[rv + t] & 63) << 30);
                 }
             }
         }
@@ -318,8 +341,9 @@ struct PredTarget {
 //   alpha = L^-T D^-1 (t_y - b t_1)   (one backward solve).
 template <int N>
 __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
-                                           const double* __restrict__ yl, uint32_t pm, double lambda,
-                                           double* out, const PredTarget* pt) {
+                                           const double* __restrict__ yl, uint32_t pm,
+                                           const double* __restrict__ dl, double* out,
+                                           const PredTarget* pt) {
     int vb[N];
     double ty[N], t1[N], L[tri(N)], dinv[N];
     uint32_t x = pm;
@@ -341,7 +365,7 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
             c[k] = s;
             L[tri(i) + k] = s * dinv[k];
         }
-        double d = __ldg(Kp + vb[i] * RS_GRAM_LD + vb[i]) + lambda;
+        double d = __ldg(dl + vb[i]);      // K[v][v] + lambda
 #pragma unroll
         for (int m = 0; m < i; ++m) d = fma(-c[m], L[tri(i) + m], d);
         if (!pos_finite(d)) return RS_FIT_NOTPD;
@@ -394,12 +418,13 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
 
 template <int N, int NHI>
 __device__ __forceinline__ int solve_dispatch(int n, const double* Kp, const uint8_t* pb, const double* yl,
-                                              uint32_t pm, double lambda, double* out, const PredTarget* pt) {
+                                              uint32_t pm, const double* dl, double* out,
+                                              const PredTarget* pt) {
     if constexpr (N >= NHI) {
-        return solve_fixed<N>(Kp, pb, yl, pm, lambda, out, pt);
+        return solve_fixed<N>(Kp, pb, yl, pm, dl, out, pt);
     } else {
-        if (n == N) return solve_fixed<N>(Kp, pb, yl, pm, lambda, out, pt);
-        return solve_dispatch<N + 1, NHI>(n, Kp, pb, yl, pm, lambda, out, pt);
+        if (n == N) return solve_fixed<N>(Kp, pb, yl, pm, dl, out, pt);
+        return solve_dispatch<N + 1, NHI>(n, Kp, pb, yl, pm, dl, out, pt);
     }
 }
 
@@ -419,6 +444,7 @@ struct SolveArgs {
     int coef_user;
     uint8_t* status;
     double lambda;
+    const double* dlam;   // [P][64] K[t][t] + lambda
     unsigned long long* counters;
     // predictions (batched predict/rank only; predbuf == nullptr for fits alone)
     const int64_t* row_off;
@@ -492,8 +518,8 @@ solve_small_kernel(const SolveArgs a) {
             double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
             PredTarget ptv;
             const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
-            st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f], a.lambda,
-                                          out, pt);
+            st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f],
+                                          a.dlam + (int64_t)p * RS_MAXV, out, pt);
             finish_record(a, f, n, st, out);
         }
         count_status(a, st, active);
@@ -645,7 +671,7 @@ struct RankPassArgs {
     int64_t R;
     const uint32_t* rowinfo;     // [P][64]
     const int* row_split;        // [R] split of each test row
-    const uint8_t* row_slot;     // [R] version slot of each test row
+    const unsigned long long* row_info;  // [R] scoring summary | version mask << 30
     int* dstatus;
     int k;
     long long ktau;
@@ -658,7 +684,7 @@ struct RankPassArgs {
 
 constexpr int kRankThreads = 256;
 
-__global__ void __launch_bounds__(kRankThreads)
+__global__ void __launch_bounds__(kRankThreads, 4)
 rank_pass_kernel(const RankPassArgs a) {
     const int lane = threadIdx.x & 31;
     uint32_t c_rows = 0, c_pred = 0, c_scored = 0, c_sign = 0, c_rec = 0, c_reck = 0, c_rech = 0;
@@ -669,18 +695,18 @@ rank_pass_kernel(const RankPassArgs a) {
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nrows;
          row += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = a.row_split[row];
-        const int t = a.row_slot[row];
+        const unsigned long long info64 = a.row_info[row];
+        const uint32_t info = (uint32_t)info64;
+        const int mt = (int)(info64 >> 30) & 63;
+        const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
         double pred[RS_NOPT];
 #pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) pred[j] = a.predbuf[(int64_t)j * a.R + row];
-        const int p = a.split_prog[s];
+        for (int j = 0; j < RS_NOPT; ++j)
+            pred[j] = ((candm >> j) & 1) ? a.predbuf[(int64_t)j * a.R + row] : 0.0;
         const uint8_t* stp = a.status + s * RS_NOPT;
         int okm = 0;
 #pragma unroll
         for (int j = 0; j < RS_NOPT; ++j) okm |= (stp[j] == RS_FIT_OK) << j;
-        const int mt = a.masks[a.row_off[p] + t] & 63;
-        const uint32_t info = a.rowinfo[(int64_t)p * RS_MAXV + t];
-        const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
         const int validm = candm & okm;
         long long key[RS_NOPT];
         int above = 0, spos = 0;
@@ -1107,8 +1133,9 @@ struct FitWs {
     int* npair;          // [P][6]
     uint64_t* cand;      // [P][6]
     uint32_t* rowinfo;   // [P][64]
+    double* dlam;        // [P][64] K[t][t] + lambda
     int* row_split;      // [Rcap]
-    uint8_t* row_slot;   // [Rcap]
+    unsigned long long* row_info;   // [Rcap] scoring summary | mask << 30
     int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
     uint8_t* fit_n;      // [S*6]
@@ -1136,8 +1163,9 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.npair = (int*)take(P * RS_NOPT * sizeof(int));
     w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
     w.rowinfo = (uint32_t*)take(P * RS_MAXV * sizeof(uint32_t));
+    w.dlam = (double*)take(P * RS_MAXV * sizeof(double));
     w.row_split = (int*)take((size_t)Rcap * sizeof(int));
-    w.row_slot = (uint8_t*)take((size_t)Rcap);
+    w.row_info = (unsigned long long*)take((size_t)Rcap * sizeof(unsigned long long));
     w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
     w.fit_n = (uint8_t*)take(S6);
@@ -1192,15 +1220,15 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     mark(0);
     pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
-                                     w.npair, w.cand, w.rowinfo, a.dstatus);
+                                     w.npair, w.cand, w.rowinfo, a.K, a.lambda, w.dlam, a.dstatus);
     mark(1);
     const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
     plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
                                                 a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
                                                 nmax, w.split_prog, a.rec_offsets,
                                                 a.rec_code ? a.rows_cap : 0,
-                                                a.rec_code ? w.row_split : nullptr, w.row_slot,
-                                                a.dstatus);
+                                                a.rec_code ? w.row_split : nullptr, w.row_info,
+                                                a.masks, w.rowinfo, a.dstatus);
     mark(2);
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
@@ -1209,7 +1237,8 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     mark(3);
     const bool rank = a.rec_code != nullptr;
     SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
-                 w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, a.counters,
+                 w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
+                 a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
                  a.rows_cap, a.flags, a.dstatus};
     int dev = 0, sms = 0;
@@ -1224,11 +1253,11 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (rank) {
         RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.train_masks, a.S,
                         a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo, w.row_split,
-                        w.row_slot, a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all,
+                        w.row_info, a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all,
                         a.counters};
         ra.ktau = okey_host(a.log_tau);
         int64_t blocks = (a.rows_cap + kRankThreads - 1) / kRankThreads;
-        if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
+        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
         if (blocks < 1) blocks = 1;
         rank_pass_kernel<<<(unsigned)blocks, kRankThreads, 0, st>>>(ra);
     }
