@@ -211,6 +211,34 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
                      uint32_t* rec_code, double* rec_pred, double* pred_all,
                      uint64_t* counters);
 
+/* ---- the whole step, allocating nothing -------------------------------------------------
+ * The paper has no counterpart: this is a deployment variant of rs_cv_step for callers that
+ * cannot allocate device memory -- for instance a host that must finish all of its
+ * cudaMalloc calls before it starts serving, or a caller that only owns the input and output
+ * buffers it hands in and has no allocator to obtain a workspace from.  It runs the same
+ * kernels as rs_cv_step (FP64 Gram, batched form) with its scratch (status words, the
+ * row-planning scan, Z, the Gram blocks and the fit workspace) in one array of
+ * RS_STATIC_SCRATCH_BYTES bytes that this library defines in device memory; every GPU that
+ * loads the library keeps that array until the process exits.  It needs no rs_ctx and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on a device (the current device) looks up the array's device address
+ *     and caches it; make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; the call clears what
+ *     must start at zero itself.  Calls whose work overlaps on the GPU (two streams, two
+ *     threads) race on the array: serialise them.
+ *   - A batch whose scratch would exceed RS_STATIC_SCRATCH_BYTES is rejected with
+ *     RS_ENOMEM before anything is launched; errbuf (host, nullable) gets the reason.
+ * Arguments as in rs_cv_step (X raw counters; the Gram is FP64; flags: RS_RANK_ALL only),
+ * with the stream given directly.  rec_offsets (int64 [S+1]) is an output here.
+ * device_status (device int, nullable) receives the device status word of the call
+ * (0, or RS_EDATA / RS_ETIMEOUT as rs_check_device_status would report).              */
+#define RS_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+rs_status rs_cv_step_static(void* cuda_stream, const rs_batch* batch, const rs_splits* splits,
+                            double lambda, int k, double tau, int flags, int64_t* rec_offsets,
+                            uint32_t* rec_code, double* rec_pred, double* pred_all,
+                            uint64_t* counters, int* device_status, char* errbuf,
+                            size_t errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

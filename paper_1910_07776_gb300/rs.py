@@ -32,7 +32,7 @@ EXPORTS = [
     "rs_create", "rs_destroy", "rs_set_stream", "rs_last_error", "rs_check_device_status",
     "rs_standardize", "rs_gram", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
     "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak", "rs_fit_workspace_bytes",
-    "rs_profile_enable", "rs_profile_read",
+    "rs_profile_enable", "rs_profile_read", "rs_cv_step_static",
 ]
 
 
@@ -90,6 +90,7 @@ def load(path: str = SO):
     L.rs_cv_workspace_bytes.restype = C.c_size_t
     L.rs_cv_step.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
+    L.rs_cv_step_static.argtypes = [P, P, P, d, i, d, i, P, P, P, P, P, P, C.c_char_p, C.c_size_t]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     for name in EXPORTS:
