@@ -211,6 +211,14 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
                      uint32_t* rec_code, double* rec_pred, double* pred_all,
                      uint64_t* counters);
 
+/* ---- tensor-core BF16 GEMM (the surrogate's and the tensor-core Gram's building block) ----
+ * D[M][N] = A[M][K] * B[N][K]^T with A, B BF16 row-major (K contiguous, leading dimensions
+ * lda, ldb in elements, multiples of 8, 16-byte aligned bases) and D FP32 row-major (ldd).
+ * Runs on tcgen05 tensor cores (FP32 accumulation in tensor memory, TMA-fed shared memory
+ * stages).  Not a step of the paper's method; exposed for tests and reuse.            */
+rs_status rs_gemm_bf16(rs_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       float* D, int64_t ldd, int M, int N, int K);
+
 /* ---- the whole step, allocating nothing -------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of rs_cv_step for callers that
  * cannot allocate device memory -- for instance a host that must finish all of its

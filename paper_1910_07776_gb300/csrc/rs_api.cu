@@ -311,6 +311,20 @@ rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const r
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_predict_rank");
 }
 
+rs_status rs_gemm_bf16(rs_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, float* D,
+                       int64_t ldd, int M, int N, int K) {
+    if (!c) return RS_EINVAL;
+    if (!A || !B || !D) return fail(c, RS_EINVAL, "A, B and D are required");
+    if (M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldd < N)
+        return fail(c, RS_EINVAL, "sizes: M, N, K >= 1, lda, ldb >= K, ldd >= N");
+    if ((lda * 2) % 16 || (ldb * 2) % 16 || (uintptr_t)A % 16 || (uintptr_t)B % 16)
+        return fail(c, RS_EINVAL, "A and B rows must start on 16-byte boundaries (lda, ldb multiples of 8)");
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_gemm_bf16(A, lda, B, ldb, D, ldd, M, N, K, c->dstatus, c->stream);
+    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_gemm_bf16");
+}
+
 size_t rs_cv_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
     if (!b || !sp || b->n_programs < 1 || b->x_elems < 0) return 0;
     size_t z = align256((size_t)b->x_elems * sizeof(double));

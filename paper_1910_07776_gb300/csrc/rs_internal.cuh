@@ -86,3 +86,5 @@ struct rs_fit_args {
 #define RS_NSTAGE_EVENTS 7   // before pairs, after pairs / plan / bucket / solve / solve-large / rank
 size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t rows_cap);
 cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st);
+cudaError_t rs_launch_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* D, int64_t ldd,
+                                int M, int N, int K, int* err, cudaStream_t st);

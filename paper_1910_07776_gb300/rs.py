@@ -32,7 +32,7 @@ EXPORTS = [
     "rs_create", "rs_destroy", "rs_set_stream", "rs_last_error", "rs_check_device_status",
     "rs_standardize", "rs_gram", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
     "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak", "rs_fit_workspace_bytes",
-    "rs_profile_enable", "rs_profile_read", "rs_cv_step_static",
+    "rs_profile_enable", "rs_profile_read", "rs_cv_step_static", "rs_gemm_bf16",
 ]
 
 
@@ -91,6 +91,7 @@ def load(path: str = SO):
     L.rs_cv_step.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
     L.rs_cv_step_static.argtypes = [P, P, P, d, i, d, i, P, P, P, P, P, P, C.c_char_p, C.c_size_t]
+    L.rs_gemm_bf16.argtypes = [P, P, i64, P, i64, P, i64, i, i, i]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     for name in EXPORTS:
@@ -240,6 +241,16 @@ class Context:
         n = C.c_int(0)
         self._check(self.L.rs_profile_read(self.h, ms, 8, C.byref(n)))
         return {self.STAGES[i]: float(ms[i]) for i in range(n.value)}
+
+    def gemm_bf16(self, A: torch.Tensor, B: torch.Tensor, D: Optional[torch.Tensor] = None):
+        """D = A @ B^T on the tensor cores (A [M,K], B [N,K] bfloat16 row-major; D float32)."""
+        M, K = A.shape
+        N = B.shape[0]
+        if D is None:
+            D = torch.empty(M, N, dtype=torch.float32, device=A.device)
+        self._check(self.L.rs_gemm_bf16(self.h, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(D),
+                                        D.stride(0), M, N, K))
+        return D
 
     def check_device_status(self):
         self._check(self.L.rs_check_device_status(self.h))
