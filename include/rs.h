@@ -219,6 +219,47 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
 rs_status rs_gemm_bf16(rs_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb,
                        float* D, int64_t ldd, int M, int N, int K);
 
+/* ---- A7: the learned surrogate (not in the paper) -------------------------------------------
+ * An MLP 256 -> 512 -> 512 -> 6 with GELU (u * Phi(u)) maps a standardized feature vector to
+ * the six predicted log speedups -- a learned stand-in for the tier-2 predictor (Sec. 2),
+ * trained on labels that the plain ridge predictor produces.  BF16 weights and activations
+ * on the tcgen05 tensor cores with FP32 accumulation, FP32 master weights, AdamW (beta1
+ * 0.9, beta2 0.999, eps 1e-8), loss = mean squared error over the six outputs.
+ * The state lives in one caller-owned FP32 "blob" of rs_surrogate_blob_bytes() bytes
+ * (256-byte aligned).  rs_surrogate_offset(w) gives float offsets of: 0 W1 [512][256],
+ * 1 b1 [512], 2 W2 [512][512], 3 b2 [512], 4 W3 [16][512] (rows 6..15 must be zero),
+ * 5 b3 [16], 6 Adam m, 7 Adam v, 8 last gradients (each laid out like 0..5), 9 feature
+ * mean [256] then std [256] of the training rows, 10 counters.  The caller writes the
+ * initial weights and zeros m and v.
+ * rs_surrogate_train: rows (double, [n][256] standardized features; labels [n][6] double,
+ * NaN = no label, trained as 0) are taken in order in minibatches of cfg->batch_rows,
+ * wrapping around; cfg->steps optimizer steps (0: only the feature statistics and the BF16
+ * weight copies are prepared).  use_graph = 1 captures one step in a CUDA graph and replays
+ * it.  loss_curve (nullable, float [steps]) gets each minibatch's loss.
+ * rs_surrogate_infer: pred [n][6] (float); ood_score [n] (nullable) = mean over features of
+ * ((x - mean) / std)^2 against the training statistics; used_fallback [n] (nullable) = 1
+ * where ood_score > ood_threshold (those rows should be predicted by the plain method).
+ * workspace: rs_surrogate_workspace_bytes(batch_rows) bytes, 256-byte aligned; inference
+ * processes chunk_rows rows at a time (chunk_rows <= the batch_rows the workspace was
+ * sized for).  RS_ETIMEOUT in the device status if a tensor-core pipeline wait gave up. */
+typedef struct {
+    int32_t batch_rows;
+    int32_t use_graph;
+    int64_t steps;
+    float lr;
+    float weight_decay;
+} rs_mlp_cfg;
+size_t rs_surrogate_blob_bytes(void);
+int64_t rs_surrogate_offset(int which);
+size_t rs_surrogate_workspace_bytes(int batch_rows);
+rs_status rs_surrogate_train(rs_ctx* ctx, float* blob, const double* X, const double* Y, int64_t n,
+                             const rs_mlp_cfg* cfg, float* loss_curve, void* workspace,
+                             size_t workspace_bytes);
+rs_status rs_surrogate_infer(rs_ctx* ctx, const float* blob, const double* X, int64_t n,
+                             float ood_threshold, float* pred, float* ood_score,
+                             uint8_t* used_fallback, void* workspace, size_t workspace_bytes,
+                             int chunk_rows);
+
 /* ---- the whole step, allocating nothing -------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of rs_cv_step for callers that
  * cannot allocate device memory -- for instance a host that must finish all of its

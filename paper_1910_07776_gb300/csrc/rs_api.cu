@@ -325,6 +325,52 @@ rs_status rs_gemm_bf16(rs_ctx* c, const void* A, int64_t lda, const void* B, int
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_gemm_bf16");
 }
 
+size_t rs_surrogate_blob_bytes(void) { return rs_surrogate_blob_floats() * sizeof(float); }
+
+int64_t rs_surrogate_offset(int which) { return rs_surrogate_blob_offset(which); }
+
+size_t rs_surrogate_workspace_bytes(int batch_rows) {
+    if (batch_rows < 1) return 0;
+    const size_t t = rs_surrogate_train_ws_bytes(batch_rows);
+    const size_t i = rs_surrogate_infer_ws_bytes(batch_rows);
+    return t > i ? t : i;
+}
+
+rs_status rs_surrogate_train(rs_ctx* c, float* blob, const double* X, const double* Y, int64_t n,
+                             const rs_mlp_cfg* cfg, float* loss_curve, void* ws, size_t ws_bytes) {
+    if (!c) return RS_EINVAL;
+    if (!blob || !X || !Y || !cfg || !ws) return fail(c, RS_EINVAL, "blob, X, Y, cfg and workspace are required");
+    if (n < 1 || cfg->batch_rows < 16 || cfg->batch_rows % 8 || cfg->batch_rows > n || cfg->steps < 0)
+        return fail(c, RS_EINVAL, "need n >= batch_rows >= 16, batch_rows a multiple of 8, steps >= 0");
+    if (!(cfg->lr >= 0.f) || !(cfg->weight_decay >= 0.f)) return fail(c, RS_EINVAL, "lr and weight_decay must be >= 0");
+    if ((uintptr_t)blob % 256 || (uintptr_t)ws % 256) return fail(c, RS_EINVAL, "blob and workspace must be 256-byte aligned");
+    if (ws_bytes < rs_surrogate_workspace_bytes(cfg->batch_rows))
+        return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes,
+                    rs_surrogate_workspace_bytes(cfg->batch_rows));
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_surrogate_train(blob, X, Y, n, cfg->batch_rows, cfg->steps, cfg->lr,
+                                              cfg->weight_decay, loss_curve, ws, cfg->use_graph, c->dstatus,
+                                              c->stream);
+    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_surrogate_train");
+}
+
+rs_status rs_surrogate_infer(rs_ctx* c, const float* blob, const double* X, int64_t n, float ood_threshold,
+                             float* pred, float* ood_score, uint8_t* used_fallback, void* ws, size_t ws_bytes,
+                             int chunk_rows) {
+    if (!c) return RS_EINVAL;
+    if (!blob || !X || !pred || !ws) return fail(c, RS_EINVAL, "blob, X, pred and workspace are required");
+    if (n < 1 || chunk_rows < 16 || chunk_rows % 8) return fail(c, RS_EINVAL, "n >= 1, chunk_rows >= 16, multiple of 8");
+    if ((uintptr_t)blob % 256 || (uintptr_t)ws % 256) return fail(c, RS_EINVAL, "blob and workspace must be 256-byte aligned");
+    if (ws_bytes < rs_surrogate_infer_ws_bytes(chunk_rows))
+        return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, rs_surrogate_infer_ws_bytes(chunk_rows));
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_surrogate_infer(blob, X, n, ood_threshold, pred, ood_score, used_fallback, ws,
+                                              chunk_rows, c->dstatus, c->stream);
+    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_surrogate_infer");
+}
+
 size_t rs_cv_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
     if (!b || !sp || b->n_programs < 1 || b->x_elems < 0) return 0;
     size_t z = align256((size_t)b->x_elems * sizeof(double));

@@ -86,5 +86,15 @@ struct rs_fit_args {
 #define RS_NSTAGE_EVENTS 7   // before pairs, after pairs / plan / bucket / solve / solve-large / rank
 size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t rows_cap);
 cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st);
+size_t rs_surrogate_blob_floats();
+size_t rs_surrogate_train_ws_bytes(int B);
+size_t rs_surrogate_infer_ws_bytes(int64_t chunk);
+int64_t rs_surrogate_blob_offset(int which);
+cudaError_t rs_launch_surrogate_train(float* blob, const double* X, const double* Y, int64_t n, int B,
+                                      int64_t steps, float lr, float wd, float* loss_curve, void* ws,
+                                      int use_graph, int* err, cudaStream_t st);
+cudaError_t rs_launch_surrogate_infer(const float* blob, const double* X, int64_t n, float ood_thr,
+                                      float* pred, float* score, uint8_t* fallback, void* ws, int64_t chunk,
+                                      int* err, cudaStream_t st);
 cudaError_t rs_launch_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* D, int64_t ldd,
                                 int M, int N, int K, int* err, cudaStream_t st);

@@ -33,6 +33,8 @@ EXPORTS = [
     "rs_standardize", "rs_gram", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
     "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak", "rs_fit_workspace_bytes",
     "rs_profile_enable", "rs_profile_read", "rs_cv_step_static", "rs_gemm_bf16",
+    "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
+    "rs_surrogate_train", "rs_surrogate_infer",
 ]
 
 
@@ -50,6 +52,11 @@ class _Batch(C.Structure):
         ("x_offsets", C.c_void_p), ("feat_offsets", C.c_void_p), ("X", C.c_void_p),
         ("masks", C.c_void_p), ("log_time", C.c_void_p), ("cycles", C.c_void_p),
     ]
+
+
+class _MlpCfg(C.Structure):
+    _fields_ = [("batch_rows", C.c_int32), ("use_graph", C.c_int32), ("steps", C.c_int64),
+                ("lr", C.c_float), ("weight_decay", C.c_float)]
 
 
 class _Splits(C.Structure):
@@ -92,10 +99,19 @@ def load(path: str = SO):
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
     L.rs_cv_step_static.argtypes = [P, P, P, d, i, d, i, P, P, P, P, P, P, C.c_char_p, C.c_size_t]
     L.rs_gemm_bf16.argtypes = [P, P, i64, P, i64, P, i64, i, i, i]
+    L.rs_surrogate_blob_bytes.argtypes = []
+    L.rs_surrogate_blob_bytes.restype = C.c_size_t
+    L.rs_surrogate_offset.argtypes = [i]
+    L.rs_surrogate_offset.restype = C.c_int64
+    L.rs_surrogate_workspace_bytes.argtypes = [i]
+    L.rs_surrogate_workspace_bytes.restype = C.c_size_t
+    L.rs_surrogate_train.argtypes = [P, P, P, P, i64, P, P, P, C.c_size_t]
+    L.rs_surrogate_infer.argtypes = [P, P, P, i64, C.c_float, P, P, P, P, C.c_size_t, i]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     for name in EXPORTS:
-        if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes"):
+        if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes",
+                        "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -321,6 +337,58 @@ class Context:
             self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags),
             int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
+
+
+class Surrogate:
+    """The MLP surrogate's state (one device blob) and its training / inference calls."""
+    NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+    SHAPES = {"W1": (512, 256), "b1": (512,), "W2": (512, 512), "b2": (512,), "W3": (16, 512), "b3": (16,)}
+
+    def __init__(self, ctx: "Context", batch_rows: int = 8192):
+        self.ctx = ctx
+        L = ctx.L
+        self.blob = torch.zeros(L.rs_surrogate_blob_bytes() // 4, dtype=torch.float32,
+                                device=f"cuda:{ctx.device}")
+        self.batch_rows = batch_rows
+        self.ws = ctx.workspace(L.rs_surrogate_workspace_bytes(batch_rows))
+        self.off = {n: int(L.rs_surrogate_offset(i)) for i, n in enumerate(self.NAMES)}
+        self.off.update({"m": int(L.rs_surrogate_offset(6)), "v": int(L.rs_surrogate_offset(7)),
+                         "grad": int(L.rs_surrogate_offset(8)), "stats": int(L.rs_surrogate_offset(9))})
+
+    def view(self, name: str, region: str = "param") -> torch.Tensor:
+        base = {"param": 0, "m": self.off["m"], "v": self.off["v"], "grad": self.off["grad"]}[region]
+        o = base + self.off[name]
+        shp = self.SHAPES[name]
+        n = int(np.prod(shp))
+        return self.blob[o:o + n].view(*shp)
+
+    def load(self, params: dict):
+        """Write initial weights (numpy, shapes of the FP64 reference; W3 is [6][512])."""
+        self.blob.zero_()
+        for k, v in params.items():
+            t = torch.from_numpy(np.asarray(v, dtype=np.float32)).to(self.blob.device)
+            dst = self.view(k)
+            if k in ("W3", "b3"):
+                dst[:t.shape[0]].copy_(t)
+            else:
+                dst.copy_(t)
+
+    def train(self, X, Y, steps: int, lr: float = 1e-3, weight_decay: float = 0.0, use_graph: bool = True,
+              loss_curve=None):
+        cfg = _MlpCfg(self.batch_rows, 1 if use_graph else 0, int(steps), float(lr), float(weight_decay))
+        self.ctx._check(self.ctx.L.rs_surrogate_train(
+            self.ctx.h, _ptr(self.blob), _ptr(X), _ptr(Y), X.shape[0], C.byref(cfg), _ptr(loss_curve),
+            _ptr(self.ws), self.ws.numel()))
+
+    def infer(self, X, ood_threshold: float = 1e30, want_ood: bool = False, chunk_rows=None):
+        n = X.shape[0]
+        pred = torch.empty(n, 6, dtype=torch.float32, device=X.device)
+        score = torch.empty(n, dtype=torch.float32, device=X.device) if want_ood else None
+        fb = torch.empty(n, dtype=torch.uint8, device=X.device) if want_ood else None
+        self.ctx._check(self.ctx.L.rs_surrogate_infer(
+            self.ctx.h, _ptr(self.blob), _ptr(X), n, float(ood_threshold), _ptr(pred), _ptr(score), _ptr(fb),
+            _ptr(self.ws), self.ws.numel(), int(chunk_rows or self.batch_rows)))
+        return pred, score, fb
 
 
 def measure_fma_peak(f64: bool = True, iters: int = 4096) -> float:
