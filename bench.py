@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-epochs", type=int, default=2)
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
                          "used for profiler captures")
@@ -347,6 +349,10 @@ def main():
     # end to end through the C ABI single call with host buffers (pinned), copies timed
     e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
+    sur = None
+    if rank == 0 and not args.only_step and not args.no_surrogate:
+        sur = run_surrogate(rs, ctx, dev, stream, flush, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.only_step:
         cpu = cpu_reference_sample(batch, splits, args.cpu_seconds)
@@ -366,6 +372,7 @@ def main():
         "roofline": roof,
         "accuracy": acc,
         "plain_form": plain,
+        "surrogate_form": sur,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -437,6 +444,141 @@ def run_plain(rs, ctx, batch, splits, dev, stream, flush, args):
     return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n,
             "launches_per_step": 6 * len(progs),
             "sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1)}
+
+
+def run_surrogate(rs, ctx, dev, stream, flush, args):
+    """Learned surrogate: 2 M training vectors labelled by the plain ridge predictor, ranked
+    inference on 1 M held-out vectors, against the batched plain method on the same rows."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    from oracle import mlp
+    P_tr, P_te = 31250, 15625
+    t0 = time.perf_counter()
+    b = synth.make_batch_fast(P_tr + P_te, versions=64, feat=256, dtype=np.float32, seed=11)
+    sp = synth.make_complementary_halves(b, seed=11)
+    gen_s = time.perf_counter() - t0
+    n_all = b.n_rows
+    db = rs.DeviceBatch.from_host(b, dev)
+    ds = rs.DeviceSplits.from_host(sp, dev, b)
+    # plain labels: every version predicted by the fit on the other half of its program
+    Z = ctx.standardize(db)
+    zb = db.with_X(Z)
+    K = ctx.gram(zb)
+    ro = ctx.rec_offsets(zb, ds)
+    R = ds.n_test_rows
+    out = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev)
+    ctx.predict_rank(zb, K, ds, ro, out.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                     flags=rs.RS_RANK_ALL, rec_pred=out.rec_pred, pred_all=out.pred_all)
+    torch.cuda.synchronize()
+    # row -> version: split 2p tests the complement of A, split 2p+1 tests A (slot order)
+    tm = sp.train_masks.astype(np.uint64)
+    ver = np.empty(R, dtype=np.int64)
+    r = 0
+    for p in range(b.n_programs):
+        for s_ in (2 * p, 2 * p + 1):
+            T = int(tm[s_])
+            for v in range(64):
+                if not (T >> v) & 1:
+                    ver[r] = p * 64 + v
+                    r += 1
+    inv = torch.from_numpy(np.argsort(ver)).to(dev)
+    Y = out.pred_all.view(R, 6)[inv].contiguous()                         # [n_all][6], version order
+    Zm = Z.view(n_all, 256)
+    n_tr = P_tr * 64
+    Xtr, Ytr = Zm[:n_tr], Y[:n_tr]
+    Xte = Zm[n_tr:].contiguous()
+    masks_te = db.masks[n_tr:].contiguous()
+    sur = rs.Surrogate(ctx, 8192)
+    sur.load(mlp.init_params(11))
+    steps = args.surrogate_epochs * (n_tr // 8192)
+    lc = torch.zeros(steps, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sur.train(Xtr, Ytr, steps=steps, lr=1e-3, use_graph=True, loss_curve=lc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    n_te = Xte.shape[0]
+    code = torch.empty(n_te, dtype=torch.int32, device=dev)
+    rp = torch.empty(n_te * CFG["k"], dtype=torch.float64, device=dev)
+    thr = 3.0
+    # timed: ranked surrogate inference with OOD flags
+    for _ in range(2):
+        sur.infer(Xte, ood_threshold=thr, want_ood=True, masks=masks_te, k=CFG["k"], tau=CFG["tau"],
+                  rec_code=code, rec_pred=rp, want_pred=False)
+    torch.cuda.synchronize()
+    reps = 5
+    inf_ms = 0.0
+    for _ in range(reps):
+        flush.fill_(1)
+        e0.record(stream)
+        _, score, fb = sur.infer(Xte, ood_threshold=thr, want_ood=True, masks=masks_te, k=CFG["k"],
+                                 tau=CFG["tau"], rec_code=code, rec_pred=rp, want_pred=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        inf_ms += e0.elapsed_time(e1)
+    inf_ms /= reps
+    pred_s, _, _ = sur.infer(Xte)
+    torch.cuda.synchronize()
+    fb_frac = float(fb.float().mean())
+    # the plain batched method on the held-out programs (same protocol), timed
+    te = synth.ProgramBatch(X=b.X[n_tr * 256:], x_offsets=b.x_offsets[P_tr:] - b.x_offsets[P_tr],
+                            row_offsets=b.row_offsets[P_tr:] - b.row_offsets[P_tr],
+                            feat_width=b.feat_width[P_tr:], masks=b.masks[n_tr:],
+                            log_time=b.log_time[n_tr:], cycles=b.cycles[n_tr:])
+    tsp = synth.Splits(split_offsets=sp.split_offsets[2 * P_tr:] - sp.split_offsets[2 * P_tr],
+                       train_masks=sp.train_masks[2 * P_tr:])
+    tdb = rs.DeviceBatch.from_host(te, dev)
+    tds = rs.DeviceSplits.from_host(tsp, dev, te)
+    tout = rs.alloc_outputs(tds.n_test_rows, tds.n_splits, CFG["k"], dev, pred_all=False)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(tdb, tds))
+    for _ in range(2):
+        ctx.cv_step(tdb, tds, ws, tout.rec_offsets, tout.rec_code, lam=CFG["lam"], k=CFG["k"],
+                    tau=CFG["tau"], rec_pred=tout.rec_pred)
+    torch.cuda.synchronize()
+    plain_ms = 0.0
+    for _ in range(reps):
+        flush.fill_(1)
+        e0.record(stream)
+        ctx.cv_step(tdb, tds, ws, tout.rec_offsets, tout.rec_code, lam=CFG["lam"], k=CFG["k"],
+                    tau=CFG["tau"], rec_pred=tout.rec_pred)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+    plain_ms /= reps
+    # accuracy against the ground truth (all 64 masks present: t|j always exists)
+    lt = b.log_time[n_tr:].reshape(P_te, 64)
+    m = np.arange(64)
+    act = np.stack([lt - lt[:, m | (1 << j)] for j in range(6)], axis=2)   # [P,64,6]
+    cand = ((m[:, None] >> np.arange(6)[None, :]) & 1) == 0                 # [64,6]
+    ps = pred_s.cpu().numpy().reshape(P_te, 64, 6).astype(np.float64)
+    pp = Y[n_tr:].cpu().numpy().reshape(P_te, 64, 6)
+    cm = np.broadcast_to(cand, ps.shape) & np.isfinite(pp)
+
+    def acc(pr):
+        sign = float(np.mean(((pr > 0) == (act > 0))[cm]))
+        prm = np.where(cm, pr, -np.inf)
+        acm = np.where(cm, act, -np.inf)
+        rows = cm.any(axis=2)
+        top1 = float(np.mean((prm.argmax(2) == acm.argmax(2))[rows]))
+        return sign, top1
+
+    s_sign, s_top1 = acc(ps)
+    p_sign, p_top1 = acc(pp)
+    mae = float(np.mean(np.abs(ps - pp)[cm]))
+    rate_s = n_te / (inf_ms * 1e-3)
+    rate_p = tds.n_test_rows / (plain_ms * 1e-3)
+    eff = n_te / (inf_ms * 1e-3 + fb_frac * n_te / rate_p)
+    return {"workload": "surrogate MLP 256-512-512-6: train 2,000,000 vectors (31,250 programs x 64 "
+                        "versions, labels = plain ridge CV predictions), infer 1,000,000 held-out vectors",
+            "value": rate_s, "unit": UNIT, "infer_ms": inf_ms, "train_ms": train_ms,
+            "train_steps": steps, "batch_rows": 8192, "loss_first": float(lc[0]), "loss_last": float(lc[-1]),
+            "plain_batched_same_rows": {"value": rate_p, "ms": plain_ms},
+            "speedup_vs_plain_batched": rate_s / rate_p,
+            "ood_threshold": thr, "fallback_fraction": fb_frac, "value_with_plain_fallback": eff,
+            "accuracy": {"surrogate_sign": s_sign, "surrogate_top1": s_top1, "plain_sign": p_sign,
+                         "plain_top1": p_top1, "mae_vs_plain_log_speedup": mae},
+            "data_gen_s": gen_s}
 
 
 def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):

@@ -236,9 +236,13 @@ rs_status rs_gemm_bf16(rs_ctx* ctx, const void* A, int64_t lda, const void* B, i
  * wrapping around; cfg->steps optimizer steps (0: only the feature statistics and the BF16
  * weight copies are prepared).  use_graph = 1 captures one step in a CUDA graph and replays
  * it.  loss_curve (nullable, float [steps]) gets each minibatch's loss.
- * rs_surrogate_infer: pred [n][6] (float); ood_score [n] (nullable) = mean over features of
- * ((x - mean) / std)^2 against the training statistics; used_fallback [n] (nullable) = 1
- * where ood_score > ood_threshold (those rows should be predicted by the plain method).
+ * rs_surrogate_infer: pred [n][6] (float, nullable); ood_score [n] (nullable) = mean over
+ * features of ((x - mean) / std)^2 against the training statistics; used_fallback [n]
+ * (nullable) = 1 where ood_score > ood_threshold (those rows should be predicted by the
+ * plain method).  With rec_code (nullable) the six outputs of each row are also ranked as
+ * in rs_predict_rank (candidates: bits not set in masks[row]; all six with RS_RANK_ALL or
+ * masks == NULL; threshold log(tau) compared in FP32; ties to the lower index; top k):
+ * rec_code [n] and rec_pred [n][k] (double, nullable) in the rs_predict_rank format.
  * workspace: rs_surrogate_workspace_bytes(batch_rows) bytes, 256-byte aligned; inference
  * processes chunk_rows rows at a time (chunk_rows <= the batch_rows the workspace was
  * sized for).  RS_ETIMEOUT in the device status if a tensor-core pipeline wait gave up. */
@@ -257,8 +261,9 @@ rs_status rs_surrogate_train(rs_ctx* ctx, float* blob, const double* X, const do
                              size_t workspace_bytes);
 rs_status rs_surrogate_infer(rs_ctx* ctx, const float* blob, const double* X, int64_t n,
                              float ood_threshold, float* pred, float* ood_score,
-                             uint8_t* used_fallback, void* workspace, size_t workspace_bytes,
-                             int chunk_rows);
+                             uint8_t* used_fallback, const uint8_t* masks, int k, double tau,
+                             int flags, uint32_t* rec_code, double* rec_pred, void* workspace,
+                             size_t workspace_bytes, int chunk_rows);
 
 /* ---- the whole step, allocating nothing -------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of rs_cv_step for callers that

@@ -78,8 +78,57 @@ struct EpiOutput {           // out = acc + b3; training: residual, loss, dO, dO
     int64_t ldt;
     float scale;             // 2 / (6 B)
     float* pred;             // [B][6] (inference) or null
+    // inference ranking (Sec. 2 tier 3 on the surrogate's predictions), optional
+    const uint8_t* masks;    // [B] version masks (candidates: optimizations not applied)
+    int flags, k;
+    float log_tau;
+    uint32_t* rec_code;      // [B]
+    double* rec_pred;        // [B][k]
+    __device__ void rank_row(int row, const float (&o)[16]) const {
+        const int cand = (flags & RS_RANK_ALL) || !masks ? 63 : (~masks[row] & 63);
+        int above = 0, bm[kOut];
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) {
+            bm[j] = 0;
+            above |= (((cand >> j) & 1) && o[j] >= log_tau) << j;
+        }
+#pragma unroll
+        for (int i = 0; i < kOut; ++i)
+#pragma unroll
+            for (int j = i + 1; j < kOut; ++j) {
+                if (o[i] >= o[j]) bm[j] |= 1 << i;
+                else bm[i] |= 1 << j;
+            }
+        uint32_t code = 0x0FFFFFF0u;
+        int c = 0;
+        double rp[kOut];
+#pragma unroll
+        for (int x = 0; x < kOut; ++x) rp[x] = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) {
+            const int pos = __popc(bm[j] & above);
+            if (((above >> j) & 1) && pos < k) {
+                code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
+#pragma unroll
+                for (int x = 0; x < kOut; ++x)
+                    if (x == pos) rp[x] = o[j];
+                ++c;
+            }
+        }
+        rec_code[row] = (code & ~0xFu) | (uint32_t)c;
+        if (rec_pred)
+#pragma unroll
+            for (int x = 0; x < kOut; ++x)
+                if (x < k) rec_pred[(int64_t)row * k + x] = rp[x];
+    }
     __device__ void operator()(int row, int col0, const float (&v)[16]) const {
         if (col0 != 0) return;
+        if (rec_code) {
+            float o[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = v[i] + bias[i];
+            rank_row(row, o);
+        }
         float l = 0.f;
         alignas(16) __nv_bfloat16 g[16];
 #pragma unroll
@@ -374,7 +423,8 @@ cudaError_t step_body(float* blob, const TrainWs& w, const Maps& m, int B, float
         e = gemm<128>(m.H1, m.W2, B, kHid, kHid, EpiHidden{P + Blob::ob2, w.U2, w.H2, w.H2t, B}, err, st);
     if (e == cudaSuccess)
         e = gemm<32>(m.H2, m.W3, B, kOutP, kHid,
-                     EpiOutput{P + Blob::ob3, w.Ys, loss_slot, w.dO, w.dOt, B, sc, nullptr}, err, st);
+                     EpiOutput{P + Blob::ob3, w.Ys, loss_slot, w.dO, w.dOt, B, sc, nullptr, nullptr, 0, 0, 0.f,
+                               nullptr, nullptr}, err, st);
     if (e == cudaSuccess)      // dU2 = (dO W3) * gelu'(U2)
         e = gemm<128>(m.dO, m.W3t, B, kHid, kOutP, EpiGeluGrad{w.U2, w.dU2, w.dU2t, B}, err, st);
     if (e == cudaSuccess)      // dU1 = (dU2 W2) * gelu'(U1)
@@ -499,8 +549,9 @@ cudaError_t rs_launch_surrogate_train(float* blob, const double* X, const double
 
 // Forward pass over n rows in chunks: pred [n][6] (FP32); optional OOD score and fallback flags.
 cudaError_t rs_launch_surrogate_infer(const float* blob, const double* X, int64_t n, float ood_thr,
-                                      float* pred, float* score, uint8_t* fallback, void* ws, int64_t chunk,
-                                      int* err, cudaStream_t st) {
+                                      float* pred, float* score, uint8_t* fallback, const uint8_t* masks,
+                                      int k, double tau, int flags, uint32_t* rec_code, double* rec_pred,
+                                      void* ws, int64_t chunk, int* err, cudaStream_t st) {
     const __nv_bfloat16* bf = reinterpret_cast<const __nv_bfloat16*>(blob + Blob::oBf);
     char* c = (char*)ws;
     __nv_bfloat16* Xs = (__nv_bfloat16*)c;
@@ -523,7 +574,10 @@ cudaError_t rs_launch_surrogate_infer(const float* blob, const double* X, int64_
             e = gemm<128>(tH1, tW2, B, kHid, kHid, EpiHidden{blob + Blob::ob2, nullptr, H2, nullptr, B}, err, st);
         if (e == cudaSuccess)
             e = gemm<32>(tH2, tW3, B, kOutP, kHid,
-                         EpiOutput{blob + Blob::ob3, nullptr, nullptr, nullptr, nullptr, B, 0.f, pred + r0 * kOut},
+                         EpiOutput{blob + Blob::ob3, nullptr, nullptr, nullptr, nullptr, B, 0.f,
+                                   pred ? pred + r0 * kOut : nullptr, masks ? masks + r0 : nullptr, flags, k,
+                                   (float)log(tau), rec_code ? rec_code + r0 : nullptr,
+                                   rec_pred ? rec_pred + r0 * k : nullptr},
                          err, st);
     }
     if (e == cudaSuccess && (score || fallback)) {

@@ -356,17 +356,22 @@ rs_status rs_surrogate_train(rs_ctx* c, float* blob, const double* X, const doub
 }
 
 rs_status rs_surrogate_infer(rs_ctx* c, const float* blob, const double* X, int64_t n, float ood_threshold,
-                             float* pred, float* ood_score, uint8_t* used_fallback, void* ws, size_t ws_bytes,
-                             int chunk_rows) {
+                             float* pred, float* ood_score, uint8_t* used_fallback, const uint8_t* masks,
+                             int k, double tau, int flags, uint32_t* rec_code, double* rec_pred, void* ws,
+                             size_t ws_bytes, int chunk_rows) {
     if (!c) return RS_EINVAL;
-    if (!blob || !X || !pred || !ws) return fail(c, RS_EINVAL, "blob, X, pred and workspace are required");
+    if (!blob || !X || !ws) return fail(c, RS_EINVAL, "blob, X and workspace are required");
+    if (!pred && !rec_code) return fail(c, RS_EINVAL, "ask for pred and/or rec_code");
+    if (rec_code && (k < 1 || k > RS_NOPT || !(tau > 0.0) || (flags & ~RS_RANK_ALL)))
+        return fail(c, RS_EINVAL, "ranking: k in 1..6, tau > 0, flags RS_RANK_ALL only");
     if (n < 1 || chunk_rows < 16 || chunk_rows % 8) return fail(c, RS_EINVAL, "n >= 1, chunk_rows >= 16, multiple of 8");
     if ((uintptr_t)blob % 256 || (uintptr_t)ws % 256) return fail(c, RS_EINVAL, "blob and workspace must be 256-byte aligned");
     if (ws_bytes < rs_surrogate_infer_ws_bytes(chunk_rows))
         return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, rs_surrogate_infer_ws_bytes(chunk_rows));
     cudaSetDevice(c->device);
-    cudaError_t e = rs_launch_surrogate_infer(blob, X, n, ood_threshold, pred, ood_score, used_fallback, ws,
-                                              chunk_rows, c->dstatus, c->stream);
+    cudaError_t e = rs_launch_surrogate_infer(blob, X, n, ood_threshold, pred, ood_score, used_fallback, masks,
+                                              k, tau, flags, rec_code, rec_pred, ws, chunk_rows, c->dstatus,
+                                              c->stream);
     if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_surrogate_infer");
 }

@@ -94,7 +94,8 @@ cudaError_t rs_launch_surrogate_train(float* blob, const double* X, const double
                                       int64_t steps, float lr, float wd, float* loss_curve, void* ws,
                                       int use_graph, int* err, cudaStream_t st);
 cudaError_t rs_launch_surrogate_infer(const float* blob, const double* X, int64_t n, float ood_thr,
-                                      float* pred, float* score, uint8_t* fallback, void* ws, int64_t chunk,
-                                      int* err, cudaStream_t st);
+                                      float* pred, float* score, uint8_t* fallback, const uint8_t* masks,
+                                      int k, double tau, int flags, uint32_t* rec_code, double* rec_pred,
+                                      void* ws, int64_t chunk, int* err, cudaStream_t st);
 cudaError_t rs_launch_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* D, int64_t ldd,
                                 int M, int N, int K, int* err, cudaStream_t st);

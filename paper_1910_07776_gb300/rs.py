@@ -106,7 +106,7 @@ def load(path: str = SO):
     L.rs_surrogate_workspace_bytes.argtypes = [i]
     L.rs_surrogate_workspace_bytes.restype = C.c_size_t
     L.rs_surrogate_train.argtypes = [P, P, P, P, i64, P, P, P, C.c_size_t]
-    L.rs_surrogate_infer.argtypes = [P, P, P, i64, C.c_float, P, P, P, P, C.c_size_t, i]
+    L.rs_surrogate_infer.argtypes = [P, P, P, i64, C.c_float, P, P, P, P, i, d, i, P, P, P, C.c_size_t, i]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     for name in EXPORTS:
@@ -380,13 +380,16 @@ class Surrogate:
             self.ctx.h, _ptr(self.blob), _ptr(X), _ptr(Y), X.shape[0], C.byref(cfg), _ptr(loss_curve),
             _ptr(self.ws), self.ws.numel()))
 
-    def infer(self, X, ood_threshold: float = 1e30, want_ood: bool = False, chunk_rows=None):
+    def infer(self, X, ood_threshold: float = 1e30, want_ood: bool = False, chunk_rows=None,
+              want_pred: bool = True, masks=None, k: int = 3, tau: float = 1.05, flags: int = 0,
+              rec_code=None, rec_pred=None):
         n = X.shape[0]
-        pred = torch.empty(n, 6, dtype=torch.float32, device=X.device)
+        pred = torch.empty(n, 6, dtype=torch.float32, device=X.device) if want_pred else None
         score = torch.empty(n, dtype=torch.float32, device=X.device) if want_ood else None
         fb = torch.empty(n, dtype=torch.uint8, device=X.device) if want_ood else None
         self.ctx._check(self.ctx.L.rs_surrogate_infer(
             self.ctx.h, _ptr(self.blob), _ptr(X), n, float(ood_threshold), _ptr(pred), _ptr(score), _ptr(fb),
+            _ptr(masks), int(k), float(tau), int(flags), _ptr(rec_code), _ptr(rec_pred),
             _ptr(self.ws), self.ws.numel(), int(chunk_rows or self.batch_rows)))
         return pred, score, fb
 

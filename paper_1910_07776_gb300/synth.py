@@ -259,6 +259,112 @@ def make_half_splits_fast(batch: ProgramBatch, n_splits: int, seed: int = 0) -> 
     return Splits(split_offsets=offs, train_masks=tm)
 
 
+def make_batch_fast(n_programs: int, versions: IntOrRange = 64, feat: int = 256,
+                    feat_choices: Optional[Sequence[int]] = None, dtype=np.float32, seed: int = 0,
+                    with_cycles: bool = True, label_noise: float = 0.05, feat_noise: float = 0.3,
+                    chunk: int = 512) -> ProgramBatch:
+    """The recipe of ``make_batch`` drawn in vectorised chunks of programs (for batches of
+    thousands of programs).  Same distribution, different random stream."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0xFA57))
+    P = int(n_programs)
+    Vs = _pick(rng, versions, P)
+    if feat_choices is not None:
+        Fs = rng.choice(np.asarray(feat_choices, dtype=np.int64), size=P)
+    else:
+        Fs = np.full(P, int(feat), dtype=np.int64)
+    w = rng.standard_normal((N_OPT, LATENT))
+    u = rng.standard_normal((N_OPT, N_OPT, LATENT))
+    Fmax = int(Fs.max())
+    U = (0.5 * rng.standard_normal((N_OPT, Fmax))).astype(np.float32)
+    Cm = rng.standard_normal((N_OPT, Fmax, LATENT)).astype(np.float32)
+    sM = np.sqrt(max(2.25 - 3.0 * (0.25 + 0.09 * 1.0) - feat_noise ** 2, 0.1) / LATENT)
+    M = (sM * rng.standard_normal((Fmax, LATENT))).astype(np.float32)
+    all_masks = np.arange(N_MASK)
+    bits = ((all_masks[:, None] >> np.arange(N_OPT)[None, :]) & 1).astype(np.float32)
+    wn = w / np.linalg.norm(w, axis=1, keepdims=True)
+    un = u / np.linalg.norm(u, axis=2, keepdims=True)
+    row_off = np.zeros(P + 1, dtype=np.int64)
+    row_off[1:] = np.cumsum(Vs)
+    x_off = np.zeros(P, dtype=np.int64)
+    x_off[1:] = np.cumsum(Vs * Fs)[:-1]
+    X = np.empty(int((Vs * Fs).sum()), dtype=dtype)
+    masks = np.empty(int(row_off[-1]), dtype=np.uint8)
+    log_time = np.empty(int(row_off[-1]), dtype=np.float64)
+    cycles = np.empty(int(row_off[-1]), dtype=np.float64) if with_cycles else None
+    for F in np.unique(Fs):
+        idx = np.nonzero(Fs == F)[0]
+        for c0 in range(0, len(idx), chunk):
+            ps = idx[c0:c0 + chunk]
+            G = len(ps)
+            h = rng.standard_normal((G, LATENT))
+            a = 0.3 * h @ wn.T                                            # [G,6]
+            b = 0.1 * np.einsum("jkl,gl->gjk", un, h)
+            b = np.triu(b, 1) if b.ndim == 2 else b * np.triu(np.ones((N_OPT, N_OPT)), 1)[None]
+            keys = rng.random((G, N_MASK))
+            order = np.argsort(keys, axis=1)
+            t0 = rng.standard_normal(G)
+            shift = U[None, :, :F] + 0.3 * (Cm[:, :F, :].reshape(-1, LATENT) @ h.astype(np.float32).T).T.reshape(
+                G, N_OPT, F) / np.sqrt(LATENT)
+            base = (h.astype(np.float32) @ M[:F].T)                         # [G,F]
+            if np.all(Vs[ps] == N_MASK):     # every program owns all 64 masks: fully vectorised
+                mb = bits                                                  # [64,6]
+                ls = a @ mb.T + np.einsum("vj,gjk,vk->gv", mb, b, mb)
+                ls = ls + label_noise * rng.standard_normal((G, N_MASK))
+                lt = t0[:, None] - ls                                      # [G,64]
+                logx = base[:, None, :] + np.matmul(mb[None], shift)
+                logx = logx + feat_noise * rng.standard_normal((G, N_MASK, F), dtype=np.float32)
+                xx = np.exp(logx)
+                if with_cycles:
+                    cyc = np.exp(lt + 20.0 + 0.02 * rng.standard_normal((G, N_MASK)))
+                    xx = xx * cyc[:, :, None].astype(np.float32)
+                for gi, p in enumerate(ps):
+                    r0 = int(row_off[p])
+                    X[int(x_off[p]):int(x_off[p]) + N_MASK * F] = xx[gi].reshape(-1)
+                    masks[r0:r0 + N_MASK] = all_masks.astype(np.uint8)
+                    log_time[r0:r0 + N_MASK] = lt[gi]
+                    if with_cycles:
+                        cycles[r0:r0 + N_MASK] = cyc[gi]
+                continue
+            for gi, p in enumerate(ps):
+                V = int(Vs[p])
+                ms = all_masks.copy() if V == N_MASK else np.sort(order[gi, :V])
+                mb = bits[ms]                                             # [V,6]
+                ls = mb @ a[gi] + np.einsum("vj,jk,vk->v", mb, b[gi], mb) + label_noise * rng.standard_normal(V)
+                lt = t0[gi] - ls
+                logx = base[gi][None, :] + mb @ shift[gi] + feat_noise * rng.standard_normal((V, F), dtype=np.float32)
+                xx = np.exp(logx)
+                r0 = int(row_off[p])
+                if with_cycles:
+                    cyc = np.exp(lt + 20.0 + 0.02 * rng.standard_normal(V))
+                    xx = xx * cyc[:, None]
+                    cycles[r0:r0 + V] = cyc
+                X[int(x_off[p]):int(x_off[p]) + V * F] = xx.reshape(-1).astype(dtype)
+                masks[r0:r0 + V] = ms.astype(np.uint8)
+                log_time[r0:r0 + V] = lt
+    return ProgramBatch(X=X, x_offsets=x_off, row_offsets=row_off, feat_width=Fs.astype(np.int32),
+                        masks=masks, log_time=log_time, cycles=cycles,
+                        meta=dict(gen=GEN_VERSION + "-fast", seed=seed, n_programs=P))
+
+
+def make_complementary_halves(batch: ProgramBatch, seed: int = 0) -> Splits:
+    """Two splits per program: a random half of its versions and the other half, so that every
+    version is a test row exactly once (its prediction comes from a fit on the other half)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0xC0FE))
+    P = batch.n_programs
+    offs = np.arange(P + 1, dtype=np.int64) * 2
+    tm = np.zeros(2 * P, dtype=np.uint64)
+    for p in range(P):
+        V = batch.versions(p)
+        sel = np.argsort(rng.random(V))[:V // 2]
+        m = 0
+        for r in sel:
+            m |= 1 << int(r)
+        full = (1 << V) - 1 if V < 64 else (1 << 64) - 1
+        tm[2 * p] = np.uint64(m)
+        tm[2 * p + 1] = np.uint64(full & ~m)
+    return Splits(split_offsets=offs, train_masks=tm)
+
+
 def make_vectors(n: int, F: int = 256, seed: int = 0, dtype=np.float32) -> np.ndarray:
     """Standard-normal stand-ins for standardized feature vectors (surrogate inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed ^ 0x7EC7))

@@ -138,3 +138,29 @@ def test_training_learns_and_ood_flags_shifted_rows(env):
     s = score.cpu().numpy()
     ref = mlp.ood_score(Xs, X.mean(0), X.std(0))
     np.testing.assert_allclose(s, ref, rtol=1e-4)
+
+
+def test_inference_ranking_matches_reference_ranking(env):
+    rs, ctx = env
+    import math
+    import oracle
+    X, Y, Xd, Yd = data(700, 6)
+    p = mlp.init_params(6)
+    p["b3"] = np.array([0.05, -0.02, 0.1, 0.049, 0.3, 0.0])       # spread the outputs around log 1.05
+    sur = rs.Surrogate(ctx, 256)
+    sur.load(p)
+    sur.train(Xd[:256], Yd[:256], steps=0)
+    masks = torch.from_numpy(np.random.default_rng(6).integers(0, 64, size=700).astype(np.uint8)).cuda()
+    code = torch.empty(700, dtype=torch.int32, device="cuda")
+    rp = torch.empty(700 * 3, dtype=torch.float64, device="cuda")
+    pred, _, _ = sur.infer(Xd, masks=masks, k=3, tau=1.05, rec_code=code, rec_pred=rp, chunk_rows=256)
+    torch.cuda.synchronize()
+    P = pred.cpu().numpy().astype(np.float64)
+    m = masks.cpu().numpy()
+    lt = float(np.float32(math.log(1.05)))
+    got = oracle.decode_rec(code.cpu().numpy().view(np.uint32))
+    for r in range(700):
+        valid = np.array([not (m[r] >> j) & 1 for j in range(6)], dtype=np.int32)
+        want = list(oracle.rank(P[r], valid, 3, lt))
+        assert got[r] == want, (r, got[r], want, P[r])
+        np.testing.assert_array_equal(rp.cpu().numpy().reshape(700, 3)[r, :len(want)], P[r, want])
