@@ -472,15 +472,10 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
     torch.cuda.synchronize()
     # row -> version: split 2p tests the complement of A, split 2p+1 tests A (slot order)
     tm = sp.train_masks.astype(np.uint64)
-    ver = np.empty(R, dtype=np.int64)
-    r = 0
-    for p in range(b.n_programs):
-        for s_ in (2 * p, 2 * p + 1):
-            T = int(tm[s_])
-            for v in range(64):
-                if not (T >> v) & 1:
-                    ver[r] = p * 64 + v
-                    r += 1
+    bitsv = ((tm[:, None] >> np.arange(64, dtype=np.uint64)[None, :]) & np.uint64(1)) == 0   # test slots
+    split_prog = np.repeat(np.arange(b.n_programs), 2)
+    ver = (split_prog[:, None] * 64 + np.arange(64)[None, :])[bitsv]      # split-major, slot order
+    assert ver.shape[0] == R
     inv = torch.from_numpy(np.argsort(ver)).to(dev)
     Y = out.pred_all.view(R, 6)[inv].contiguous()                         # [n_all][6], version order
     Zm = Z.view(n_all, 256)
@@ -526,7 +521,7 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
                             row_offsets=b.row_offsets[P_tr:] - b.row_offsets[P_tr],
                             feat_width=b.feat_width[P_tr:], masks=b.masks[n_tr:],
                             log_time=b.log_time[n_tr:], cycles=b.cycles[n_tr:])
-    tsp = synth.Splits(split_offsets=sp.split_offsets[2 * P_tr:] - sp.split_offsets[2 * P_tr],
+    tsp = synth.Splits(split_offsets=sp.split_offsets[P_tr:] - sp.split_offsets[P_tr],
                        train_masks=sp.train_masks[2 * P_tr:])
     tdb = rs.DeviceBatch.from_host(te, dev)
     tds = rs.DeviceSplits.from_host(tsp, dev, te)
