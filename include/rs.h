@@ -142,11 +142,15 @@ rs_status rs_standardize(rs_ctx* ctx, const rs_batch* batch, double* Z, double* 
 /* ---- A3: per-program Gram of the standardized feature vectors -------------------------
  * K_p[a][b] = sum_f Z[a][f] * Z[b][f] for a, b < V_p, written to
  * K[p * 64 * 64 + a * 64 + b] (double; entries outside V_p x V_p are left untouched).
- * std: a batch whose X is Z (double).  precision: RS_GRAM_F64 (FP64 FMAs) or
- * RS_GRAM_BF16X3 (tcgen05 tensor cores, BF16 hi/lo split of Z, three products per term,
- * FP32 accumulation; relative error about 2^-16 per entry).  Every ridge fit of a split
- * reads its kernel entries from this block (the dual form of the regression).         */
-rs_status rs_gram(rs_ctx* ctx, const rs_batch* std, int precision, double* K);
+ * std: a batch whose X is Z (double).  precision: RS_GRAM_F64 (FP64 FMAs, no workspace) or
+ * RS_GRAM_BF16X3 (tcgen05 tensor cores: z = hi + lo with hi = bf16(z), lo = bf16(z - hi),
+ * K ~ hi hi^T + hi lo^T + lo hi^T accumulated in FP32 -- relative error about 2^-16 per
+ * entry; symmetric; needs rs_gram_workspace_bytes(std, precision) bytes of workspace,
+ * 256-byte aligned, and at most 65535 programs per call).  Every ridge fit of a split reads
+ * its kernel entries from this block (the dual form of the regression).             */
+size_t rs_gram_workspace_bytes(const rs_batch* std, int precision);
+rs_status rs_gram(rs_ctx* ctx, const rs_batch* std, int precision, double* K, void* workspace,
+                  size_t workspace_bytes);
 
 /* ---- A2: test-row planning ------------------------------------------------------------
  * rec_offsets[i] = number of test rows (version slots outside the train mask) of all
@@ -190,7 +194,11 @@ rs_status rs_fit_batched(rs_ctx* ctx, const rs_batch* std, const double* K,
  *   rec_pred  double [R][k]: predicted log speedups of the reported list (NaN unused), nullable
  *   pred_all  double [R][6]: every prediction (NaN where none), nullable
  *   counters  uint64 [16]: accuracy counters (listed above), added to; nullable
- * flags: RS_RANK_ALL; RS_REFINE_X is reserved (RS_EUNSUPPORTED).  tau > 0.             */
+ * flags: RS_RANK_ALL; RS_REFINE_X (batched form, coef == NULL): every fit gets one step of
+ * iterative refinement of its bordered system with the residual computed from Z in FP64
+ * (r_a = y_a - b - lambda alpha_a - z_a . beta, beta = sum_a alpha_a z_a), solved with the
+ * same factor, and predictions are taken through Z (b + z_t . beta) -- for Gram blocks made
+ * with RS_GRAM_BF16X3.  tau > 0.                                                      */
 rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
                           const rs_splits* splits, double lambda, const double* coef,
                           int k, double tau, int flags, int form, void* workspace,

@@ -455,6 +455,11 @@ struct SolveArgs {
     int64_t R;
     int flags;
     int* dstatus;
+    // refinement through Z (RS_REFINE_X)
+    const double* Z;
+    const int64_t* x_offsets;
+    const int32_t* feat_width;
+    int max_feat;
 };
 
 __device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j, int p, PredTarget& pt) {
@@ -527,11 +532,30 @@ solve_small_kernel(const SolveArgs a) {
 }
 
 // ====================================================================== solve, one fit per warp
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// One step of iterative refinement through the feature vectors, for a Gram block that is
+// only approximately Z Z^T (the tensor-core form): the exact bordered residual
+//   r_a = y_a - b - lambda alpha_a - z_{v_a} . beta,  r_0 = -sum_a alpha_a,  beta = sum_a alpha_a z_{v_a}
+// is computed in FP64 from Z, the correction solves the same factored system, and the
+// predictions are b + z_t . beta (through Z, not through the Gram block).
+struct RefineCtx {
+    const double* Zp;     // the program's standardized rows, [V][F]
+    int F;
+    double* beta;         // per-warp shared buffer of F doubles
+    double* sh;           // per-warp shared buffer of 64 doubles (coefficients)
+    int* vsh;             // per-warp shared buffer of 32 ints (pair slots)
+};
+
 // Lane a owns row a (a < n <= 32).  K is read with leading dimension ld.  Lsh: [32][33].
 // Writes b to coef[0] and alpha to coef[1..n]; returns a warp-uniform status.
 __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double* ylab,
                         const double* K, int ld, double lambda, double* Lsh, double* coef,
-                        const PredTarget* pt = nullptr) {
+                        const PredTarget* pt = nullptr, const RefineCtx* rf = nullptr) {
     const int lane = threadIdx.x & 31;
     const bool act = lane < n;
     int v = 0;
@@ -594,14 +618,77 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
         su += __shfl_xor_sync(0xffffffffu, su, o);
         sw += __shfl_xor_sync(0xffffffffu, sw, o);
     }
-    const double b = su / sw;
-    const double al = fma(-b, w, u);
-    const int fin = __all_sync(0xffffffffu, !act || finite_bits(al)) && finite_bits(b);
+    double b = su / sw;
+    double al = fma(-b, w, u);
+    int fin = __all_sync(0xffffffffu, !act || finite_bits(al)) && finite_bits(b);
+    if (rf && fin) {
+        const int F = rf->F;
+        const double* Zp = rf->Zp;
+        double* beta = rf->beta;
+        if (act) {
+            rf->sh[lane] = al;
+            rf->vsh[lane] = v;
+        }
+        __syncwarp();
+        for (int f = lane; f < F; f += 32) {          // beta = sum_a alpha_a z_{v_a}
+            double acc = 0.0;
+            for (int q = 0; q < n; ++q) acc = fma(rf->sh[q], Zp[(int64_t)rf->vsh[q] * F + f], acc);
+            beta[f] = acc;
+        }
+        __syncwarp();
+        double ra = 0.0;                              // z_{v_q} . beta, lane q keeps its own
+        for (int q = 0; q < n; ++q) {
+            double part = 0.0;
+            for (int f = lane; f < F; f += 32) part = fma(Zp[(int64_t)rf->vsh[q] * F + f], beta[f], part);
+            part = warp_sum(part);
+            if (lane == q) ra = part;
+        }
+        ra = act ? y - b - lambda * al - ra : 0.0;
+        const double r0 = -warp_sum(act ? al : 0.0);
+        double uu = ra;
+        for (int kk = 0; kk < n; ++kk) {              // forward with the same factor
+            const double r = __shfl_sync(0xffffffffu, rinv, kk);
+            const double uk = __shfl_sync(0xffffffffu, uu, kk) * r;
+            if (lane == kk) uu = uk;
+            else if (act && lane > kk) uu = fma(-Lsh[lane * 33 + kk], uk, uu);
+        }
+        for (int kk = n - 1; kk >= 0; --kk) {         // backward
+            const double r = __shfl_sync(0xffffffffu, rinv, kk);
+            const double uk = __shfl_sync(0xffffffffu, uu, kk) * r;
+            if (lane == kk) uu = uk;
+            else if (lane < kk) uu = fma(-Lsh[kk * 33 + lane], uk, uu);
+        }
+        const double db = (warp_sum(act ? uu : 0.0) - r0) / warp_sum(act ? w : 0.0);
+        const double da = act ? fma(-db, w, uu) : 0.0;
+        al += da;
+        b += db;
+        if (act) rf->sh[32 + lane] = da;
+        __syncwarp();
+        for (int f = lane; f < F; f += 32) {          // beta += sum_a dalpha_a z_{v_a}
+            double acc = beta[f];
+            for (int q = 0; q < n; ++q) acc = fma(rf->sh[32 + q], Zp[(int64_t)rf->vsh[q] * F + f], acc);
+            beta[f] = acc;
+        }
+        __syncwarp();
+        fin = __all_sync(0xffffffffu, !act || finite_bits(al)) && finite_bits(b);
+    }
     if (act) coef[1 + lane] = al;
     if (lane == 0) coef[0] = b;
     __syncwarp();
     if (!fin) return RS_FIT_NONFINITE;
-    if (pt) {                                 // predictions, one candidate row per lane
+    if (pt && rf) {                           // predictions through Z: b + z_t . beta
+        for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
+            const int t = __ffsll((long long)cm) - 1;
+            double part = 0.0;
+            for (int f = lane; f < rf->F; f += 32) part = fma(rf->Zp[(int64_t)t * rf->F + f], rf->beta[f], part);
+            part = warp_sum(part);
+            if (lane == 0) {
+                const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+                if (r < pt->room) pt->dst[r] = b + part;
+            }
+        }
+        __syncwarp();
+    } else if (pt) {                          // predictions, one candidate row per lane
         const int nc = __popcll(pt->cand);
         for (int r0 = 0; r0 < nc; r0 += 32) {
             const bool mine = r0 + lane < nc;
@@ -624,16 +711,22 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
 
 constexpr int kLargeWarps = 4;
 
+// Dynamic shared memory: Lsh [4][32*33] doubles, then with refinement per warp: beta [Fmax],
+// coefficients [64] doubles, pair slots [32] ints.
 __global__ void __launch_bounds__(kLargeWarps * 32)
 solve_large_kernel(const SolveArgs a) {
     __shared__ long long start[kHist], cstart[kHist];
-    __shared__ double Lsh[kLargeWarps][32 * 33];
+    extern __shared__ __align__(16) double dsm[];
+    double* Lall = dsm;
     bucket_tables(a.hist, start, cstart);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long first = start[kNReg + 1], end = start[RS_MAXPAIRS + 1];
+    double* Lsh = Lall + warp * 32 * 33;
+    const bool refine = (a.flags & RS_REFINE_X) != 0;
+    double* rbase = Lall + kLargeWarps * 32 * 33 + (int64_t)warp * (a.max_feat + 64 + 16);
+    const long long first = refine ? start[1] : start[kNReg + 1], end = start[RS_MAXPAIRS + 1];
     for (long long pos = first + (long long)blockIdx.x * kLargeWarps + warp; pos < end;
          pos += (long long)gridDim.x * kLargeWarps) {
-        int n = kNReg + 1;
+        int n = 1;
         while (start[n + 1] <= pos) ++n;
         const int64_t f = a.order[pos];
         const int64_t s = f / RS_NOPT;
@@ -644,8 +737,16 @@ solve_large_kernel(const SolveArgs a) {
         double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
         PredTarget ptv;
         const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
+        RefineCtx rc;
+        if (refine) {
+            rc.Zp = a.Z + a.x_offsets[p];
+            rc.F = a.feat_width[p];
+            rc.beta = rbase;
+            rc.sh = rbase + a.max_feat;
+            rc.vsh = reinterpret_cast<int*>(rbase + a.max_feat + 64);
+        }
         const int st = fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
-                                a.lambda, Lsh[warp], out, pt);
+                                a.lambda, Lsh, out, pt, refine ? &rc : nullptr);
         if (lane == 0) finish_record(a, f, n, st, out);
         if (a.counters && lane == 0) atomicAdd(a.counters + (st == RS_FIT_OK ? 9 : st == RS_FIT_NOTPD ? 11 : 12), 1ull);
         __syncwarp();
@@ -1240,15 +1341,22 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
-                 a.rows_cap, a.flags, a.dstatus};
+                 a.rows_cap, a.flags, a.dstatus, a.Z, a.x_offsets, a.feat_width, a.max_feat};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = launch_small<1, 6, 4>(sa, sms, S6, st);
-    if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, st);
-    if (e != cudaSuccess) return e;
+    const bool refine = (a.flags & RS_REFINE_X) != 0;
+    if (!refine) {
+        e = launch_small<1, 6, 4>(sa, sms, S6, st);
+        if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, st);
+        if (e != cudaSuccess) return e;
+    }
     mark(4);
-    solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, 0, st>>>(sa);
+    const size_t lsmem = (size_t)kLargeWarps * 32 * 33 * sizeof(double) +
+                         (refine ? (size_t)kLargeWarps * (a.max_feat + 64 + 16) * sizeof(double) : 0);
+    e = cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+    if (e != cudaSuccess) return e;
+    solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, lsmem, st>>>(sa);
     mark(5);
     if (rank) {
         RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.train_masks, a.S,

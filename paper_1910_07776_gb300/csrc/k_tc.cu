@@ -49,6 +49,22 @@ cudaError_t rs_make_tmap_bf16(CUtensorMap* map, const void* ptr, int64_t rows, i
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t rs_make_tmap_bf16_3d(CUtensorMap* map, const void* ptr, int64_t batch, int64_t rows, int64_t cols,
+                                 int64_t ld, int box_rows) {
+    std::call_once(g_encode_once, load_encode);
+    if (!g_encode) return cudaErrorNotSupported;
+    if (batch < 1 || rows < 1 || cols < 1 || ld < cols || (ld * 2) % 16 != 0 || ((uintptr_t)ptr % 16) != 0)
+        return cudaErrorInvalidValue;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(rows * ld * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int BN>
 static cudaError_t launch_store(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, float* D,
                                 int64_t ldd, int* err, cudaStream_t st) {

@@ -179,17 +179,30 @@ rs_status rs_standardize(rs_ctx* c, const rs_batch* b, double* Z, double* mu, do
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_standardize");
 }
 
-rs_status rs_gram(rs_ctx* c, const rs_batch* b, int precision, double* K) {
+size_t rs_gram_workspace_bytes(const rs_batch* b, int precision) {
+    if (!b || b->n_programs < 1 || b->max_feat < 1) return 0;
+    return precision == RS_GRAM_BF16X3 ? rs_gram_tc_workspace_bytes(b->n_programs, b->max_feat) : 0;
+}
+
+rs_status rs_gram(rs_ctx* c, const rs_batch* b, int precision, double* K, void* ws, size_t ws_bytes) {
     if (!c) return RS_EINVAL;
     rs_status s = check_batch(c, b, false);
     if (s != RS_OK) return s;
     if (!K) return fail(c, RS_EINVAL, "K is NULL");
     cudaSetDevice(c->device);
     cudaError_t e;
-    if (precision == RS_GRAM_F64) e = rs_launch_gram_f64(b, K, c->dstatus, c->stream);
-    else if (precision == RS_GRAM_BF16X3) e = rs_launch_gram_bf16x3(b, K, c->dstatus, c->stream);
-    else return fail(c, RS_EINVAL, "precision must be RS_GRAM_F64 or RS_GRAM_BF16X3");
-    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "rs_gram: precision not built");
+    if (precision == RS_GRAM_F64) {
+        e = rs_launch_gram_f64(b, K, c->dstatus, c->stream);
+    } else if (precision == RS_GRAM_BF16X3) {
+        const size_t need = rs_gram_workspace_bytes(b, precision);
+        if (!ws || ws_bytes < need) return fail(c, RS_ENOMEM, "the tensor-core Gram needs %zu bytes of workspace", need);
+        if ((uintptr_t)ws % 256) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
+        if (b->n_programs > 65535) return fail(c, RS_EINVAL, "the tensor-core Gram takes at most 65535 programs per call");
+        e = rs_launch_gram_bf16x3_ws(b, K, ws, ws_bytes, c->dstatus, c->stream);
+    } else {
+        return fail(c, RS_EINVAL, "precision must be RS_GRAM_F64 or RS_GRAM_BF16X3");
+    }
+    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "rs_gram: cuTensorMapEncodeTiled unavailable");
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_gram");
 }
 
@@ -230,6 +243,7 @@ static rs_status fit_common(rs_ctx* c, const rs_batch* b, const double* K, const
     a.train_masks = sp->train_masks;
     a.lambda = lambda;
     a.form = form;
+    a.max_feat = b->max_feat;
     a.dstatus = c->dstatus;
     a.queue = (unsigned int*)(c->dstatus + RS_DST_QUEUE);
     a.ev = c->profiling ? c->ev : nullptr;
@@ -295,7 +309,9 @@ rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const r
     if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
     if (flags & ~(RS_RANK_ALL | RS_REFINE_X)) return fail(c, RS_EINVAL, "unknown flag bits");
-    if (flags & RS_REFINE_X) return fail(c, RS_EUNSUPPORTED, "RS_REFINE_X is not built");
+    if ((flags & RS_REFINE_X) && (form != RS_FORM_BATCHED || coef))
+        return fail(c, RS_EINVAL, "RS_REFINE_X needs the batched form and refits in the call (coef = NULL)");
+    if ((flags & RS_REFINE_X) && b->max_feat > 4096) return fail(c, RS_EINVAL, "RS_REFINE_X: max_feat <= 4096");
     if (!rec_offsets || !rec_code) return fail(c, RS_EINVAL, "rec_offsets and rec_code are required");
     a.coef_in = coef;
     a.k = k;
@@ -380,7 +396,9 @@ size_t rs_cv_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
     if (!b || !sp || b->n_programs < 1 || b->x_elems < 0) return 0;
     size_t z = align256((size_t)b->x_elems * sizeof(double));
     size_t k = align256((size_t)b->n_programs * RS_GRAM_LD * RS_GRAM_LD * sizeof(double));
-    return z + k + align256(rs_fit_workspace_bytes(b, sp));
+    size_t f = align256(rs_fit_workspace_bytes(b, sp));
+    size_t g = align256(rs_gram_workspace_bytes(b, RS_GRAM_BF16X3));
+    return z + k + (f > g ? f : g);     // the Gram's scratch is free again when the fits start
 }
 
 rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double lambda, int k,
@@ -406,7 +424,7 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
     rs_batch zb = *b;
     zb.X = Z;
     zb.dtype = RS_F64;
-    s = rs_gram(c, &zb, precision, K);
+    s = rs_gram(c, &zb, precision, K, fws, ws_bytes - zbytes - kbytes);
     if (s != RS_OK) return s;
     s = rs_rec_offsets(c, &zb, sp, rec_offsets);
     if (s != RS_OK) return s;

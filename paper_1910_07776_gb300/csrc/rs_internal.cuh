@@ -39,7 +39,9 @@ __device__ __forceinline__ uint64_t rs_full_mask(int V) {
 cudaError_t rs_launch_standardize(const rs_batch* b, double* Z, double* mu, double* sigma,
                                   int* dstatus, cudaStream_t st);
 cudaError_t rs_launch_gram_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st);
-cudaError_t rs_launch_gram_bf16x3(const rs_batch* b, double* K, int* dstatus, cudaStream_t st);
+size_t rs_gram_tc_workspace_bytes(int64_t P, int max_feat);
+cudaError_t rs_launch_gram_bf16x3_ws(const rs_batch* b, double* K, void* ws, size_t ws_bytes, int* dstatus,
+                                     cudaStream_t st);
 cudaError_t rs_launch_rec_offsets(const rs_batch* b, const rs_splits* s, int64_t* rec_offsets,
                                   int64_t* scratch_blocksums, int* dstatus, cudaStream_t st);
 size_t rs_rec_offsets_scratch_elems(int64_t n_splits);
@@ -77,6 +79,7 @@ struct rs_fit_args {
     unsigned int* queue;          // persistent work queue head (zeroed before launch)
     // batched form only
     int max_train;                // host bound on popcount(train mask)
+    int max_feat;                 // host bound on F_p (refinement buffers)
     int64_t rows_cap;             // rows of the prediction buffer (>= rec_offsets[S])
     void* workspace;
     size_t workspace_bytes;

@@ -72,6 +72,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         ::"r"(dst), "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
         : "memory");
 }
+// 3-D tile load: x = K coordinate, y = row within the matrix, z = batch index.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(dst), "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
                  : "memory");
@@ -139,7 +146,9 @@ struct Layout {
 
 // Epi: __device__ void operator()(int row, int col0, const float (&v)[16]) const; called for
 // every row < M of the tile with the 16 accumulator columns starting at col0 (col0 < N).
-template <int BN, int STAGES, class Epi>
+// BATCHED: the operands are rank-3 tensor maps [batch][rows][K]; CTA z works on batch z and
+// the epilogue is called as epi(z, row, col0, v).
+template <int BN, int STAGES, class Epi, bool BATCHED = false>
 __global__ void __launch_bounds__(128, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
             int K, Epi epi, int* err) {
@@ -180,11 +189,19 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
         const uint32_t idesc = idesc_bf16(BM, BN);
         const int pre = nk < STAGES ? nk : STAGES;
         int issued = 0, consumed = 0;
+        auto load = [&](int kb, uint32_t a, uint32_t b, uint32_t bar) {
+            mbar_expect_tx(bar, L::kStage);
+            if (BATCHED) {
+                tma_load_3d(a, &ta, bar, kb * BK, m0, blockIdx.z);
+                tma_load_3d(b, &tb, bar, kb * BK, n0, blockIdx.z);
+            } else {
+                tma_load_2d(a, &ta, bar, kb * BK, m0);
+                tma_load_2d(b, &tb, bar, kb * BK, n0);
+            }
+        };
         for (int kb = 0; kb < pre; ++kb, ++issued) {
             const uint32_t a = base + kb * L::kStage, b = a + L::kA;
-            mbar_expect_tx(full(kb), L::kStage);
-            tma_load_2d(a, &ta, full(kb), kb * BK, m0);
-            tma_load_2d(b, &tb, full(kb), kb * BK, n0);
+            load(kb, a, b, full(kb));
         }
         for (int kb = 0; kb < nk && ok; ++kb) {
             const int s = kb % STAGES;
@@ -204,9 +221,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
                 ok = mbar_wait(empty(sp), ((kb - 1) / STAGES) & 1, err, 2);
                 if (!ok) break;
                 const uint32_t a2 = base + sp * L::kStage, b2 = a2 + L::kA;
-                mbar_expect_tx(full(sp), L::kStage);
-                tma_load_2d(a2, &ta, full(sp), kr * BK, m0);
-                tma_load_2d(b2, &tb, full(sp), kr * BK, n0);
+                load(kr, a2, b2, full(sp));
                 ++issued;
             }
         }
@@ -225,7 +240,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
             if (n0 + c >= N) break;                  // warp-uniform
             float v[16];
             tmem_ld16(trow + (uint32_t)c, v);
-            if (row < M) epi(row, n0 + c, v);
+            if (row < M) {
+                if constexpr (BATCHED) epi((int)blockIdx.z, row, n0 + c, v);
+                else epi(row, n0 + c, v);
+            }
         }
     }
     fence_before();
@@ -241,3 +259,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
 // Returns cudaErrorInvalidValue for shapes TMA cannot describe (ld * 2 not a multiple of 16).
 cudaError_t rs_make_tmap_bf16(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld,
                               int box_rows);
+// Rank-3 variant over [batch][rows][cols] (row stride ld, batch stride rows * ld elements):
+// box = 64 columns x box_rows rows x 1 batch; rows beyond `rows` read as zero.
+cudaError_t rs_make_tmap_bf16_3d(CUtensorMap* map, const void* ptr, int64_t batch, int64_t rows, int64_t cols,
+                                 int64_t ld, int box_rows);

@@ -30,7 +30,7 @@ NCOUNTERS = 16
 # every symbol include/rs.h declares (tests check that the library exports all of them)
 EXPORTS = [
     "rs_create", "rs_destroy", "rs_set_stream", "rs_last_error", "rs_check_device_status",
-    "rs_standardize", "rs_gram", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
+    "rs_standardize", "rs_gram", "rs_gram_workspace_bytes", "rs_rec_offsets", "rs_fit_batched", "rs_predict_rank",
     "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak", "rs_fit_workspace_bytes",
     "rs_profile_enable", "rs_profile_read", "rs_cv_step_static", "rs_gemm_bf16",
     "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
@@ -87,7 +87,9 @@ def load(path: str = SO):
     L.rs_last_error.restype = C.c_char_p
     L.rs_check_device_status.argtypes = [P]
     L.rs_standardize.argtypes = [P, P, P, P, P]
-    L.rs_gram.argtypes = [P, P, i, P]
+    L.rs_gram.argtypes = [P, P, i, P, P, C.c_size_t]
+    L.rs_gram_workspace_bytes.argtypes = [P, i]
+    L.rs_gram_workspace_bytes.restype = C.c_size_t
     L.rs_rec_offsets.argtypes = [P, P, P, P]
     L.rs_fit_batched.argtypes = [P, P, P, P, d, i, P, C.c_size_t, P, P]
     L.rs_predict_rank.argtypes = [P, P, P, P, d, P, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
@@ -110,7 +112,7 @@ def load(path: str = SO):
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     for name in EXPORTS:
-        if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes",
+        if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes", "rs_gram_workspace_bytes",
                         "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
@@ -279,11 +281,15 @@ class Context:
         self._check(self.L.rs_standardize(self.h, C.byref(bc), _ptr(Z), _ptr(mu), _ptr(sigma)))
         return Z
 
-    def gram(self, zb: DeviceBatch, precision: int = RS_GRAM_F64, K=None):
+    def gram(self, zb: DeviceBatch, precision: int = RS_GRAM_F64, K=None, workspace=None):
         if K is None:
             K = torch.zeros(zb.n_programs * GRAM_LD * GRAM_LD, dtype=torch.float64, device=zb.X.device)
         bc = zb.c()
-        self._check(self.L.rs_gram(self.h, C.byref(bc), precision, _ptr(K)))
+        need = int(self.L.rs_gram_workspace_bytes(C.byref(bc), precision))
+        if workspace is None and need:
+            workspace = self.workspace(need)
+        wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
+        self._check(self.L.rs_gram(self.h, C.byref(bc), precision, _ptr(K), _ptr(workspace), wsb))
         return K
 
     def rec_offsets(self, b: DeviceBatch, s: DeviceSplits, out=None):
