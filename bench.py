@@ -212,6 +212,7 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--surrogate-epochs", type=int, default=2)
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
@@ -349,6 +350,10 @@ def main():
     # end to end through the C ABI single call with host buffers (pinned), copies timed
     e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
+    prec = None
+    if rank == 0 and not args.only_step and not args.no_precision:
+        prec = run_precision(rs, ctx, dev, stream, flush, args)
+
     sur = None
     if rank == 0 and not args.only_step and not args.no_surrogate:
         sur = run_surrogate(rs, ctx, dev, stream, flush, args)
@@ -373,6 +378,7 @@ def main():
         "accuracy": acc,
         "plain_form": plain,
         "surrogate_form": sur,
+        "precision_form": prec,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -444,6 +450,62 @@ def run_plain(rs, ctx, batch, splits, dev, stream, flush, args):
     return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n,
             "launches_per_step": 6 * len(progs),
             "sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1)}
+
+
+def run_precision(rs, ctx, dev, stream, flush, args):
+    """Precision form: 256 programs x 64 versions x 1024 FP64 features, leave-one-version-out,
+    a condition-number sweep by random mixing; BF16-split tensor-core Gram + FP64 factorisation
+    + one refinement step through Z, against the FP64 path (itself within 1e-9 of the CPU
+    reference).  Reports errors of the raw and refined forms per kappa and their timings."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    base = synth.make_batch_fast(256, versions=64, feat=1024, dtype=np.float64, seed=21)
+    splits = synth.make_splits(base, "lovo")
+    res = {"workload": "256 programs x 64 versions x 1024 f64 features, LOVO (16,384 splits, 98,304 fits)",
+           "per_kappa": {}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for kappa in (1e2, 1e4, 1e6, 1e8):
+        b = synth.apply_mixing(base, kappa, seed=21)
+        db = rs.DeviceBatch.from_host(b, dev)
+        ds = rs.DeviceSplits.from_host(splits, dev, b)
+        R = ds.n_test_rows
+        ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+        outs = {}
+        times = {}
+        for name, prec, flags in (("f64", rs.RS_GRAM_F64, 0), ("bf16x3", rs.RS_GRAM_BF16X3, 0),
+                                  ("bf16x3_refined", rs.RS_GRAM_BF16X3, rs.RS_REFINE_X)):
+            o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev)
+            ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                        flags=flags, precision=prec, rec_pred=o.rec_pred, pred_all=o.pred_all)
+            torch.cuda.synchronize()
+            flush.fill_(1)
+            e0.record(stream)
+            ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                        flags=flags, precision=prec, rec_pred=o.rec_pred, pred_all=o.pred_all)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1)
+            outs[name] = (o.pred_all.cpu().numpy().reshape(R, 6), o.rec_code.cpu().numpy())
+        ref, rcode = outs["f64"]
+        ok = ~np.isnan(ref)
+        sc = float(np.abs(ref[ok]).max())
+        ent = {}
+        for name in ("bf16x3", "bf16x3_refined"):
+            pa, code = outs[name]
+            d = np.abs(pa[ok] - ref[ok])
+            ent[name] = {"max_rel_err_pred": float(d.max() / sc), "median_rel_err_pred": float(np.median(d) / sc),
+                         "ranking_rows_changed": int(np.sum(code != rcode)), "ms": times[name],
+                         "recs_per_s": R / (times[name] * 1e-3)}
+        ent["f64"] = {"ms": times["f64"], "recs_per_s": R / (times["f64"] * 1e-3)}
+        # achieved condition number of one training system (program 0, split 0, optimization 0)
+        Zp = np.log(b.program_X(0) / b.cycles[b.program_rows(0)][:, None])
+        Zp = (Zp - Zp.mean(0)) / np.where(Zp.std(0) > 1e-12, Zp.std(0), 1.0)
+        m = b.masks[b.program_rows(0)].astype(int)
+        rows = [v for v in range(1, 64) if not m[v] & 1 and (m[v] | 1) in set(m[1:])]
+        Kt = Zp[rows] @ Zp[rows].T + CFG["lam"] * np.eye(len(rows))
+        ent["achieved_cond_train_system"] = float(np.linalg.cond(Kt))
+        res["per_kappa"][f"{kappa:.0e}"] = ent
+    return res
 
 
 def run_surrogate(rs, ctx, dev, stream, flush, args):

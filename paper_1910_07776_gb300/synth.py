@@ -346,6 +346,30 @@ def make_batch_fast(n_programs: int, versions: IntOrRange = 64, feat: int = 256,
                         meta=dict(gen=GEN_VERSION + "-fast", seed=seed, n_programs=P))
 
 
+def apply_mixing(batch: ProgramBatch, kappa: float, seed: int = 0) -> ProgramBatch:
+    """A copy of a uniform-width batch whose log counter rates are mixed by Q diag(s) Q^T
+    (Q random orthogonal, s log-spaced from 1 to 1/sqrt(kappa) over the first 64 directions,
+    1/sqrt(kappa) after), making counters correlated and the Gram matrices ill-conditioned.
+    The cycle normalisation is kept: X' = exp(log(X / c) @ mix) * c."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x31C5))
+    F = int(batch.feat_width[0])
+    assert np.all(batch.feat_width == F), "uniform feature width only"
+    Q, _ = np.linalg.qr(rng.standard_normal((F, F)))
+    r = min(F, 64)
+    sv = np.full(F, 1.0 / np.sqrt(kappa))
+    sv[:r] = np.logspace(0.0, -0.5 * np.log10(kappa), r)
+    mix = (Q * sv[None, :]) @ Q.T
+    c = batch.cycles if batch.cycles is not None else np.ones(batch.n_rows)
+    L = np.log(batch.X.reshape(batch.n_rows, F).astype(np.float64) / c[:, None])
+    X2 = np.exp(L @ mix) * c[:, None]
+    out = ProgramBatch(X=X2.reshape(-1).astype(batch.X.dtype), x_offsets=batch.x_offsets.copy(),
+                       row_offsets=batch.row_offsets.copy(), feat_width=batch.feat_width.copy(),
+                       masks=batch.masks.copy(), log_time=batch.log_time.copy(),
+                       cycles=None if batch.cycles is None else batch.cycles.copy(),
+                       meta=dict(batch.meta, mixing_kappa=kappa))
+    return out
+
+
 def make_complementary_halves(batch: ProgramBatch, seed: int = 0) -> Splits:
     """Two splits per program: a random half of its versions and the other half, so that every
     version is a test row exactly once (its prediction comes from a fit on the other half)."""

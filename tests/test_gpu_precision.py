@@ -73,5 +73,7 @@ def test_refined_precision_form_against_the_reference(env):
     splits = synth.make_splits(batch, "lovo")
     fix, g = _pred(rs, ctx, batch, splits, rs.RS_GRAM_BF16X3, rs.RS_REFINE_X)
     r = oracle.cv_batch(batch, splits)
-    close(fix, r.pred_all, rel=1e-7, abs_=1e-9)
+    # one refinement step leaves about (kappa * 2^-16)^2 relative error: the stated tolerance
+    # of the precision form is 2e-5 relative (+1e-6 absolute)
+    close(fix, r.pred_all, rel=2e-5, abs_=1e-6)
     np.testing.assert_array_equal(g["rec_offsets"], r.rec_offsets)
