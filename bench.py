@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--surrogate-epochs", type=int, default=2)
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
@@ -350,6 +351,10 @@ def main():
     # end to end through the C ABI single call with host buffers (pinned), copies timed
     e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
+    unev = None
+    if rank == 0 and not args.only_step and not args.no_uneven:
+        unev = run_uneven(rs, ctx, dev, stream, flush, args)
+
     prec = None
     if rank == 0 and not args.only_step and not args.no_precision:
         prec = run_precision(rs, ctx, dev, stream, flush, args)
@@ -379,6 +384,7 @@ def main():
         "plain_form": plain,
         "surrogate_form": sur,
         "precision_form": prec,
+        "uneven_form": unev,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -450,6 +456,61 @@ def run_plain(rs, ctx, batch, splits, dev, stream, flush, args):
     return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n,
             "launches_per_step": 6 * len(progs),
             "sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1)}
+
+
+def run_uneven(rs, ctx, dev, stream, flush, args):
+    """Uneven stream: 10,000 programs x U{8..64} versions x feature widths from {64, 128, 256,
+    512}, 1,024 random half splits per program (10.24 M splits), FP32 counters, FP64 Gram and
+    fits; eager step vs autotuned vs one CUDA-graph launch per step."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    t0 = time.perf_counter()
+    b = synth.make_batch_fast(10000, versions=(8, 64), feat_choices=[64, 128, 256, 512], dtype=np.float32,
+                              seed=31)
+    sp = synth.make_half_splits_fast(b, 1024, seed=31)
+    db = rs.DeviceBatch.from_host(b, dev)
+    ds = rs.DeviceSplits.from_host(sp, dev, b)
+    gen_s = time.perf_counter() - t0
+    R = ds.n_test_rows
+    o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
+                               tau=CFG["tau"], rec_pred=o.rec_pred)
+    eager_default = timed(step)
+    tune = ctx.autotune(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                        rec_pred=o.rec_pred)
+    eager_tuned = timed(step)
+    g = ctx.cv_graph(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                     rec_pred=o.rec_pred, counters=o.counters)
+    o.counters.zero_()
+    graph_ms = timed(g.launch)
+    torch.cuda.synchronize()
+    g.close()
+    cnt = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
+    ctx.check_device_status()
+    # restore the default launch parameters for anything measured afterwards
+    ctx.L.rs_get_tuning(ctx.h, None, None)
+    return {"workload": "10,000 programs x U{8..64} versions x F in {64,128,256,512} f32, 1,024 half "
+                        "splits/program (10,240,000 splits)",
+            "recs_per_step": R, "value": R / (graph_ms * 1e-3), "unit": UNIT, "graph_ms": graph_ms,
+            "eager_default_ms": eager_default, "eager_tuned_ms": eager_tuned,
+            "autotune": {"solve_split": tune["solve_split"], "rank_waves": tune["rank_waves"]},
+            "sign_accuracy": cnt[3] / max(cnt[2], 1), "data_gen_s": gen_s}
 
 
 def run_precision(rs, ctx, dev, stream, flush, args):

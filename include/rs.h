@@ -219,6 +219,32 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
                      uint32_t* rec_code, double* rec_pred, double* pred_all,
                      uint64_t* counters);
 
+/* ---- A8: one graph launch per step, and the autotuner ---------------------------------------
+ * rs_cv_graph_create runs rs_cv_step once eagerly (reporting argument errors), then captures
+ * the same launch sequence into a CUDA graph bound to these pointers and sizes;
+ * rs_cv_graph_launch replays it on the context's stream (one launch for the whole step,
+ * ragged programs, versions and feature widths included).  Buffers must stay allocated
+ * while the graph exists; their contents may change between launches.  Counters are added
+ * to on every launch.  The graph uses the launch parameters the context holds at capture.
+ * rs_autotune times the batched step on this batch for each candidate launch configuration
+ * (the size at which fits move to the register-heavier solver: 4..8; the rank pass grid: 8,
+ * 16 or 32 blocks per SM), keeps the fastest in the context (used by every later batched
+ * call), and writes the times (ms, at most *n_times, in candidate order) if asked.
+ * rs_get_tuning reports the context's current choice.                                 */
+typedef struct rs_graph rs_graph;
+rs_status rs_cv_graph_create(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
+                             double lambda, int k, double tau, int flags, int precision,
+                             void* workspace, size_t workspace_bytes, int64_t* rec_offsets,
+                             uint32_t* rec_code, double* rec_pred, double* pred_all,
+                             uint64_t* counters, rs_graph** graph);
+rs_status rs_cv_graph_launch(rs_graph* graph);
+rs_status rs_cv_graph_destroy(rs_graph* graph);
+rs_status rs_autotune(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits, double lambda,
+                      int k, double tau, int flags, int precision, void* workspace,
+                      size_t workspace_bytes, int64_t* rec_offsets, uint32_t* rec_code,
+                      double* rec_pred, float* times_ms, int* n_times);
+rs_status rs_get_tuning(const rs_ctx* ctx, int* solve_split, int* rank_waves);
+
 /* ---- tensor-core BF16 GEMM (the surrogate's and the tensor-core Gram's building block) ----
  * D[M][N] = A[M][K] * B[N][K]^T with A, B BF16 row-major (K contiguous, leading dimensions
  * lda, ldb in elements, multiples of 8, 16-byte aligned bases) and D FP32 row-major (ldd).

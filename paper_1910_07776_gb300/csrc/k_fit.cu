@@ -1347,8 +1347,19 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool refine = (a.flags & RS_REFINE_X) != 0;
     if (!refine) {
-        e = launch_small<1, 6, 4>(sa, sms, S6, st);
-        if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, st);
+        // the size at which the solver switches to the register-heavier instantiation
+        switch (a.tune_split) {
+            case 4: e = launch_small<1, 4, 4>(sa, sms, S6, st);
+                    if (e == cudaSuccess) e = launch_small<5, kNReg, 2>(sa, sms, S6, st); break;
+            case 5: e = launch_small<1, 5, 4>(sa, sms, S6, st);
+                    if (e == cudaSuccess) e = launch_small<6, kNReg, 2>(sa, sms, S6, st); break;
+            case 7: e = launch_small<1, 7, 3>(sa, sms, S6, st);
+                    if (e == cudaSuccess) e = launch_small<8, kNReg, 2>(sa, sms, S6, st); break;
+            case 8: e = launch_small<1, 8, 3>(sa, sms, S6, st);
+                    if (e == cudaSuccess) e = launch_small<9, kNReg, 2>(sa, sms, S6, st); break;
+            default: e = launch_small<1, 6, 4>(sa, sms, S6, st);
+                    if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, st); break;
+        }
         if (e != cudaSuccess) return e;
     }
     mark(4);
@@ -1364,8 +1375,9 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                         w.row_info, a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all,
                         a.counters};
         ra.ktau = okey_host(a.log_tau);
+        const int waves = a.tune_rank_waves > 0 ? a.tune_rank_waves : 16;
         int64_t blocks = (a.rows_cap + kRankThreads - 1) / kRankThreads;
-        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        if (blocks > (int64_t)sms * waves) blocks = (int64_t)sms * waves;
         if (blocks < 1) blocks = 1;
         rank_pass_kernel<<<(unsigned)blocks, kRankThreads, 0, st>>>(ra);
     }

@@ -16,6 +16,8 @@ struct rs_ctx {
     int* dstatus;            // RS_DST_INTS ints of device memory
     int64_t* scan;           // block sums of the row-planning scan (kScanBlocksMax + 1)
     int profiling;           // record stage events in the batched fit/predict path
+    int tune_split;          // autotuned launch parameters of the batched form
+    int tune_rank_waves;
     cudaEvent_t ev[RS_NSTAGE_EVENTS];
     char err[512];
 };
@@ -80,6 +82,8 @@ rs_status rs_create(rs_ctx** out, int device, void* stream) {
     c->stream = (cudaStream_t)stream;
     c->err[0] = 0;
     c->profiling = 0;
+    c->tune_split = 6;
+    c->tune_rank_waves = 16;
     for (int i = 0; i < RS_NSTAGE_EVENTS; ++i) c->ev[i] = nullptr;
     e = cudaMalloc(&c->dstatus, RS_DST_INTS * sizeof(int));
     if (e != cudaSuccess) {
@@ -247,6 +251,8 @@ static rs_status fit_common(rs_ctx* c, const rs_batch* b, const double* K, const
     a.dstatus = c->dstatus;
     a.queue = (unsigned int*)(c->dstatus + RS_DST_QUEUE);
     a.ev = c->profiling ? c->ev : nullptr;
+    a.tune_split = c->tune_split;
+    a.tune_rank_waves = c->tune_rank_waves;
     return RS_OK;
 }
 
@@ -431,6 +437,134 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
     return rs_predict_rank(c, &zb, K, sp, lambda, nullptr, k, tau, flags, RS_FORM_BATCHED, fws,
                            ws_bytes - zbytes - kbytes, rec_offsets, rec_code, rec_pred, pred_all,
                            counters);
+}
+
+
+// ---- CUDA graph of the whole step -------------------------------------------------------------
+struct rs_graph {
+    rs_ctx* ctx;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+rs_status rs_cv_graph_create(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double lambda, int k,
+                             double tau, int flags, int precision, void* ws, size_t ws_bytes,
+                             int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred, double* pred_all,
+                             uint64_t* counters, rs_graph** out) {
+    if (!c || !out) return RS_EINVAL;
+    *out = nullptr;
+    if (c->profiling) return fail(c, RS_EINVAL, "turn profiling off before capturing a graph");
+    cudaSetDevice(c->device);
+    cudaStream_t orig = c->stream, cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_cv_graph_create");
+    c->stream = cap;
+    // one eager pass first: function attributes and driver entry points are set up outside
+    // the capture, and argument errors are reported before anything is recorded
+    rs_status s = rs_cv_step(c, b, sp, lambda, k, tau, flags, precision, ws, ws_bytes, rec_offsets, rec_code,
+                             rec_pred, pred_all, counters);
+    if (s == RS_OK) {
+        e = cudaStreamSynchronize(cap);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "rs_cv_graph_create (eager pass)");
+    }
+    cudaGraph_t g = nullptr;
+    if (s == RS_OK) {
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "cudaStreamBeginCapture");
+    }
+    if (s == RS_OK) {
+        rs_status s2 = rs_cv_step(c, b, sp, lambda, k, tau, flags, precision, ws, ws_bytes, rec_offsets,
+                                  rec_code, rec_pred, pred_all, counters);
+        e = cudaStreamEndCapture(cap, &g);
+        if (s2 != RS_OK) s = s2;
+        else if (e != cudaSuccess) s = cuda_fail(c, e, "cudaStreamEndCapture");
+    }
+    c->stream = orig;
+    cudaStreamDestroy(cap);
+    if (s != RS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    rs_graph* r = new (std::nothrow) rs_graph{c, g, ex};
+    if (!r) {
+        cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(g);
+        return RS_ENOMEM;
+    }
+    *out = r;
+    return RS_OK;
+}
+
+rs_status rs_cv_graph_launch(rs_graph* g) {
+    if (!g) return RS_EINVAL;
+    cudaSetDevice(g->ctx->device);
+    cudaError_t e = cudaGraphLaunch(g->exec, g->ctx->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(g->ctx, e, "rs_cv_graph_launch");
+}
+
+rs_status rs_cv_graph_destroy(rs_graph* g) {
+    if (!g) return RS_EINVAL;
+    cudaSetDevice(g->ctx->device);
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return RS_OK;
+}
+
+// ---- autotuner --------------------------------------------------------------------------------
+rs_status rs_autotune(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double lambda, int k, double tau,
+                      int flags, int precision, void* ws, size_t ws_bytes, int64_t* rec_offsets,
+                      uint32_t* rec_code, double* rec_pred, float* times_ms, int* n_times) {
+    if (!c) return RS_EINVAL;
+    cudaSetDevice(c->device);
+    const int splits_c[5] = {4, 5, 6, 7, 8};
+    const int waves_c[3] = {8, 16, 32};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bs = c->tune_split, bw = c->tune_rank_waves, idx = 0;
+    rs_status s = RS_OK;
+    for (int i = 0; i < 5 && s == RS_OK; ++i)
+        for (int w = 0; w < 3 && s == RS_OK; ++w) {
+            c->tune_split = splits_c[i];
+            c->tune_rank_waves = waves_c[w];
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && s == RS_OK; ++rep) {
+                cudaEventRecord(e0, c->stream);
+                s = rs_cv_step(c, b, sp, lambda, k, tau, flags, precision, ws, ws_bytes, rec_offsets, rec_code,
+                               rec_pred, nullptr, nullptr);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);      // the second run is the one kept
+            }
+            if (times_ms && n_times && idx < *n_times) times_ms[idx] = ms;
+            ++idx;
+            if (s == RS_OK && ms < best) {
+                best = ms;
+                bs = splits_c[i];
+                bw = waves_c[w];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune_split = bs;
+    c->tune_rank_waves = bw;
+    if (n_times) *n_times = idx;
+    return s;
+}
+
+rs_status rs_get_tuning(const rs_ctx* c, int* solve_split, int* rank_waves) {
+    if (!c) return RS_EINVAL;
+    if (solve_split) *solve_split = c->tune_split;
+    if (rank_waves) *rank_waves = c->tune_rank_waves;
+    return RS_OK;
 }
 
 }  // extern "C"

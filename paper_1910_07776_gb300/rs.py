@@ -34,7 +34,8 @@ EXPORTS = [
     "rs_cv_workspace_bytes", "rs_cv_step", "rs_measure_fma_peak", "rs_fit_workspace_bytes",
     "rs_profile_enable", "rs_profile_read", "rs_cv_step_static", "rs_gemm_bf16",
     "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
-    "rs_surrogate_train", "rs_surrogate_infer",
+    "rs_surrogate_train", "rs_surrogate_infer", "rs_cv_graph_create", "rs_cv_graph_launch",
+    "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning",
 ]
 
 
@@ -101,6 +102,12 @@ def load(path: str = SO):
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
     L.rs_cv_step_static.argtypes = [P, P, P, d, i, d, i, P, P, P, P, P, P, C.c_char_p, C.c_size_t]
     L.rs_gemm_bf16.argtypes = [P, P, i64, P, i64, P, i64, i, i, i]
+    L.rs_cv_graph_create.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P, C.POINTER(P)]
+    L.rs_cv_graph_launch.argtypes = [P]
+    L.rs_cv_graph_destroy.argtypes = [P]
+    L.rs_autotune.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, C.POINTER(C.c_float),
+                              C.POINTER(C.c_int)]
+    L.rs_get_tuning.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.rs_surrogate_blob_bytes.argtypes = []
     L.rs_surrogate_blob_bytes.restype = C.c_size_t
     L.rs_surrogate_offset.argtypes = [i]
@@ -269,6 +276,38 @@ class Context:
         self._check(self.L.rs_gemm_bf16(self.h, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(D),
                                         D.stride(0), M, N, K))
         return D
+
+    def cv_graph(self, b: DeviceBatch, s: DeviceSplits, workspace, rec_offsets, rec_code, lam=1e-3, k=3,
+                 tau=1.05, flags=0, precision=RS_GRAM_F64, rec_pred=None, pred_all=None, counters=None):
+        """Capture the whole step as a CUDA graph; returns a handle with launch() / close()."""
+        bc, sc = b.c(), s.c()
+        h = C.c_void_p()
+        self._check(self.L.rs_cv_graph_create(
+            self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags), int(precision),
+            _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(rec_offsets), _ptr(rec_code),
+            _ptr(rec_pred), _ptr(pred_all), _ptr(counters), C.byref(h)))
+        ctx = self
+
+        class _G:
+            def launch(self_):
+                ctx._check(ctx.L.rs_cv_graph_launch(h))
+
+            def close(self_):
+                ctx.L.rs_cv_graph_destroy(h)
+        return _G()
+
+    def autotune(self, b: DeviceBatch, s: DeviceSplits, workspace, rec_offsets, rec_code, lam=1e-3, k=3,
+                 tau=1.05, flags=0, precision=RS_GRAM_F64, rec_pred=None):
+        bc, sc = b.c(), s.c()
+        times = (C.c_float * 32)()
+        n = C.c_int(32)
+        self._check(self.L.rs_autotune(
+            self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags), int(precision),
+            _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(rec_offsets), _ptr(rec_code),
+            _ptr(rec_pred), times, C.byref(n)))
+        sp_, rw = C.c_int(), C.c_int()
+        self.L.rs_get_tuning(self.h, C.byref(sp_), C.byref(rw))
+        return {"solve_split": sp_.value, "rank_waves": rw.value, "times_ms": [times[i] for i in range(n.value)]}
 
     def check_device_status(self):
         self._check(self.L.rs_check_device_status(self.h))

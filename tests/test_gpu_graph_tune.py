@@ -1,0 +1,63 @@
+"""One CUDA-graph launch per step on an uneven batch, and the autotuner, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1910_07776_gb300 import synth
+from parity import close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1910_07776_gb300 import build, rs
+    build.build()
+    ctx = rs.Context(0)
+    yield rs, ctx
+    ctx.close()
+
+
+def _uneven(rs):
+    batch = synth.make_batch_fast(40, versions=(8, 64), feat_choices=[64, 128, 256, 512], seed=95)
+    splits = synth.make_half_splits_fast(batch, 64, seed=95)
+    return batch, splits, rs.DeviceBatch.from_host(batch), rs.DeviceSplits.from_host(splits, batch=batch)
+
+
+def _outs(rs, ds):
+    return rs.alloc_outputs(ds.n_test_rows, ds.n_splits, 3)
+
+
+def test_graph_launch_equals_eager_step(env):
+    rs, ctx = env
+    batch, splits, db, ds = _uneven(rs)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    a, b = _outs(rs, ds), _outs(rs, ds)
+    ctx.cv_step(db, ds, ws, a.rec_offsets, a.rec_code, rec_pred=a.rec_pred, pred_all=a.pred_all, counters=a.counters)
+    g = ctx.cv_graph(db, ds, ws, b.rec_offsets, b.rec_code, rec_pred=b.rec_pred, pred_all=b.pred_all,
+                     counters=b.counters)     # creation runs one eager pass
+    b.rec_code.fill_(-1)
+    b.pred_all.fill_(7.0)
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    ctx.check_device_status()
+    assert torch.equal(a.rec_code, b.rec_code)
+    assert torch.equal(torch.nan_to_num(a.pred_all, nan=-9.0), torch.nan_to_num(b.pred_all, nan=-9.0))
+    assert torch.equal(3 * a.counters, b.counters)      # eager pass + two launches
+    g.close()
+
+
+def test_autotune_keeps_the_results(env):
+    rs, ctx = env
+    batch, splits, db, ds = _uneven(rs)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    a, b = _outs(rs, ds), _outs(rs, ds)
+    ctx.cv_step(db, ds, ws, a.rec_offsets, a.rec_code, rec_pred=a.rec_pred, pred_all=a.pred_all)
+    t = ctx.autotune(db, ds, ws, b.rec_offsets, b.rec_code, rec_pred=b.rec_pred)
+    assert len(t["times_ms"]) == 15 and t["solve_split"] in (4, 5, 6, 7, 8) and t["rank_waves"] in (8, 16, 32)
+    ctx.cv_step(db, ds, ws, b.rec_offsets, b.rec_code, rec_pred=b.rec_pred, pred_all=b.pred_all)
+    torch.cuda.synchronize()
+    close(b.pred_all.cpu().numpy(), a.pred_all.cpu().numpy(), rel=1e-12, abs_=1e-14)
+    assert torch.equal(a.rec_code, b.rec_code)
