@@ -351,6 +351,7 @@ def main():
     # end to end through the C ABI single call with host buffers (pinned), copies timed
     e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
+    ctx.profile_enable(False)
     unev = None
     if rank == 0 and not args.only_step and not args.no_uneven:
         unev = run_uneven(rs, ctx, dev, stream, flush, args)
@@ -503,8 +504,6 @@ def run_uneven(rs, ctx, dev, stream, flush, args):
     g.close()
     cnt = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
     ctx.check_device_status()
-    # restore the default launch parameters for anything measured afterwards
-    ctx.L.rs_get_tuning(ctx.h, None, None)
     return {"workload": "10,000 programs x U{8..64} versions x F in {64,128,256,512} f32, 1,024 half "
                         "splits/program (10,240,000 splits)",
             "recs_per_step": R, "value": R / (graph_ms * 1e-3), "unit": UNIT, "graph_ms": graph_ms,
