@@ -32,6 +32,24 @@ CFG = dict(programs=64, versions=(16, 64), feat=256, splits=4096, lam=1e-3, k=3,
 FP64_PEAK_NOMINAL_GFLOPS = 152 * 4 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 
 
+def profiled_traffic(stage):
+    """DRAM bytes per step of a stage from the committed ncu summary, or None when the kernel
+    source has changed since the capture (its sha256 prefix is recorded in the summary)."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "batched_cv_kernels.md")).read()
+        src = open(os.path.join(ROOT, "paper_1910_07776_gb300", "csrc", "k_fit.cu"), "rb").read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    if f"source_sha256_prefix k_fit.cu = {sha}" not in txt:
+        return None
+    for line in txt.splitlines():
+        if line.startswith(f"traffic_bytes_per_step {stage} = "):
+            return float(line.split("=")[1].split()[0])
+    return None
+
+
 def measured_hbm_peak():
     """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the machine's fallback figure."""
     try:
@@ -322,13 +340,14 @@ def main():
     if top == "rank":
         achieved = work["rank_bytes"] / (stage_ms[top] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "rank_pass_kernel", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": profiled_traffic("rank"),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
                 "bytes_per_launch": work["rank_bytes"]}
     else:
         achieved = work[top] / (stage_ms[top] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "solve_" + top.split("_")[1] + "_kernel", "achieved": achieved,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": profiled_traffic(top) if top == "solve_small" else None,
                 "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
                 "flops_per_launch": work[top]}
     path_flops = work["solve_small"] + work["solve_large"]
