@@ -624,7 +624,7 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
     Xtr, Ytr = Zm[:n_tr], Y[:n_tr]
     Xte = Zm[n_tr:].contiguous()
     masks_te = db.masks[n_tr:].contiguous()
-    sur = rs.Surrogate(ctx, 8192)
+    sur = rs.Surrogate(ctx, 8192, infer_chunk=131072)
     sur.load(mlp.init_params(11))
     steps = args.surrogate_epochs * (n_tr // 8192)
     lc = torch.zeros(steps, device=dev)

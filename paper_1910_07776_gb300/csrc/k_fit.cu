@@ -215,17 +215,22 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         const int j = (int)(f - s * RS_NOPT);
         const int p = rs_find_segment(split_off, P, s);
         const int V = (int)(row_off[p + 1] - row_off[p]);
-        if (j == 0) {
-            split_prog[s] = p;
-            if (row_split && V >= 1 && V <= RS_MAXV) {   // the split's test rows, in slot order
-                int64_t r = rec_offsets[s];
-                const int64_t rv = row_off[p];
-                for (uint64_t x = ~tm[s] & rs_full_mask(V); x && r < rows_cap; x &= x - 1, ++r) {
-                    const int t = __ffsll((long long)x) - 1;
-                    row_split[r] = (int)s;
-                    row_info[r] = (unsigned long long)rowinfo[(int64_t)p * RS_MAXV + t] |
-                                  ((unsigned long long)(masks[rv + t] & 63) << 30);
-                }
+        if (j == 0) split_prog[s] = p;
+        if (row_split && V >= 1 && V <= RS_MAXV) {
+            // the split's test rows (slot order): the six threads of the split take the slots
+            // [11 j, 11 j + 11) each, so the writes are spread evenly
+            const uint64_t test = ~tm[s] & rs_full_mask(V);
+            const int lo = 11 * j, hi = lo + 11 < 64 ? lo + 11 : 64;
+            const uint64_t mine = test & (((hi == 64) ? ~0ull : ((1ull << hi) - 1ull)) & ~((1ull << lo) - 1ull));
+            const int64_t r0 = rec_offsets[s];
+            const int64_t rv = row_off[p];
+            for (uint64_t x = mine; x; x &= x - 1) {
+                const int t = __ffsll((long long)x) - 1;
+                const int64_t r = r0 + __popcll(test & ((1ull << t) - 1ull));
+                if (r >= rows_cap) break;
+                row_split[r] = (int)s;
+                row_info[r] = (unsigned long long)rowinfo[(int64_t)p * RS_MAXV + t] |
+                              ((unsigned long long)(masks[rv + t] & 63) << 30);
             }
         }
         uint32_t pm = 0;

@@ -24,6 +24,7 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     __shared__ double lv[RS_MAXV][kFeat];
     __shared__ double part[kGroups][kFeat];
     __shared__ double stat[2][kFeat];
+    __shared__ double inv_c[RS_MAXV];
     const int p = blockIdx.x;
     const int64_t r0 = row_off[p];
     const int V = (int)(row_off[p + 1] - r0);
@@ -37,11 +38,15 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     }
     const int64_t base = xo[p];
     const bool active = f < F;
+    // one reciprocal per version instead of a division per element (FP64 divisions are
+    // expensive on this part's narrow FP64 pipe)
+    if (cycles && threadIdx.x < V) inv_c[threadIdx.x] = 1.0 / cycles[r0 + threadIdx.x];
+    __syncthreads();
     double s = 0.0;
     if (active)
         for (int r = g; r < V; r += kGroups) {
             double x = (double)X[base + (int64_t)r * F + f];
-            if (cycles) x = x / cycles[r0 + r];
+            if (cycles) x = x * inv_c[r];
             const double l = log(x > 1e-30 ? x : 1e-30);
             lv[r][fl] = l;
             s += l;

@@ -389,13 +389,16 @@ class Surrogate:
     NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
     SHAPES = {"W1": (512, 256), "b1": (512,), "W2": (512, 512), "b2": (512,), "W3": (16, 512), "b3": (16,)}
 
-    def __init__(self, ctx: "Context", batch_rows: int = 8192):
+    def __init__(self, ctx: "Context", batch_rows: int = 8192, infer_chunk: int = 0):
         self.ctx = ctx
         L = ctx.L
         self.blob = torch.zeros(L.rs_surrogate_blob_bytes() // 4, dtype=torch.float32,
                                 device=f"cuda:{ctx.device}")
         self.batch_rows = batch_rows
         self.ws = ctx.workspace(L.rs_surrogate_workspace_bytes(batch_rows))
+        self.infer_chunk = infer_chunk or batch_rows
+        self.iws = self.ws if self.infer_chunk == batch_rows else ctx.workspace(
+            L.rs_surrogate_workspace_bytes(self.infer_chunk))
         self.off = {n: int(L.rs_surrogate_offset(i)) for i, n in enumerate(self.NAMES)}
         self.off.update({"m": int(L.rs_surrogate_offset(6)), "v": int(L.rs_surrogate_offset(7)),
                          "grad": int(L.rs_surrogate_offset(8)), "stats": int(L.rs_surrogate_offset(9))})
@@ -435,7 +438,7 @@ class Surrogate:
         self.ctx._check(self.ctx.L.rs_surrogate_infer(
             self.ctx.h, _ptr(self.blob), _ptr(X), n, float(ood_threshold), _ptr(pred), _ptr(score), _ptr(fb),
             _ptr(masks), int(k), float(tau), int(flags), _ptr(rec_code), _ptr(rec_pred),
-            _ptr(self.ws), self.ws.numel(), int(chunk_rows or self.batch_rows)))
+            _ptr(self.iws), self.iws.numel(), int(chunk_rows or self.infer_chunk)))
         return pred, score, fb
 
 
