@@ -50,6 +50,21 @@ def profiled_traffic(stage):
     return None
 
 
+def aggregate_over_ranks(total_ms, recs, world, device):
+    """Weak scaling: every rank times its own batch; the job's time is the slowest rank's and
+    its work is the sum of all ranks' recommendations (no data-path collective)."""
+    if world <= 1:
+        return float(total_ms), float(recs)
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor([float(recs)], dtype=torch.float64, device=device)
+    dist.all_reduce(r)
+    return float(t.item()), float(r.item())
+
+
 def measured_hbm_peak():
     """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the machine's fallback figure."""
     try:
@@ -186,9 +201,10 @@ def cpu_reference_sample(batch, splits, target_s, seed=1):
         dt = time.perf_counter() - t0
         return int(r.counters[0]), dt, nsplit
 
-    rows, dt, n = run(max(threads, 8))
+    run(threads)                                 # warms the library and the thread pool
+    rows, dt, n = run(8 * threads)
     per_split = dt / n
-    n2 = int(min(splits.n_splits, max(threads, target_s / max(per_split, 1e-6))))
+    n2 = int(min(splits.n_splits, max(threads, 0.95 * target_s / max(per_split, 1e-6))))
     rows, dt, n = run(n2)
     return dict(value=rows / dt, unit=UNIT, cores=threads, kind="oracle",
                 sample=f"{n} random splits of the {splits.n_splits} ({rows} ranked rows), "
@@ -313,16 +329,7 @@ def main():
             stages[k_] = stages.get(k_, 0.0) + v_
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-        t = torch.tensor([tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-        r_all = torch.tensor([R], dtype=torch.float64, device=dev)
-        dist.all_reduce(r_all)
-        R_total = float(r_all.item())
-    else:
-        R_total = float(R)
+    tot, R_total = aggregate_over_ranks(tot, R, world, dev)
     ctx.check_device_status()
     ms_step = tot / args.steps
     value = R_total * args.steps / (tot / 1e3)
