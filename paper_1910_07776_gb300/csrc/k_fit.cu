@@ -83,16 +83,21 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
     return r;
 }
 
-// 1/d for a positive finite d: FP32 seed, then two Newton steps r <- r + r (1 - d r)
-// (Newton's method on f(r) = 1/r - d).  Outside [1e-30, 1e30]: plain division.
+// Bit patterns of 2^-100 and 2^100 (positive doubles are ordered like their bit patterns).
+constexpr long long kRcpLoBits = 0x39b0000000000000ll;
+constexpr long long kRcpHiBits = 0x4630000000000000ll;
+
+// 1/d for a positive finite d with three FP64 instructions.  r0 = the FP32 reciprocal of d
+// (mantissa truncated to FP32) has relative error |t| < 2^-22 with t = 1 - d r0, and
+// 1/d = r0 / (1 - t) = r0 (1 + t + t^2 + ...); keeping terms up to t^2 leaves |t|^3 < 2^-66,
+// far below the final rounding:  t = fma(-d, r0, 1), u = fma(t, t, t), r = fma(r0, u, r0).
+// The range test is an integer compare; outside [2^-100, 2^100]: plain division.
 __device__ __forceinline__ double rcp_newton(double d) {
-    if (d < 1e-30 || d > 1e30) return 1.0 / d;
-    double r = f64_of(__frcp_rn(f32_of(d)));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    return r;
+    const long long bits = __double_as_longlong(d);
+    if (bits < kRcpLoBits || bits > kRcpHiBits) return 1.0 / d;
+    const double r0 = f64_of(__frcp_rn(f32_of(d)));
+    const double t = fma(-d, r0, 1.0);
+    return fma(r0, fma(t, t, t), r0);
 }
 
 long long okey_host(double x) {
@@ -203,7 +208,7 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                  const uint64_t* __restrict__ tm, int64_t S, const uint8_t* __restrict__ pb,
                  const uint8_t* __restrict__ pa, const int* __restrict__ npair, uint32_t* fit_pm,
                  uint8_t* fit_n, unsigned* hist, int nmax, int* split_prog,
-                 const int64_t* __restrict__ rec_offsets, int64_t rows_cap, int* row_split,
+                 const int64_t* __restrict__ rec_offsets, int64_t rows_cap,
                  unsigned long long* row_info, const uint8_t* __restrict__ masks,
                  const uint32_t* __restrict__ rowinfo, int* dstatus) {
     __shared__ unsigned h[kHist];
@@ -216,7 +221,7 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         const int p = rs_find_segment(split_off, P, s);
         const int V = (int)(row_off[p + 1] - row_off[p]);
         if (j == 0) split_prog[s] = p;
-        if (row_split && V >= 1 && V <= RS_MAXV) {
+        if (row_info && V >= 1 && V <= RS_MAXV) {
             // the split's test rows (slot order): the six threads of the split take the slots
             // [11 j, 11 j + 11) each, so the writes are spread evenly
             const uint64_t test = ~tm[s] & rs_full_mask(V);
@@ -228,7 +233,6 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                 const int t = __ffsll((long long)x) - 1;
                 const int64_t r = r0 + __popcll(test & ((1ull << t) - 1ull));
                 if (r >= rows_cap) break;
-                row_split[r] = (int)s;
                 row_info[r] = (unsigned long long)rowinfo[(int64_t)p * RS_MAXV + t] |
                               ((unsigned long long)(masks[rv + t] & 63) << 30);
             }
@@ -288,48 +292,6 @@ __device__ __forceinline__ void bucket_tables(const unsigned* hist, long long* s
     __syncthreads();
 }
 
-// ====================================================================== bucket
-// Counting sort of the fits by n.  Each block counts its fits per n in shared memory,
-// reserves one range per n with a single global atomic, and places its fits inside it.
-__global__ void __launch_bounds__(256)
-bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
-                   unsigned* cursor, int* order, int64_t* fit_off, uint8_t* status, double* coef_user,
-                   unsigned long long* counters) {
-    __shared__ long long start[kHist], cstart[kHist];
-    __shared__ unsigned lcount[kHist], lbase[kHist];
-    if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
-    bucket_tables(hist, start, cstart);
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = f < S6 ? fit_n[f] : 0;
-    unsigned local = 0;
-    if (f < S6 && n > 0) local = atomicAdd(&lcount[n], 1u);
-    __syncthreads();
-    if (threadIdx.x < kHist && lcount[threadIdx.x])
-        lbase[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], lcount[threadIdx.x]);
-    __syncthreads();
-    unsigned empty = 0;
-    if (f < S6) {
-        if (n == 0) {
-            fit_off[f] = -1;
-            status[f] = RS_FIT_EMPTY;
-            empty = 1;
-            if (coef_user) {
-                double* o = coef_user + f * RS_COEF_STRIDE;
-                o[0] = nan_d();
-                for (int e = 1; e < RS_COEF_STRIDE; ++e) o[e] = 0.0;
-            }
-        } else {
-            const long long pos = start[n] + lbase[n] + local;
-            order[pos] = (int)f;
-            fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
-        }
-    }
-    if (counters) {
-        const unsigned e = __reduce_add_sync(0xffffffffu, empty);
-        if ((threadIdx.x & 31) == 0 && e) atomicAdd(counters + 10, (unsigned long long)e);
-    }
-}
-
 // ====================================================================== solve, n <= kNReg
 // Where the predictions of one fit go: the test rows of its split that are candidates for
 // its optimization; row r of the split (r-th test slot in ascending order) is dst[r].
@@ -339,6 +301,21 @@ struct PredTarget {
     uint64_t cand;        // test slots to predict (candidates)
     int64_t room;         // rows left in the buffer from dst (guards a wrong size hint)
 };
+
+// A fit that failed (or had no training pair) writes this signalling-NaN pattern to its
+// candidate rows instead of predictions.  Arithmetic never produces a signalling NaN, so the
+// rank pass tells failed fits from predictions by the value alone, without reading the
+// fit status of each row's split.
+constexpr long long kFailBits = 0x7ff4000000000001ll;
+
+__device__ __forceinline__ void mark_failed(const PredTarget& pt) {
+    const double fail = __longlong_as_double(kFailBits);
+    for (uint64_t cm = pt.cand; cm; cm &= cm - 1) {
+        const int t = __ffsll((long long)cm) - 1;
+        const int r = __popcll(pt.test & ((1ull << t) - 1ull));
+        if (r < pt.room) pt.dst[r] = fail;
+    }
+}
 
 // One fit of n = N pairs in registers.  M = K_TT + lambda I = L D L^T (unit lower L, no
 // square roots; reciprocal pivots by rcp_newton).  With t_y = L^-1 y and t_1 = L^-1 1:
@@ -358,6 +335,23 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
         x &= x - 1;
         vb[a] = pb[q];
         ty[a] = yl[q];
+    }
+    if constexpr (N == 1) {
+        // one pair: 1^T alpha = 0 forces alpha = 0, so b = y and every prediction is b
+        if (!pos_finite(__ldg(dl + vb[0]))) return RS_FIT_NOTPD;
+        const double b = ty[0];
+        if (out) {
+            out[0] = b;
+            out[1] = 0.0;
+        }
+        if (!finite_bits(b)) return RS_FIT_NONFINITE;
+        if (pt)
+            for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
+                const int t = __ffsll((long long)cm) - 1;
+                const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+                if (r < pt->room) pt->dst[r] = b;
+            }
+        return RS_FIT_OK;
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -400,11 +394,12 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
 #pragma unroll
         for (int k = i + 1; k < N; ++k) ty[i] = fma(-L[tri(k) + i], ty[k], ty[i]);
     bool fin = finite_bits(b);
-    out[0] = b;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        fin = fin && finite_bits(ty[i]);
-        out[1 + i] = ty[i];
+    for (int i = 0; i < N; ++i) fin = fin && finite_bits(ty[i]);
+    if (out) {
+        out[0] = b;
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[1 + i] = ty[i];
     }
     if (!fin) return RS_FIT_NONFINITE;
     if (pt) {                              // predictions b + sum_a alpha_a K[t][v_a]
@@ -481,13 +476,78 @@ __device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j
 }
 
 __device__ __forceinline__ void finish_record(const SolveArgs& a, int64_t f, int n, int st, double* out) {
-    if (st != RS_FIT_OK) {
+    if (out && st != RS_FIT_OK) {
         out[0] = nan_d();
         for (int e = 1; e <= n; ++e) out[e] = 0.0;
     }
-    if (a.coef_user)
+    if (out && a.coef_user)
         for (int e = n + 1; e < RS_COEF_STRIDE; ++e) out[e] = 0.0;
     a.status[f] = (uint8_t)st;
+}
+
+// Where a fit's coefficients go: the caller's [S][6][33] array, else (fits without
+// predictions) the compact records; the predict-and-rank path keeps none.
+__device__ __forceinline__ double* coef_out(const SolveArgs& a, int64_t f) {
+    if (a.coef_user) return a.coef + f * RS_COEF_STRIDE;
+    return a.predbuf ? nullptr : a.coef + a.fit_off[f];
+}
+
+// ====================================================================== bucket
+// Counting sort of the fits by n.  Each block counts its fits per n in shared memory,
+// reserves one range per n with a single global atomic, and places its fits inside it.
+// A fit without a training pair (n = 0) is finished here: status RS_FIT_EMPTY, and, when
+// predictions are made, the failure pattern in its candidate rows.
+__global__ void __launch_bounds__(256)
+bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
+                   unsigned* cursor, int* order, int64_t* fit_off, uint8_t* status, double* coef_user,
+                   unsigned long long* counters, const SolveArgs sa) {
+    __shared__ long long start[kHist], cstart[kHist];
+    __shared__ unsigned lcount[kHist], lbase[kHist];
+    if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
+    bucket_tables(hist, start, cstart);
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = f < S6 ? fit_n[f] : 0;
+    unsigned local = 0;
+    if (f < S6 && n > 0) local = atomicAdd(&lcount[n], 1u);
+    __syncthreads();
+    if (threadIdx.x < kHist && lcount[threadIdx.x])
+        lbase[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], lcount[threadIdx.x]);
+    __syncthreads();
+    unsigned empty = 0;
+    if (f < S6) {
+        if (n == 0) {
+            fit_off[f] = -1;
+            status[f] = RS_FIT_EMPTY;
+            empty = 1;
+            if (coef_user) {
+                double* o = coef_user + f * RS_COEF_STRIDE;
+                o[0] = nan_d();
+                for (int e = 1; e < RS_COEF_STRIDE; ++e) o[e] = 0.0;
+            }
+            const int64_t s = f / RS_NOPT;
+            const int j = (int)(f - s * RS_NOPT);
+            PredTarget pt;
+            if (pred_target(sa, s, j, sa.split_prog[s], pt)) mark_failed(pt);
+        } else {
+            const long long pos = start[n] + lbase[n] + local;
+            order[pos] = (int)f;
+            fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
+        }
+    }
+    if (counters) {
+        const unsigned e = __reduce_add_sync(0xffffffffu, empty);
+        if ((threadIdx.x & 31) == 0 && e) atomicAdd(counters + 10, (unsigned long long)e);
+    }
+}
+
+// Dynamic work distribution: a warp takes the next 32 positions of its range from a global
+// counter; the following range is requested before the current one is solved, so the
+// atomic's latency is hidden.  Kernels sharing the GPU with another one (or with a late
+// block) thus never leave a statically assigned share behind.
+__device__ __forceinline__ unsigned long long take32(unsigned long long* ctr) {
+    unsigned long long got = 0;
+    if ((threadIdx.x & 31) == 0) got = atomicAdd(ctr, 32ull);
+    return got;
 }
 
 __device__ __forceinline__ void count_status(const SolveArgs& a, int st, bool active) {
@@ -507,14 +567,18 @@ __device__ __forceinline__ void count_status(const SolveArgs& a, int st, bool ac
 // bucket boundaries).  Grid-stride over the bucket positions of that range.
 template <int NLO, int NHI, int MINB>
 __global__ void __launch_bounds__(128, MINB)
-solve_small_kernel(const SolveArgs a) {
+solve_small_kernel(const SolveArgs a, unsigned long long* work) {
     __shared__ long long start[kHist], cstart[kHist];
     bucket_tables(a.hist, start, cstart);
     const long long lo = start[NLO], hi = start[NHI + 1];
-    for (long long base = lo + (long long)blockIdx.x * blockDim.x; base < hi;
-         base += (long long)gridDim.x * blockDim.x) {
-        const long long pos = base + threadIdx.x;
-        const bool active = pos < hi;
+    unsigned long long got = take32(work);
+    long long base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+    while (base < hi) {
+        got = take32(work);
+        // positions from the top of the range down: the largest fits first, the cheapest
+        // last, so the final ranges (the tail of the kernel) are short
+        const long long pos = hi - 1 - (base - lo) - (threadIdx.x & 31);
+        const bool active = pos >= lo;
         int st = RS_FIT_OK;
         if (active) {
             int n = NLO;
@@ -525,14 +589,137 @@ solve_small_kernel(const SolveArgs a) {
             const int p = a.split_prog[s];
             const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
             const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-            double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
+            double* out = coef_out(a, f);
             PredTarget ptv;
             const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
             st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f],
                                           a.dlam + (int64_t)p * RS_MAXV, out, pt);
+            if (st != RS_FIT_OK && pt) mark_failed(*pt);
             finish_record(a, f, n, st, out);
         }
         count_status(a, st, active);
+        base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+    }
+}
+
+// One fit of kNReg < n <= nmax pairs per thread, the same arithmetic as solve_fixed with
+// run-time loops.  The factor and the work vectors live in shared memory, element-major
+// across the 32 lanes of the warp (element e of this lane at W[32 e]): every access of a
+// warp touches 32 distinct banks.  Layout per lane: L (tri(nmax)), D^-1, t_y, t_1 (nmax each).
+__device__ int solve_var(int n, int nmax, const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
+                         const double* __restrict__ yl, uint32_t pm, const double* __restrict__ dl,
+                         double* out, const PredTarget* pt, double* W, int* VB) {
+    const int oD = tri(nmax), oY = oD + nmax, oT = oY + nmax;
+#define LW(e) W[(size_t)(e) * 32]
+    uint32_t x = pm;
+    for (int q = 0; q < n; ++q) {
+        const int bit = __ffs(x) - 1;
+        x &= x - 1;
+        VB[q * 32] = pb[bit];
+        LW(oY + q) = yl[bit];
+    }
+    for (int i = 0; i < n; ++i) {
+        const double* Ki = Kp + VB[i * 32] * RS_GRAM_LD;
+        for (int k = 0; k < i; ++k) {          // c_k of row i, kept in the slot of L(i, k)
+            double s = __ldg(Ki + VB[k * 32]);
+            for (int m = 0; m < k; ++m) s = fma(-LW(tri(i) + m), LW(tri(k) + m), s);
+            LW(tri(i) + k) = s;
+        }
+        double d = __ldg(dl + VB[i * 32]);
+        for (int m = 0; m < i; ++m) {          // L(i, m) = c_m / d_m; d_i = M_ii - sum c_m L(i, m)
+            const double c = LW(tri(i) + m);
+            const double l = c * LW(oD + m);
+            LW(tri(i) + m) = l;
+            d = fma(-c, l, d);
+        }
+        if (!pos_finite(d)) return RS_FIT_NOTPD;
+        LW(oD + i) = rcp_newton(d);
+    }
+    for (int i = 0; i < n; ++i) {              // L t = rhs, two right-hand sides
+        double ty = LW(oY + i), t1 = 1.0;
+        for (int k = 0; k < i; ++k) {
+            const double l = LW(tri(i) + k);
+            ty = fma(-l, LW(oY + k), ty);
+            t1 = fma(-l, LW(oT + k), t1);
+        }
+        LW(oY + i) = ty;
+        LW(oT + i) = t1;
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double sc = LW(oT + i) * LW(oD + i);
+        num = fma(sc, LW(oY + i), num);
+        den = fma(sc, LW(oT + i), den);
+    }
+    const double b = num * rcp_newton(den);
+    for (int i = 0; i < n; ++i) LW(oY + i) = fma(-b, LW(oT + i), LW(oY + i)) * LW(oD + i);
+    for (int i = n - 1; i >= 0; --i) {         // L^T alpha = D^-1 (t_y - b t_1)
+        double v = LW(oY + i);
+        for (int k = i + 1; k < n; ++k) v = fma(-LW(tri(k) + i), LW(oY + k), v);
+        LW(oY + i) = v;
+    }
+    bool fin = finite_bits(b);
+    for (int i = 0; i < n; ++i) fin = fin && finite_bits(LW(oY + i));
+    if (out) {
+        out[0] = b;
+        for (int i = 0; i < n; ++i) out[1 + i] = LW(oY + i);
+    }
+    if (!fin) return RS_FIT_NONFINITE;
+    if (pt)
+        for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
+            const int t = __ffsll((long long)cm) - 1;
+            const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+            const double* Kt = Kp + t * RS_GRAM_LD;
+            double yh = b;
+            for (int q = 0; q < n; ++q) yh = fma(LW(oY + q), __ldg(Kt + VB[q * 32]), yh);
+            if (r < pt->room) pt->dst[r] = yh;
+        }
+#undef LW
+    return RS_FIT_OK;
+}
+
+// Shared memory of solve_mid_kernel per warp, in bytes.
+__host__ __device__ constexpr size_t mid_warp_bytes(int nmax) {
+    return (size_t)32 * ((size_t)(tri(nmax) + 3 * nmax) * sizeof(double) + (size_t)nmax * sizeof(int));
+}
+
+// Fits with kNReg < n, one per thread (solve_var), dynamic work distribution.
+__global__ void __launch_bounds__(128)
+solve_mid_kernel(const SolveArgs a, int nmax, unsigned long long* work) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ long long start[kHist], cstart[kHist];
+    bucket_tables(a.hist, start, cstart);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = tri(nmax) + 3 * nmax;
+    double* W = dsm + (size_t)warp * per * 32 + lane;
+    int* VB = reinterpret_cast<int*>(dsm + (size_t)(blockDim.x >> 5) * per * 32) + (size_t)warp * nmax * 32 + lane;
+    const long long lo = start[kNReg + 1], hi = start[nmax + 1];
+    unsigned long long got = take32(work);
+    long long base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+    while (base < hi) {
+        got = take32(work);
+        const long long pos = hi - 1 - (base - lo) - lane;
+        const bool active = pos >= lo;
+        int st = RS_FIT_OK;
+        if (active) {
+            int n = kNReg + 1;
+            while (start[n + 1] <= pos) ++n;
+            const int64_t f = a.order[pos];
+            const int64_t s = f / RS_NOPT;
+            const int j = (int)(f - s * RS_NOPT);
+            const int p = a.split_prog[s];
+            const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+            const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+            double* out = coef_out(a, f);
+            PredTarget ptv;
+            const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
+            st = solve_var(n, nmax, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f],
+                           a.dlam + (int64_t)p * RS_MAXV, out, pt, W, VB);
+            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            finish_record(a, f, n, st, out);
+        }
+        count_status(a, st, active);
+        base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
     }
 }
 
@@ -752,7 +939,10 @@ solve_large_kernel(const SolveArgs a) {
         }
         const int st = fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
                                 a.lambda, Lsh, out, pt, refine ? &rc : nullptr);
-        if (lane == 0) finish_record(a, f, n, st, out);
+        if (lane == 0) {
+            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            finish_record(a, f, n, st, out);
+        }
         if (a.counters && lane == 0) atomicAdd(a.counters + (st == RS_FIT_OK ? 9 : st == RS_FIT_NOTPD ? 11 : 12), 1ull);
         __syncwarp();
     }
@@ -776,7 +966,6 @@ struct RankPassArgs {
     const double* predbuf;       // [6][R]
     int64_t R;
     const uint32_t* rowinfo;     // [P][64]
-    const int* row_split;        // [R] split of each test row
     const unsigned long long* row_info;  // [R] scoring summary | version mask << 30
     int* dstatus;
     int k;
@@ -790,7 +979,22 @@ struct RankPassArgs {
 
 constexpr int kRankThreads = 256;
 
-__global__ void __launch_bounds__(kRankThreads, 4)
+// The inputs of one test row: its scoring record and the six prediction planes.
+struct RankRow {
+    unsigned long long info;
+    double pred[RS_NOPT];
+};
+
+__device__ __forceinline__ void load_rank_row(const RankPassArgs& a, int64_t row, RankRow& x) {
+    x.info = a.row_info[row];
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) x.pred[j] = a.predbuf[(int64_t)j * a.R + row];
+}
+
+// One thread per test row (grid-stride).  All loads of a row are independent of each other
+// (one round trip), and the next row's loads are issued before the current row is ranked, so
+// each thread keeps two rows in flight.
+__global__ void __launch_bounds__(kRankThreads, 2)
 rank_pass_kernel(const RankPassArgs a) {
     const int lane = threadIdx.x & 31;
     uint32_t c_rows = 0, c_pred = 0, c_scored = 0, c_sign = 0, c_rec = 0, c_reck = 0, c_rech = 0;
@@ -798,21 +1002,20 @@ rank_pass_kernel(const RankPassArgs a) {
     const int64_t total = a.rec_offsets[a.S];
     const int64_t nrows = total < a.R ? total : a.R;
     if (total > a.R && blockIdx.x == 0 && threadIdx.x == 0) rs_dev_flag(a.dstatus, RS_EDATA, -3);
-    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nrows;
-         row += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = a.row_split[row];
-        const unsigned long long info64 = a.row_info[row];
-        const uint32_t info = (uint32_t)info64;
-        const int mt = (int)(info64 >> 30) & 63;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    RankRow cur;
+    if (row < nrows) load_rank_row(a, row, cur);
+    for (; row < nrows; row += stride) {
+        RankRow nxt;
+        if (row + stride < nrows) load_rank_row(a, row + stride, nxt);
+        const double* pred = cur.pred;
+        const uint32_t info = (uint32_t)cur.info;
+        const int mt = (int)(cur.info >> 30) & 63;
         const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
-        double pred[RS_NOPT];
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j)
-            pred[j] = ((candm >> j) & 1) ? a.predbuf[(int64_t)j * a.R + row] : 0.0;
-        const uint8_t* stp = a.status + s * RS_NOPT;
         int okm = 0;
 #pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) okm |= (stp[j] == RS_FIT_OK) << j;
+        for (int j = 0; j < RS_NOPT; ++j) okm |= (__double_as_longlong(pred[j]) != kFailBits) << j;
         const int validm = candm & okm;
         long long key[RS_NOPT];
         int above = 0, spos = 0;
@@ -835,34 +1038,26 @@ rank_pass_kernel(const RankPassArgs a) {
             }
         uint32_t code = 0x0FFFFFF0u;
         int rk = 0;
-        double rp[RS_NOPT];
-#pragma unroll
-        for (int x = 0; x < RS_NOPT; ++x) rp[x] = nan_d();
+        int pos[RS_NOPT];
 #pragma unroll
         for (int j = 0; j < RS_NOPT; ++j) {
-            const int pos = __popc(bm[j] & above);
-            if (((above >> j) & 1) && pos < a.k) {
-                code = (code & ~(0xFu << (4 + 4 * pos))) | ((uint32_t)j << (4 + 4 * pos));
-#pragma unroll
-                for (int x = 0; x < RS_NOPT; ++x)
-                    if (x == pos) rp[x] = pred[j];
+            pos[j] = __popc(bm[j] & above);
+            if (((above >> j) & 1) && pos[j] < a.k) {
+                code = (code & ~(0xFu << (4 + 4 * pos[j]))) | ((uint32_t)j << (4 + 4 * pos[j]));
                 rk |= 1 << j;
             }
         }
         const int c = __popc(rk);
         code = (code & ~0xFu) | (uint32_t)c;
         a.rec_code[row] = code;
-        if (a.rec_pred) {
-            if (a.k == 3) {
-                double* o = a.rec_pred + row * 3;
-                o[0] = rp[0];
-                o[1] = rp[1];
-                o[2] = rp[2];
-            } else {
+        if (a.rec_pred) {                      // each chosen candidate writes its own slot
+            double* o = a.rec_pred + row * a.k;
 #pragma unroll
-                for (int x = 0; x < RS_NOPT; ++x)
-                    if (x < a.k) a.rec_pred[row * a.k + x] = rp[x];
-            }
+            for (int j = 0; j < RS_NOPT; ++j)
+                if ((rk >> j) & 1) o[pos[j]] = pred[j];
+#pragma unroll
+            for (int x = 0; x < RS_NOPT; ++x)
+                if (x >= c && x < a.k) o[x] = nan_d();
         }
         if (a.pred_all)
 #pragma unroll
@@ -892,6 +1087,7 @@ rank_pass_kernel(const RankPassArgs a) {
             c_t1 += 1;
             c_t1h += (bp == ba);
         }
+        cur = nxt;
     }
     if (a.counters) {
         const uint32_t vals[10] = {c_rows, c_pred, c_scored, c_sign, c_rec, c_reck, c_rech, c_t1, c_t1h, c_inv};
@@ -1233,6 +1429,7 @@ cudaError_t launch_rank(const rs_fit_args& a, const int64_t* coef_off, const uin
 struct FitWs {
     unsigned* hist;      // [kHist]
     unsigned* cursor;    // [kHist]
+    unsigned long long* work;   // [4] work counters of the solve kernels
     uint8_t* pb;         // [P][6][32]
     uint8_t* pa;         // [P][6][32]
     double* ylab;        // [P][6][32]
@@ -1240,7 +1437,6 @@ struct FitWs {
     uint64_t* cand;      // [P][6]
     uint32_t* rowinfo;   // [P][64]
     double* dlam;        // [P][64] K[t][t] + lambda
-    int* row_split;      // [Rcap]
     unsigned long long* row_info;   // [Rcap] scoring summary | mask << 30
     int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
@@ -1255,14 +1451,18 @@ struct FitWs {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// histogram + bucket cursors (unsigned) and four 64-bit work counters, zeroed per call
+constexpr size_t kCounterBytes = 2 * kHist * sizeof(unsigned) + 4 * sizeof(unsigned long long);
+
 FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     FitWs w{};
     char* c = (char*)base;
     size_t o = 0;
     auto take = [&](size_t b) { char* p = c ? c + o : nullptr; o += a256(b); return p; };
     const int64_t S6 = S * RS_NOPT;
-    w.hist = (unsigned*)take(2 * kHist * sizeof(unsigned));
+    w.hist = (unsigned*)take(kCounterBytes);
     w.cursor = w.hist ? w.hist + kHist : nullptr;
+    w.work = w.hist ? reinterpret_cast<unsigned long long*>(w.hist + 2 * kHist) : nullptr;
     w.pb = (uint8_t*)take(P * RS_NOPT * RS_MAXPAIRS);
     w.pa = (uint8_t*)take(P * RS_NOPT * RS_MAXPAIRS);
     w.ylab = (double*)take(P * RS_NOPT * RS_MAXPAIRS * sizeof(double));
@@ -1270,7 +1470,6 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
     w.rowinfo = (uint32_t*)take(P * RS_MAXV * sizeof(uint32_t));
     w.dlam = (double*)take(P * RS_MAXV * sizeof(double));
-    w.row_split = (int*)take((size_t)Rcap * sizeof(int));
     w.row_info = (unsigned long long*)take((size_t)Rcap * sizeof(unsigned long long));
     w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
@@ -1285,7 +1484,7 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
 }
 
 template <int NLO, int NHI, int MINB>
-cudaError_t launch_small(const SolveArgs& sa, int sms, int64_t S6, cudaStream_t st) {
+cudaError_t launch_small(const SolveArgs& sa, int sms, int64_t S6, unsigned long long* work, cudaStream_t st) {
     auto kern = solve_small_kernel<NLO, NHI, MINB>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
@@ -1294,7 +1493,25 @@ cudaError_t launch_small(const SolveArgs& sa, int sms, int64_t S6, cudaStream_t 
     const int64_t need = (S6 + 127) / 128;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, 128, 0, st>>>(sa);
+    kern<<<(unsigned)grid, 128, 0, st>>>(sa, work);
+    return cudaGetLastError();
+}
+
+// The one-fit-per-thread solver of kNReg < n <= nmax: as many warps per block as fit in
+// 200 KB of shared memory (1..4), as many blocks as can be resident.
+cudaError_t launch_mid(const SolveArgs& sa, int sms, int nmax, unsigned long long* work, cudaStream_t st) {
+    const size_t per_warp = mid_warp_bytes(nmax);
+    int warps = (int)((size_t)200 * 1024 / per_warp);
+    if (warps > 4) warps = 4;
+    if (warps < 1) warps = 1;
+    const size_t smem = per_warp * warps;
+    cudaError_t e = cudaFuncSetAttribute(solve_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_mid_kernel, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    solve_mid_kernel<<<(unsigned)grid, warps * 32, smem, st>>>(sa, nmax, work);
     return cudaGetLastError();
 }
 
@@ -1322,7 +1539,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (w.bytes > a.workspace_bytes) return cudaErrorInvalidValue;
     const int64_t S6 = a.S * RS_NOPT;
     auto mark = [&](int i) { if (a.ev) cudaEventRecord(a.ev[i], st); };
-    cudaError_t e = cudaMemsetAsync(w.hist, 0, 2 * kHist * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(w.hist, 0, kCounterBytes, st);
     if (e != cudaSuccess) return e;
     mark(0);
     pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
@@ -1333,50 +1550,77 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                                                 a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
                                                 nmax, w.split_prog, a.rec_offsets,
                                                 a.rec_code ? a.rows_cap : 0,
-                                                a.rec_code ? w.row_split : nullptr, w.row_info,
+                                                a.rec_code ? w.row_info : nullptr,
                                                 a.masks, w.rowinfo, a.dstatus);
     mark(2);
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
-    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order, w.fit_off,
-                                                  status, user ? a.coef_out : nullptr, a.counters);
-    mark(3);
     const bool rank = a.rec_code != nullptr;
     SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
                  a.rows_cap, a.flags, a.dstatus, a.Z, a.x_offsets, a.feat_width, a.max_feat};
+    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order, w.fit_off,
+                                                  status, user ? a.coef_out : nullptr, a.counters, sa);
+    mark(3);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool refine = (a.flags & RS_REFINE_X) != 0;
     if (!refine) {
-        // the size at which the solver switches to the register-heavier instantiation
-        switch (a.tune_split) {
-            case 4: e = launch_small<1, 4, 4>(sa, sms, S6, st);
-                    if (e == cudaSuccess) e = launch_small<5, kNReg, 2>(sa, sms, S6, st); break;
-            case 5: e = launch_small<1, 5, 4>(sa, sms, S6, st);
-                    if (e == cudaSuccess) e = launch_small<6, kNReg, 2>(sa, sms, S6, st); break;
-            case 7: e = launch_small<1, 7, 3>(sa, sms, S6, st);
-                    if (e == cudaSuccess) e = launch_small<8, kNReg, 2>(sa, sms, S6, st); break;
-            case 8: e = launch_small<1, 8, 3>(sa, sms, S6, st);
-                    if (e == cudaSuccess) e = launch_small<9, kNReg, 2>(sa, sms, S6, st); break;
-            default: e = launch_small<1, 6, 4>(sa, sms, S6, st);
-                    if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, st); break;
+        // n > kNReg: one fit per thread from shared memory.  With a side stream it runs
+        // beside the register solvers (which take their work dynamically, so they lose
+        // nothing to it); without one it runs first.
+        // Three solvers over disjoint ranges of the bucket order.  The shared-memory solver
+        // (n > kNReg, few fits, latency-bound) runs on the side stream when there is one, beside
+        // the two register solvers (n <= split, then split < n <= kNReg) on the call's stream;
+        // all three take their work dynamically, so the one sharing the SMs with the others
+        // costs neither of them a statically assigned share.
+        const bool mid = nmax > kNReg;
+        const bool fork = mid && a.side && a.fork && a.join;
+        if (fork) {
+            e = cudaEventRecord(a.fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.fork, 0);
+            if (e == cudaSuccess) e = launch_mid(sa, sms, nmax, w.work + 2, a.side);
+            if (e == cudaSuccess) e = cudaEventRecord(a.join, a.side);
+        } else if (mid) {
+            e = launch_mid(sa, sms, nmax, w.work + 2, st);
         }
         if (e != cudaSuccess) return e;
+        unsigned long long* w0 = w.work;
+        unsigned long long* w1 = w.work + 1;
+        switch (a.tune_split) {
+            case 4: e = launch_small<1, 4, 4>(sa, sms, S6, w0, st);
+                    if (e == cudaSuccess) e = launch_small<5, kNReg, 2>(sa, sms, S6, w1, st); break;
+            case 5: e = launch_small<1, 5, 4>(sa, sms, S6, w0, st);
+                    if (e == cudaSuccess) e = launch_small<6, kNReg, 2>(sa, sms, S6, w1, st); break;
+            case 7: e = launch_small<1, 7, 3>(sa, sms, S6, w0, st);
+                    if (e == cudaSuccess) e = launch_small<8, kNReg, 2>(sa, sms, S6, w1, st); break;
+            case 8: e = launch_small<1, 8, 3>(sa, sms, S6, w0, st);
+                    if (e == cudaSuccess) e = launch_small<9, kNReg, 2>(sa, sms, S6, w1, st); break;
+            default: e = launch_small<1, 6, 4>(sa, sms, S6, w0, st);
+                    if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, w1, st); break;
+        }
+        if (e != cudaSuccess) return e;
+        mark(4);
+        if (fork) {
+            e = cudaStreamWaitEvent(st, a.join, 0);
+            if (e != cudaSuccess) return e;
+        }
+    } else {
+        mark(4);
+        // refinement through Z: every fit by one warp (solve_large_kernel)
+        const size_t lsmem = (size_t)kLargeWarps * 32 * 33 * sizeof(double) +
+                             (size_t)kLargeWarps * (a.max_feat + 64 + 16) * sizeof(double);
+        e = cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+        if (e != cudaSuccess) return e;
+        solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, lsmem, st>>>(sa);
     }
-    mark(4);
-    const size_t lsmem = (size_t)kLargeWarps * 32 * 33 * sizeof(double) +
-                         (refine ? (size_t)kLargeWarps * (a.max_feat + 64 + 16) * sizeof(double) : 0);
-    e = cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
-    if (e != cudaSuccess) return e;
-    solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, lsmem, st>>>(sa);
     mark(5);
     if (rank) {
         RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.train_masks, a.S,
-                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo, w.row_split,
+                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo,
                         w.row_info, a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all,
                         a.counters};
         ra.ktau = okey_host(a.log_tau);

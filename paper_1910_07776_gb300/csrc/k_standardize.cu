@@ -1,11 +1,61 @@
 // K1: feature vectors (Sec. 2: counters normalised by the cycle count), followed by the
-// library's log / per-program z-score reading.  HBM-bound: one read of X, one write of Z.
+// library's log / per-program z-score reading.  One read of X, one write of Z.
 //
-// X is read once and the FP64 log -- expensive on this part's narrow FP64 pipe -- runs once
-// per element, spread over eight row groups per feature so that every SM has FP64 work.
+// The logarithm runs once per element on this part's narrow FP64 pipe, so it is written
+// here to need few FP64 instructions (log_pos below, 12 of them); X is read once, spread
+// over eight row groups per feature so that every SM has work.
 #include "rs_internal.cuh"
+#include "rs_log_table.h"
 
 namespace {
+
+constexpr long long kClampBits = 0x39b4484bfeebc2a0ll;   // bit pattern of 1e-30
+constexpr long long kInfBits = 0x7ff0000000000000ll;
+
+// log q for a positive, normal, finite q, table-driven (P. T. P. Tang, "Table-driven
+// implementation of the logarithm function in IEEE floating-point arithmetic", ACM TOMS
+// 16(4), 1990): q = 2^e m with m in [1, 2); F = the centre of m's interval of width 1/256
+// (index i = the top eight fraction bits of m); r = (m - F) / F with |r| <= 2^-9, m - F exact;
+//     log q = e ln2 + log F + log1p(r),
+// log1p(r) by its Taylor series up to r^6 (the first term left out is below 2^-65).
+// e ln2 = e ln2_hi (exact) + e ln2_lo.  12 FP64 instructions; the absolute error is about one
+// ulp of max(1, |log q|) (near q = 1 the result is small and its relative error larger, which
+// the z-score, a difference of logs, does not see).
+__device__ __forceinline__ double log_pos(double q, const double* tlog, const double* tinv) {
+    const long long b = __double_as_longlong(q);
+    const int i = (int)((b >> 44) & 0xff);
+    const double m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+    const double F = __longlong_as_double(0x3ff0000000000000ll | ((long long)(2 * i + 1) << 43));
+    const double r = (m - F) * tinv[i];
+    double p = fma(r, -1.0 / 6.0, 0.2);
+    p = fma(p, r, -0.25);
+    p = fma(p, r, 1.0 / 3.0);
+    p = fma(p, r, -0.5);
+    const double l1p = fma(r * r, p, r);
+    // e as a double without a conversion instruction: 2^52 + 2048 + e, minus 2^52 + 2048
+    const long long eb = (b >> 52) - 1023 + 2048;
+    const double ed = __longlong_as_double(0x4330000000000000ll | eb) - 4503599627372544.0;
+    return fma(ed, kLn2Hi, tlog[i]) + fma(ed, kLn2Lo, l1p);
+}
+
+// log(max(q, 1e-30)) with the branches of the plain definition: q above the clamp and finite
+// -> log_pos (subnormal q never reach it); +inf -> +inf; q <= 1e-30 or NaN -> log(1e-30).
+__device__ __forceinline__ double log_clamped(double q, const double* tlog, const double* tinv) {
+    const long long b = __double_as_longlong(q);
+    if (b > kClampBits && b < kInfBits) return log_pos(q, tlog, tinv);
+    return b == kInfBits ? q : kLogClamp;
+}
+
+// An input element as a double: FP32 values are re-packed with integer operations (exact for
+// normal numbers); zeros, subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double as_double(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned ex = (u >> 23) & 0xff;
+    if (ex == 0 || ex == 0xff) return (double)x;
+    return __longlong_as_double(((long long)(u & 0x80000000u) << 32) |
+                                ((long long)(ex - 127 + 1023) << 52) | ((long long)(u & 0x7fffff) << 29));
+}
+__device__ __forceinline__ double as_double(double x) { return x; }
 
 constexpr int kFeat = 32;                    // features per block (one warp-wide row slice)
 constexpr int kGroups = 8;                   // row groups per block
@@ -25,6 +75,7 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     __shared__ double part[kGroups][kFeat];
     __shared__ double stat[2][kFeat];
     __shared__ double inv_c[RS_MAXV];
+    __shared__ double tlog[256], tinv[256];
     const int p = blockIdx.x;
     const int64_t r0 = row_off[p];
     const int V = (int)(row_off[p + 1] - r0);
@@ -41,13 +92,17 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     // one reciprocal per version instead of a division per element (FP64 divisions are
     // expensive on this part's narrow FP64 pipe)
     if (cycles && threadIdx.x < V) inv_c[threadIdx.x] = 1.0 / cycles[r0 + threadIdx.x];
+    for (int t = threadIdx.x; t < 256; t += kThreads) {
+        tlog[t] = kLogTabF[t];
+        tinv[t] = kLogTabInv[t];
+    }
     __syncthreads();
     double s = 0.0;
     if (active)
         for (int r = g; r < V; r += kGroups) {
-            double x = (double)X[base + (int64_t)r * F + f];
+            double x = as_double(X[base + (int64_t)r * F + f]);
             if (cycles) x = x * inv_c[r];
-            const double l = log(x > 1e-30 ? x : 1e-30);
+            const double l = log_clamped(x, tlog, tinv);
             lv[r][fl] = l;
             s += l;
         }

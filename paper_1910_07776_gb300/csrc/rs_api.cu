@@ -19,6 +19,8 @@ struct rs_ctx {
     int tune_split;          // autotuned launch parameters of the batched form
     int tune_rank_waves;
     cudaEvent_t ev[RS_NSTAGE_EVENTS];
+    cudaStream_t side;       // second stream of the batched solver (fork/join on events)
+    cudaEvent_t fork, join;
     char err[512];
 };
 
@@ -85,6 +87,8 @@ rs_status rs_create(rs_ctx** out, int device, void* stream) {
     c->tune_split = 6;
     c->tune_rank_waves = 16;
     for (int i = 0; i < RS_NSTAGE_EVENTS; ++i) c->ev[i] = nullptr;
+    c->side = nullptr;
+    c->fork = c->join = nullptr;
     e = cudaMalloc(&c->dstatus, RS_DST_INTS * sizeof(int));
     if (e != cudaSuccess) {
         delete c;
@@ -103,6 +107,17 @@ rs_status rs_create(rs_ctx** out, int device, void* stream) {
         delete c;
         return RS_ECUDA;
     }
+    // the side stream is an optimisation: without it every launch stays on the call's stream
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->fork) cudaEventDestroy(c->fork);
+        if (c->join) cudaEventDestroy(c->join);
+        c->side = nullptr;
+        c->fork = c->join = nullptr;
+    }
     *out = c;
     return RS_OK;
 }
@@ -114,6 +129,9 @@ rs_status rs_destroy(rs_ctx* c) {
     cudaFree(c->scan);
     for (int i = 0; i < RS_NSTAGE_EVENTS; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     delete c;
     return RS_OK;
 }
@@ -253,6 +271,9 @@ static rs_status fit_common(rs_ctx* c, const rs_batch* b, const double* K, const
     a.ev = c->profiling ? c->ev : nullptr;
     a.tune_split = c->tune_split;
     a.tune_rank_waves = c->tune_rank_waves;
+    a.side = c->side;
+    a.fork = c->fork;
+    a.join = c->join;
     return RS_OK;
 }
 

@@ -87,6 +87,10 @@ struct rs_fit_args {
     size_t workspace_bytes;
     // optional stage events (recorded on the stream before and after each internal launch)
     cudaEvent_t* ev;
+    // optional second stream and fork/join events: the solver of the largest fits runs on
+    // `side` beside the others (all three NULL: everything on the call's stream)
+    cudaStream_t side;
+    cudaEvent_t fork, join;
 };
 #define RS_NSTAGE_EVENTS 7   // before pairs, after pairs / plan / bucket / solve / solve-large / rank
 size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t rows_cap);

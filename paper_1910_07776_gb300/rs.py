@@ -256,7 +256,7 @@ class Context:
         self.stream = stream
         self._check(self.L.rs_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
 
-    STAGES = ["pairs", "plan_fits", "bucket_fits", "solve_small", "solve_large", "rank"]
+    STAGES = ["pairs", "plan_fits", "bucket_fits", "solve", "solve_join", "rank"]
 
     def profile_enable(self, on: bool = True):
         self._check(self.L.rs_profile_enable(self.h, 1 if on else 0))

@@ -69,6 +69,41 @@ def test_standardize_and_gram(rs, ctx, dtype, cycles):
         np.testing.assert_array_equal(K[p, :V, :V], K[p, :V, :V].T)
 
 
+@pytest.mark.parametrize("dtype,cycles", [(np.float64, False), (np.float32, True), (np.float64, True)])
+def test_standardize_logarithm_accuracy(rs, ctx, dtype, cycles):
+    """The standardization's own table-driven logarithm against the FP64 library log.  With one
+    version per program the per-feature mean is the log itself, so mu = log(max(x / c, 1e-30))
+    element by element.  The device forms q = x * (1 / c); the same two IEEE operations on the
+    host give the same q.  Bound: 4 ulp of max(1, |log q|)."""
+    rng = np.random.default_rng(23)
+    P, F = 24, 512
+    if dtype == np.float32:
+        x = (10.0 ** rng.uniform(-37, 38, size=(P, F))).astype(np.float32)
+        x.flat[:8] = [0.0, 1.0, 2.0, 0.5, 1e-40, 3e38, np.float32(1) + np.float32(2 ** -23), 7.0]
+    else:
+        x = 10.0 ** rng.uniform(-300, 300, size=(P, F))
+        x.flat[:8] = [0.0, 1.0, 2.0, 0.5, 1e-310, 1e300, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -53]
+    x[1] = 1.0 + rng.uniform(-1e-3, 1e-3, size=F)         # q near 1: small logs
+    c = 10.0 ** rng.uniform(0, 9, size=P) if cycles else None
+    batch = synth.ProgramBatch(
+        X=x.reshape(-1), x_offsets=np.arange(P, dtype=np.int64) * F,
+        row_offsets=np.arange(P + 1, dtype=np.int64), feat_width=np.full(P, F, dtype=np.int32),
+        masks=np.zeros(P, dtype=np.uint8), log_time=np.zeros(P), cycles=c)
+    db = rs.DeviceBatch.from_host(batch)
+    mu = torch.empty(P * F, dtype=torch.float64, device="cuda")
+    sg = torch.empty(P * F, dtype=torch.float64, device="cuda")
+    ctx.standardize(db, mu=mu, sigma=sg)
+    torch.cuda.synchronize()
+    got = mu.cpu().numpy().reshape(P, F)
+    q = x.astype(np.float64)
+    if cycles:
+        q = q * (1.0 / c)[:, None]
+    ref = np.log(np.maximum(q, 1e-30))
+    bound = 4 * 2.0 ** -53 * np.maximum(1.0, np.abs(ref))
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+    assert np.all(sg.cpu().numpy() == 0)
+
+
 # ------------------------------------------------------------------------------ A2..A6
 @pytest.mark.parametrize("form", [0, 1])
 def test_tiny_config_lovo_full(rs, ctx, form):
