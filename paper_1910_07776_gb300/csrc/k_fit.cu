@@ -26,6 +26,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "mbar.cuh"
 #include "rs_internal.cuh"
 
 namespace {
@@ -203,6 +204,10 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
 }
 
 // ====================================================================== plan
+// One thread per split: the six pair masks of its fits (the pair loops run over one
+// program's pair tables, uniform across a warp whose splits share the program), the
+// histogram of fit sizes (warp-aggregated), and the split's row records in slot order:
+// the row's scoring summary | version mask << 30 | mask of the split's empty fits << 36.
 __global__ void __launch_bounds__(256)
 plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __restrict__ split_off,
                  const uint64_t* __restrict__ tm, int64_t S, const uint8_t* __restrict__ pb,
@@ -214,46 +219,45 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
     __shared__ unsigned h[kHist];
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f < S * RS_NOPT) {
-        const int64_t s = f / RS_NOPT;
-        const int j = (int)(f - s * RS_NOPT);
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) {
         const int p = rs_find_segment(split_off, P, s);
         const int V = (int)(row_off[p + 1] - row_off[p]);
-        if (j == 0) split_prog[s] = p;
-        if (row_info && V >= 1 && V <= RS_MAXV) {
-            // the split's test rows (slot order): the six threads of the split take the slots
-            // [11 j, 11 j + 11) each, so the writes are spread evenly
+        const bool okV = V >= 1 && V <= RS_MAXV;
+        split_prog[s] = p;
+        const uint64_t T = okV ? tm[s] & rs_full_mask(V) : 0ull;
+        int emptym = 0;
+        for (int j = 0; j < RS_NOPT; ++j) {
+            uint32_t pm = 0;
+            if (okV) {
+                const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+                const int np = npair[p * RS_NOPT + j];
+                for (int q = 0; q < np; ++q)
+                    pm |= (uint32_t)((T >> pb[base + q]) & (T >> pa[base + q]) & 1ull) << q;
+            }
+            int n = __popc(pm);
+            if (n > nmax) {        // more pairs than the workspace was sized for
+                rs_dev_flag(dstatus, RS_EDATA, -2);
+                pm = 0;
+                n = 0;
+            }
+            fit_pm[s * RS_NOPT + j] = pm;
+            fit_n[s * RS_NOPT + j] = (uint8_t)n;
+            emptym |= (n == 0) << j;
+            const unsigned grp = __match_any_sync(__activemask(), n);
+            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&h[n], (unsigned)__popc(grp));
+        }
+        if (row_info && okV) {
             const uint64_t test = ~tm[s] & rs_full_mask(V);
-            const int lo = 11 * j, hi = lo + 11 < 64 ? lo + 11 : 64;
-            const uint64_t mine = test & (((hi == 64) ? ~0ull : ((1ull << hi) - 1ull)) & ~((1ull << lo) - 1ull));
-            const int64_t r0 = rec_offsets[s];
             const int64_t rv = row_off[p];
-            for (uint64_t x = mine; x; x &= x - 1) {
+            int64_t r = rec_offsets[s];
+            for (uint64_t x = test; x && r < rows_cap; x &= x - 1, ++r) {
                 const int t = __ffsll((long long)x) - 1;
-                const int64_t r = r0 + __popcll(test & ((1ull << t) - 1ull));
-                if (r >= rows_cap) break;
                 row_info[r] = (unsigned long long)rowinfo[(int64_t)p * RS_MAXV + t] |
-                              ((unsigned long long)(masks[rv + t] & 63) << 30);
+                              ((unsigned long long)(masks[rv + t] & 63) << 30) |
+                              ((unsigned long long)emptym << 36);
             }
         }
-        uint32_t pm = 0;
-        if (V >= 1 && V <= RS_MAXV) {
-            const uint64_t T = tm[s] & rs_full_mask(V);
-            const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-            const int np = npair[p * RS_NOPT + j];
-            for (int q = 0; q < np; ++q)
-                if (((T >> pb[base + q]) & 1) && ((T >> pa[base + q]) & 1)) pm |= 1u << q;
-        }
-        int n = __popc(pm);
-        if (n > nmax) {            // more pairs than the workspace was sized for
-            rs_dev_flag(dstatus, RS_EDATA, -2);
-            pm = 0;
-            n = 0;
-        }
-        fit_pm[f] = pm;
-        fit_n[f] = (uint8_t)n;
-        atomicAdd(&h[n], 1u);
     }
     __syncthreads();
     if (threadIdx.x < kHist && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
@@ -302,10 +306,10 @@ struct PredTarget {
     int64_t room;         // rows left in the buffer from dst (guards a wrong size hint)
 };
 
-// A fit that failed (or had no training pair) writes this signalling-NaN pattern to its
-// candidate rows instead of predictions.  Arithmetic never produces a signalling NaN, so the
-// rank pass tells failed fits from predictions by the value alone, without reading the
-// fit status of each row's split.
+// A fit that failed writes this signalling-NaN pattern to its candidate rows instead of
+// predictions.  Arithmetic never produces a signalling NaN, so the rank pass tells failed
+// fits from predictions by the value alone, without reading the fit status of each row's
+// split (fits without a training pair are marked in the row records instead).
 constexpr long long kFailBits = 0x7ff4000000000001ll;
 
 __device__ __forceinline__ void mark_failed(const PredTarget& pt) {
@@ -451,8 +455,9 @@ struct SolveArgs {
     const uint64_t* train_masks;
     const int64_t* rec_offsets;
     const uint64_t* cand;
-    double* predbuf;      // [6][R]
-    int64_t R;
+    double* predbuf;      // [6][PS]: plane j holds the predictions of optimization j
+    int64_t R;            // rows of the buffer (the bound every write is checked against)
+    int64_t PS;           // plane stride (rows), even
     int flags;
     int* dstatus;
     // refinement through Z (RS_REFINE_X)
@@ -469,7 +474,7 @@ __device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j
     pt.test = ~a.train_masks[s] & full;
     pt.cand = pt.test & ((a.flags & RS_RANK_ALL) ? full : a.cand[p * RS_NOPT + j]);
     const int64_t r0 = a.rec_offsets[s];
-    pt.dst = a.predbuf + (int64_t)j * a.R + r0;
+    pt.dst = a.predbuf + (int64_t)j * a.PS + r0;
     pt.room = a.R - r0;
     if (r0 + __popcll(pt.test) > a.R) rs_dev_flag(a.dstatus, RS_EDATA, -3);
     return true;
@@ -495,12 +500,14 @@ __device__ __forceinline__ double* coef_out(const SolveArgs& a, int64_t f) {
 // ====================================================================== bucket
 // Counting sort of the fits by n.  Each block counts its fits per n in shared memory,
 // reserves one range per n with a single global atomic, and places its fits inside it.
-// A fit without a training pair (n = 0) is finished here: status RS_FIT_EMPTY, and, when
-// predictions are made, the failure pattern in its candidate rows.
+// Counting sort of the fits by n: each block counts its fits per n in shared memory,
+// reserves one range per n with a single global atomic, and places its fits inside it.
+// A fit without a training pair (n = 0) is finished here (status RS_FIT_EMPTY); the rank
+// pass knows it from the row records.
 __global__ void __launch_bounds__(256)
 bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
                    unsigned* cursor, int* order, int64_t* fit_off, uint8_t* status, double* coef_user,
-                   unsigned long long* counters, const SolveArgs sa) {
+                   unsigned long long* counters) {
     __shared__ long long start[kHist], cstart[kHist];
     __shared__ unsigned lcount[kHist], lbase[kHist];
     if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
@@ -516,7 +523,7 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
     unsigned empty = 0;
     if (f < S6) {
         if (n == 0) {
-            fit_off[f] = -1;
+            if (fit_off) fit_off[f] = -1;
             status[f] = RS_FIT_EMPTY;
             empty = 1;
             if (coef_user) {
@@ -524,14 +531,10 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
                 o[0] = nan_d();
                 for (int e = 1; e < RS_COEF_STRIDE; ++e) o[e] = 0.0;
             }
-            const int64_t s = f / RS_NOPT;
-            const int j = (int)(f - s * RS_NOPT);
-            PredTarget pt;
-            if (pred_target(sa, s, j, sa.split_prog[s], pt)) mark_failed(pt);
         } else {
             const long long pos = start[n] + lbase[n] + local;
             order[pos] = (int)f;
-            fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
+            if (fit_off) fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
         }
     }
     if (counters) {
@@ -864,8 +867,10 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
         __syncwarp();
         fin = __all_sync(0xffffffffu, !act || finite_bits(al)) && finite_bits(b);
     }
-    if (act) coef[1 + lane] = al;
-    if (lane == 0) coef[0] = b;
+    if (coef) {
+        if (act) coef[1 + lane] = al;
+        if (lane == 0) coef[0] = b;
+    }
     __syncwarp();
     if (!fin) return RS_FIT_NONFINITE;
     if (pt && rf) {                           // predictions through Z: b + z_t . beta
@@ -926,7 +931,7 @@ solve_large_kernel(const SolveArgs a) {
         const int p = a.split_prog[s];
         const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-        double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : a.coef + a.fit_off[f];
+        double* out = coef_out(a, f);
         PredTarget ptv;
         const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
         RefineCtx rc;
@@ -955,17 +960,11 @@ solve_large_kernel(const SolveArgs a) {
 // before it (larger key; on equal keys the lower index); its place is the popcount of
 // that set restricted to the candidates at or above the threshold.
 struct RankPassArgs {
-    int P;
-    const int* split_prog;
-    const int64_t* row_off;
-    const uint8_t* masks;
-    const uint64_t* tm;
-    int64_t S;
     const int64_t* rec_offsets;
-    const uint8_t* status;
-    const double* predbuf;       // [6][R]
-    int64_t R;
-    const uint32_t* rowinfo;     // [P][64]
+    int64_t S;
+    const double* predbuf;       // [6][PS]
+    int64_t R;                   // rows of the buffer
+    int64_t PS;                  // plane stride (even)
     const unsigned long long* row_info;  // [R] scoring summary | version mask << 30
     int* dstatus;
     int k;
@@ -977,125 +976,189 @@ struct RankPassArgs {
     unsigned long long* counters;
 };
 
-constexpr int kRankThreads = 256;
+constexpr int kRankTile = 256;               // rows per tile = threads per block
+constexpr int kRankStages = 3;
+constexpr int kRankPlanes = 1 + RS_NOPT;     // the row records, then the six prediction planes
+constexpr size_t kRankStageBytes = (size_t)kRankPlanes * kRankTile * 8;
+constexpr size_t kRankSmem = kRankStages * kRankStageBytes + kRankStages * 8;
 
-// The inputs of one test row: its scoring record and the six prediction planes.
-struct RankRow {
-    unsigned long long info;
-    double pred[RS_NOPT];
+// Per-thread tallies of the scoring counters.
+struct RankTally {
+    uint32_t rows = 0, pred = 0, scored = 0, sign = 0, rec = 0, reck = 0, rech = 0, t1 = 0, t1h = 0, inv = 0;
 };
 
-__device__ __forceinline__ void load_rank_row(const RankPassArgs& a, int64_t row, RankRow& x) {
-    x.info = a.row_info[row];
+// Ranking, threshold, top-k, outputs and scoring of one test row (Sec. 2 tier 3, Sec. 6):
+// candidates (versions lacking j, or all with RS_RANK_ALL) whose fit succeeded are ranked by
+// their predictions as order-preserving integer keys (ties: lower j first); those at or
+// above log tau form the recommendation, the first k of them reported.
+__device__ __forceinline__ void rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
+                                         const double (&pred)[RS_NOPT], RankTally& c) {
+    const uint32_t info = (uint32_t)info64;
+    const int mt = (int)(info64 >> 30) & 63;
+    const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
+    // a candidate counts when its fit had a training pair (row record) and did not fail
+    // (the failure pattern in the prediction plane)
+    int okm = ~(int)(info64 >> 36) & 63;
 #pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) x.pred[j] = a.predbuf[(int64_t)j * a.R + row];
+    for (int j = 0; j < RS_NOPT; ++j) okm &= ~((int)(__double_as_longlong(pred[j]) == kFailBits) << j);
+    const int validm = candm & okm;
+    long long key[RS_NOPT];
+    int above = 0, spos = 0;
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) {
+        key[j] = okey(pred[j]);
+        above |= (key[j] >= a.ktau) << j;
+        spos |= (key[j] > 0) << j;
+    }
+    above &= validm;
+    int bm[RS_NOPT];                           // bm[j]: candidates ranking before j
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
+#pragma unroll
+    for (int i = 0; i < RS_NOPT; ++i)
+#pragma unroll
+        for (int j = i + 1; j < RS_NOPT; ++j) {
+            if (key[i] >= key[j]) bm[j] |= 1 << i;
+            else bm[i] |= 1 << j;
+        }
+    uint32_t code = 0x0FFFFFF0u;
+    int rk = 0;
+    int pos[RS_NOPT];
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) {
+        pos[j] = __popc(bm[j] & above);
+        if (((above >> j) & 1) && pos[j] < a.k) {
+            code = (code & ~(0xFu << (4 + 4 * pos[j]))) | ((uint32_t)j << (4 + 4 * pos[j]));
+            rk |= 1 << j;
+        }
+    }
+    const int nrec = __popc(rk);
+    code = (code & ~0xFu) | (uint32_t)nrec;
+    a.rec_code[row] = code;
+    if (a.rec_pred) {                          // each chosen candidate writes its own slot
+        double* o = a.rec_pred + row * a.k;
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            if ((rk >> j) & 1) o[pos[j]] = pred[j];
+#pragma unroll
+        for (int x = 0; x < RS_NOPT; ++x)
+            if (x >= nrec && x < a.k) o[x] = nan_d();
+    }
+    if (a.pred_all)
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
+    const int known = info & 63, apos = (info >> 6) & 63;
+    const int scored = validm & known;
+    c.rows += 1;
+    c.pred += __popc(validm);
+    c.scored += __popc(scored);
+    c.sign += __popc(scored & ~(spos ^ apos));
+    c.rec += nrec;
+    c.reck += __popc(rk & scored);
+    c.rech += __popc(rk & scored & apos);
+    c.inv += __popc(candm & ~okm);
+    if (scored) {
+        int bp = 0;
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
+        int ba = -1;
+#pragma unroll
+        for (int x = 0; x < RS_NOPT; ++x) {
+            const int j = (info >> (12 + 3 * x)) & 7;
+            if (ba < 0 && ((scored >> j) & 1)) ba = j;
+        }
+        c.t1 += 1;
+        c.t1h += (bp == ba);
+    }
 }
 
-// One thread per test row (grid-stride).  All loads of a row are independent of each other
-// (one round trip), and the next row's loads are issued before the current row is ranked, so
-// each thread keeps two rows in flight.
-__global__ void __launch_bounds__(kRankThreads, 2)
+// Persistent blocks over tiles of 256 rows.  Thread 0 streams each tile -- the row records
+// and the six prediction planes, seven 1-D TMA bulk copies -- into a 3-stage shared-memory
+// ring (one mbarrier per stage); the threads read their row from shared memory, the stage
+// is refilled with the tile three ahead, and the row is ranked while those copies fly.
+// Bounded waits: on a timeout RS_ETIMEOUT is set, the copies still in flight are waited
+// for (bounded) and the block returns.
+__global__ void __launch_bounds__(kRankTile, 2)
 rank_pass_kernel(const RankPassArgs a) {
-    const int lane = threadIdx.x & 31;
-    uint32_t c_rows = 0, c_pred = 0, c_scored = 0, c_sign = 0, c_rec = 0, c_reck = 0, c_rech = 0;
-    uint32_t c_t1 = 0, c_t1h = 0, c_inv = 0;
+    extern __shared__ __align__(128) unsigned char rsm[];
+    const int tid = threadIdx.x;
     const int64_t total = a.rec_offsets[a.S];
     const int64_t nrows = total < a.R ? total : a.R;
-    if (total > a.R && blockIdx.x == 0 && threadIdx.x == 0) rs_dev_flag(a.dstatus, RS_EDATA, -3);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    RankRow cur;
-    if (row < nrows) load_rank_row(a, row, cur);
-    for (; row < nrows; row += stride) {
-        RankRow nxt;
-        if (row + stride < nrows) load_rank_row(a, row + stride, nxt);
-        const double* pred = cur.pred;
-        const uint32_t info = (uint32_t)cur.info;
-        const int mt = (int)(cur.info >> 30) & 63;
-        const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
-        int okm = 0;
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) okm |= (__double_as_longlong(pred[j]) != kFailBits) << j;
-        const int validm = candm & okm;
-        long long key[RS_NOPT];
-        int above = 0, spos = 0;
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) {
-            key[j] = okey(pred[j]);
-            above |= (key[j] >= a.ktau) << j;
-            spos |= (key[j] > 0) << j;
+    if (total > a.R && blockIdx.x == 0 && tid == 0) rs_dev_flag(a.dstatus, RS_EDATA, -3);
+    const int64_t ntiles = (nrows + kRankTile - 1) / kRankTile;
+    const uint32_t sbase = tc::smem_u32(rsm);
+    const uint32_t bar0 = sbase + (uint32_t)(kRankStages * kRankStageBytes);
+    if (tid == 0) {
+        for (int st = 0; st < kRankStages; ++st) tc::mbar_init(bar0 + 8 * st, 1);
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t tile, int st) {   // thread 0
+        const int64_t row0 = tile * kRankTile;
+        int64_t rows = nrows - row0 < kRankTile ? nrows - row0 : kRankTile;
+        rows = (rows + 1) & ~(int64_t)1;       // even: 16-byte multiple (stays inside the buffers)
+        const uint32_t bytes = (uint32_t)rows * 8;
+        const uint32_t bar = bar0 + 8 * st;
+        const uint32_t dst = sbase + (uint32_t)(st * kRankStageBytes);
+        tc::mbar_expect_tx(bar, bytes * kRankPlanes);
+        tc::bulk_load(dst, a.row_info + row0, bytes, bar);
+        for (int j = 0; j < RS_NOPT; ++j)
+            tc::bulk_load(dst + (uint32_t)((1 + j) * kRankTile * 8), a.predbuf + (int64_t)j * a.PS + row0, bytes, bar);
+    };
+    if (tid == 0)
+        for (int st = 0; st < kRankStages; ++st) {
+            const int64_t tile = blockIdx.x + (int64_t)st * gridDim.x;
+            if (tile < ntiles) issue(tile, st);
         }
-        above &= validm;
-        int bm[RS_NOPT];                       // bm[j]: candidates ranking before j
+    RankTally c;
+    int64_t i = 0;
+    bool failed = false;
+    for (;; ++i) {
+        const int64_t tile = blockIdx.x + i * gridDim.x;
+        if (tile >= ntiles) break;
+        const int st = (int)(i % kRankStages);
+        const uint32_t par = (uint32_t)((i / kRankStages) & 1);
+        const bool ok = tc::mbar_wait(bar0 + 8 * st, par, a.dstatus, -20);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const unsigned char* stage = rsm + st * kRankStageBytes;
+        const unsigned long long info = reinterpret_cast<const unsigned long long*>(stage)[tid];
+        double pred[RS_NOPT];
 #pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
-#pragma unroll
-        for (int i = 0; i < RS_NOPT; ++i)
-#pragma unroll
-            for (int j = i + 1; j < RS_NOPT; ++j) {
-                if (key[i] >= key[j]) bm[j] |= 1 << i;
-                else bm[i] |= 1 << j;
+        for (int j = 0; j < RS_NOPT; ++j)
+            pred[j] = reinterpret_cast<const double*>(stage + (1 + j) * kRankTile * 8)[tid];
+        __syncthreads();                       // the stage has been read: refill it
+        if (tid == 0) {
+            const int64_t next = tile + (int64_t)kRankStages * gridDim.x;
+            if (next < ntiles) {
+                tc::fence_proxy_async_smem();
+                issue(next, st);
             }
-        uint32_t code = 0x0FFFFFF0u;
-        int rk = 0;
-        int pos[RS_NOPT];
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) {
-            pos[j] = __popc(bm[j] & above);
-            if (((above >> j) & 1) && pos[j] < a.k) {
-                code = (code & ~(0xFu << (4 + 4 * pos[j]))) | ((uint32_t)j << (4 + 4 * pos[j]));
-                rk |= 1 << j;
+        }
+        const int64_t row = tile * kRankTile + tid;
+        if (row < nrows) rank_row(a, row, info, pred, c);
+    }
+    if (failed) {                              // drain this block's copies still in flight
+        if (tid == 0)
+            for (int64_t q = i; q < i + kRankStages; ++q) {   // tiles i .. i + 2 were issued
+                const int64_t tile = blockIdx.x + q * gridDim.x;
+                if (tile >= ntiles) break;
+                tc::mbar_wait(bar0 + 8 * (int)(q % kRankStages), (uint32_t)((q / kRankStages) & 1), a.dstatus, -21);
             }
-        }
-        const int c = __popc(rk);
-        code = (code & ~0xFu) | (uint32_t)c;
-        a.rec_code[row] = code;
-        if (a.rec_pred) {                      // each chosen candidate writes its own slot
-            double* o = a.rec_pred + row * a.k;
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j)
-                if ((rk >> j) & 1) o[pos[j]] = pred[j];
-#pragma unroll
-            for (int x = 0; x < RS_NOPT; ++x)
-                if (x >= c && x < a.k) o[x] = nan_d();
-        }
-        if (a.pred_all)
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j)
-                a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
-        const int known = info & 63, apos = (info >> 6) & 63;
-        const int scored = validm & known;
-        c_rows += 1;
-        c_pred += __popc(validm);
-        c_scored += __popc(scored);
-        c_sign += __popc(scored & ~(spos ^ apos));
-        c_rec += c;
-        c_reck += __popc(rk & scored);
-        c_rech += __popc(rk & scored & apos);
-        c_inv += __popc(candm & ~okm);
-        if (scored) {
-            int bp = 0;
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j)
-                if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
-            int ba = -1;
-#pragma unroll
-            for (int x = 0; x < RS_NOPT; ++x) {
-                const int j = (info >> (12 + 3 * x)) & 7;
-                if (ba < 0 && ((scored >> j) & 1)) ba = j;
-            }
-            c_t1 += 1;
-            c_t1h += (bp == ba);
-        }
-        cur = nxt;
+        __syncthreads();
+        return;
     }
     if (a.counters) {
-        const uint32_t vals[10] = {c_rows, c_pred, c_scored, c_sign, c_rec, c_reck, c_rech, c_t1, c_t1h, c_inv};
+        const uint32_t vals[10] = {c.rows, c.pred, c.scored, c.sign, c.rec, c.reck, c.rech, c.t1, c.t1h, c.inv};
         const int slot[10] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 13};
 #pragma unroll
-        for (int c = 0; c < 10; ++c) {
-            const uint32_t v = __reduce_add_sync(0xffffffffu, vals[c]);
-            if (lane == 0 && v) atomicAdd(a.counters + slot[c], (unsigned long long)v);
+        for (int q = 0; q < 10; ++q) {
+            const uint32_t v = __reduce_add_sync(0xffffffffu, vals[q]);
+            if ((tid & 31) == 0 && v) atomicAdd(a.counters + slot[q], (unsigned long long)v);
         }
     }
 }
@@ -1451,6 +1514,10 @@ struct FitWs {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Row stride of the six prediction planes: even, so that every plane starts on a 16-byte
+// boundary (the rank pass copies row ranges of the planes with TMA bulk copies).
+int64_t plane_stride(int64_t Rcap) { return (Rcap + 1) & ~(int64_t)1; }
+
 // histogram + bucket cursors (unsigned) and four 64-bit work counters, zeroed per call
 constexpr size_t kCounterBytes = 2 * kHist * sizeof(unsigned) + 4 * sizeof(unsigned long long);
 
@@ -1478,7 +1545,7 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.fit_off = (int64_t*)take(S6 * sizeof(int64_t));
     w.status = (uint8_t*)take(S6);
     w.coef = (double*)take(S6 * (size_t)(nmax + 1) * sizeof(double));
-    w.predbuf = (double*)take((size_t)RS_NOPT * Rcap * sizeof(double));
+    w.predbuf = (double*)take((size_t)RS_NOPT * plane_stride(Rcap) * sizeof(double));
     w.bytes = o;
     return w;
 }
@@ -1546,7 +1613,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                                      w.npair, w.cand, w.rowinfo, a.K, a.lambda, w.dlam, a.dstatus);
     mark(1);
     const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
-    plan_fits_kernel<<<blocks256, 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
+    plan_fits_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
                                                 a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
                                                 nmax, w.split_prog, a.rec_offsets,
                                                 a.rec_code ? a.rows_cap : 0,
@@ -1560,9 +1627,13 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
-                 a.rows_cap, a.flags, a.dstatus, a.Z, a.x_offsets, a.feat_width, a.max_feat};
-    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order, w.fit_off,
-                                                  status, user ? a.coef_out : nullptr, a.counters, sa);
+                 a.rows_cap, plane_stride(a.rows_cap), a.flags, a.dstatus, a.Z, a.x_offsets,
+                 a.feat_width, a.max_feat};
+    // compact records (and their offsets) only for fits without predictions or caller array
+    const bool need_off = !user && !rank;
+    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order,
+                                                  need_off ? w.fit_off : nullptr,
+                                                  status, user ? a.coef_out : nullptr, a.counters);
     mark(3);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1599,7 +1670,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                     if (e == cudaSuccess) e = launch_small<8, kNReg, 2>(sa, sms, S6, w1, st); break;
             case 8: e = launch_small<1, 8, 3>(sa, sms, S6, w0, st);
                     if (e == cudaSuccess) e = launch_small<9, kNReg, 2>(sa, sms, S6, w1, st); break;
-            default: e = launch_small<1, 6, 4>(sa, sms, S6, w0, st);
+            default: e = launch_small<1, 6, 5>(sa, sms, S6, w0, st);
                     if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, w1, st); break;
         }
         if (e != cudaSuccess) return e;
@@ -1619,16 +1690,22 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     }
     mark(5);
     if (rank) {
-        RankPassArgs ra{a.P, w.split_prog, a.row_offsets, a.masks, a.train_masks, a.S,
-                        a.rec_offsets, status, w.predbuf, a.rows_cap, w.rowinfo,
-                        w.row_info, a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all,
-                        a.counters};
+        RankPassArgs ra{a.rec_offsets, a.S, w.predbuf, a.rows_cap, plane_stride(a.rows_cap), w.row_info,
+                        a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all, a.counters};
         ra.ktau = okey_host(a.log_tau);
-        const int waves = a.tune_rank_waves > 0 ? a.tune_rank_waves : 16;
-        int64_t blocks = (a.rows_cap + kRankThreads - 1) / kRankThreads;
-        if (blocks > (int64_t)sms * waves) blocks = (int64_t)sms * waves;
+        e = cudaFuncSetAttribute(rank_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_pass_kernel, kRankTile, kRankSmem);
+        if (e != cudaSuccess) return e;
+        // persistent: tune_rank_waves (8, 16, 32) scales the resident blocks per SM by 1/4, 1/2, 1
+        int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        const int waves = a.tune_rank_waves > 0 ? a.tune_rank_waves : 32;
+        blocks = blocks * waves / 32;
+        const int64_t tiles = (a.rows_cap + kRankTile - 1) / kRankTile;
+        if (blocks > tiles) blocks = tiles;
         if (blocks < 1) blocks = 1;
-        rank_pass_kernel<<<(unsigned)blocks, kRankThreads, 0, st>>>(ra);
+        rank_pass_kernel<<<(unsigned)blocks, kRankTile, kRankSmem, st>>>(ra);
     }
     mark(6);
     return cudaGetLastError();

@@ -3,8 +3,8 @@
 // program p reads its kernel entries K_p[v_a][v_b] from this block (dual form of the
 // regression family of Sec. 3.4), so it is formed once per program, not once per fit.
 //
-// Grid: (program, chunk of 128 upper-triangle entries).  Entry e of a program (row-major
-// over a <= b) is computed by thread e % 128 of chunk e / 128: one dot product over all F
+// Grid: (program, chunk of 64 upper-triangle entries).  Entry e of a program (row-major
+// over a <= b) is computed by thread e % 64 of chunk e / 64: one dot product over all F
 // features, sequentially in f, from 64-feature slices of the program's rows staged in
 // shared memory.  Every FMA is one of the V (V + 1) / 2 * F the block needs (no padding
 // tiles); the mirrored entry is written by the same thread.
@@ -12,7 +12,7 @@
 
 namespace {
 
-constexpr int kGramThreads = 128;
+constexpr int kGramThreads = 64;
 constexpr int kGramSlice = 64;
 constexpr int kGramChunks = (RS_MAXV * (RS_MAXV + 1) / 2 + kGramThreads - 1) / kGramThreads;
 

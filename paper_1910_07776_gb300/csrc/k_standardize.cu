@@ -3,7 +3,8 @@
 //
 // The logarithm runs once per element on this part's narrow FP64 pipe, so it is written
 // here to need few FP64 instructions (log_pos below, 12 of them); X is read once, spread
-// over eight row groups per feature so that every SM has work.
+// over sixteen row groups per feature, in blocks small enough (16 features) that programs
+// of different sizes spread evenly over the SMs.
 #include "rs_internal.cuh"
 #include "rs_log_table.h"
 
@@ -57,13 +58,13 @@ __device__ __forceinline__ double as_double(float x) {
 }
 __device__ __forceinline__ double as_double(double x) { return x; }
 
-constexpr int kFeat = 32;                    // features per block (one warp-wide row slice)
-constexpr int kGroups = 8;                   // row groups per block
+constexpr int kFeat = 16;                    // features per block
+constexpr int kGroups = 16;                  // row groups per block
 constexpr int kThreads = kFeat * kGroups;
 
-// Block = (program, 32-feature slice); thread (g, f) takes rows g, g + 8, ... of feature f.
-// A warp reads 32 consecutive features of one row (coalesced).  The log values stay in
-// shared memory; per-feature sums are combined from the 8 row groups in a fixed order.
+// Block = (program, 16-feature slice); thread (g, f) takes rows g, g + 16, ... of feature f.
+// A warp reads 16 consecutive features of two rows (64-byte segments).  The log values stay in
+// shared memory; per-feature sums are combined from the 16 row groups in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __restrict__ fw,

@@ -85,7 +85,7 @@ rs_status rs_create(rs_ctx** out, int device, void* stream) {
     c->err[0] = 0;
     c->profiling = 0;
     c->tune_split = 6;
-    c->tune_rank_waves = 16;
+    c->tune_rank_waves = 32;
     for (int i = 0; i < RS_NSTAGE_EVENTS; ++i) c->ev[i] = nullptr;
     c->side = nullptr;
     c->fork = c->join = nullptr;

@@ -18,54 +18,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mbar.cuh"
 #include "rs_internal.cuh"
 
 namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;                       // one 128-byte swizzle row of BF16
-constexpr unsigned long long kWaitNs = 1000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtime() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: true when the phase completed, false (and RS_ETIMEOUT flagged) after 1 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, int site) {
-    if (mbar_try_wait(bar, phase)) return true;
-    const unsigned long long t0 = gtime();
-    for (;;) {
-        if (mbar_try_wait(bar, phase)) return true;
-        if (gtime() - t0 > kWaitNs) {
-            rs_dev_flag(err, RS_ETIMEOUT, site);
-            return false;
-        }
-    }
-}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
