@@ -227,13 +227,39 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         split_prog[s] = p;
         const uint64_t T = okV ? tm[s] & rs_full_mask(V) : 0ull;
         int emptym = 0;
+        // the program's pair tables (32 before / 32 after slots per optimization) come in as
+        // 16-byte vectors, all issued before the first is used
+        ulonglong2 vb[RS_NOPT][2], va[RS_NOPT][2];
+        int np[RS_NOPT];
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j) {
+            const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+            const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(pb + base);
+            const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(pa + base);
+            vb[j][0] = __ldg(b2);
+            vb[j][1] = __ldg(b2 + 1);
+            va[j][0] = __ldg(a2);
+            va[j][1] = __ldg(a2 + 1);
+            np[j] = okV ? npair[p * RS_NOPT + j] : 0;
+        }
+#pragma unroll
         for (int j = 0; j < RS_NOPT; ++j) {
             uint32_t pm = 0;
-            if (okV) {
-                const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-                const int np = npair[p * RS_NOPT + j];
-                for (int q = 0; q < np; ++q)
-                    pm |= (uint32_t)((T >> pb[base + q]) & (T >> pa[base + q]) & 1ull) << q;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (8 * w >= np[j]) break;
+                const unsigned long long wb = (w & 1) ? vb[j][w >> 1].y : vb[j][w >> 1].x;
+                const unsigned long long wa = (w & 1) ? va[j][w >> 1].y : va[j][w >> 1].x;
+                uint32_t part = 0;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const unsigned sb = (unsigned)(wb >> (8 * e)) & 63u;
+                    const unsigned sa = (unsigned)(wa >> (8 * e)) & 63u;
+                    part |= (uint32_t)((T >> sb) & (T >> sa) & 1ull) << e;
+                }
+                const int keep = np[j] - 8 * w;           // pairs of this word that exist
+                if (keep < 8) part &= (1u << keep) - 1u;
+                pm |= part << (8 * w);
             }
             int n = __popc(pm);
             if (n > nmax) {        // more pairs than the workspace was sized for

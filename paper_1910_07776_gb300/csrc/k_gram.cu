@@ -3,24 +3,42 @@
 // program p reads its kernel entries K_p[v_a][v_b] from this block (dual form of the
 // regression family of Sec. 3.4), so it is formed once per program, not once per fit.
 //
-// Grid: (program, chunk of 64 upper-triangle entries).  Entry e of a program (row-major
-// over a <= b) is computed by thread e % 64 of chunk e / 64: one dot product over all F
-// features, sequentially in f, from 64-feature slices of the program's rows staged in
-// shared memory.  Every FMA is one of the V (V + 1) / 2 * F the block needs (no padding
+// Grid: (program, chunk of 128 upper-triangle entries).  Entry e of a program (row-major
+// over a <= b) is computed by thread e % 128 of chunk e / 128: one dot product over all F
+// features, sequentially in f.  The program's rows come through shared memory in slices of
+// 32 features, double-buffered with cp.async (the next slice lands while the current one is
+// multiplied).  Every FMA is one of the V (V + 1) / 2 * F the block needs (no padding
 // tiles); the mirrored entry is written by the same thread.
 #include "rs_internal.cuh"
 
 namespace {
 
-constexpr int kGramThreads = 64;
-constexpr int kGramSlice = 64;
+constexpr int kGramThreads = 128;
+constexpr int kGramSlice = 32;
+constexpr int kGramLd = kGramSlice + 1;
 constexpr int kGramChunks = (RS_MAXV * (RS_MAXV + 1) / 2 + kGramThreads - 1) / kGramThreads;
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Issues the copies of features [f0, f0 + w) of the program's V rows into buffer Zs.
+__device__ __forceinline__ void stage_slice(double (*Zs)[kGramLd], const double* Zp, int V, int F, int f0, int w) {
+    for (int t = threadIdx.x; t < V * kGramSlice; t += kGramThreads) {
+        const int r = t / kGramSlice, c = t % kGramSlice;
+        if (c < w) cp_async8(&Zs[r][c], Zp + (int64_t)r * F + f0 + c);
+    }
+}
 
 __global__ void __launch_bounds__(kGramThreads)
 gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __restrict__ fw,
                 const int64_t* __restrict__ xo, const double* __restrict__ Z,
                 double* __restrict__ K, int* dstatus) {
-    __shared__ double Zs[RS_MAXV][kGramSlice + 1];
+    __shared__ double Zs[2][RS_MAXV][kGramLd];
     const int p = blockIdx.x;
     const int V = (int)(row_off[p + 1] - row_off[p]);
     if (V < 1 || V > RS_MAXV) {
@@ -39,19 +57,26 @@ gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __res
     const int b = a + rem;
     const int F = fw[p];
     const double* Zp = Z + xo[p];
+    const int nsl = (F + kGramSlice - 1) / kGramSlice;
+    stage_slice(Zs[0], Zp, V, F, 0, F < kGramSlice ? F : kGramSlice);
+    cp_async_commit();
     double acc = 0.0;
-    for (int f0 = 0; f0 < F; f0 += kGramSlice) {
+    for (int k = 0; k < nsl; ++k) {
+        const int f0 = k * kGramSlice;
         const int w = F - f0 < kGramSlice ? F - f0 : kGramSlice;
-        for (int t = threadIdx.x; t < V * kGramSlice; t += kGramThreads) {
-            const int r = t / kGramSlice, c = t % kGramSlice;
-            if (c < w) Zs[r][c] = Zp[(int64_t)r * F + f0 + c];
+        if (k + 1 < nsl) {
+            const int f1 = f0 + kGramSlice;
+            stage_slice(Zs[(k + 1) & 1], Zp, V, F, f1, F - f1 < kGramSlice ? F - f1 : kGramSlice);
         }
-        __syncthreads();
+        cp_async_commit();                  // (an empty group on the last slice)
+        cp_async_wait1();                   // slice k has landed (for this thread's copies)
+        __syncthreads();                    // ... and for everyone's
         if (act) {
+            const double (*S)[kGramLd] = Zs[k & 1];
 #pragma unroll 8
-            for (int c = 0; c < w; ++c) acc = fma(Zs[a][c], Zs[b][c], acc);
+            for (int c = 0; c < w; ++c) acc = fma(S[a][c], S[b][c], acc);
         }
-        __syncthreads();
+        __syncthreads();                    // buffer k & 1 is refilled in iteration k + 1
     }
     if (act) {
         double* Kp = K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
