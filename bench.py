@@ -222,7 +222,7 @@ def cpu_reference_sample(batch, splits, target_s, seed=1):
         r_, d_, n_ = run(int(min(splits.n_splits, max(threads, nxt))))
         rows, dt, n, chunks = rows + r_, dt + d_, n + n_, chunks + 1
         nxt = (target_s - dt) * n_ / max(d_, 1e-6)
-    return dict(value=rows / dt, unit=UNIT, cores=threads, kind="oracle",
+    return dict(value=rows / dt, unit=UNIT, cores=threads, kind="oracle", seconds=dt,
                 sample=f"{n} random splits of the {splits.n_splits} in {chunks} samples "
                        f"({rows} ranked rows), {dt:.1f} s of oracle wall time, FP64 primal normal "
                        f"equations, OpenMP over splits")
@@ -234,16 +234,15 @@ def run_reference(args, rank, world):
     batch, splits = make_inputs(CFG["seed"])
     for _ in range(args.warmup):
         cpu_reference_sample(batch, splits, args.ref_step_seconds, seed=7)
-    vals, cores, sample = [], None, None
-    t_all = 0.0
-    rows_all = 0
+    vals, cores, sample, secs = [], None, None, []
     for i in range(args.steps):
         c = cpu_reference_sample(batch, splits, args.ref_step_seconds, seed=100 + i)
         vals.append(c["value"])
+        secs.append(c["seconds"])
         cores, sample = c["cores"], c["sample"]
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, **{k: (list(v_) if isinstance(v_, tuple) else v_) for k, v_ in CFG.items()}},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -416,6 +415,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.only_step:
         cpu = cpu_reference_sample(batch, splits, args.cpu_seconds)
+        cpu.pop("seconds")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
