@@ -264,6 +264,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-ibk", action="store_true")
     ap.add_argument("--surrogate-epochs", type=int, default=2)
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
@@ -400,6 +401,10 @@ def main():
     e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
     ctx.profile_enable(False)
+    ibk = None
+    if rank == 0 and not args.only_step and not args.no_ibk:
+        ibk = run_ibk(rs, ctx, batch, splits, dev, stream, flush, args)
+
     unev = None
     if rank == 0 and not args.only_step and not args.no_uneven:
         unev = run_uneven(rs, ctx, dev, stream, flush, args)
@@ -435,6 +440,7 @@ def main():
         "surrogate_form": sur,
         "precision_form": prec,
         "uneven_form": unev,
+        "ibk_form": ibk,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -506,6 +512,55 @@ def run_plain(rs, ctx, batch, splits, dev, stream, flush, args):
     return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n,
             "launches_per_step": 6 * len(progs),
             "sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1)}
+
+
+def run_ibk(rs, ctx, batch, splits, dev, stream, flush, args):
+    """The instance-based learner (Sec. 3.4, IBK k = 10) beside ridge, through the one-call
+    step on the same inputs: the batched-CV workload (where most fits have at most 10 pairs,
+    so the mean of all labels is the prediction) and a leave-one-version-out workload over all
+    64 masks (31 pairs per fit: the 10-nearest selection decides every prediction)."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def measure(b, sp, reps):
+        db = rs.DeviceBatch.from_host(b, dev)
+        ds = rs.DeviceSplits.from_host(sp, dev, b)
+        R = ds.n_test_rows
+        ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+        res = {}
+        for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK)):
+            o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
+            step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
+                                       tau=CFG["tau"], flags=flags, rec_pred=o.rec_pred, counters=o.counters)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            o.counters.zero_()
+            tot = 0.0
+            for _ in range(reps):
+                flush.fill_(1)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ctx.check_device_status()
+            c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
+            ms = tot / reps
+            res[name] = {"ms": ms, "value": R / (ms * 1e-3), "unit": UNIT,
+                         "sign_accuracy": c[3] / max(c[2], 1), "top1_hit_rate": c[8] / max(c[7], 1),
+                         "rec_precision": c[6] / max(c[5], 1)}
+        res["recs_per_step"] = R
+        return res
+
+    out = {"neighbors": rs.IBK_NEIGHBORS,
+           "batched_cv": {"workload": WORKLOAD, **measure(batch, splits, 20)}}
+    b = synth.make_batch_fast(256, versions=64, feat=256, dtype=np.float32, seed=41)
+    sp = synth.make_splits(b, "lovo")
+    out["lovo"] = {"workload": "256 programs x 64 versions (all masks) x 256 f32 features, leave-one-"
+                               "version-out (16,384 splits, 98,304 fits of 31 pairs)", **measure(b, sp, 20)}
+    return out
 
 
 def run_uneven(rs, ctx, dev, stream, flush, args):

@@ -48,17 +48,21 @@ typedef enum {
 enum { RS_FIT_OK = 0, RS_FIT_EMPTY = 1, RS_FIT_NOTPD = 2, RS_FIT_NONFINITE = 3 };
 enum { RS_F32 = 0, RS_F64 = 1 };
 /* Gram precision: plain FP64 FMAs, or the BF16 hi/lo split on the tensor cores (three
- * BF16 products per term, FP32 accumulation in tensor memory).                         */
-enum { RS_GRAM_F64 = 0, RS_GRAM_BF16X3 = 1 };
+ * BF16 products per term, FP32 accumulation in tensor memory).  RS_GRAM_DIST2 makes the
+ * block of squared Euclidean distances instead, for the instance-based learner.         */
+enum { RS_GRAM_F64 = 0, RS_GRAM_BF16X3 = 1, RS_GRAM_DIST2 = 2 };
 /* Fit forms: the batched form (fits binned by size, one thread per small fit), or the
  * plain form (one warp per fit, lanes = matrix rows).  Both give the same results.     */
 enum { RS_FORM_BATCHED = 0, RS_FORM_PLAIN = 1 };
 /* Flags for rs_predict_rank. */
 enum {
     RS_RANK_ALL = 1,      /* rank all six optimizations, not only those not yet applied */
-    RS_REFINE_X = 2       /* one step of iterative refinement with residual and
+    RS_REFINE_X = 2,      /* one step of iterative refinement with residual and
                              predictions taken through Z (for an inexact Gram)        */
+    RS_MODEL_IBK = 4      /* the instance-based learner (IBK, k nearest neighbours)
+                             instead of ridge regression; K is the distance block    */
 };
+#define RS_IBK_NEIGHBORS 10  /* k of the instance-based learner (Sec. 3.4: k = 10)        */
 
 #define RS_NOPT 6
 #define RS_MAXV 64          /* versions per program (6-bit masks)                       */
@@ -147,7 +151,11 @@ rs_status rs_standardize(rs_ctx* ctx, const rs_batch* batch, double* Z, double* 
  * K ~ hi hi^T + hi lo^T + lo hi^T accumulated in FP32 -- relative error about 2^-16 per
  * entry; symmetric; needs rs_gram_workspace_bytes(std, precision) bytes of workspace,
  * 256-byte aligned, and at most 65535 programs per call).  Every ridge fit of a split reads
- * its kernel entries from this block (the dual form of the regression).             */
+ * its kernel entries from this block (the dual form of the regression).
+ * RS_GRAM_DIST2 (no workspace): K_p[a][b] = sum_f (Z[a][f] - Z[b][f])^2, the squared
+ * Euclidean distances of the instance-based learner (Sec. 3.4), each summed in ascending f
+ * with one rounding per subtraction, product and addition (no fused multiply-add), so the
+ * entries are those of the plain definition.                                          */
 size_t rs_gram_workspace_bytes(const rs_batch* std, int precision);
 rs_status rs_gram(rs_ctx* ctx, const rs_batch* std, int precision, double* K, void* workspace,
                   size_t workspace_bytes);
@@ -198,7 +206,12 @@ rs_status rs_fit_batched(rs_ctx* ctx, const rs_batch* std, const double* K,
  * iterative refinement of its bordered system with the residual computed from Z in FP64
  * (r_a = y_a - b - lambda alpha_a - z_a . beta, beta = sum_a alpha_a z_a), solved with the
  * same factor, and predictions are taken through Z (b + z_t . beta) -- for Gram blocks made
- * with RS_GRAM_BF16X3.  tau > 0.                                                      */
+ * with RS_GRAM_BF16X3.  RS_MODEL_IBK (batched form, coef == NULL, not with RS_REFINE_X; K
+ * from rs_gram with RS_GRAM_DIST2): the instance-based learner of Sec. 3.4 replaces the
+ * regression -- a fit is OK when it has a training pair; the prediction for test row t is
+ * the mean label of the RS_IBK_NEIGHBORS training pairs whose before versions are nearest
+ * to t (distance K[t][v_a]; equal distances take the lower pair first; all pairs when there
+ * are fewer), summed in ascending pair order.  lambda is ignored.  tau > 0.           */
 rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
                           const rs_splits* splits, double lambda, const double* coef,
                           int k, double tau, int flags, int form, void* workspace,
@@ -211,7 +224,8 @@ rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
  * given), plan rows into rec_offsets, then the batched fit/predict/rank.  workspace:
  * device memory of at least rs_cv_workspace_bytes(batch, splits) bytes, 256-byte
  * aligned, owned by the caller and used as scratch (Z, the Gram blocks and the fit
- * workspace).  Outputs as in rs_predict_rank.                                          */
+ * workspace).  Outputs as in rs_predict_rank.  With RS_MODEL_IBK the block is the
+ * distance block (precision RS_GRAM_F64 or RS_GRAM_DIST2).                             */
 size_t rs_cv_workspace_bytes(const rs_batch* batch, const rs_splits* splits);
 rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
                      double lambda, int k, double tau, int flags, int precision,
@@ -227,8 +241,9 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
  * while the graph exists; their contents may change between launches.  Counters are added
  * to on every launch.  The graph uses the launch parameters the context holds at capture.
  * rs_autotune times the batched step on this batch for each candidate launch configuration
- * (the size at which fits move to the register-heavier solver: 4..8; the rank pass grid: 8,
- * 16 or 32 blocks per SM), keeps the fastest in the context (used by every later batched
+ * (the size at which fits move to the register-heavier solver: 4..8; the rank pass's
+ * persistent grid: a quarter, half or all of its resident blocks, given as 8, 16, 32),
+ * keeps the fastest in the context (used by every later batched
  * call), and writes the times (ms, at most *n_times, in candidate order) if asked.
  * rs_get_tuning reports the context's current choice.                                 */
 typedef struct rs_graph rs_graph;

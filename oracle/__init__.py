@@ -32,6 +32,8 @@ COUNTER_NAMES = [
 ]
 FIT_OK, FIT_EMPTY, FIT_NOTPD, FIT_NONFINITE = 0, 1, 2, 3
 RANK_ALL = 1
+MODEL_IBK = 4
+IBK_NEIGHBORS = 10          # k of the instance-based learner (Sec. 3.4: k = 10)
 
 
 def build(force: bool = False) -> str:
@@ -65,7 +67,9 @@ def lib():
         L.orc_rec_offsets.argtypes = [C.c_int, P, P, P, P]
         L.orc_cv_batch.argtypes = [C.c_int, P, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double,
                                    C.c_int, C.c_double, C.c_int, C.c_double, P, P, P, P, P, P,
-                                   P, P, P, C.c_int]
+                                   P, P, P, C.c_int, C.c_int]
+        L.orc_ibk_predict.argtypes = [C.c_int, C.c_int, P, P, P, C.c_int]
+        L.orc_ibk_predict.restype = C.c_double
         L.orc_num_threads_available.restype = C.c_int
         _lib = L
     return _lib
@@ -148,8 +152,14 @@ def rec_offsets(batch, splits) -> np.ndarray:
 
 
 def cv_batch(batch, splits, lam: float = 1e-3, k: int = 3, tau: float = 1.05, flags: int = 0,
-             nthreads: int = 1, want_Z: bool = True) -> CVResult:
-    """Whole pass (standardize, pairs, fits, predictions, ranking, counters) for a batch."""
+             nthreads: int = 1, want_Z: bool = True, model: str = "ridge",
+             ibk_k: int = IBK_NEIGHBORS) -> CVResult:
+    """Whole pass (standardize, pairs, fits, predictions, ranking, counters) for a batch.
+    model "ridge" (Sec. 3.4 regression) or "ibk" (Sec. 3.4 instance-based, ibk_k nearest)."""
+    if model not in ("ridge", "ibk"):
+        raise ValueError("model must be 'ridge' or 'ibk'")
+    if model == "ibk":
+        flags |= MODEL_IBK
     L = lib()
     P = batch.n_programs
     fo = np.zeros(P + 1, dtype=np.int64)
@@ -176,10 +186,18 @@ def cv_batch(batch, splits, lam: float = 1e-3, k: int = 3, tau: float = 1.05, fl
                    _p(np.ascontiguousarray(splits.split_offsets)),
                    _p(np.ascontiguousarray(splits.train_masks)), float(lam), int(k),
                    float(np.log(tau)), int(flags), EPS, _p(Z), _p(mu), _p(sg), _p(fs), _p(ro),
-                   _p(code), _p(rp), _p(pa), _p(cnt), int(nthreads))
+                   _p(code), _p(rp), _p(pa), _p(cnt), int(nthreads), int(ibk_k))
     return CVResult(Z=Z, mu=mu, sigma=sg, fit_status=fs.reshape(S, N_OPT), rec_offsets=ro,
                     rec_code=code, rec_pred=rp.reshape(R, k), pred_all=pa.reshape(R, N_OPT),
                     counters=cnt)
+
+
+def ibk_predict(Zrows, y, zt, k: int = IBK_NEIGHBORS) -> float:
+    """Sec. 3.4 IBK for one test vector: mean label of the k nearest training rows."""
+    Zrows = np.ascontiguousarray(Zrows, dtype=np.float64)
+    n, F = Zrows.shape
+    return float(lib().orc_ibk_predict(n, F, _p(Zrows), _p(np.ascontiguousarray(y, dtype=np.float64)),
+                                       _p(np.ascontiguousarray(zt, dtype=np.float64)), int(k)))
 
 
 def decode_rec(code: np.ndarray):

@@ -13,7 +13,9 @@
  *            feature vector of the "before" version, labelled with the log speedup
  *            log t(before) - log t(after);
  *   Sec. 3.4 the regression family: ridge regression with an unpenalised intercept,
- *            solved from the primal normal equations with a textbook Cholesky;
+ *            solved from the primal normal equations with a textbook Cholesky; or
+ *   Sec. 3.4 the instance-based learner IBK: the k = 10 training instances nearest to the
+ *            test vector by Euclidean distance, their labels combined into the prediction;
  *   Sec. 5   evaluation: test versions are those outside the split's training set; each
  *            gets one predicted speedup per optimization it does not already contain;
  *   Sec. 2   Tier 3 sorts by expected benefit, keeps those at or above a threshold and
@@ -28,7 +30,11 @@
  *   - candidates are the optimizations not yet in the test version (a flag ranks all 6);
  *   - ties in predicted speedup rank the lower optimization index first;
  *   - the threshold is compared in log space, inclusive (pred >= log tau);
- *   - "gain" means log speedup > 0 for both predicted and actual values.
+ *   - "gain" means log speedup > 0 for both predicted and actual values;
+ *   - IBK: distances between z-scored feature vectors; the "mode" of the neighbours'
+ *     labels, which are continuous log speedups, is read as their mean (summed in pair
+ *     order); equal distances take the lower pair index first; fewer than k training
+ *     pairs use all of them.
  *
  * All arithmetic is double precision, in plain loops, with no blocking or reordering
  * beyond the definitions above.
@@ -47,6 +53,7 @@
 #define ORC_FIT_NOTPD 2
 #define ORC_FIT_NONFINITE 3
 #define ORC_RANK_ALL 1
+#define ORC_MODEL_IBK 4
 #define ORC_NCOUNTERS 16
 
 /* ---------------------------------------------------------------------------------- */
@@ -191,6 +198,42 @@ int orc_ridge_fit(int n, int F, const double* Zrows, const double* y, double lam
 /* Sec. 2 Tier 3: order candidate optimizations by predicted log speedup (descending;
  * equal values keep the lower index first), keep those >= log_tau, report at most k.
  * pred[6] with valid[6] flags.  Writes the chosen indices into idx; returns the count. */
+/* Sec. 3.4, IBK: the prediction for test vector zt from n training rows Zrows [n][F] with
+ * labels y: squared Euclidean distances d_a = sum_f (zt_f - z_a,f)^2, the kn nearest
+ * (insertion into a list ordered by (d, a), so equal distances keep the lower index first),
+ * and the mean of their labels, summed in ascending index a.  n must be >= 1.        */
+double orc_ibk_predict(int n, int F, const double* Zrows, const double* y, const double* zt, int kn) {
+    int sel[64];
+    double sd[64];
+    int m = 0;
+    for (int a = 0; a < n; ++a) {
+        double d = 0.0;
+        for (int f = 0; f < F; ++f) {
+            double e = zt[f] - Zrows[(size_t)a * F + f];
+            d += e * e;
+        }
+        /* insert (d, a) after every kept entry with distance <= d */
+        int pos = m;
+        while (pos > 0 && sd[pos - 1] > d) --pos;
+        if (pos >= kn) continue;
+        int last = m < kn ? m : kn - 1;
+        for (int q = last; q > pos; --q) {
+            sd[q] = sd[q - 1];
+            sel[q] = sel[q - 1];
+        }
+        sd[pos] = d;
+        sel[pos] = a;
+        if (m < kn) ++m;
+    }
+    int chosen[64];
+    for (int a = 0; a < n; ++a) chosen[a] = 0;
+    for (int q = 0; q < m; ++q) chosen[sel[q]] = 1;
+    double sum = 0.0;
+    for (int a = 0; a < n; ++a)
+        if (chosen[a]) sum += y[a];
+    return sum / m;
+}
+
 int orc_rank(const double* pred, const int* valid, int k, double log_tau, int* idx) {
     int order[ORC_NOPT];
     int m = 0;
@@ -260,7 +303,7 @@ void orc_cv_batch(int P, const int64_t* row_offsets, const int32_t* feat_width,
                   const uint64_t* train_masks, double lambda, int k, double log_tau,
                   int flags, double eps, double* Z_out, double* mu_out, double* sigma_out,
                   uint8_t* fit_status, const int64_t* rec_offsets, uint32_t* rec_code,
-                  double* rec_pred, double* pred_all, uint64_t* counters, int nthreads) {
+                  double* rec_pred, double* pred_all, uint64_t* counters, int nthreads, int ibk_k) {
     (void)nthreads;
     int64_t S = split_offsets[P];
     uint64_t* per_split = (uint64_t*)calloc((size_t)(S > 0 ? S : 1) * ORC_NCOUNTERS, sizeof(uint64_t));
@@ -301,19 +344,28 @@ void orc_cv_batch(int P, const int64_t* row_offsets, const int32_t* feat_width,
             double bias[ORC_NOPT];
             int ok[ORC_NOPT];
             double* work = (double*)malloc(sizeof(double) * ((size_t)F * F + 2 * (size_t)F));
-            double* Zr = (double*)malloc(sizeof(double) * 64 * (size_t)F);
-            double yv[64];
+            /* the training pairs of each optimization: before-version rows and labels */
+            double* Zr = (double*)malloc(sizeof(double) * ORC_NOPT * 64 * (size_t)F);
+            double yv[ORC_NOPT][64];
+            int nj[ORC_NOPT];
+            const int ibk = (flags & ORC_MODEL_IBK) != 0;
             for (int j = 0; j < ORC_NOPT; ++j) {
                 int n = 0;
+                double* Zj = Zr + (size_t)j * 64 * F;
                 for (int q = 0; q < np_[j]; ++q) {
                     int v = pb[j][q], w = pa[j][q];
                     if (((T >> v) & 1) && ((T >> w) & 1)) {
-                        memcpy(Zr + (size_t)n * F, Z + (size_t)v * F, sizeof(double) * F);
-                        yv[n] = lt[v] - lt[w];   /* log speedup of adding j (Sec. 5) */
+                        memcpy(Zj + (size_t)n * F, Z + (size_t)v * F, sizeof(double) * F);
+                        yv[j][n] = lt[v] - lt[w];   /* log speedup of adding j (Sec. 5) */
                         ++n;
                     }
                 }
-                int st = orc_ridge_fit(n, F, Zr, yv, lambda, beta + (size_t)j * F, &bias[j], work);
+                nj[j] = n;
+                int st;
+                if (ibk)   /* IBK stores the instances; a model exists when there is one */
+                    st = n > 0 ? ORC_FIT_OK : ORC_FIT_EMPTY;
+                else
+                    st = orc_ridge_fit(n, F, Zj, yv[j], lambda, beta + (size_t)j * F, &bias[j], work);
                 ok[j] = (st == ORC_FIT_OK);
                 if (fit_status) fit_status[s * ORC_NOPT + j] = (uint8_t)st;
                 cnt[9 + st] += 1;
@@ -334,8 +386,13 @@ void orc_cv_batch(int P, const int64_t* row_offsets, const int32_t* feat_width,
                         cnt[13] += 1;
                         continue;
                     }
-                    double yh = bias[j];
-                    for (int f = 0; f < F; ++f) yh += Z[(size_t)t * F + f] * beta[(size_t)j * F + f];
+                    double yh;
+                    if (ibk) {
+                        yh = orc_ibk_predict(nj[j], F, Zr + (size_t)j * 64 * F, yv[j], Z + (size_t)t * F, ibk_k);
+                    } else {
+                        yh = bias[j];
+                        for (int f = 0; f < F; ++f) yh += Z[(size_t)t * F + f] * beta[(size_t)j * F + f];
+                    }
                     pred[j] = yh;
                     valid[j] = 1;
                     cnt[1] += 1;

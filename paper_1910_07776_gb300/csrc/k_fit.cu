@@ -17,7 +17,8 @@
 //   plan   -> per fit, the mask of its training pairs and its size n; histogram of n;
 //   bucket -> a counting sort of all fits of the batch by n;
 //   solve  -> n <= kNReg: one fit per thread, fully unrolled for that n, registers only;
-//             n >  kNReg: one fit per warp, lanes = matrix rows;
+//             kNReg < n <= kNMid: one fit per thread, factor in shared memory;
+//             n >  kNMid: one fit per warp, lanes = matrix rows;
 //   rank   -> per chunk of splits of one program: predictions, sort, threshold, top-k,
 //             scores; comparisons on order-preserving integer keys (no FP64 compares).
 // Reciprocal square roots of the pivots come from an FP32 seed refined by two Newton
@@ -35,6 +36,7 @@ constexpr int kChunk = 16;                  // splits per work item of the rank 
 constexpr int kFits = kChunk * RS_NOPT;
 constexpr int kKld = RS_MAXV + 1;           // padded row stride of K in shared memory
 constexpr int kNReg = 10;                   // largest n solved by one thread in registers
+constexpr int kNMid = 16;                   // largest n solved by one thread from shared memory
 constexpr int kHist = RS_MAXPAIRS + 2;      // n = 0..32, plus one end slot
 constexpr long long kNaNBits = 0x7ff8000000000000ll;
 
@@ -631,6 +633,96 @@ solve_small_kernel(const SolveArgs a, unsigned long long* work) {
     }
 }
 
+// ====================================================================== IBK (Sec. 3.4)
+constexpr int kIbkK = RS_IBK_NEIGHBORS;
+
+// The instance-based learner, one fit per thread (bucket order, dynamic work, largest n
+// first).  K is the distance block D_p[t][v] = |z_t - z_v|^2.  For each candidate test row t,
+// the kIbkK training pairs whose before versions are nearest to t are kept in a list ordered
+// by (distance, pair index) -- distances are non-negative, so their bit patterns order like
+// the values, and a pair replaces the list's last entry only when strictly nearer -- and the
+// prediction is the mean of their labels, summed in ascending pair index.  With at most
+// kIbkK pairs every pair is a neighbour, whatever t, so the mean is formed once.
+__global__ void __launch_bounds__(128)
+ibk_kernel(const SolveArgs a, int nmax, unsigned long long* work) {
+    __shared__ long long start[kHist], cstart[kHist];
+    bucket_tables(a.hist, start, cstart);
+    const long long lo = start[1], hi = start[nmax + 1];
+    unsigned long long got = take32(work);
+    long long base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+    while (base < hi) {
+        got = take32(work);
+        const long long pos = hi - 1 - (base - lo) - (threadIdx.x & 31);
+        const bool active = pos >= lo;
+        if (active) {
+            int n = 1;
+            while (start[n + 1] <= pos) ++n;
+            const int64_t f = a.order[pos];
+            const int64_t s = f / RS_NOPT;
+            const int j = (int)(f - s * RS_NOPT);
+            const int p = a.split_prog[s];
+            const double* Dp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+            const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+            const uint32_t pm = a.fit_pm[f];
+            const double* yl = a.ylab + pbase;
+            PredTarget pt;
+            if (pred_target(a, s, j, p, pt)) {
+                if (n <= kIbkK) {
+                    double sum = 0.0;
+                    for (uint32_t x = pm; x; x &= x - 1) sum += yl[__ffs(x) - 1];
+                    const double mean = sum / (double)n;
+                    for (uint64_t cm = pt.cand; cm; cm &= cm - 1) {
+                        const int t = __ffsll((long long)cm) - 1;
+                        const int r = __popcll(pt.test & ((1ull << t) - 1ull));
+                        if (r < pt.room) pt.dst[r] = mean;
+                    }
+                } else {
+                    const uint8_t* pb = a.pb + pbase;
+                    for (uint64_t cm = pt.cand; cm; cm &= cm - 1) {
+                        const int t = __ffsll((long long)cm) - 1;
+                        const double* Dt = Dp + t * RS_GRAM_LD;
+                        unsigned long long kd[kIbkK];
+                        int kq[kIbkK];
+#pragma unroll
+                        for (int i = 0; i < kIbkK; ++i) {
+                            kd[i] = ~0ull;
+                            kq[i] = 0;
+                        }
+                        for (uint32_t x = pm; x; x &= x - 1) {
+                            const int q = __ffs(x) - 1;
+                            const unsigned long long d = (unsigned long long)__double_as_longlong(__ldg(Dt + pb[q]));
+                            if (d < kd[kIbkK - 1]) {
+                                // insertion into the ordered list, from the old values
+#pragma unroll
+                                for (int i = kIbkK - 1; i > 0; --i) {
+                                    const bool shift = kd[i - 1] > d;
+                                    const bool here = !shift && kd[i] > d;
+                                    kd[i] = shift ? kd[i - 1] : (here ? d : kd[i]);
+                                    kq[i] = shift ? kq[i - 1] : (here ? q : kq[i]);
+                                }
+                                if (kd[0] > d) {
+                                    kd[0] = d;
+                                    kq[0] = q;
+                                }
+                            }
+                        }
+                        uint32_t chosen = 0;
+#pragma unroll
+                        for (int i = 0; i < kIbkK; ++i) chosen |= 1u << kq[i];
+                        double sum = 0.0;
+                        for (uint32_t x = chosen; x; x &= x - 1) sum += yl[__ffs(x) - 1];
+                        const int r = __popcll(pt.test & ((1ull << t) - 1ull));
+                        if (r < pt.room) pt.dst[r] = sum / (double)kIbkK;
+                    }
+                }
+            }
+            finish_record(a, f, n, RS_FIT_OK, a.coef_user ? a.coef + f * RS_COEF_STRIDE : nullptr);
+        }
+        count_status(a, RS_FIT_OK, active);
+        base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+    }
+}
+
 // One fit of kNReg < n <= nmax pairs per thread, the same arithmetic as solve_fixed with
 // run-time loops.  The factor and the work vectors live in shared memory, element-major
 // across the 32 lanes of the warp (element e of this lane at W[32 e]): every access of a
@@ -932,10 +1024,102 @@ __device__ int fit_warp(int n, uint32_t pm, const uint8_t* pair_b, const double*
     return RS_FIT_OK;
 }
 
+// One fit per warp for the batched form without refinement: lane a owns row a (a < n <= 32)
+// of M = K_TT + lambda I = L D L^T (unit lower L, no square roots), factored left-looking in
+// shared memory.  Lsh holds L ([32][33]); Ush holds U = L D by rows, the operand every lane
+// reads when a column is formed: s_i = M_i,j - sum_m L_i,m U_j,m, d_j = s_j, L_i,j = s_i / d_j,
+// U_i,j = s_i.  Then t_y = L^-1 y, t_1 = L^-1 1 (one FMA per lane per step each), b = t_1^T D^-1
+// t_y / t_1^T D^-1 t_1 and alpha = L^-T D^-1 (t_y - b t_1), the solve_fixed arithmetic with
+// lanes for rows.  Predictions: one candidate row per lane.  Returns a warp-uniform status.
+__device__ int fit_warp_ldl(int n, uint32_t pm, const uint8_t* pair_b, const double* ylab, const double* K,
+                            const double* dl, double* Lsh, double* Ush, double* coef, const PredTarget* pt) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < n;
+    int v = 0;
+    double y = 0.0;
+    if (act) {
+        const int q = select_bit(pm, lane);
+        v = pair_b[q];
+        y = ylab[q];
+    }
+    for (int b = 0; b < n; ++b) {            // row a of M below the diagonal: independent loads
+        const int vb = __shfl_sync(0xffffffffu, v, b);
+        if (act && b < lane) Lsh[lane * 33 + b] = __ldg(K + v * RS_GRAM_LD + vb);
+    }
+    double dinv = 0.0;                       // lane a: 1 / d_a
+    __syncwarp();
+    for (int jj = 0; jj < n; ++jj) {
+        double sv = 0.0;
+        if (act && lane >= jj) {
+            sv = lane == jj ? __ldg(dl + v) : Lsh[lane * 33 + jj];
+            for (int m = 0; m < jj; ++m) sv = fma(-Lsh[lane * 33 + m], Ush[jj * 33 + m], sv);
+        }
+        const double d = __shfl_sync(0xffffffffu, sv, jj);
+        if (!pos_finite(d)) return RS_FIT_NOTPD;
+        const double r = rcp_newton(d);
+        if (lane == jj) dinv = r;
+        else if (act && lane > jj) {
+            Lsh[lane * 33 + jj] = sv * r;
+            Ush[lane * 33 + jj] = sv;
+        }
+        __syncwarp();
+    }
+    double ty = y, t1 = act ? 1.0 : 0.0;
+    for (int kk = 0; kk < n; ++kk) {         // L t = rhs, unit diagonal
+        const double yk = __shfl_sync(0xffffffffu, ty, kk);
+        const double ok = __shfl_sync(0xffffffffu, t1, kk);
+        if (act && lane > kk) {
+            const double l = Lsh[lane * 33 + kk];
+            ty = fma(-l, yk, ty);
+            t1 = fma(-l, ok, t1);
+        }
+    }
+    const double sc = act ? t1 * dinv : 0.0;
+    double num = act ? sc * ty : 0.0, den = act ? sc * t1 : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    const double b = num * rcp_newton(den);
+    double al = act ? fma(-b, t1, ty) * dinv : 0.0;
+    for (int kk = n - 1; kk >= 0; --kk) {    // L^T alpha = D^-1 (t_y - b t_1)
+        const double ak = __shfl_sync(0xffffffffu, al, kk);
+        if (lane < kk) al = fma(-Lsh[kk * 33 + lane], ak, al);
+    }
+    const int fin = __all_sync(0xffffffffu, !act || finite_bits(al)) && finite_bits(b);
+    if (coef) {
+        if (act) coef[1 + lane] = al;
+        if (lane == 0) coef[0] = b;
+    }
+    __syncwarp();
+    if (!fin) return RS_FIT_NONFINITE;
+    if (pt) {                                // predictions, one candidate row per lane
+        const int nc = __popcll(pt->cand);
+        for (int r0 = 0; r0 < nc; r0 += 32) {
+            const bool mine = r0 + lane < nc;
+            int t = 0;
+            if (mine) t = select_bit(pt->cand, r0 + lane);
+            double yh = b;
+            for (int q = 0; q < n; ++q) {
+                const double aq = __shfl_sync(0xffffffffu, al, q);
+                const int vq = __shfl_sync(0xffffffffu, v, q);
+                if (mine) yh = fma(aq, __ldg(K + t * RS_GRAM_LD + vq), yh);
+            }
+            if (mine) {
+                const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+                if (r < pt->room) pt->dst[r] = yh;
+            }
+        }
+    }
+    return RS_FIT_OK;
+}
+
 constexpr int kLargeWarps = 4;
 
-// Dynamic shared memory: Lsh [4][32*33] doubles, then with refinement per warp: beta [Fmax],
-// coefficients [64] doubles, pair slots [32] ints.
+// Dynamic shared memory: Lsh [4][32*33] doubles, then without refinement Ush [4][32*33]
+// (fit_warp_ldl), with refinement per warp: beta [Fmax], coefficients [64] doubles, pair
+// slots [32] ints (fit_warp).
 __global__ void __launch_bounds__(kLargeWarps * 32)
 solve_large_kernel(const SolveArgs a) {
     __shared__ long long start[kHist], cstart[kHist];
@@ -945,8 +1129,9 @@ solve_large_kernel(const SolveArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* Lsh = Lall + warp * 32 * 33;
     const bool refine = (a.flags & RS_REFINE_X) != 0;
+    double* Ush = Lall + (kLargeWarps + warp) * 32 * 33;   // without refinement only
     double* rbase = Lall + kLargeWarps * 32 * 33 + (int64_t)warp * (a.max_feat + 64 + 16);
-    const long long first = refine ? start[1] : start[kNReg + 1], end = start[RS_MAXPAIRS + 1];
+    const long long first = refine ? start[1] : start[kNMid + 1], end = start[RS_MAXPAIRS + 1];
     for (long long pos = first + (long long)blockIdx.x * kLargeWarps + warp; pos < end;
          pos += (long long)gridDim.x * kLargeWarps) {
         int n = 1;
@@ -968,8 +1153,10 @@ solve_large_kernel(const SolveArgs a) {
             rc.sh = rbase + a.max_feat;
             rc.vsh = reinterpret_cast<int*>(rbase + a.max_feat + 64);
         }
-        const int st = fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
-                                a.lambda, Lsh, out, pt, refine ? &rc : nullptr);
+        const int st = refine ? fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
+                                         a.lambda, Lsh, out, pt, &rc)
+                              : fit_warp_ldl(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp,
+                                             a.dlam + (int64_t)p * RS_MAXV, Lsh, Ush, out, pt);
         if (lane == 0) {
             if (st != RS_FIT_OK && pt) mark_failed(*pt);
             finish_record(a, f, n, st, out);
@@ -1665,25 +1852,43 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool refine = (a.flags & RS_REFINE_X) != 0;
-    if (!refine) {
-        // n > kNReg: one fit per thread from shared memory.  With a side stream it runs
-        // beside the register solvers (which take their work dynamically, so they lose
-        // nothing to it); without one it runs first.
-        // Three solvers over disjoint ranges of the bucket order.  The shared-memory solver
-        // (n > kNReg, few fits, latency-bound) runs on the side stream when there is one, beside
-        // the two register solvers (n <= split, then split < n <= kNReg) on the call's stream;
-        // all three take their work dynamically, so the one sharing the SMs with the others
-        // costs neither of them a statically assigned share.
+    if (a.flags & RS_MODEL_IBK) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ibk_kernel, 128, 0);
+        if (e != cudaSuccess) return e;
+        int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        const int64_t need = (S6 + 127) / 128;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        ibk_kernel<<<(unsigned)grid, 128, 0, st>>>(sa, nmax, w.work + 3);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        mark(4);
+    } else if (!refine) {
+        // Solvers over disjoint ranges of the bucket order.  The larger fits -- one thread per
+        // fit from shared memory for kNReg < n <= kNMid (four warps per block fit), one warp per
+        // fit above that (a thread's factor would no longer leave room for more than one warp
+        // per SM) -- run on the side stream when there is one, beside the two register solvers
+        // (n <= split, then split < n <= kNReg) on the call's stream; all take their work
+        // dynamically, so the kernels sharing the SMs cost none of them a statically assigned
+        // share.
         const bool mid = nmax > kNReg;
         const bool fork = mid && a.side && a.fork && a.join;
+        cudaStream_t s2 = fork ? a.side : st;
         if (fork) {
             e = cudaEventRecord(a.fork, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(a.side, a.fork, 0);
-            if (e == cudaSuccess) e = launch_mid(sa, sms, nmax, w.work + 2, a.side);
-            if (e == cudaSuccess) e = cudaEventRecord(a.join, a.side);
-        } else if (mid) {
-            e = launch_mid(sa, sms, nmax, w.work + 2, st);
         }
+        if (e == cudaSuccess && mid) e = launch_mid(sa, sms, nmax < kNMid ? nmax : kNMid, w.work + 2, s2);
+        if (e == cudaSuccess && nmax > kNMid) {
+            const size_t lsmem = (size_t)2 * kLargeWarps * 32 * 33 * sizeof(double);
+            e = cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+            if (e == cudaSuccess) {
+                solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, lsmem, s2>>>(sa);
+                e = cudaGetLastError();
+            }
+        }
+        if (e == cudaSuccess && fork) e = cudaEventRecord(a.join, a.side);
         if (e != cudaSuccess) return e;
         unsigned long long* w0 = w.work;
         unsigned long long* w1 = w.work + 1;

@@ -34,6 +34,10 @@ __device__ __forceinline__ void stage_slice(double (*Zs)[kGramLd], const double*
     }
 }
 
+// DIST = false: K_p[a][b] = sum_f z_a,f z_b,f (FMA chain).  DIST = true: the squared
+// Euclidean distance sum_f (z_a,f - z_b,f)^2 with one rounding per subtraction, product and
+// addition (no contraction), in ascending f -- the plain definition's arithmetic.
+template <bool DIST>
 __global__ void __launch_bounds__(kGramThreads)
 gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __restrict__ fw,
                 const int64_t* __restrict__ xo, const double* __restrict__ Z,
@@ -73,8 +77,16 @@ gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __res
         __syncthreads();                    // ... and for everyone's
         if (act) {
             const double (*S)[kGramLd] = Zs[k & 1];
+            if constexpr (DIST) {
 #pragma unroll 8
-            for (int c = 0; c < w; ++c) acc = fma(S[a][c], S[b][c], acc);
+                for (int c = 0; c < w; ++c) {
+                    const double e = __dsub_rn(S[a][c], S[b][c]);
+                    acc = __dadd_rn(acc, __dmul_rn(e, e));
+                }
+            } else {
+#pragma unroll 8
+                for (int c = 0; c < w; ++c) acc = fma(S[a][c], S[b][c], acc);
+            }
         }
         __syncthreads();                    // buffer k & 1 is refilled in iteration k + 1
     }
@@ -89,7 +101,14 @@ gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __res
 
 cudaError_t rs_launch_gram_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st) {
     dim3 grid((unsigned)b->n_programs, kGramChunks);
-    gram_f64_kernel<<<grid, kGramThreads, 0, st>>>(b->n_programs, b->row_offsets, b->feat_width,
+    gram_f64_kernel<false><<<grid, kGramThreads, 0, st>>>(b->n_programs, b->row_offsets, b->feat_width,
+                                            b->x_offsets, (const double*)b->X, K, dstatus);
+    return cudaGetLastError();
+}
+
+cudaError_t rs_launch_dist2_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st) {
+    dim3 grid((unsigned)b->n_programs, kGramChunks);
+    gram_f64_kernel<true><<<grid, kGramThreads, 0, st>>>(b->n_programs, b->row_offsets, b->feat_width,
                                             b->x_offsets, (const double*)b->X, K, dstatus);
     return cudaGetLastError();
 }

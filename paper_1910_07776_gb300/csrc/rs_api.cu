@@ -215,6 +215,8 @@ rs_status rs_gram(rs_ctx* c, const rs_batch* b, int precision, double* K, void* 
     cudaError_t e;
     if (precision == RS_GRAM_F64) {
         e = rs_launch_gram_f64(b, K, c->dstatus, c->stream);
+    } else if (precision == RS_GRAM_DIST2) {
+        e = rs_launch_dist2_f64(b, K, c->dstatus, c->stream);
     } else if (precision == RS_GRAM_BF16X3) {
         const size_t need = rs_gram_workspace_bytes(b, precision);
         if (!ws || ws_bytes < need) return fail(c, RS_ENOMEM, "the tensor-core Gram needs %zu bytes of workspace", need);
@@ -222,7 +224,7 @@ rs_status rs_gram(rs_ctx* c, const rs_batch* b, int precision, double* K, void* 
         if (b->n_programs > 65535) return fail(c, RS_EINVAL, "the tensor-core Gram takes at most 65535 programs per call");
         e = rs_launch_gram_bf16x3_ws(b, K, ws, ws_bytes, c->dstatus, c->stream);
     } else {
-        return fail(c, RS_EINVAL, "precision must be RS_GRAM_F64 or RS_GRAM_BF16X3");
+        return fail(c, RS_EINVAL, "precision must be RS_GRAM_F64, RS_GRAM_BF16X3 or RS_GRAM_DIST2");
     }
     if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "rs_gram: cuTensorMapEncodeTiled unavailable");
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_gram");
@@ -335,7 +337,9 @@ rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const r
     }
     if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
-    if (flags & ~(RS_RANK_ALL | RS_REFINE_X)) return fail(c, RS_EINVAL, "unknown flag bits");
+    if (flags & ~(RS_RANK_ALL | RS_REFINE_X | RS_MODEL_IBK)) return fail(c, RS_EINVAL, "unknown flag bits");
+    if ((flags & RS_MODEL_IBK) && (form != RS_FORM_BATCHED || coef || (flags & RS_REFINE_X)))
+        return fail(c, RS_EINVAL, "RS_MODEL_IBK needs the batched form, coef = NULL and no RS_REFINE_X");
     if ((flags & RS_REFINE_X) && (form != RS_FORM_BATCHED || coef))
         return fail(c, RS_EINVAL, "RS_REFINE_X needs the batched form and refits in the call (coef = NULL)");
     if ((flags & RS_REFINE_X) && b->max_feat > 4096) return fail(c, RS_EINVAL, "RS_REFINE_X: max_feat <= 4096");
@@ -451,6 +455,11 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
     rs_batch zb = *b;
     zb.X = Z;
     zb.dtype = RS_F64;
+    if (flags & RS_MODEL_IBK) {
+        if (precision != RS_GRAM_F64 && precision != RS_GRAM_DIST2)
+            return fail(c, RS_EINVAL, "RS_MODEL_IBK takes precision RS_GRAM_F64 or RS_GRAM_DIST2");
+        precision = RS_GRAM_DIST2;
+    }
     s = rs_gram(c, &zb, precision, K, fws, ws_bytes - zbytes - kbytes);
     if (s != RS_OK) return s;
     s = rs_rec_offsets(c, &zb, sp, rec_offsets);

@@ -39,6 +39,7 @@ __device__ __forceinline__ uint64_t rs_full_mask(int V) {
 cudaError_t rs_launch_standardize(const rs_batch* b, double* Z, double* mu, double* sigma,
                                   int* dstatus, cudaStream_t st);
 cudaError_t rs_launch_gram_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st);
+cudaError_t rs_launch_dist2_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st);
 size_t rs_gram_tc_workspace_bytes(int64_t P, int max_feat);
 cudaError_t rs_launch_gram_bf16x3_ws(const rs_batch* b, double* K, void* ws, size_t ws_bytes, int* dstatus,
                                      cudaStream_t st);

@@ -19,9 +19,10 @@ SO = os.path.join(HERE, "_build", "librs.so")
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EUNSUPPORTED, RS_EDATA = range(7)
 RS_F32, RS_F64 = 0, 1
-RS_GRAM_F64, RS_GRAM_BF16X3 = 0, 1
+RS_GRAM_F64, RS_GRAM_BF16X3, RS_GRAM_DIST2 = 0, 1, 2
 RS_FORM_BATCHED, RS_FORM_PLAIN = 0, 1
-RS_RANK_ALL, RS_REFINE_X = 1, 2
+RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK = 1, 2, 4
+IBK_NEIGHBORS = 10
 NOPT = 6
 COEF_STRIDE = 33
 GRAM_LD = 64
@@ -473,7 +474,10 @@ def alloc_outputs(n_rows_total: int, n_splits: int, k: int, device="cuda", pred_
 
 def cv_run(ctx: Context, b: DeviceBatch, s: DeviceSplits, lam=1e-3, k=3, tau=1.05, flags=0,
            precision=RS_GRAM_F64, form=RS_FORM_BATCHED, want_pred_all=True, want_Z=False):
-    """The whole pass through the individual entry points; returns host numpy outputs."""
+    """The whole pass through the individual entry points; returns host numpy outputs.
+    With RS_MODEL_IBK in flags the block is the distance block (RS_GRAM_DIST2)."""
+    if flags & RS_MODEL_IBK:
+        precision = RS_GRAM_DIST2
     dev = b.X.device
     Z = torch.empty(b.x_elems, dtype=torch.float64, device=dev)
     mu = torch.empty(b.feat_total, dtype=torch.float64, device=dev)
