@@ -269,7 +269,8 @@ rs_status rs_gemm_bf16(rs_ctx* ctx, const void* A, int64_t lda, const void* B, i
                        float* D, int64_t ldd, int M, int N, int K);
 
 /* ---- A7: the learned surrogate (not in the paper) -------------------------------------------
- * An MLP 256 -> 512 -> 512 -> 6 with GELU (u * Phi(u)) maps a standardized feature vector to
+ * An MLP 256 -> 512 -> 512 -> 6 with GELU (tanh form: u (1 + tanh(sqrt(2/pi) (u + 0.044715
+ * u^3))) / 2) maps a standardized feature vector to
  * the six predicted log speedups -- a learned stand-in for the tier-2 predictor (Sec. 2),
  * trained on labels that the plain ridge predictor produces.  BF16 weights and activations
  * on the tcgen05 tensor cores with FP32 accumulation, FP32 master weights, AdamW (beta1
@@ -285,7 +286,8 @@ rs_status rs_gemm_bf16(rs_ctx* ctx, const void* A, int64_t lda, const void* B, i
  * wrapping around; cfg->steps optimizer steps (0: only the feature statistics and the BF16
  * weight copies are prepared).  use_graph = 1 captures one step in a CUDA graph and replays
  * it.  loss_curve (nullable, float [steps]) gets each minibatch's loss.
- * rs_surrogate_infer: pred [n][6] (float, nullable); ood_score [n] (nullable) = mean over
+ * rs_surrogate_infer: X 16-byte aligned (RS_EINVAL otherwise; it is read with 16-byte
+ * loads); pred [n][6] (float, nullable); ood_score [n] (nullable) = mean over
  * features of ((x - mean) / std)^2 against the training statistics; used_fallback [n]
  * (nullable) = 1 where ood_score > ood_threshold (those rows should be predicted by the
  * plain method).  With rec_code (nullable) the six outputs of each row are also ranked as

@@ -7,7 +7,8 @@ The surrogate (not in the paper; a learned stand-in for the tier-2 predictor of 
 a standardized feature vector straight to the six per-optimization log speedups:
 
     h1 = gelu(W1 x + b1),  h2 = gelu(W2 h1 + b2),  out = W3 h2 + b3,
-    gelu(u) = u * Phi(u)  (Phi: standard normal CDF, the exact form),
+    gelu(u) = u (1 + tanh(c (u + a u^3))) / 2,  c = sqrt(2 / pi),  a = 0.044715
+    (the tanh form of GELU, Hendrycks and Gimpel 2016, within 1e-3 of u * Phi(u)),
 
 trained on the mean squared error  L = sum_{b, j} (out_bj - y_bj)^2 / (B * 6)  with AdamW
 (bias-corrected first and second moments, decoupled weight decay).  Shapes: W1 [512, 256],
@@ -26,18 +27,22 @@ DIMS = (256, 512, 512, 6)
 NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
 
 
-def _erf(x: np.ndarray) -> np.ndarray:
-    return np.vectorize(math.erf, otypes=[np.float64])(x)
+GELU_C = math.sqrt(2.0 / math.pi)
+GELU_A = 0.044715
 
 
 def gelu(u: np.ndarray) -> np.ndarray:
-    """u * Phi(u), Phi(u) = (1 + erf(u / sqrt 2)) / 2."""
-    return u * 0.5 * (1.0 + _erf(u / math.sqrt(2.0)))
+    """The tanh form: u (1 + tanh(c (u + a u^3))) / 2."""
+    u = np.asarray(u, dtype=np.float64)
+    return 0.5 * u * (1.0 + np.tanh(GELU_C * (u + GELU_A * u ** 3)))
 
 
 def gelu_grad(u: np.ndarray) -> np.ndarray:
-    """d/du [u Phi(u)] = Phi(u) + u phi(u),  phi(u) = exp(-u^2 / 2) / sqrt(2 pi)."""
-    return 0.5 * (1.0 + _erf(u / math.sqrt(2.0))) + u * np.exp(-0.5 * u * u) / math.sqrt(2.0 * math.pi)
+    """d/du of the tanh form: (1 + t) / 2 + u (1 - t^2) c (1 + 3 a u^2) / 2,
+    t = tanh(c (u + a u^3))."""
+    u = np.asarray(u, dtype=np.float64)
+    t = np.tanh(GELU_C * (u + GELU_A * u ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * u * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * u * u)
 
 
 def init_params(seed: int = 0, dims=DIMS) -> Dict[str, np.ndarray]:

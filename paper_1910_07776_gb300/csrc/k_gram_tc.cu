@@ -77,12 +77,6 @@ cudaError_t rs_launch_gram_bf16x3_ws(const rs_batch* b, double* K, void* ws, siz
     cudaError_t e = rs_make_tmap_bf16_3d(&ta, A, P, RS_MAXV, 3 * Fp, 3 * Fp, tc::BM);
     if (e == cudaSuccess) e = rs_make_tmap_bf16_3d(&tb, B, P, RS_MAXV, 3 * Fp, 3 * Fp, RS_MAXV);
     if (e != cudaSuccess) return e;
-    constexpr int BN = 64, S = 4;
-    auto kern = tc::gemm_kernel<BN, S, EpiGram, true>;
-    const int smem = tc::Layout<BN, S>::kBytes;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<dim3(1, 1, (unsigned)P), 128, smem, st>>>(ta, tb, RS_MAXV, RS_MAXV, 3 * Fp,
-                                                     EpiGram{b->row_offsets, K}, dstatus);
-    return cudaGetLastError();
+    return tc::gemm_launch<64, 4, EpiGram, true>(ta, tb, RS_MAXV, RS_MAXV, 3 * Fp, (int)P,
+                                                  EpiGram{b->row_offsets, K}, dstatus, st);
 }

@@ -42,9 +42,26 @@ struct Blob {
     static constexpr int64_t nFloats = oCount + 64;
 };
 
-__device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f)); }
+// GELU in its tanh form (Hendrycks and Gimpel 2016): gelu(u) = u (1 + tanh(c (u + a u^3))) / 2,
+// c = sqrt(2 / pi), a = 0.044715, with the hardware tanh (tanh.approx.f32, relative error
+// about 2^-11, below the BF16 rounding of the activations): eight FP32 instructions and one
+// special-function instruction, so the epilogue stays near the tensor cores' pace.
+constexpr float kGeluC = 0.7978845608028654f;
+constexpr float kGeluA = 0.044715f;
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu_f(float u) {
+    const float t = tanh_hw(kGeluC * fmaf(kGeluA * u * u, u, u));
+    return 0.5f * u * (1.0f + t);
+}
+// d/du: (1 + t) / 2 + u (1 - t^2) c (1 + 3 a u^2) / 2
 __device__ __forceinline__ float gelu_grad_f(float u) {
-    return 0.5f * (1.0f + erff(u * 0.70710678118654752f)) + u * 0.39894228040143268f * expf(-0.5f * u * u);
+    const float u2 = u * u;
+    const float t = tanh_hw(kGeluC * fmaf(kGeluA * u2, u, u));
+    return 0.5f * (1.0f + t) + 0.5f * u * (1.0f - t * t) * kGeluC * fmaf(3.0f * kGeluA, u2, 1.0f);
 }
 
 // ---- epilogues ---------------------------------------------------------------------------------
@@ -56,11 +73,24 @@ struct EpiHidden {           // U = acc + b (FP32, optional); H = gelu(U) (BF16)
     int64_t ldt;             // rows of the batch (leading dimension of H^T)
     __device__ void operator()(int row, int col0, const float (&v)[16]) const {
         alignas(16) __nv_bfloat16 hb[16];
+        alignas(16) float u[16];
+        const float4* b4 = reinterpret_cast<const float4*>(bias + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 b = __ldg(b4 + q);
+            u[4 * q] = v[4 * q] + b.x;
+            u[4 * q + 1] = v[4 * q + 1] + b.y;
+            u[4 * q + 2] = v[4 * q + 2] + b.z;
+            u[4 * q + 3] = v[4 * q + 3] + b.w;
+        }
+        if (U) {
+            float4* d = reinterpret_cast<float4*>(U + (int64_t)row * kHid + col0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = reinterpret_cast<const float4*>(u)[q];
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const float u = v[i] + bias[col0 + i];
-            if (U) U[(int64_t)row * kHid + col0 + i] = u;
-            hb[i] = __float2bfloat16(gelu_f(u));
+            hb[i] = __float2bfloat16(gelu_f(u[i]));
             if (Ht) Ht[(int64_t)(col0 + i) * ldt + row] = hb[i];
         }
         uint4* dst = reinterpret_cast<uint4*>(H + (int64_t)row * kHid + col0);
@@ -162,9 +192,13 @@ struct EpiGeluGrad {         // dU = acc * gelu'(U): BF16 dU (optional) and dU^T
     int64_t ldt;
     __device__ void operator()(int row, int col0, const float (&v)[16]) const {
         alignas(16) __nv_bfloat16 g[16];
+        alignas(16) float u[16];
+        const float4* u4 = reinterpret_cast<const float4*>(U + (int64_t)row * kHid + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(u)[q] = u4[q];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            g[i] = __float2bfloat16(v[i] * gelu_grad_f(U[(int64_t)row * kHid + col0 + i]));
+            g[i] = __float2bfloat16(v[i] * gelu_grad_f(u[i]));
             dUt[(int64_t)(col0 + i) * ldt + row] = g[i];
         }
         if (dU) {
@@ -175,52 +209,64 @@ struct EpiGeluGrad {         // dU = acc * gelu'(U): BF16 dU (optional) and dU^T
     }
 };
 
-struct EpiF32 {              // plain FP32 store (weight gradients)
+struct EpiF32Part {          // split-K partial of a weight gradient: slice z -> D + z * zstride
+                             // (N, ldd, zstride multiples of 16: whole 16-column chunks)
+    float* D;
+    int64_t ldd;
+    int64_t zstride;
+    int N;
+    __device__ void operator()(int z, int row, int col0, const float (&v)[16]) const {
+        float4* d = reinterpret_cast<float4*>(D + (int64_t)z * zstride + (int64_t)row * ldd + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+};
+
+struct EpiF32 {              // plain FP32 store (weight gradients; N, ldd multiples of 16)
     float* D;
     int64_t ldd;
     int N;
     __device__ void operator()(int row, int col0, const float (&v)[16]) const {
+        float4* d = reinterpret_cast<float4*>(D + (int64_t)row * ldd + col0);
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (col0 + i < N) D[(int64_t)row * ldd + col0 + i] = v[i];
+        for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
 };
 
-template <int BN, class Epi>
+// Pipeline depth of the persistent GEMM (one CTA per SM): four 32 KB stages (BN = 128).
+constexpr int kStages = 4;
+
+template <int BN, int S, class Epi>
 cudaError_t gemm_attr();
 
-bool graph_capturing(cudaStream_t st) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+template <int BN, class Epi, bool BATCHED = false>
+cudaError_t gemm_attr() {
+    return cudaFuncSetAttribute(tc::gemm_kernel<BN, kStages, Epi, BATCHED>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Layout<BN, kStages>::kBytes);
 }
 
+// The function attributes of every product of a training step, set before a graph capture.
 cudaError_t all_attrs() {
     cudaError_t e = gemm_attr<128, EpiHidden>();
     if (e == cudaSuccess) e = gemm_attr<32, EpiOutput>();
     if (e == cudaSuccess) e = gemm_attr<128, EpiGeluGrad>();
     if (e == cudaSuccess) e = gemm_attr<128, EpiF32>();
+    if (e == cudaSuccess) e = gemm_attr<128, EpiF32Part, true>();
     return e;
 }
 
+// Split-K product over `slices` K ranges (rank-3 maps from rs_make_tmap_bf16_kslices): batch z
+// is range z; the epilogue gets z.
 template <int BN, class Epi>
-cudaError_t gemm_attr() {
-    constexpr int S = 4;
-    return cudaFuncSetAttribute(tc::gemm_kernel<BN, S, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc::Layout<BN, S>::kBytes);
+cudaError_t gemm_slices(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int Kslice, int slices,
+                        const Epi& epi, int* err, cudaStream_t st) {
+    return tc::gemm_launch<BN, kStages, Epi, true>(ta, tb, M, N, Kslice, slices, epi, err, st);
 }
 
 template <int BN, class Epi>
 cudaError_t gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const Epi& epi, int* err,
                  cudaStream_t st) {
-    constexpr int S = 4;
-    auto kern = tc::gemm_kernel<BN, S, Epi>;
-    const int smem = tc::Layout<BN, S>::kBytes;
-    cudaError_t e = cudaSuccess;
-    if (!graph_capturing(st)) e = gemm_attr<BN, Epi>();
-    if (e != cudaSuccess) return e;
-    dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
-    kern<<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
-    return cudaGetLastError();
+    return tc::gemm_launch<BN, kStages, Epi>(ta, tb, M, N, K, 1, epi, err, st);
 }
 
 // ---- small kernels -----------------------------------------------------------------------------
@@ -249,6 +295,82 @@ stage_kernel(const double* __restrict__ X, const double* __restrict__ Yin, int64
     }
 }
 
+// double -> BF16 and double -> float with integer operations only (this part's double
+// conversions run on its narrow FP64 pipe).  BF16: round to nearest, ties to even, on the 52
+// fraction bits; float: truncated fraction (used for the OOD score).  Values outside the
+// normal float range take the conversion instructions.
+__device__ __forceinline__ bool f32_normal_range(long long b) {
+    const int e = (int)((b >> 52) & 0x7ff);
+    return e > 1023 - 126 && e < 1023 + 127;
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_of(double x) {
+    const long long b = __double_as_longlong(x);
+    if (!f32_normal_range(b)) return __float2bfloat16((float)x);
+    const unsigned long long u = (unsigned long long)b;
+    // keep 7 fraction bits: round on bit 45, ties to even on bit 45 of the kept part
+    const unsigned long long r = u + ((1ull << 44) - 1ull) + ((u >> 45) & 1ull);
+    const unsigned long long m = (r >> 45) & 0x7full;                // 7 fraction bits
+    const int e = (int)((r >> 52) & 0x7ff) - 1023 + 127;             // carry may bump the exponent
+    const unsigned short h = (unsigned short)(((u >> 63) << 15) | ((unsigned)e << 7) | (unsigned)m);
+    return __ushort_as_bfloat16(h);
+}
+__device__ __forceinline__ float f32_trunc_of(double x) {
+    const long long b = __double_as_longlong(x);
+    if (!f32_normal_range(b)) return (float)x;
+    const unsigned long long u = (unsigned long long)b;
+    const unsigned e = (unsigned)((u >> 52) & 0x7ff) - 1023u + 127u;
+    return __uint_as_float((unsigned)((u >> 63) << 31) | (e << 23) | (unsigned)((u >> 29) & 0x7fffff));
+}
+
+// Inference staging: rows of X (double [n][256]) -> BF16 X_s, one warp per row (lane l takes
+// features 8l .. 8l+7: 64 contiguous bytes in, 16 out), grid-stride over the chunk; with the
+// training statistics given, the same pass forms the out-of-distribution score (mean over
+// features of ((x - mean) / sd)^2, FP32) and the fallback flag of each row.
+__global__ void __launch_bounds__(256)
+infer_stage_kernel(const double* __restrict__ X, int64_t B, __nv_bfloat16* Xs, const float* __restrict__ mean,
+                   const float* __restrict__ sd, float thr, float* score, uint8_t* fallback) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    float mu[8], sinv[8];                    // per feature: mean and 1 / sd (0 where sd = 0)
+    if (mean) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            mu[e] = mean[8 * lane + e];
+            const float d = sd[8 * lane + e];
+            sinv[e] = d > 0.f ? 1.0f / d : 0.f;
+        }
+    }
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < B; r += wstride) {
+        const double2* src = reinterpret_cast<const double2*>(X + r * kIn + 8 * lane);
+        double x[8];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const double2 v = __ldcs(src + e);       // read once: streaming
+            x[2 * e] = v.x;
+            x[2 * e + 1] = v.y;
+        }
+        alignas(16) __nv_bfloat16 hb[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) hb[e] = bf16_of(x[e]);
+        *reinterpret_cast<uint4*>(Xs + r * kIn + 8 * lane) = *reinterpret_cast<const uint4*>(hb);
+        if (mean) {
+            float s = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float d = (f32_trunc_of(x[e]) - mu[e]) * sinv[e];
+                s = fmaf(d, d, s);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                s /= kIn;
+                if (score) score[r] = s;
+                if (fallback) fallback[r] = s > thr ? 1 : 0;
+            }
+        }
+    }
+}
+
 // Row sums of a transposed gradient [rows][B] (BF16) -> FP32 bias gradient; one warp per row.
 __global__ void __launch_bounds__(256)
 rowsum_kernel(const __nv_bfloat16* __restrict__ T, int rows, int B, float* out) {
@@ -259,6 +381,22 @@ rowsum_kernel(const __nv_bfloat16* __restrict__ T, int rows, int B, float* out) 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[w] = s;
+}
+
+// Sum of the split-K partials of the three weight gradients, slice 0 first (a fixed order,
+// so every step and every graph replay adds the same numbers the same way).  The partials
+// of one slice are laid out [W1 | W2 | W3] (nW1 + nW2 + nW3 floats).
+__global__ void __launch_bounds__(256)
+reduce_wgrad_kernel(const float* __restrict__ part, int slices, float* G) {
+    constexpr int64_t n = Blob::nW1 + Blob::nW2 + Blob::nW3;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int z = 0; z < slices; ++z) s += part[(int64_t)z * n + i];
+    const int64_t o = i < Blob::nW1 ? Blob::oW1 + i
+                    : i < Blob::nW1 + Blob::nW2 ? Blob::oW2 + (i - Blob::nW1)
+                                                : Blob::oW3 + (i - Blob::nW1 - Blob::nW2);
+    G[o] = s;
 }
 
 // BF16 copies of the master weights: W1, W2, W3 (padded rows) and the transposes W2^T, W3^T.
@@ -327,34 +465,24 @@ __global__ void feature_stats_finish(const double* acc, int64_t n, float* mean, 
     sd[f] = (float)sqrt(fmax(acc[kIn + f] / n - m * m, 0.0));
 }
 
-// OOD score = mean over features of ((x - mean) / sd)^2; rows above the threshold fall back.
-__global__ void __launch_bounds__(256)
-ood_kernel(const double* __restrict__ X, int64_t n, const float* mean, const float* sd, float thr,
-           float* score, uint8_t* fallback) {
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= n) return;
-    float s = 0.f;
-    for (int f = lane; f < kIn; f += 32) {
-        const float d = sd[f] > 0.f ? ((float)X[r * kIn + f] - mean[f]) / sd[f] : 0.f;
-        s += d * d;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-        s /= kIn;
-        if (score) score[r] = s;
-        if (fallback) fallback[r] = s > thr ? 1 : 0;
-    }
-}
-
 // ---- training workspace --------------------------------------------------------------------------
 struct TrainWs {
     __nv_bfloat16 *Xs, *Xt, *H1, *H1t, *H2, *H2t, *dO, *dOt, *dU2, *dU2t, *dU1t;
     float *Ys, *U1, *U2;
     double* stats_acc;
+    float* part;              // split-K partials of the weight gradients (slices > 1)
+    int slices;
     size_t bytes;
 };
+
+// K ranges of the weight-gradient products (K = the minibatch rows): the largest power of two
+// up to 16 that leaves at least 256 rows per range in whole 64-row blocks.  A few output tiles
+// then spread over up to 16x as many CTAs.
+int wgrad_slices(int B) {
+    int s = 1;
+    while (s < 16 && B % (64 * 2 * s) == 0 && B / (2 * s) >= 256) s *= 2;
+    return s;
+}
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -379,12 +507,17 @@ TrainWs carve_train(void* base, int B) {
     w.U1 = (float*)take((size_t)B * kHid * sizeof(float));
     w.U2 = (float*)take((size_t)B * kHid * sizeof(float));
     w.stats_acc = (double*)take(2 * kIn * sizeof(double));
+    w.slices = wgrad_slices(B);
+    w.part = w.slices > 1 ? (float*)take((size_t)w.slices * (Blob::nW1 + Blob::nW2 + Blob::nW3) * sizeof(float))
+                          : nullptr;
     w.bytes = o;
     return w;
 }
 
 struct Maps {
     CUtensorMap Xs, W1, H1, W2, H2, W3, dO, W3t, dU2, W2t, dOt, H2t, dU2t, H1t, dU1t, Xt;
+    // split-K views of the transposed operands of the weight gradients (slices > 1)
+    CUtensorMap sdOt, sH2t, sdU2t, sH1t, sdU1t, sXt;
 };
 
 cudaError_t make_maps(Maps& m, const TrainWs& w, const __nv_bfloat16* bf, int B) {
@@ -408,6 +541,17 @@ cudaError_t make_maps(Maps& m, const TrainWs& w, const __nv_bfloat16* bf, int B)
     mk(&m.H1t, w.H1t, kHid, B, 128);
     mk(&m.dU1t, w.dU1t, kHid, B, 128);
     mk(&m.Xt, w.Xt, kIn, B, 128);
+    if (w.slices > 1) {
+        auto ks = [&](CUtensorMap* t, const void* p, int64_t rows, int box) {
+            if (e == cudaSuccess) e = rs_make_tmap_bf16_kslices(t, p, rows, B, B, w.slices, box);
+        };
+        ks(&m.sdOt, w.dOt, kOutP, 128);
+        ks(&m.sH2t, w.H2t, kHid, 128);
+        ks(&m.sdU2t, w.dU2t, kHid, 128);
+        ks(&m.sH1t, w.H1t, kHid, 128);
+        ks(&m.sdU1t, w.dU1t, kHid, 128);
+        ks(&m.sXt, w.Xt, kIn, 128);
+    }
     return e;
 }
 
@@ -429,12 +573,30 @@ cudaError_t step_body(float* blob, const TrainWs& w, const Maps& m, int B, float
         e = gemm<128>(m.dO, m.W3t, B, kHid, kOutP, EpiGeluGrad{w.U2, w.dU2, w.dU2t, B}, err, st);
     if (e == cudaSuccess)      // dU1 = (dU2 W2) * gelu'(U1)
         e = gemm<128>(m.dU2, m.W2t, B, kHid, kHid, EpiGeluGrad{w.U1, nullptr, w.dU1t, B}, err, st);
-    if (e == cudaSuccess)      // dW3 = dO^T H2
-        e = gemm<128>(m.dOt, m.H2t, kOutP, kHid, B, EpiF32{G + Blob::oW3, kHid, kHid}, err, st);
-    if (e == cudaSuccess)      // dW2 = dU2^T H1
-        e = gemm<128>(m.dU2t, m.H1t, kHid, kHid, B, EpiF32{G + Blob::oW2, kHid, kHid}, err, st);
-    if (e == cudaSuccess)      // dW1 = dU1^T X
-        e = gemm<128>(m.dU1t, m.Xt, kHid, kIn, B, EpiF32{G + Blob::oW1, kIn, kIn}, err, st);
+    if (w.slices > 1) {        // weight gradients split over K ranges, then summed in order
+        constexpr int64_t nPart = Blob::nW1 + Blob::nW2 + Blob::nW3;
+        const int S = w.slices, ks = B / S;
+        if (e == cudaSuccess)  // dW3 = dO^T H2
+            e = gemm_slices<128>(m.sdOt, m.sH2t, kOutP, kHid, ks, S,
+                                                EpiF32Part{w.part + Blob::nW1 + Blob::nW2, kHid, nPart, kHid}, err, st);
+        if (e == cudaSuccess)  // dW2 = dU2^T H1
+            e = gemm_slices<128>(m.sdU2t, m.sH1t, kHid, kHid, ks, S,
+                                                EpiF32Part{w.part + Blob::nW1, kHid, nPart, kHid}, err, st);
+        if (e == cudaSuccess)  // dW1 = dU1^T X
+            e = gemm_slices<128>(m.sdU1t, m.sXt, kHid, kIn, ks, S,
+                                                EpiF32Part{w.part, kIn, nPart, kIn}, err, st);
+        if (e == cudaSuccess) {
+            reduce_wgrad_kernel<<<(unsigned)((nPart + 255) / 256), 256, 0, st>>>(w.part, S, G);
+            e = cudaGetLastError();
+        }
+    } else {
+        if (e == cudaSuccess)  // dW3 = dO^T H2
+            e = gemm<128>(m.dOt, m.H2t, kOutP, kHid, B, EpiF32{G + Blob::oW3, kHid, kHid}, err, st);
+        if (e == cudaSuccess)  // dW2 = dU2^T H1
+            e = gemm<128>(m.dU2t, m.H1t, kHid, kHid, B, EpiF32{G + Blob::oW2, kHid, kHid}, err, st);
+        if (e == cudaSuccess)  // dW1 = dU1^T X
+            e = gemm<128>(m.dU1t, m.Xt, kHid, kIn, B, EpiF32{G + Blob::oW1, kIn, kIn}, err, st);
+    }
     if (e == cudaSuccess) {
         rowsum_kernel<<<(kOut * 32 + 255) / 256, 256, 0, st>>>(w.dOt, kOut, B, G + Blob::ob3);
         rowsum_kernel<<<(kHid * 32 + 255) / 256, 256, 0, st>>>(w.dU2t, kHid, B, G + Blob::ob2);
@@ -568,7 +730,12 @@ cudaError_t rs_launch_surrogate_infer(const float* blob, const double* X, int64_
         if (e == cudaSuccess) e = rs_make_tmap_bf16(&tH2, H2, B, kHid, kHid, 128);
         if (e == cudaSuccess) e = rs_make_tmap_bf16(&tW3, bf + Blob::bW3, kOutP, kHid, kHid, 32);
         if (e != cudaSuccess) break;
-        stage_kernel<<<B, 256, 0, st>>>(X + r0 * kIn, nullptr, n - r0, B, nullptr, 0, Xs, nullptr, nullptr);
+        const bool ood = score || fallback;
+        const int sblocks = (int)((B + 7) / 8) < 4096 ? (int)((B + 7) / 8) : 4096;
+        infer_stage_kernel<<<sblocks, 256, 0, st>>>(X + r0 * kIn, B, Xs, ood ? blob + Blob::oStats : nullptr,
+                                                     blob + Blob::oStats + kIn, ood_thr,
+                                                     score ? score + r0 : nullptr,
+                                                     fallback ? fallback + r0 : nullptr);
         e = gemm<128>(tX, tW1, B, kHid, kIn, EpiHidden{blob + Blob::ob1, nullptr, H1, nullptr, B}, err, st);
         if (e == cudaSuccess)
             e = gemm<128>(tH1, tW2, B, kHid, kHid, EpiHidden{blob + Blob::ob2, nullptr, H2, nullptr, B}, err, st);
@@ -579,12 +746,6 @@ cudaError_t rs_launch_surrogate_infer(const float* blob, const double* X, int64_
                                    (float)log(tau), rec_code ? rec_code + r0 : nullptr,
                                    rec_pred ? rec_pred + r0 * k : nullptr},
                          err, st);
-    }
-    if (e == cudaSuccess && (score || fallback)) {
-        ood_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(X, n, blob + Blob::oStats,
-                                                                      blob + Blob::oStats + kIn, ood_thr, score,
-                                                                      fallback);
-        e = cudaGetLastError();
     }
     return e;
 }

@@ -413,6 +413,7 @@ rs_status rs_surrogate_infer(rs_ctx* c, const float* blob, const double* X, int6
         return fail(c, RS_EINVAL, "ranking: k in 1..6, tau > 0, flags RS_RANK_ALL only");
     if (n < 1 || chunk_rows < 16 || chunk_rows % 8) return fail(c, RS_EINVAL, "n >= 1, chunk_rows >= 16, multiple of 8");
     if ((uintptr_t)blob % 256 || (uintptr_t)ws % 256) return fail(c, RS_EINVAL, "blob and workspace must be 256-byte aligned");
+    if ((uintptr_t)X % 16) return fail(c, RS_EINVAL, "X must be 16-byte aligned");
     if (ws_bytes < rs_surrogate_infer_ws_bytes(chunk_rows))
         return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, rs_surrogate_infer_ws_bytes(chunk_rows));
     cudaSetDevice(c->device);

@@ -12,16 +12,20 @@ def _small(seed=0, dims=(7, 5, 4, 3)):
     return mlp.init_params(seed, dims)
 
 
-def test_gelu_matches_library_normal_cdf():
+def test_gelu_is_the_tanh_form_of_u_times_the_normal_cdf():
     special = pytest.importorskip("scipy.special")
     u = np.linspace(-6, 6, 241)
-    np.testing.assert_allclose(mlp.gelu(u), u * special.ndtr(u), rtol=1e-14, atol=1e-15)
+    # the tanh form stays within 1e-3 of the exact u * Phi(u) (library normal CDF)
+    assert np.max(np.abs(mlp.gelu(u) - u * special.ndtr(u))) < 1e-3
     # derivative by central differences
     h = 1e-6
     fd = (mlp.gelu(u + h) - mlp.gelu(u - h)) / (2 * h)
     np.testing.assert_allclose(mlp.gelu_grad(u), fd, rtol=1e-7, atol=1e-9)
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
     assert abs(mlp.gelu(np.array([8.0]))[0] - 8.0) < 1e-12
+    assert abs(mlp.gelu(np.array([-8.0]))[0]) < 1e-12
+    # odd part: gelu(u) - gelu(-u) = u
+    np.testing.assert_allclose(mlp.gelu(u) - mlp.gelu(-u), u, rtol=1e-14, atol=1e-14)
 
 
 def test_gradients_by_central_differences():
