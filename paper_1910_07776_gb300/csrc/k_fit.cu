@@ -354,12 +354,11 @@ __device__ __forceinline__ void mark_failed(const PredTarget& pt) {
 //   1^T M^-1 y = t_1^T D^-1 t_y,  1^T M^-1 1 = t_1^T D^-1 t_1,  b = their ratio,
 //   alpha = L^-T D^-1 (t_y - b t_1)   (one backward solve).
 template <int N>
-__device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
-                                           const double* __restrict__ yl, uint32_t pm,
-                                           const double* __restrict__ dl, double* out,
-                                           const PredTarget* pt) {
-    int vb[N];
-    double ty[N], t1[N], L[tri(N)], dinv[N];
+__device__ __forceinline__ int fit_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
+                                         const double* __restrict__ yl, uint32_t pm,
+                                         const double* __restrict__ dl, double* out, double (&ty)[N],
+                                         double& b, int (&vb)[N]) {
+    double t1[N], L[tri(N)], dinv[N];
     uint32_t x = pm;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
@@ -371,19 +370,13 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
     if constexpr (N == 1) {
         // one pair: 1^T alpha = 0 forces alpha = 0, so b = y and every prediction is b
         if (!pos_finite(__ldg(dl + vb[0]))) return RS_FIT_NOTPD;
-        const double b = ty[0];
+        b = ty[0];
+        ty[0] = 0.0;
         if (out) {
             out[0] = b;
             out[1] = 0.0;
         }
-        if (!finite_bits(b)) return RS_FIT_NONFINITE;
-        if (pt)
-            for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
-                const int t = __ffsll((long long)cm) - 1;
-                const int r = __popcll(pt->test & ((1ull << t) - 1ull));
-                if (r < pt->room) pt->dst[r] = b;
-            }
-        return RS_FIT_OK;
+        return finite_bits(b) ? RS_FIT_OK : RS_FIT_NONFINITE;
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -418,7 +411,7 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
         num = fma(sc, ty[i], num);
         den = fma(sc, t1[i], den);
     }
-    const double b = num * rcp_newton(den);
+    b = num * rcp_newton(den);
 #pragma unroll
     for (int i = 0; i < N; ++i) ty[i] = fma(-b, t1[i], ty[i]) * dinv[i];
 #pragma unroll
@@ -433,19 +426,32 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
 #pragma unroll
         for (int i = 0; i < N; ++i) out[1 + i] = ty[i];
     }
-    if (!fin) return RS_FIT_NONFINITE;
-    if (pt) {                              // predictions b + sum_a alpha_a K[t][v_a]
-        for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
-            const int t = __ffsll((long long)cm) - 1;
-            const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+    return fin ? RS_FIT_OK : RS_FIT_NONFINITE;
+}
+
+// One fit of n = N pairs in registers (fit_fixed), then its predictions b + sum_a alpha_a
+// K[t][v_a] for the candidate test rows of its split.
+template <int N>
+__device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const uint8_t* __restrict__ pb,
+                                           const double* __restrict__ yl, uint32_t pm,
+                                           const double* __restrict__ dl, double* out,
+                                           const PredTarget* pt) {
+    double al[N], b = 0.0;
+    int vb[N];
+    const int st = fit_fixed<N>(Kp, pb, yl, pm, dl, out, al, b, vb);
+    if (st != RS_FIT_OK || !pt) return st;
+    for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
+        const int t = __ffsll((long long)cm) - 1;
+        const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+        double yh = b;
+        if constexpr (N > 1) {             // with one pair alpha = 0: every prediction is b
             const double* Kt = Kp + t * RS_GRAM_LD;
-            double yh = b;
 #pragma unroll
-            for (int a = 0; a < N; ++a) yh = fma(ty[a], __ldg(Kt + vb[a]), yh);
-            if (r < pt->room) pt->dst[r] = yh;
+            for (int a = 0; a < N; ++a) yh = fma(al[a], __ldg(Kt + vb[a]), yh);
         }
+        if (r < pt->room) pt->dst[r] = yh;
     }
-    return RS_FIT_OK;
+    return st;
 }
 
 template <int N, int NHI>
@@ -469,7 +475,7 @@ struct SolveArgs {
     const double* ylab;
     const uint32_t* fit_pm;
     const uint8_t* fit_n;
-    const int* order;
+    const uint4* recs;    // [S*6] in bucket order: fit index, program, pair mask, versions
     const unsigned* hist;
     const int64_t* fit_off;
     double* coef;         // compact records, or the caller's [S][6][33] array
@@ -495,9 +501,8 @@ struct SolveArgs {
     int max_feat;
 };
 
-__device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j, int p, PredTarget& pt) {
+__device__ __forceinline__ bool pred_target_v(const SolveArgs& a, int64_t s, int j, int p, int V, PredTarget& pt) {
     if (!a.predbuf) return false;
-    const int V = (int)(a.row_off[p + 1] - a.row_off[p]);
     const uint64_t full = rs_full_mask(V);
     pt.test = ~a.train_masks[s] & full;
     pt.cand = pt.test & ((a.flags & RS_RANK_ALL) ? full : a.cand[p * RS_NOPT + j]);
@@ -506,6 +511,9 @@ __device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j
     pt.room = a.R - r0;
     if (r0 + __popcll(pt.test) > a.R) rs_dev_flag(a.dstatus, RS_EDATA, -3);
     return true;
+}
+__device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j, int p, PredTarget& pt) {
+    return pred_target_v(a, s, j, p, (int)(a.row_off[p + 1] - a.row_off[p]), pt);
 }
 
 __device__ __forceinline__ void finish_record(const SolveArgs& a, int64_t f, int n, int st, double* out) {
@@ -529,13 +537,15 @@ __device__ __forceinline__ double* coef_out(const SolveArgs& a, int64_t f) {
 // Counting sort of the fits by n.  Each block counts its fits per n in shared memory,
 // reserves one range per n with a single global atomic, and places its fits inside it.
 // Counting sort of the fits by n: each block counts its fits per n in shared memory,
-// reserves one range per n with a single global atomic, and places its fits inside it.
+// reserves one range per n with a single global atomic, and places its fits' records inside
+// it (fit index, program, pair mask, version count: what a solver needs first).
 // A fit without a training pair (n = 0) is finished here (status RS_FIT_EMPTY); the rank
 // pass knows it from the row records.
 __global__ void __launch_bounds__(256)
 bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
-                   unsigned* cursor, int* order, int64_t* fit_off, uint8_t* status, double* coef_user,
-                   unsigned long long* counters) {
+                   unsigned* cursor, uint4* recs, int64_t* fit_off, uint8_t* status, double* coef_user,
+                   unsigned long long* counters, const uint32_t* __restrict__ fit_pm,
+                   const int* __restrict__ split_prog, const int64_t* __restrict__ row_off) {
     __shared__ long long start[kHist], cstart[kHist];
     __shared__ unsigned lcount[kHist], lbase[kHist];
     if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
@@ -561,7 +571,9 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
             }
         } else {
             const long long pos = start[n] + lbase[n] + local;
-            order[pos] = (int)f;
+            // the solver's whole first round trip in one 16-byte record
+            const int p = split_prog[f / RS_NOPT];
+            recs[pos] = make_uint4((unsigned)f, (unsigned)p, fit_pm[f], (unsigned)(row_off[p + 1] - row_off[p]));
             if (fit_off) fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
         }
     }
@@ -602,34 +614,43 @@ solve_small_kernel(const SolveArgs a, unsigned long long* work) {
     __shared__ long long start[kHist], cstart[kHist];
     bucket_tables(a.hist, start, cstart);
     const long long lo = start[NLO], hi = start[NHI + 1];
+    const int lane = threadIdx.x & 31;
+    // positions from the top of the range down: the largest fits first, the cheapest last, so
+    // the final ranges (the tail of the kernel) are short
+    auto position = [&](long long b) { return hi - 1 - (b - lo) - lane; };
+    // two ranges ahead: the record of the next range is loaded while this one is solved
+    long long base = lo + (long long)__shfl_sync(0xffffffffu, take32(work), 0);
     unsigned long long got = take32(work);
-    long long base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+    uint4 rec = make_uint4(0, 0, 0, 0);
+    if (base < hi && position(base) >= lo) rec = a.recs[position(base)];
     while (base < hi) {
+        const long long next = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
         got = take32(work);
-        // positions from the top of the range down: the largest fits first, the cheapest
-        // last, so the final ranges (the tail of the kernel) are short
-        const long long pos = hi - 1 - (base - lo) - (threadIdx.x & 31);
+        uint4 nrec = make_uint4(0, 0, 0, 0);
+        if (next < hi && position(next) >= lo) nrec = a.recs[position(next)];
+        const long long pos = position(base);
         const bool active = pos >= lo;
         int st = RS_FIT_OK;
         if (active) {
             int n = NLO;
             while (start[n + 1] <= pos) ++n;
-            const int64_t f = a.order[pos];
+            const int64_t f = rec.x;
             const int64_t s = f / RS_NOPT;
             const int j = (int)(f - s * RS_NOPT);
-            const int p = a.split_prog[s];
+            const int p = (int)rec.y;
             const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
             const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
             double* out = coef_out(a, f);
             PredTarget ptv;
-            const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
-            st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f],
+            const PredTarget* pt = pred_target_v(a, s, j, p, (int)rec.w, ptv) ? &ptv : nullptr;
+            st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, rec.z,
                                           a.dlam + (int64_t)p * RS_MAXV, out, pt);
             if (st != RS_FIT_OK && pt) mark_failed(*pt);
             finish_record(a, f, n, st, out);
         }
         count_status(a, st, active);
-        base = lo + (long long)__shfl_sync(0xffffffffu, got, 0);
+        base = next;
+        rec = nrec;
     }
 }
 
@@ -657,13 +678,14 @@ ibk_kernel(const SolveArgs a, int nmax, unsigned long long* work) {
         if (active) {
             int n = 1;
             while (start[n + 1] <= pos) ++n;
-            const int64_t f = a.order[pos];
+            const uint4 rec = a.recs[pos];
+            const int64_t f = rec.x;
             const int64_t s = f / RS_NOPT;
             const int j = (int)(f - s * RS_NOPT);
-            const int p = a.split_prog[s];
+            const int p = (int)rec.y;
             const double* Dp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
             const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-            const uint32_t pm = a.fit_pm[f];
+            const uint32_t pm = rec.z;
             const double* yl = a.ylab + pbase;
             PredTarget pt;
             if (pred_target(a, s, j, p, pt)) {
@@ -825,16 +847,17 @@ solve_mid_kernel(const SolveArgs a, int nmax, unsigned long long* work) {
         if (active) {
             int n = kNReg + 1;
             while (start[n + 1] <= pos) ++n;
-            const int64_t f = a.order[pos];
+            const uint4 rec = a.recs[pos];
+            const int64_t f = rec.x;
             const int64_t s = f / RS_NOPT;
             const int j = (int)(f - s * RS_NOPT);
-            const int p = a.split_prog[s];
+            const int p = (int)rec.y;
             const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
             const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
             double* out = coef_out(a, f);
             PredTarget ptv;
             const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
-            st = solve_var(n, nmax, Kp, a.pb + pbase, a.ylab + pbase, a.fit_pm[f],
+            st = solve_var(n, nmax, Kp, a.pb + pbase, a.ylab + pbase, rec.z,
                            a.dlam + (int64_t)p * RS_MAXV, out, pt, W, VB);
             if (st != RS_FIT_OK && pt) mark_failed(*pt);
             finish_record(a, f, n, st, out);
@@ -1136,10 +1159,11 @@ solve_large_kernel(const SolveArgs a) {
          pos += (long long)gridDim.x * kLargeWarps) {
         int n = 1;
         while (start[n + 1] <= pos) ++n;
-        const int64_t f = a.order[pos];
+        const uint4 rec = a.recs[pos];
+        const int64_t f = rec.x;
         const int64_t s = f / RS_NOPT;
         const int j = (int)(f - s * RS_NOPT);
-        const int p = a.split_prog[s];
+        const int p = (int)rec.y;
         const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
         double* out = coef_out(a, f);
@@ -1153,9 +1177,9 @@ solve_large_kernel(const SolveArgs a) {
             rc.sh = rbase + a.max_feat;
             rc.vsh = reinterpret_cast<int*>(rbase + a.max_feat + 64);
         }
-        const int st = refine ? fit_warp(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
+        const int st = refine ? fit_warp(n, rec.z, a.pb + base, a.ylab + base, Kp, RS_GRAM_LD,
                                          a.lambda, Lsh, out, pt, &rc)
-                              : fit_warp_ldl(n, a.fit_pm[f], a.pb + base, a.ylab + base, Kp,
+                              : fit_warp_ldl(n, rec.z, a.pb + base, a.ylab + base, Kp,
                                              a.dlam + (int64_t)p * RS_MAXV, Lsh, Ush, out, pt);
         if (lane == 0) {
             if (st != RS_FIT_OK && pt) mark_failed(*pt);
@@ -1717,7 +1741,7 @@ struct FitWs {
     int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
     uint8_t* fit_n;      // [S*6]
-    int* order;          // [S*6]
+    uint4* recs;         // [S*6] fit records in bucket order
     int64_t* fit_off;    // [S*6]
     uint8_t* status;     // [S*6]
     double* coef;        // compact records
@@ -1754,7 +1778,7 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
     w.fit_n = (uint8_t*)take(S6);
-    w.order = (int*)take(S6 * sizeof(int));
+    w.recs = (uint4*)take(S6 * sizeof(uint4));
     w.fit_off = (int64_t*)take(S6 * sizeof(int64_t));
     w.status = (uint8_t*)take(S6);
     w.coef = (double*)take(S6 * (size_t)(nmax + 1) * sizeof(double));
@@ -1836,7 +1860,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
     const bool rank = a.rec_code != nullptr;
-    SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.order, w.hist,
+    SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.recs, w.hist,
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
@@ -1844,9 +1868,10 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                  a.feat_width, a.max_feat};
     // compact records (and their offsets) only for fits without predictions or caller array
     const bool need_off = !user && !rank;
-    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.order,
+    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.recs,
                                                   need_off ? w.fit_off : nullptr,
-                                                  status, user ? a.coef_out : nullptr, a.counters);
+                                                  status, user ? a.coef_out : nullptr, a.counters,
+                                                  w.fit_pm, w.split_prog, a.row_offsets);
     mark(3);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1901,7 +1926,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                     if (e == cudaSuccess) e = launch_small<8, kNReg, 2>(sa, sms, S6, w1, st); break;
             case 8: e = launch_small<1, 8, 3>(sa, sms, S6, w0, st);
                     if (e == cudaSuccess) e = launch_small<9, kNReg, 2>(sa, sms, S6, w1, st); break;
-            default: e = launch_small<1, 6, 5>(sa, sms, S6, w0, st);
+            default: e = launch_small<1, 6, 4>(sa, sms, S6, w0, st);
                     if (e == cudaSuccess) e = launch_small<7, kNReg, 2>(sa, sms, S6, w1, st); break;
         }
         if (e != cudaSuccess) return e;

@@ -42,10 +42,11 @@ def test_workspace_query_needs_no_gpu():
     S = 100
     cs = rs._Splits(S, 0, 32, 0, None, None)
     fit = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
-    # per fit: pair mask, size, order, offset, status, and up to 17 coefficient doubles;
+    # per fit: pair mask, size, 16-byte record in bucket order, offset, status, and up to 17
+    # coefficient doubles;
     # per test row (bound: S x max_versions when no row count is given): six predictions
     # and the row's scoring record
-    need_fit = S * 6 * (4 + 1 + 4 + 8 + 1 + 17 * 8) + S * 64 * (6 * 8 + 8)
+    need_fit = S * 6 * (4 + 1 + 16 + 8 + 1 + 17 * 8) + S * 64 * (6 * 8 + 8)
     assert need_fit <= fit <= need_fit + 64 * 1024
     cs.n_test_rows = 1000
     fit2 = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
