@@ -69,6 +69,7 @@ enum {
 #define RS_MAXPAIRS 32      /* pairs per optimization per program                        */
 #define RS_COEF_STRIDE 33   /* doubles per fit in the coefficient array: b, alpha[32]   */
 #define RS_GRAM_LD 64       /* leading dimension of each program's Gram block           */
+#define RS_MAXRUNS 4        /* runs in one training group of rs_transfer                 */
 #define RS_NCOUNTERS 16
 
 /* Accuracy counters (uint64, accumulated, never reset by the library):
@@ -76,7 +77,7 @@ enum {
  *  3 sign hits (pred > 0 and actual > 0 agree: the accuracy of Table 3)
  *  4 recommendations emitted 5 ... with a known actual   6 ... whose actual speedup > 1
  *  7 rows with >= 1 scored prediction  8 ... whose top prediction is the best actual
- *  9..12 fits by status OK / EMPTY / NOTPD / NONFINITE (rs_predict_rank only)
+ *  9..12 fits by status OK / EMPTY / NOTPD / NONFINITE (rs_predict_rank, rs_transfer)
  * 13 candidates skipped because their fit was not OK     14, 15 reserved (0)          */
 
 typedef struct rs_ctx rs_ctx;
@@ -232,6 +233,42 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
                      void* workspace, size_t workspace_bytes, int64_t* rec_offsets,
                      uint32_t* rec_code, double* rec_pred, double* pred_all,
                      uint64_t* counters);
+
+/* ---- Table 2: transfer to another run, input or program (Sec. 5) -------------------------
+ * Q transfer problems.  Problem q trains on a group of runs of `train` -- runs
+ * group_offsets[q] .. group_offsets[q+1]-1, each laid out like one program of a batch (at most
+ * 64 versions with distinct masks), 1..max_runs of them -- and tests on program q of `test`
+ * (Q = test->n_programs).  groups == NULL: one run per problem, run q for problem q (then
+ * train->n_programs == Q).  The runs of a group and its test program have one feature width.
+ * Both sets hold raw counters (dtype, cycles as in rs_standardize).  Per problem: the vectors
+ * of all the group's runs are standardized together (mu, sigma over all of them, as
+ * rs_standardize) and the test program with those statistics; per optimization j the model
+ * is trained from every before/after pair (v, v|j) of every run of the group (a pair never
+ * spans two runs), labelled with its run's log speedup -- ridge (lambda, FP64, the bordered
+ * dual system of rs_fit_batched on up to 32 * max_runs pairs) or, with RS_MODEL_IBK, the
+ * instance-based learner (as rs_predict_rank; pairs in run order, then ascending before
+ * slot) -- and predicts for every version t of the test program each candidate j that is
+ * outside t's mask (all six with RS_RANK_ALL) and inside opt_mask (bits of the optimizations
+ * that may be recommended: 0x3F for all, fewer for transfer between programs that share only
+ * some optimizations).  Ranking, threshold, top-k and scoring as in rs_predict_rank, the
+ * actual speedups taken from the test program's own times.  Rows: the test set's versions in
+ * order (R = test->n_rows).  Outputs (device memory): rec_code [R] (required), rec_pred
+ * [R][k], pred_all [R][6], counters [16] (9..12 count the Q * 6 fits) and fit_status [Q][6]
+ * (nullable).  A problem whose group or test program breaks these rules is skipped (its rows
+ * are not written) and reported as RS_EDATA in the device status.  workspace: device memory
+ * of at least rs_transfer_workspace_bytes(train, test, groups) bytes, 256-byte aligned,
+ * scratch.  flags: RS_RANK_ALL, RS_MODEL_IBK.  tau > 0, k in 1..6.                       */
+typedef struct {
+    int64_t n_groups;             /* host: Q, equal to test->n_programs                      */
+    int32_t max_runs;             /* host: upper bound on runs per group, 1..RS_MAXRUNS      */
+    int32_t reserved;
+    const int64_t* group_offsets; /* [Q+1] device: group_offsets[0] = 0, non-decreasing      */
+} rs_groups;
+size_t rs_transfer_workspace_bytes(const rs_batch* train, const rs_batch* test, const rs_groups* groups);
+rs_status rs_transfer(rs_ctx* ctx, const rs_batch* train, const rs_batch* test, const rs_groups* groups,
+                      double lambda, int k, double tau, int flags, int opt_mask, void* workspace,
+                      size_t workspace_bytes, uint8_t* fit_status, uint32_t* rec_code, double* rec_pred,
+                      double* pred_all, uint64_t* counters);
 
 /* ---- A8: one graph launch per step, and the autotuner ---------------------------------------
  * rs_cv_graph_create runs rs_cv_step once eagerly (reporting argument errors), then captures

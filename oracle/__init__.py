@@ -69,6 +69,9 @@ def lib():
                                    C.c_int, C.c_double, C.c_int, C.c_double, P, P, P, P, P, P,
                                    P, P, P, C.c_int, C.c_int]
         L.orc_ibk_predict.argtypes = [C.c_int, C.c_int, P, P, P, C.c_int]
+        L.orc_transfer.argtypes = [C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_double,
+                                   C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P, P,
+                                   P]
         L.orc_ibk_predict.restype = C.c_double
         L.orc_num_threads_available.restype = C.c_int
         _lib = L
@@ -190,6 +193,57 @@ def cv_batch(batch, splits, lam: float = 1e-3, k: int = 3, tau: float = 1.05, fl
     return CVResult(Z=Z, mu=mu, sigma=sg, fit_status=fs.reshape(S, N_OPT), rec_offsets=ro,
                     rec_code=code, rec_pred=rp.reshape(R, k), pred_all=pa.reshape(R, N_OPT),
                     counters=cnt)
+
+
+@dataclass
+class TransferResult:
+    fit_status: np.ndarray       # [Q][6]
+    rec_offsets: np.ndarray      # [Q + 1]: test rows of problem q start at rec_offsets[q]
+    rec_code: np.ndarray
+    rec_pred: np.ndarray
+    pred_all: np.ndarray
+    counters: np.ndarray
+
+    def counter(self, name: str) -> int:
+        return int(self.counters[COUNTER_NAMES.index(name)])
+
+
+def transfer(train, test, groups=None, lam: float = 1e-3, k: int = 3, tau: float = 1.05, flags: int = 0,
+             opt_mask: int = 0x3F, model: str = "ridge", ibk_k: int = IBK_NEIGHBORS) -> TransferResult:
+    """Sec. 5 / Table 2: for every problem q, a model trained on all pairs of the runs
+    groups[q] .. groups[q+1]-1 of ``train`` (standardized together) predicts, ranks and scores
+    every version of ``test``'s program q (standardized with the training runs' statistics).
+    groups defaults to one run per problem.  opt_mask limits the candidate optimizations."""
+    if model not in ("ridge", "ibk"):
+        raise ValueError("model must be 'ridge' or 'ibk'")
+    if model == "ibk":
+        flags |= MODEL_IBK
+    L = lib()
+    Q = test.n_programs
+    g = np.arange(Q + 1, dtype=np.int64) if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
+    assert g.shape == (Q + 1,) and g[0] == 0 and g[-1] <= train.n_programs and np.all(np.diff(g) >= 1)
+    for q in range(Q):
+        assert np.all(train.feat_width[g[q]:g[q + 1]] == test.feat_width[q])
+    ro = np.zeros(Q + 1, dtype=np.int64)
+    ro[1:] = np.cumsum(np.diff(test.row_offsets))
+    R = int(ro[-1])
+    fs = np.zeros(Q * N_OPT, dtype=np.uint8)
+    code = np.zeros(R, dtype=np.uint32)
+    rp = np.zeros(R * k, dtype=np.float64)
+    pa = np.zeros(R * N_OPT, dtype=np.float64)
+    cnt = np.zeros(N_COUNTERS, dtype=np.uint64)
+    c64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    cy = lambda b: None if b.cycles is None else c64(b.cycles)
+    L.orc_transfer(Q, _p(g), _p(np.ascontiguousarray(train.feat_width, dtype=np.int32)),
+                   _p(np.ascontiguousarray(train.row_offsets)), _p(np.ascontiguousarray(train.x_offsets)),
+                   _p(c64(train.X)), _p(np.ascontiguousarray(train.masks)), _p(c64(train.log_time)),
+                   _p(cy(train)), _p(np.ascontiguousarray(test.row_offsets)),
+                   _p(np.ascontiguousarray(test.x_offsets)), _p(c64(test.X)),
+                   _p(np.ascontiguousarray(test.masks)), _p(c64(test.log_time)), _p(cy(test)),
+                   float(lam), int(k), float(np.log(tau)), int(flags), int(opt_mask), int(ibk_k), EPS,
+                   _p(fs), _p(code), _p(rp), _p(pa), _p(cnt))
+    return TransferResult(fit_status=fs.reshape(Q, N_OPT), rec_offsets=ro, rec_code=code,
+                          rec_pred=rp.reshape(R, k), pred_all=pa.reshape(R, N_OPT), counters=cnt)
 
 
 def ibk_predict(Zrows, y, zt, k: int = IBK_NEIGHBORS) -> float:

@@ -20,7 +20,9 @@
  *            gets one predicted speedup per optimization it does not already contain;
  *   Sec. 2   Tier 3 sorts by expected benefit, keeps those at or above a threshold and
  *            reports at most k;
- *   Sec. 5/6 scoring: actual vs expected speedup (AC/EX) and sign accuracy (Table 3).
+ *   Sec. 5/6 scoring: actual vs expected speedup (AC/EX) and sign accuracy (Table 3);
+ *   Sec. 5   Table 2 transfer: a model trained on one set of feature vectors (one program,
+ *            input and run) predicts for another set (another run, input or program).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - log(max(x / cycles, eps)) with eps = 1e-30, then population mean / standard
@@ -34,7 +36,13 @@
  *   - IBK: distances between z-scored feature vectors; the "mode" of the neighbours'
  *     labels, which are continuous log speedups, is read as their mean (summed in pair
  *     order); equal distances take the lower pair index first; fewer than k training
- *     pairs use all of them.
+ *     pairs use all of them;
+ *   - transfer (Table 2): the training set is a group of runs (one program and input, or
+ *     several runs of it); their vectors are standardized together and the test set with the
+ *     same statistics; a model is trained from all pairs of all runs, a pair never spanning
+ *     two runs; every version of the test set is a test row, scored against the test set's
+ *     own times; an optimization mask limits the candidates (the optimizations two programs
+ *     share, for cross-program transfer).
  *
  * All arithmetic is double precision, in plain loops, with no blocking or reordering
  * beyond the definitions above.
@@ -451,6 +459,170 @@ void orc_cv_batch(int P, const int64_t* row_offsets, const int32_t* feat_width,
     for (int64_t s = 0; s < S; ++s)
         for (int c = 0; c < ORC_NCOUNTERS; ++c) counters[c] += per_split[(size_t)s * ORC_NCOUNTERS + c];
     free(per_split);
+}
+
+/* Sec. 5, Table 2: train on a group of runs of set A, predict and score a program of set B.
+ * Problem q trains on runs group_offsets[q] .. group_offsets[q+1]-1 of A (each run laid out
+ * like one program of orc_cv_batch's input: a_row_offsets, a_feat_width, a_x_offsets, a_X,
+ * a_masks, a_log_time, a_cycles) and tests on program q of B (b_row_offsets, b_x_offsets,
+ * b_X, b_masks, b_log_time, b_cycles), which has the runs' feature width.  For each q: the
+ * vectors of all the group's runs are standardized together (mu, sigma over all of them),
+ * B's program with those statistics; per optimization j the training pairs are the
+ * before/after pairs of every run (Sec. 3.3; a pair never spans two runs), run by run, in
+ * ascending before slot, labelled with that run's log speedups; the model (ridge, or IBK
+ * with ORC_MODEL_IBK) predicts for every version t of B's program its candidates j (not in
+ * t's mask, or all six with ORC_RANK_ALL) that are also in opt_mask; ranking, threshold and
+ * scoring as in orc_cv_batch with B's times for the actual speedups.  Test rows: B's
+ * versions, program by program, in slot order (R = B's row total).  fit_status [Q][6].     */
+void orc_transfer(int Q, const int64_t* group_offsets, const int32_t* a_feat_width,
+                  const int64_t* a_row_offsets, const int64_t* a_x_offsets, const double* a_X,
+                  const uint8_t* a_masks, const double* a_log_time, const double* a_cycles,
+                  const int64_t* b_row_offsets, const int64_t* b_x_offsets, const double* b_X,
+                  const uint8_t* b_masks, const double* b_log_time, const double* b_cycles,
+                  double lambda, int k, double log_tau, int flags, int opt_mask, int ibk_k, double eps,
+                  uint8_t* fit_status, uint32_t* rec_code, double* rec_pred, double* pred_all,
+                  uint64_t* counters) {
+    const int ibk = (flags & ORC_MODEL_IBK) != 0;
+    int64_t row = 0;
+    for (int q = 0; q < Q; ++q) {
+        const int64_t g0 = group_offsets[q], g1 = group_offsets[q + 1];
+        const int F = a_feat_width[g0];
+        int N = 0;                                   /* versions of all runs of the group */
+        for (int64_t r = g0; r < g1; ++r) N += (int)(a_row_offsets[r + 1] - a_row_offsets[r]);
+        const int VB = (int)(b_row_offsets[q + 1] - b_row_offsets[q]);
+        const int64_t rb = b_row_offsets[q];
+        double* XA = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * F);
+        double* CA = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+        double* LA = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+        double* ZA = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * F);
+        double* ZB = (double*)malloc(sizeof(double) * (size_t)(VB > 0 ? VB : 1) * F);
+        double* mu = (double*)malloc(sizeof(double) * F);
+        double* sg = (double*)malloc(sizeof(double) * F);
+        int u = 0;
+        for (int64_t r = g0; r < g1; ++r) {          /* the runs' rows, one after another */
+            const int V = (int)(a_row_offsets[r + 1] - a_row_offsets[r]);
+            for (int v = 0; v < V; ++v, ++u) {
+                memcpy(XA + (size_t)u * F, a_X + a_x_offsets[r] + (int64_t)v * F, sizeof(double) * F);
+                CA[u] = a_cycles ? a_cycles[a_row_offsets[r] + v] : 1.0;
+                LA[u] = a_log_time[a_row_offsets[r] + v];
+            }
+        }
+        orc_standardize(N, F, XA, a_cycles ? CA : NULL, eps, ZA, mu, sg);
+        for (int t = 0; t < VB; ++t)        /* B with A's statistics */
+            for (int f = 0; f < F; ++f) {
+                double x = b_X[b_x_offsets[q] + (int64_t)t * F + f];
+                if (b_cycles) x = x / b_cycles[rb + t];
+                double l = log(x > eps ? x : eps);
+                ZB[(size_t)t * F + f] = (sg[f] > 1e-12) ? (l - mu[f]) / sg[f] : 0.0;
+            }
+        const uint8_t* mb = b_masks + rb;
+        const double* ltb = b_log_time + rb;
+        const size_t cap = (size_t)(N > 0 ? N : 1);  /* pairs per optimization <= versions */
+        double* beta = (double*)malloc(sizeof(double) * ORC_NOPT * F);
+        double* work = (double*)malloc(sizeof(double) * ((size_t)F * F + 2 * (size_t)F));
+        double* Zr = (double*)malloc(sizeof(double) * ORC_NOPT * cap * F);
+        double* yv = (double*)malloc(sizeof(double) * ORC_NOPT * cap);
+        double bias[ORC_NOPT];
+        int nj[ORC_NOPT], ok[ORC_NOPT];
+        for (int j = 0; j < ORC_NOPT; ++j) {
+            double* Zj = Zr + (size_t)j * cap * F;
+            double* yj = yv + (size_t)j * cap;
+            int n = 0, u0 = 0;
+            for (int64_t r = g0; r < g1; ++r) {      /* pairs within each run (Sec. 3.3) */
+                const int V = (int)(a_row_offsets[r + 1] - a_row_offsets[r]);
+                int before[64], after[64];
+                const int np = orc_pairs(V, a_masks + a_row_offsets[r], j, before, after);
+                for (int e = 0; e < np; ++e, ++n) {
+                    memcpy(Zj + (size_t)n * F, ZA + (size_t)(u0 + before[e]) * F, sizeof(double) * F);
+                    yj[n] = LA[u0 + before[e]] - LA[u0 + after[e]];
+                }
+                u0 += V;
+            }
+            nj[j] = n;
+            int st;
+            if (ibk) st = n > 0 ? ORC_FIT_OK : ORC_FIT_EMPTY;
+            else st = orc_ridge_fit(n, F, Zj, yj, lambda, beta + (size_t)j * F, &bias[j], work);
+            ok[j] = st == ORC_FIT_OK;
+            if (fit_status) fit_status[q * ORC_NOPT + j] = (uint8_t)st;
+            counters[9 + st] += 1;
+        }
+        int slot_of[64];
+        for (int m = 0; m < 64; ++m) slot_of[m] = -1;
+        for (int v = 0; v < VB; ++v) slot_of[mb[v]] = v;
+        for (int t = 0; t < VB; ++t, ++row) {
+            double pred[ORC_NOPT], act[ORC_NOPT];
+            int valid[ORC_NOPT], known[ORC_NOPT];
+            for (int j = 0; j < ORC_NOPT; ++j) {
+                const int cand = ((flags & ORC_RANK_ALL) || !((mb[t] >> j) & 1)) && ((opt_mask >> j) & 1);
+                valid[j] = known[j] = 0;
+                pred[j] = act[j] = NAN;
+                if (!cand) continue;
+                if (!ok[j]) {
+                    counters[13] += 1;
+                    continue;
+                }
+                double yh;
+                if (ibk) {
+                    yh = orc_ibk_predict(nj[j], F, Zr + (size_t)j * cap * F, yv + (size_t)j * cap,
+                                         ZB + (size_t)t * F, ibk_k);
+                } else {
+                    yh = bias[j];
+                    for (int f = 0; f < F; ++f) yh += ZB[(size_t)t * F + f] * beta[(size_t)j * F + f];
+                }
+                pred[j] = yh;
+                valid[j] = 1;
+                counters[1] += 1;
+                if (!((mb[t] >> j) & 1)) {
+                    const int w = slot_of[mb[t] | (1 << j)];
+                    if (w >= 0) {
+                        act[j] = ltb[t] - ltb[w];
+                        known[j] = 1;
+                    }
+                }
+                if (known[j]) {
+                    counters[2] += 1;
+                    if ((pred[j] > 0.0) == (act[j] > 0.0)) counters[3] += 1;
+                }
+            }
+            int idx[ORC_NOPT];
+            const int c = orc_rank(pred, valid, k, log_tau, idx);
+            uint32_t code = (uint32_t)c;
+            for (int a = 0; a < ORC_NOPT; ++a) code |= (uint32_t)(a < c ? idx[a] : 0xF) << (4 + 4 * a);
+            if (rec_code) rec_code[row] = code;
+            if (rec_pred)
+                for (int a = 0; a < k; ++a) rec_pred[row * k + a] = a < c ? pred[idx[a]] : NAN;
+            if (pred_all)
+                for (int j = 0; j < ORC_NOPT; ++j) pred_all[row * ORC_NOPT + j] = pred[j];
+            counters[0] += 1;
+            counters[4] += (uint64_t)c;
+            for (int a = 0; a < c; ++a)
+                if (known[idx[a]]) {
+                    counters[5] += 1;
+                    if (act[idx[a]] > 0.0) counters[6] += 1;
+                }
+            int bp = -1, ba = -1;
+            for (int j = 0; j < ORC_NOPT; ++j) {
+                if (!(valid[j] && known[j])) continue;
+                if (bp < 0 || pred[j] > pred[bp]) bp = j;
+                if (ba < 0 || act[j] > act[ba]) ba = j;
+            }
+            if (bp >= 0) {
+                counters[7] += 1;
+                if (bp == ba) counters[8] += 1;
+            }
+        }
+        free(XA);
+        free(CA);
+        free(LA);
+        free(ZA);
+        free(ZB);
+        free(mu);
+        free(sg);
+        free(beta);
+        free(work);
+        free(Zr);
+        free(yv);
+    }
 }
 
 int orc_num_threads_available(void) {

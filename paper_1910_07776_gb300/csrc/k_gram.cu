@@ -97,7 +97,83 @@ gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __res
     }
 }
 
+// Blocks of a transfer problem q (Table 2).  Its training runs form one list of N versions
+// (rs_group_layout); the rows are the list itself (CROSS false: the group's Gram KA[q][i][u],
+// ld x ld) or the versions of the test program q (CROSS true: Kx[q][t][u], 64 x ld).  Entry =
+// sum_f z_i[f] z_u[f] (FMA chain), or with DIST sum_f (z_t[f] - z_u[f])^2 with unfused
+// operations (the plain definition's arithmetic), ascending f.  One thread per entry; the
+// rows come from L1 / L2.  Problems that fail the layout checks (reported by the
+// standardization) are skipped.
+template <bool CROSS, bool DIST>
+__global__ void __launch_bounds__(128)
+transfer_block_kernel(const int64_t* __restrict__ group_off, int max_runs, int64_t n_runs, int stat_stride,
+                      const int64_t* __restrict__ a_row, const int32_t* __restrict__ a_fw,
+                      const int64_t* __restrict__ a_xo, const double* __restrict__ ZA,
+                      const int64_t* __restrict__ b_row, const int32_t* __restrict__ b_fw,
+                      const int64_t* __restrict__ b_xo, const double* __restrict__ ZB, int ld,
+                      double* __restrict__ out) {
+    __shared__ int64_t rowx[RS_MAXV * RS_MAXRUNS];
+    const int q = blockIdx.x;
+    int start[RS_MAXRUNS + 1], F = 0;
+    const int N = rs_group_layout(q, group_off, max_runs, n_runs, a_row, a_fw, b_fw, stat_stride, start, F);
+    if (N < 0 || N > ld) return;
+    const int VB = (int)(b_row[q + 1] - b_row[q]);
+    if (CROSS && (VB < 1 || VB > RS_MAXV)) return;
+    const int rows = CROSS ? VB : N;
+    if ((int64_t)blockIdx.y * blockDim.x >= (int64_t)rows * N) return;
+    const int64_t g0 = group_off[q];
+    for (int u = threadIdx.x; u < N; u += blockDim.x) {
+        int r = 0;
+        while (u >= start[r + 1]) ++r;
+        rowx[u] = a_xo[g0 + r] + (int64_t)(u - start[r]) * F;
+    }
+    __syncthreads();
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= rows * N) return;
+    const int i = e / N, u = e - i * N;
+    const double* zi = CROSS ? ZB + b_xo[q] + (int64_t)i * F : ZA + rowx[i];
+    const double* zu = ZA + rowx[u];
+    double acc = 0.0;
+    for (int f = 0; f < F; ++f) {
+        if constexpr (DIST) {
+            const double d = __dsub_rn(__ldg(zi + f), __ldg(zu + f));
+            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        } else {
+            acc = fma(__ldg(zi + f), __ldg(zu + f), acc);
+        }
+    }
+    const int64_t rows_ld = CROSS ? RS_MAXV : ld;
+    out[((int64_t)q * rows_ld + i) * ld + u] = acc;
+}
+
 }  // namespace
+
+cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch* test_std, const int64_t* group_off,
+                                      int max_runs, int stat_stride, int ld, double* KA, double* Kx, int dist,
+                                      cudaStream_t st) {
+    const unsigned Q = (unsigned)test_std->n_programs;
+    const int n = RS_MAXV * max_runs;
+    const double* ZA = (const double*)train_std->X;
+    const double* ZB = (const double*)test_std->X;
+    if (KA) {
+        dim3 grid(Q, (unsigned)(((int64_t)n * n + 127) / 128));
+        transfer_block_kernel<false, false><<<grid, 128, 0, st>>>(
+            group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
+            ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, KA);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(Q, (unsigned)(((int64_t)RS_MAXV * n + 127) / 128));
+    if (dist)
+        transfer_block_kernel<true, true><<<grid, 128, 0, st>>>(
+            group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
+            ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, Kx);
+    else
+        transfer_block_kernel<true, false><<<grid, 128, 0, st>>>(
+            group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
+            ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, Kx);
+    return cudaGetLastError();
+}
 
 cudaError_t rs_launch_gram_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st) {
     dim3 grid((unsigned)b->n_programs, kGramChunks);

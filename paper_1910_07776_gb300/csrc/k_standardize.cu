@@ -142,7 +142,161 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     }
 }
 
+// Standardization of the training side of a transfer (Table 2): problem q trains on the runs
+// group_off[q] .. group_off[q+1]-1 (each laid out like one program: at most 64 versions, all
+// with the width F of the problem's test program), standardized together -- mu, sigma over
+// the vectors of all of them -- into Z in X's layout; mu, sigma at q * stat_stride + f.
+// Block = (problem, 16-feature slice), as standardize_kernel with up to kGroupRows rows.
+constexpr int kGroupRows = RS_MAXV * RS_MAXRUNS;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+group_standardize_kernel(const int64_t* __restrict__ group_off, int max_runs, int64_t n_runs,
+                         const int64_t* __restrict__ row_off,
+                         const int32_t* __restrict__ fw, const int64_t* __restrict__ xo,
+                         const T* __restrict__ X, const double* __restrict__ cycles,
+                         const int32_t* __restrict__ fw_test, int stat_stride, double* __restrict__ Z,
+                         double* __restrict__ mu, double* __restrict__ sigma, int* dstatus) {
+    __shared__ double lv[kGroupRows][kFeat];
+    __shared__ double part[kGroups][kFeat];
+    __shared__ double stat[2][kFeat];
+    __shared__ double inv_c[kGroupRows];
+    __shared__ int64_t rowx[kGroupRows];
+    __shared__ double tlog[256], tinv[256];
+    const int q = blockIdx.x;
+    int start[RS_MAXRUNS + 1], F = 0;
+    const int N = rs_group_layout(q, group_off, max_runs, n_runs, row_off, fw, fw_test, stat_stride, start, F);
+    if (N < 0) {
+        if (threadIdx.x == 0 && blockIdx.y == 0) rs_dev_flag(dstatus, RS_EDATA, q);
+        return;
+    }
+    if (blockIdx.y * kFeat >= F) return;
+    const int fl = threadIdx.x % kFeat, g = threadIdx.x / kFeat;
+    const int f = blockIdx.y * kFeat + fl;
+    const bool active = f < F;
+    const int64_t g0 = group_off[q];
+    for (int u = threadIdx.x; u < N; u += kThreads) {
+        int r = 0;
+        while (u >= start[r + 1]) ++r;
+        const int v = u - start[r];
+        rowx[u] = xo[g0 + r] + (int64_t)v * F;
+        if (cycles) inv_c[u] = 1.0 / cycles[row_off[g0 + r] + v];
+    }
+    for (int t = threadIdx.x; t < 256; t += kThreads) {
+        tlog[t] = kLogTabF[t];
+        tinv[t] = kLogTabInv[t];
+    }
+    __syncthreads();
+    double s = 0.0;
+    if (active)
+        for (int u = g; u < N; u += kGroups) {
+            double x = as_double(X[rowx[u] + f]);
+            if (cycles) x = x * inv_c[u];
+            const double l = log_clamped(x, tlog, tinv);
+            lv[u][fl] = l;
+            s += l;
+        }
+    part[g][fl] = s;
+    __syncthreads();
+    if (g == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kGroups; ++i) t += part[i][fl];
+        stat[0][fl] = t / N;
+    }
+    __syncthreads();
+    const double m = stat[0][fl];
+    double q2 = 0.0;
+    if (active)
+        for (int u = g; u < N; u += kGroups) {
+            const double d = lv[u][fl] - m;
+            q2 += d * d;
+        }
+    part[g][fl] = q2;
+    __syncthreads();
+    if (g == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kGroups; ++i) t += part[i][fl];
+        stat[1][fl] = sqrt(t / N);
+    }
+    __syncthreads();
+    if (!active) return;
+    const double sd = stat[1][fl];
+    const bool ok = sd > 1e-12;
+    const double rs = ok ? 1.0 / sd : 0.0;
+    for (int u = g; u < N; u += kGroups) Z[rowx[u] + f] = ok ? (lv[u][fl] - m) * rs : 0.0;
+    if (g == 0) {
+        mu[(int64_t)q * stat_stride + f] = m;
+        sigma[(int64_t)q * stat_stride + f] = sd;
+    }
+}
+
+// The test side: program q standardized with its training group's statistics (at
+// q * stat_stride + f): z = (log max(x / c, 1e-30) - mu) / sigma, or 0 where sigma <= 1e-12.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+standardize_apply_kernel(const int64_t* __restrict__ row_off, const int32_t* __restrict__ fw,
+                         const int64_t* __restrict__ xo, const T* __restrict__ X,
+                         const double* __restrict__ cycles, const double* __restrict__ mu,
+                         const double* __restrict__ sigma, int stat_stride, double* __restrict__ Z) {
+    __shared__ double inv_c[RS_MAXV];
+    __shared__ double tlog[256], tinv[256];
+    const int p = blockIdx.x;
+    const int64_t r0 = row_off[p];
+    const int V = (int)(row_off[p + 1] - r0);
+    const int F = fw[p];
+    const int fl = threadIdx.x % kFeat, g = threadIdx.x / kFeat;
+    const int f = blockIdx.y * kFeat + fl;
+    // a bad program was reported by group_standardize_kernel
+    if (blockIdx.y * kFeat >= F || V < 1 || V > RS_MAXV || F > stat_stride) return;
+    if (cycles && threadIdx.x < V) inv_c[threadIdx.x] = 1.0 / cycles[r0 + threadIdx.x];
+    for (int t = threadIdx.x; t < 256; t += kThreads) {
+        tlog[t] = kLogTabF[t];
+        tinv[t] = kLogTabInv[t];
+    }
+    __syncthreads();
+    if (f >= F) return;
+    const double m = mu[(int64_t)p * stat_stride + f], sd = sigma[(int64_t)p * stat_stride + f];
+    const bool ok = sd > 1e-12;
+    const double rs = ok ? 1.0 / sd : 0.0;
+    const int64_t base = xo[p];
+    for (int r = g; r < V; r += kGroups) {
+        double x = as_double(X[base + (int64_t)r * F + f]);
+        if (cycles) x = x * inv_c[r];
+        const double l = log_clamped(x, tlog, tinv);
+        Z[base + (int64_t)r * F + f] = ok ? (l - m) * rs : 0.0;
+    }
+}
+
 }  // namespace
+
+cudaError_t rs_launch_transfer_standardize(const rs_batch* train, const rs_batch* test, const int64_t* group_off,
+                                           int max_runs, int stat_stride, double* ZA, double* ZB, double* mu,
+                                           double* sigma, int* dstatus, cudaStream_t st) {
+    const int Q = test->n_programs;
+    dim3 ga((unsigned)Q, (unsigned)((stat_stride + kFeat - 1) / kFeat));
+    if (train->dtype == RS_F32)
+        group_standardize_kernel<float><<<ga, kThreads, 0, st>>>(
+            group_off, max_runs, train->n_programs, train->row_offsets, train->feat_width, train->x_offsets,
+            (const float*)train->X,
+            train->cycles, test->feat_width, stat_stride, ZA, mu, sigma, dstatus);
+    else
+        group_standardize_kernel<double><<<ga, kThreads, 0, st>>>(
+            group_off, max_runs, train->n_programs, train->row_offsets, train->feat_width, train->x_offsets,
+            (const double*)train->X,
+            train->cycles, test->feat_width, stat_stride, ZA, mu, sigma, dstatus);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 gb((unsigned)Q, (unsigned)((test->max_feat + kFeat - 1) / kFeat));
+    if (test->dtype == RS_F32)
+        standardize_apply_kernel<float><<<gb, kThreads, 0, st>>>(test->row_offsets, test->feat_width, test->x_offsets,
+                                                                 (const float*)test->X, test->cycles, mu, sigma,
+                                                                 stat_stride, ZB);
+    else
+        standardize_apply_kernel<double><<<gb, kThreads, 0, st>>>(test->row_offsets, test->feat_width,
+                                                                  test->x_offsets, (const double*)test->X,
+                                                                  test->cycles, mu, sigma, stat_stride, ZB);
+    return cudaGetLastError();
+}
 
 cudaError_t rs_launch_standardize(const rs_batch* b, double* Z, double* mu, double* sigma,
                                   int* dstatus, cudaStream_t st) {

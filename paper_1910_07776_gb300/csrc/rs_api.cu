@@ -471,6 +471,124 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
 }
 
 
+// ---- Table 2 transfer ----------------------------------------------------------------------------
+namespace {
+struct TransferWs {
+    double *ZA, *ZB, *mu, *sigma, *KA, *Kx;
+    int64_t* iota;
+    size_t bytes;
+};
+
+int transfer_runs(const rs_groups* g) { return g ? g->max_runs : 1; }
+
+TransferWs transfer_carve(void* base, const rs_batch* train, const rs_batch* test, const rs_groups* g) {
+    TransferWs w{};
+    char* c = (char*)base;
+    size_t o = 0;
+    auto take = [&](size_t b) { char* p = c ? c + o : nullptr; o += align256(b); return p; };
+    const size_t Q = (size_t)test->n_programs;
+    const size_t ld = (size_t)RS_MAXV * transfer_runs(g);
+    w.ZA = (double*)take((size_t)train->x_elems * sizeof(double));
+    w.ZB = (double*)take((size_t)test->x_elems * sizeof(double));
+    w.mu = (double*)take(Q * (size_t)train->max_feat * sizeof(double));
+    w.sigma = (double*)take(Q * (size_t)train->max_feat * sizeof(double));
+    w.KA = (double*)take(Q * ld * ld * sizeof(double));
+    w.Kx = (double*)take(Q * RS_MAXV * ld * sizeof(double));
+    w.iota = g ? nullptr : (int64_t*)take((Q + 1) * sizeof(int64_t));
+    w.bytes = o;
+    return w;
+}
+}  // namespace
+
+size_t rs_transfer_workspace_bytes(const rs_batch* train, const rs_batch* test, const rs_groups* groups) {
+    if (!train || !test || test->n_programs < 1 || train->x_elems < 0 || test->x_elems < 0 ||
+        train->max_feat < 1 || (groups && (groups->max_runs < 1 || groups->max_runs > RS_MAXRUNS)))
+        return 0;
+    return transfer_carve(nullptr, train, test, groups).bytes;
+}
+
+rs_status rs_transfer(rs_ctx* c, const rs_batch* train, const rs_batch* test, const rs_groups* groups,
+                      double lambda, int k, double tau, int flags, int opt_mask, void* ws, size_t ws_bytes,
+                      uint8_t* fit_status, uint32_t* rec_code, double* rec_pred, double* pred_all,
+                      uint64_t* counters) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, train, true);
+    if (s == RS_OK) s = check_batch(c, test, true);
+    if (s != RS_OK) return s;
+    if (groups) {
+        if (groups->n_groups != test->n_programs)
+            return fail(c, RS_EINVAL, "groups->n_groups must equal the test set's n_programs");
+        if (groups->max_runs < 1 || groups->max_runs > RS_MAXRUNS)
+            return fail(c, RS_EINVAL, "groups->max_runs must be in 1..%d", RS_MAXRUNS);
+        if (!groups->group_offsets) return fail(c, RS_EINVAL, "groups->group_offsets is NULL");
+    } else if (train->n_programs != test->n_programs) {
+        return fail(c, RS_EINVAL, "without groups the training and test sets hold the same number of programs");
+    }
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(c, RS_EINVAL, "lambda must be finite and >= 0");
+    if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
+    if (flags & ~(RS_RANK_ALL | RS_MODEL_IBK)) return fail(c, RS_EINVAL, "flags: RS_RANK_ALL and RS_MODEL_IBK only");
+    if (opt_mask < 0 || opt_mask > 63) return fail(c, RS_EINVAL, "opt_mask must be in 0..63");
+    if (!rec_code) return fail(c, RS_EINVAL, "rec_code is required");
+    if (!ws) return fail(c, RS_EINVAL, "workspace is NULL");
+    if ((uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
+    const size_t need = rs_transfer_workspace_bytes(train, test, groups);
+    if (ws_bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    TransferWs w = transfer_carve(ws, train, test, groups);
+    cudaSetDevice(c->device);
+    const bool ibk = (flags & RS_MODEL_IBK) != 0;
+    const int Q = test->n_programs;
+    const int max_runs = transfer_runs(groups);
+    const int ld = RS_MAXV * max_runs;
+    const int stride = train->max_feat;
+    cudaError_t e = cudaSuccess;
+    const int64_t* goff = groups ? groups->group_offsets : w.iota;
+    if (!groups) e = rs_launch_iota64(w.iota, (int64_t)Q + 1, c->stream);
+    if (e == cudaSuccess)
+        e = rs_launch_transfer_standardize(train, test, goff, max_runs, stride, w.ZA, w.ZB, w.mu, w.sigma,
+                                           c->dstatus, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_transfer (standardize)");
+    rs_batch za = *train, zb = *test;
+    za.X = w.ZA;
+    za.dtype = RS_F64;
+    zb.X = w.ZB;
+    zb.dtype = RS_F64;
+    e = rs_launch_transfer_blocks(&za, &zb, goff, max_runs, stride, ld, ibk ? nullptr : w.KA, w.Kx, ibk ? 1 : 0,
+                                  c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_transfer (blocks)");
+    rs_transfer_args t{};
+    t.Q = Q;
+    t.group_off = goff;
+    t.max_runs = max_runs;
+    t.n_runs = train->n_programs;
+    t.stat_stride = stride;
+    t.a_row_offsets = train->row_offsets;
+    t.a_feat_width = train->feat_width;
+    t.a_masks = train->masks;
+    t.a_log_time = train->log_time;
+    t.b_row_offsets = test->row_offsets;
+    t.b_feat_width = test->feat_width;
+    t.b_masks = test->masks;
+    t.b_log_time = test->log_time;
+    t.KA = w.KA;
+    t.Kx = w.Kx;
+    t.ld = ld;
+    t.lambda = lambda;
+    t.ibk = ibk ? 1 : 0;
+    t.opt_mask = opt_mask;
+    t.k = k;
+    t.log_tau = log(tau);   // host libm, as in rs_predict_rank
+    t.flags = flags;
+    t.fit_status = fit_status;
+    t.rec_code = rec_code;
+    t.rec_pred = rec_pred;
+    t.pred_all = pred_all;
+    t.counters = (unsigned long long*)counters;
+    t.dstatus = c->dstatus;
+    e = rs_launch_transfer(t, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_transfer");
+}
+
 // ---- CUDA graph of the whole step -------------------------------------------------------------
 struct rs_graph {
     rs_ctx* ctx;

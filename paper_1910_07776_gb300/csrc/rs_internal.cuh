@@ -35,11 +35,43 @@ __device__ __forceinline__ uint64_t rs_full_mask(int V) {
     return V >= 64 ? ~0ull : ((1ull << V) - 1ull);
 }
 
+// Transfer (Table 2): the training runs of problem q are runs group_off[q] .. group_off[q+1]-1,
+// concatenated into one list of N versions (run r's versions at start[r] .. start[r+1]-1).
+// Checks 1..max_runs runs (inside the n_runs runs of the training set) of 1..64 versions, each of width F == fw_test[q] (the width of the
+// problem's test program) with 1 <= F <= stat_stride.  Returns N, or -1 if a check fails.
+__device__ __forceinline__ int rs_group_layout(int q, const int64_t* group_off, int max_runs, int64_t n_runs,
+                                               const int64_t* row_off, const int32_t* fw, const int32_t* fw_test,
+                                               int stat_stride, int (&start)[RS_MAXRUNS + 1], int& F) {
+    const int64_t g0 = group_off[q], g1 = group_off[q + 1];
+    if (g0 < 0 || g1 > n_runs || g1 - g0 < 1 || g1 - g0 > max_runs || g1 - g0 > RS_MAXRUNS) return -1;
+    const int R = (int)(g1 - g0);
+    F = fw_test[q];
+    if (F < 1 || F > stat_stride) return -1;
+    int N = 0;
+    for (int r = 0; r < RS_MAXRUNS + 1; ++r) start[r] = 0;
+    for (int r = 0; r < R; ++r) {
+        const int64_t V = row_off[g0 + r + 1] - row_off[g0 + r];
+        if (V < 1 || V > RS_MAXV || fw[g0 + r] != F) return -1;
+        N += (int)V;
+        start[r + 1] = N;
+    }
+    for (int r = R + 1; r < RS_MAXRUNS + 1; ++r) start[r] = N;
+    return N;
+}
+
 // ---- launchers (defined in the kernel translation units) -------------------------------
 cudaError_t rs_launch_standardize(const rs_batch* b, double* Z, double* mu, double* sigma,
                                   int* dstatus, cudaStream_t st);
 cudaError_t rs_launch_gram_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st);
 cudaError_t rs_launch_dist2_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st);
+cudaError_t rs_launch_transfer_standardize(const rs_batch* train, const rs_batch* test, const int64_t* group_off,
+                                           int max_runs, int stat_stride, double* ZA, double* ZB, double* mu,
+                                           double* sigma, int* dstatus, cudaStream_t st);
+// Blocks of a transfer: KA[q] (ld x ld, the group's Gram, ridge only) and Kx[q] (64 x ld:
+// test row t against group version u, dot products or, with dist, squared distances).
+cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch* test_std, const int64_t* group_off,
+                                      int max_runs, int stat_stride, int ld, double* KA, double* Kx, int dist,
+                                      cudaStream_t st);
 size_t rs_gram_tc_workspace_bytes(int64_t P, int max_feat);
 cudaError_t rs_launch_gram_bf16x3_ws(const rs_batch* b, double* K, void* ws, size_t ws_bytes, int* dstatus,
                                      cudaStream_t st);
@@ -96,6 +128,40 @@ struct rs_fit_args {
 #define RS_NSTAGE_EVENTS 7   // before pairs, after pairs / plan / bucket / solve / solve-large / rank
 size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t rows_cap);
 cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st);
+// Table 2 transfer: fits of each problem's training group, predictions for its test program,
+// ranking and scoring (one block per problem).
+struct rs_transfer_args {
+    int Q;
+    const int64_t* group_off;     // [Q+1]
+    int max_runs;
+    int64_t n_runs;               // runs of the training set
+    int stat_stride;
+    const int64_t* a_row_offsets;
+    const int32_t* a_feat_width;
+    const uint8_t* a_masks;
+    const double* a_log_time;
+    const int64_t* b_row_offsets;
+    const int32_t* b_feat_width;
+    const uint8_t* b_masks;
+    const double* b_log_time;
+    const double* KA;             // [Q][ld][ld] group Gram (ridge)
+    const double* Kx;             // [Q][64][ld] cross block (dot products, or squared distances for IBK)
+    int ld;
+    double lambda;
+    int ibk;
+    int opt_mask;
+    int k;
+    double log_tau;
+    int flags;
+    uint8_t* fit_status;          // [Q][6], nullable
+    uint32_t* rec_code;
+    double* rec_pred;
+    double* pred_all;
+    unsigned long long* counters;
+    int* dstatus;
+};
+cudaError_t rs_launch_transfer(const rs_transfer_args& a, cudaStream_t st);
+cudaError_t rs_launch_iota64(int64_t* out, int64_t n, cudaStream_t st);
 size_t rs_surrogate_blob_floats();
 size_t rs_surrogate_train_ws_bytes(int B);
 size_t rs_surrogate_infer_ws_bytes(int64_t chunk);

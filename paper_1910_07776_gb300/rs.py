@@ -36,7 +36,7 @@ EXPORTS = [
     "rs_profile_enable", "rs_profile_read", "rs_cv_step_static", "rs_gemm_bf16",
     "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
     "rs_surrogate_train", "rs_surrogate_infer", "rs_cv_graph_create", "rs_cv_graph_launch",
-    "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning",
+    "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning", "rs_transfer", "rs_transfer_workspace_bytes",
 ]
 
 
@@ -59,6 +59,11 @@ class _Batch(C.Structure):
 class _MlpCfg(C.Structure):
     _fields_ = [("batch_rows", C.c_int32), ("use_graph", C.c_int32), ("steps", C.c_int64),
                 ("lr", C.c_float), ("weight_decay", C.c_float)]
+
+
+class _Groups(C.Structure):
+    _fields_ = [("n_groups", C.c_int64), ("max_runs", C.c_int32), ("reserved", C.c_int32),
+                ("group_offsets", C.c_void_p)]
 
 
 class _Splits(C.Structure):
@@ -119,9 +124,12 @@ def load(path: str = SO):
     L.rs_surrogate_infer.argtypes = [P, P, P, i64, C.c_float, P, P, P, P, i, d, i, P, P, P, C.c_size_t, i]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
+    L.rs_transfer_workspace_bytes.argtypes = [P, P, P]
+    L.rs_transfer_workspace_bytes.restype = C.c_size_t
+    L.rs_transfer.argtypes = [P, P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes", "rs_gram_workspace_bytes",
-                        "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
+                        "rs_transfer_workspace_bytes", "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -384,6 +392,34 @@ class Context:
             int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
 
+    def transfer_workspace_bytes(self, train: DeviceBatch, test: DeviceBatch, groups=None) -> int:
+        ac, bc = train.c(), test.c()
+        g = _groups_c(groups, test)
+        return int(self.L.rs_transfer_workspace_bytes(C.byref(ac), C.byref(bc), None if g is None else C.byref(g)))
+
+    def transfer(self, train: DeviceBatch, test: DeviceBatch, workspace, rec_code, groups=None, lam: float = 1e-3,
+                 k: int = 3, tau: float = 1.05, flags: int = 0, opt_mask: int = 0x3F, fit_status=None,
+                 rec_pred=None, pred_all=None, counters=None):
+        """Table 2 transfer: problem q trains on the runs ``groups[q] .. groups[q+1]-1`` of
+        ``train`` (a device int64 tensor of offsets; None: run q) and ranks the versions of
+        ``test``'s program q; rows are the test set's versions in order."""
+        ac, bc = train.c(), test.c()
+        g = _groups_c(groups, test)
+        self._check(self.L.rs_transfer(
+            self.h, C.byref(ac), C.byref(bc), None if g is None else C.byref(g), float(lam), int(k), float(tau),
+            int(flags), int(opt_mask), _ptr(workspace), workspace.numel() * workspace.element_size(),
+            _ptr(fit_status), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
+
+
+def _groups_c(groups, test: "DeviceBatch"):
+    """(offsets tensor on the device, max runs) -> the C struct; None stays None."""
+    if groups is None:
+        return None
+    offs, max_runs = groups
+    if offs.dtype != torch.int64 or offs.numel() != test.n_programs + 1:
+        raise ValueError("group offsets: int64 tensor of n_programs + 1 entries")
+    return _Groups(test.n_programs, int(max_runs), 0, _ptr(offs))
+
 
 class Surrogate:
     """The MLP surrogate's state (one device blob) and its training / inference calls."""
@@ -502,3 +538,27 @@ def cv_run(ctx: Context, b: DeviceBatch, s: DeviceSplits, lam=1e-3, k=3, tau=1.0
     if want_Z:
         res["Z"] = Z.cpu().numpy()
     return res
+
+
+def transfer_run(ctx: Context, train: DeviceBatch, test: DeviceBatch, groups=None, lam=1e-3, k=3, tau=1.05,
+                 flags=0, opt_mask=0x3F):
+    """One transfer call with fresh outputs; returns host numpy outputs.  groups: host array of
+    Q + 1 run offsets, or None (run q trains problem q)."""
+    dev = train.X.device
+    R, Q = test.n_rows, test.n_programs
+    g = None
+    if groups is not None:
+        offs = np.ascontiguousarray(groups, dtype=np.int64)
+        g = (torch.from_numpy(offs).to(dev), int(np.diff(offs).max()))
+    ws = ctx.workspace(ctx.transfer_workspace_bytes(train, test, g))
+    out = alloc_outputs(R, 0, k, dev)
+    st = torch.empty(Q * NOPT, dtype=torch.uint8, device=dev)
+    ctx.transfer(train, test, ws, out.rec_code, groups=g, lam=lam, k=k, tau=tau, flags=flags, opt_mask=opt_mask,
+                 fit_status=st, rec_pred=out.rec_pred, pred_all=out.pred_all, counters=out.counters)
+    torch.cuda.synchronize(dev)
+    ctx.check_device_status()
+    return dict(rec_code=out.rec_code.cpu().numpy().view(np.uint32),
+                rec_pred=out.rec_pred.cpu().numpy().reshape(R, k),
+                pred_all=out.pred_all.cpu().numpy().reshape(R, NOPT),
+                counters=out.counters.cpu().numpy().view(np.uint64),
+                fit_status=st.cpu().numpy().reshape(Q, NOPT))

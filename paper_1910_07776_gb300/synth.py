@@ -393,3 +393,156 @@ def make_vectors(n: int, F: int = 256, seed: int = 0, dtype=np.float32) -> np.nd
     """Standard-normal stand-ins for standardized feature vectors (surrogate inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed ^ 0x7EC7))
     return rng.standard_normal((n, F)).astype(dtype)
+
+
+# ---------------------------------------------------------------------- Table 2 protocols
+# Two subject codes, an irregular one ("BH", six inputs) and a regular one ("NB", four inputs),
+# each profiled three times per input (Sec. 5, Table 1).  Optimizations 4 and 5 (FTZ and RSQRT
+# in the paper's numbering) are the only ones the two codes share (Sec. 6.2); bits 0-3 stand
+# for different source changes in each code.
+CODES = (("BH", 6), ("NB", 4))
+SHARED_OPTS = 0b110000
+
+
+def make_runs(codes=CODES, runs: int = 3, feat: int = 96, dtype=np.float64, seed: int = 0,
+              with_cycles: bool = True, input_spread: float = 0.4, version_noise: float = 0.3,
+              run_noise: float = 0.05, label_noise: float = 0.05, run_label_noise: float = 0.01) -> ProgramBatch:
+    """One program entry per (code, input, run), all 64 versions, in that nesting order; the
+    list of (code, input, run) is ``meta["index"]``.
+
+    Recipe (one PCG64 stream): per code a latent state ``h_c ~ N(0, I_8)`` and, for its own
+    optimizations (bits 0-3), its own effect directions and counter shifts; the shared ones
+    (bits 4, 5) use directions and shifts common to both codes.  Input i moves the state,
+    ``h_ci = h_c + input_spread * N(0, I_8)``, and scales the effects by
+    ``0.6 + 0.4 i / (n_inputs - 1)`` (larger inputs, clearer effects).  A version's log
+    speedup and log counter rates get a per-input draw (``label_noise``, ``version_noise``)
+    that every run of that input repeats, and each run adds its own small noise
+    (``run_label_noise``, ``run_noise``).  Otherwise as ``make_batch``: main effects
+    ``0.3 w_j.h / |w_j|``, interactions ``0.1 u_jk.h / |u_jk|``, counter shifts
+    ``U_{k,f} + 0.3 (C_k h)_f / sqrt(8)``, cycles ``exp(log t + 20 + N(0, 0.02^2))``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    F = int(feat)
+    w_sh = rng.standard_normal((N_OPT, LATENT))
+    u_sh = rng.standard_normal((N_OPT, N_OPT, LATENT))
+    U_sh = 0.5 * rng.standard_normal((N_OPT, F))
+    C_sh = rng.standard_normal((N_OPT, F, LATENT))
+    sM = np.sqrt(max(2.25 - 3.0 * (0.25 + 0.09) - version_noise ** 2, 0.1) / LATENT)
+    M = sM * rng.standard_normal((F, LATENT))
+    all_masks = np.arange(N_MASK, dtype=np.int64)
+    mb = ((all_masks[:, None] >> np.arange(N_OPT)[None, :]) & 1).astype(np.float64)   # [64,6]
+    own = np.arange(N_OPT) < 4
+    X_parts, m_parts, lt_parts, cyc_parts, index = [], [], [], [], []
+    for code, n_inputs in codes:
+        h_c = rng.standard_normal(LATENT)
+        w = np.where(own[:, None], rng.standard_normal((N_OPT, LATENT)), w_sh)
+        u = np.where(own[:, None, None] | own[None, :, None], rng.standard_normal((N_OPT, N_OPT, LATENT)), u_sh)
+        U = np.where(own[:, None], 0.5 * rng.standard_normal((N_OPT, F)), U_sh)
+        Cc = np.where(own[:, None, None], rng.standard_normal((N_OPT, F, LATENT)), C_sh)
+        t0_c = rng.standard_normal()
+        for i in range(n_inputs):
+            h = h_c + input_spread * rng.standard_normal(LATENT)
+            scale = 0.6 + 0.4 * i / max(n_inputs - 1, 1)
+            a = scale * 0.3 * (w @ h) / np.linalg.norm(w, axis=1)
+            b = np.triu(scale * 0.1 * (u @ h) / np.linalg.norm(u, axis=2), 1)
+            ls_in = mb @ a + np.einsum("vj,jk,vk->v", mb, b, mb) + label_noise * rng.standard_normal(N_MASK)
+            shift = U + 0.3 * np.einsum("kfl,l->kf", Cc, h) / np.sqrt(LATENT)
+            logx_in = (M @ h)[None, :] + mb @ shift + version_noise * rng.standard_normal((N_MASK, F))
+            t0 = t0_c + 0.7 * i
+            for r in range(runs):
+                ls = ls_in + run_label_noise * rng.standard_normal(N_MASK)
+                log_t = t0 - ls
+                x = np.exp(logx_in + run_noise * rng.standard_normal((N_MASK, F)))
+                if with_cycles:
+                    cyc = np.exp(log_t + 20.0 + 0.02 * rng.standard_normal(N_MASK))
+                    x = x * cyc[:, None]
+                    cyc_parts.append(cyc)
+                X_parts.append(x.reshape(-1))
+                m_parts.append(all_masks.astype(np.uint8))
+                lt_parts.append(log_t)
+                index.append((code, i, r))
+    P = len(index)
+    return ProgramBatch(
+        X=np.concatenate(X_parts).astype(dtype), x_offsets=np.arange(P, dtype=np.int64) * N_MASK * F,
+        row_offsets=np.arange(P + 1, dtype=np.int64) * N_MASK, feat_width=np.full(P, F, dtype=np.int32),
+        masks=np.concatenate(m_parts), log_time=np.concatenate(lt_parts).astype(np.float64),
+        cycles=(np.concatenate(cyc_parts).astype(np.float64) if with_cycles else None),
+        meta=dict(gen=GEN_VERSION + "/runs", seed=seed, index=index, runs=runs, codes=tuple(codes)))
+
+
+def take_programs(batch: ProgramBatch, programs: Sequence[int]) -> ProgramBatch:
+    """A new batch holding copies of the given programs, in the given order."""
+    xs, ms, lts, cys, xo, ro, fw = [], [], [], [], [], [0], []
+    pos = 0
+    for p in programs:
+        V, F = batch.versions(p), int(batch.feat_width[p])
+        rows = batch.program_rows(p)
+        xs.append(batch.program_X(p).reshape(-1))
+        ms.append(batch.masks[rows])
+        lts.append(batch.log_time[rows])
+        if batch.cycles is not None:
+            cys.append(batch.cycles[rows])
+        xo.append(pos)
+        pos += V * F
+        ro.append(ro[-1] + V)
+        fw.append(F)
+    return ProgramBatch(
+        X=np.concatenate(xs), x_offsets=np.asarray(xo, dtype=np.int64), row_offsets=np.asarray(ro, dtype=np.int64),
+        feat_width=np.asarray(fw, dtype=np.int32), masks=np.concatenate(ms), log_time=np.concatenate(lts),
+        cycles=np.concatenate(cys) if batch.cycles is not None else None, meta=dict(batch.meta, taken=list(programs)))
+
+
+@dataclass
+class TransferProblems:
+    """The problems of one Table 2 experiment: problem q trains on runs
+    ``groups[q] .. groups[q+1]-1`` of ``train`` and tests on program q of ``test``."""
+    experiment: int
+    train: ProgramBatch
+    test: ProgramBatch
+    groups: np.ndarray          # int64 [Q+1]
+    opt_mask: int
+    pairs: list                 # (train (code, input, runs), test (code, input, run)) per problem
+
+
+def table2_problems(runs: ProgramBatch, experiment: int) -> TransferProblems:
+    """Table 2's six experiments on a batch from ``make_runs`` (Sec. 5 / 6):
+    1. one run of a BH input trains; every run of that input (its own included) is tested;
+    2. as 1, but only the other runs are tested;
+    3. two runs of a BH input train; the third is tested;
+    4. all runs of a BH input train; every run of every other BH input is tested;
+    5. all runs of a BH input train; every run of every NB input is tested (FTZ and RSQRT only);
+    6. all runs of an NB input train; every run of every BH input is tested (FTZ and RSQRT only)."""
+    idx = {key: p for p, key in enumerate(runs.meta["index"])}
+    n_runs = runs.meta["runs"]
+    n_in = dict(runs.meta["codes"])
+    probs = []          # (list of training programs, test program, description)
+    if experiment in (1, 2):
+        for i in range(n_in["BH"]):
+            for r in range(n_runs):
+                for r2 in range(n_runs):
+                    if experiment == 2 and r2 == r:
+                        continue
+                    probs.append(([idx[("BH", i, r)]], idx[("BH", i, r2)], (("BH", i, (r,)), ("BH", i, r2))))
+    elif experiment == 3:
+        for i in range(n_in["BH"]):
+            for r2 in range(n_runs):
+                tr = tuple(r for r in range(n_runs) if r != r2)
+                probs.append(([idx[("BH", i, r)] for r in tr], idx[("BH", i, r2)], (("BH", i, tr), ("BH", i, r2))))
+    elif experiment in (4, 5, 6):
+        src, dst = {4: ("BH", "BH"), 5: ("BH", "NB"), 6: ("NB", "BH")}[experiment]
+        for i in range(n_in[src]):
+            tr = tuple(range(n_runs))
+            for i2 in range(n_in[dst]):
+                if experiment == 4 and i2 == i:
+                    continue
+                for r2 in range(n_runs):
+                    probs.append(([idx[(src, i, r)] for r in tr], idx[(dst, i2, r2)],
+                                  ((src, i, tr), (dst, i2, r2))))
+    else:
+        raise ValueError("experiment must be 1..6")
+    train_list = [p for tr, _, _ in probs for p in tr]
+    groups = np.zeros(len(probs) + 1, dtype=np.int64)
+    groups[1:] = np.cumsum([len(tr) for tr, _, _ in probs])
+    return TransferProblems(
+        experiment=experiment, train=take_programs(runs, train_list),
+        test=take_programs(runs, [te for _, te, _ in probs]), groups=groups,
+        opt_mask=SHARED_OPTS if experiment in (5, 6) else 0x3F, pairs=[d for _, _, d in probs])
