@@ -35,17 +35,25 @@ CFG = dict(programs=64, versions=(16, 64), feat=256, splits=4096, lam=1e-3, k=3,
 FP64_PEAK_NOMINAL_GFLOPS = 152 * 4 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 
 
+def source_sha():
+    """sha256 prefix of the sources of the profiled step kernels (the fit/predict/rank file and
+    the ranking header it includes)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_fit.cu", "rank_row.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1910_07776_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(stage):
     """DRAM bytes per step of a stage from the committed ncu summary, or None when the kernel
-    source has changed since the capture (its sha256 prefix is recorded in the summary)."""
-    import hashlib
+    sources have changed since the capture (their sha256 prefix is recorded in the summary)."""
     try:
         txt = open(os.path.join(ROOT, "profiles", "batched_cv_kernels.md")).read()
-        src = open(os.path.join(ROOT, "paper_1910_07776_gb300", "csrc", "k_fit.cu"), "rb").read()
+        sha = source_sha()
     except OSError:
         return None
-    sha = hashlib.sha256(src).hexdigest()[:16]
-    if f"source_sha256_prefix k_fit.cu = {sha}" not in txt:
+    if f"source_sha256_prefix k_fit.cu+rank_row.cuh = {sha}" not in txt:
         return None
     for line in txt.splitlines():
         if line.startswith(f"traffic_bytes_per_step {stage} = "):
@@ -265,6 +273,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-ibk", action="store_true")
+    ap.add_argument("--no-transfer", action="store_true")
     ap.add_argument("--surrogate-epochs", type=int, default=2)
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
@@ -405,6 +414,10 @@ def main():
     if rank == 0 and not args.only_step and not args.no_ibk:
         ibk = run_ibk(rs, ctx, batch, splits, dev, stream, flush, args)
 
+    xfer = None
+    if rank == 0 and not args.only_step and not args.no_transfer:
+        xfer = run_transfer(rs, ctx, dev, stream, flush, args)
+
     unev = None
     if rank == 0 and not args.only_step and not args.no_uneven:
         unev = run_uneven(rs, ctx, dev, stream, flush, args)
@@ -441,6 +454,7 @@ def main():
         "precision_form": prec,
         "uneven_form": unev,
         "ibk_form": ibk,
+        "table2_transfer": xfer,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -560,6 +574,75 @@ def run_ibk(rs, ctx, batch, splits, dev, stream, flush, args):
     sp = synth.make_splits(b, "lovo")
     out["lovo"] = {"workload": "256 programs x 64 versions (all masks) x 256 f32 features, leave-one-"
                                "version-out (16,384 splits, 98,304 fits of 31 pairs)", **measure(b, sp, 20)}
+    return out
+
+
+PAPER_TABLE3_IBK = {1: 97.3, 2: 96.0, 3: 96.3, 4: 92.0, 5: 83.6, 6: 55.7}   # Table 3, % (real profiles)
+
+
+def run_transfer(rs, ctx, dev, stream, flush, args):
+    """Table 2's six experiments (Sec. 5) on the seeded stand-ins of the BH / NB runs
+    (synth.make_runs: 6 + 4 inputs x 3 runs x 64 versions x 96 counters): per experiment and
+    learner one rs_transfer call (device time, after warm-up), the sign accuracy of Table 3,
+    the top-1 hit rate, and the AC/EX ratios (actual over expected speedup, Sec. 5) of every
+    scored prediction.  Table 3's values come from the paper's real profiles: context only."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = synth.make_runs(seed=0)
+    out = {"data": "synthetic stand-ins: 2 codes (6 and 4 inputs) x 3 runs x 64 versions x 96 f64 counters",
+           "experiments": {}}
+    for e in range(1, 7):
+        pr = synth.table2_problems(runs, e)
+        dtr = rs.DeviceBatch.from_host(pr.train, dev)
+        dte = rs.DeviceBatch.from_host(pr.test, dev)
+        offs = torch.from_numpy(pr.groups).to(dev)
+        g = (offs, int(np.diff(pr.groups).max()))
+        ws = ctx.workspace(ctx.transfer_workspace_bytes(dtr, dte, g))
+        R = dte.n_rows
+        # actual log speedups of the test rows (host, from the test set's own times)
+        act = np.full((R, 6), np.nan)
+        for q in range(pr.test.n_programs):
+            rows = pr.test.program_rows(q)
+            m = pr.test.masks[rows].astype(int)
+            lt = pr.test.log_time[rows]
+            slot = {int(v): i for i, v in enumerate(m)}
+            for t in range(len(m)):
+                for j in range(6):
+                    w = slot.get(int(m[t]) | (1 << j))
+                    if not (m[t] >> j) & 1 and w is not None:
+                        act[rows.start + t, j] = lt[t] - lt[w]
+        res = {"problems": int(pr.test.n_programs), "train_runs_per_problem": int(np.diff(pr.groups).max()),
+               "test_rows": int(R), "opt_mask": int(pr.opt_mask), "paper_ibk_accuracy_pct": PAPER_TABLE3_IBK[e]}
+        for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK)):
+            o = rs.alloc_outputs(R, 0, CFG["k"], dev)
+            call = lambda: ctx.transfer(dtr, dte, ws, o.rec_code, groups=g, lam=CFG["lam"], k=CFG["k"],
+                                        tau=CFG["tau"], flags=flags, opt_mask=pr.opt_mask, rec_pred=o.rec_pred,
+                                        pred_all=o.pred_all, counters=o.counters)
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            o.counters.zero_()
+            reps, tot = 10, 0.0
+            for _ in range(reps):
+                flush.fill_(1)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ctx.check_device_status()
+            c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64) / reps
+            pa = o.pred_all.cpu().numpy().reshape(R, 6)
+            sc = ~np.isnan(pa) & ~np.isnan(act)
+            ratio = np.exp(act[sc] - pa[sc])
+            res[name] = {"ms": tot / reps, "sign_accuracy": c[3] / max(c[2], 1),
+                         "top1_hit_rate": c[8] / max(c[7], 1), "rec_precision": c[6] / max(c[5], 1),
+                         "scored": int(c[2]),
+                         "ac_ex_quantiles_5_25_50_75_95": [float(x) for x in np.quantile(ratio, [.05, .25, .5, .75, .95])]
+                         if ratio.size else None,
+                         "ac_ex_within_10pct": float(np.mean(np.abs(ratio - 1.0) <= 0.1)) if ratio.size else None}
+        out["experiments"][str(e)] = res
     return out
 
 

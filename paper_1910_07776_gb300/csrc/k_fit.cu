@@ -28,7 +28,7 @@
 #include <string.h>
 
 #include "mbar.cuh"
-#include "rs_internal.cuh"
+#include "rank_row.cuh"
 
 namespace {
 
@@ -38,26 +38,7 @@ constexpr int kKld = RS_MAXV + 1;           // padded row stride of K in shared 
 constexpr int kNReg = 10;                   // largest n solved by one thread in registers
 constexpr int kNMid = 16;                   // largest n solved by one thread from shared memory
 constexpr int kHist = RS_MAXPAIRS + 2;      // n = 0..32, plus one end slot
-constexpr long long kNaNBits = 0x7ff8000000000000ll;
-
 __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
-
-__device__ __forceinline__ double nan_d() { return __longlong_as_double(kNaNBits); }
-
-// x > 0 and finite, decided on the bit pattern (no FP64 instruction).
-__device__ __forceinline__ bool pos_finite(double x) {
-    const long long b = __double_as_longlong(x);
-    return b > 0 && b < 0x7ff0000000000000ll;
-}
-__device__ __forceinline__ bool finite_bits(double x) {
-    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
-}
-// Order-preserving integer key of a non-NaN double; -0.0 and +0.0 share key 0.
-__device__ __forceinline__ long long okey(double x) {
-    long long b = __double_as_longlong(x);
-    if (b == (long long)0x8000000000000000ull) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
 
 // float <-> double for values inside the float normal range, by re-packing the IEEE-754
 // fields with integer operations (the mantissa is truncated).  Used only to seed Newton
@@ -103,48 +84,10 @@ __device__ __forceinline__ double rcp_newton(double d) {
     return fma(r0, fma(t, t, t), r0);
 }
 
-long long okey_host(double x) {
-    long long b;
-    memcpy(&b, &x, sizeof(b));
-    if (b == (long long)0x8000000000000000ull) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-
 // The a-th set bit (0-based) of x; x must have more than a set bits.
 __device__ __forceinline__ int select_bit(uint64_t x, int a) {
     for (int i = 0; i < a; ++i) x &= x - 1;
     return __ffsll((long long)x) - 1;
-}
-
-// Scoring summary of version t of a program (its masks msk, log times lt, and the slot of each
-// mask, -1 if absent): bits 0-5 known (version t|j exists), bits 6-11 actual speedup > 1,
-// bits 12-29 the six optimizations ordered by actual log speedup (descending, lower index
-// first on ties, unknown last), 3 bits each.  t >= V gives the summary of an empty row.
-__device__ __forceinline__ uint32_t row_summary(int t, int V, const uint8_t* msk, const double* lt,
-                                                const int8_t* slot_of) {
-    long long key[RS_NOPT];
-    int kn = 0, apos = 0;
-    for (int j = 0; j < RS_NOPT; ++j) {
-        key[j] = (long long)0x8000000000000000ull;
-        if (t < V && !((msk[t] >> j) & 1)) {
-            const int w = slot_of[msk[t] | (1 << j)];
-            if (w >= 0) {
-                key[j] = okey(lt[t] - lt[w]);
-                kn |= 1 << j;
-                apos |= (key[j] > 0) << j;
-            }
-        }
-    }
-    uint32_t ord = 0;
-    int used = 0;
-    for (int x = 0; x < RS_NOPT; ++x) {
-        int best = -1;
-        for (int j = 0; j < RS_NOPT; ++j)
-            if (!((used >> j) & 1) && (best < 0 || key[j] > key[best])) best = j;
-        used |= 1 << best;
-        ord |= (uint32_t)best << (3 * x);
-    }
-    return (uint32_t)kn | ((uint32_t)apos << 6) | (ord << 12);
 }
 
 // ====================================================================== pair tables
@@ -339,12 +282,6 @@ struct PredTarget {
     uint64_t cand;        // test slots to predict (candidates)
     int64_t room;         // rows left in the buffer from dst (guards a wrong size hint)
 };
-
-// A fit that failed writes this signalling-NaN pattern to its candidate rows instead of
-// predictions.  Arithmetic never produces a signalling NaN, so the rank pass tells failed
-// fits from predictions by the value alone, without reading the fit status of each row's
-// split (fits without a training pair are marked in the row records instead).
-constexpr long long kFailBits = 0x7ff4000000000001ll;
 
 __device__ __forceinline__ void mark_failed(const PredTarget& pt) {
     const double fail = __longlong_as_double(kFailBits);
@@ -661,7 +598,6 @@ solve_small_kernel(const SolveArgs a, unsigned long long* work) {
 }
 
 // ====================================================================== IBK (Sec. 3.4)
-constexpr int kIbkK = RS_IBK_NEIGHBORS;
 
 // Mean label of the kIbkK pairs of pm (more than kIbkK of them) whose before versions are
 // nearest to a test row, Dt being that row of the distance block and pb the before slot of
@@ -679,21 +615,7 @@ __device__ __forceinline__ double ibk_nearest_mean(uint32_t pm, const double* __
     }
     for (uint32_t x = pm; x; x &= x - 1) {
         const int q = __ffs(x) - 1;
-        const unsigned long long d = (unsigned long long)__double_as_longlong(__ldg(Dt + pb[q]));
-        if (d < kd[kIbkK - 1]) {
-            // insertion into the ordered list, from the old values
-#pragma unroll
-            for (int i = kIbkK - 1; i > 0; --i) {
-                const bool shift = kd[i - 1] > d;
-                const bool here = !shift && kd[i] > d;
-                kd[i] = shift ? kd[i - 1] : (here ? d : kd[i]);
-                kq[i] = shift ? kq[i - 1] : (here ? q : kq[i]);
-            }
-            if (kd[0] > d) {
-                kd[0] = d;
-                kq[0] = q;
-            }
-        }
+        ibk_insert(kd, kq, (unsigned long long)__double_as_longlong(__ldg(Dt + pb[q])), q);
     }
     uint32_t chosen = 0;
 #pragma unroll
@@ -1205,125 +1127,13 @@ solve_large_kernel(const SolveArgs a) {
 }
 
 // ====================================================================== rank pass
-// One warp per split; its test rows are compacted onto the lanes (one row per lane).  No
-// FP64 arithmetic: predictions (written by the solve kernels) are compared as order keys.
-// Ranking: 15 comparisons give, for each candidate j, the set of candidates that rank
-// before it (larger key; on equal keys the lower index); its place is the popcount of
-// that set restricted to the candidates at or above the threshold.
-struct RankPassArgs {
-    const int64_t* rec_offsets;
-    int64_t S;
-    const double* predbuf;       // [6][PS]
-    int64_t R;                   // rows of the buffer
-    int64_t PS;                  // plane stride (even)
-    const unsigned long long* row_info;  // [R] scoring summary | version mask << 30
-    int* dstatus;
-    int k;
-    long long ktau;
-    int flags;
-    uint32_t* rec_code;
-    double* rec_pred;
-    double* pred_all;
-    unsigned long long* counters;
-};
-
+// One thread per test row: its row record and its six predictions (written by the solve
+// kernels) go through rank_row; no FP64 arithmetic.
 constexpr int kRankTile = 256;               // rows per tile = threads per block
 constexpr int kRankStages = 3;
 constexpr int kRankPlanes = 1 + RS_NOPT;     // the row records, then the six prediction planes
 constexpr size_t kRankStageBytes = (size_t)kRankPlanes * kRankTile * 8;
 constexpr size_t kRankSmem = kRankStages * kRankStageBytes + kRankStages * 8;
-
-// Per-thread tallies of the scoring counters.
-struct RankTally {
-    uint32_t rows = 0, pred = 0, scored = 0, sign = 0, rec = 0, reck = 0, rech = 0, t1 = 0, t1h = 0, inv = 0;
-};
-
-// Ranking, threshold, top-k, outputs and scoring of one test row (Sec. 2 tier 3, Sec. 6):
-// candidates (versions lacking j, or all with RS_RANK_ALL) whose fit succeeded are ranked by
-// their predictions as order-preserving integer keys (ties: lower j first); those at or
-// above log tau form the recommendation, the first k of them reported.
-__device__ __forceinline__ void rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
-                                         const double (&pred)[RS_NOPT], RankTally& c) {
-    const uint32_t info = (uint32_t)info64;
-    const int mt = (int)(info64 >> 30) & 63;
-    const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
-    // a candidate counts when its fit had a training pair (row record) and did not fail
-    // (the failure pattern in the prediction plane)
-    int okm = ~(int)(info64 >> 36) & 63;
-#pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) okm &= ~((int)(__double_as_longlong(pred[j]) == kFailBits) << j);
-    const int validm = candm & okm;
-    long long key[RS_NOPT];
-    int above = 0, spos = 0;
-#pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) {
-        key[j] = okey(pred[j]);
-        above |= (key[j] >= a.ktau) << j;
-        spos |= (key[j] > 0) << j;
-    }
-    above &= validm;
-    int bm[RS_NOPT];                           // bm[j]: candidates ranking before j
-#pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
-#pragma unroll
-    for (int i = 0; i < RS_NOPT; ++i)
-#pragma unroll
-        for (int j = i + 1; j < RS_NOPT; ++j) {
-            if (key[i] >= key[j]) bm[j] |= 1 << i;
-            else bm[i] |= 1 << j;
-        }
-    uint32_t code = 0x0FFFFFF0u;
-    int rk = 0;
-    int pos[RS_NOPT];
-#pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) {
-        pos[j] = __popc(bm[j] & above);
-        if (((above >> j) & 1) && pos[j] < a.k) {
-            code = (code & ~(0xFu << (4 + 4 * pos[j]))) | ((uint32_t)j << (4 + 4 * pos[j]));
-            rk |= 1 << j;
-        }
-    }
-    const int nrec = __popc(rk);
-    code = (code & ~0xFu) | (uint32_t)nrec;
-    a.rec_code[row] = code;
-    if (a.rec_pred) {                          // each chosen candidate writes its own slot
-        double* o = a.rec_pred + row * a.k;
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j)
-            if ((rk >> j) & 1) o[pos[j]] = pred[j];
-#pragma unroll
-        for (int x = 0; x < RS_NOPT; ++x)
-            if (x >= nrec && x < a.k) o[x] = nan_d();
-    }
-    if (a.pred_all)
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j)
-            a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
-    const int known = info & 63, apos = (info >> 6) & 63;
-    const int scored = validm & known;
-    c.rows += 1;
-    c.pred += __popc(validm);
-    c.scored += __popc(scored);
-    c.sign += __popc(scored & ~(spos ^ apos));
-    c.rec += nrec;
-    c.reck += __popc(rk & scored);
-    c.rech += __popc(rk & scored & apos);
-    c.inv += __popc(candm & ~okm);
-    if (scored) {
-        int bp = 0;
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j)
-            if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
-        int ba = -1;
-#pragma unroll
-        for (int x = 0; x < RS_NOPT; ++x) {
-            const int j = (info >> (12 + 3 * x)) & 7;
-            if (ba < 0 && ((scored >> j) & 1)) ba = j;
-        }
-        c.t1 += 1;
-        c.t1h += (bp == ba);
-    }
-}
 
 // Persistent blocks over tiles of 256 rows.  Thread 0 streams each tile -- the row records
 // and the six prediction planes, seven 1-D TMA bulk copies -- into a 3-stage shared-memory
@@ -1412,297 +1222,6 @@ rank_pass_kernel(const RankPassArgs a) {
             if ((tid & 31) == 0 && v) atomicAdd(a.counters + slot[q], (unsigned long long)v);
         }
     }
-}
-
-// ====================================================================== transfer (Table 2)
-// One block per transfer problem q: the fits of its training group (every before/after pair
-// of every run, run by run in ascending before slot, a pair never spanning two runs), the
-// predictions for every version t of its test program, ranking and scoring.  The group's
-// versions form one list of N (rs_group_layout); KA[q] is their Gram, Kx[q][t][u] the block
-// between test row t and version u (dot products; squared distances for IBK).
-// Ridge: the bordered dual system of each optimization, M = KA(pairs) + lambda I = L D L^T
-// (right-looking, one thread per row, in shared memory), then b and alpha as in fit_fixed and
-// the prediction b + sum_a alpha_a Kx[t][u_a].  IBK: the mean label of the kIbkK pairs
-// nearest to t.  Candidates: outside t's mask (all six with RS_RANK_ALL) and inside
-// opt_mask; ranking, threshold, top-k and scoring as in the rank pass with the test
-// program's own times.
-constexpr int kTrPairs = RS_MAXPAIRS * RS_MAXRUNS;   // pairs of one fit
-constexpr int kTrRows = RS_MAXV * RS_MAXRUNS;        // versions of one group
-constexpr int kTrThreads = kTrPairs;                 // one thread per matrix row
-constexpr int kTrLd = kTrPairs + 1;
-
-struct TransferSmem {
-    double M[kTrPairs * kTrLd];          // the factor (lower triangle, D on the diagonal)
-    double col[kTrPairs];
-    double ty[kTrPairs], t1[kTrPairs];
-    double coef[RS_NOPT][kTrPairs + 1];  // b, alpha
-    double yl[RS_NOPT][kTrPairs];
-    double lt_a[kTrRows];
-    double lt_b[RS_MAXV];
-    double bval;
-    uint16_t pu[RS_NOPT][kTrPairs];      // group version of each pair's before side
-    uint8_t msk_a[kTrRows];
-    int8_t slot_a[RS_MAXRUNS][RS_MAXV];
-    uint8_t msk_b[RS_MAXV];
-    int8_t slot_b[RS_MAXV];
-    int np[RS_NOPT], st[RS_NOPT];
-};
-
-struct TransferArgs {
-    const int64_t* group_off;
-    int max_runs, stat_stride;
-    int64_t n_runs;
-    const int64_t* a_row;
-    const int32_t* a_fw;
-    const uint8_t* a_masks;
-    const double* a_lt;
-    const int64_t* b_row;
-    const int32_t* b_fw;
-    const uint8_t* b_masks;
-    const double* b_lt;
-    const double* KA;
-    const double* Kx;
-    int ld;
-    double lambda;
-    int ibk, opt_mask, rank_all;
-    uint8_t* fit_status;
-    RankPassArgs r;                      // k, ktau, flags (without RS_RANK_ALL), outputs, counters
-};
-
-// Insertion of (d, q) into the list of the kIbkK nearest, ordered by (distance, index):
-// distances are non-negative, so their bit patterns order like the values; a candidate
-// replaces the last entry only when strictly nearer.
-__device__ __forceinline__ void ibk_insert(unsigned long long (&kd)[kIbkK], int (&kq)[kIbkK],
-                                           unsigned long long d, int q) {
-    if (d >= kd[kIbkK - 1]) return;
-#pragma unroll
-    for (int i = kIbkK - 1; i > 0; --i) {
-        const bool shift = kd[i - 1] > d;
-        const bool here = !shift && kd[i] > d;
-        kd[i] = shift ? kd[i - 1] : (here ? d : kd[i]);
-        kq[i] = shift ? kq[i - 1] : (here ? q : kq[i]);
-    }
-    if (kd[0] > d) {
-        kd[0] = d;
-        kq[0] = q;
-    }
-}
-
-// ibk_nearest_mean for a list of n > kIbkK pairs (n up to kTrPairs): the chosen labels are
-// summed in ascending pair index.
-__device__ __forceinline__ double ibk_nearest_mean_n(int n, const double* __restrict__ Dt, const uint16_t* pu,
-                                                     const double* yl) {
-    unsigned long long kd[kIbkK];
-    int kq[kIbkK];
-#pragma unroll
-    for (int i = 0; i < kIbkK; ++i) {
-        kd[i] = ~0ull;
-        kq[i] = 0;
-    }
-    for (int q = 0; q < n; ++q) ibk_insert(kd, kq, (unsigned long long)__double_as_longlong(__ldg(Dt + pu[q])), q);
-    for (int i = 1; i < kIbkK; ++i)          // indices ascending
-        for (int m = i; m > 0 && kq[m - 1] > kq[m]; --m) {
-            const int x = kq[m];
-            kq[m] = kq[m - 1];
-            kq[m - 1] = x;
-        }
-    double sum = 0.0;
-    for (int i = 0; i < kIbkK; ++i) sum += yl[kq[i]];
-    return sum / (double)kIbkK;
-}
-
-// The bordered ridge system of one fit with n >= 2 pairs, block-wide.  Writes b, alpha into
-// coef and returns the status (the same for every thread).
-__device__ int transfer_fit(TransferSmem& S, int j, int n, const double* __restrict__ KAq, int ld, double lambda) {
-    const int tid = threadIdx.x;
-    for (int e = tid; e < n * n; e += kTrThreads) {
-        const int i = e / n, c = e - i * n;
-        if (c <= i) S.M[i * kTrLd + c] = __ldg(KAq + (int64_t)S.pu[j][i] * ld + S.pu[j][c]) + (i == c ? lambda : 0.0);
-    }
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const double d = S.M[k * kTrLd + k];
-        if (!pos_finite(d)) return RS_FIT_NOTPD;      // every thread read the same pivot
-        const double dinv = 1.0 / d;
-        if (tid > k && tid < n) S.col[tid] = S.M[tid * kTrLd + k];
-        __syncthreads();
-        if (tid > k && tid < n) {
-            const double l = S.col[tid] * dinv;
-            for (int c = k + 1; c <= tid; ++c) S.M[tid * kTrLd + c] = fma(-l, S.col[c], S.M[tid * kTrLd + c]);
-            S.M[tid * kTrLd + k] = l;
-        }
-        __syncthreads();
-    }
-    if (tid < n) {                               // L t = rhs, two right-hand sides
-        S.ty[tid] = S.yl[j][tid];
-        S.t1[tid] = 1.0;
-    }
-    __syncthreads();
-    for (int k = 0; k < n - 1; ++k) {
-        if (tid > k && tid < n) {
-            const double l = S.M[tid * kTrLd + k];
-            S.ty[tid] = fma(-l, S.ty[k], S.ty[tid]);
-            S.t1[tid] = fma(-l, S.t1[k], S.t1[tid]);
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        double num = 0.0, den = 0.0;
-        for (int i = 0; i < n; ++i) {
-            const double sc = S.t1[i] / S.M[i * kTrLd + i];
-            num = fma(sc, S.ty[i], num);
-            den = fma(sc, S.t1[i], den);
-        }
-        S.bval = num / den;
-    }
-    __syncthreads();
-    const double b = S.bval;
-    if (tid < n) S.ty[tid] = fma(-b, S.t1[tid], S.ty[tid]) / S.M[tid * kTrLd + tid];
-    __syncthreads();
-    for (int k = n - 1; k > 0; --k) {            // L^T alpha = D^-1 (t_y - b t_1)
-        if (tid < k) S.ty[tid] = fma(-S.M[k * kTrLd + tid], S.ty[k], S.ty[tid]);
-        __syncthreads();
-    }
-    bool fin = finite_bits(b);
-    if (tid < n) {
-        S.coef[j][1 + tid] = S.ty[tid];
-        fin = finite_bits(S.ty[tid]);
-    }
-    if (tid == 0) S.coef[j][0] = b;
-    return __syncthreads_and(fin || tid >= n) && finite_bits(b) ? RS_FIT_OK : RS_FIT_NONFINITE;
-}
-
-__global__ void __launch_bounds__(kTrThreads, 1)
-transfer_kernel(const TransferArgs a) {
-    extern __shared__ __align__(16) unsigned char tsm[];
-    TransferSmem& S = *reinterpret_cast<TransferSmem*>(tsm);
-    const int q = blockIdx.x, tid = threadIdx.x;
-    int start[RS_MAXRUNS + 1], F = 0;
-    const int N = rs_group_layout(q, a.group_off, a.max_runs, a.n_runs, a.a_row, a.a_fw, a.b_fw, a.stat_stride, start, F);
-    const int64_t rb = a.b_row[q];
-    const int VB = (int)(a.b_row[q + 1] - rb);
-    if (N < 0 || N > a.ld || VB < 1 || VB > RS_MAXV) {
-        if (tid == 0) rs_dev_flag(a.r.dstatus, RS_EDATA, q);
-        return;
-    }
-    const int64_t g0 = a.group_off[q];
-    const int R = (int)(a.group_off[q + 1] - g0);
-    for (int e = tid; e < RS_MAXRUNS * RS_MAXV; e += kTrThreads) S.slot_a[e / RS_MAXV][e % RS_MAXV] = -1;
-    if (tid < RS_MAXV) S.slot_b[tid] = -1;
-    for (int u = tid; u < N; u += kTrThreads) {
-        int r = 0;
-        while (u >= start[r + 1]) ++r;
-        const int64_t row = a.a_row[g0 + r] + (u - start[r]);
-        S.msk_a[u] = a.a_masks[row] & 63;
-        S.lt_a[u] = a.a_lt[row];
-    }
-    if (tid < VB) {
-        S.msk_b[tid] = a.b_masks[rb + tid] & 63;
-        S.lt_b[tid] = a.b_lt[rb + tid];
-    }
-    __syncthreads();
-    for (int u = tid; u < N; u += kTrThreads) {
-        int r = 0;
-        while (u >= start[r + 1]) ++r;
-        S.slot_a[r][S.msk_a[u]] = (int8_t)(u - start[r]);
-    }
-    if (tid < VB) S.slot_b[S.msk_b[tid]] = (int8_t)tid;
-    __syncthreads();
-    if (tid < RS_NOPT) {
-        const int j = tid;
-        int np = 0;
-        for (int r = 0; r < R; ++r)
-            for (int u = start[r]; u < start[r + 1]; ++u) {
-                const int m = S.msk_a[u];
-                if ((m >> j) & 1) continue;
-                const int w = S.slot_a[r][m | (1 << j)];
-                if (w < 0) continue;
-                if (np == kTrPairs) {            // only possible with repeated masks
-                    rs_dev_flag(a.r.dstatus, RS_EDATA, q);
-                    continue;
-                }
-                S.pu[j][np] = (uint16_t)u;
-                S.yl[j][np] = S.lt_a[u] - S.lt_a[start[r] + w];
-                ++np;
-            }
-        S.np[j] = np;
-        S.st[j] = np > 0 ? RS_FIT_OK : RS_FIT_EMPTY;
-        if (np == 1) {                           // one pair: alpha = 0, b = its label
-            S.coef[j][0] = S.yl[j][0];
-            S.coef[j][1] = 0.0;
-            if (!finite_bits(S.yl[j][0])) S.st[j] = RS_FIT_NONFINITE;
-        }
-    }
-    __syncthreads();
-    if (!a.ibk) {
-        const double* KAq = a.KA + (int64_t)q * a.ld * a.ld;
-        for (int j = 0; j < RS_NOPT; ++j) {
-            const int n = S.np[j];
-            if (n < 2) continue;
-            const int st = transfer_fit(S, j, n, KAq, a.ld, a.lambda);
-            __syncthreads();
-            if (tid == 0) S.st[j] = st;
-        }
-        __syncthreads();
-    }
-    RankTally c;
-    const int t = tid;
-    if (t < VB) {
-        const int mt = S.msk_b[t];
-        const uint32_t info = row_summary(t, VB, S.msk_b, S.lt_b, S.slot_b);
-        const int candm = (a.rank_all ? 63 : (~mt & 63)) & a.opt_mask;
-        int okm = 0;
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) okm |= (S.st[j] == RS_FIT_OK) << j;
-        const double* Kt = a.Kx + ((int64_t)q * RS_MAXV + t) * a.ld;
-        double pred[RS_NOPT];
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) {
-            pred[j] = 0.0;
-            if (!(((candm & okm) >> j) & 1)) continue;
-            const int n = S.np[j];
-            if (a.ibk) {
-                if (n <= kIbkK) {
-                    double sum = 0.0;
-                    for (int i = 0; i < n; ++i) sum += S.yl[j][i];
-                    pred[j] = sum / (double)n;
-                } else {
-                    pred[j] = ibk_nearest_mean_n(n, Kt, S.pu[j], S.yl[j]);
-                }
-            } else {
-                double yh = S.coef[j][0];
-                if (n > 1)
-                    for (int i = 0; i < n; ++i) yh = fma(S.coef[j][1 + i], __ldg(Kt + S.pu[j][i]), yh);
-                pred[j] = yh;
-            }
-        }
-        // rank_row's candidates are the optimizations outside the version-mask field: put the
-        // excluded ones there (t's own unless all six are ranked, and those outside opt_mask);
-        // the fits that are not OK go in the empty-fit field
-        const int mfield = ((a.rank_all ? 0 : mt) | ~a.opt_mask) & 63;
-        const unsigned long long info64 = (unsigned long long)info | ((unsigned long long)mfield << 30) |
-                                          ((unsigned long long)(~okm & 63) << 36);
-        rank_row(a.r, rb + t, info64, pred, c);
-    }
-    if (tid < RS_NOPT) {
-        const int st = S.st[tid];
-        if (a.fit_status) a.fit_status[(int64_t)q * RS_NOPT + tid] = (uint8_t)st;
-        if (a.r.counters) atomicAdd(a.r.counters + 9 + st, 1ull);
-    }
-    if (a.r.counters) {
-        const uint32_t vals[10] = {c.rows, c.pred, c.scored, c.sign, c.rec, c.reck, c.rech, c.t1, c.t1h, c.inv};
-        const int slot[10] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 13};
-#pragma unroll
-        for (int i = 0; i < 10; ++i) {
-            const uint32_t v = __reduce_add_sync(0xffffffffu, vals[i]);
-            if ((tid & 31) == 0 && v) atomicAdd(a.r.counters + slot[i], (unsigned long long)v);
-        }
-    }
-}
-
-__global__ void iota64_kernel(int64_t* out, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = i;
 }
 
 // ====================================================================== predict / rank (chunked)
@@ -2269,41 +1788,5 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         rank_pass_kernel<<<(unsigned)blocks, kRankTile, kRankSmem, st>>>(ra);
     }
     mark(6);
-    return cudaGetLastError();
-}
-
-cudaError_t rs_launch_iota64(int64_t* out, int64_t n, cudaStream_t st) {
-    if (n > 0) iota64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n);
-    return cudaGetLastError();
-}
-
-cudaError_t rs_launch_transfer(const rs_transfer_args& t, cudaStream_t st) {
-    TransferArgs a{};
-    a.group_off = t.group_off;
-    a.max_runs = t.max_runs;
-    a.stat_stride = t.stat_stride;
-    a.n_runs = t.n_runs;
-    a.a_row = t.a_row_offsets;
-    a.a_fw = t.a_feat_width;
-    a.a_masks = t.a_masks;
-    a.a_lt = t.a_log_time;
-    a.b_row = t.b_row_offsets;
-    a.b_fw = t.b_feat_width;
-    a.b_masks = t.b_masks;
-    a.b_lt = t.b_log_time;
-    a.KA = t.KA;
-    a.Kx = t.Kx;
-    a.ld = t.ld;
-    a.lambda = t.lambda;
-    a.ibk = t.ibk;
-    a.opt_mask = t.opt_mask & 63;
-    a.rank_all = (t.flags & RS_RANK_ALL) != 0;
-    a.fit_status = t.fit_status;
-    a.r = RankPassArgs{nullptr, 0, nullptr, 0, 0, nullptr, t.dstatus, t.k, okey_host(t.log_tau),
-                       t.flags & ~RS_RANK_ALL, t.rec_code, t.rec_pred, t.pred_all, t.counters};
-    const size_t smem = sizeof(TransferSmem);
-    cudaError_t e = cudaFuncSetAttribute(transfer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    transfer_kernel<<<(unsigned)t.Q, kTrThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -1,0 +1,209 @@
+// rank_row.cuh -- device pieces shared by the batched predict/rank path (k_fit.cu) and the
+// transfer path (k_transfer.cu): order keys of doubles, the failure pattern of a fit, the
+// scoring summary of a version, and the ranking, threshold, top-k and scoring of one test
+// row (Sec. 2 tier 3, Sec. 5, Sec. 6), plus the neighbour list of the instance-based learner.
+#pragma once
+#include <string.h>
+
+#include "rs_internal.cuh"
+
+namespace {
+
+constexpr long long kNaNBits = 0x7ff8000000000000ll;
+
+__device__ __forceinline__ double nan_d() { return __longlong_as_double(kNaNBits); }
+
+// x > 0 and finite, decided on the bit pattern (no FP64 instruction).
+__device__ __forceinline__ bool pos_finite(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+// Order-preserving integer key of a non-NaN double; -0.0 and +0.0 share key 0.
+__device__ __forceinline__ long long okey(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+inline long long okey_host(double x) {
+    long long b;
+    memcpy(&b, &x, sizeof(b));
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// Scoring summary of version t of a program (its masks msk, log times lt, and the slot of each
+// mask, -1 if absent): bits 0-5 known (version t|j exists), bits 6-11 actual speedup > 1,
+// bits 12-29 the six optimizations ordered by actual log speedup (descending, lower index
+// first on ties, unknown last), 3 bits each.  t >= V gives the summary of an empty row.
+__device__ __forceinline__ uint32_t row_summary(int t, int V, const uint8_t* msk, const double* lt,
+                                                const int8_t* slot_of) {
+    long long key[RS_NOPT];
+    int kn = 0, apos = 0;
+    for (int j = 0; j < RS_NOPT; ++j) {
+        key[j] = (long long)0x8000000000000000ull;
+        if (t < V && !((msk[t] >> j) & 1)) {
+            const int w = slot_of[msk[t] | (1 << j)];
+            if (w >= 0) {
+                key[j] = okey(lt[t] - lt[w]);
+                kn |= 1 << j;
+                apos |= (key[j] > 0) << j;
+            }
+        }
+    }
+    uint32_t ord = 0;
+    int used = 0;
+    for (int x = 0; x < RS_NOPT; ++x) {
+        int best = -1;
+        for (int j = 0; j < RS_NOPT; ++j)
+            if (!((used >> j) & 1) && (best < 0 || key[j] > key[best])) best = j;
+        used |= 1 << best;
+        ord |= (uint32_t)best << (3 * x);
+    }
+    return (uint32_t)kn | ((uint32_t)apos << 6) | (ord << 12);
+}
+
+// A fit that failed writes this signalling-NaN pattern to its candidate rows instead of
+// predictions.  Arithmetic never produces a signalling NaN, so the rank pass tells failed
+// fits from predictions by the value alone, without reading the fit status of each row's
+// split (fits without a training pair are marked in the row records instead).
+constexpr long long kFailBits = 0x7ff4000000000001ll;
+
+constexpr int kIbkK = RS_IBK_NEIGHBORS;   // neighbours of the instance-based learner
+
+struct RankPassArgs {
+    const int64_t* rec_offsets;
+    int64_t S;
+    const double* predbuf;       // [6][PS]
+    int64_t R;                   // rows of the buffer
+    int64_t PS;                  // plane stride (even)
+    const unsigned long long* row_info;  // [R] scoring summary | version mask << 30
+    int* dstatus;
+    int k;
+    long long ktau;
+    int flags;
+    uint32_t* rec_code;
+    double* rec_pred;
+    double* pred_all;
+    unsigned long long* counters;
+};
+
+// Per-thread tallies of the scoring counters.
+struct RankTally {
+    uint32_t rows = 0, pred = 0, scored = 0, sign = 0, rec = 0, reck = 0, rech = 0, t1 = 0, t1h = 0, inv = 0;
+};
+
+// Ranking, threshold, top-k, outputs and scoring of one test row (Sec. 2 tier 3, Sec. 6):
+// candidates (versions lacking j, or all with RS_RANK_ALL) whose fit succeeded are ranked by
+// their predictions as order-preserving integer keys (ties: lower j first); those at or
+// above log tau form the recommendation, the first k of them reported.  15 comparisons give,
+// for each candidate j, the set of candidates that rank before it; its place is the
+// popcount of that set restricted to the candidates at or above the threshold.
+// info64: the row's scoring summary (row_summary) | version mask << 30 | mask of the
+// optimizations whose fit has no training pair << 36.
+__device__ __forceinline__ void rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
+                                         const double (&pred)[RS_NOPT], RankTally& c) {
+    const uint32_t info = (uint32_t)info64;
+    const int mt = (int)(info64 >> 30) & 63;
+    const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
+    // a candidate counts when its fit had a training pair (row record) and did not fail
+    // (the failure pattern in the prediction plane)
+    int okm = ~(int)(info64 >> 36) & 63;
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) okm &= ~((int)(__double_as_longlong(pred[j]) == kFailBits) << j);
+    const int validm = candm & okm;
+    long long key[RS_NOPT];
+    int above = 0, spos = 0;
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) {
+        key[j] = okey(pred[j]);
+        above |= (key[j] >= a.ktau) << j;
+        spos |= (key[j] > 0) << j;
+    }
+    above &= validm;
+    int bm[RS_NOPT];                           // bm[j]: candidates ranking before j
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) bm[j] = 0;
+#pragma unroll
+    for (int i = 0; i < RS_NOPT; ++i)
+#pragma unroll
+        for (int j = i + 1; j < RS_NOPT; ++j) {
+            if (key[i] >= key[j]) bm[j] |= 1 << i;
+            else bm[i] |= 1 << j;
+        }
+    uint32_t code = 0x0FFFFFF0u;
+    int rk = 0;
+    int pos[RS_NOPT];
+#pragma unroll
+    for (int j = 0; j < RS_NOPT; ++j) {
+        pos[j] = __popc(bm[j] & above);
+        if (((above >> j) & 1) && pos[j] < a.k) {
+            code = (code & ~(0xFu << (4 + 4 * pos[j]))) | ((uint32_t)j << (4 + 4 * pos[j]));
+            rk |= 1 << j;
+        }
+    }
+    const int nrec = __popc(rk);
+    code = (code & ~0xFu) | (uint32_t)nrec;
+    a.rec_code[row] = code;
+    if (a.rec_pred) {                          // each chosen candidate writes its own slot
+        double* o = a.rec_pred + row * a.k;
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            if ((rk >> j) & 1) o[pos[j]] = pred[j];
+#pragma unroll
+        for (int x = 0; x < RS_NOPT; ++x)
+            if (x >= nrec && x < a.k) o[x] = nan_d();
+    }
+    if (a.pred_all)
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            a.pred_all[row * RS_NOPT + j] = ((validm >> j) & 1) ? pred[j] : nan_d();
+    const int known = info & 63, apos = (info >> 6) & 63;
+    const int scored = validm & known;
+    c.rows += 1;
+    c.pred += __popc(validm);
+    c.scored += __popc(scored);
+    c.sign += __popc(scored & ~(spos ^ apos));
+    c.rec += nrec;
+    c.reck += __popc(rk & scored);
+    c.rech += __popc(rk & scored & apos);
+    c.inv += __popc(candm & ~okm);
+    if (scored) {
+        int bp = 0;
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
+        int ba = -1;
+#pragma unroll
+        for (int x = 0; x < RS_NOPT; ++x) {
+            const int j = (info >> (12 + 3 * x)) & 7;
+            if (ba < 0 && ((scored >> j) & 1)) ba = j;
+        }
+        c.t1 += 1;
+        c.t1h += (bp == ba);
+    }
+}
+
+// Insertion of (d, q) into the list of the kIbkK nearest, ordered by (distance, index):
+// distances are non-negative, so their bit patterns order like the values; a candidate
+// replaces the last entry only when strictly nearer.
+__device__ __forceinline__ void ibk_insert(unsigned long long (&kd)[kIbkK], int (&kq)[kIbkK],
+                                           unsigned long long d, int q) {
+    if (d >= kd[kIbkK - 1]) return;
+#pragma unroll
+    for (int i = kIbkK - 1; i > 0; --i) {
+        const bool shift = kd[i - 1] > d;
+        const bool here = !shift && kd[i] > d;
+        kd[i] = shift ? kd[i - 1] : (here ? d : kd[i]);
+        kq[i] = shift ? kq[i - 1] : (here ? q : kq[i]);
+    }
+    if (kd[0] > d) {
+        kd[0] = d;
+        kq[0] = q;
+    }
+}
+
+}  // namespace

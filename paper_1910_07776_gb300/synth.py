@@ -406,11 +406,14 @@ SHARED_OPTS = 0b110000
 
 def make_runs(codes=CODES, runs: int = 3, feat: int = 96, dtype=np.float64, seed: int = 0,
               with_cycles: bool = True, input_spread: float = 0.4, version_noise: float = 0.3,
-              run_noise: float = 0.05, label_noise: float = 0.05, run_label_noise: float = 0.01) -> ProgramBatch:
+              run_noise: float = 0.05, label_noise: float = 0.05, run_label_noise: float = 0.01,
+              code_similarity: float = 0.8) -> ProgramBatch:
     """One program entry per (code, input, run), all 64 versions, in that nesting order; the
     list of (code, input, run) is ``meta["index"]``.
 
-    Recipe (one PCG64 stream): per code a latent state ``h_c ~ N(0, I_8)`` and, for its own
+    Recipe (one PCG64 stream): per code a latent state ``h_c = rho h_0 + sqrt(1 - rho^2) e_c``
+    (``h_0, e_c ~ N(0, I_8)``, ``rho = code_similarity``: the codes are two GPU n-body
+    programs, alike in part) and, for its own
     optimizations (bits 0-3), its own effect directions and counter shifts; the shared ones
     (bits 4, 5) use directions and shifts common to both codes.  Input i moves the state,
     ``h_ci = h_c + input_spread * N(0, I_8)``, and scales the effects by
@@ -431,9 +434,10 @@ def make_runs(codes=CODES, runs: int = 3, feat: int = 96, dtype=np.float64, seed
     all_masks = np.arange(N_MASK, dtype=np.int64)
     mb = ((all_masks[:, None] >> np.arange(N_OPT)[None, :]) & 1).astype(np.float64)   # [64,6]
     own = np.arange(N_OPT) < 4
+    h_0 = rng.standard_normal(LATENT)
     X_parts, m_parts, lt_parts, cyc_parts, index = [], [], [], [], []
     for code, n_inputs in codes:
-        h_c = rng.standard_normal(LATENT)
+        h_c = code_similarity * h_0 + np.sqrt(1.0 - code_similarity ** 2) * rng.standard_normal(LATENT)
         w = np.where(own[:, None], rng.standard_normal((N_OPT, LATENT)), w_sh)
         u = np.where(own[:, None, None] | own[None, :, None], rng.standard_normal((N_OPT, N_OPT, LATENT)), u_sh)
         U = np.where(own[:, None], 0.5 * rng.standard_normal((N_OPT, F)), U_sh)
