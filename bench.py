@@ -695,7 +695,8 @@ def run_uneven(rs, ctx, dev, stream, flush, args):
                         "splits/program (10,240,000 splits)",
             "recs_per_step": R, "value": R / (graph_ms * 1e-3), "unit": UNIT, "graph_ms": graph_ms,
             "eager_default_ms": eager_default, "eager_tuned_ms": eager_tuned,
-            "autotune": {"solve_split": tune["solve_split"], "rank_waves": tune["rank_waves"]},
+            "autotune": {"solve_split": tune["solve_split"], "rank_waves": tune["rank_waves"],
+                         "solve_order": tune["solve_order"]},
             "sign_accuracy": cnt[3] / max(cnt[2], 1), "data_gen_s": gen_s}
 
 

@@ -278,11 +278,14 @@ rs_status rs_transfer(rs_ctx* ctx, const rs_batch* train, const rs_batch* test, 
  * while the graph exists; their contents may change between launches.  Counters are added
  * to on every launch.  The graph uses the launch parameters the context holds at capture.
  * rs_autotune times the batched step on this batch for each candidate launch configuration
- * (the size at which fits move to the register-heavier solver: 4..8; the rank pass's
- * persistent grid: a quarter, half or all of its resident blocks, given as 8, 16, 32),
- * keeps the fastest in the context (used by every later batched
- * call), and writes the times (ms, at most *n_times, in candidate order) if asked.
- * rs_get_tuning reports the context's current choice.                                 */
+ * (the order in which the register solvers take their fits: 0 = largest first, 1 = ranges
+ * alternately from the largest and the smallest end; the size at which fits move to the
+ * register-heavier solver: 4..8; the rank pass's persistent grid: a quarter, half or all of
+ * its resident blocks, given as 8, 16, 32), keeps the fastest in the context (used by every
+ * later batched call), and writes the times (ms, at most *n_times: 30 candidates, order-major,
+ * then size, then grid) if asked.  rs_get_tuning reports the context's current choice (any
+ * pointer may be NULL); rs_set_tuning sets it (RS_EINVAL outside those values).  The
+ * parameters change the work distribution only, never a result.                       */
 typedef struct rs_graph rs_graph;
 rs_status rs_cv_graph_create(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
                              double lambda, int k, double tau, int flags, int precision,
@@ -295,7 +298,8 @@ rs_status rs_autotune(rs_ctx* ctx, const rs_batch* batch, const rs_splits* split
                       int k, double tau, int flags, int precision, void* workspace,
                       size_t workspace_bytes, int64_t* rec_offsets, uint32_t* rec_code,
                       double* rec_pred, float* times_ms, int* n_times);
-rs_status rs_get_tuning(const rs_ctx* ctx, int* solve_split, int* rank_waves);
+rs_status rs_get_tuning(const rs_ctx* ctx, int* solve_split, int* rank_waves, int* solve_order);
+rs_status rs_set_tuning(rs_ctx* ctx, int solve_split, int rank_waves, int solve_order);
 
 /* ---- tensor-core BF16 GEMM (the surrogate's and the tensor-core Gram's building block) ----
  * D[M][N] = A[M][K] * B[N][K]^T with A, B BF16 row-major (K contiguous, leading dimensions

@@ -442,6 +442,7 @@ struct SolveArgs {
     const int64_t* x_offsets;
     const int32_t* feat_width;
     int max_feat;
+    int order;            // 0: largest fits first; 1: alternate ranges from both ends
 };
 
 __device__ __forceinline__ bool pred_target_v(const SolveArgs& a, int64_t s, int j, int p, int V, PredTarget& pt) {
@@ -550,7 +551,12 @@ __device__ __forceinline__ void count_status(const SolveArgs& a, int st, bool ac
 }
 
 // Fits with NLO <= n <= NHI, one per thread, in bucket order (n is warp-uniform except at
-// bucket boundaries).  Grid-stride over the bucket positions of that range.
+// bucket boundaries).  Warps take ranges of 32 bucket positions from a global counter.
+// Order 0: from the top of the range down -- the largest fits first, the cheapest last, so
+// the final ranges (the tail of the kernel) are short.  Order 1: the q-th range taken comes
+// alternately from the top (largest fits, descending) and from the bottom (smallest fits,
+// ascending), meeting in the middle: the FP64-light fits, whose time goes to memory
+// latency, run beside FP64-heavy ones instead of in a phase of their own.
 template <int NLO, int NHI, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 solve_small_kernel(const SolveArgs a, unsigned long long* work) {
@@ -558,9 +564,16 @@ solve_small_kernel(const SolveArgs a, unsigned long long* work) {
     bucket_tables(a.hist, start, cstart);
     const long long lo = start[NLO], hi = start[NHI + 1];
     const int lane = threadIdx.x & 31;
-    // positions from the top of the range down: the largest fits first, the cheapest last, so
-    // the final ranges (the tail of the kernel) are short
-    auto position = [&](long long b) { return hi - 1 - (b - lo) - lane; };
+    const long long nr = (hi - lo + 31) >> 5;           // ranges
+    const long long split = hi - 32 * ((nr + 1) >> 1);  // top ranges cover [split, hi)
+    const bool both = a.order == 1;
+    auto position = [&](long long b) {
+        const long long q = (b - lo) >> 5;
+        if (!both) return hi - 1 - (b - lo) - lane;
+        if ((q & 1) == 0) return hi - 1 - 32 * (q >> 1) - lane;
+        const long long p = lo + 32 * (q >> 1) + lane;
+        return p < split ? p : lo - 1;                   // past the top ranges: inactive
+    };
     // two ranges ahead: the record of the next range is loaded while this one is solved
     long long base = lo + (long long)__shfl_sync(0xffffffffu, take32(work), 0);
     unsigned long long got = take32(work);
@@ -1689,7 +1702,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
                  a.rows_cap, plane_stride(a.rows_cap), a.flags, a.dstatus, a.Z, a.x_offsets,
-                 a.feat_width, a.max_feat};
+                 a.feat_width, a.max_feat, a.tune_order};
     // compact records (and their offsets) only for fits without predictions or caller array
     const bool need_off = !user && !rank;
     bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.recs,

@@ -115,6 +115,7 @@ struct rs_fit_args {
     int max_feat;                 // host bound on F_p (refinement buffers)
     int tune_split;               // largest n of the lighter one-fit-per-thread solver (4..8)
     int tune_rank_waves;          // rank-pass grid = SMs x this (0: default)
+    int tune_order;               // register solvers' work order: 0 largest fits first, 1 from both ends
     int64_t rows_cap;             // rows of the prediction buffer (>= rec_offsets[S])
     void* workspace;
     size_t workspace_bytes;

@@ -36,7 +36,7 @@ EXPORTS = [
     "rs_profile_enable", "rs_profile_read", "rs_cv_step_static", "rs_gemm_bf16",
     "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
     "rs_surrogate_train", "rs_surrogate_infer", "rs_cv_graph_create", "rs_cv_graph_launch",
-    "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning", "rs_transfer", "rs_transfer_workspace_bytes",
+    "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning", "rs_set_tuning", "rs_transfer", "rs_transfer_workspace_bytes",
 ]
 
 
@@ -113,7 +113,8 @@ def load(path: str = SO):
     L.rs_cv_graph_destroy.argtypes = [P]
     L.rs_autotune.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, C.POINTER(C.c_float),
                               C.POINTER(C.c_int)]
-    L.rs_get_tuning.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rs_get_tuning.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rs_set_tuning.argtypes = [P, i, i, i]
     L.rs_surrogate_blob_bytes.argtypes = []
     L.rs_surrogate_blob_bytes.restype = C.c_size_t
     L.rs_surrogate_offset.argtypes = [i]
@@ -308,15 +309,21 @@ class Context:
     def autotune(self, b: DeviceBatch, s: DeviceSplits, workspace, rec_offsets, rec_code, lam=1e-3, k=3,
                  tau=1.05, flags=0, precision=RS_GRAM_F64, rec_pred=None):
         bc, sc = b.c(), s.c()
-        times = (C.c_float * 32)()
-        n = C.c_int(32)
+        times = (C.c_float * 64)()
+        n = C.c_int(64)
         self._check(self.L.rs_autotune(
             self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags), int(precision),
             _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(rec_offsets), _ptr(rec_code),
             _ptr(rec_pred), times, C.byref(n)))
-        sp_, rw = C.c_int(), C.c_int()
-        self.L.rs_get_tuning(self.h, C.byref(sp_), C.byref(rw))
-        return {"solve_split": sp_.value, "rank_waves": rw.value, "times_ms": [times[i] for i in range(n.value)]}
+        return {**self.get_tuning(), "times_ms": [times[i] for i in range(n.value)]}
+
+    def get_tuning(self) -> dict:
+        sp_, rw, so = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.L.rs_get_tuning(self.h, C.byref(sp_), C.byref(rw), C.byref(so)))
+        return {"solve_split": sp_.value, "rank_waves": rw.value, "solve_order": so.value}
+
+    def set_tuning(self, solve_split: int = 6, rank_waves: int = 32, solve_order: int = 0):
+        self._check(self.L.rs_set_tuning(self.h, int(solve_split), int(rank_waves), int(solve_order)))
 
     def check_device_status(self):
         self._check(self.L.rs_check_device_status(self.h))

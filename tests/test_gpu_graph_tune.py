@@ -56,8 +56,33 @@ def test_autotune_keeps_the_results(env):
     a, b = _outs(rs, ds), _outs(rs, ds)
     ctx.cv_step(db, ds, ws, a.rec_offsets, a.rec_code, rec_pred=a.rec_pred, pred_all=a.pred_all)
     t = ctx.autotune(db, ds, ws, b.rec_offsets, b.rec_code, rec_pred=b.rec_pred)
-    assert len(t["times_ms"]) == 15 and t["solve_split"] in (4, 5, 6, 7, 8) and t["rank_waves"] in (8, 16, 32)
+    assert len(t["times_ms"]) == 30 and t["solve_split"] in (4, 5, 6, 7, 8) and t["rank_waves"] in (8, 16, 32)
+    assert t["solve_order"] in (0, 1)
     ctx.cv_step(db, ds, ws, b.rec_offsets, b.rec_code, rec_pred=b.rec_pred, pred_all=b.pred_all)
     torch.cuda.synchronize()
     close(b.pred_all.cpu().numpy(), a.pred_all.cpu().numpy(), rel=1e-12, abs_=1e-14)
     assert torch.equal(a.rec_code, b.rec_code)
+
+
+def test_work_order_and_tuning_setter_change_no_result(env):
+    # the launch parameters only redistribute work: every configuration gives the same bits
+    rs, ctx = env
+    batch, splits, db, ds = _uneven(rs)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    ref = None
+    for cfg in ((6, 32, 0), (6, 32, 1), (4, 8, 1), (8, 16, 0)):
+        ctx.set_tuning(*cfg)
+        assert tuple(ctx.get_tuning().values()) == cfg
+        o = _outs(rs, ds)
+        ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, rec_pred=o.rec_pred, pred_all=o.pred_all)
+        torch.cuda.synchronize()
+        got = (o.pred_all.cpu().numpy(), o.rec_code.cpu().numpy())
+        if ref is None:
+            ref = got
+        else:
+            np.testing.assert_array_equal(got[0], ref[0])
+            np.testing.assert_array_equal(got[1], ref[1])
+    for bad in ((3, 32, 0), (6, 12, 0), (6, 32, 2)):
+        with pytest.raises(rs.RsError):
+            ctx.set_tuning(*bad)
+    ctx.set_tuning(6, 32, 1)
