@@ -40,50 +40,6 @@ constexpr int kNMid = 16;                   // largest n solved by one thread fr
 constexpr int kHist = RS_MAXPAIRS + 2;      // n = 0..32, plus one end slot
 __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
 
-// float <-> double for values inside the float normal range, by re-packing the IEEE-754
-// fields with integer operations (the mantissa is truncated).  Used only to seed Newton
-// iterations, so no FP64 instruction is spent on the conversion.
-__device__ __forceinline__ float f32_of(double d) {
-    const long long b = __double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-    const unsigned m = (unsigned)((b >> 29) & 0x7fffff);
-    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | m);
-}
-__device__ __forceinline__ double f64_of(float f) {
-    const unsigned u = __float_as_uint(f);
-    const long long e = (long long)((u >> 23) & 0xff) - 127 + 1023;
-    return __longlong_as_double(((long long)(u & 0x80000000u) << 32) | (e << 52) |
-                                ((long long)(u & 0x7fffff) << 29));
-}
-
-// 1/sqrt(d) for a positive finite d: FP32 seed, then two Newton steps of r <- r (3 - d r^2) / 2
-// (Newton's method on f(r) = r^-2 - d).  Outside [1e-30, 1e30]: plain division.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-    if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);
-    const double hd = 0.5 * d;
-    double r = f64_of(rsqrtf(f32_of(d)));
-    r = r * fma(-hd, r * r, 1.5);
-    r = r * fma(-hd, r * r, 1.5);
-    return r;
-}
-
-// Bit patterns of 2^-100 and 2^100 (positive doubles are ordered like their bit patterns).
-constexpr long long kRcpLoBits = 0x39b0000000000000ll;
-constexpr long long kRcpHiBits = 0x4630000000000000ll;
-
-// 1/d for a positive finite d with three FP64 instructions.  r0 = the FP32 reciprocal of d
-// (mantissa truncated to FP32) has relative error |t| < 2^-22 with t = 1 - d r0, and
-// 1/d = r0 / (1 - t) = r0 (1 + t + t^2 + ...); keeping terms up to t^2 leaves |t|^3 < 2^-66,
-// far below the final rounding:  t = fma(-d, r0, 1), u = fma(t, t, t), r = fma(r0, u, r0).
-// The range test is an integer compare; outside [2^-100, 2^100]: plain division.
-__device__ __forceinline__ double rcp_newton(double d) {
-    const long long bits = __double_as_longlong(d);
-    if (bits < kRcpLoBits || bits > kRcpHiBits) return 1.0 / d;
-    const double r0 = f64_of(__frcp_rn(f32_of(d)));
-    const double t = fma(-d, r0, 1.0);
-    return fma(r0, fma(t, t, t), r0);
-}
-
 // The a-th set bit (0-based) of x; x must have more than a set bits.
 __device__ __forceinline__ int select_bit(uint64_t x, int a) {
     for (int i = 0; i < a; ++i) x &= x - 1;

@@ -98,8 +98,9 @@ gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __res
 }
 
 // Blocks of a transfer problem q (Table 2).  Its training runs form one list of N versions
-// (rs_group_layout); the rows are the list itself (CROSS false: the group's Gram KA[q][i][u],
-// ld x ld) or the versions of the test program q (CROSS true: Kx[q][t][u], 64 x ld).  Entry =
+// (rs_group_layout); the rows are the list itself (CROSS false: the lower triangle u <= i of
+// the group's Gram KA[q][i][u], ld x ld -- all that the fits read) or the versions of the
+// test program q (CROSS true: Kx[q][t][u], 64 x ld).  Entry =
 // sum_f z_i[f] z_u[f] (FMA chain), or with DIST sum_f (z_t[f] - z_u[f])^2 with unfused
 // operations (the plain definition's arithmetic), ascending f.  One thread per entry; the
 // rows come from L1 / L2.  Problems that fail the layout checks (reported by the
@@ -120,7 +121,8 @@ transfer_block_kernel(const int64_t* __restrict__ group_off, int max_runs, int64
     const int VB = (int)(b_row[q + 1] - b_row[q]);
     if (CROSS && (VB < 1 || VB > RS_MAXV)) return;
     const int rows = CROSS ? VB : N;
-    if ((int64_t)blockIdx.y * blockDim.x >= (int64_t)rows * N) return;
+    const int entries = CROSS ? rows * N : N * (N + 1) / 2;
+    if ((int64_t)blockIdx.y * blockDim.x >= entries) return;
     const int64_t g0 = group_off[q];
     for (int u = threadIdx.x; u < N; u += blockDim.x) {
         int r = 0;
@@ -129,8 +131,17 @@ transfer_block_kernel(const int64_t* __restrict__ group_off, int max_runs, int64
     }
     __syncthreads();
     const int e = blockIdx.y * blockDim.x + threadIdx.x;
-    if (e >= rows * N) return;
-    const int i = e / N, u = e - i * N;
+    if (e >= entries) return;
+    int i, u;
+    if constexpr (CROSS) {
+        i = e / N;
+        u = e - i * N;
+    } else {                                   // e = i (i + 1) / 2 + u, u <= i
+        i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (i * (i + 1) / 2 > e) --i;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        u = e - i * (i + 1) / 2;
+    }
     const double* zi = CROSS ? ZB + b_xo[q] + (int64_t)i * F : ZA + rowx[i];
     const double* zu = ZA + rowx[u];
     double acc = 0.0;
@@ -156,7 +167,7 @@ cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch*
     const double* ZA = (const double*)train_std->X;
     const double* ZB = (const double*)test_std->X;
     if (KA) {
-        dim3 grid(Q, (unsigned)(((int64_t)n * n + 127) / 128));
+        dim3 grid(Q, (unsigned)(((int64_t)n * (n + 1) / 2 + 127) / 128));
         transfer_block_kernel<false, false><<<grid, 128, 0, st>>>(
             group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
             ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, KA);

@@ -1,7 +1,8 @@
 // rank_row.cuh -- device pieces shared by the batched predict/rank path (k_fit.cu) and the
-// transfer path (k_transfer.cu): order keys of doubles, the failure pattern of a fit, the
-// scoring summary of a version, and the ranking, threshold, top-k and scoring of one test
-// row (Sec. 2 tier 3, Sec. 5, Sec. 6), plus the neighbour list of the instance-based learner.
+// transfer path (k_transfer.cu): order keys of doubles, FP64 reciprocals with few FP64
+// instructions, the failure pattern of a fit, the scoring summary of a version, and the
+// ranking, threshold, top-k and scoring of one test row (Sec. 2 tier 3, Sec. 5, Sec. 6), plus
+// the neighbour list of the instance-based learner.
 #pragma once
 #include <string.h>
 
@@ -26,6 +27,50 @@ __device__ __forceinline__ long long okey(double x) {
     long long b = __double_as_longlong(x);
     if (b == (long long)0x8000000000000000ull) b = 0;
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// float <-> double for values inside the float normal range, by re-packing the IEEE-754
+// fields with integer operations (the mantissa is truncated).  Used only to seed Newton
+// iterations, so no FP64 instruction is spent on the conversion.
+__device__ __forceinline__ float f32_of(double d) {
+    const long long b = __double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    const unsigned m = (unsigned)((b >> 29) & 0x7fffff);
+    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | m);
+}
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned u = __float_as_uint(f);
+    const long long e = (long long)((u >> 23) & 0xff) - 127 + 1023;
+    return __longlong_as_double(((long long)(u & 0x80000000u) << 32) | (e << 52) |
+                                ((long long)(u & 0x7fffff) << 29));
+}
+
+// 1/sqrt(d) for a positive finite d: FP32 seed, then two Newton steps of r <- r (3 - d r^2) / 2
+// (Newton's method on f(r) = r^-2 - d).  Outside [1e-30, 1e30]: plain division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);
+    const double hd = 0.5 * d;
+    double r = f64_of(rsqrtf(f32_of(d)));
+    r = r * fma(-hd, r * r, 1.5);
+    r = r * fma(-hd, r * r, 1.5);
+    return r;
+}
+
+// Bit patterns of 2^-100 and 2^100 (positive doubles are ordered like their bit patterns).
+constexpr long long kRcpLoBits = 0x39b0000000000000ll;
+constexpr long long kRcpHiBits = 0x4630000000000000ll;
+
+// 1/d for a positive finite d with three FP64 instructions.  r0 = the FP32 reciprocal of d
+// (mantissa truncated to FP32) has relative error |t| < 2^-22 with t = 1 - d r0, and
+// 1/d = r0 / (1 - t) = r0 (1 + t + t^2 + ...); keeping terms up to t^2 leaves |t|^3 < 2^-66,
+// far below the final rounding:  t = fma(-d, r0, 1), u = fma(t, t, t), r = fma(r0, u, r0).
+// The range test is an integer compare; outside [2^-100, 2^100]: plain division.
+__device__ __forceinline__ double rcp_newton(double d) {
+    const long long bits = __double_as_longlong(d);
+    if (bits < kRcpLoBits || bits > kRcpHiBits) return 1.0 / d;
+    const double r0 = f64_of(__frcp_rn(f32_of(d)));
+    const double t = fma(-d, r0, 1.0);
+    return fma(r0, fma(t, t, t), r0);
 }
 
 inline long long okey_host(double x) {

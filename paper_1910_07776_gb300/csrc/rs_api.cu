@@ -478,7 +478,7 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
 // ---- Table 2 transfer ----------------------------------------------------------------------------
 namespace {
 struct TransferWs {
-    double *ZA, *ZB, *mu, *sigma, *KA, *Kx;
+    double *ZA, *ZB, *mu, *sigma, *KA, *Kx, *fit;
     int64_t* iota;
     size_t bytes;
 };
@@ -498,6 +498,7 @@ TransferWs transfer_carve(void* base, const rs_batch* train, const rs_batch* tes
     w.sigma = (double*)take(Q * (size_t)train->max_feat * sizeof(double));
     w.KA = (double*)take(Q * ld * ld * sizeof(double));
     w.Kx = (double*)take(Q * RS_MAXV * ld * sizeof(double));
+    w.fit = (double*)take(rs_transfer_fit_bytes((int64_t)Q));
     w.iota = g ? nullptr : (int64_t*)take((Q + 1) * sizeof(int64_t));
     w.bytes = o;
     return w;
@@ -584,6 +585,7 @@ rs_status rs_transfer(rs_ctx* c, const rs_batch* train, const rs_batch* test, co
     t.log_tau = log(tau);   // host libm, as in rs_predict_rank
     t.flags = flags;
     t.fit_status = fit_status;
+    t.fit_ws = w.fit;
     t.rec_code = rec_code;
     t.rec_pred = rec_pred;
     t.pred_all = pred_all;

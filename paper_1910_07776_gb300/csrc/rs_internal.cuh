@@ -155,6 +155,7 @@ struct rs_transfer_args {
     double log_tau;
     int flags;
     uint8_t* fit_status;          // [Q][6], nullable
+    double* fit_ws;               // rs_transfer_fit_bytes(Q) of device scratch for the ridge fits
     uint32_t* rec_code;
     double* rec_pred;
     double* pred_all;
@@ -162,6 +163,7 @@ struct rs_transfer_args {
     int* dstatus;
 };
 cudaError_t rs_launch_transfer(const rs_transfer_args& a, cudaStream_t st);
+size_t rs_transfer_fit_bytes(int64_t Q);
 cudaError_t rs_launch_iota64(int64_t* out, int64_t n, cudaStream_t st);
 size_t rs_surrogate_blob_floats();
 size_t rs_surrogate_train_ws_bytes(int B);
