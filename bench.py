@@ -961,8 +961,27 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
     torch.cuda.synchronize()
     tot = e0.elapsed_time(e1)
     ctx.check_device_status()
+    # the host link's own rates (one bulk copy each way of a step's output size), the bound of
+    # this leg: a step cannot finish before its outputs have crossed the link
+    big_d = outs[0].rec_pred
+    reps, t_d2h, t_h2d = 3, 0.0, 0.0
+    for _ in range(reps):
+        e0.record(stream)
+        h_pred[0].copy_(big_d, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_d2h += e0.elapsed_time(e1)
+        e0.record(stream)
+        big_d.copy_(h_pred[0], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_h2d += e0.elapsed_time(e1)
+    nb = big_d.numel() * 8
+    d2h_gbs, h2d_gbs = nb * reps / (t_d2h * 1e6), nb * reps / (t_h2d * 1e6)
     return {"value": R * n / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / n, "steps": n,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "host_link_gbs": {"d2h": d2h_gbs, "h2d": h2d_gbs},
+            "copy_bound_ms_per_step": d2h / (d2h_gbs * 1e6) + h2d / (h2d_gbs * 1e6),
             "path": "per step: pinned host -> device copies of the inputs, L2 flush, rs_cv_step, device -> "
                     "pinned host copies of rec_code / rec_pred / counters on a second stream (outputs "
                     "double-buffered: a step's copies overlap the next step's compute)"}
