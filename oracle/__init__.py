@@ -3,7 +3,7 @@
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  The CUDA library never loads it and shares no code with it.
 
-``build()`` compiles ``rs_oracle.c`` (plain C, double precision, ``-ffp-contract=off`` so
+``build()`` compiles ``rs_oracle.c`` and ``rs_m5p.c`` (plain C, double precision, ``-ffp-contract=off`` so
 the host results are the same on x86-64 and AArch64) into ``oracle/_build``.  The Python
 functions below only marshal numpy arrays into the C functions; the MLP reference used
 for the surrogate lives in ``mlp.py`` (numpy, float64).
@@ -33,17 +33,18 @@ COUNTER_NAMES = [
 FIT_OK, FIT_EMPTY, FIT_NOTPD, FIT_NONFINITE = 0, 1, 2, 3
 RANK_ALL = 1
 MODEL_IBK = 4
+MODEL_M5P = 8
 IBK_NEIGHBORS = 10          # k of the instance-based learner (Sec. 3.4: k = 10)
 
 
 def build(force: bool = False) -> str:
     """Compile the C reference with gcc (OpenMP over splits, IEEE double, no FP contraction)."""
-    src = os.path.join(_HERE, "rs_oracle.c")
+    srcs = [os.path.join(_HERE, f) for f in ("rs_oracle.c", "rs_m5p.c")]
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(f) for f in srcs):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, src, "-lm"])
+                               "-fno-fast-math", "-o", tmp, *srcs, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -73,6 +74,8 @@ def lib():
                                    C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P, P,
                                    P]
         L.orc_ibk_predict.restype = C.c_double
+        L.orc_m5p_fit_predict.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P, P, P]
+        L.orc_m5p_fit_predict.restype = C.c_int
         L.orc_num_threads_available.restype = C.c_int
         _lib = L
     return _lib
@@ -214,10 +217,12 @@ def transfer(train, test, groups=None, lam: float = 1e-3, k: int = 3, tau: float
     groups[q] .. groups[q+1]-1 of ``train`` (standardized together) predicts, ranks and scores
     every version of ``test``'s program q (standardized with the training runs' statistics).
     groups defaults to one run per problem.  opt_mask limits the candidate optimizations."""
-    if model not in ("ridge", "ibk"):
-        raise ValueError("model must be 'ridge' or 'ibk'")
+    if model not in ("ridge", "ibk", "m5p"):
+        raise ValueError("model must be 'ridge', 'ibk' or 'm5p'")
     if model == "ibk":
         flags |= MODEL_IBK
+    if model == "m5p":
+        flags |= MODEL_M5P
     L = lib()
     Q = test.n_programs
     g = np.arange(Q + 1, dtype=np.int64) if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
@@ -244,6 +249,21 @@ def transfer(train, test, groups=None, lam: float = 1e-3, k: int = 3, tau: float
                    _p(fs), _p(code), _p(rp), _p(pa), _p(cnt))
     return TransferResult(fit_status=fs.reshape(Q, N_OPT), rec_offsets=ro, rec_code=code,
                           rec_pred=rp.reshape(R, k), pred_all=pa.reshape(R, N_OPT), counters=cnt)
+
+
+def m5p_fit_predict(Zrows, y, Zt):
+    """The M5P model tree (rs_m5p.c) fitted on (Zrows, y), predicting the rows of Zt; returns
+    (predictions, leaves, nodes after pruning)."""
+    Zrows = np.ascontiguousarray(Zrows, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    Zt = np.ascontiguousarray(np.atleast_2d(Zt), dtype=np.float64)
+    n, F = Zrows.shape
+    out = np.zeros(Zt.shape[0])
+    lv, nd = C.c_int(0), C.c_int(0)
+    st = lib().orc_m5p_fit_predict(n, F, _p(Zrows), _p(y), Zt.shape[0], _p(Zt), _p(out), C.byref(lv), C.byref(nd))
+    if st:
+        raise ValueError("m5p: 1 <= n <= 128 instances")
+    return out, lv.value, nd.value
 
 
 def ibk_predict(Zrows, y, zt, k: int = IBK_NEIGHBORS) -> float:

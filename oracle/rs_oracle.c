@@ -16,6 +16,7 @@
  *            solved from the primal normal equations with a textbook Cholesky; or
  *   Sec. 3.4 the instance-based learner IBK: the k = 10 training instances nearest to the
  *            test vector by Euclidean distance, their labels combined into the prediction;
+ *   Sec. 3.4 the M5P model tree (rs_m5p.c), for the transfer protocol;
  *   Sec. 5   evaluation: test versions are those outside the split's training set; each
  *            gets one predicted speedup per optimization it does not already contain;
  *   Sec. 2   Tier 3 sorts by expected benefit, keeps those at or above a threshold and
@@ -37,6 +38,7 @@
  *     labels, which are continuous log speedups, is read as their mean (summed in pair
  *     order); equal distances take the lower pair index first; fewer than k training
  *     pairs use all of them;
+ *   - M5P: the readings listed in rs_m5p.c;
  *   - transfer (Table 2): the training set is a group of runs (one program and input, or
  *     several runs of it); their vectors are standardized together and the test set with the
  *     same statistics; a model is trained from all pairs of all runs, a pair never spanning
@@ -62,6 +64,13 @@
 #define ORC_FIT_NONFINITE 3
 #define ORC_RANK_ALL 1
 #define ORC_MODEL_IBK 4
+#define ORC_MODEL_M5P 8
+
+/* The M5P model tree (rs_m5p.c). */
+typedef struct orc_m5_tree orc_m5_tree_t;
+int orc_m5p_tree_bytes(void);
+int orc_m5p_fit_tree(int n, int F, const double* Zrows, const double* y, void* T);
+double orc_m5p_predict_tree(const void* T, const double* z);
 #define ORC_NCOUNTERS 16
 
 /* ---------------------------------------------------------------------------------- */
@@ -483,6 +492,8 @@ void orc_transfer(int Q, const int64_t* group_offsets, const int32_t* a_feat_wid
                   uint8_t* fit_status, uint32_t* rec_code, double* rec_pred, double* pred_all,
                   uint64_t* counters) {
     const int ibk = (flags & ORC_MODEL_IBK) != 0;
+    const int m5p = !ibk && (flags & ORC_MODEL_M5P) != 0;
+    void* trees = m5p ? malloc((size_t)orc_m5p_tree_bytes() * ORC_NOPT) : NULL;
     int64_t row = 0;
     for (int q = 0; q < Q; ++q) {
         const int64_t g0 = group_offsets[q], g1 = group_offsets[q + 1];
@@ -541,6 +552,10 @@ void orc_transfer(int Q, const int64_t* group_offsets, const int32_t* a_feat_wid
             nj[j] = n;
             int st;
             if (ibk) st = n > 0 ? ORC_FIT_OK : ORC_FIT_EMPTY;
+            else if (m5p)
+                st = n == 0 ? ORC_FIT_EMPTY
+                            : (orc_m5p_fit_tree(n, F, Zj, yj, (char*)trees + (size_t)j * orc_m5p_tree_bytes())
+                                   ? ORC_FIT_NOTPD : ORC_FIT_OK);
             else st = orc_ridge_fit(n, F, Zj, yj, lambda, beta + (size_t)j * F, &bias[j], work);
             ok[j] = st == ORC_FIT_OK;
             if (fit_status) fit_status[q * ORC_NOPT + j] = (uint8_t)st;
@@ -565,6 +580,8 @@ void orc_transfer(int Q, const int64_t* group_offsets, const int32_t* a_feat_wid
                 if (ibk) {
                     yh = orc_ibk_predict(nj[j], F, Zr + (size_t)j * cap * F, yv + (size_t)j * cap,
                                          ZB + (size_t)t * F, ibk_k);
+                } else if (m5p) {
+                    yh = orc_m5p_predict_tree((char*)trees + (size_t)j * orc_m5p_tree_bytes(), ZB + (size_t)t * F);
                 } else {
                     yh = bias[j];
                     for (int f = 0; f < F; ++f) yh += ZB[(size_t)t * F + f] * beta[(size_t)j * F + f];
@@ -623,6 +640,7 @@ void orc_transfer(int Q, const int64_t* group_offsets, const int32_t* a_feat_wid
         free(Zr);
         free(yv);
     }
+    free(trees);
 }
 
 int orc_num_threads_available(void) {
