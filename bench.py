@@ -598,7 +598,7 @@ def run_transfer(rs, ctx, dev, stream, flush, args):
         dte = rs.DeviceBatch.from_host(pr.test, dev)
         offs = torch.from_numpy(pr.groups).to(dev)
         g = (offs, int(np.diff(pr.groups).max()))
-        ws = ctx.workspace(ctx.transfer_workspace_bytes(dtr, dte, g))
+        ws = ctx.workspace(ctx.transfer_workspace_bytes(dtr, dte, g, rs.RS_MODEL_M5P))
         R = dte.n_rows
         # actual log speedups of the test rows (host, from the test set's own times)
         act = np.full((R, 6), np.nan)
@@ -614,7 +614,7 @@ def run_transfer(rs, ctx, dev, stream, flush, args):
                         act[rows.start + t, j] = lt[t] - lt[w]
         res = {"problems": int(pr.test.n_programs), "train_runs_per_problem": int(np.diff(pr.groups).max()),
                "test_rows": int(R), "opt_mask": int(pr.opt_mask), "paper_ibk_accuracy_pct": PAPER_TABLE3_IBK[e]}
-        for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK)):
+        for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK), ("m5p", rs.RS_MODEL_M5P)):
             o = rs.alloc_outputs(R, 0, CFG["k"], dev)
             call = lambda: ctx.transfer(dtr, dte, ws, o.rec_code, groups=g, lam=CFG["lam"], k=CFG["k"],
                                         tau=CFG["tau"], flags=flags, opt_mask=pr.opt_mask, rec_pred=o.rec_pred,

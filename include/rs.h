@@ -59,8 +59,9 @@ enum {
     RS_RANK_ALL = 1,      /* rank all six optimizations, not only those not yet applied */
     RS_REFINE_X = 2,      /* one step of iterative refinement with residual and
                              predictions taken through Z (for an inexact Gram)        */
-    RS_MODEL_IBK = 4      /* the instance-based learner (IBK, k nearest neighbours)
+    RS_MODEL_IBK = 4,     /* the instance-based learner (IBK, k nearest neighbours)
                              instead of ridge regression; K is the distance block    */
+    RS_MODEL_M5P = 8      /* the M5P model tree instead of ridge regression (rs_transfer) */
 };
 #define RS_IBK_NEIGHBORS 10  /* k of the instance-based learner (Sec. 3.4: k = 10)        */
 
@@ -257,14 +258,24 @@ rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits
  * (nullable).  A problem whose group or test program breaks these rules is skipped (its rows
  * are not written) and reported as RS_EDATA in the device status.  workspace: device memory
  * of at least rs_transfer_workspace_bytes(train, test, groups) bytes, 256-byte aligned,
- * scratch.  flags: RS_RANK_ALL, RS_MODEL_IBK.  tau > 0, k in 1..6.                       */
+ * scratch.  flags: RS_RANK_ALL, and RS_MODEL_IBK or RS_MODEL_M5P.  tau > 0, k in 1..6.
+ * RS_MODEL_M5P (Sec. 3.4's model tree, after the published M5' description): per fit, a tree
+ * grown by the standard deviation reduction (nodes of fewer than 4 instances, or whose label
+ * deviation is at most 5 % of the root's, are leaves; thresholds halfway between consecutive
+ * distinct values, at least 2 instances a side, ties to the lower attribute), a least-squares
+ * model at every node on the attributes tested below it (at most 64), simplified by greedy
+ * elimination on the estimated error mean|residual| (m + v) / (m - v), bottom-up pruning,
+ * and smoothing on the way up, p = (n p + 15 q) / (n + 15); at most 256 features (else
+ * RS_EUNSUPPORTED).  Its workspace (rs_transfer_workspace_bytes with the same flags) holds
+ * the trees.                                                                             */
 typedef struct {
     int64_t n_groups;             /* host: Q, equal to test->n_programs                      */
     int32_t max_runs;             /* host: upper bound on runs per group, 1..RS_MAXRUNS      */
     int32_t reserved;
     const int64_t* group_offsets; /* [Q+1] device: group_offsets[0] = 0, non-decreasing      */
 } rs_groups;
-size_t rs_transfer_workspace_bytes(const rs_batch* train, const rs_batch* test, const rs_groups* groups);
+size_t rs_transfer_workspace_bytes(const rs_batch* train, const rs_batch* test, const rs_groups* groups,
+                                   int flags);
 rs_status rs_transfer(rs_ctx* ctx, const rs_batch* train, const rs_batch* test, const rs_groups* groups,
                       double lambda, int k, double tau, int flags, int opt_mask, void* workspace,
                       size_t workspace_bytes, uint8_t* fit_status, uint32_t* rec_code, double* rec_pred,

@@ -12,7 +12,8 @@
  *           at least 2 instances on each side (ties: lower attribute, then lower threshold);
  *           no split with SDR > 0 makes a leaf; instances with z <= threshold go left;
  *   models  every node gets a linear model (least squares with an intercept) on the
- *           attributes tested in splits of its subtree, simplified by greedy elimination:
+ *           attributes tested in splits of its subtree -- as pruned so far, since the
+ *           children are modelled and pruned first -- simplified by greedy elimination:
  *           while dropping one attribute (the one giving the lowest estimate) does not raise
  *           the estimated error, drop it; estimated error = mean |residual| on the node's
  *           instances x (m + v) / (m - v), m instances, v = terms + 1 (infinite if m <= v);

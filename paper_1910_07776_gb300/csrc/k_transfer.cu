@@ -1,6 +1,8 @@
 // Table 2 transfer (Sec. 5): the fits of each problem's training group of runs (one block per
 // problem and optimization), then the predictions for its test program, ranking and scoring
 // (one block per problem).
+#include <float.h>
+
 #include "rank_row.cuh"
 
 namespace {
@@ -69,6 +71,8 @@ __device__ int build_pairs(const GroupSmem& G, int j, int R, const int (&start)[
     return np;
 }
 
+struct M5Tree;
+
 struct TransferArgs {
     const int64_t* group_off;
     int max_runs, stat_stride;
@@ -88,6 +92,12 @@ struct TransferArgs {
     double* coef;                        // [Q][6][kTrCoef] ridge fits (written by the fit kernel)
     uint8_t* fst;                        // [Q][6] their status
     int ibk, opt_mask, rank_all;
+    int m5p;                             // the M5P model tree instead of ridge
+    M5Tree* trees;                       // [Q][6] M5P trees
+    const double* ZA;                    // standardized training group rows (M5P fits)
+    const int64_t* a_xo;
+    const double* ZB;                    // standardized test rows (M5P predictions)
+    const int64_t* b_xo;
     uint8_t* fit_status;
     RankPassArgs r;                      // k, ktau, flags (without RS_RANK_ALL), outputs, counters
 };
@@ -223,6 +233,481 @@ transfer_fit_kernel(const TransferArgs a, int nmax) {
     if (tid == 0) *st_out = (uint8_t)st;
 }
 
+// ====================================================================== M5P (Sec. 3.4)
+// The model tree of each (problem, optimization), after the M5' description: grow by the
+// standard deviation reduction (SDR), a linear model at every node on the attributes tested
+// in its subtree as pruned so far (children are modelled and pruned first), simplified by
+// greedy elimination, bottom-up pruning by estimated error, and smoothing on the way up at
+// prediction time (k = 15).
+constexpr int kM5MaxN = kTrPairs;                 // instances of one fit
+constexpr int kM5MaxNodes = 2 * kM5MaxN - 1;
+constexpr int kM5MaxTerms = 64;
+constexpr int kM5MaxFeat = 256;                   // attributes (one thread each in the split search)
+constexpr int kM5Threads = 256;
+constexpr int kM5Ld = kM5MaxTerms + 1;
+constexpr double kM5SdFrac = 0.05, kM5Smooth = 15.0, kM5Ridge = 1e-8;
+
+struct M5Tree {
+    int n_nodes;
+    int count[kM5MaxNodes];
+    int nterm[kM5MaxNodes];
+    int16_t attr[kM5MaxNodes], left[kM5MaxNodes], right[kM5MaxNodes], parent[kM5MaxNodes];
+    double thr[kM5MaxNodes], b[kM5MaxNodes];
+    int16_t term_attr[kM5MaxNodes][kM5MaxTerms];
+    double term_w[kM5MaxNodes][kM5MaxTerms];
+};
+
+struct M5Smem {
+    uint8_t sorted[kM5MaxFeat][kM5MaxN];          // per attribute: instances in (value, index) order
+    uint8_t scratch[kM5Threads][kM5MaxN];
+    double G[kM5MaxTerms * kM5Ld];                // centred normal equations of the node's candidates
+    double H[kM5MaxTerms * kM5Ld];                // inverse of the current subset's system
+    double colk[kM5MaxTerms], rowk[kM5MaxTerms];
+    double zbar[kM5MaxTerms], r[kM5MaxTerms], w[kM5MaxTerms], cand_err[kM5MaxTerms];
+    double res[kM5MaxN];
+    double y[kM5MaxN];
+    const double* zp[kM5MaxN];                    // each instance's standardized row
+    double thr[kM5MaxNodes], est[kM5MaxNodes];
+    unsigned long long tested[kM5MaxNodes][kM5MaxFeat / 64];
+    int16_t attr[kM5MaxNodes], left[kM5MaxNodes], right[kM5MaxNodes];
+    uint8_t lo[kM5MaxNodes], hi[kM5MaxNodes];
+    uint8_t ids[kM5MaxN];
+    uint8_t side[kM5MaxN];
+    uint8_t sel[kM5MaxTerms];                     // current subset: positions in the candidate list
+    int16_t cand[kM5MaxTerms];
+    double red_v[kM5Threads / 32];
+    int red_i[kM5Threads / 32];
+    int stack_node[kM5MaxNodes], stack_lo[kM5MaxNodes], stack_hi[kM5MaxNodes];
+    int sp, nn, cur, cur_lo, cur_hi, ncand, nsel, split_attr, drop;
+    double split_thr, sd_root, e_cur, bval;
+};
+
+// The standard deviation from a count, sum and sum of squares: sqrt(max(0, (s2 - s1 s1 / c) / c)),
+// with one rounding per operation (the reference's arithmetic).
+__device__ __forceinline__ double m5_sd(int c, double s1, double s2) {
+    const double cd = (double)c;
+    const double v = __ddiv_rn(__dsub_rn(s2, __ddiv_rn(__dmul_rn(s1, s1), cd)), cd);
+    return __dsqrt_rn(v > 0.0 ? v : 0.0);
+}
+
+// In-place inverse of the nb x nb leading block of M (row stride kM5Ld) by Gauss-Jordan
+// elimination without pivoting (the systems are symmetric positive definite).  Block-wide.
+__device__ void m5_invert(M5Smem& S, double* M, int nb) {
+    const int tid = threadIdx.x;
+    for (int k = 0; k < nb; ++k) {
+        const double piv = 1.0 / M[k * kM5Ld + k];
+        for (int i = tid; i < nb; i += kM5Threads) {
+            S.colk[i] = M[i * kM5Ld + k];
+            S.rowk[i] = M[k * kM5Ld + i] * piv;
+        }
+        __syncthreads();
+        for (int e = tid; e < nb * nb; e += kM5Threads) {
+            const int i = e / nb, j = e - i * nb;
+            if (i == k && j == k) M[k * kM5Ld + k] = piv;
+            else if (i == k) M[k * kM5Ld + j] = S.rowk[j];
+            else if (j == k) M[i * kM5Ld + k] = -S.colk[i] * piv;
+            else M[i * kM5Ld + j] = fma(-S.colk[i], S.rowk[j], M[i * kM5Ld + j]);
+        }
+        __syncthreads();
+    }
+}
+
+// Estimated error of a model (b, w on the selected candidates) over the node's instances:
+// mean |y - prediction| * (m + v) / (m - v), v = terms + 1; DBL_MAX when m <= v.  One warp.
+__device__ double m5_warp_err(const M5Smem& S, int lo, int m, const double* w, double b, int nsel,
+                              const uint8_t* selpos, int skip) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int a = lane; a < m; a += 32) {
+        const int i = S.ids[lo + a];
+        const double* z = S.zp[i];
+        double p = b;
+        for (int q = 0; q < nsel; ++q) {
+            if (q == skip) continue;
+            p = fma(w[q], __ldg(z + S.cand[selpos[q]]), p);
+        }
+        acc += fabs(S.y[i] - p);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const int v = nsel - (skip >= 0 ? 1 : 0) + 1;
+    if (m <= v) return DBL_MAX;
+    return acc / m * ((double)(m + v) / (double)(m - v));
+}
+
+__global__ void __launch_bounds__(kM5Threads, 1)
+m5p_fit_kernel(const TransferArgs a) {
+    extern __shared__ __align__(16) unsigned char m5sm[];
+    M5Smem& S = *reinterpret_cast<M5Smem*>(m5sm);
+    __shared__ GroupSmem G;
+    __shared__ uint16_t pu[kTrPairs];
+    __shared__ double yl[kTrPairs];
+    __shared__ int np_s;
+    const int q = blockIdx.x, j = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kM5Threads / 32;
+    int start[RS_MAXRUNS + 1], F = 0;
+    const int N = rs_group_layout(q, a.group_off, a.max_runs, a.n_runs, a.a_row, a.a_fw, a.b_fw, a.stat_stride, start, F);
+    if (N < 0 || N > a.ld || F > kM5MaxFeat) return;   // reported by the predict / rank kernel
+    const int64_t g0 = a.group_off[q];
+    const int R = (int)(a.group_off[q + 1] - g0);
+    load_group(G, a.a_row, a.a_masks, a.a_lt, g0, start, N);
+    if (tid == 0) np_s = build_pairs(G, j, R, start, pu, yl, nullptr, q);
+    __syncthreads();
+    const int n = np_s;
+    M5Tree* T = a.trees + ((int64_t)q * RS_NOPT + j);
+    uint8_t* st_out = a.fst + (int64_t)q * RS_NOPT + j;
+    if (n == 0) {
+        if (tid == 0) *st_out = RS_FIT_EMPTY;
+        return;
+    }
+    for (int i = tid; i < n; i += kM5Threads) {
+        const int u = pu[i];
+        int r = 0;
+        while (u >= start[r + 1]) ++r;
+        S.zp[i] = a.ZA + a.a_xo[g0 + r] + (int64_t)(u - start[r]) * F;
+        S.y[i] = yl[i];
+        S.ids[i] = (uint8_t)i;
+    }
+    __syncthreads();
+    // presort: attribute f's instances by (value, index)
+    for (int f = tid; f < F; f += kM5Threads) {
+        uint8_t* o = S.sorted[f];
+        for (int i = 0; i < n; ++i) {
+            const double v = __ldg(S.zp[i] + f);
+            int p = i;
+            while (p > 0) {
+                const int w = o[p - 1];
+                const double u = __ldg(S.zp[w] + f);
+                if (u > v || (u == v && w > i)) {
+                    o[p] = (uint8_t)w;
+                    --p;
+                } else {
+                    break;
+                }
+            }
+            o[p] = (uint8_t)i;
+        }
+    }
+    if (tid == 0) {
+        S.nn = 1;
+        S.sp = 1;
+        S.stack_node[0] = 0;
+        S.stack_lo[0] = 0;
+        S.stack_hi[0] = n;
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            s1 = __dadd_rn(s1, S.y[i]);
+            s2 = __dadd_rn(s2, __dmul_rn(S.y[i], S.y[i]));
+        }
+        S.sd_root = m5_sd(n, s1, s2);
+    }
+    __syncthreads();
+    // ---- grow (depth first, left child first: the reference's node numbering).  Thread 0 pops
+    // the next node; every path through the body ends at a barrier before the next pop.
+    for (;;) {
+        if (tid == 0) {
+            if (S.sp > 0) {
+                --S.sp;
+                S.cur = S.stack_node[S.sp];
+                S.cur_lo = S.stack_lo[S.sp];
+                S.cur_hi = S.stack_hi[S.sp];
+            } else {
+                S.cur = -1;
+            }
+        }
+        __syncthreads();
+        const int t = S.cur, lo = S.cur_lo, hi = S.cur_hi, m = hi - lo;
+        if (t < 0) break;
+        if (tid == 0) {
+            S.attr[t] = -1;
+            S.lo[t] = (uint8_t)lo;
+            S.hi[t] = (uint8_t)hi;
+        }
+        // the node's label sums in instance order
+        double s1 = 0.0, s2 = 0.0;
+        for (int a2 = lo; a2 < hi; ++a2) {
+            const double yv = S.y[S.ids[a2]];
+            s1 = __dadd_rn(s1, yv);
+            s2 = __dadd_rn(s2, __dmul_rn(yv, yv));
+        }
+        const double sd = m5_sd(m, s1, s2);
+        if (m < 4 || sd <= __dmul_rn(kM5SdFrac, S.sd_root)) {
+            __syncthreads();
+            continue;
+        }
+        // split search: one thread per attribute, candidates in sorted order
+        double best = 0.0, bthr = 0.0;
+        int battr = -1;
+        for (int f = tid; f < F; f += kM5Threads) {
+            const uint8_t* o = S.sorted[f];
+            double l1 = 0.0, l2 = 0.0;
+            for (int c = 1; c < m; ++c) {
+                const int ia = o[lo + c - 1], ib = o[lo + c];
+                const double yv = S.y[ia];
+                l1 = __dadd_rn(l1, yv);
+                l2 = __dadd_rn(l2, __dmul_rn(yv, yv));
+                const double va = __ldg(S.zp[ia] + f), vb = __ldg(S.zp[ib] + f);
+                if (!(va < vb) || c < 2 || m - c < 2) continue;
+                const double sdl = m5_sd(c, l1, l2), sdr = m5_sd(m - c, __dsub_rn(s1, l1), __dsub_rn(s2, l2));
+                const double red = __dsub_rn(sd, __ddiv_rn(__dadd_rn(__dmul_rn((double)c, sdl),
+                                                                     __dmul_rn((double)(m - c), sdr)),
+                                                           (double)m));
+                if (red > best) {
+                    best = red;
+                    battr = f;
+                    bthr = __dmul_rn(__dadd_rn(va, vb), 0.5);
+                }
+            }
+        }
+        // block argmax: largest SDR, ties to the lower attribute
+#pragma unroll
+        for (int o2 = 16; o2 >= 1; o2 >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o2);
+            const int oa = __shfl_xor_sync(0xffffffffu, battr, o2);
+            const double ot = __shfl_xor_sync(0xffffffffu, bthr, o2);
+            if (oa >= 0 && (battr < 0 || ob > best || (ob == best && oa < battr))) {
+                best = ob;
+                battr = oa;
+                bthr = ot;
+            }
+        }
+        if (lane == 0) {
+            S.red_v[warp] = best;
+            S.red_i[warp] = battr;
+            S.colk[warp] = bthr;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bb = 0.0, bt = 0.0;
+            int ba = -1;
+            for (int w2 = 0; w2 < nwarps; ++w2) {
+                const int oa = S.red_i[w2];
+                if (oa >= 0 && (ba < 0 || S.red_v[w2] > bb || (S.red_v[w2] == bb && oa < ba))) {
+                    bb = S.red_v[w2];
+                    ba = oa;
+                    bt = S.colk[w2];
+                }
+            }
+            S.split_attr = ba;
+            S.split_thr = bt;
+        }
+        __syncthreads();
+        const int sa = S.split_attr;
+        if (sa < 0) {                              // no admissible split: a leaf (uniform)
+            __syncthreads();
+            continue;
+        }
+        const double sthr = S.split_thr;
+        for (int a2 = lo + tid; a2 < hi; a2 += kM5Threads) {
+            const int i = S.ids[a2];
+            S.side[i] = __ldg(S.zp[i] + sa) <= sthr ? 0 : 1;
+        }
+        __syncthreads();
+        // stable partition of the node's instance list and of every attribute's sorted list
+        int nl = 0;
+        for (int f = tid; f < F + 1; f += kM5Threads) {
+            uint8_t* o = f < F ? S.sorted[f] : S.ids;
+            uint8_t* sc = S.scratch[tid];
+            int k = 0;
+            for (int a2 = lo; a2 < hi; ++a2)
+                if (S.side[o[a2]] == 0) sc[k++] = o[a2];
+            nl = k;
+            for (int a2 = lo; a2 < hi; ++a2)
+                if (S.side[o[a2]] == 1) sc[k++] = o[a2];
+            for (int a2 = 0; a2 < m; ++a2) o[lo + a2] = sc[a2];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int cnt = 0;
+            for (int a2 = lo; a2 < hi; ++a2) cnt += S.side[S.ids[a2]] == 0;
+            const int l = S.nn, r = S.nn + 1;
+            S.nn += 2;
+            S.attr[t] = (int16_t)sa;
+            S.thr[t] = sthr;
+            S.left[t] = (int16_t)l;
+            S.right[t] = (int16_t)r;
+            T->parent[l] = T->parent[r] = (int16_t)t;
+            S.stack_node[S.sp] = r;
+            S.stack_lo[S.sp] = lo + cnt;
+            S.stack_hi[S.sp] = hi;
+            ++S.sp;
+            S.stack_node[S.sp] = l;
+            S.stack_lo[S.sp] = lo;
+            S.stack_hi[S.sp] = lo + cnt;
+            ++S.sp;
+        }
+        (void)nl;
+        __syncthreads();
+    }
+    const int nn = S.nn;
+    // ---- models and pruning, children before parents (children have larger node numbers)
+    for (int t = nn - 1; t >= 0; --t) {
+        const int lo = S.lo[t], m = S.hi[t] - S.lo[t];
+        const bool internal = S.attr[t] >= 0;
+        if (tid < kM5MaxFeat / 64) {
+            unsigned long long bits = 0;
+            if (internal) {
+                bits = S.tested[S.left[t]][tid] | S.tested[S.right[t]][tid];
+                if (S.attr[t] / 64 == tid) bits |= 1ull << (S.attr[t] % 64);
+            }
+            S.tested[t][tid] = bits;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int nc = 0;
+            for (int f = 0; f < F && nc < kM5MaxTerms; ++f)
+                if ((S.tested[t][f / 64] >> (f % 64)) & 1ull) S.cand[nc++] = (int16_t)f;
+            S.ncand = nc;
+            S.nsel = nc;
+            for (int k = 0; k < nc; ++k) S.sel[k] = (uint8_t)k;
+            double yb = 0.0;
+            for (int a2 = 0; a2 < m; ++a2) yb += S.y[S.ids[lo + a2]];
+            S.bval = yb / m;                       // the label mean, for now
+        }
+        __syncthreads();
+        const int nc = S.ncand;
+        const double ybar = S.bval;
+        for (int f = tid; f < nc; f += kM5Threads) {
+            double s = 0.0;
+            for (int a2 = 0; a2 < m; ++a2) s += __ldg(S.zp[S.ids[lo + a2]] + S.cand[f]);
+            S.zbar[f] = s / m;
+        }
+        __syncthreads();
+        for (int e = tid; e < nc * (nc + 1); e += kM5Threads) {
+            const int f = e / (nc + 1), g = e - f * (nc + 1);
+            double s = 0.0;
+            if (g < nc) {
+                if (g > f) continue;
+                for (int a2 = 0; a2 < m; ++a2) {
+                    const double* z = S.zp[S.ids[lo + a2]];
+                    s += (__ldg(z + S.cand[f]) - S.zbar[f]) * (__ldg(z + S.cand[g]) - S.zbar[g]);
+                }
+                S.G[f * kM5Ld + g] = s + (f == g ? kM5Ridge : 0.0);
+                S.G[g * kM5Ld + f] = s + (f == g ? kM5Ridge : 0.0);
+            } else {
+                for (int a2 = 0; a2 < m; ++a2) {
+                    const int i = S.ids[lo + a2];
+                    s += (__ldg(S.zp[i] + S.cand[f]) - S.zbar[f]) * (S.y[i] - ybar);
+                }
+                S.r[f] = s;
+            }
+        }
+        __syncthreads();
+        // greedy elimination
+        for (;;) {
+            const int ns = S.nsel;
+            for (int e = tid; e < ns * ns; e += kM5Threads) {
+                const int i = e / ns, k = e - i * ns;
+                S.H[i * kM5Ld + k] = S.G[S.sel[i] * kM5Ld + S.sel[k]];
+            }
+            __syncthreads();
+            m5_invert(S, S.H, ns);
+            for (int i = tid; i < ns; i += kM5Threads) {
+                double s = 0.0;
+                for (int k = 0; k < ns; ++k) s = fma(S.H[i * kM5Ld + k], S.r[S.sel[k]], s);
+                S.w[i] = s;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double b = ybar;
+                for (int i = 0; i < ns; ++i) b -= S.w[i] * S.zbar[S.sel[i]];
+                S.rowk[0] = b;                     // the model's intercept
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const double e_full = m5_warp_err(S, lo, m, S.w, S.rowk[0], ns, S.sel, -1);
+                if (lane == 0) S.e_cur = e_full;
+            }
+            // drop-one candidates: w' = w - H[:, d] w_d / H_dd, one warp each
+            for (int d = warp; d < ns; d += nwarps) {
+                const double fac = S.w[d] / S.H[d * kM5Ld + d];
+                double wd[kM5MaxTerms];
+                double b = ybar;
+                for (int i = 0; i < ns; ++i) {
+                    wd[i] = i == d ? 0.0 : fma(-S.H[i * kM5Ld + d], fac, S.w[i]);
+                    if (i != d) b -= wd[i] * S.zbar[S.sel[i]];
+                }
+                const double ed = m5_warp_err(S, lo, m, wd, b, ns, S.sel, d);
+                if (lane == 0) S.cand_err[d] = ed;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double bestd = DBL_MAX;
+                int drop = -1;
+                for (int d = 0; d < ns; ++d)
+                    if (S.cand_err[d] < bestd) {
+                        bestd = S.cand_err[d];
+                        drop = d;
+                    }
+                S.drop = (ns > 0 && drop >= 0 && bestd <= S.e_cur) ? drop : -1;
+                if (S.drop >= 0) {
+                    for (int k = S.drop; k < ns - 1; ++k) S.sel[k] = S.sel[k + 1];
+                    S.nsel = ns - 1;
+                }
+            }
+            __syncthreads();
+            if (S.drop < 0) break;
+        }
+        // the node's model and the pruning decision
+        if (tid == 0) {
+            const int ns = S.nsel;
+            T->nterm[t] = ns;
+            for (int k = 0; k < ns; ++k) {
+                T->term_attr[t][k] = S.cand[S.sel[k]];
+                T->term_w[t][k] = S.w[k];
+            }
+            T->b[t] = S.rowk[0];
+            T->count[t] = m;
+            const double e = S.e_cur;
+            double keep = DBL_MAX;
+            if (internal) {
+                const int l = S.left[t], r = S.right[t];
+                const int ml = S.hi[l] - S.lo[l], mr = S.hi[r] - S.lo[r];
+                keep = (ml * S.est[l] + mr * S.est[r]) / m;
+            }
+            if (internal && !(e <= keep)) {
+                S.est[t] = keep;
+            } else {                               // a leaf: its parent's candidates get no test
+                S.attr[t] = -1;                    // from here down
+                S.est[t] = e;
+                for (int k = 0; k < kM5MaxFeat / 64; ++k) S.tested[t][k] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < nn; t += kM5Threads) {
+        T->attr[t] = S.attr[t];
+        T->thr[t] = S.thr[t];
+        T->left[t] = S.left[t];
+        T->right[t] = S.right[t];
+    }
+    if (tid == 0) {
+        T->n_nodes = nn;
+        T->parent[0] = -1;
+        *st_out = RS_FIT_OK;
+    }
+}
+
+// The M5P prediction for one test vector: the leaf's model, then smoothing with every
+// ancestor's model on the way up, p = (n_c p + k q) / (n_c + k).
+__device__ double m5_predict(const M5Tree* __restrict__ T, const double* __restrict__ z) {
+    auto model = [&](int t) {
+        double p = T->b[t];
+        for (int k = 0; k < T->nterm[t]; ++k) p = fma(T->term_w[t][k], __ldg(z + T->term_attr[t][k]), p);
+        return p;
+    };
+    int t = 0;
+    while (T->attr[t] >= 0) t = __ldg(z + T->attr[t]) <= T->thr[t] ? T->left[t] : T->right[t];
+    double p = model(t);
+    while (T->parent[t] >= 0) {
+        const int u = T->parent[t];
+        const double nc = (double)T->count[t];
+        p = (nc * p + kM5Smooth * model(u)) / (nc + kM5Smooth);
+        t = u;
+    }
+    return p;
+}
+
 // ibk_nearest_mean for a list of n > kIbkK pairs (n up to kTrPairs): the chosen labels are
 // summed in ascending pair index.
 __device__ __forceinline__ double ibk_nearest_mean_n(int n, const double* __restrict__ Dt, const uint16_t* pu,
@@ -286,6 +771,7 @@ transfer_rank_kernel(const TransferArgs a) {
         const int np = build_pairs(S.G, j, R, start, S.pu[j], S.yl[j], a.r.dstatus, q);
         S.np[j] = np;
         S.st[j] = a.ibk ? (np > 0 ? RS_FIT_OK : RS_FIT_EMPTY) : a.fst[(int64_t)q * RS_NOPT + j];
+        if (a.m5p && np > kM5MaxN) S.st[j] = RS_FIT_NOTPD;
     }
     __syncthreads();
     RankTally c;
@@ -304,7 +790,9 @@ transfer_rank_kernel(const TransferArgs a) {
             pred[j] = 0.0;
             if (!(((candm & okm) >> j) & 1)) continue;
             const int n = S.np[j];
-            if (a.ibk) {
+            if (a.m5p) {
+                pred[j] = m5_predict(a.trees + ((int64_t)q * RS_NOPT + j), a.ZB + a.b_xo[q] + (int64_t)t * F);
+            } else if (a.ibk) {
                 if (n <= kIbkK) {
                     double sum = 0.0;
                     for (int i = 0; i < n; ++i) sum += S.yl[j][i];
@@ -356,6 +844,9 @@ cudaError_t rs_launch_iota64(int64_t* out, int64_t n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+size_t rs_m5p_tree_bytes() { return sizeof(M5Tree); }
+int rs_m5p_max_feat() { return kM5MaxFeat; }
+
 size_t rs_transfer_fit_bytes(int64_t Q) {
     return (size_t)Q * RS_NOPT * kTrCoef * sizeof(double) + (size_t)Q * RS_NOPT;
 }
@@ -384,10 +875,23 @@ cudaError_t rs_launch_transfer(const rs_transfer_args& t, cudaStream_t st) {
     a.opt_mask = t.opt_mask & 63;
     a.rank_all = (t.flags & RS_RANK_ALL) != 0;
     a.fit_status = t.fit_status;
+    a.m5p = t.m5p;
+    a.trees = reinterpret_cast<M5Tree*>(t.m5_ws);
+    a.ZA = t.ZA;
+    a.a_xo = t.a_x_offsets;
+    a.ZB = t.ZB;
+    a.b_xo = t.b_x_offsets;
     a.r = RankPassArgs{nullptr, 0, nullptr, 0, 0, nullptr, t.dstatus, t.k, okey_host(t.log_tau),
                        t.flags & ~RS_RANK_ALL, t.rec_code, t.rec_pred, t.pred_all, t.counters};
     cudaError_t e = cudaSuccess;
-    if (!t.ibk) {
+    if (t.m5p) {
+        const size_t msmem = sizeof(M5Smem);
+        e = cudaFuncSetAttribute(m5p_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+        if (e != cudaSuccess) return e;
+        m5p_fit_kernel<<<dim3((unsigned)t.Q, RS_NOPT), kM5Threads, msmem, st>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    } else if (!t.ibk) {
         const int nmax = RS_MAXPAIRS * t.max_runs;
         const size_t fsmem = ((size_t)nmax * (nmax + 1) + 5 * (size_t)nmax) * sizeof(double);
         e = cudaFuncSetAttribute(transfer_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);

@@ -479,13 +479,14 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
 namespace {
 struct TransferWs {
     double *ZA, *ZB, *mu, *sigma, *KA, *Kx, *fit;
+    void* m5;
     int64_t* iota;
     size_t bytes;
 };
 
 int transfer_runs(const rs_groups* g) { return g ? g->max_runs : 1; }
 
-TransferWs transfer_carve(void* base, const rs_batch* train, const rs_batch* test, const rs_groups* g) {
+TransferWs transfer_carve(void* base, const rs_batch* train, const rs_batch* test, const rs_groups* g, int flags) {
     TransferWs w{};
     char* c = (char*)base;
     size_t o = 0;
@@ -499,17 +500,19 @@ TransferWs transfer_carve(void* base, const rs_batch* train, const rs_batch* tes
     w.KA = (double*)take(Q * ld * ld * sizeof(double));
     w.Kx = (double*)take(Q * RS_MAXV * ld * sizeof(double));
     w.fit = (double*)take(rs_transfer_fit_bytes((int64_t)Q));
+    w.m5 = (flags & RS_MODEL_M5P) ? take(Q * RS_NOPT * rs_m5p_tree_bytes()) : nullptr;
     w.iota = g ? nullptr : (int64_t*)take((Q + 1) * sizeof(int64_t));
     w.bytes = o;
     return w;
 }
 }  // namespace
 
-size_t rs_transfer_workspace_bytes(const rs_batch* train, const rs_batch* test, const rs_groups* groups) {
+size_t rs_transfer_workspace_bytes(const rs_batch* train, const rs_batch* test, const rs_groups* groups,
+                                   int flags) {
     if (!train || !test || test->n_programs < 1 || train->x_elems < 0 || test->x_elems < 0 ||
         train->max_feat < 1 || (groups && (groups->max_runs < 1 || groups->max_runs > RS_MAXRUNS)))
         return 0;
-    return transfer_carve(nullptr, train, test, groups).bytes;
+    return transfer_carve(nullptr, train, test, groups, flags).bytes;
 }
 
 rs_status rs_transfer(rs_ctx* c, const rs_batch* train, const rs_batch* test, const rs_groups* groups,
@@ -532,16 +535,21 @@ rs_status rs_transfer(rs_ctx* c, const rs_batch* train, const rs_batch* test, co
     if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(c, RS_EINVAL, "lambda must be finite and >= 0");
     if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
-    if (flags & ~(RS_RANK_ALL | RS_MODEL_IBK)) return fail(c, RS_EINVAL, "flags: RS_RANK_ALL and RS_MODEL_IBK only");
+    if (flags & ~(RS_RANK_ALL | RS_MODEL_IBK | RS_MODEL_M5P))
+        return fail(c, RS_EINVAL, "flags: RS_RANK_ALL, RS_MODEL_IBK and RS_MODEL_M5P only");
+    if ((flags & RS_MODEL_IBK) && (flags & RS_MODEL_M5P)) return fail(c, RS_EINVAL, "one model: IBK or M5P");
+    if ((flags & RS_MODEL_M5P) && train->max_feat > rs_m5p_max_feat())
+        return fail(c, RS_EUNSUPPORTED, "RS_MODEL_M5P takes at most %d features", rs_m5p_max_feat());
     if (opt_mask < 0 || opt_mask > 63) return fail(c, RS_EINVAL, "opt_mask must be in 0..63");
     if (!rec_code) return fail(c, RS_EINVAL, "rec_code is required");
     if (!ws) return fail(c, RS_EINVAL, "workspace is NULL");
     if ((uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
-    const size_t need = rs_transfer_workspace_bytes(train, test, groups);
+    const size_t need = rs_transfer_workspace_bytes(train, test, groups, flags);
     if (ws_bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
-    TransferWs w = transfer_carve(ws, train, test, groups);
+    TransferWs w = transfer_carve(ws, train, test, groups, flags);
     cudaSetDevice(c->device);
     const bool ibk = (flags & RS_MODEL_IBK) != 0;
+    const bool m5p = (flags & RS_MODEL_M5P) != 0;
     const int Q = test->n_programs;
     const int max_runs = transfer_runs(groups);
     const int ld = RS_MAXV * max_runs;
@@ -558,9 +566,11 @@ rs_status rs_transfer(rs_ctx* c, const rs_batch* train, const rs_batch* test, co
     za.dtype = RS_F64;
     zb.X = w.ZB;
     zb.dtype = RS_F64;
-    e = rs_launch_transfer_blocks(&za, &zb, goff, max_runs, stride, ld, ibk ? nullptr : w.KA, w.Kx, ibk ? 1 : 0,
-                                  c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "rs_transfer (blocks)");
+    if (!m5p) {                 // the model tree reads the standardized rows themselves
+        e = rs_launch_transfer_blocks(&za, &zb, goff, max_runs, stride, ld, ibk ? nullptr : w.KA, w.Kx, ibk ? 1 : 0,
+                                      c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rs_transfer (blocks)");
+    }
     rs_transfer_args t{};
     t.Q = Q;
     t.group_off = goff;
@@ -586,6 +596,12 @@ rs_status rs_transfer(rs_ctx* c, const rs_batch* train, const rs_batch* test, co
     t.flags = flags;
     t.fit_status = fit_status;
     t.fit_ws = w.fit;
+    t.m5p = m5p ? 1 : 0;
+    t.m5_ws = w.m5;
+    t.ZA = w.ZA;
+    t.a_x_offsets = train->x_offsets;
+    t.ZB = w.ZB;
+    t.b_x_offsets = test->x_offsets;
     t.rec_code = rec_code;
     t.rec_pred = rec_pred;
     t.pred_all = pred_all;

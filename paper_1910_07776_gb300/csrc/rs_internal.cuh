@@ -156,6 +156,12 @@ struct rs_transfer_args {
     int flags;
     uint8_t* fit_status;          // [Q][6], nullable
     double* fit_ws;               // rs_transfer_fit_bytes(Q) of device scratch for the ridge fits
+    int m5p;                      // the M5P model tree (RS_MODEL_M5P)
+    void* m5_ws;                  // Q * 6 * rs_m5p_tree_bytes() of device scratch for its trees
+    const double* ZA;             // standardized training rows (train's x_offsets)
+    const int64_t* a_x_offsets;
+    const double* ZB;             // standardized test rows (test's x_offsets)
+    const int64_t* b_x_offsets;
     uint32_t* rec_code;
     double* rec_pred;
     double* pred_all;
@@ -164,6 +170,8 @@ struct rs_transfer_args {
 };
 cudaError_t rs_launch_transfer(const rs_transfer_args& a, cudaStream_t st);
 size_t rs_transfer_fit_bytes(int64_t Q);
+size_t rs_m5p_tree_bytes();
+int rs_m5p_max_feat();
 cudaError_t rs_launch_iota64(int64_t* out, int64_t n, cudaStream_t st);
 size_t rs_surrogate_blob_floats();
 size_t rs_surrogate_train_ws_bytes(int B);

@@ -21,7 +21,7 @@ RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EUNSUPPORTED, RS_EDATA = 
 RS_F32, RS_F64 = 0, 1
 RS_GRAM_F64, RS_GRAM_BF16X3, RS_GRAM_DIST2 = 0, 1, 2
 RS_FORM_BATCHED, RS_FORM_PLAIN = 0, 1
-RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK = 1, 2, 4
+RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK, RS_MODEL_M5P = 1, 2, 4, 8
 IBK_NEIGHBORS = 10
 NOPT = 6
 COEF_STRIDE = 33
@@ -125,7 +125,7 @@ def load(path: str = SO):
     L.rs_surrogate_infer.argtypes = [P, P, P, i64, C.c_float, P, P, P, P, i, d, i, P, P, P, C.c_size_t, i]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
-    L.rs_transfer_workspace_bytes.argtypes = [P, P, P]
+    L.rs_transfer_workspace_bytes.argtypes = [P, P, P, i]
     L.rs_transfer_workspace_bytes.restype = C.c_size_t
     L.rs_transfer.argtypes = [P, P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     for name in EXPORTS:
@@ -399,10 +399,11 @@ class Context:
             int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
 
-    def transfer_workspace_bytes(self, train: DeviceBatch, test: DeviceBatch, groups=None) -> int:
+    def transfer_workspace_bytes(self, train: DeviceBatch, test: DeviceBatch, groups=None, flags: int = 0) -> int:
         ac, bc = train.c(), test.c()
         g = _groups_c(groups, test)
-        return int(self.L.rs_transfer_workspace_bytes(C.byref(ac), C.byref(bc), None if g is None else C.byref(g)))
+        return int(self.L.rs_transfer_workspace_bytes(C.byref(ac), C.byref(bc), None if g is None else C.byref(g),
+                                                      int(flags)))
 
     def transfer(self, train: DeviceBatch, test: DeviceBatch, workspace, rec_code, groups=None, lam: float = 1e-3,
                  k: int = 3, tau: float = 1.05, flags: int = 0, opt_mask: int = 0x3F, fit_status=None,
@@ -557,7 +558,7 @@ def transfer_run(ctx: Context, train: DeviceBatch, test: DeviceBatch, groups=Non
     if groups is not None:
         offs = np.ascontiguousarray(groups, dtype=np.int64)
         g = (torch.from_numpy(offs).to(dev), int(np.diff(offs).max()))
-    ws = ctx.workspace(ctx.transfer_workspace_bytes(train, test, g))
+    ws = ctx.workspace(ctx.transfer_workspace_bytes(train, test, g, flags))
     out = alloc_outputs(R, 0, k, dev)
     st = torch.empty(Q * NOPT, dtype=torch.uint8, device=dev)
     ctx.transfer(train, test, ws, out.rec_code, groups=g, lam=lam, k=k, tau=tau, flags=flags, opt_mask=opt_mask,
