@@ -578,12 +578,14 @@ def run_ibk(rs, ctx, batch, splits, dev, stream, flush, args):
 
 
 PAPER_TABLE3_IBK = {1: 97.3, 2: 96.0, 3: 96.3, 4: 92.0, 5: 83.6, 6: 55.7}   # Table 3, % (real profiles)
+PAPER_TABLE3_M5P = {1: 86.4, 2: 86.4, 3: 33.3, 4: 81.6, 5: 33.3, 6: 60.1}
 
 
 def run_transfer(rs, ctx, dev, stream, flush, args):
     """Table 2's six experiments (Sec. 5) on the seeded stand-ins of the BH / NB runs
     (synth.make_runs: 6 + 4 inputs x 3 runs x 64 versions x 96 counters): per experiment and
-    learner one rs_transfer call (device time, after warm-up), the sign accuracy of Table 3,
+    learner (ridge, IBK, M5P) one rs_transfer call (device time, after warm-up), the sign
+    accuracy of Table 3,
     the top-1 hit rate, and the AC/EX ratios (actual over expected speedup, Sec. 5) of every
     scored prediction.  Table 3's values come from the paper's real profiles: context only."""
     import torch
@@ -613,7 +615,8 @@ def run_transfer(rs, ctx, dev, stream, flush, args):
                     if not (m[t] >> j) & 1 and w is not None:
                         act[rows.start + t, j] = lt[t] - lt[w]
         res = {"problems": int(pr.test.n_programs), "train_runs_per_problem": int(np.diff(pr.groups).max()),
-               "test_rows": int(R), "opt_mask": int(pr.opt_mask), "paper_ibk_accuracy_pct": PAPER_TABLE3_IBK[e]}
+               "test_rows": int(R), "opt_mask": int(pr.opt_mask), "paper_ibk_accuracy_pct": PAPER_TABLE3_IBK[e],
+               "paper_m5p_accuracy_pct": PAPER_TABLE3_M5P[e]}
         for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK), ("m5p", rs.RS_MODEL_M5P)):
             o = rs.alloc_outputs(R, 0, CFG["k"], dev)
             call = lambda: ctx.transfer(dtr, dte, ws, o.rec_code, groups=g, lam=CFG["lam"], k=CFG["k"],
