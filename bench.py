@@ -892,11 +892,12 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
 def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
     """End to end through rs_cv_step with host buffers, as a stream of batches: every step
     copies its inputs from pinned host memory, flushes L2, computes, and brings its
-    recommendations (rec_code, rec_pred) and counters back into pinned host memory.  Outputs are
-    double-buffered: step i's results are copied back on a second stream while step i + 1
-    computes, so the ~150 MB of device-to-host copies per step overlap the compute.  The timed
-    region runs from the first step's input copy to the last step's results landing in host
-    memory; ms_per_step is that time over the steps."""
+    recommendations back into pinned host memory -- rec_code and the reported predictions
+    packed back to back (RS_PACK_PRED: ~1.2 values per row instead of k = 3, ~73 MB per step
+    instead of ~150) -- with the counters.  Outputs are double-buffered: step i's results are
+    copied back on a second stream while step i + 1 computes.  The timed region runs from the
+    first step's input copy to the last step's results landing in host memory; ms_per_step is
+    that time over the steps."""
     import torch
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     fo = np.zeros(batch.n_programs + 1, np.int64)
@@ -925,11 +926,11 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
     h_pred = [torch.empty(R * k, dtype=torch.float64).pin_memory() for _ in range(2)]
     h_cnt = [torch.empty(16, dtype=torch.int64).pin_memory() for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = R * 4 + R * k * 8 + 16 * 8
     cs = torch.cuda.Stream(dev)
     computed = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    moved = [0]
 
     def step(i):
         b = i % 2
@@ -940,30 +941,46 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
         stream.wait_event(copied[b])           # this output set's previous copy has landed
         o.counters.zero_()
         ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=k, tau=CFG["tau"],
-                    rec_pred=o.rec_pred, counters=o.counters)
+                    flags=rs.RS_PACK_PRED, rec_pred=o.rec_pred, counters=o.counters)
+        h_cnt[b].copy_(o.counters, non_blocking=True)
         computed[b].record(stream)
+
+    def bring_back(i):
+        # issued after step i + 1 is queued: the host waits for step i's counters (the packed
+        # length) while the device works on step i + 1
+        b = i % 2
+        o = outs[b]
+        computed[b].synchronize()
+        total = int(h_cnt[b][4].item())
         cs.wait_event(computed[b])
         with torch.cuda.stream(cs):
             h_code[b].copy_(o.rec_code, non_blocking=True)
-            h_pred[b].copy_(o.rec_pred, non_blocking=True)
-            h_cnt[b].copy_(o.counters, non_blocking=True)
+            h_pred[b][:total].copy_(o.rec_pred[:total], non_blocking=True)
         copied[b].record(cs)
+        moved[0] += R * 4 + total * 8 + 16 * 8
+
+    def run(n_steps):
+        for i in range(n_steps):
+            step(i)
+            if i > 0:
+                bring_back(i - 1)
+        bring_back(n_steps - 1)
 
     for b in range(2):
         copied[b].record(cs)
-    for i in range(3):
-        step(i)
+    run(3)
     torch.cuda.synchronize()
+    moved[0] = 0
     n = max(4, min(args.steps, 10))
     e0.record(stream)
-    for i in range(n):
-        step(i)
+    run(n)
     for b in range(2):
         stream.wait_event(copied[b])
     e1.record(stream)
     torch.cuda.synchronize()
     tot = e0.elapsed_time(e1)
     ctx.check_device_status()
+    d2h = moved[0] / n
     # the host link's own rates (one bulk copy each way of a step's output size), the bound of
     # this leg: a step cannot finish before its outputs have crossed the link
     big_d = outs[0].rec_pred
@@ -985,9 +1002,10 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "host_link_gbs": {"d2h": d2h_gbs, "h2d": h2d_gbs},
             "copy_bound_ms_per_step": d2h / (d2h_gbs * 1e6) + h2d / (h2d_gbs * 1e6),
-            "path": "per step: pinned host -> device copies of the inputs, L2 flush, rs_cv_step, device -> "
-                    "pinned host copies of rec_code / rec_pred / counters on a second stream (outputs "
-                    "double-buffered: a step's copies overlap the next step's compute)"}
+            "path": "per step: pinned host -> device copies of the inputs, L2 flush, rs_cv_step with packed "
+                    "predictions (RS_PACK_PRED), device -> pinned host copies of rec_code, the packed "
+                    "predictions and the counters on a second stream (outputs double-buffered: a step's "
+                    "copies overlap the next step's compute)"}
 
 
 if __name__ == "__main__":

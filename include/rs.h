@@ -61,7 +61,8 @@ enum {
                              predictions taken through Z (for an inexact Gram)        */
     RS_MODEL_IBK = 4,     /* the instance-based learner (IBK, k nearest neighbours)
                              instead of ridge regression; K is the distance block    */
-    RS_MODEL_M5P = 8      /* the M5P model tree instead of ridge regression (rs_transfer) */
+    RS_MODEL_M5P = 8,     /* the M5P model tree instead of ridge regression (rs_transfer) */
+    RS_PACK_PRED = 16     /* rec_pred packed: the reported lists back to back (rs_predict_rank) */
 };
 #define RS_IBK_NEIGHBORS 10  /* k of the instance-based learner (Sec. 3.4: k = 10)        */
 
@@ -202,6 +203,10 @@ rs_status rs_fit_batched(rs_ctx* ctx, const rs_batch* std, const double* K,
  * rec_offsets: from rs_rec_offsets.  Outputs per row (R = rec_offsets[S]):
  *   rec_code  uint32 [R]: bits 0-3 = count c, bits 4+4i..7+4i = i-th optimization (0xF unused)
  *   rec_pred  double [R][k]: predicted log speedups of the reported list (NaN unused), nullable
+ *             with RS_PACK_PRED (batched form, fits in the call): packed instead, row r's c_r
+ *             reported predictions at rec_pred[P_r .. P_r + c_r - 1], P_r = sum of c over the
+ *             rows before r (c from rec_code; the total is counter 4 when counters are
+ *             given), no NaN padding -- about 1.2 values per row instead of k
  *   pred_all  double [R][6]: every prediction (NaN where none), nullable
  *   counters  uint64 [16]: accuracy counters (listed above), added to; nullable
  * flags: RS_RANK_ALL; RS_REFINE_X (batched form, coef == NULL): every fit gets one step of

@@ -1170,7 +1170,11 @@ rank_pass_kernel(const RankPassArgs a) {
             }
         }
         const int64_t row = tile * kRankTile + tid;
-        if (row < nrows) rank_row(a, row, info, pred, c);
+        const int nrec = row < nrows ? rank_row(a, row, info, pred, c) : 0;
+        if (a.tile_sum) {                      // the tile's recommendations, for the packed output
+            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)nrec);
+            if ((tid & 31) == 0 && v) atomicAdd(a.tile_sum + tile, (unsigned long long)v);
+        }
     }
     if (failed) {                              // drain this block's copies still in flight
         if (tid == 0)
@@ -1191,6 +1195,74 @@ rank_pass_kernel(const RankPassArgs a) {
             if ((tid & 31) == 0 && v) atomicAdd(a.counters + slot[q], (unsigned long long)v);
         }
     }
+}
+
+// ====================================================================== packed predictions
+// RS_PACK_PRED: row r's c_r reported predictions go to rec_pred[P_r .. P_r + c_r - 1] with
+// P_r = sum of c over the rows before r.  The rank pass leaves each row's list in its plane
+// slots and the per-tile totals; tile_scan_kernel turns the totals into tile offsets (one
+// block: contiguous chunks per thread, then a block scan), pack_pred_kernel scans the counts
+// of each tile's rows (from rec_code) and writes the lists in place.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads)
+tile_scan_kernel(const unsigned long long* __restrict__ tile_sum, unsigned long long* __restrict__ tile_off,
+                 int64_t ntiles) {
+    __shared__ unsigned long long wsum[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t chunk = (ntiles + kScanThreads - 1) / kScanThreads;
+    const int64_t c0 = tid * chunk, c1 = c0 + chunk < ntiles ? c0 + chunk : ntiles;
+    unsigned long long s = 0;
+    for (int64_t t = c0; t < c1; ++t) s += tile_sum[t];
+    unsigned long long incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += v;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long off = incl - s + (warp > 0 ? wsum[warp - 1] : 0ull);
+    for (int64_t t = c0; t < c1; ++t) {
+        tile_off[t] = off;
+        off += tile_sum[t];
+    }
+}
+
+__global__ void __launch_bounds__(kRankTile)
+pack_pred_kernel(const int64_t* __restrict__ rec_offsets, int64_t S, int64_t R, const uint32_t* __restrict__ rec_code,
+                 const double* __restrict__ planes, int64_t PS, const unsigned long long* __restrict__ tile_off,
+                 double* __restrict__ out) {
+    __shared__ unsigned wsum[kRankTile / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t total = rec_offsets[S];
+    const int64_t nrows = total < R ? total : R;
+    const int64_t tile = blockIdx.x;
+    if (tile * kRankTile >= nrows) return;
+    const int64_t row = tile * kRankTile + tid;
+    const unsigned c = row < nrows ? (rec_code[row] & 0xFu) : 0u;
+    unsigned incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    unsigned before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const unsigned long long off = tile_off[tile] + before + (incl - c);
+    for (unsigned pos = 0; pos < c && pos < (unsigned)RS_NOPT; ++pos) out[off + pos] = planes[pos * PS + row];
 }
 
 // ====================================================================== predict / rank (chunked)
@@ -1539,6 +1611,8 @@ struct FitWs {
     uint8_t* status;     // [S*6]
     double* coef;        // compact records
     double* predbuf;     // [6][Rcap]
+    unsigned long long* tile_sum;   // [ceil(Rcap / 256)] recommendations per rank tile (packed output)
+    unsigned long long* tile_off;   // [ceil(Rcap / 256)] their exclusive scan
     size_t bytes;
 };
 
@@ -1576,6 +1650,9 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.status = (uint8_t*)take(S6);
     w.coef = (double*)take(S6 * (size_t)(nmax + 1) * sizeof(double));
     w.predbuf = (double*)take((size_t)RS_NOPT * plane_stride(Rcap) * sizeof(double));
+    const size_t ntiles = (size_t)((Rcap + kRankTile - 1) / kRankTile);
+    w.tile_sum = (unsigned long long*)take(ntiles * sizeof(unsigned long long));
+    w.tile_off = (unsigned long long*)take(ntiles * sizeof(unsigned long long));
     w.bytes = o;
     return w;
 }
@@ -1742,6 +1819,14 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         RankPassArgs ra{a.rec_offsets, a.S, w.predbuf, a.rows_cap, plane_stride(a.rows_cap), w.row_info,
                         a.dstatus, a.k, 0, a.flags, a.rec_code, a.rec_pred, a.pred_all, a.counters};
         ra.ktau = okey_host(a.log_tau);
+        const bool packed = (a.flags & RS_PACK_PRED) != 0 && a.rec_pred != nullptr;
+        const int64_t tiles_cap = (a.rows_cap + kRankTile - 1) / kRankTile;
+        if (packed) {
+            ra.pack_dst = w.predbuf;
+            ra.tile_sum = w.tile_sum;
+            e = cudaMemsetAsync(w.tile_sum, 0, (size_t)tiles_cap * sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return e;
+        }
         e = cudaFuncSetAttribute(rank_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -1755,6 +1840,16 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         if (blocks > tiles) blocks = tiles;
         if (blocks < 1) blocks = 1;
         rank_pass_kernel<<<(unsigned)blocks, kRankTile, kRankSmem, st>>>(ra);
+        if (packed && tiles_cap > 0) {
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            tile_scan_kernel<<<1, kScanThreads, 0, st>>>(w.tile_sum, w.tile_off, tiles_cap);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            pack_pred_kernel<<<(unsigned)tiles_cap, kRankTile, 0, st>>>(a.rec_offsets, a.S, a.rows_cap, a.rec_code,
+                                                                        w.predbuf, plane_stride(a.rows_cap),
+                                                                        w.tile_off, a.rec_pred);
+        }
     }
     mark(6);
     return cudaGetLastError();

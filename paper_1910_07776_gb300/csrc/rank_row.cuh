@@ -134,6 +134,11 @@ struct RankPassArgs {
     double* rec_pred;
     double* pred_all;
     unsigned long long* counters;
+    // packed predictions (RS_PACK_PRED): a row's chosen predictions go to its slots of the
+    // prediction planes (pack_dst[pos * PS + row], already read by then) and each tile's
+    // number of recommendations is added to tile_sum; a compaction pass writes rec_pred
+    double* pack_dst;
+    unsigned long long* tile_sum;
 };
 
 // Per-thread tallies of the scoring counters.
@@ -149,8 +154,8 @@ struct RankTally {
 // popcount of that set restricted to the candidates at or above the threshold.
 // info64: the row's scoring summary (row_summary) | version mask << 30 | mask of the
 // optimizations whose fit has no training pair << 36.
-__device__ __forceinline__ void rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
-                                         const double (&pred)[RS_NOPT], RankTally& c) {
+__device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
+                                        const double (&pred)[RS_NOPT], RankTally& c) {
     const uint32_t info = (uint32_t)info64;
     const int mt = (int)(info64 >> 30) & 63;
     const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
@@ -193,7 +198,11 @@ __device__ __forceinline__ void rank_row(const RankPassArgs& a, int64_t row, uns
     const int nrec = __popc(rk);
     code = (code & ~0xFu) | (uint32_t)nrec;
     a.rec_code[row] = code;
-    if (a.rec_pred) {                          // each chosen candidate writes its own slot
+    if (a.pack_dst) {                          // packed: park the list in the row's plane slots
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            if ((rk >> j) & 1) a.pack_dst[pos[j] * a.PS + row] = pred[j];
+    } else if (a.rec_pred) {                   // each chosen candidate writes its own slot
         double* o = a.rec_pred + row * a.k;
 #pragma unroll
         for (int j = 0; j < RS_NOPT; ++j)
@@ -230,6 +239,7 @@ __device__ __forceinline__ void rank_row(const RankPassArgs& a, int64_t row, uns
         c.t1 += 1;
         c.t1h += (bp == ba);
     }
+    return nrec;
 }
 
 // Insertion of (d, q) into the list of the kIbkK nearest, ordered by (distance, index):

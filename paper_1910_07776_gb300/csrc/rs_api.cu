@@ -341,7 +341,9 @@ rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const r
     }
     if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
-    if (flags & ~(RS_RANK_ALL | RS_REFINE_X | RS_MODEL_IBK)) return fail(c, RS_EINVAL, "unknown flag bits");
+    if (flags & ~(RS_RANK_ALL | RS_REFINE_X | RS_MODEL_IBK | RS_PACK_PRED)) return fail(c, RS_EINVAL, "unknown flag bits");
+    if ((flags & RS_PACK_PRED) && (form != RS_FORM_BATCHED || coef))
+        return fail(c, RS_EINVAL, "RS_PACK_PRED needs the batched form with the fits computed in the call (coef = NULL)");
     if ((flags & RS_MODEL_IBK) && (form != RS_FORM_BATCHED || coef || (flags & RS_REFINE_X)))
         return fail(c, RS_EINVAL, "RS_MODEL_IBK needs the batched form, coef = NULL and no RS_REFINE_X");
     if ((flags & RS_REFINE_X) && (form != RS_FORM_BATCHED || coef))

@@ -21,7 +21,7 @@ RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EUNSUPPORTED, RS_EDATA = 
 RS_F32, RS_F64 = 0, 1
 RS_GRAM_F64, RS_GRAM_BF16X3, RS_GRAM_DIST2 = 0, 1, 2
 RS_FORM_BATCHED, RS_FORM_PLAIN = 0, 1
-RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK, RS_MODEL_M5P = 1, 2, 4, 8
+RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK, RS_MODEL_M5P, RS_PACK_PRED = 1, 2, 4, 8, 16
 IBK_NEIGHBORS = 10
 NOPT = 6
 COEF_STRIDE = 33
