@@ -1110,6 +1110,7 @@ constexpr size_t kRankSmem = kRankStages * kRankStageBytes + kRankStages * 8;
 // is refilled with the tile three ahead, and the row is ranked while those copies fly.
 // Bounded waits: on a timeout RS_ETIMEOUT is set, the copies still in flight are waited
 // for (bounded) and the block returns.
+template <bool PACK>
 __global__ void __launch_bounds__(kRankTile, 2)
 rank_pass_kernel(const RankPassArgs a) {
     extern __shared__ __align__(128) unsigned char rsm[];
@@ -1170,10 +1171,12 @@ rank_pass_kernel(const RankPassArgs a) {
             }
         }
         const int64_t row = tile * kRankTile + tid;
-        const int nrec = row < nrows ? rank_row(a, row, info, pred, c) : 0;
-        if (a.tile_sum) {                      // the tile's recommendations, for the packed output
+        if constexpr (PACK) {                  // the tile's recommendations, for the packed output
+            const int nrec = row < nrows ? rank_row<true>(a, row, info, pred, c) : 0;
             const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)nrec);
             if ((tid & 31) == 0 && v) atomicAdd(a.tile_sum + tile, (unsigned long long)v);
+        } else {
+            if (row < nrows) rank_row(a, row, info, pred, c);
         }
     }
     if (failed) {                              // drain this block's copies still in flight
@@ -1827,10 +1830,11 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
             e = cudaMemsetAsync(w.tile_sum, 0, (size_t)tiles_cap * sizeof(unsigned long long), st);
             if (e != cudaSuccess) return e;
         }
-        e = cudaFuncSetAttribute(rank_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
+        auto rank_kern = packed ? rank_pass_kernel<true> : rank_pass_kernel<false>;
+        e = cudaFuncSetAttribute(rank_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_pass_kernel, kRankTile, kRankSmem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_kern, kRankTile, kRankSmem);
         if (e != cudaSuccess) return e;
         // persistent: tune_rank_waves (8, 16, 32) scales the resident blocks per SM by 1/4, 1/2, 1
         int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
@@ -1839,7 +1843,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         const int64_t tiles = (a.rows_cap + kRankTile - 1) / kRankTile;
         if (blocks > tiles) blocks = tiles;
         if (blocks < 1) blocks = 1;
-        rank_pass_kernel<<<(unsigned)blocks, kRankTile, kRankSmem, st>>>(ra);
+        rank_kern<<<(unsigned)blocks, kRankTile, kRankSmem, st>>>(ra);
         if (packed && tiles_cap > 0) {
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;

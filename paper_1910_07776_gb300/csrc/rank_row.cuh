@@ -154,6 +154,7 @@ struct RankTally {
 // popcount of that set restricted to the candidates at or above the threshold.
 // info64: the row's scoring summary (row_summary) | version mask << 30 | mask of the
 // optimizations whose fit has no training pair << 36.
+template <bool PACK = false>
 __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
                                         const double (&pred)[RS_NOPT], RankTally& c) {
     const uint32_t info = (uint32_t)info64;
@@ -198,7 +199,7 @@ __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsi
     const int nrec = __popc(rk);
     code = (code & ~0xFu) | (uint32_t)nrec;
     a.rec_code[row] = code;
-    if (a.pack_dst) {                          // packed: park the list in the row's plane slots
+    if constexpr (PACK) {                      // packed: park the list in the row's plane slots
 #pragma unroll
         for (int j = 0; j < RS_NOPT; ++j)
             if ((rk >> j) & 1) a.pack_dst[pos[j] * a.PS + row] = pred[j];
