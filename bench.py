@@ -931,6 +931,11 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
     copied = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     moved = [0]
+    # the step of each output set as one CUDA graph (rs_cv_graph_create, packed predictions)
+    for k_, v in host.items():
+        devb[k_].copy_(v, non_blocking=True)
+    graphs = [ctx.cv_graph(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=k, tau=CFG["tau"],
+                           flags=rs.RS_PACK_PRED, rec_pred=o.rec_pred, counters=o.counters) for o in outs]
 
     def step(i):
         b = i % 2
@@ -940,8 +945,7 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
         flush.fill_(1)
         stream.wait_event(copied[b])           # this output set's previous copy has landed
         o.counters.zero_()
-        ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=k, tau=CFG["tau"],
-                    flags=rs.RS_PACK_PRED, rec_pred=o.rec_pred, counters=o.counters)
+        graphs[b].launch()
         h_cnt[b].copy_(o.counters, non_blocking=True)
         computed[b].record(stream)
 
@@ -980,6 +984,8 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
     torch.cuda.synchronize()
     tot = e0.elapsed_time(e1)
     ctx.check_device_status()
+    for g in graphs:
+        g.close()
     d2h = moved[0] / n
     # the host link's own rates (one bulk copy each way of a step's output size), the bound of
     # this leg: a step cannot finish before its outputs have crossed the link
@@ -1002,8 +1008,9 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "host_link_gbs": {"d2h": d2h_gbs, "h2d": h2d_gbs},
             "copy_bound_ms_per_step": d2h / (d2h_gbs * 1e6) + h2d / (h2d_gbs * 1e6),
-            "path": "per step: pinned host -> device copies of the inputs, L2 flush, rs_cv_step with packed "
-                    "predictions (RS_PACK_PRED), device -> pinned host copies of rec_code, the packed "
+            "path": "per step: pinned host -> device copies of the inputs, L2 flush, the step as one CUDA-graph "
+                    "launch (rs_cv_graph_create with packed predictions, RS_PACK_PRED), device -> pinned "
+                    "host copies of rec_code, the packed "
                     "predictions and the counters on a second stream (outputs double-buffered: a step's "
                     "copies overlap the next step's compute)"}
 
