@@ -3,8 +3,10 @@
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  The CUDA library never loads it and shares no code with it.
 
-``build()`` compiles ``rs_oracle.c`` and ``rs_m5p.c`` (plain C, double precision, ``-ffp-contract=off`` so
-the host results are the same on x86-64 and AArch64) into ``oracle/_build``.  The Python
+``build()`` compiles ``rs_oracle.c`` and ``rs_m5p.c`` (plain C, double precision, ``-ffp-contract=off``
+so every operation rounds once, in source order) into ``oracle/_build``.  The C library's
+``log`` may still differ in the last ulp between machines (x86-64 and AArch64 do), so the
+reference is always run on the machine whose results it is compared with.  The Python
 functions below only marshal numpy arrays into the C functions; the MLP reference used
 for the surrogate lives in ``mlp.py`` (numpy, float64).
 """
