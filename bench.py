@@ -275,6 +275,9 @@ def main():
     ap.add_argument("--no-ibk", action="store_true")
     ap.add_argument("--no-transfer", action="store_true")
     ap.add_argument("--surrogate-epochs", type=int, default=2)
+    ap.add_argument("--profile-surrogate", action="store_true",
+                    help="a short surrogate run for profiler captures of its tensor-core GEMMs: 16 training "
+                         "steps of 8192 rows and one ranked inference of 131,072 rows (seeded random rows)")
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain form, e2e, CPU baseline or FMA peak); "
                          "used for profiler captures")
@@ -286,6 +289,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.profile_surrogate:
+        return profile_surrogate()
 
     import torch
     import torch.distributed as dist
@@ -757,6 +762,35 @@ def run_precision(rs, ctx, dev, stream, flush, args):
         ent["achieved_cond_train_system"] = float(np.linalg.cond(Kt))
         res["per_kappa"][f"{kappa:.0e}"] = ent
     return res
+
+
+def profile_surrogate():
+    """The surrogate's kernels on a small seeded case, for ncu captures (not a bench line)."""
+    import torch
+    from paper_1910_07776_gb300 import build as _b
+    _b.build()
+    from paper_1910_07776_gb300 import rs
+    from oracle import mlp
+    dev = torch.device("cuda", 0)
+    ctx = rs.Context(0, torch.cuda.current_stream(dev))
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    Xtr = torch.randn(65536, 256, device=dev, dtype=torch.float64, generator=g)
+    Ytr = 0.3 * torch.randn(65536, 6, device=dev, dtype=torch.float64, generator=g)
+    Xte = torch.randn(131072, 256, device=dev, dtype=torch.float64, generator=g)
+    masks = torch.randint(0, 64, (131072,), device=dev, dtype=torch.uint8, generator=g)
+    sur = rs.Surrogate(ctx, 8192, infer_chunk=131072)
+    sur.load(mlp.init_params(11))
+    sur.train(Xtr, Ytr, steps=16)
+    code = torch.empty(131072, dtype=torch.int32, device=dev)
+    rp = torch.empty(131072 * CFG["k"], dtype=torch.float64, device=dev)
+    sur.infer(Xte, ood_threshold=3.0, want_ood=True, masks=masks, k=CFG["k"], tau=CFG["tau"], rec_code=code,
+              rec_pred=rp, want_pred=False)
+    torch.cuda.synchronize()
+    ctx.check_device_status()
+    print(json.dumps({"profile": "surrogate", "train_rows": 65536, "train_steps": 16, "infer_rows": 131072}))
+    ctx.close()
+    return 0
 
 
 def run_surrogate(rs, ctx, dev, stream, flush, args):
