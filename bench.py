@@ -928,8 +928,8 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
     copies its inputs from pinned host memory, flushes L2, computes, and brings its
     recommendations back into pinned host memory -- rec_code and the reported predictions
     packed back to back (RS_PACK_PRED: ~1.2 values per row instead of k = 3, ~73 MB per step
-    instead of ~150) -- with the counters.  Outputs are double-buffered: step i's results are
-    copied back on a second stream while step i + 1 computes.  The timed region runs from the
+    instead of ~150) -- with the counters.  Inputs and outputs are double-buffered: step i + 1's
+    inputs arrive and step i - 1's results leave on two more streams while step i computes.  The timed region runs from the
     first step's input copy to the last step's results landing in host memory; ms_per_step is
     that time over the steps."""
     import torch
@@ -942,40 +942,58 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
                 masks=pin(batch.masks), log_time=pin(batch.log_time), cycles=pin(batch.cycles),
                 split_offsets=pin(splits.split_offsets.astype(np.int64)),
                 train_masks=pin(splits.train_masks.view(np.int64)))
-    devb = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    db = rs.DeviceBatch(n_programs=batch.n_programs, dtype=rs.RS_F32, n_rows=batch.n_rows,
-                        max_versions=64, max_feat=int(batch.feat_width.max()),
-                        x_elems=int(batch.X.shape[0]), feat_total=int(fo[-1]),
-                        row_offsets=devb["row_offsets"], feat_width=devb["feat_width"],
-                        x_offsets=devb["x_offsets"], feat_offsets=devb["feat_offsets"],
-                        X=devb["X"], masks=devb["masks"], log_time=devb["log_time"],
-                        cycles=devb["cycles"])
-    ds = rs.DeviceSplits(n_splits=splits.n_splits, max_train=int(CFG["versions"][1]) // 2 + 1,
-                         split_offsets=devb["split_offsets"], train_masks=devb["train_masks"],
-                         n_test_rows=R)
-    ws = torch.empty(ctx.cv_workspace_bytes(db, ds), dtype=torch.uint8, device=dev)
+    # inputs and outputs double-buffered: set b serves steps b, b + 2, ...
+    devbs = [{k: torch.empty_like(v, device=dev) for k, v in host.items()} for _ in range(2)]
+
+    def views(devb):
+        db = rs.DeviceBatch(n_programs=batch.n_programs, dtype=rs.RS_F32, n_rows=batch.n_rows,
+                            max_versions=64, max_feat=int(batch.feat_width.max()),
+                            x_elems=int(batch.X.shape[0]), feat_total=int(fo[-1]),
+                            row_offsets=devb["row_offsets"], feat_width=devb["feat_width"],
+                            x_offsets=devb["x_offsets"], feat_offsets=devb["feat_offsets"],
+                            X=devb["X"], masks=devb["masks"], log_time=devb["log_time"],
+                            cycles=devb["cycles"])
+        ds = rs.DeviceSplits(n_splits=splits.n_splits, max_train=int(CFG["versions"][1]) // 2 + 1,
+                             split_offsets=devb["split_offsets"], train_masks=devb["train_masks"],
+                             n_test_rows=R)
+        return db, ds
+
+    vw = [views(d) for d in devbs]
+    ws = torch.empty(ctx.cv_workspace_bytes(*vw[0]), dtype=torch.uint8, device=dev)
     k = CFG["k"]
-    outs = [rs.alloc_outputs(R, ds.n_splits, k, dev, pred_all=False) for _ in range(2)]
+    outs = [rs.alloc_outputs(R, splits.n_splits, k, dev, pred_all=False) for _ in range(2)]
     h_code = [torch.empty(R, dtype=torch.int32).pin_memory() for _ in range(2)]
     h_pred = [torch.empty(R * k, dtype=torch.float64).pin_memory() for _ in range(2)]
     h_cnt = [torch.empty(16, dtype=torch.int64).pin_memory() for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    cs = torch.cuda.Stream(dev)
+    cs = torch.cuda.Stream(dev)                # device -> host copies
+    ins = torch.cuda.Stream(dev)               # host -> device copies of the next step's inputs
     computed = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
+    loaded = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     moved = [0]
-    # the step of each output set as one CUDA graph (rs_cv_graph_create, packed predictions)
-    for k_, v in host.items():
-        devb[k_].copy_(v, non_blocking=True)
-    graphs = [ctx.cv_graph(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=k, tau=CFG["tau"],
-                           flags=rs.RS_PACK_PRED, rec_pred=o.rec_pred, counters=o.counters) for o in outs]
+    # the step of each buffer set as one CUDA graph (rs_cv_graph_create, packed predictions)
+    for devb in devbs:
+        for k_, v in host.items():
+            devb[k_].copy_(v, non_blocking=True)
+    graphs = [ctx.cv_graph(vw[b][0], vw[b][1], ws, outs[b].rec_offsets, outs[b].rec_code, lam=CFG["lam"], k=k,
+                           tau=CFG["tau"], flags=rs.RS_PACK_PRED, rec_pred=outs[b].rec_pred,
+                           counters=outs[b].counters) for b in range(2)]
+
+    def load(i):
+        # step i's inputs, on their own stream once step i - 2 (the same set) has computed
+        b = i % 2
+        ins.wait_event(computed[b])
+        with torch.cuda.stream(ins):
+            for k_, v in host.items():
+                devbs[b][k_].copy_(v, non_blocking=True)
+        loaded[b].record(ins)
 
     def step(i):
         b = i % 2
         o = outs[b]
-        for k_, v in host.items():
-            devb[k_].copy_(v, non_blocking=True)
+        stream.wait_event(loaded[b])
         flush.fill_(1)
         stream.wait_event(copied[b])           # this output set's previous copy has landed
         o.counters.zero_()
@@ -998,7 +1016,11 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
         moved[0] += R * 4 + total * 8 + 16 * 8
 
     def run(n_steps):
+        ins.wait_stream(stream)                # the first input copy starts inside the region
+        load(0)
         for i in range(n_steps):
+            if i + 1 < n_steps:
+                load(i + 1)                    # beside step i's compute
             step(i)
             if i > 0:
                 bring_back(i - 1)
@@ -1006,6 +1028,7 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
 
     for b in range(2):
         copied[b].record(cs)
+        computed[b].record(stream)
     run(3)
     torch.cuda.synchronize()
     moved[0] = 0
@@ -1042,8 +1065,9 @@ def run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "host_link_gbs": {"d2h": d2h_gbs, "h2d": h2d_gbs},
             "copy_bound_ms_per_step": d2h / (d2h_gbs * 1e6) + h2d / (h2d_gbs * 1e6),
-            "path": "per step: pinned host -> device copies of the inputs, L2 flush, the step as one CUDA-graph "
-                    "launch (rs_cv_graph_create with packed predictions, RS_PACK_PRED), device -> pinned "
+            "path": "per step: pinned host -> device copies of the inputs (on a third stream, beside the "
+                    "previous step's compute), L2 flush, the step as one CUDA-graph launch "
+                    "(rs_cv_graph_create with packed predictions, RS_PACK_PRED), device -> pinned "
                     "host copies of rec_code, the packed "
                     "predictions and the counters on a second stream (outputs double-buffered: a step's "
                     "copies overlap the next step's compute)"}
