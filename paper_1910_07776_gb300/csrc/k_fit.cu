@@ -38,6 +38,15 @@ constexpr int kKld = RS_MAXV + 1;           // padded row stride of K in shared 
 constexpr int kNReg = 10;                   // largest n solved by one thread in registers
 constexpr int kNMid = 16;                   // largest n solved by one thread from shared memory
 constexpr int kHist = RS_MAXPAIRS + 2;      // n = 0..32, plus one end slot
+// Within the fits of one n, the bucket order is by the number of predictions c (0..64) the
+// fit makes, inside each block's share of 4096 fits: a warp's 32 fits then mostly run
+// prediction loops of one length.  Sort key n * kCntBins + c.
+constexpr int kCntBins = RS_MAXV + 1;
+constexpr int kKeys = (RS_MAXPAIRS + 1) * kCntBins;
+constexpr int kBucketThreads = 512;
+constexpr int kBucketPer = 8;                // fits per thread of the bucket kernel
+static_assert(3 * 32 >= kCntBins, "a warp scans one n's counts three per lane");
+static_assert(kBucketThreads / 32 * 2 >= RS_MAXPAIRS, "the bucket kernel's warps take two n each");
 __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
 
 // The a-th set bit (0-based) of x; x must have more than a set bits.
@@ -112,17 +121,19 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
 
 // ====================================================================== plan
 // One thread per split: the six pair masks of its fits (the pair loops run over one
-// program's pair tables, uniform across a warp whose splits share the program), the
-// histogram of fit sizes (warp-aggregated), and the split's row records in slot order:
+// program's pair tables, uniform across a warp whose splits share the program), their sort
+// keys n * kCntBins + c (c = the predictions the fit makes when predictions are wanted, else
+// 0), the histogram of fit sizes (warp-aggregated), and the split's row records in slot order:
 // the row's scoring summary | version mask << 30 | mask of the split's empty fits << 36.
 __global__ void __launch_bounds__(256)
 plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __restrict__ split_off,
                  const uint64_t* __restrict__ tm, int64_t S, const uint8_t* __restrict__ pb,
                  const uint8_t* __restrict__ pa, const int* __restrict__ npair, uint32_t* fit_pm,
-                 uint8_t* fit_n, unsigned* hist, int nmax, int* split_prog,
+                 uint16_t* fit_key, unsigned* hist, int nmax, int* split_prog,
                  const int64_t* __restrict__ rec_offsets, int64_t rows_cap,
                  unsigned long long* row_info, const uint8_t* __restrict__ masks,
-                 const uint32_t* __restrict__ rowinfo, int* dstatus) {
+                 const uint32_t* __restrict__ rowinfo, const uint64_t* __restrict__ cand, int cand_all,
+                 int count_preds, int* dstatus) {
     __shared__ unsigned h[kHist];
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
     __syncthreads();
@@ -132,7 +143,8 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         const int V = (int)(row_off[p + 1] - row_off[p]);
         const bool okV = V >= 1 && V <= RS_MAXV;
         split_prog[s] = p;
-        const uint64_t T = okV ? tm[s] & rs_full_mask(V) : 0ull;
+        const uint64_t full = okV ? rs_full_mask(V) : 0ull;
+        const uint64_t T = tm[s] & full;
         int emptym = 0;
         // the program's pair tables (32 before / 32 after slots per optimization) come in as
         // 16-byte vectors, all issued before the first is used
@@ -174,8 +186,12 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                 pm = 0;
                 n = 0;
             }
+            // c = the predictions the fit makes: its split's test rows that are candidates
+            int c = 0;
+            if (count_preds && n > 0) c = __popcll(~T & full & (cand_all ? full : __ldg(cand + p * RS_NOPT + j)));
+            const int key = n * kCntBins + c;
             fit_pm[s * RS_NOPT + j] = pm;
-            fit_n[s * RS_NOPT + j] = (uint8_t)n;
+            fit_key[s * RS_NOPT + j] = (uint16_t)key;
             emptym |= (n == 0) << j;
             const unsigned grp = __match_any_sync(__activemask(), n);
             if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&h[n], (unsigned)__popc(grp));
@@ -373,7 +389,7 @@ struct SolveArgs {
     const uint8_t* pb;
     const double* ylab;
     const uint32_t* fit_pm;
-    const uint8_t* fit_n;
+    const uint16_t* fit_key;
     const uint4* recs;    // [S*6] in bucket order: fit index, program, pair mask, versions
     const unsigned* hist;
     const int64_t* fit_off;
@@ -434,43 +450,81 @@ __device__ __forceinline__ double* coef_out(const SolveArgs& a, int64_t f) {
 }
 
 // ====================================================================== bucket
-// Counting sort of the fits by n.  Each block counts its fits per n in shared memory,
-// reserves one range per n with a single global atomic, and places its fits inside it.
-// Counting sort of the fits by n: each block counts its fits per n in shared memory,
-// reserves one range per n with a single global atomic, and places its fits' records inside
-// it (fit index, program, pair mask, version count: what a solver needs first).
+// Counting sort of the fits by n, and by c inside each block's share: a block of 4096 fits
+// counts them per (n, c) in shared memory, reserves one range per n with a single global
+// atomic, and places its fits' records inside it in ascending c (fit index, program, pair
+// mask, version count: what a solver needs first).  The order inside a bucket is immaterial
+// to the results: every result goes to its fit's own place.
 // A fit without a training pair (n = 0) is finished here (status RS_FIT_EMPTY); the rank
 // pass knows it from the row records.
-__global__ void __launch_bounds__(256)
-bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned* __restrict__ hist,
+__global__ void __launch_bounds__(kBucketThreads)
+bucket_fits_kernel(int64_t S6, const uint16_t* __restrict__ fit_key, const unsigned* __restrict__ hist,
                    unsigned* cursor, uint4* recs, int64_t* fit_off, uint8_t* status, double* coef_user,
                    unsigned long long* counters, const uint32_t* __restrict__ fit_pm,
                    const int* __restrict__ split_prog, const int64_t* __restrict__ row_off) {
     __shared__ long long start[kHist], cstart[kHist];
-    __shared__ unsigned lcount[kHist], lbase[kHist];
-    if (threadIdx.x < kHist) lcount[threadIdx.x] = 0;
-    bucket_tables(hist, start, cstart);
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = f < S6 ? fit_n[f] : 0;
-    unsigned local = 0;
-    if (f < S6 && n > 0) local = atomicAdd(&lcount[n], 1u);
+    __shared__ unsigned lcount[kKeys];       // fits per (n, c); then their offsets inside n's range
+    __shared__ unsigned lbase[kHist];
+    for (int i = threadIdx.x; i < kKeys; i += kBucketThreads) lcount[i] = 0;
+    bucket_tables(hist, start, cstart);      // (ends with a barrier)
+    const int64_t f0 = (int64_t)blockIdx.x * (kBucketThreads * kBucketPer) + threadIdx.x;
+    int key[kBucketPer];
+    unsigned local[kBucketPer];
+#pragma unroll
+    for (int q = 0; q < kBucketPer; ++q) {
+        const int64_t f = f0 + (int64_t)q * kBucketThreads;
+        key[q] = f < S6 ? fit_key[f] : 0;
+        local[q] = key[q] >= kCntBins ? atomicAdd(&lcount[key[q]], 1u) : 0u;
+    }
     __syncthreads();
-    if (threadIdx.x < kHist && lcount[threadIdx.x])
-        lbase[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], lcount[threadIdx.x]);
+    // warp w scans the counts of n = w + 1 and n = w + 17: exclusive offsets over c, and the
+    // block's range of that n
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int n = warp + 1; n <= RS_MAXPAIRS; n += kBucketThreads / 32) {
+        unsigned* row = lcount + n * kCntBins;
+        unsigned v[3], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int c = 3 * lane + i;
+            v[i] = c < kCntBins ? row[c] : 0u;
+            sum += v[i];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        unsigned run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int c = 3 * lane + i;
+            if (c < kCntBins) {
+                row[c] = run;
+                run += v[i];
+            }
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane == 0) lbase[n] = total ? atomicAdd(&cursor[n], total) : 0u;
+    }
     __syncthreads();
     unsigned empty = 0;
-    if (f < S6) {
+#pragma unroll
+    for (int q = 0; q < kBucketPer; ++q) {
+        const int64_t f = f0 + (int64_t)q * kBucketThreads;
+        if (f >= S6) break;
+        const int n = key[q] / kCntBins;
         if (n == 0) {
             if (fit_off) fit_off[f] = -1;
             status[f] = RS_FIT_EMPTY;
-            empty = 1;
+            ++empty;
             if (coef_user) {
                 double* o = coef_user + f * RS_COEF_STRIDE;
                 o[0] = nan_d();
                 for (int e = 1; e < RS_COEF_STRIDE; ++e) o[e] = 0.0;
             }
         } else {
-            const long long pos = start[n] + lbase[n] + local;
+            const long long pos = start[n] + lbase[n] + lcount[key[q]] + local[q];
             // the solver's whole first round trip in one 16-byte record
             const int p = split_prog[f / RS_NOPT];
             recs[pos] = make_uint4((unsigned)f, (unsigned)p, fit_pm[f], (unsigned)(row_off[p + 1] - row_off[p]));
@@ -479,7 +533,7 @@ bucket_fits_kernel(int64_t S6, const uint8_t* __restrict__ fit_n, const unsigned
     }
     if (counters) {
         const unsigned e = __reduce_add_sync(0xffffffffu, empty);
-        if ((threadIdx.x & 31) == 0 && e) atomicAdd(counters + 10, (unsigned long long)e);
+        if (lane == 0 && e) atomicAdd(counters + 10, (unsigned long long)e);
     }
 }
 
@@ -1595,7 +1649,7 @@ cudaError_t launch_rank(const rs_fit_args& a, const int64_t* coef_off, const uin
 
 // Workspace carve-up for the batched form.
 struct FitWs {
-    unsigned* hist;      // [kHist]
+    unsigned* hist;      // [kHist] fits per n
     unsigned* cursor;    // [kHist]
     unsigned long long* work;   // [4] work counters of the solve kernels
     uint8_t* pb;         // [P][6][32]
@@ -1608,7 +1662,7 @@ struct FitWs {
     unsigned long long* row_info;   // [Rcap] scoring summary | mask << 30
     int* split_prog;     // [S]
     uint32_t* fit_pm;    // [S*6]
-    uint8_t* fit_n;      // [S*6]
+    uint16_t* fit_key;   // [S*6] n * kCntBins + c
     uint4* recs;         // [S*6] fit records in bucket order
     int64_t* fit_off;    // [S*6]
     uint8_t* status;     // [S*6]
@@ -1647,7 +1701,7 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.row_info = (unsigned long long*)take((size_t)Rcap * sizeof(unsigned long long));
     w.split_prog = (int*)take(S * sizeof(int));
     w.fit_pm = (uint32_t*)take(S6 * sizeof(uint32_t));
-    w.fit_n = (uint8_t*)take(S6);
+    w.fit_key = (uint16_t*)take(S6 * sizeof(uint16_t));
     w.recs = (uint4*)take(S6 * sizeof(uint4));
     w.fit_off = (int64_t*)take(S6 * sizeof(int64_t));
     w.status = (uint8_t*)take(S6);
@@ -1722,18 +1776,19 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
                                      w.npair, w.cand, w.rowinfo, a.K, a.lambda, w.dlam, a.dstatus);
     mark(1);
-    const unsigned blocks256 = (unsigned)((S6 + 255) / 256);
+    const unsigned bucket_blocks = (unsigned)((S6 + kBucketThreads * kBucketPer - 1) / (kBucketThreads * kBucketPer));
     plan_fits_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
-                                                a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_n, w.hist,
+                                                a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_key, w.hist,
                                                 nmax, w.split_prog, a.rec_offsets,
                                                 a.rec_code ? a.rows_cap : 0,
                                                 a.rec_code ? w.row_info : nullptr,
-                                                a.masks, w.rowinfo, a.dstatus);
+                                                a.masks, w.rowinfo, w.cand, (a.flags & RS_RANK_ALL) ? 1 : 0,
+                                                a.rec_code ? 1 : 0, a.dstatus);
     mark(2);
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
     const bool rank = a.rec_code != nullptr;
-    SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_n, w.recs, w.hist,
+    SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_key, w.recs, w.hist,
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
@@ -1741,7 +1796,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                  a.feat_width, a.max_feat, a.tune_order};
     // compact records (and their offsets) only for fits without predictions or caller array
     const bool need_off = !user && !rank;
-    bucket_fits_kernel<<<blocks256, 256, 0, st>>>(S6, w.fit_n, w.hist, w.cursor, w.recs,
+    bucket_fits_kernel<<<bucket_blocks, kBucketThreads, 0, st>>>(S6, w.fit_key, w.hist, w.cursor, w.recs,
                                                   need_off ? w.fit_off : nullptr,
                                                   status, user ? a.coef_out : nullptr, a.counters,
                                                   w.fit_pm, w.split_prog, a.row_offsets);
