@@ -406,6 +406,8 @@ def main():
         "fit_predict_path": {"ms": fit_ms, "fp64_flops": path_flops,
                              "frac_fp64": path_flops / (fit_ms * 1e-3) / 1e12 / fp64_peak}}
 
+    ctx.profile_enable(False)                  # (stage events only for the step above)
+
     # plain GPU form: one launch per step per program, FP64, one warp per fit, no persistence
     plain = None
     if not args.no_plain and not args.only_step and rank == 0:
@@ -414,7 +416,6 @@ def main():
     # end to end through the C ABI single call with host buffers (pinned), copies timed
     e2e = None if args.only_step else run_e2e(rs, ctx, batch, splits, dev, stream, flush, args, R)
 
-    ctx.profile_enable(False)
     ibk = None
     if rank == 0 and not args.only_step and not args.no_ibk:
         ibk = run_ibk(rs, ctx, batch, splits, dev, stream, flush, args)
