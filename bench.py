@@ -135,6 +135,14 @@ def algorithmic_work(batch, splits, k=3, nreg=10):
             out["solve_large"] += float(np.sum(fl * (n > nreg)))
             out["preds"] += int(np.sum(cnt * (n > 0)))
     out["rank_bytes"] = float(out["rows"] * (1 + 4 + 4 + 8 * k) + 8 * out["preds"])
+    # the other stages' minimum work: the standardization reads X and writes Z (FP64); the
+    # Gram's upper triangle is V (V + 1) / 2 dot products of F features (2 flops each); the
+    # row planning reads each split's train mask once
+    V = np.diff(batch.row_offsets).astype(np.float64)
+    F = batch.feat_width.astype(np.float64)
+    out["std_bytes"] = float(np.sum(V * F) * (batch.X.dtype.itemsize + 8))
+    out["gram_flops"] = float(np.sum(V * (V + 1) / 2 * F * 2))
+    out["mask_bytes"] = float(len(splits.train_masks) * 8)
     return out
 
 
@@ -405,6 +413,17 @@ def main():
                  "frac_hbm": work["rank_bytes"] / (stage_ms["rank"] * 1e-3) / 1e9 / hbm_peak},
         "fit_predict_path": {"ms": fit_ms, "fp64_flops": path_flops,
                              "frac_fp64": path_flops / (fit_ms * 1e-3) / 1e12 / fp64_peak}}
+    # the whole step against the sum of its stages' roofline times (HBM bytes at the measured
+    # copy bandwidth, FP64 flops at the FP64 peak), on the executed (dual) form
+    bounds = {"standardize": work["std_bytes"] / (hbm_peak * 1e6),
+              "gram": work["gram_flops"] / (fp64_peak * 1e9),
+              "plan": work["mask_bytes"] / (hbm_peak * 1e6),
+              "solve": work["solve_group"] / (fp64_peak * 1e9),
+              "rank": work["rank_bytes"] / (hbm_peak * 1e6)}
+    roof["stages"]["step"] = {"ms": ms_step, "bound_ms": sum(bounds.values()),
+                              "frac": sum(bounds.values()) / ms_step,
+                              "bound_ms_parts": bounds,
+                              "note": "sum of the stages' roofline times / measured step time"}
 
     ctx.profile_enable(False)                  # (stage events only for the step above)
 
