@@ -60,12 +60,11 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
 // the before slot, and their labels.  Tables: [P][6][32] (u8, u8, double), counts [P][6].
 // Also, per program: cand[p][j] = slots whose mask lacks j (uint64), and for every slot t a
 // summary of the actual log speedups of adding each j (Sec. 5: the measured speedup of the
-// pair, used only for scoring).
+// pair, used only for scoring).  Needs no Gram block: it may run beside the Gram.
 __global__ void __launch_bounds__(64)
 pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restrict__ masks,
              const double* __restrict__ log_time, uint8_t* pb, uint8_t* pa, double* ylab,
-             int* npair, uint64_t* cand, uint32_t* rowinfo, const double* __restrict__ K,
-             double lambda, double* dlam, int* dstatus) {
+             int* npair, uint64_t* cand, uint32_t* rowinfo, int* dstatus) {
     __shared__ int8_t slot_of[RS_MAXV];
     __shared__ uint8_t msk[RS_MAXV];
     __shared__ double lt[RS_MAXV];
@@ -111,12 +110,16 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
         npair[p * RS_NOPT + j] = np;
         cand[p * RS_NOPT + j] = cm;
     }
-    {
-        const int t = tid;
-        rowinfo[(int64_t)p * RS_MAXV + t] = row_summary(t, V, msk, lt, slot_of);
-        if (t < V) dlam[(int64_t)p * RS_MAXV + t] =
-            K[(int64_t)p * RS_GRAM_LD * RS_GRAM_LD + t * RS_GRAM_LD + t] + lambda;
-    }
+    rowinfo[(int64_t)p * RS_MAXV + tid] = row_summary(tid, V, msk, lt, slot_of);
+}
+
+// dlam[p][t] = K_p[t][t] + lambda, the diagonal the solvers factor (one block per program).
+__global__ void __launch_bounds__(64)
+dlam_kernel(const int64_t* __restrict__ row_off, const double* __restrict__ K, double lambda, double* dlam) {
+    const int p = blockIdx.x, t = threadIdx.x;
+    const int V = (int)(row_off[p + 1] - row_off[p]);
+    if (V >= 1 && V <= RS_MAXV && t < V)
+        dlam[(int64_t)p * RS_MAXV + t] = K[(int64_t)p * RS_GRAM_LD * RS_GRAM_LD + t * RS_GRAM_LD + t] + lambda;
 }
 
 // ====================================================================== plan
@@ -1770,37 +1773,44 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
     if (w.bytes > a.workspace_bytes) return cudaErrorInvalidValue;
     const int64_t S6 = a.S * RS_NOPT;
     auto mark = [&](int i) { if (a.ev) cudaEventRecord(a.ev[i], st); };
-    cudaError_t e = cudaMemsetAsync(w.hist, 0, kCounterBytes, st);
-    if (e != cudaSuccess) return e;
-    mark(0);
-    pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
-                                     w.npair, w.cand, w.rowinfo, a.K, a.lambda, w.dlam, a.dstatus);
-    mark(1);
+    const bool plan = a.phase != 2, solve = a.phase != 1;
+    cudaError_t e = cudaSuccess;
     const unsigned bucket_blocks = (unsigned)((S6 + kBucketThreads * kBucketPer - 1) / (kBucketThreads * kBucketPer));
-    plan_fits_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
-                                                a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_key, w.hist,
-                                                nmax, w.split_prog, a.rec_offsets,
-                                                a.rec_code ? a.rows_cap : 0,
-                                                a.rec_code ? w.row_info : nullptr,
-                                                a.masks, w.rowinfo, w.cand, (a.flags & RS_RANK_ALL) ? 1 : 0,
-                                                a.rec_code ? 1 : 0, a.dstatus);
-    mark(2);
     const bool user = a.coef_out != nullptr;
     uint8_t* status = a.status_out ? a.status_out : w.status;
     const bool rank = a.rec_code != nullptr;
+    // compact records (and their offsets) only for fits without predictions or caller array
+    const bool need_off = !user && !rank;
+    if (plan) {
+        e = cudaMemsetAsync(w.hist, 0, kCounterBytes, st);
+        if (e != cudaSuccess) return e;
+        mark(0);
+        pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
+                                         w.npair, w.cand, w.rowinfo, a.dstatus);
+        mark(1);
+        plan_fits_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
+                                                    a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_key, w.hist,
+                                                    nmax, w.split_prog, a.rec_offsets,
+                                                    a.rec_code ? a.rows_cap : 0,
+                                                    a.rec_code ? w.row_info : nullptr,
+                                                    a.masks, w.rowinfo, w.cand, (a.flags & RS_RANK_ALL) ? 1 : 0,
+                                                    a.rec_code ? 1 : 0, a.dstatus);
+        mark(2);
+        bucket_fits_kernel<<<bucket_blocks, kBucketThreads, 0, st>>>(S6, w.fit_key, w.hist, w.cursor, w.recs,
+                                                      need_off ? w.fit_off : nullptr,
+                                                      status, user ? a.coef_out : nullptr, a.counters,
+                                                      w.fit_pm, w.split_prog, a.row_offsets);
+        mark(3);
+    }
+    if (!solve) return cudaGetLastError();
+    dlam_kernel<<<a.P, 64, 0, st>>>(a.row_offsets, a.K, a.lambda, w.dlam);
+    if (!plan) mark(3);                        // the solvers start here, on this stream
     SolveArgs sa{a.P, a.split_offsets, w.split_prog, a.K, w.pb, w.ylab, w.fit_pm, w.fit_key, w.recs, w.hist,
                  w.fit_off, user ? a.coef_out : w.coef, user ? 1 : 0, status, a.lambda, w.dlam,
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
                  a.rows_cap, plane_stride(a.rows_cap), a.flags, a.dstatus, a.Z, a.x_offsets,
                  a.feat_width, a.max_feat, a.tune_order};
-    // compact records (and their offsets) only for fits without predictions or caller array
-    const bool need_off = !user && !rank;
-    bucket_fits_kernel<<<bucket_blocks, kBucketThreads, 0, st>>>(S6, w.fit_key, w.hist, w.cursor, w.recs,
-                                                  need_off ? w.fit_off : nullptr,
-                                                  status, user ? a.coef_out : nullptr, a.counters,
-                                                  w.fit_pm, w.split_prog, a.row_offsets);
-    mark(3);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -326,13 +326,12 @@ rs_status rs_fit_batched(rs_ctx* c, const rs_batch* b, const double* K, const rs
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_fit_batched");
 }
 
-rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
-                          double lambda, const double* coef, int k, double tau, int flags,
-                          int form, void* workspace, size_t workspace_bytes,
-                          const int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
-                          double* pred_all, uint64_t* counters) {
-    if (!c) return RS_EINVAL;
-    rs_fit_args a;
+// The checks and arguments of rs_predict_rank (no launch).
+static rs_status predict_args(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
+                              double lambda, const double* coef, int k, double tau, int flags,
+                              int form, void* workspace, size_t workspace_bytes,
+                              const int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
+                              double* pred_all, uint64_t* counters, rs_fit_args& a) {
     rs_status s = fit_common(c, b, K, sp, lambda, form, a);
     if (s != RS_OK) return s;
     if (form == RS_FORM_BATCHED && !coef) {
@@ -359,6 +358,19 @@ rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const r
     a.rec_pred = rec_pred;
     a.pred_all = pred_all;
     a.counters = (unsigned long long*)counters;
+    return RS_OK;
+}
+
+rs_status rs_predict_rank(rs_ctx* c, const rs_batch* b, const double* K, const rs_splits* sp,
+                          double lambda, const double* coef, int k, double tau, int flags,
+                          int form, void* workspace, size_t workspace_bytes,
+                          const int64_t* rec_offsets, uint32_t* rec_code, double* rec_pred,
+                          double* pred_all, uint64_t* counters) {
+    if (!c) return RS_EINVAL;
+    rs_fit_args a;
+    rs_status s = predict_args(c, b, K, sp, lambda, coef, k, tau, flags, form, workspace, workspace_bytes,
+                               rec_offsets, rec_code, rec_pred, pred_all, counters, a);
+    if (s != RS_OK) return s;
     cudaSetDevice(c->device);
     cudaError_t e = rs_launch_fit_predict(a, c->stream);
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_predict_rank");
@@ -457,8 +469,7 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
     const size_t kbytes = align256((size_t)b->n_programs * RS_GRAM_LD * RS_GRAM_LD * sizeof(double));
     double* K = (double*)((char*)ws + zbytes);
     void* fws = (char*)ws + zbytes + kbytes;
-    s = rs_standardize(c, b, Z, nullptr, nullptr);
-    if (s != RS_OK) return s;
+    const size_t fbytes = ws_bytes - zbytes - kbytes;
     rs_batch zb = *b;
     zb.X = Z;
     zb.dtype = RS_F64;
@@ -467,13 +478,42 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
             return fail(c, RS_EINVAL, "RS_MODEL_IBK takes precision RS_GRAM_F64 or RS_GRAM_DIST2");
         precision = RS_GRAM_DIST2;
     }
-    s = rs_gram(c, &zb, precision, K, fws, ws_bytes - zbytes - kbytes);
+    if (precision != RS_GRAM_F64 && precision != RS_GRAM_DIST2 && precision != RS_GRAM_BF16X3)
+        return fail(c, RS_EINVAL, "unknown precision %d", precision);
+    if (!rec_offsets) return fail(c, RS_EINVAL, "rec_offsets is NULL");
+    rs_fit_args a;
+    s = predict_args(c, &zb, K, sp, lambda, nullptr, k, tau, flags, RS_FORM_BATCHED, fws, fbytes,
+                     rec_offsets, rec_code, rec_pred, pred_all, counters, a);
     if (s != RS_OK) return s;
-    s = rs_rec_offsets(c, &zb, sp, rec_offsets);
+    cudaSetDevice(c->device);
+    // The planning (row offsets, pair tables, fit plan, bucketing) reads only masks, times and
+    // splits: on the side stream it runs beside the standardization and the Gram, and the
+    // solvers wait for both.  (Not with the tensor-core Gram, whose scratch is the fit
+    // workspace the planning fills.)
+    const bool overlap = c->side && c->fork && c->join && precision != RS_GRAM_BF16X3;
+    cudaStream_t ps = overlap ? c->side : c->stream;
+    cudaError_t e = cudaSuccess;
+    if (overlap) {
+        e = cudaEventRecord(c->fork, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+    }
+    if (e == cudaSuccess) e = rs_launch_rec_offsets(&zb, sp, rec_offsets, c->scan, c->dstatus, ps);
+    if (e == cudaSuccess) {
+        a.phase = 1;
+        e = rs_launch_fit_predict(a, ps);
+    }
+    if (overlap && e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_cv_step (planning)");
+    s = rs_standardize(c, b, Z, nullptr, nullptr);
+    if (s == RS_OK) s = rs_gram(c, &zb, precision, K, fws, fbytes);
+    if (overlap) {                              // joined whatever happened above
+        e = cudaStreamWaitEvent(c->stream, c->join, 0);
+        if (e != cudaSuccess && s == RS_OK) return cuda_fail(c, e, "rs_cv_step (join)");
+    }
     if (s != RS_OK) return s;
-    return rs_predict_rank(c, &zb, K, sp, lambda, nullptr, k, tau, flags, RS_FORM_BATCHED, fws,
-                           ws_bytes - zbytes - kbytes, rec_offsets, rec_code, rec_pred, pred_all,
-                           counters);
+    a.phase = 2;
+    e = rs_launch_fit_predict(a, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_cv_step");
 }
 
 

@@ -125,6 +125,10 @@ struct rs_fit_args {
     // `side` beside the others (all three NULL: everything on the call's stream)
     cudaStream_t side;
     cudaEvent_t fork, join;
+    // batched form: 0 the whole call; 1 only the planning (pairs, plan, bucket: no K read);
+    // 2 only what follows it (K's diagonal, solvers, rank pass), after a phase-1 call with
+    // the same arguments and workspace
+    int phase;
 };
 #define RS_NSTAGE_EVENTS 7   // before pairs, after pairs / plan / bucket / solve / solve-large / rank
 size_t rs_fit_workspace_bytes_impl(int64_t P, int64_t S, int max_train, int64_t rows_cap);
