@@ -29,8 +29,8 @@ METRIC = "ranked recommendations/sec (CV-split fits+predicts) vs plain GPU form 
 UNIT = "recommendations/s"
 WORKLOAD = "batched_cv: 64 programs x U{16..64} versions x 256 f32 features, 4096 half splits/program"
 # kernels of one step: standardize, Gram, row planning (count, block sums, finish), pairs,
-# plan, bucket, three solvers, rank pass
-LAUNCHES_PER_STEP = 12
+# plan, bucket, the Gram diagonal + lambda, three solvers, rank pass
+LAUNCHES_PER_STEP = 13
 CFG = dict(programs=64, versions=(16, 64), feat=256, splits=4096, lam=1e-3, k=3, tau=1.05, seed=0)
 FP64_PEAK_NOMINAL_GFLOPS = 152 * 4 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 
