@@ -486,31 +486,34 @@ rs_status rs_cv_step(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double l
                      rec_offsets, rec_code, rec_pred, pred_all, counters, a);
     if (s != RS_OK) return s;
     cudaSetDevice(c->device);
-    // The planning (row offsets, pair tables, fit plan, bucketing) reads only masks, times and
-    // splits: on the side stream it runs beside the standardization and the Gram, and the
-    // solvers wait for both.  (Not with the tensor-core Gram, whose scratch is the fit
-    // workspace the planning fills.)
-    const bool overlap = c->side && c->fork && c->join && precision != RS_GRAM_BF16X3;
-    cudaStream_t ps = overlap ? c->side : c->stream;
     cudaError_t e = cudaSuccess;
-    if (overlap) {
-        e = cudaEventRecord(c->fork, c->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+    if (!c->side || !c->fork || !c->join || precision == RS_GRAM_BF16X3) {
+        // one stream, in order: the tensor-core Gram's scratch is the fit workspace, which the
+        // planning fills afterwards
+        s = rs_standardize(c, b, Z, nullptr, nullptr);
+        if (s == RS_OK) s = rs_gram(c, &zb, precision, K, fws, fbytes);
+        if (s != RS_OK) return s;
+        e = rs_launch_rec_offsets(&zb, sp, rec_offsets, c->scan, c->dstatus, c->stream);
+        if (e == cudaSuccess) e = rs_launch_fit_predict(a, c->stream);
+        return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_cv_step");
     }
-    if (e == cudaSuccess) e = rs_launch_rec_offsets(&zb, sp, rec_offsets, c->scan, c->dstatus, ps);
+    // The planning (row offsets, pair tables, fit plan, bucketing) reads only masks, times and
+    // splits: on the side stream it runs beside the standardization and the Gram (which use
+    // no part of the fit workspace), and the solvers wait for both.
+    e = cudaEventRecord(c->fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+    if (e == cudaSuccess) e = rs_launch_rec_offsets(&zb, sp, rec_offsets, c->scan, c->dstatus, c->side);
     if (e == cudaSuccess) {
         a.phase = 1;
-        e = rs_launch_fit_predict(a, ps);
+        e = rs_launch_fit_predict(a, c->side);
     }
-    if (overlap && e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+    if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
     if (e != cudaSuccess) return cuda_fail(c, e, "rs_cv_step (planning)");
     s = rs_standardize(c, b, Z, nullptr, nullptr);
     if (s == RS_OK) s = rs_gram(c, &zb, precision, K, fws, fbytes);
-    if (overlap) {                              // joined whatever happened above
-        e = cudaStreamWaitEvent(c->stream, c->join, 0);
-        if (e != cudaSuccess && s == RS_OK) return cuda_fail(c, e, "rs_cv_step (join)");
-    }
+    e = cudaStreamWaitEvent(c->stream, c->join, 0);   // joined whatever happened above
     if (s != RS_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_cv_step (join)");
     a.phase = 2;
     e = rs_launch_fit_predict(a, c->stream);
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_cv_step");

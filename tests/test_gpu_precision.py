@@ -77,3 +77,31 @@ def test_refined_precision_form_against_the_reference(env):
     # of the precision form is 2e-5 relative (+1e-6 absolute)
     close(fix, r.pred_all, rel=2e-5, abs_=1e-6)
     np.testing.assert_array_equal(g["rec_offsets"], r.rec_offsets)
+
+
+@pytest.mark.parametrize("precision,flags", [("f64", 0), ("bf16x3", 0), ("bf16x3", "refine"), ("f64", "ibk")])
+def test_one_call_step_equals_the_separate_calls(env, precision, flags):
+    # rs_cv_step orders its launches itself (the planning beside the Gram on a second stream,
+    # or after the tensor-core Gram, whose scratch is the fit workspace): its outputs equal
+    # those of the individual entry points, bit for bit
+    rs, ctx = env
+    prec = {"f64": rs.RS_GRAM_F64, "bf16x3": rs.RS_GRAM_BF16X3}[precision]
+    fl = {0: 0, "refine": rs.RS_REFINE_X, "ibk": rs.RS_MODEL_IBK}[flags]
+    batch = synth.make_batch(5, versions=(20, 64), feat=160, dtype=np.float64, seed=84, mixing_kappa=1e3)
+    for kind in ("lovo", "half"):
+        splits = synth.make_splits(batch, kind, 40, seed=84)
+        db, ds = rs.DeviceBatch.from_host(batch), rs.DeviceSplits.from_host(splits, batch=batch)
+        ref = rs.cv_run(ctx, db, ds, precision=prec, flags=fl)
+        R = int(ref["rec_offsets"][-1])
+        out = rs.alloc_outputs(R, ds.n_splits, 3)
+        ws = torch.empty(ctx.cv_workspace_bytes(db, ds), dtype=torch.uint8, device="cuda")
+        for _ in range(2):                       # twice: the second call reuses the workspace
+            out.counters.zero_()
+            ctx.cv_step(db, ds, ws, out.rec_offsets, out.rec_code, flags=fl, precision=prec,
+                        rec_pred=out.rec_pred, pred_all=out.pred_all, counters=out.counters)
+            torch.cuda.synchronize()
+            ctx.check_device_status()
+            np.testing.assert_array_equal(out.rec_offsets.cpu().numpy(), ref["rec_offsets"])
+            np.testing.assert_array_equal(out.rec_code.cpu().numpy().view(np.uint32), ref["rec_code"])
+            np.testing.assert_array_equal(out.pred_all.cpu().numpy().reshape(R, 6), ref["pred_all"])
+            np.testing.assert_array_equal(out.counters.cpu().numpy().view(np.uint64), ref["counters"])
