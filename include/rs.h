@@ -231,8 +231,14 @@ rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
  * given), plan rows into rec_offsets, then the batched fit/predict/rank.  workspace:
  * device memory of at least rs_cv_workspace_bytes(batch, splits) bytes, 256-byte
  * aligned, owned by the caller and used as scratch (Z, the Gram blocks and the fit
- * workspace).  Outputs as in rs_predict_rank.  With RS_MODEL_IBK the block is the
- * distance block (precision RS_GRAM_F64 or RS_GRAM_DIST2).                             */
+ * workspace).  Outputs as in rs_predict_rank, equal bit for bit to those of the individual
+ * calls.  With RS_MODEL_IBK the block is the distance block (precision RS_GRAM_F64 or
+ * RS_GRAM_DIST2).  Ordering: the row planning and the fit plan (they read only masks, times
+ * and splits) run on the context's internal second stream beside the standardization and
+ * the Gram, forked from and joined back into the context's stream with events, so the call
+ * is still ordered on the context's stream as a whole; with RS_GRAM_BF16X3 (whose scratch is
+ * the fit workspace) every stage runs on the context's stream in order.  One context must
+ * not run two calls at once from different host threads.                                */
 size_t rs_cv_workspace_bytes(const rs_batch* batch, const rs_splits* splits);
 rs_status rs_cv_step(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
                      double lambda, int k, double tau, int flags, int precision,
