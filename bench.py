@@ -431,6 +431,13 @@ def main():
               "plan": work["mask_bytes"] / (hbm_peak * 1e6),
               "solve": work["solve_group"] / (fp64_peak * 1e9),
               "rank": work["rank_bytes"] / (hbm_peak * 1e6)}
+    # the stages before the solvers, from their stand-alone times
+    roof["stages"]["gram_alone"] = {"ms": alone["gram_f64"], "flops": work["gram_flops"],
+                                    "frac_fp64": work["gram_flops"] / (alone["gram_f64"] * 1e-3) / 1e12 / fp64_peak}
+    roof["stages"]["standardize_alone"] = {
+        "ms": alone["standardize"], "bytes": work["std_bytes"],
+        "frac_hbm": work["std_bytes"] / (alone["standardize"] * 1e-3) / 1e9 / hbm_peak,
+        "note": "bound by the FP64 logarithm (12 FP64 instructions per element), not by HBM"}
     roof["stages"]["step"] = {"ms": ms_step, "bound_ms": sum(bounds.values()),
                               "frac": sum(bounds.values()) / ms_step,
                               "bound_ms_parts": bounds,
