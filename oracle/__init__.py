@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "librs_oracle.so")
+_SO_ASAN = os.path.join(_HERE, "_build", "librs_oracle_asan.so")
 _lib = None
 
 N_OPT = 6
@@ -39,23 +40,28 @@ MODEL_M5P = 8
 IBK_NEIGHBORS = 10          # k of the instance-based learner (Sec. 3.4: k = 10)
 
 
-def build(force: bool = False) -> str:
-    """Compile the C reference with gcc (OpenMP over splits, IEEE double, no FP contraction)."""
+def build(force: bool = False, sanitize: bool = False) -> str:
+    """Compile the C reference with gcc (OpenMP over splits, IEEE double, no FP contraction).
+    sanitize=True builds a separate AddressSanitizer copy (``librs_oracle_asan.so``, same
+    arithmetic) that a test loads in a child process to check the oracle's memory accesses."""
     srcs = [os.path.join(_HERE, f) for f in ("rs_oracle.c", "rs_m5p.c")]
-    os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(f) for f in srcs):
-        tmp = _SO + f".tmp{os.getpid()}"
+    so = _SO_ASAN if sanitize else _SO
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    if force or not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(f) for f in srcs):
+        tmp = so + f".tmp{os.getpid()}"
+        extra = ["-g", "-fsanitize=address", "-fno-omit-frame-pointer"] if sanitize else []
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, *srcs, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+                               "-fno-fast-math", *extra, "-o", tmp, *srcs, "-lm"])
+        os.replace(tmp, so)
+    return so
 
 
 def lib():
+    """The oracle's C library; ``RS_ORACLE_SO`` names another build of it (the sanitized one)."""
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_SO)
+        so = os.environ.get("RS_ORACLE_SO") or build()
+        L = C.CDLL(so)
         P = C.c_void_p
         L.orc_standardize.argtypes = [C.c_int, C.c_int, P, P, C.c_double, P, P, P]
         L.orc_pairs.argtypes = [C.c_int, P, C.c_int, P, P]
@@ -151,6 +157,16 @@ class CVResult:
         return int(self.counters[COUNTER_NAMES.index(name)])
 
 
+def _check_versions(batch):
+    """A program (or run) holds at most 64 versions, one per 6-bit mask (Sec. 3.3); the C
+    code keeps per-program tables of that size."""
+    v = np.diff(np.asarray(batch.row_offsets))
+    if v.size and (v.min() < 0 or v.max() > 64):
+        raise ValueError("every program needs 0..64 versions")
+    if batch.masks.size and int(np.max(batch.masks)) > 63:
+        raise ValueError("optimization masks are 6-bit")
+
+
 def rec_offsets(batch, splits) -> np.ndarray:
     out = np.zeros(splits.n_splits + 1, dtype=np.int64)
     lib().orc_rec_offsets(batch.n_programs, _p(np.ascontiguousarray(batch.row_offsets)),
@@ -168,6 +184,7 @@ def cv_batch(batch, splits, lam: float = 1e-3, k: int = 3, tau: float = 1.05, fl
         raise ValueError("model must be 'ridge' or 'ibk'")
     if model == "ibk":
         flags |= MODEL_IBK
+    _check_versions(batch)
     L = lib()
     P = batch.n_programs
     fo = np.zeros(P + 1, dtype=np.int64)
@@ -225,6 +242,8 @@ def transfer(train, test, groups=None, lam: float = 1e-3, k: int = 3, tau: float
         flags |= MODEL_IBK
     if model == "m5p":
         flags |= MODEL_M5P
+    _check_versions(train)
+    _check_versions(test)
     L = lib()
     Q = test.n_programs
     g = np.arange(Q + 1, dtype=np.int64) if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
@@ -272,6 +291,8 @@ def ibk_predict(Zrows, y, zt, k: int = IBK_NEIGHBORS) -> float:
     """Sec. 3.4 IBK for one test vector: mean label of the k nearest training rows."""
     Zrows = np.ascontiguousarray(Zrows, dtype=np.float64)
     n, F = Zrows.shape
+    if n < 1 or not 1 <= k <= 64:
+        raise ValueError("IBK needs n >= 1 training rows and 1 <= k <= 64")
     return float(lib().orc_ibk_predict(n, F, _p(Zrows), _p(np.ascontiguousarray(y, dtype=np.float64)),
                                        _p(np.ascontiguousarray(zt, dtype=np.float64)), int(k)))
 

@@ -218,11 +218,14 @@ int orc_ridge_fit(int n, int F, const double* Zrows, const double* y, double lam
 /* Sec. 3.4, IBK: the prediction for test vector zt from n training rows Zrows [n][F] with
  * labels y: squared Euclidean distances d_a = sum_f (zt_f - z_a,f)^2, the kn nearest
  * (insertion into a list ordered by (d, a), so equal distances keep the lower index first),
- * and the mean of their labels, summed in ascending index a.  n must be >= 1.        */
+ * and the mean of their labels, summed in ascending index a.  Any n >= 1 (the transfer
+ * protocol pools up to 32 pairs per run); 1 <= kn <= ORC_IBK_MAXK, else NaN.         */
+#define ORC_IBK_MAXK 64
 double orc_ibk_predict(int n, int F, const double* Zrows, const double* y, const double* zt, int kn) {
-    int sel[64];
-    double sd[64];
+    int sel[ORC_IBK_MAXK];
+    double sd[ORC_IBK_MAXK];
     int m = 0;
+    if (n < 1 || kn < 1 || kn > ORC_IBK_MAXK) return NAN;
     for (int a = 0; a < n; ++a) {
         double d = 0.0;
         for (int f = 0; f < F; ++f) {
@@ -242,12 +245,18 @@ double orc_ibk_predict(int n, int F, const double* Zrows, const double* y, const
         sel[pos] = a;
         if (m < kn) ++m;
     }
-    int chosen[64];
-    for (int a = 0; a < n; ++a) chosen[a] = 0;
-    for (int q = 0; q < m; ++q) chosen[sel[q]] = 1;
+    /* the chosen indices in ascending order (insertion sort of the m <= kn entries) */
+    for (int q = 1; q < m; ++q) {
+        const int cur = sel[q];
+        int p = q - 1;
+        while (p >= 0 && sel[p] > cur) {
+            sel[p + 1] = sel[p];
+            --p;
+        }
+        sel[p + 1] = cur;
+    }
     double sum = 0.0;
-    for (int a = 0; a < n; ++a)
-        if (chosen[a]) sum += y[a];
+    for (int q = 0; q < m; ++q) sum += y[sel[q]];
     return sum / m;
 }
 

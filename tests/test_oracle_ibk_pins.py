@@ -119,3 +119,27 @@ def test_ibk_is_invariant_to_feature_order():
     a = oracle.ibk_predict(Z, y, zt, 10)
     b = oracle.ibk_predict(Z[:, perm], y, zt[perm], 10)
     assert abs(a - b) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [65, 96, 128, 257])
+@pytest.mark.parametrize("k", [10, 64])
+def test_ibk_many_training_pairs_match_brute_force(n, k):
+    # the transfer protocol pools up to 32 pairs per run (Sec. 5, Table 2): 96 for three
+    # runs, 128 for four; the neighbour list must not depend on n being small
+    rng = np.random.default_rng(n * 7 + k)
+    F = 9
+    Z = rng.normal(size=(n, F))
+    Z[n - 1] = Z[0]                                 # exact ties across the whole range
+    Z[n // 2] = Z[3]
+    y = rng.normal(size=n)
+    for trial in range(6):
+        zt = Z[int(rng.integers(0, n))] if trial % 2 else rng.normal(size=F)
+        assert abs(oracle.ibk_predict(Z, y, zt, k) - _brute(Z, y, zt, k)) <= 1e-12
+
+
+def test_ibk_rejects_out_of_range_k():
+    Z = np.zeros((3, 2))
+    with pytest.raises(ValueError):
+        oracle.ibk_predict(Z, np.zeros(3), np.zeros(2), 65)
+    with pytest.raises(ValueError):
+        oracle.ibk_predict(Z, np.zeros(3), np.zeros(2), 0)

@@ -186,3 +186,23 @@ def test_empty_and_single_pair_fits():
         # candidates for optimization 0: test versions 0 (mask 0) and 2 (mask 2)
         assert r.pred_all[0, 0] == pytest.approx(0.2, abs=1e-15) and r.pred_all[2, 0] == r.pred_all[0, 0]
         assert np.isnan(r.pred_all[1, 0])
+
+
+@pytest.mark.parametrize("model", ["ibk", "ridge"])
+def test_transfer_three_and_four_run_groups_match_numpy(model):
+    # groups of three and four runs of all 64 masks pool 96 and 128 training pairs per
+    # optimization (Sec. 5: a model trained on every run of an input); the IBK neighbour
+    # search then runs over more pairs than one program can hold
+    runs = _small_runs(31, inputs=1, runs=4, feat=8)
+    idx = {key: p for p, key in enumerate(runs.meta["index"])}
+    bh = [idx[("BH", 0, r)] for r in range(4)]
+    nb = [idx[("NB", 0, r)] for r in range(4)]
+    train = synth.take_programs(runs, bh + bh[:3])
+    test = synth.take_programs(runs, [nb[0], nb[1]])
+    groups = np.array([0, 4, 7])
+    res = oracle.transfer(train, test, groups, model=model)
+    ref = _numpy_transfer(train, test, groups, 1e-3, 0x3F, model)
+    assert np.array_equal(np.isnan(res.pred_all), np.isnan(ref))
+    m = ~np.isnan(ref)
+    tol = 1e-12 if model == "ibk" else 1e-8
+    np.testing.assert_allclose(res.pred_all[m], ref[m], rtol=0, atol=tol)
