@@ -85,23 +85,47 @@ def measured_hbm_peak():
         return 6800.0
 
 
-def make_inputs(seed):
+def make_inputs(seed, programs=None):
     from paper_1910_07776_gb300 import synth
-    b = synth.make_batch(CFG["programs"], versions=CFG["versions"], feat=CFG["feat"],
+    b = synth.make_batch(programs or CFG["programs"], versions=CFG["versions"], feat=CFG["feat"],
                          dtype=np.float32, seed=seed)
     s = synth.make_half_splits_fast(b, CFG["splits"], seed=seed)
     return b, s
 
 
+def rank_inputs(rank, world):
+    """This rank's share of the job.  One GPU: the whole batched-CV workload.  N GPUs (weak
+    scaling): the job is N times the workload (64 N programs), split over the ranks by the
+    longest-processing-time rule on each program's estimated work, so every rank holds about
+    one workload's worth of fits and no data moves between ranks."""
+    if world <= 1:
+        return make_inputs(CFG["seed"])
+    from paper_1910_07776_gb300 import shard
+    b, s = make_inputs(CFG["seed"], CFG["programs"] * world)
+    mine = shard.lpt_partition(shard.program_costs(b, s), world)[rank]
+    return shard.shard(b, s, mine)
+
+
+def fit_flops(n):
+    """FP64 operations of one ridge fit of n >= 2 pairs by the square-root-free LDL^T route
+    the solvers take (an FMA counts 2, a multiply 1, a reciprocal 1):
+      factorisation   (n-1)n(n+1)/6 FMAs, n(n-1)/2 multiplies (L = c / d), n reciprocals;
+      two forward solves with the unit lower factor   n(n-1) FMAs;
+      num, den = t_1^T D^-1 (t_y, t_1)   n multiplies, 2n FMAs; b   1 multiply, 1 reciprocal;
+      D^-1 (t_y - b t_1)   n FMAs, n multiplies;  backward solve   n(n-1)/2 FMAs.
+    Total (n-1)n(n+1)/3 + 3.5 n(n-1) + 9n + 2.  Each prediction adds n FMAs (2n flops)."""
+    n = np.asarray(n, dtype=np.float64)
+    return (n - 1) * n * (n + 1) / 3 + 3.5 * n * (n - 1) + 9 * n + 2
+
+
 def algorithmic_work(batch, splits, k=3, nreg=10):
     """Algorithmic work of the fit/predict stages, counted from the definitions.
-    FP64 flops: per fit with n pairs a factorisation (n^3/3), two right-hand sides through
-    both triangular solves (4 n^2) and the intercept / dual update (4 n); per prediction
-    2 n.  A fit of one pair needs no arithmetic (alpha = 0, b = y: every prediction is
-    b), so it counts zero flops.  Fits with n <= nreg (and their predictions) belong to the
-    register solvers, larger ones to the shared-memory solver.  Rank stage bytes: per test row the
-    version mask (1 B), its scoring summary (4 B), the code word (4 B) and k reported
-    values (8 B each), plus 8 B per prediction read."""
+    FP64 flops: per fit with n pairs fit_flops(n); per prediction 2 n.  A fit of one pair
+    needs no arithmetic (alpha = 0, b = y: every prediction is b), so it counts zero flops.
+    Fits with n <= nreg (and their predictions) belong to the register solvers, larger ones
+    to the shared-memory solver.  Rank stage bytes: per test row the version mask (1 B), its
+    scoring summary (4 B), the code word (4 B) and k reported values (8 B each), plus 8 B per
+    prediction read."""
     out = {"solve_small": 0.0, "solve_large": 0.0, "rows": 0, "preds": 0}
     for p in range(batch.n_programs):
         rs_ = batch.program_rows(p)
@@ -130,7 +154,7 @@ def algorithmic_work(batch, splits, k=3, nreg=10):
             for _ in range(V):
                 cnt += (x & np.uint64(1)).astype(np.float64)
                 x = x >> np.uint64(1)
-            fl = n ** 3 / 3 + 4 * n ** 2 + 4 * n + 2 * n * cnt
+            fl = fit_flops(n) + 2 * n * cnt
             out["solve_small"] += float(np.sum(fl * (n >= 2) * (n <= nreg)))
             out["solve_large"] += float(np.sum(fl * (n > nreg)))
             out["preds"] += int(np.sum(cnt * (n > 0)))
@@ -147,62 +171,117 @@ def algorithmic_work(batch, splits, k=3, nreg=10):
 
 
 class ClockSampler:
+    """SM clock, power and clock-event reasons of one GPU, sampled every millisecond through
+    NVML (read-only queries of libnvidia-ml) on a background thread; nvidia-smi at 50 ms if
+    NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_s=0.001):
         self.gpu = gpu_index
+        self.period = period_s
+        self.samples = []          # (t, sm_mhz, max_mhz, power_w, reasons bitmask)
+        self.marks = {}
         self.proc = None
-        self.lines = []
+        self.nvml = self._load_nvml()
+        self._stop = threading.Event()
 
-    def start(self):
+    def _load_nvml(self):
+        import ctypes as C
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except FileNotFoundError:
-            self.proc = None
-            return
-        t0 = time.time()                # the timed region starts once sampling runs
-        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
-            time.sleep(0.01)
-        self.lines.clear()
+            L = C.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                return None
+            h = C.c_void_p()
+            if L.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.gpu), C.byref(h)) != 0:
+                return None
+            reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                L.nvmlDeviceGetCurrentClocksThrottleReasons
+            return (C, L, h, reasons)
+        except (OSError, AttributeError):
+            return None
 
-    def _read(self):
+    def _poll_nvml(self):
+        C, L, h, reasons = self.nvml
+        sm, mx, mw, rs = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        L.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))
+        while not self._stop.is_set():
+            ok = L.nvmlDeviceGetClockInfo(h, 1, C.byref(sm)) == 0
+            L.nvmlDeviceGetPowerUsage(h, C.byref(mw))
+            reasons(h, C.byref(rs))
+            if ok:
+                self.samples.append((time.perf_counter(), float(sm.value), float(mx.value),
+                                     mw.value / 1e3, int(rs.value)))
+            time.sleep(self.period)
+
+    def _read_smi(self):
+        bits = [0x8, 0x40, 0x20, 0x4]
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        sm, mx, reasons, pw = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
+            f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-                pw.append(float(f[3]))
+                r = sum(b for b, v in zip(bits, f[5:9]) if v.lower() == "active")
+                self.samples.append((time.perf_counter(), float(f[1]), float(f[2]), float(f[3]), r))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": float(max(mx)) if mx else None,
-                "power_w_max": float(max(pw)) if pw else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+
+    def start(self):
+        if self.nvml is not None:
+            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
+        else:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", "50"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except FileNotFoundError:
+                return
+            self.t = threading.Thread(target=self._read_smi, daemon=True)
+        self.t.start()
+        t0 = time.time()                # the timed region starts once sampling runs
+        while not self.samples and time.time() - t0 < 3.0:
+            time.sleep(0.001)
+        self.samples.clear()
+
+    def mark(self, name):
+        self.marks[name] = time.perf_counter()
+
+    def stop(self):
+        self._stop.set()
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if getattr(self, "t", None) is not None:
+            self.t.join(timeout=5)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": ["no clock samples"]}
+        arr = list(self.samples)
+
+        def summary(rows):
+            sm = [r[1] for r in rows]
+            rs_ = set()
+            for r in rows:
+                for bit, nm in self.REASONS.items():
+                    if r[4] & bit:
+                        rs_.add(nm)
+            return {"sm_mhz": float(np.median(sm)) if sm else None, "samples": len(sm),
+                    "reasons": sorted(rs_)}
+
+        out = summary(arr)
+        out["sm_max_mhz"] = float(max(r[2] for r in arr))
+        out["power_w_max"] = float(max(r[3] for r in arr))
+        out["source"] = "NVML, 1 ms" if self.nvml is not None else "nvidia-smi, 50 ms"
+        if "timed_end" in self.marks:
+            out["timed_region"] = summary([r for r in arr if r[0] <= self.marks["timed_end"]])
+            out["seconds"] = arr[-1][0] - arr[0][0]
+        return out
 
 
 def cpu_reference_sample(batch, splits, target_s, seed=1):
@@ -282,6 +361,10 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-ibk", action="store_true")
     ap.add_argument("--no-transfer", action="store_true")
+    ap.add_argument("--no-lovo", action="store_true")
+    ap.add_argument("--only-lovo", type=int, default=0, metavar="PROGRAMS",
+                    help="time only the leave-one-version-out form on this many programs (for profiler "
+                         "captures of its solver)")
     ap.add_argument("--surrogate-epochs", type=int, default=2)
     ap.add_argument("--profile-surrogate", action="store_true",
                     help="a short surrogate run for profiler captures of its tensor-core GEMMs: 16 training "
@@ -309,10 +392,15 @@ def main():
     _b.build()
     from paper_1910_07776_gb300 import rs
 
-    batch, splits = make_inputs(CFG["seed"] + rank)
+    batch, splits = rank_inputs(rank, world)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = rs.Context(local, stream)
+    if args.only_lovo:
+        flush = torch.empty(32 * 1024 * 1024, dtype=torch.int64, device=dev)
+        print(json.dumps({"lovo_form": run_lovo(rs, ctx, dev, stream, flush, args, args.only_lovo)}), flush=True)
+        ctx.close()
+        return 0
     db = rs.DeviceBatch.from_host(batch, dev)
     ds = rs.DeviceSplits.from_host(splits, dev, batch)
     Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
@@ -351,6 +439,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    t_clk = time.perf_counter()
     stages = {}
     tot = 0.0
     for _ in range(args.steps):
@@ -361,11 +450,26 @@ def main():
         for k_, v_ in ctx.profile_read().items():
             stages[k_] = stages.get(k_, 0.0) + v_
     torch.cuda.synchronize()
+    clocks.mark("timed_end")
+    # the same step keeps running until the clock record spans at least one second (a short
+    # timed region alone would hold few samples); these steps are timed separately
+    sus_ms, sus_n = 0.0, 0
+    while time.perf_counter() - t_clk < 1.0:
+        between()
+        step()
+        torch.cuda.synchronize()
+        sus_ms += ev[0].elapsed_time(ev[1])
+        sus_n += 1
+        ctx.profile_read()
     clk = clocks.stop()
+    clk["after_timed_region"] = {"steps": sus_n, "ms_per_step": sus_ms / sus_n if sus_n else None}
     tot, R_total = aggregate_over_ranks(tot, R, world, dev)
     ctx.check_device_status()
     ms_step = tot / args.steps
     value = R_total * args.steps / (tot / 1e3)
+    if world > 1:                              # the job's accuracy counters: a sum over the ranks
+        from paper_1910_07776_gb300 import shard
+        shard.allreduce_counters(out.counters)
     cnt = out.counters.cpu().numpy().view(np.uint64).astype(np.float64)
     acc = {"sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1),
            "rec_precision": cnt[6] / max(cnt[5], 1), "recs_per_row": cnt[4] / max(cnt[0], 1)}
@@ -457,6 +561,10 @@ def main():
     if rank == 0 and not args.only_step and not args.no_ibk:
         ibk = run_ibk(rs, ctx, batch, splits, dev, stream, flush, args)
 
+    lovo = None
+    if rank == 0 and not args.only_step and not args.no_lovo:
+        lovo = run_lovo(rs, ctx, dev, stream, flush, args)
+
     xfer = None
     if rank == 0 and not args.only_step and not args.no_transfer:
         xfer = run_transfer(rs, ctx, dev, stream, flush, args)
@@ -486,7 +594,9 @@ def main():
                    "features": CFG["feat"], "splits_per_program": CFG["splits"],
                    "recs_per_step": R, "lambda": CFG["lam"], "k": CFG["k"], "tau": CFG["tau"],
                    "l2": "flushed between timed steps (256 MB write, untimed)",
-                   "parallelism": f"programs sharded, {world} GPU(s), no collective"},
+                   "parallelism": (f"{world} GPUs, a job of {world} x 64 programs split by the longest-"
+                                   "processing-time rule, no data-path collective, counters summed at the end"
+                                   if world > 1 else "1 GPU")},
         "kernels_ms": {"step": ms_step, **{k_ + "_alone": v_ for k_, v_ in alone.items()},
                        "solve_and_rank": fit_ms,
                        **{"fit." + k_: v_ for k_, v_ in stage_ms.items()},
@@ -501,6 +611,7 @@ def main():
         "precision_form": prec,
         "uneven_form": unev,
         "ibk_form": ibk,
+        "lovo_form": lovo,
         "table2_transfer": xfer,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -622,6 +733,73 @@ def run_ibk(rs, ctx, batch, splits, dev, stream, flush, args):
     out["lovo"] = {"workload": "256 programs x 64 versions (all masks) x 256 f32 features, leave-one-"
                                "version-out (16,384 splits, 98,304 fits of 31 pairs)", **measure(b, sp, 20)}
     return out
+
+
+def run_lovo(rs, ctx, dev, stream, flush, args, programs=256):
+    """Leave-one-version-out (the paper's protocol over all 64 masks, Sec. 5) at the
+    precision form's shape: 256 programs x 64 versions x 1024 FP64 features, 16,384 splits,
+    98,304 ridge fits of 31 pairs each, every stage in FP64 through the one-call step.  The
+    fits of more than 16 pairs run in solve_wide_kernel; its stage time (from the end of the
+    planning to the join of the solver streams) against its FP64 flops gives its roofline
+    fraction, and the Gram (1.07 GFLOP) is timed alone beside it."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    b = synth.make_batch_fast(programs, versions=64, feat=1024, dtype=np.float64, seed=43)
+    sp = synth.make_splits(b, "lovo")
+    db = rs.DeviceBatch.from_host(b, dev)
+    ds = rs.DeviceSplits.from_host(sp, dev, b)
+    R = ds.n_test_rows
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
+                               tau=CFG["tau"], rec_pred=o.rec_pred, counters=o.counters)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    o.counters.zero_()
+    ctx.profile_enable(True)
+    reps, tot, stages = 10, 0.0, {}
+    for _ in range(reps):
+        flush.fill_(1)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+        for k_, v_ in ctx.profile_read().items():
+            stages[k_] = stages.get(k_, 0.0) + v_ / reps
+    ctx.profile_enable(False)
+    ctx.check_device_status()
+    Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
+    K = torch.zeros(db.n_programs * 64 * 64, dtype=torch.float64, device=dev)
+    ctx.standardize(db, Z)
+    g_ms = 0.0
+    for _ in range(3):
+        flush.fill_(1)
+        e0.record(stream)
+        ctx.gram(db.with_X(Z), rs.RS_GRAM_F64, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g_ms += e0.elapsed_time(e1) / 3
+    work = algorithmic_work(b, sp, CFG["k"])
+    fp64_peak = FP64_PEAK_NOMINAL_GFLOPS / 1e3
+    solve_ms = stages.get("solve", 0.0) + stages.get("solve_join", 0.0)
+    flops = work["solve_small"] + work["solve_large"]
+    c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
+    ms = tot / reps
+    return {"workload": f"{programs} programs x 64 versions (all masks) x 1024 f64 features, "
+                        f"leave-one-version-out ({64 * programs:,} splits, {384 * programs:,} fits of 31 pairs)",
+            "ms_per_step": ms, "value": R / (ms * 1e-3), "unit": UNIT, "recs_per_step": R,
+            "sign_accuracy": c[3] / max(c[2], 1), "top1_hit_rate": c[8] / max(c[7], 1),
+            "stages_ms": stages,
+            "roofline": {"bound": "alu", "kernel": "solve_wide_kernel (fits of 17..32 pairs)",
+                         "achieved": flops / (solve_ms * 1e-3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": flops / (solve_ms * 1e-3) / 1e12 / fp64_peak, "flops_per_launch": flops,
+                         "ms": solve_ms,
+                         "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FMA/clk x 2.07 GHz)"},
+            "gram_alone": {"ms": g_ms, "flops": work["gram_flops"],
+                           "frac_fp64": work["gram_flops"] / (g_ms * 1e-3) / 1e12 / fp64_peak}}
 
 
 PAPER_TABLE3_IBK = {1: 97.3, 2: 96.0, 3: 96.3, 4: 92.0, 5: 83.6, 6: 55.7}   # Table 3, % (real profiles)
@@ -750,6 +928,68 @@ def run_uneven(rs, ctx, dev, stream, flush, args):
             "sign_accuracy": cnt[3] / max(cnt[2], 1), "data_gen_s": gen_s}
 
 
+def _rel_stats(d, ref):
+    d, ref = np.abs(np.ravel(d)), np.abs(np.ravel(ref))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        e = np.where(ref > 0, d / ref, np.where(d > 0, np.inf, 0.0))
+    return {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)), "max": float(e.max()),
+            "normwise_max": float(d.max() / max(ref.max(), 1e-300))}
+
+
+def precision_coef_errors(rs, ctx, batch, dev, programs=4):
+    """Per-coefficient errors of the BF16x3 forms (raw, refined) against the FP64 GPU path on
+    the first `programs` programs of a leave-one-version-out batch: the dual alpha and b of
+    every fit and the primal beta = sum_a alpha_a z_a it implies (computed on the host in FP64
+    from the standardized features), each as elementwise relative error (median, 99th
+    percentile, max) and normwise (max |error| / max |value|)."""
+    import torch
+    from paper_1910_07776_gb300 import synth
+    sub = synth.take_programs(batch, list(range(programs)))
+    sp = synth.make_splits(sub, "lovo")
+    db = rs.DeviceBatch.from_host(sub, dev)
+    ds = rs.DeviceSplits.from_host(sp, dev, sub)
+    Z = ctx.standardize(db)
+    zb = db.with_X(Z)
+    Zh = Z.cpu().numpy()
+    S = ds.n_splits
+    coefs = {}
+    for name, prec, flags in (("f64", rs.RS_GRAM_F64, 0), ("bf16x3", rs.RS_GRAM_BF16X3, 0),
+                              ("bf16x3_refined", rs.RS_GRAM_BF16X3, rs.RS_REFINE_X)):
+        K = ctx.gram(zb, prec)
+        c = torch.zeros(S * 6 * 33, dtype=torch.float64, device=dev)
+        ctx.fit_batched(zb, K, ds, CFG["lam"], rs.RS_FORM_BATCHED | flags, c)
+        coefs[name] = c.cpu().numpy().reshape(S, 6, 33)
+    beta = {k: [] for k in coefs}
+    alpha = {k: [] for k in coefs}
+    bias = {k: [] for k in coefs}
+    for p in range(programs):
+        V, F = sub.versions(p), int(sub.feat_width[p])
+        Zp = Zh[int(sub.x_offsets[p]):int(sub.x_offsets[p]) + V * F].reshape(V, F)
+        m = sub.masks[sub.program_rows(p)].astype(int)
+        slot = {int(x): i for i, x in enumerate(m)}
+        for s_ in range(int(sp.split_offsets[p]), int(sp.split_offsets[p + 1])):
+            T = int(sp.train_masks[s_])
+            for j in range(6):
+                vs = [v for v in range(V) if not (m[v] >> j) & 1 and (m[v] | 1 << j) in slot
+                      and (T >> v) & 1 and (T >> slot[m[v] | 1 << j]) & 1]
+                n = len(vs)
+                if n == 0:
+                    continue
+                for k_, cf in coefs.items():
+                    al = cf[s_, j, 1:1 + n]
+                    alpha[k_].append(al)
+                    beta[k_].append(al @ Zp[vs])
+                    bias[k_].append(cf[s_, j, :1])
+    out = {"sample": f"{programs} programs, {S} leave-one-out splits, {S * 6} fits"}
+    ref = {"beta": np.concatenate(beta["f64"]), "alpha": np.concatenate(alpha["f64"]),
+           "b": np.concatenate(bias["f64"])}
+    for k_ in ("bf16x3", "bf16x3_refined"):
+        out[k_] = {"beta": _rel_stats(np.concatenate(beta[k_]) - ref["beta"], ref["beta"]),
+                   "alpha": _rel_stats(np.concatenate(alpha[k_]) - ref["alpha"], ref["alpha"]),
+                   "b": _rel_stats(np.concatenate(bias[k_]) - ref["b"], ref["b"])}
+    return out
+
+
 def run_precision(rs, ctx, dev, stream, flush, args):
     """Precision form: 256 programs x 64 versions x 1024 FP64 features, leave-one-version-out,
     a condition-number sweep by random mixing; BF16-split tensor-core Gram + FP64 factorisation
@@ -792,9 +1032,11 @@ def run_precision(rs, ctx, dev, stream, flush, args):
             pa, code = outs[name]
             d = np.abs(pa[ok] - ref[ok])
             ent[name] = {"max_rel_err_pred": float(d.max() / sc), "median_rel_err_pred": float(np.median(d) / sc),
+                         "pred_elementwise": _rel_stats(pa[ok] - ref[ok], ref[ok]),
                          "ranking_rows_changed": int(np.sum(code != rcode)), "ms": times[name],
                          "recs_per_s": R / (times[name] * 1e-3)}
         ent["f64"] = {"ms": times["f64"], "recs_per_s": R / (times["f64"] * 1e-3)}
+        ent["coefficients_vs_f64_path"] = precision_coef_errors(rs, ctx, b, dev, programs=4)
         # achieved condition number of one training system (program 0, split 0, optimization 0)
         Zp = np.log(b.program_X(0) / b.cycles[b.program_rows(0)][:, None])
         Zp = (Zp - Zp.mean(0)) / np.where(Zp.std(0) > 1e-12, Zp.std(0), 1.0)
@@ -811,8 +1053,7 @@ def profile_surrogate():
     import torch
     from paper_1910_07776_gb300 import build as _b
     _b.build()
-    from paper_1910_07776_gb300 import rs
-    from oracle import mlp
+    from paper_1910_07776_gb300 import rs, synth
     dev = torch.device("cuda", 0)
     ctx = rs.Context(0, torch.cuda.current_stream(dev))
     g = torch.Generator(device=dev)
@@ -822,7 +1063,7 @@ def profile_surrogate():
     Xte = torch.randn(131072, 256, device=dev, dtype=torch.float64, generator=g)
     masks = torch.randint(0, 64, (131072,), device=dev, dtype=torch.uint8, generator=g)
     sur = rs.Surrogate(ctx, 8192, infer_chunk=131072)
-    sur.load(mlp.init_params(11))
+    sur.load(synth.init_mlp_params(11))
     sur.train(Xtr, Ytr, steps=16)
     code = torch.empty(131072, dtype=torch.int32, device=dev)
     rp = torch.empty(131072 * CFG["k"], dtype=torch.float64, device=dev)
@@ -840,7 +1081,6 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
     inference on 1 M held-out vectors, against the batched plain method on the same rows."""
     import torch
     from paper_1910_07776_gb300 import synth
-    from oracle import mlp
     P_tr, P_te = 31250, 15625
     t0 = time.perf_counter()
     b = synth.make_batch_fast(P_tr + P_te, versions=64, feat=256, dtype=np.float32, seed=11)
@@ -873,7 +1113,7 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
     Xte = Zm[n_tr:].contiguous()
     masks_te = db.masks[n_tr:].contiguous()
     sur = rs.Surrogate(ctx, 8192, infer_chunk=131072)
-    sur.load(mlp.init_params(11))
+    sur.load(synth.init_mlp_params(11))
     steps = args.surrogate_epochs * (n_tr // 8192)
     lc = torch.zeros(steps, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -952,14 +1192,66 @@ def run_surrogate(rs, ctx, dev, stream, flush, args):
     mae = float(np.mean(np.abs(ps - pp)[cm]))
     rate_s = n_te / (inf_ms * 1e-3)
     rate_p = tds.n_test_rows / (plain_ms * 1e-3)
-    eff = n_te / (inf_ms * 1e-3 + fb_frac * n_te / rate_p)
+
+    # the plain fallback, executed and timed: the held-out programs again, with 5 % of them
+    # holding three versions whose every counter is scaled by e^4 (profiles unlike the rest
+    # of their program).  Timed per repetition: ranked surrogate inference with OOD flags, then
+    # rs_surrogate_fallback (selection, gather, the plain pass over the flagged programs, merge)
+    shifted, sprogs = synth.with_anomalous_versions(te, 0.05, per_program=3, seed=12)
+    sdb = rs.DeviceBatch.from_host(shifted, dev)
+    Zs = ctx.standardize(sdb).view(n_te, 256)
+    fws = ctx.workspace(ctx.fallback_workspace_bytes(sdb, tds))
+    code2 = torch.empty(n_te, dtype=torch.int32, device=dev)
+    rp2 = torch.empty(n_te * CFG["k"], dtype=torch.float64, device=dev)
+
+    def infer_with_fallback():
+        _, _, fb2 = sur.infer(Zs, ood_threshold=thr, want_ood=True, masks=sdb.masks, k=CFG["k"], tau=CFG["tau"],
+                              rec_code=code2, rec_pred=rp2, want_pred=False)
+        refit = ctx.surrogate_fallback(sdb, tds, fb2, code2, rp2, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                                       workspace=fws)
+        return fb2, refit
+
+    for _ in range(2):
+        infer_with_fallback()
+    torch.cuda.synchronize()
+    fbk_ms = 0.0
+    for _ in range(reps):
+        flush.fill_(1)
+        e0.record(stream)
+        fb2, refit = infer_with_fallback()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fbk_ms += e0.elapsed_time(e1)
+    fbk_ms /= reps
+    ctx.check_device_status()
+    # agreement of the merged ranking with the plain method's own ranking of the same rows
+    sout = rs.alloc_outputs(tds.n_test_rows, tds.n_splits, CFG["k"], dev, pred_all=False)
+    ctx.cv_step(sdb, tds, ws, sout.rec_offsets, sout.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
+                rec_pred=sout.rec_pred)
+    tm_te = tsp.train_masks.astype(np.uint64)
+    tbits = ((tm_te[:, None] >> np.arange(64, dtype=np.uint64)[None, :]) & np.uint64(1)) == 0
+    tver = (np.repeat(np.arange(P_te), 2)[:, None] * 64 + np.arange(64)[None, :])[tbits]
+    plain_code = np.empty(n_te, dtype=np.int32)
+    plain_code[tver] = sout.rec_code.cpu().numpy()
+    merged = code2.cpu().numpy()
+    flg = fb2.cpu().numpy().astype(bool)
+    fallback = {"workload": "the 1,000,000 held-out vectors with 5 % of their programs holding 3 versions "
+                            "whose counters are all scaled by e^4 (anomalous profiles)",
+                "value_with_plain_fallback": n_te / (fbk_ms * 1e-3), "unit": UNIT, "ms": fbk_ms,
+                "fallback_fraction": float(flg.mean()), "programs_refitted": refit[0],
+                "versions_refitted": refit[1], "programs_shifted": int(len(sprogs)),
+                "rec_code_equal_to_plain": {"all_rows": float(np.mean(merged == plain_code)),
+                                            "flagged_rows": float(np.mean(merged[flg] == plain_code[flg]))
+                                            if flg.any() else None,
+                                            "unflagged_rows": float(np.mean(merged[~flg] == plain_code[~flg]))}}
     return {"workload": "surrogate MLP 256-512-512-6: train 2,000,000 vectors (31,250 programs x 64 "
                         "versions, labels = plain ridge CV predictions), infer 1,000,000 held-out vectors",
             "value": rate_s, "unit": UNIT, "infer_ms": inf_ms, "train_ms": train_ms,
             "train_steps": steps, "batch_rows": 8192, "loss_first": float(lc[0]), "loss_last": float(lc[-1]),
             "plain_batched_same_rows": {"value": rate_p, "ms": plain_ms},
             "speedup_vs_plain_batched": rate_s / rate_p,
-            "ood_threshold": thr, "fallback_fraction": fb_frac, "value_with_plain_fallback": eff,
+            "ood_threshold": thr, "fallback_fraction": fb_frac, "value_with_plain_fallback": fallback["value_with_plain_fallback"],
+            "plain_fallback": fallback,
             "accuracy": {"surrogate_sign": s_sign, "surrogate_top1": s_top1, "plain_sign": p_sign,
                          "plain_top1": p_top1, "mae_vs_plain_log_speedup": mae},
             "data_gen_s": gen_s}

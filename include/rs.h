@@ -182,7 +182,10 @@ rs_status rs_rec_offsets(rs_ctx* ctx, const rs_batch* batch, const rs_splits* sp
  * fit_status (nullable): uint8 [S][6] RS_FIT_*.  lambda >= 0 (at lambda = 0 the dual
  * system is the minimum-norm interpolant when n <= F).
  * form: RS_FORM_BATCHED (fits of the whole batch sorted by size, one thread per fit up to
- * 10 pairs, one warp per larger fit) or RS_FORM_PLAIN (one warp per fit, per chunk).
+ * 10 pairs, lanes sharing the larger fits) or RS_FORM_PLAIN (one warp per fit, per chunk);
+ * with the batched form, form | RS_REFINE_X takes one step of iterative refinement of every
+ * fit through the standardized features of `std` (for a K from RS_GRAM_BF16X3), as the
+ * flag does in rs_predict_rank.
  * workspace: caller-owned device scratch of at least rs_fit_workspace_bytes(std, splits)
  * bytes, 256-byte aligned, required by the batched form (may be NULL for the plain form);
  * its contents are undefined after the call.  RS_ENOMEM if it is too small.  A fit with
@@ -292,6 +295,31 @@ rs_status rs_transfer(rs_ctx* ctx, const rs_batch* train, const rs_batch* test, 
                       size_t workspace_bytes, uint8_t* fit_status, uint32_t* rec_code, double* rec_pred,
                       double* pred_all, uint64_t* counters);
 
+/* ---- A7: the plain predictor as the surrogate's fallback -----------------------------------
+ * After rs_surrogate_infer has ranked one row per version of `batch` (raw counters, the
+ * batch's row order) and set used_fallback[row] (device uint8 [n_rows]) where the row's
+ * feature vector lies out of the training distribution, rs_surrogate_fallback predicts
+ * those rows with the plain method instead: every program with at least one flagged row is
+ * copied into a sub-batch in the workspace, the sub-batch goes through the whole plain pass
+ * (rs_cv_step, FP64 Gram: standardization, Gram, fits, predictions, ranking; Sec. 2 tiers 2
+ * and 3 with the Sec. 3.4 ridge model) over that program's splits in `splits` (the plain
+ * protocol's train/test splits of every program of `batch`), and each flagged row takes the
+ * plain ranking of its version from the first split of its program that tests it:
+ * rec_code [n_rows] and rec_pred [n_rows][k] (device, the rs_predict_rank format, as
+ * rs_surrogate_infer wrote them) are overwritten for those rows only; rows that no split
+ * tests keep the surrogate's output.  Only the selected programs are standardized, Gram'd
+ * and fitted.  refit (host int64 [2], nullable) receives the number of programs and of
+ * versions that were refitted.  The call reads the selection's sizes back to the host
+ * once (it synchronises the context's stream at that point), so it cannot be captured in a
+ * CUDA graph.  workspace: rs_fallback_workspace_bytes(batch, splits) bytes (sized for every
+ * program selected), 256-byte aligned, caller-owned; RS_ENOMEM if smaller.  lambda, k, tau
+ * and flags (RS_RANK_ALL only) as in rs_cv_step.                                         */
+size_t rs_fallback_workspace_bytes(const rs_batch* batch, const rs_splits* splits);
+rs_status rs_surrogate_fallback(rs_ctx* ctx, const rs_batch* batch, const rs_splits* splits,
+                                const uint8_t* used_fallback, double lambda, int k, double tau,
+                                int flags, void* workspace, size_t workspace_bytes,
+                                uint32_t* rec_code, double* rec_pred, int64_t* refit);
+
 /* ---- A8: one graph launch per step, and the autotuner ---------------------------------------
  * rs_cv_graph_create runs rs_cv_step once eagerly (reporting argument errors), then captures
  * the same launch sequence into a CUDA graph bound to these pointers and sizes;
@@ -390,7 +418,12 @@ rs_status rs_surrogate_infer(rs_ctx* ctx, const float* blob, const double* X, in
  * loads the library keeps that array until the process exits.  It needs no rs_ctx and
  * calls no cudaMalloc, cudaFree or other allocating routine.
  *   - The first call on a device (the current device) looks up the array's device address
- *     and caches it; make that first call before any stream capture.
+ *     and caches it with the identity of the current CUDA context; make that first call
+ *     before any stream capture.  If the context is destroyed and created again (after
+ *     cudaDeviceReset, say) the next call looks the address up again, so it too should
+ *     come before any capture.
+ *   - Arguments follow rs_cv_step's rules (RS_EINVAL, with the reason in errbuf), and
+ *     sizes that cannot fit are refused before any product of them is formed.
  *   - Every call uses the same array and leaves its contents behind; the call clears what
  *     must start at zero itself.  Calls whose work overlaps on the GPU (two streams, two
  *     threads) race on the array: serialise them.

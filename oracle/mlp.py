@@ -46,15 +46,9 @@ def gelu_grad(u: np.ndarray) -> np.ndarray:
 
 
 def init_params(seed: int = 0, dims=DIMS) -> Dict[str, np.ndarray]:
-    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases (seeded)."""
-    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5A5A))
-    p = {}
-    for i in range(3):
-        fi, fo = dims[i], dims[i + 1]
-        s = 1.0 / math.sqrt(fi)
-        p[f"W{i+1}"] = rng.uniform(-s, s, size=(fo, fi))
-        p[f"b{i+1}"] = rng.uniform(-s, s, size=fo)
-    return p
+    """The seeded initial weights (drawn by the shared input generator, synth.init_mlp_params)."""
+    from paper_1910_07776_gb300 import synth
+    return synth.init_mlp_params(seed, dims)
 
 
 def forward(p, x):

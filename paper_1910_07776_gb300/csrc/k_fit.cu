@@ -358,16 +358,36 @@ __device__ __forceinline__ int solve_fixed(const double* __restrict__ Kp, const 
     int vb[N];
     const int st = fit_fixed<N>(Kp, pb, yl, pm, dl, out, al, b, vb);
     if (st != RS_FIT_OK || !pt) return st;
-    for (uint64_t cm = pt->cand; cm; cm &= cm - 1) {
-        const int t = __ffsll((long long)cm) - 1;
-        const int r = __popcll(pt->test & ((1ull << t) - 1ull));
-        double yh = b;
-        if constexpr (N > 1) {             // with one pair alpha = 0: every prediction is b
-            const double* Kt = Kp + t * RS_GRAM_LD;
-#pragma unroll
-            for (int a = 0; a < N; ++a) yh = fma(al[a], __ldg(Kt + vb[a]), yh);
+    uint64_t cm = pt->cand;
+    if constexpr (N == 1) {                // with one pair alpha = 0: every prediction is b
+        for (; cm; cm &= cm - 1) {
+            const int t = __ffsll((long long)cm) - 1;
+            const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+            if (r < pt->room) pt->dst[r] = b;
         }
-        if (r < pt->room) pt->dst[r] = yh;
+    } else if (cm) {
+        // software pipeline: the Gram entries of the next candidate row are loaded while the
+        // current row's dot product runs
+        int t = __ffsll((long long)cm) - 1;
+        double kv[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) kv[a] = __ldg(Kp + t * RS_GRAM_LD + vb[a]);
+        for (;;) {
+            cm &= cm - 1;
+            const int tn = cm ? __ffsll((long long)cm) - 1 : t;
+            double kn[N];
+#pragma unroll
+            for (int a = 0; a < N; ++a) kn[a] = __ldg(Kp + tn * RS_GRAM_LD + vb[a]);
+            double yh = b;
+#pragma unroll
+            for (int a = 0; a < N; ++a) yh = fma(al[a], kv[a], yh);
+            const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+            if (r < pt->room) pt->dst[r] = yh;
+            if (!cm) break;
+            t = tn;
+#pragma unroll
+            for (int a = 0; a < N; ++a) kv[a] = kn[a];
+        }
     }
     return st;
 }
@@ -1152,6 +1172,220 @@ solve_large_kernel(const SolveArgs a) {
     }
 }
 
+// ====================================================================== solve, n > kNMid
+// Fits of kNMid < n <= 32 pairs (the leave-one-version-out protocol: 31 pairs per fit), without
+// refinement.  kWideLanes lanes share one fit, so a warp works on kWideGroups fits at once.
+// The fit's bordered system M = K_TT + lambda I is factored right-looking, M = L D L^T, in a
+// packed lower triangle in shared memory: at pivot k every element of the trailing triangle
+// takes one FMA, S_ij -= L_ik S_jk, and those elements are spread evenly over the group's
+// lanes, so the lanes stay busy as the triangle shrinks (one lane per row would leave half of
+// them idle).  The reciprocal of a pivot is one warp instruction for kWideGroups fits.  Then,
+// as in solve_fixed: t_y = L^-1 y and t_1 = L^-1 1 (taken in the factorisation's sweep),
+// b = t_1^T D^-1 t_y / t_1^T D^-1 t_1, alpha = L^-T D^-1 (t_y - b t_1), predictions
+// b + sum_a alpha_a K[t][v_a]
+// with the candidate rows spread over the lanes.  Every loop that shuffles runs to the warp's
+// largest n, so the groups of a warp (equal n except at bucket boundaries) stay converged.
+constexpr int kWideLanes = 8;
+constexpr int kWideGroups = 32 / kWideLanes;
+constexpr int kWideWarps = 2;
+constexpr int kWideTri = tri(RS_MAXPAIRS);                 // packed lower triangle with diagonal
+constexpr int kWideDoubles = kWideTri + 4 * RS_MAXPAIRS;   // + two pivot columns, t_y, t_1
+constexpr size_t kWideSmem = (size_t)kWideWarps * kWideGroups * (kWideDoubles * sizeof(double) +
+                                                                 RS_MAXPAIRS * sizeof(int));
+
+// Sum over the kWideLanes lanes of a group (xor offsets stay inside the group).
+__device__ __forceinline__ double group_sum(double x) {
+#pragma unroll
+    for (int o = kWideLanes / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Row and column of entry e of a packed lower triangle (row i holds columns 0..i), and the
+// step to entry e + kWideLanes.
+__device__ __forceinline__ void tri_pos(int e, int& i, int& j) {
+    i = 0;
+    while (tri(i + 1) <= e) ++i;
+    j = e - tri(i);
+}
+__device__ __forceinline__ void tri_step(int& i, int& j) {
+    j += kWideLanes;
+    while (j > i) {
+        j -= i + 1;
+        ++i;
+    }
+}
+
+__global__ void __launch_bounds__(kWideWarps * 32)
+solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
+    __shared__ long long start[kHist], cstart[kHist];
+    extern __shared__ __align__(16) double wsm[];
+    bucket_tables(a.hist, start, cstart);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / kWideLanes, l = lane % kWideLanes;
+    const int gb = warp * kWideGroups + g;                  // fit group of the block
+    double* A = wsm + (size_t)gb * kWideDoubles;
+    double* C0 = A + kWideTri;
+    double* C1 = C0 + RS_MAXPAIRS;
+    double* Ty = C1 + RS_MAXPAIRS;
+    double* T1 = Ty + RS_MAXPAIRS;
+    int* VS = reinterpret_cast<int*>(wsm + (size_t)kWideWarps * kWideGroups * kWideDoubles) + gb * RS_MAXPAIRS;
+    const long long lo = start[kNMid + 1], hi = start[RS_MAXPAIRS + 1];
+    for (;;) {
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(work, (unsigned long long)kWideGroups);
+        const long long pos = lo + (long long)__shfl_sync(0xffffffffu, got, 0) + g;
+        if (__shfl_sync(0xffffffffu, pos, 0) >= hi) break;
+        const bool active = pos < hi;
+        int n = 0;
+        uint4 rec = make_uint4(0, 0, 0, 0);
+        if (active) {
+            n = kNMid + 1;
+            while (start[n + 1] <= pos) ++n;
+            rec = a.recs[pos];
+        }
+        const int nw = __reduce_max_sync(0xffffffffu, n);
+        const int64_t f = rec.x;
+        const int64_t s = f / RS_NOPT;
+        const int j = (int)(f - s * RS_NOPT);
+        const int p = (int)rec.y;
+        const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+        const double* dl = a.dlam + (int64_t)p * RS_MAXV;
+        const int64_t pbase = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
+        double* out = active ? coef_out(a, f) : nullptr;
+        PredTarget ptv;
+        const PredTarget* pt = active && pred_target_v(a, s, j, p, (int)rec.w, ptv) ? &ptv : nullptr;
+        // the pairs of the fit: slot of the before version, label
+        for (int q = l; q < n; q += kWideLanes) {
+            const int bit = select_bit(rec.z, q);
+            VS[q] = a.pb[pbase + bit];
+            Ty[q] = a.ylab[pbase + bit];
+            T1[q] = 1.0;
+        }
+        __syncwarp();
+        {                                                    // M, lower triangle
+            int i, jj;
+            tri_pos(l, i, jj);
+            for (int e = l; e < tri(n); e += kWideLanes, tri_step(i, jj))
+                A[e] = i == jj ? __ldg(dl + VS[i]) : __ldg(Kp + VS[i] * RS_GRAM_LD + VS[jj]);
+        }
+        __syncwarp();
+        // Right-looking LDL^T with a one-pivot lookahead, and the forward substitution of both
+        // right-hand sides folded into the same sweep.  Step k: one lane forms the next pivot
+        // d_{k+1} first, so its reciprocal is issued before the trailing update instead of
+        // after it; the update of column k+1 also stores that column's L = S / d_{k+1} (and
+        // its S for step k+1, in the other pivot-column buffer); the right-hand sides take
+        // column k.  One warp barrier per pivot.  From its pivot on, a diagonal slot holds 1/d.
+        int st = active ? RS_FIT_OK : RS_FIT_EMPTY;
+        {
+            const bool kin = n > 0;
+            const double d = kin ? A[0] : 1.0;
+            if (kin && !pos_finite(d)) st = RS_FIT_NOTPD;
+            const bool go = kin && st == RS_FIT_OK;
+            const double r = rcp_newton(go ? d : 1.0);
+            if (go)
+                for (int i = 1 + l; i < n; i += kWideLanes) {
+                    const double c = A[tri(i)];
+                    C0[i] = c;
+                    A[tri(i)] = c * r;
+                }
+            __syncwarp();
+            if (go && l == 0) A[0] = r;
+        }
+        for (int k = 0; k + 1 < nw; ++k) {
+            const bool kin = k + 1 < n && st == RS_FIT_OK;
+            const double* Ck = (k & 1) ? C1 : C0;
+            double* Cn = (k & 1) ? C0 : C1;
+            double dn = 1.0;                                 // S_{k+1,k+1} - L_{k+1,k} S_{k+1,k}
+            if (kin && l == 0) dn = fma(-A[tri(k + 1) + k], Ck[k + 1], A[tri(k + 1) + k + 1]);
+            dn = __shfl_sync(0xffffffffu, dn, g * kWideLanes);
+            if (kin && !pos_finite(dn)) st = RS_FIT_NOTPD;
+            const bool go = kin && st == RS_FIT_OK;
+            const double rn = rcp_newton(go ? dn : 1.0);
+            if (go) {
+                // the work items of the step, dealt to the group's lanes round-robin across
+                // the three loops (o: the lane that takes a loop's first item)
+                const int m = n - k - 1;
+                int o = 0;
+                for (int ri = k + 2 + ((l - o) & (kWideLanes - 1)); ri < n; ri += kWideLanes) {
+                    const double v = fma(-A[tri(ri) + k], Ck[k + 1], A[tri(ri) + k + 1]);
+                    Cn[ri] = v;                              // column k+1: S for step k+1,
+                    A[tri(ri) + k + 1] = v * rn;             // L = S / d_{k+1}
+                }
+                o = (o + m - 1) & (kWideLanes - 1);
+                {                                            // rows and columns > k+1
+                    const int e0 = (l - o) & (kWideLanes - 1);
+                    int i, jj;
+                    tri_pos(e0, i, jj);
+                    for (int e = e0; e < tri(m - 1); e += kWideLanes, tri_step(i, jj)) {
+                        const int ri = k + 2 + i, cj = k + 2 + jj;
+                        A[tri(ri) + cj] = fma(-A[tri(ri) + k], Ck[cj], A[tri(ri) + cj]);
+                    }
+                }
+                o = (o + tri(m - 1)) & (kWideLanes - 1);
+                const double yk = Ty[k], ok1 = T1[k];        // t -= L_{.,k} t_k
+                for (int ri = k + 1 + ((l - o) & (kWideLanes - 1)); ri < n; ri += kWideLanes) {
+                    const double L = A[tri(ri) + k];
+                    Ty[ri] = fma(-L, yk, Ty[ri]);
+                    T1[ri] = fma(-L, ok1, T1[ri]);
+                }
+                if (l == 0) A[tri(k + 1) + k + 1] = rn;
+            }
+            __syncwarp();
+        }
+        const bool ok = active && st == RS_FIT_OK;
+        double num = 0.0, den = 0.0;
+        if (ok)
+            for (int i = l; i < n; i += kWideLanes) {
+                const double sc = T1[i] * A[tri(i) + i];
+                num = fma(sc, Ty[i], num);
+                den = fma(sc, T1[i], den);
+            }
+        num = group_sum(num);
+        den = group_sum(den);
+        const double b = num * rcp_newton(ok ? den : 1.0);
+        if (ok)
+            for (int i = l; i < n; i += kWideLanes) Ty[i] = fma(-b, T1[i], Ty[i]) * A[tri(i) + i];
+        __syncwarp();
+        for (int k = nw - 1; k >= 0; --k) {                  // L^T alpha = D^-1 (t_y - b t_1)
+            if (ok && k < n) {
+                const double ak = Ty[k];
+                for (int i = l; i < k; i += kWideLanes) Ty[i] = fma(-A[tri(k) + i], ak, Ty[i]);
+            }
+            __syncwarp();
+        }
+        bool bad = ok && !finite_bits(b);
+        if (ok)
+            for (int i = l; i < n; i += kWideLanes) bad = bad || !finite_bits(Ty[i]);
+        const unsigned gm = ((1u << kWideLanes) - 1u) << (g * kWideLanes);
+        const unsigned badm = __ballot_sync(0xffffffffu, bad);
+        if (ok && (badm & gm)) st = RS_FIT_NONFINITE;
+        if (out && st == RS_FIT_OK) {
+            if (l == 0) out[0] = b;
+            for (int i = l; i < n; i += kWideLanes) out[1 + i] = Ty[i];
+        }
+        // predictions b + sum_a alpha_a K[t][v_a], summed in pair order like every other
+        // solver; the group's lanes take the candidate rows in turn
+        if (pt && st == RS_FIT_OK) {
+            int c = 0;
+            for (uint64_t cm = pt->cand; cm; cm &= cm - 1, ++c) {
+                if (c % kWideLanes != l) continue;
+                const int t = __ffsll((long long)cm) - 1;
+                const double* Kt = Kp + t * RS_GRAM_LD;
+                double yh = b;
+                for (int q = 0; q < n; ++q) yh = fma(Ty[q], __ldg(Kt + VS[q]), yh);
+                const int r = __popcll(pt->test & ((1ull << t) - 1ull));
+                if (r < pt->room) pt->dst[r] = yh;
+            }
+        }
+        if (active && l == 0) {
+            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            finish_record(a, f, n, st, out);
+        }
+        count_status(a, st, active && l == 0);
+        __syncwarp();
+    }
+}
+
 // ====================================================================== rank pass
 // One thread per test row: its row record and its six predictions (written by the solve
 // kernels) go through rank_row; no FP64 arithmetic.
@@ -1682,8 +1916,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 // boundary (the rank pass copies row ranges of the planes with TMA bulk copies).
 int64_t plane_stride(int64_t Rcap) { return (Rcap + 1) & ~(int64_t)1; }
 
-// histogram + bucket cursors (unsigned) and four 64-bit work counters, zeroed per call
-constexpr size_t kCounterBytes = 2 * kHist * sizeof(unsigned) + 4 * sizeof(unsigned long long);
+// histogram + bucket cursors (unsigned) and five 64-bit work counters, zeroed per call
+constexpr size_t kCounterBytes = 2 * kHist * sizeof(unsigned) + 5 * sizeof(unsigned long long);
 
 FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     FitWs w{};
@@ -1844,10 +2078,17 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         }
         if (e == cudaSuccess && mid) e = launch_mid(sa, sms, nmax < kNMid ? nmax : kNMid, w.work + 2, s2);
         if (e == cudaSuccess && nmax > kNMid) {
-            const size_t lsmem = (size_t)2 * kLargeWarps * 32 * 33 * sizeof(double);
-            e = cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem);
+            // kWideGroups fits per warp, persistent blocks taking their fits dynamically
+            e = cudaFuncSetAttribute(solve_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideSmem);
+            int per_sm = 0;
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_wide_kernel, kWideWarps * 32, kWideSmem);
             if (e == cudaSuccess) {
-                solve_large_kernel<<<(unsigned)(sms * 4), kLargeWarps * 32, lsmem, s2>>>(sa);
+                int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+                const int64_t need = (S6 + kWideWarps * kWideGroups - 1) / (kWideWarps * kWideGroups);
+                if (grid > need) grid = need;
+                if (grid < 1) grid = 1;
+                solve_wide_kernel<<<(unsigned)grid, kWideWarps * 32, kWideSmem, s2>>>(sa, w.work + 4);
                 e = cudaGetLastError();
             }
         }

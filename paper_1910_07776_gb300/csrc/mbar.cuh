@@ -41,17 +41,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: true when the phase completed, false (and RS_ETIMEOUT flagged) after 1 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, int site) {
+// Bounded wait: true when the phase completed, false (and RS_ETIMEOUT flagged with the
+// caller's site number) after limit_ns of %globaltimer.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t phase, int* err, int site,
+                                              unsigned long long limit_ns) {
     if (mbar_try_wait(bar, phase)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
         if (mbar_try_wait(bar, phase)) return true;
-        if (gtime() - t0 > kWaitNs) {
+        if (gtime() - t0 > limit_ns) {
             rs_dev_flag(err, RS_ETIMEOUT, site);
             return false;
         }
     }
+}
+// The kernels' wait: bounded by 1 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, int site) {
+    return mbar_wait_for(bar, phase, err, site, kWaitNs);
 }
 // 1-D bulk copy global -> shared (TMA, non-tensor form), completing on the mbarrier's
 // transaction count.  Both addresses 16-byte aligned, bytes a multiple of 16.

@@ -46,14 +46,19 @@ __device__ __forceinline__ double f64_of(float f) {
 }
 
 // 1/sqrt(d) for a positive finite d: FP32 seed, then two Newton steps of r <- r (3 - d r^2) / 2
-// (Newton's method on f(r) = r^-2 - d).  Outside [1e-30, 1e30]: plain division.
+// (Newton's method on f(r) = r^-2 - d).  The second step takes the residual 1/2 - (d/2) r^2
+// from the exact square r^2 = s + s_lo (s_lo = fma(r, r, -s), Dekker's product), so the
+// correction r e adds no more than the final rounding of r + r e.  Outside [1e-30, 1e30]:
+// plain division.
 __device__ __forceinline__ double rsqrt_newton(double d) {
     if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);
     const double hd = 0.5 * d;
     double r = f64_of(rsqrtf(f32_of(d)));
     r = r * fma(-hd, r * r, 1.5);
-    r = r * fma(-hd, r * r, 1.5);
-    return r;
+    const double s = r * r;
+    const double s_lo = fma(r, r, -s);
+    const double e = fma(-hd, s_lo, fma(-hd, s, 0.5));
+    return fma(r, e, r);
 }
 
 // Bit patterns of 2^-100 and 2^100 (positive doubles are ordered like their bit patterns).

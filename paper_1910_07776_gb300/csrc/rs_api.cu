@@ -42,26 +42,13 @@ rs_status cuda_fail(rs_ctx* c, cudaError_t e, const char* where) {
 }
 
 rs_status check_batch(rs_ctx* c, const rs_batch* b, bool need_raw) {
-    if (!b) return fail(c, RS_EINVAL, "batch is NULL");
-    if (b->n_programs < 1) return fail(c, RS_EINVAL, "n_programs must be >= 1");
-    if (b->max_versions < 1 || b->max_versions > RS_MAXV)
-        return fail(c, RS_EINVAL, "max_versions must be in 1..64");
-    if (b->max_feat < 1 || b->max_feat > 4096) return fail(c, RS_EINVAL, "max_feat must be in 1..4096");
-    if (!b->row_offsets || !b->feat_width || !b->x_offsets || !b->X || !b->masks || !b->log_time)
-        return fail(c, RS_EINVAL, "a required batch pointer is NULL");
-    if (need_raw && b->dtype != RS_F32 && b->dtype != RS_F64)
-        return fail(c, RS_EINVAL, "dtype must be RS_F32 or RS_F64");
-    if ((uintptr_t)b->X % (b->dtype == RS_F32 ? 4 : 8) != 0) return fail(c, RS_EINVAL, "X is misaligned");
-    return RS_OK;
+    const char* why = rs_batch_problem(b, need_raw);
+    return why ? fail(c, RS_EINVAL, "%s", why) : RS_OK;
 }
 
 rs_status check_splits(rs_ctx* c, const rs_splits* s) {
-    if (!s) return fail(c, RS_EINVAL, "splits is NULL");
-    if (s->n_splits < 0) return fail(c, RS_EINVAL, "n_splits must be >= 0");
-    if (s->n_splits > 0 && (!s->split_offsets || !s->train_masks))
-        return fail(c, RS_EINVAL, "a required splits pointer is NULL");
-    if (s->n_splits > (int64_t)4096 * 4096) return fail(c, RS_EINVAL, "at most 16,777,216 splits per call");
-    return RS_OK;
+    const char* why = rs_splits_problem(s);
+    return why ? fail(c, RS_EINVAL, "%s", why) : RS_OK;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -310,13 +297,18 @@ rs_status rs_fit_batched(rs_ctx* c, const rs_batch* b, const double* K, const rs
                          double lambda, int form, void* workspace, size_t workspace_bytes,
                          double* coef, uint8_t* fit_status) {
     if (!c) return RS_EINVAL;
+    const int refine = form & RS_REFINE_X;
+    form &= ~RS_REFINE_X;
     rs_fit_args a;
     rs_status s = fit_common(c, b, K, sp, lambda, form, a);
     if (s != RS_OK) return s;
+    if (refine && form != RS_FORM_BATCHED) return fail(c, RS_EINVAL, "RS_REFINE_X needs the batched form");
+    if (refine && b->max_feat > 4096) return fail(c, RS_EINVAL, "RS_REFINE_X: max_feat <= 4096");
     if (form == RS_FORM_BATCHED) {
         s = check_ws(c, b, sp, workspace, workspace_bytes, a);
         if (s != RS_OK) return s;
     }
+    a.flags |= refine;
     a.coef_out = coef;
     a.status_out = fit_status;
     a.k = 1;
@@ -440,6 +432,113 @@ rs_status rs_surrogate_infer(rs_ctx* c, const float* blob, const double* X, int6
                                               c->stream);
     if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_surrogate_infer");
+}
+
+}  // extern "C"
+
+namespace {
+
+// The fallback's scratch inside the caller's workspace, sized for the whole batch (every
+// program selected), 256-byte aligned pieces; base == nullptr only measures.
+rs_fallback_ws carve_fallback(void* base, const rs_batch* b, const rs_splits* sp) {
+    rs_fallback_ws w{};
+    char* c = (char*)base;
+    size_t o = 0;
+    auto take = [&](size_t n) -> void* {
+        void* p = c ? (void*)(c + o) : nullptr;
+        o += align256(n > 0 ? n : 1);
+        return p;
+    };
+    const int64_t P = b->n_programs, S = sp->n_splits;
+    const int64_t rows_cap = sp->n_test_rows > 0 ? sp->n_test_rows : S * (int64_t)b->max_versions;
+    const size_t es = b->dtype == RS_F32 ? 4 : 8;
+    w.totals = (long long*)take(8 * sizeof(long long));
+    w.prog_map = (int32_t*)take((size_t)P * sizeof(int32_t));
+    w.sub_prog = (int32_t*)take((size_t)P * sizeof(int32_t));
+    w.sub_row_off = (int64_t*)take((size_t)(P + 1) * sizeof(int64_t));
+    w.sub_x_off = (int64_t*)take((size_t)P * sizeof(int64_t));
+    w.sub_feat_off = (int64_t*)take((size_t)(P + 1) * sizeof(int64_t));
+    w.sub_split_off = (int64_t*)take((size_t)(P + 1) * sizeof(int64_t));
+    w.sub_fw = (int32_t*)take((size_t)P * sizeof(int32_t));
+    w.sX = take((size_t)b->x_elems * es);
+    w.s_masks = (uint8_t*)take((size_t)b->n_rows);
+    w.s_lt = (double*)take((size_t)b->n_rows * sizeof(double));
+    w.s_cyc = (double*)take((size_t)b->n_rows * sizeof(double));
+    w.s_train = (uint64_t*)take((size_t)S * sizeof(uint64_t));
+    w.s_rec_off = (int64_t*)take((size_t)(S + 1) * sizeof(int64_t));
+    w.s_code = (uint32_t*)take((size_t)rows_cap * sizeof(uint32_t));
+    w.s_pred = (double*)take((size_t)rows_cap * RS_NOPT * sizeof(double));
+    w.cv_ws_bytes = rs_cv_workspace_bytes(b, sp);
+    w.cv_ws = take(w.cv_ws_bytes);
+    w.bytes = o;
+    return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rs_fallback_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
+    if (rs_batch_problem(b, true) || rs_splits_problem(sp)) return 0;
+    return carve_fallback(nullptr, b, sp).bytes;
+}
+
+rs_status rs_surrogate_fallback(rs_ctx* c, const rs_batch* b, const rs_splits* sp, const uint8_t* used_fallback,
+                                double lambda, int k, double tau, int flags, void* ws, size_t ws_bytes,
+                                uint32_t* rec_code, double* rec_pred, int64_t* refit) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, true);
+    if (s == RS_OK) s = check_splits(c, sp);
+    if (s != RS_OK) return s;
+    if (!used_fallback || !rec_code) return fail(c, RS_EINVAL, "used_fallback and rec_code are required");
+    if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(c, RS_EINVAL, "lambda must be finite and >= 0");
+    if (flags & ~RS_RANK_ALL) return fail(c, RS_EINVAL, "flags: RS_RANK_ALL only");
+    if (!ws || (uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    const size_t need = carve_fallback(nullptr, b, sp).bytes;
+    if (ws_bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    const rs_fallback_ws w = carve_fallback(ws, b, sp);
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemsetAsync(w.totals, 0, 8 * sizeof(long long), c->stream);
+    if (e == cudaSuccess) e = rs_launch_fallback_select(b, sp, used_fallback, w, c->stream);
+    long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tot, w.totals, sizeof(tot), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);     // the sub-batch's sizes
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_surrogate_fallback (selection)");
+    const int Q = (int)tot[0];
+    if (Q > 0) {
+        e = rs_launch_fallback_gather(b, sp, Q, w, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rs_surrogate_fallback (gather)");
+        rs_batch sb = *b;
+        sb.n_programs = Q;
+        sb.n_rows = tot[1];
+        sb.x_elems = tot[2];
+        sb.feat_total = tot[5];
+        sb.row_offsets = w.sub_row_off;
+        sb.feat_width = w.sub_fw;
+        sb.x_offsets = w.sub_x_off;
+        sb.feat_offsets = w.sub_feat_off;
+        sb.X = w.sX;
+        sb.masks = w.s_masks;
+        sb.log_time = w.s_lt;
+        sb.cycles = b->cycles ? w.s_cyc : nullptr;
+        rs_splits ss = *sp;
+        ss.n_splits = tot[3];
+        ss.n_test_rows = tot[4];
+        ss.split_offsets = w.sub_split_off;
+        ss.train_masks = w.s_train;
+        s = rs_cv_step(c, &sb, &ss, lambda, k, tau, flags, RS_GRAM_F64, w.cv_ws, w.cv_ws_bytes, w.s_rec_off,
+                       w.s_code, w.s_pred, nullptr, nullptr);
+        if (s != RS_OK) return s;
+        e = rs_launch_fallback_merge(b, used_fallback, w, k, rec_code, rec_pred, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "rs_surrogate_fallback (merge)");
+    }
+    if (refit) {
+        refit[0] = Q;
+        refit[1] = tot[1];
+    }
+    return RS_OK;
 }
 
 size_t rs_cv_workspace_bytes(const rs_batch* b, const rs_splits* sp) {

@@ -31,6 +31,31 @@ __device__ __forceinline__ int rs_find_segment(const int64_t* offs, int P, int64
     return lo;
 }
 
+// Host-side argument rules shared by every entry point that takes a batch or a set of splits:
+// nullptr when the arguments are acceptable, else the reason.
+inline const char* rs_batch_problem(const rs_batch* b, bool need_raw) {
+    if (!b) return "batch is NULL";
+    if (b->n_programs < 1) return "n_programs must be >= 1";
+    if (b->max_versions < 1 || b->max_versions > RS_MAXV) return "max_versions must be in 1..64";
+    if (b->max_feat < 1 || b->max_feat > 4096) return "max_feat must be in 1..4096";
+    if (b->x_elems < 0) return "x_elems must be >= 0";
+    if (!b->row_offsets || !b->feat_width || !b->x_offsets || !b->X || !b->masks || !b->log_time)
+        return "a required batch pointer is NULL";
+    if (need_raw && b->dtype != RS_F32 && b->dtype != RS_F64) return "dtype must be RS_F32 or RS_F64";
+    if ((uintptr_t)b->X % (b->dtype == RS_F32 ? 4 : 8) != 0) return "X is misaligned";
+    return nullptr;
+}
+inline const char* rs_splits_problem(const rs_splits* s) {
+    if (!s) return "splits is NULL";
+    if (s->n_splits < 0) return "n_splits must be >= 0";
+    if (s->n_splits > 0 && (!s->split_offsets || !s->train_masks)) return "a required splits pointer is NULL";
+    if (s->n_splits > (int64_t)4096 * 4096) return "at most 16,777,216 splits per call";
+    if (s->max_train < 0 || s->max_train > RS_MAXV) return "max_train must be in 0..64";
+    if (s->n_test_rows < 0 || s->n_test_rows > s->n_splits * (int64_t)RS_MAXV)
+        return "n_test_rows must be in 0..64 * n_splits";
+    return nullptr;
+}
+
 __device__ __forceinline__ uint64_t rs_full_mask(int V) {
     return V >= 64 ? ~0ull : ((1ull << V) - 1ull);
 }
@@ -78,6 +103,35 @@ cudaError_t rs_launch_gram_bf16x3_ws(const rs_batch* b, double* K, void* ws, siz
 cudaError_t rs_launch_rec_offsets(const rs_batch* b, const rs_splits* s, int64_t* rec_offsets,
                                   int64_t* scratch_blocksums, int* dstatus, cudaStream_t st);
 size_t rs_rec_offsets_scratch_elems(int64_t n_splits);
+
+// The surrogate's plain fallback (k_fallback.cu): scratch carved from the caller's workspace.
+struct rs_fallback_ws {
+    long long* totals;        // [8]: programs, rows, X elements, splits, test rows, features, merged rows
+    int32_t* prog_map;        // [P] sub-batch index of each program, -1 if not selected
+    int32_t* sub_prog;        // [P] program of each sub-batch entry
+    int64_t* sub_row_off;     // [P+1]
+    int64_t* sub_x_off;       // [P]
+    int64_t* sub_feat_off;    // [P+1]
+    int64_t* sub_split_off;   // [P+1]
+    int32_t* sub_fw;          // [P]
+    void* sX;                 // the selected programs' X
+    uint8_t* s_masks;
+    double* s_lt;
+    double* s_cyc;
+    uint64_t* s_train;
+    int64_t* s_rec_off;       // [S+1]
+    uint32_t* s_code;         // [rows cap]
+    double* s_pred;           // [rows cap][k]
+    void* cv_ws;              // rs_cv_step's workspace for the sub-batch
+    size_t cv_ws_bytes;
+    size_t bytes;             // total
+};
+cudaError_t rs_launch_fallback_select(const rs_batch* b, const rs_splits* sp, const uint8_t* used,
+                                      const rs_fallback_ws& w, cudaStream_t st);
+cudaError_t rs_launch_fallback_gather(const rs_batch* b, const rs_splits* sp, int Q, const rs_fallback_ws& w,
+                                      cudaStream_t st);
+cudaError_t rs_launch_fallback_merge(const rs_batch* b, const uint8_t* used, const rs_fallback_ws& w, int k,
+                                     uint32_t* rec_code, double* rec_pred, cudaStream_t st);
 
 struct rs_fit_args {
     // batch (standardized)

@@ -6,11 +6,16 @@
 //
 // g_rs_scratch below lives in device memory for as long as the library stays loaded (on
 // every GPU that loads this module).  Host code must not use its name as an address: the
-// device address is looked up once per device with cudaGetSymbolAddress and cached.
+// device address is looked up with cudaGetSymbolAddress, with the device current, and cached
+// per device together with the identity of the CUDA context it belongs to.  A context torn
+// down and created again (cudaDeviceReset, for one) reloads the module, so a changed context
+// identity triggers a fresh lookup instead of reusing a stale address.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <cuda.h>
 
 #include <mutex>
 
@@ -21,20 +26,55 @@ static __device__ __align__(256) unsigned char g_rs_scratch[RS_STATIC_SCRATCH_BY
 namespace {
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+    unsigned long long ctx_id;   // identity of the context the address was looked up in
+    void* addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// The unique identity of the current context, 0 if there is none or it cannot be read (then
+// the address is looked up again on every call).  Called with g_scratch_mu held.
+unsigned long long current_context_id() {
+    static bool resolved = false;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!resolved) {
+        resolved = true;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    unsigned long long id = 0;
+    return get_id(ctx, &id) == CUDA_SUCCESS ? id : 0;
+}
+
 // The device address of g_rs_scratch on device `dev` (which must be current): looked up on
-// the first call for that device, cached afterwards.
+// the first call in each context of that device, cached afterwards.
 cudaError_t scratch_address(int dev, void** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    ScratchSlot& slot = g_slot[dev];
+    if (!slot.addr || id == 0 || id != slot.ctx_id) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_rs_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        slot.addr = p;
+        slot.ctx_id = current_context_id();   // the lookup may have created the context
     }
-    *out = g_scratch_addr[dev];
+    *out = slot.addr;
     return cudaSuccess;
 }
 
@@ -59,22 +99,20 @@ extern "C" rs_status rs_cv_step_static(void* cuda_stream, const rs_batch* b, con
                                        char* errbuf, size_t errbuf_len) {
     if (errbuf && errbuf_len) errbuf[0] = 0;
     // ---- arguments (the same rules as rs_cv_step)
-    if (!b || !sp) return say(errbuf, errbuf_len, RS_EINVAL, "batch or splits is NULL");
-    if (b->n_programs < 1 || b->max_versions < 1 || b->max_versions > RS_MAXV || b->max_feat < 1 ||
-        b->max_feat > 4096 || b->x_elems < 0)
-        return say(errbuf, errbuf_len, RS_EINVAL, "batch sizes out of range");
-    if (!b->row_offsets || !b->feat_width || !b->x_offsets || !b->X || !b->masks || !b->log_time)
-        return say(errbuf, errbuf_len, RS_EINVAL, "a required batch pointer is NULL");
-    if (b->dtype != RS_F32 && b->dtype != RS_F64)
-        return say(errbuf, errbuf_len, RS_EINVAL, "dtype must be RS_F32 or RS_F64");
-    if (sp->n_splits < 0 || sp->n_splits > (int64_t)4096 * 4096 || sp->max_train < 0 || sp->max_train > 64 ||
-        (sp->n_splits > 0 && (!sp->split_offsets || !sp->train_masks)))
-        return say(errbuf, errbuf_len, RS_EINVAL, "bad splits");
+    const char* why = rs_batch_problem(b, true);
+    if (!why) why = rs_splits_problem(sp);
+    if (why) return say(errbuf, errbuf_len, RS_EINVAL, "%s", why);
     if (!(lambda >= 0.0) || lambda > 1e300) return say(errbuf, errbuf_len, RS_EINVAL, "lambda must be >= 0");
     if (k < 1 || k > RS_NOPT) return say(errbuf, errbuf_len, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || tau > 1e300) return say(errbuf, errbuf_len, RS_EINVAL, "tau must be > 0");
     if (flags & ~RS_RANK_ALL) return say(errbuf, errbuf_len, RS_EINVAL, "only RS_RANK_ALL is accepted");
     if (!rec_offsets || !rec_code) return say(errbuf, errbuf_len, RS_EINVAL, "rec_offsets and rec_code are required");
+    // sizes that cannot fit are refused before any product of them is formed
+    if (b->x_elems > (int64_t)(RS_STATIC_SCRATCH_BYTES / sizeof(double)) ||
+        b->n_programs > (int64_t)(RS_STATIC_SCRATCH_BYTES / (RS_GRAM_LD * RS_GRAM_LD * sizeof(double))) ||
+        sp->n_splits > (int64_t)(RS_STATIC_SCRATCH_BYTES / (RS_NOPT * sizeof(uint32_t))))
+        return say(errbuf, errbuf_len, RS_ENOMEM, "this batch cannot fit in the static scratch (%zu bytes)",
+                   (size_t)RS_STATIC_SCRATCH_BYTES);
 
     // ---- scratch layout inside g_rs_scratch: status words | scan sums | Z | K | fit workspace
     const int64_t rows_cap = sp->n_test_rows > 0 ? sp->n_test_rows : sp->n_splits * (int64_t)b->max_versions;

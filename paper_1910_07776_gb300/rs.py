@@ -37,6 +37,7 @@ EXPORTS = [
     "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
     "rs_surrogate_train", "rs_surrogate_infer", "rs_cv_graph_create", "rs_cv_graph_launch",
     "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning", "rs_set_tuning", "rs_transfer", "rs_transfer_workspace_bytes",
+    "rs_check_reciprocals", "rs_check_wait_timeout", "rs_fallback_workspace_bytes", "rs_surrogate_fallback",
 ]
 
 
@@ -106,6 +107,11 @@ def load(path: str = SO):
     L.rs_cv_workspace_bytes.restype = C.c_size_t
     L.rs_cv_step.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
+    L.rs_check_reciprocals.argtypes = [P, i64, P, P]
+    L.rs_check_wait_timeout.argtypes = [P, P, i64, P]
+    L.rs_fallback_workspace_bytes.argtypes = [P, P]
+    L.rs_fallback_workspace_bytes.restype = C.c_size_t
+    L.rs_surrogate_fallback.argtypes = [P, P, P, P, d, i, d, i, P, C.c_size_t, P, P, C.POINTER(i64)]
     L.rs_cv_step_static.argtypes = [P, P, P, d, i, d, i, P, P, P, P, P, P, C.c_char_p, C.c_size_t]
     L.rs_gemm_bf16.argtypes = [P, P, i64, P, i64, P, i64, i, i, i]
     L.rs_cv_graph_create.argtypes = [P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P, C.POINTER(P)]
@@ -130,6 +136,7 @@ def load(path: str = SO):
     L.rs_transfer.argtypes = [P, P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes", "rs_gram_workspace_bytes",
+                        "rs_fallback_workspace_bytes",
                         "rs_transfer_workspace_bytes", "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
@@ -364,7 +371,9 @@ class Context:
 
     def fit_batched(self, zb: DeviceBatch, K, s: DeviceSplits, lam: float = 1e-3,
                     form: int = RS_FORM_BATCHED, coef=None, fit_status=None, workspace=None):
-        if workspace is None and form == RS_FORM_BATCHED:
+        """form: RS_FORM_BATCHED or RS_FORM_PLAIN; RS_FORM_BATCHED | RS_REFINE_X refines each fit
+        once through the standardized features of zb."""
+        if workspace is None and (form & ~RS_REFINE_X) == RS_FORM_BATCHED:
             workspace = self.workspace(self.fit_workspace_bytes(zb, s))
         bc, sc = zb.c(), s.c()
         wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
@@ -398,6 +407,23 @@ class Context:
             self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags),
             int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
+
+    def fallback_workspace_bytes(self, b: DeviceBatch, s: DeviceSplits) -> int:
+        bc, sc = b.c(), s.c()
+        return int(self.L.rs_fallback_workspace_bytes(C.byref(bc), C.byref(sc)))
+
+    def surrogate_fallback(self, b: DeviceBatch, s: DeviceSplits, used_fallback, rec_code, rec_pred=None,
+                           lam: float = 1e-3, k: int = 3, tau: float = 1.05, flags: int = 0, workspace=None):
+        """rs_surrogate_fallback: the flagged rows of b re-ranked by the plain pass over their
+        programs' splits; returns (programs refitted, versions refitted)."""
+        if workspace is None:
+            workspace = self.workspace(self.fallback_workspace_bytes(b, s))
+        bc, sc = b.c(), s.c()
+        refit = (C.c_int64 * 2)()
+        self._check(self.L.rs_surrogate_fallback(
+            self.h, C.byref(bc), C.byref(sc), _ptr(used_fallback), float(lam), int(k), float(tau), int(flags),
+            _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(rec_code), _ptr(rec_pred), refit))
+        return int(refit[0]), int(refit[1])
 
     def transfer_workspace_bytes(self, train: DeviceBatch, test: DeviceBatch, groups=None, flags: int = 0) -> int:
         ac, bc = train.c(), test.c()
@@ -485,6 +511,18 @@ class Surrogate:
             _ptr(masks), int(k), float(tau), int(flags), _ptr(rec_code), _ptr(rec_pred),
             _ptr(self.iws), self.iws.numel(), int(chunk_rows or self.infer_chunk)))
         return pred, score, fb
+
+
+def check_reciprocals(d: torch.Tensor) -> torch.Tensor:
+    """[n][4]: the solvers' reciprocal and reciprocal square root of each positive double in
+    d, beside CUDA's 1.0 / d and 1.0 / sqrt(d) (rs_check_reciprocals)."""
+    L = load()
+    out = torch.empty(d.numel(), 4, dtype=torch.float64, device=d.device)
+    st = L.rs_check_reciprocals(_ptr(d), d.numel(), _ptr(out),
+                                C.c_void_p(torch.cuda.current_stream(d.device).cuda_stream))
+    if st != RS_OK:
+        raise RsError(st, "rs_check_reciprocals failed")
+    return out
 
 
 def measure_fma_peak(f64: bool = True, iters: int = 4096) -> float:

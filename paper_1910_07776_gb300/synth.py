@@ -550,3 +550,38 @@ def table2_problems(runs: ProgramBatch, experiment: int) -> TransferProblems:
         experiment=experiment, train=take_programs(runs, train_list),
         test=take_programs(runs, [te for _, te, _ in probs]), groups=groups,
         opt_mask=SHARED_OPTS if experiment in (5, 6) else 0x3F, pairs=[d for _, _, d in probs])
+
+
+def init_mlp_params(seed: int = 0, dims=(256, 512, 512, 6)):
+    """Seeded initial weights of the surrogate MLP: W_i [fan_out][fan_in] and b_i [fan_out]
+    uniform in (-1/sqrt(fan_in), 1/sqrt(fan_in)).  Random inputs, no arithmetic of the method."""
+    import math
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5A5A))
+    p = {}
+    for i in range(3):
+        fi, fo = dims[i], dims[i + 1]
+        s = 1.0 / math.sqrt(fi)
+        p[f"W{i + 1}"] = rng.uniform(-s, s, size=(fo, fi))
+        p[f"b{i + 1}"] = rng.uniform(-s, s, size=fo)
+    return p
+
+
+def with_anomalous_versions(batch: ProgramBatch, frac_programs: float, per_program: int = 3,
+                            factor: float = float(np.exp(4.0)), seed: int = 0):
+    """A copy of ``batch`` in which a random ``frac_programs`` of the programs have
+    ``per_program`` random versions whose every counter is multiplied by ``factor`` (profiles
+    unlike the rest of their program: out-of-distribution rows for a learned predictor).
+    Returns (batch, sorted array of the affected programs)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0xA70A))
+    P = batch.n_programs
+    progs = np.sort(rng.choice(P, size=max(1, int(round(frac_programs * P))), replace=False))
+    X = batch.X.copy()
+    for p in progs:
+        V, F, o = batch.versions(int(p)), int(batch.feat_width[p]), int(batch.x_offsets[p])
+        for v in rng.choice(V, size=min(per_program, V), replace=False):
+            X[o + int(v) * F:o + (int(v) + 1) * F] *= X.dtype.type(factor)
+    out = ProgramBatch(X=X, x_offsets=batch.x_offsets.copy(), row_offsets=batch.row_offsets.copy(),
+                       feat_width=batch.feat_width.copy(), masks=batch.masks.copy(),
+                       log_time=batch.log_time.copy(),
+                       cycles=None if batch.cycles is None else batch.cycles.copy(), meta=dict(batch.meta))
+    return out, progs

@@ -1,5 +1,6 @@
-"""The benchmark's multi-rank path (one batch per rank, weak scaling, time = slowest rank,
-work = sum over ranks) with two gloo ranks on the CPU."""
+"""The benchmark's multi-rank path (a job of N workloads split over N ranks by the longest-
+processing-time rule, weak scaling, time = slowest rank, work = sum over ranks) with two gloo
+ranks on the CPU."""
 import os
 import socket
 
@@ -19,10 +20,8 @@ def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    from paper_1910_07776_gb300 import synth
-    # each rank draws its own batch (seed = rank), as bench.py does under torchrun
-    b = synth.make_batch(2, versions=(16, 64), feat=16, seed=rank)
-    s = synth.make_half_splits_fast(b, 8, seed=rank)
+    # each rank takes its share of the job, as bench.py does under torchrun
+    b, s = bench.rank_inputs(rank, world)
     import oracle
     recs = int(oracle.rec_offsets(b, s)[-1])
     ms = 10.0 * (rank + 1)
@@ -44,7 +43,11 @@ def test_two_gloo_ranks_aggregate_like_the_benchmark():
         assert p.exitcode == 0
     out.sort()
     total = sum(o[1] for o in out)
+    import bench
+    import oracle
+    b, s = bench.make_inputs(bench.CFG["seed"], 2 * bench.CFG["programs"])
+    assert total == int(oracle.rec_offsets(b, s)[-1])     # the shares cover the whole job
     for rank, recs, t, r in out:
         assert t == 20.0            # the slowest rank's time
         assert r == total           # all ranks' recommendations
-    assert out[0][1] != out[1][1]   # different batches per rank
+    assert abs(out[0][1] - out[1][1]) < 0.02 * total     # balanced shares
