@@ -569,6 +569,14 @@ def main():
     if rank == 0 and not args.only_step and not args.no_transfer:
         xfer = run_transfer(rs, ctx, dev, stream, flush, args)
 
+    pooled = None
+    if rank == 0 and not args.only_step and not args.no_transfer:
+        pooled = run_pooled(rs, ctx, batch, dev, stream, flush, args)
+
+    real = None
+    if rank == 0 and not args.only_step and not args.no_transfer:
+        real = run_real_nb(rs, ctx, dev, stream, flush, args)
+
     unev = None
     if rank == 0 and not args.only_step and not args.no_uneven:
         unev = run_uneven(rs, ctx, dev, stream, flush, args)
@@ -613,6 +621,8 @@ def main():
         "ibk_form": ibk,
         "lovo_form": lovo,
         "table2_transfer": xfer,
+        "real_nb": real,
+        "pooled_form": pooled,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -806,71 +816,163 @@ PAPER_TABLE3_IBK = {1: 97.3, 2: 96.0, 3: 96.3, 4: 92.0, 5: 83.6, 6: 55.7}   # Ta
 PAPER_TABLE3_M5P = {1: 86.4, 2: 86.4, 3: 33.3, 4: 81.6, 5: 33.3, 6: 60.1}
 
 
-def run_transfer(rs, ctx, dev, stream, flush, args):
-    """Table 2's six experiments (Sec. 5) on the seeded stand-ins of the BH / NB runs
-    (synth.make_runs: 6 + 4 inputs x 3 runs x 64 versions x 96 counters): per experiment and
-    learner (ridge, IBK, M5P) one rs_transfer call (device time, after warm-up), the sign
-    accuracy of Table 3,
-    the top-1 hit rate, and the AC/EX ratios (actual over expected speedup, Sec. 5) of every
-    scored prediction.  Table 3's values come from the paper's real profiles: context only."""
+def run_pooled(rs, ctx, batch, dev, stream, flush, args):
+    """Pooled ridge in primal form (rs_fit_pooled): one model per optimization trained on the
+    pairs of 48 programs of the batched-CV workload (256 features; the Gram X^T W X of each
+    optimization's ~600 pairs as one batched tcgen05 GEMM of the BF16 hi/lo split, FP64
+    Cholesky, one FP64 refinement step), then ranking the 16 held-out programs' versions
+    (rs_predict_pooled) -- a model trained on other codes, as in Sec. 5's transfer."""
     import torch
     from paper_1910_07776_gb300 import synth
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tr = synth.take_programs(batch, list(range(48)))
+    te = synth.take_programs(batch, list(range(48, 64)))
+    dtr, dte = rs.DeviceBatch.from_host(tr, dev), rs.DeviceBatch.from_host(te, dev)
+    ztr = dtr.with_X(ctx.standardize(dtr))
+    zte = dte.with_X(ctx.standardize(dte))
+    ws = ctx.workspace(ctx.pooled_workspace_bytes(ztr))
+    fit = lambda: ctx.fit_pooled(ztr, None, lam=CFG["lam"], flags=rs.RS_REFINE_X, workspace=ws)
+    for _ in range(3):
+        coef, st = fit()
+    torch.cuda.synchronize()
+    reps, tot = 10, 0.0
+    for _ in range(reps):
+        flush.fill_(1)
+        e0.record(stream)
+        coef, st = fit()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    n = zte.n_rows
+    code = torch.empty(n, dtype=torch.int32, device=dev)
+    rp = torch.empty(n * CFG["k"], dtype=torch.float64, device=dev)
+    cnt = torch.zeros(16, dtype=torch.int64, device=dev)
+    ctx.predict_pooled(zte, coef, st, code, k=CFG["k"], tau=CFG["tau"], rec_pred=rp, counters=cnt)
+    torch.cuda.synchronize()
+    ctx.check_device_status()
+    c = cnt.cpu().numpy().astype(np.float64)
+    pairs = [sum(1 for p in range(tr.n_programs) for v in range(tr.versions(p))
+                 for mm in [tr.masks[tr.program_rows(p)].astype(int)]
+                 if not (mm[v] >> j) & 1 and (mm[v] | 1 << j) in set(mm.tolist())) for j in range(6)]
+    Np = (max(pairs) + 63) // 64 * 64
+    F = int(tr.feat_width[0])
+    gemm_flops = 6 * F * F * 3 * Np * 2
+    return {"workload": "pooled ridge: 48 programs of the batched-CV workload train (256 f32 features), "
+                        "16 held-out programs ranked",
+            "fit_ms": tot / reps, "pairs_per_optimization": pairs, "status": st.cpu().numpy().tolist(),
+            "gram_gemm_flops": gemm_flops,
+            "held_out": {"rows": n, "sign_accuracy": c[3] / max(c[2], 1), "top1_hit_rate": c[8] / max(c[7], 1),
+                         "rec_precision": c[6] / max(c[5], 1)}}
+
+
+def _transfer_experiment(rs, ctx, dev, stream, flush, pr, e):
+    """One Table 2 experiment: per learner (ridge, IBK, M5P) one rs_transfer call timed on the
+    device after warm-up, the sign accuracy of Table 3, the top-1 hit rate and the AC/EX ratios
+    (actual over expected speedup, Sec. 5) of every scored prediction."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dtr = rs.DeviceBatch.from_host(pr.train, dev)
+    dte = rs.DeviceBatch.from_host(pr.test, dev)
+    offs = torch.from_numpy(pr.groups).to(dev)
+    g = (offs, int(np.diff(pr.groups).max()))
+    ws = ctx.workspace(ctx.transfer_workspace_bytes(dtr, dte, g, rs.RS_MODEL_M5P))
+    R = dte.n_rows
+    # actual log speedups of the test rows (host, from the test set's own times)
+    act = np.full((R, 6), np.nan)
+    for q in range(pr.test.n_programs):
+        rows = pr.test.program_rows(q)
+        m = pr.test.masks[rows].astype(int)
+        lt = pr.test.log_time[rows]
+        slot = {int(v): i for i, v in enumerate(m)}
+        for t in range(len(m)):
+            for j in range(6):
+                w = slot.get(int(m[t]) | (1 << j))
+                if not (m[t] >> j) & 1 and w is not None:
+                    act[rows.start + t, j] = lt[t] - lt[w]
+    res = {"problems": int(pr.test.n_programs), "train_runs_per_problem": int(np.diff(pr.groups).max()),
+           "test_rows": int(R), "opt_mask": int(pr.opt_mask), "paper_ibk_accuracy_pct": PAPER_TABLE3_IBK[e],
+           "paper_m5p_accuracy_pct": PAPER_TABLE3_M5P[e]}
+    for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK), ("m5p", rs.RS_MODEL_M5P)):
+        o = rs.alloc_outputs(R, 0, CFG["k"], dev)
+        call = lambda: ctx.transfer(dtr, dte, ws, o.rec_code, groups=g, lam=CFG["lam"], k=CFG["k"],
+                                    tau=CFG["tau"], flags=flags, opt_mask=pr.opt_mask, rec_pred=o.rec_pred,
+                                    pred_all=o.pred_all, counters=o.counters)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        o.counters.zero_()
+        reps, tot = 10, 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ctx.check_device_status()
+        c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64) / reps
+        pa = o.pred_all.cpu().numpy().reshape(R, 6)
+        sc = ~np.isnan(pa) & ~np.isnan(act)
+        ratio = np.exp(act[sc] - pa[sc])
+        res[name] = {"ms": tot / reps, "sign_accuracy": c[3] / max(c[2], 1),
+                     "top1_hit_rate": c[8] / max(c[7], 1), "rec_precision": c[6] / max(c[5], 1),
+                     "scored": int(c[2]),
+                     "ac_ex_quantiles_5_25_50_75_95": [float(x) for x in np.quantile(ratio, [.05, .25, .5, .75, .95])]
+                     if ratio.size else None,
+                     "ac_ex_within_10pct": float(np.mean(np.abs(ratio - 1.0) <= 0.1)) if ratio.size else None}
+    return res
+
+
+def run_transfer(rs, ctx, dev, stream, flush, args):
+    """Table 2's six experiments (Sec. 5) on the seeded stand-ins of the BH / NB runs
+    (synth.make_runs: 6 + 4 inputs x 3 runs x 64 versions x 96 counters).  Table 3's values come
+    from the paper's real profiles: context only."""
+    from paper_1910_07776_gb300 import synth
     runs = synth.make_runs(seed=0)
     out = {"data": "synthetic stand-ins: 2 codes (6 and 4 inputs) x 3 runs x 64 versions x 96 f64 counters",
            "experiments": {}}
     for e in range(1, 7):
-        pr = synth.table2_problems(runs, e)
-        dtr = rs.DeviceBatch.from_host(pr.train, dev)
-        dte = rs.DeviceBatch.from_host(pr.test, dev)
-        offs = torch.from_numpy(pr.groups).to(dev)
-        g = (offs, int(np.diff(pr.groups).max()))
-        ws = ctx.workspace(ctx.transfer_workspace_bytes(dtr, dte, g, rs.RS_MODEL_M5P))
-        R = dte.n_rows
-        # actual log speedups of the test rows (host, from the test set's own times)
-        act = np.full((R, 6), np.nan)
-        for q in range(pr.test.n_programs):
-            rows = pr.test.program_rows(q)
-            m = pr.test.masks[rows].astype(int)
-            lt = pr.test.log_time[rows]
-            slot = {int(v): i for i, v in enumerate(m)}
-            for t in range(len(m)):
-                for j in range(6):
-                    w = slot.get(int(m[t]) | (1 << j))
-                    if not (m[t] >> j) & 1 and w is not None:
-                        act[rows.start + t, j] = lt[t] - lt[w]
-        res = {"problems": int(pr.test.n_programs), "train_runs_per_problem": int(np.diff(pr.groups).max()),
-               "test_rows": int(R), "opt_mask": int(pr.opt_mask), "paper_ibk_accuracy_pct": PAPER_TABLE3_IBK[e],
-               "paper_m5p_accuracy_pct": PAPER_TABLE3_M5P[e]}
-        for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK), ("m5p", rs.RS_MODEL_M5P)):
-            o = rs.alloc_outputs(R, 0, CFG["k"], dev)
-            call = lambda: ctx.transfer(dtr, dte, ws, o.rec_code, groups=g, lam=CFG["lam"], k=CFG["k"],
-                                        tau=CFG["tau"], flags=flags, opt_mask=pr.opt_mask, rec_pred=o.rec_pred,
-                                        pred_all=o.pred_all, counters=o.counters)
-            for _ in range(3):
-                call()
-            torch.cuda.synchronize()
-            o.counters.zero_()
-            reps, tot = 10, 0.0
-            for _ in range(reps):
-                flush.fill_(1)
-                e0.record(stream)
-                call()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            ctx.check_device_status()
-            c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64) / reps
-            pa = o.pred_all.cpu().numpy().reshape(R, 6)
-            sc = ~np.isnan(pa) & ~np.isnan(act)
-            ratio = np.exp(act[sc] - pa[sc])
-            res[name] = {"ms": tot / reps, "sign_accuracy": c[3] / max(c[2], 1),
-                         "top1_hit_rate": c[8] / max(c[7], 1), "rec_precision": c[6] / max(c[5], 1),
-                         "scored": int(c[2]),
-                         "ac_ex_quantiles_5_25_50_75_95": [float(x) for x in np.quantile(ratio, [.05, .25, .5, .75, .95])]
-                         if ratio.size else None,
-                         "ac_ex_within_10pct": float(np.mean(np.abs(ratio - 1.0) <= 0.1)) if ratio.size else None}
-        out["experiments"][str(e)] = res
+        out["experiments"][str(e)] = _transfer_experiment(rs, ctx, dev, stream, flush,
+                                                          synth.table2_problems(runs, e), e)
+    return out
+
+
+def run_real_nb(rs, ctx, dev, stream, flush, args):
+    """Measured tier-1 data: the 64 versions of the n-body code NB (tier1/nbody.cu, the six
+    optimizations of Sec. 3.3) profiled on this GPU (tier1/capture.py; 4 inputs x 3 runs x 64
+    versions, counters / cycles).  Leave-one-version-out on every (input, run) with ridge and
+    IBK through rs_cv_step, and Table 2's experiments 1-4 with NB in the place of BH through
+    rs_transfer.  Table 3's figures (BH / NB on a K20c) are context only."""
+    import torch
+    from paper_1910_07776_gb300 import synth, tier1
+    if not tier1.available():
+        return None
+    runs = tier1.load_nb()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp = synth.make_splits(runs, "lovo")
+    db = rs.DeviceBatch.from_host(runs, dev)
+    ds = rs.DeviceSplits.from_host(sp, dev, runs)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    out = {"data": f"measured: {runs.meta['gpu']}, n-body 64 versions x {runs.feat_width[0]} counters / cycles, "
+                   f"inputs (bodies, steps) {runs.meta['inputs']}, {runs.meta['runs']} runs",
+           "capture": runs.meta["command"], "lovo": {}, "experiments": {}}
+    for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK)):
+        o = rs.alloc_outputs(ds.n_test_rows, ds.n_splits, CFG["k"], dev, pred_all=False)
+        ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"], flags=flags,
+                    rec_pred=o.rec_pred, counters=o.counters)
+        torch.cuda.synchronize()
+        o.counters.zero_()
+        e0.record(stream)
+        ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"], flags=flags,
+                    rec_pred=o.rec_pred, counters=o.counters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
+        out["lovo"][name] = {"ms": e0.elapsed_time(e1), "sign_accuracy": c[3] / max(c[2], 1),
+                             "top1_hit_rate": c[8] / max(c[7], 1), "scored": int(c[2])}
+    for e in range(1, 5):
+        out["experiments"][str(e)] = _transfer_experiment(rs, ctx, dev, stream, flush,
+                                                          synth.table2_problems(runs, e, code="NB"), e)
     return out
 
 
@@ -919,13 +1021,27 @@ def run_uneven(rs, ctx, dev, stream, flush, args):
     g.close()
     cnt = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
     ctx.check_device_status()
+    # the precision split of the precision form on the same stream: the Gram on the tensor cores
+    # (BF16 hi/lo, tile shape autotuned for the batch's width), FP64 fits
+    gram_tune = ctx.autotune_gram(db, ws)
+    o.counters.zero_()
+    bf_step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
+                                  tau=CFG["tau"], precision=rs.RS_GRAM_BF16X3, rec_pred=o.rec_pred,
+                                  counters=o.counters)
+    bf_ms = timed(bf_step)
+    cnt_bf = o.counters.cpu().numpy().view(np.uint64).astype(np.float64) / 4
+    ctx.check_device_status()
     return {"workload": "10,000 programs x U{8..64} versions x F in {64,128,256,512} f32, 1,024 half "
                         "splits/program (10,240,000 splits)",
             "recs_per_step": R, "value": R / (graph_ms * 1e-3), "unit": UNIT, "graph_ms": graph_ms,
             "eager_default_ms": eager_default, "eager_tuned_ms": eager_tuned,
             "autotune": {"solve_split": tune["solve_split"], "rank_waves": tune["rank_waves"],
                          "solve_order": tune["solve_order"]},
-            "sign_accuracy": cnt[3] / max(cnt[2], 1), "data_gen_s": gen_s}
+            "sign_accuracy": cnt[3] / max(cnt[2], 1), "data_gen_s": gen_s,
+            "bf16x3_gram": {"ms": bf_ms, "value": R / (bf_ms * 1e-3), "gram_autotune": gram_tune,
+                            "sign_accuracy": cnt_bf[3] / max(cnt_bf[2], 1),
+                            "note": "tensor-core Gram (BF16 hi/lo split) with the autotuned tile shape, "
+                                    "FP64 fits, eager calls"}}
 
 
 def _rel_stats(d, ref):
@@ -1008,6 +1124,8 @@ def run_precision(rs, ctx, dev, stream, flush, args):
         ds = rs.DeviceSplits.from_host(splits, dev, b)
         R = ds.n_test_rows
         ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+        if "gram_autotune" not in res:              # the tensor-core Gram's tile shape, 1024 features
+            res["gram_autotune"] = ctx.autotune_gram(db, ws)
         outs = {}
         times = {}
         for name, prec, flags in (("f64", rs.RS_GRAM_F64, 0), ("bf16x3", rs.RS_GRAM_BF16X3, 0),

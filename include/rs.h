@@ -295,6 +295,40 @@ rs_status rs_transfer(rs_ctx* ctx, const rs_batch* train, const rs_batch* test, 
                       size_t workspace_bytes, uint8_t* fit_status, uint32_t* rec_code, double* rec_pred,
                       double* pred_all, uint64_t* counters);
 
+/* ---- A3 + A4, primal form: pooled ridge fits over many programs ----------------------------
+ * One ridge model per optimization j (Sec. 3.4 regression family, the same loss as the batched
+ * fits: minimise sum (y - b - z.beta)^2 + lambda |beta|^2, intercept unpenalised) trained on
+ * the before/after pairs (v, v|j) of every program p of `std` with use_program[p] != 0
+ * (device uint8 [P]; NULL = all programs), pairs formed within each program (Sec. 3.3),
+ * labelled with its log speedup (Sec. 5): the model of a tool that has seen many codes.
+ * With the pairs far outnumbering the F features the primal normal equations are solved:
+ * G_j = sum_a c_a c_a^T + lambda I with c_a = z_a - zbar_j the centred feature vectors (the
+ * Gram X^T W X, W selecting j's pairs), formed as ONE batched tcgen05 GEMM over the six j from a
+ * BF16 hi/lo split of the centred rows (K = 3 x pairs, FP32 accumulation, TMA-fed), then an FP64
+ * Cholesky; with RS_REFINE_X in flags one refinement step whose residual is taken exactly in
+ * FP64 through the rows (recovering FP64 accuracy while kappa(G) * 2^-16 << 1).
+ * std: standardized features (X = Z, double), one width F = max_feat (<= 512) for every
+ * training program (a program of another width, or of more than 64 versions, is skipped
+ * and reported as RS_EDATA); at most 65,535 programs and 65,536 pairs per optimization.
+ * coef: double [6][F + 1] (device) = b_j, then beta_j; fit_status: uint8 [6] (device);
+ * a fit without pairs is RS_FIT_EMPTY, a non-positive pivot RS_FIT_NOTPD (b = NaN).
+ * workspace: rs_pooled_workspace_bytes(std) bytes, 256-byte aligned (RS_ENOMEM if smaller).
+ * lambda > 0.  Asynchronous on the context's stream.
+ * rs_predict_pooled: for every version t of `std` (rows in batch order) the predictions
+ * b_j + z_t.beta_j of its candidate optimizations (not in t's mask; all six with
+ * RS_RANK_ALL) whose fit is OK, ranked, thresholded at log(tau), top k and scored against
+ * the version's own program (actual speedups from its times) exactly as rs_predict_rank
+ * does: rec_code [n_rows], rec_pred [n_rows][k] (nullable), pred_all [n_rows][6]
+ * (nullable), counters (nullable, added to).                                              */
+size_t rs_pooled_workspace_bytes(const rs_batch* std);
+rs_status rs_fit_pooled(rs_ctx* ctx, const rs_batch* std, const uint8_t* use_program, double lambda,
+                        int flags, void* workspace, size_t workspace_bytes, double* coef,
+                        uint8_t* fit_status);
+rs_status rs_predict_pooled(rs_ctx* ctx, const rs_batch* std, const double* coef,
+                            const uint8_t* fit_status, int k, double tau, int flags,
+                            uint32_t* rec_code, double* rec_pred, double* pred_all,
+                            uint64_t* counters);
+
 /* ---- A7: the plain predictor as the surrogate's fallback -----------------------------------
  * After rs_surrogate_infer has ranked one row per version of `batch` (raw counters, the
  * batch's row order) and set used_fallback[row] (device uint8 [n_rows]) where the row's
@@ -350,6 +384,21 @@ rs_status rs_autotune(rs_ctx* ctx, const rs_batch* batch, const rs_splits* split
                       double* rec_pred, float* times_ms, int* n_times);
 rs_status rs_get_tuning(const rs_ctx* ctx, int* solve_split, int* rank_waves, int* solve_order);
 rs_status rs_set_tuning(rs_ctx* ctx, int solve_split, int rank_waves, int solve_order);
+/* Tile shapes of the tensor-core Gram (RS_GRAM_BF16X3), chosen per feature width (rounded up
+ * to a multiple of 64; a batch of mixed widths uses its widest): the output tile's width (32 or
+ * 64 of the 64 columns of a program's block) and the split of its K = 3 x width contraction
+ * (1: one CTA; 3: the three BF16 products hi hi^T, hi lo^T, lo hi^T on three CTAs, their FP32
+ * results summed in FP64 in that order -- a result that can differ from the unsplit one in the
+ * last FP32 bits).  rs_autotune_gram standardizes `batch` (raw counters) into the workspace
+ * (at least rs_cv_workspace_bytes(batch, any splits) bytes) and times the Gram for the four
+ * shapes, keeping the fastest in the context for that width; times_ms (host float [4],
+ * nullable) gets the times in the order (64, 1), (32, 1), (64, 3), (32, 3), *choice (nullable)
+ * the index kept.  rs_autotune does the same first when its precision is RS_GRAM_BF16X3.
+ * rs_get_gram_tuning / rs_set_gram_tuning read or set the shape for a width.            */
+rs_status rs_autotune_gram(rs_ctx* ctx, const rs_batch* batch, void* workspace, size_t workspace_bytes,
+                           float* times_ms, int* choice);
+rs_status rs_get_gram_tuning(const rs_ctx* ctx, int feat_width, int* tile_n, int* ksplit);
+rs_status rs_set_gram_tuning(rs_ctx* ctx, int feat_width, int tile_n, int ksplit);
 
 /* ---- tensor-core BF16 GEMM (the surrogate's and the tensor-core Gram's building block) ----
  * D[M][N] = A[M][K] * B[N][K]^T with A, B BF16 row-major (K contiguous, leading dimensions

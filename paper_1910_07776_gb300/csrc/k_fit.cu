@@ -1185,7 +1185,11 @@ solve_large_kernel(const SolveArgs a) {
 // b + sum_a alpha_a K[t][v_a]
 // with the candidate rows spread over the lanes.  Every loop that shuffles runs to the warp's
 // largest n, so the groups of a warp (equal n except at bucket boundaries) stay converged.
-constexpr int kWideLanes = 8;
+#ifndef RS_WIDE_LANES
+#define RS_WIDE_LANES 8
+#endif
+constexpr int kWideLanes = RS_WIDE_LANES;                  // lanes per fit: 4, 8 or 16
+static_assert(kWideLanes == 4 || kWideLanes == 8 || kWideLanes == 16, "lanes per fit");
 constexpr int kWideGroups = 32 / kWideLanes;
 constexpr int kWideWarps = 2;
 constexpr int kWideTri = tri(RS_MAXPAIRS);                 // packed lower triangle with diagonal

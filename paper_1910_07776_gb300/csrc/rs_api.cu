@@ -19,6 +19,8 @@ struct rs_ctx {
     int tune_split;          // autotuned launch parameters of the batched form
     int tune_rank_waves;
     int tune_order;
+    uint8_t gram_cfg[65];    // tensor-core Gram tiles per padded width / 64: bit 0 = 32-column
+                             // tiles (else 64), bit 1 = K split in three (else whole)
     cudaEvent_t ev[RS_NSTAGE_EVENTS];
     cudaStream_t side;       // second stream of the batched solver (fork/join on events)
     cudaEvent_t fork, join;
@@ -53,6 +55,12 @@ rs_status check_splits(rs_ctx* c, const rs_splits* s) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The tensor-core Gram's tuning slot of a feature width: its width rounded up to 64, / 64.
+int gram_slot(int max_feat) {
+    const int s = (max_feat + 63) / 64;
+    return s < 1 ? 1 : (s > 64 ? 64 : s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -76,6 +84,7 @@ rs_status rs_create(rs_ctx** out, int device, void* stream) {
     c->tune_rank_waves = 32;
     c->tune_order = 1;      // measured: the solver group 7 % faster than largest-first on the
                             // batched-CV workload (0.430 vs 0.462 ms)
+    memset(c->gram_cfg, 0, sizeof(c->gram_cfg));   // 64-column tiles, whole K
     for (int i = 0; i < RS_NSTAGE_EVENTS; ++i) c->ev[i] = nullptr;
     c->side = nullptr;
     c->fork = c->join = nullptr;
@@ -212,7 +221,9 @@ rs_status rs_gram(rs_ctx* c, const rs_batch* b, int precision, double* K, void* 
         if (!ws || ws_bytes < need) return fail(c, RS_ENOMEM, "the tensor-core Gram needs %zu bytes of workspace", need);
         if ((uintptr_t)ws % 256) return fail(c, RS_EINVAL, "workspace must be 256-byte aligned");
         if (b->n_programs > 65535) return fail(c, RS_EINVAL, "the tensor-core Gram takes at most 65535 programs per call");
-        e = rs_launch_gram_bf16x3_ws(b, K, ws, ws_bytes, c->dstatus, c->stream);
+        const int cfg = c->gram_cfg[gram_slot(b->max_feat)];
+        e = rs_launch_gram_bf16x3_ws(b, K, ws, ws_bytes, c->dstatus, c->stream, (cfg & 1) ? 32 : 64,
+                                     (cfg & 2) ? 3 : 1);
     } else {
         return fail(c, RS_EINVAL, "precision must be RS_GRAM_F64, RS_GRAM_BF16X3 or RS_GRAM_DIST2");
     }
@@ -477,6 +488,48 @@ rs_fallback_ws carve_fallback(void* base, const rs_batch* b, const rs_splits* sp
 }  // namespace
 
 extern "C" {
+
+size_t rs_pooled_workspace_bytes(const rs_batch* b) {
+    if (rs_batch_problem(b, false) || b->max_feat > 512) return 0;
+    return rs_pooled_workspace_bytes_impl(b->n_programs, b->max_feat);
+}
+
+rs_status rs_fit_pooled(rs_ctx* c, const rs_batch* b, const uint8_t* use_program, double lambda, int flags,
+                        void* ws, size_t ws_bytes, double* coef, uint8_t* fit_status) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, false);
+    if (s != RS_OK) return s;
+    if (b->max_feat > 512) return fail(c, RS_EINVAL, "pooled fits: max_feat <= 512");
+    if (b->n_programs > 65535) return fail(c, RS_EINVAL, "pooled fits: at most 65,535 programs");
+    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(c, RS_EINVAL, "lambda must be finite and > 0");
+    if (flags & ~RS_REFINE_X) return fail(c, RS_EINVAL, "flags: RS_REFINE_X only");
+    if (!coef || !fit_status) return fail(c, RS_EINVAL, "coef and fit_status are required");
+    if (!ws || (uintptr_t)ws % 256 != 0) return fail(c, RS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    const size_t need = rs_pooled_workspace_bytes_impl(b->n_programs, b->max_feat);
+    if (ws_bytes < need) return fail(c, RS_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_fit_pooled(b, use_program, lambda, (flags & RS_REFINE_X) ? 1 : 0, ws, ws_bytes, coef,
+                                         fit_status, c->dstatus, c->stream);
+    if (e == cudaErrorNotSupported) return fail(c, RS_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_fit_pooled");
+}
+
+rs_status rs_predict_pooled(rs_ctx* c, const rs_batch* b, const double* coef, const uint8_t* fit_status, int k,
+                            double tau, int flags, uint32_t* rec_code, double* rec_pred, double* pred_all,
+                            uint64_t* counters) {
+    if (!c) return RS_EINVAL;
+    rs_status s = check_batch(c, b, false);
+    if (s != RS_OK) return s;
+    if (b->max_feat > 512) return fail(c, RS_EINVAL, "pooled fits: max_feat <= 512");
+    if (!coef || !fit_status || !rec_code) return fail(c, RS_EINVAL, "coef, fit_status and rec_code are required");
+    if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
+    if (flags & ~RS_RANK_ALL) return fail(c, RS_EINVAL, "flags: RS_RANK_ALL only");
+    cudaSetDevice(c->device);
+    cudaError_t e = rs_launch_predict_pooled(b, coef, fit_status, k, log(tau), flags, rec_code, rec_pred, pred_all,
+                                             (unsigned long long*)counters, c->dstatus, c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_predict_pooled");
+}
 
 size_t rs_fallback_workspace_bytes(const rs_batch* b, const rs_splits* sp) {
     if (rs_batch_problem(b, true) || rs_splits_problem(sp)) return 0;
@@ -833,6 +886,86 @@ rs_status rs_cv_graph_destroy(rs_graph* g) {
 }
 
 // ---- autotuner --------------------------------------------------------------------------------
+}  // extern "C"
+
+// Times the tensor-core Gram of this batch (raw counters: standardized into the workspace first,
+// laid out as rs_cv_step does) for the four tile configurations and keeps the fastest for the
+// batch's padded width.  times_ms (nullable) gets the four times in configuration order
+// (64-column whole-K, 32 whole, 64 split, 32 split); *choice the configuration kept.
+static rs_status rs_autotune_gram_impl(rs_ctx* c, const rs_batch* b, void* ws, size_t ws_bytes, float* times_ms,
+                                       int* choice) {
+    rs_status s = check_batch(c, b, true);
+    if (s != RS_OK) return s;
+    if (b->n_programs > 65535) return fail(c, RS_EINVAL, "the tensor-core Gram takes at most 65535 programs per call");
+    const size_t zbytes = align256((size_t)b->x_elems * sizeof(double));
+    const size_t kbytes = align256((size_t)b->n_programs * RS_GRAM_LD * RS_GRAM_LD * sizeof(double));
+    const size_t gneed = rs_gram_tc_workspace_bytes(b->n_programs, b->max_feat);
+    if (!ws || (uintptr_t)ws % 256 || ws_bytes < zbytes + kbytes + gneed)
+        return fail(c, RS_ENOMEM, "autotuning the Gram needs %zu bytes of workspace", zbytes + kbytes + gneed);
+    double* Z = (double*)ws;
+    double* K = (double*)((char*)ws + zbytes);
+    void* gws = (char*)ws + zbytes + kbytes;
+    const size_t gbytes = ws_bytes - zbytes - kbytes;
+    s = rs_standardize(c, b, Z, nullptr, nullptr);
+    if (s != RS_OK) return s;
+    rs_batch zb = *b;
+    zb.X = Z;
+    zb.dtype = RS_F64;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int keep = 0;
+    cudaError_t e = cudaSuccess;
+    for (int cfg = 0; cfg < 4 && e == cudaSuccess; ++cfg) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            e = rs_launch_gram_bf16x3_ws(&zb, K, gws, gbytes, c->dstatus, c->stream, (cfg & 1) ? 32 : 64,
+                                         (cfg & 2) ? 3 : 1);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);      // the last run is the one kept
+        }
+        if (times_ms) times_ms[cfg] = ms;
+        if (ms < best) {
+            best = ms;
+            keep = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_autotune_gram");
+    c->gram_cfg[gram_slot(b->max_feat)] = (uint8_t)keep;
+    if (choice) *choice = keep;
+    return RS_OK;
+}
+
+extern "C" {
+
+rs_status rs_autotune_gram(rs_ctx* c, const rs_batch* b, void* ws, size_t ws_bytes, float* times_ms, int* choice) {
+    if (!c) return RS_EINVAL;
+    cudaSetDevice(c->device);
+    return rs_autotune_gram_impl(c, b, ws, ws_bytes, times_ms, choice);
+}
+
+rs_status rs_get_gram_tuning(const rs_ctx* c, int feat_width, int* tile_n, int* ksplit) {
+    if (!c || feat_width < 1 || feat_width > 4096) return RS_EINVAL;
+    const int cfg = c->gram_cfg[gram_slot(feat_width)];
+    if (tile_n) *tile_n = (cfg & 1) ? 32 : 64;
+    if (ksplit) *ksplit = (cfg & 2) ? 3 : 1;
+    return RS_OK;
+}
+
+rs_status rs_set_gram_tuning(rs_ctx* c, int feat_width, int tile_n, int ksplit) {
+    if (!c) return RS_EINVAL;
+    if (feat_width < 1 || feat_width > 4096) return fail(c, RS_EINVAL, "feat_width must be in 1..4096");
+    if ((tile_n != 32 && tile_n != 64) || (ksplit != 1 && ksplit != 3))
+        return fail(c, RS_EINVAL, "tile_n must be 32 or 64 and ksplit 1 or 3");
+    c->gram_cfg[gram_slot(feat_width)] = (uint8_t)((tile_n == 32 ? 1 : 0) | (ksplit == 3 ? 2 : 0));
+    return RS_OK;
+}
+
 rs_status rs_autotune(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double lambda, int k, double tau,
                       int flags, int precision, void* ws, size_t ws_bytes, int64_t* rec_offsets,
                       uint32_t* rec_code, double* rec_pred, float* times_ms, int* n_times) {
@@ -843,6 +976,14 @@ rs_status rs_autotune(rs_ctx* c, const rs_batch* b, const rs_splits* sp, double 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    if (precision == RS_GRAM_BF16X3) {          // the Gram's tiles first, on this batch
+        rs_status gs = rs_autotune_gram_impl(c, b, ws, ws_bytes, nullptr, nullptr);
+        if (gs != RS_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return gs;
+        }
+    }
     float best = 1e30f;
     int bs = c->tune_split, bw = c->tune_rank_waves, bo = c->tune_order, idx = 0;
     rs_status s = RS_OK;

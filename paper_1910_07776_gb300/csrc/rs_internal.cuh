@@ -98,8 +98,9 @@ cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch*
                                       int max_runs, int stat_stride, int ld, double* KA, double* Kx, int dist,
                                       cudaStream_t st);
 size_t rs_gram_tc_workspace_bytes(int64_t P, int max_feat);
+// tile_n: 32 or 64 output columns per tile; ksplit: 1 or 3 (see k_gram_tc.cu).
 cudaError_t rs_launch_gram_bf16x3_ws(const rs_batch* b, double* K, void* ws, size_t ws_bytes, int* dstatus,
-                                     cudaStream_t st);
+                                     cudaStream_t st, int tile_n = 64, int ksplit = 1);
 cudaError_t rs_launch_rec_offsets(const rs_batch* b, const rs_splits* s, int64_t* rec_offsets,
                                   int64_t* scratch_blocksums, int* dstatus, cudaStream_t st);
 size_t rs_rec_offsets_scratch_elems(int64_t n_splits);
@@ -126,6 +127,13 @@ struct rs_fallback_ws {
     size_t cv_ws_bytes;
     size_t bytes;             // total
 };
+// Pooled ridge fits in primal form (k_pooled.cu).
+size_t rs_pooled_workspace_bytes_impl(int64_t P, int F);
+cudaError_t rs_launch_fit_pooled(const rs_batch* b, const uint8_t* use, double lambda, int refine, void* ws,
+                                 size_t ws_bytes, double* coef, uint8_t* status, int* dstatus, cudaStream_t st);
+cudaError_t rs_launch_predict_pooled(const rs_batch* b, const double* coef, const uint8_t* status, int k,
+                                     double log_tau, int flags, uint32_t* rec_code, double* rec_pred,
+                                     double* pred_all, unsigned long long* counters, int* dstatus, cudaStream_t st);
 cudaError_t rs_launch_fallback_select(const rs_batch* b, const rs_splits* sp, const uint8_t* used,
                                       const rs_fallback_ws& w, cudaStream_t st);
 cudaError_t rs_launch_fallback_gather(const rs_batch* b, const rs_splits* sp, int Q, const rs_fallback_ws& w,

@@ -38,6 +38,8 @@ EXPORTS = [
     "rs_surrogate_train", "rs_surrogate_infer", "rs_cv_graph_create", "rs_cv_graph_launch",
     "rs_cv_graph_destroy", "rs_autotune", "rs_get_tuning", "rs_set_tuning", "rs_transfer", "rs_transfer_workspace_bytes",
     "rs_check_reciprocals", "rs_check_wait_timeout", "rs_fallback_workspace_bytes", "rs_surrogate_fallback",
+    "rs_pooled_workspace_bytes", "rs_fit_pooled", "rs_predict_pooled",
+    "rs_autotune_gram", "rs_get_gram_tuning", "rs_set_gram_tuning",
 ]
 
 
@@ -109,6 +111,13 @@ def load(path: str = SO):
     L.rs_measure_fma_peak.argtypes = [i, i, C.POINTER(d)]
     L.rs_check_reciprocals.argtypes = [P, i64, P, P]
     L.rs_check_wait_timeout.argtypes = [P, P, i64, P]
+    L.rs_autotune_gram.argtypes = [P, P, P, C.c_size_t, C.POINTER(C.c_float), C.POINTER(C.c_int)]
+    L.rs_get_gram_tuning.argtypes = [P, i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rs_set_gram_tuning.argtypes = [P, i, i, i]
+    L.rs_pooled_workspace_bytes.argtypes = [P]
+    L.rs_pooled_workspace_bytes.restype = C.c_size_t
+    L.rs_fit_pooled.argtypes = [P, P, P, d, i, P, C.c_size_t, P, P]
+    L.rs_predict_pooled.argtypes = [P, P, P, P, i, d, i, P, P, P, P]
     L.rs_fallback_workspace_bytes.argtypes = [P, P]
     L.rs_fallback_workspace_bytes.restype = C.c_size_t
     L.rs_surrogate_fallback.argtypes = [P, P, P, P, d, i, d, i, P, C.c_size_t, P, P, C.POINTER(i64)]
@@ -136,7 +145,7 @@ def load(path: str = SO):
     L.rs_transfer.argtypes = [P, P, P, P, d, i, d, i, i, P, C.c_size_t, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes", "rs_gram_workspace_bytes",
-                        "rs_fallback_workspace_bytes",
+                        "rs_fallback_workspace_bytes", "rs_pooled_workspace_bytes",
                         "rs_transfer_workspace_bytes", "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
@@ -324,6 +333,25 @@ class Context:
             _ptr(rec_pred), times, C.byref(n)))
         return {**self.get_tuning(), "times_ms": [times[i] for i in range(n.value)]}
 
+    def autotune_gram(self, b: DeviceBatch, workspace) -> dict:
+        """rs_autotune_gram: the tensor-core Gram's tile shape for this batch's width."""
+        bc = b.c()
+        times = (C.c_float * 4)()
+        choice = C.c_int(0)
+        self._check(self.L.rs_autotune_gram(self.h, C.byref(bc), _ptr(workspace),
+                                            workspace.numel() * workspace.element_size(), times, C.byref(choice)))
+        shapes = [(64, 1), (32, 1), (64, 3), (32, 3)]
+        return {"tile_n": shapes[choice.value][0], "ksplit": shapes[choice.value][1],
+                "times_ms": {f"{n}x{k}": float(t) for (n, k), t in zip(shapes, times)}}
+
+    def get_gram_tuning(self, feat_width: int) -> dict:
+        tn, ks = C.c_int(0), C.c_int(0)
+        self._check(self.L.rs_get_gram_tuning(self.h, int(feat_width), C.byref(tn), C.byref(ks)))
+        return {"tile_n": tn.value, "ksplit": ks.value}
+
+    def set_gram_tuning(self, feat_width: int, tile_n: int, ksplit: int):
+        self._check(self.L.rs_set_gram_tuning(self.h, int(feat_width), int(tile_n), int(ksplit)))
+
     def get_tuning(self) -> dict:
         sp_, rw, so = C.c_int(), C.c_int(), C.c_int()
         self._check(self.L.rs_get_tuning(self.h, C.byref(sp_), C.byref(rw), C.byref(so)))
@@ -407,6 +435,31 @@ class Context:
             self.h, C.byref(bc), C.byref(sc), float(lam), int(k), float(tau), int(flags),
             int(precision), _ptr(workspace), workspace.numel() * workspace.element_size(),
             _ptr(rec_offsets), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all), _ptr(counters)))
+
+    def pooled_workspace_bytes(self, zb: DeviceBatch) -> int:
+        bc = zb.c()
+        return int(self.L.rs_pooled_workspace_bytes(C.byref(bc)))
+
+    def fit_pooled(self, zb: DeviceBatch, use_program=None, lam: float = 1e-3, flags: int = 0, workspace=None):
+        """rs_fit_pooled: one primal ridge model per optimization over the pairs of the selected
+        programs of a standardized batch; returns (coef [6][F+1], fit_status [6])."""
+        bc = zb.c()
+        if workspace is None:
+            workspace = self.workspace(self.pooled_workspace_bytes(zb))
+        F = zb.max_feat
+        coef = torch.empty(NOPT * (F + 1), dtype=torch.float64, device=zb.X.device)
+        st = torch.empty(NOPT, dtype=torch.uint8, device=zb.X.device)
+        self._check(self.L.rs_fit_pooled(self.h, C.byref(bc), _ptr(use_program), float(lam), int(flags),
+                                         _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                         _ptr(coef), _ptr(st)))
+        return coef.view(NOPT, F + 1), st
+
+    def predict_pooled(self, zb: DeviceBatch, coef, fit_status, rec_code, k: int = 3, tau: float = 1.05,
+                       flags: int = 0, rec_pred=None, pred_all=None, counters=None):
+        bc = zb.c()
+        self._check(self.L.rs_predict_pooled(self.h, C.byref(bc), _ptr(coef.contiguous()), _ptr(fit_status), int(k),
+                                             float(tau), int(flags), _ptr(rec_code), _ptr(rec_pred), _ptr(pred_all),
+                                             _ptr(counters)))
 
     def fallback_workspace_bytes(self, b: DeviceBatch, s: DeviceSplits) -> int:
         bc, sc = b.c(), s.c()

@@ -507,8 +507,9 @@ class TransferProblems:
     pairs: list                 # (train (code, input, runs), test (code, input, run)) per problem
 
 
-def table2_problems(runs: ProgramBatch, experiment: int) -> TransferProblems:
-    """Table 2's six experiments on a batch from ``make_runs`` (Sec. 5 / 6):
+def table2_problems(runs: ProgramBatch, experiment: int, code: str = "BH") -> TransferProblems:
+    """Table 2's six experiments on a batch from ``make_runs`` (Sec. 5 / 6); experiments 1-4
+    use the runs of ``code`` (BH in the paper; any code of the batch, e.g. a measured NB):
     1. one run of a BH input trains; every run of that input (its own included) is tested;
     2. as 1, but only the other runs are tested;
     3. two runs of a BH input train; the third is tested;
@@ -520,19 +521,19 @@ def table2_problems(runs: ProgramBatch, experiment: int) -> TransferProblems:
     n_in = dict(runs.meta["codes"])
     probs = []          # (list of training programs, test program, description)
     if experiment in (1, 2):
-        for i in range(n_in["BH"]):
+        for i in range(n_in[code]):
             for r in range(n_runs):
                 for r2 in range(n_runs):
                     if experiment == 2 and r2 == r:
                         continue
-                    probs.append(([idx[("BH", i, r)]], idx[("BH", i, r2)], (("BH", i, (r,)), ("BH", i, r2))))
+                    probs.append(([idx[(code, i, r)]], idx[(code, i, r2)], ((code, i, (r,)), (code, i, r2))))
     elif experiment == 3:
-        for i in range(n_in["BH"]):
+        for i in range(n_in[code]):
             for r2 in range(n_runs):
                 tr = tuple(r for r in range(n_runs) if r != r2)
-                probs.append(([idx[("BH", i, r)] for r in tr], idx[("BH", i, r2)], (("BH", i, tr), ("BH", i, r2))))
+                probs.append(([idx[(code, i, r)] for r in tr], idx[(code, i, r2)], ((code, i, tr), (code, i, r2))))
     elif experiment in (4, 5, 6):
-        src, dst = {4: ("BH", "BH"), 5: ("BH", "NB"), 6: ("NB", "BH")}[experiment]
+        src, dst = {4: (code, code), 5: ("BH", "NB"), 6: ("NB", "BH")}[experiment]
         for i in range(n_in[src]):
             tr = tuple(range(n_runs))
             for i2 in range(n_in[dst]):

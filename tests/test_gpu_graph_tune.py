@@ -86,3 +86,33 @@ def test_work_order_and_tuning_setter_change_no_result(env):
         with pytest.raises(rs.RsError):
             ctx.set_tuning(*bad)
     ctx.set_tuning(6, 32, 1)
+
+
+def test_gram_tile_shapes_agree_and_the_autotuner_keeps_one(env):
+    # every tile shape of the tensor-core Gram (32- or 64-column tiles, K whole or split into
+    # its three BF16 products) gives the FP64 Gram within the BF16 x 3 bound, on a batch of mixed
+    # widths and version counts; the autotuner keeps one of them for the batch's width
+    rs, ctx = env
+    batch, splits, db, ds = _uneven(rs)
+    Z = ctx.standardize(db)
+    zb = db.with_X(Z)
+    K64 = ctx.gram(zb, rs.RS_GRAM_F64).cpu().numpy().reshape(-1, 64, 64)
+    Zh = Z.cpu().numpy()
+    for tile_n in (64, 32):
+        for ksplit in (1, 3):
+            ctx.set_gram_tuning(db.max_feat, tile_n, ksplit)
+            assert ctx.get_gram_tuning(db.max_feat) == {"tile_n": tile_n, "ksplit": ksplit}
+            K = ctx.gram(zb, rs.RS_GRAM_BF16X3).cpu().numpy().reshape(-1, 64, 64)
+            for p in range(batch.n_programs):
+                V, F = batch.versions(p), int(batch.feat_width[p])
+                o = int(batch.x_offsets[p])
+                Zp = np.abs(Zh[o:o + V * F].reshape(V, F))
+                err = np.abs(K[p, :V, :V] - K64[p, :V, :V]) / (Zp @ Zp.T + 1e-300)
+                assert err.max() < 6e-5, (tile_n, ksplit, p, err.max())
+                np.testing.assert_array_equal(K[p, :V, :V], K[p, :V, :V].T)
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    got = ctx.autotune_gram(db, ws)
+    assert (got["tile_n"], got["ksplit"]) in {(64, 1), (32, 1), (64, 3), (32, 3)}
+    assert all(t > 0 for t in got["times_ms"].values())
+    assert ctx.get_gram_tuning(db.max_feat) == {"tile_n": got["tile_n"], "ksplit": got["ksplit"]}
+    ctx.set_gram_tuning(db.max_feat, 64, 1)
