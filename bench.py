@@ -362,6 +362,10 @@ def main():
     ap.add_argument("--no-ibk", action="store_true")
     ap.add_argument("--no-transfer", action="store_true")
     ap.add_argument("--no-lovo", action="store_true")
+    ap.add_argument("--profile-gram", type=int, default=0, metavar="PROGRAMS",
+                    help="a short run of the tensor-core Gram (BF16 hi/lo split) on this many programs x 64 "
+                         "versions x 1024 FP64 features, each tile shape three times, and of the pooled "
+                         "fit of the batched-CV workload's first 48 programs (for profiler captures)")
     ap.add_argument("--only-lovo", type=int, default=0, metavar="PROGRAMS",
                     help="time only the leave-one-version-out form on this many programs (for profiler "
                          "captures of its solver)")
@@ -396,6 +400,27 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = rs.Context(local, stream)
+    if args.profile_gram:
+        from paper_1910_07776_gb300 import synth
+        b = synth.make_batch_fast(args.profile_gram, versions=64, feat=1024, dtype=np.float64, seed=21)
+        db = rs.DeviceBatch.from_host(b, dev)
+        zb = db.with_X(ctx.standardize(db))
+        ws = ctx.workspace(ctx.cv_workspace_bytes(db, rs.DeviceSplits.from_host(synth.make_splits(b, "all"), dev, b)))
+        K = torch.zeros(db.n_programs * 64 * 64, dtype=torch.float64, device=dev)
+        for tile_n, ksplit in ((64, 1), (32, 1), (64, 3), (32, 3)):
+            ctx.set_gram_tuning(1024, tile_n, ksplit)
+            for _ in range(3):
+                ctx.gram(zb, rs.RS_GRAM_BF16X3, K, ws)
+        tr = synth.take_programs(batch, list(range(48)))
+        dtr = rs.DeviceBatch.from_host(tr, dev)
+        ztr = dtr.with_X(ctx.standardize(dtr))
+        for _ in range(3):
+            ctx.fit_pooled(ztr, None, lam=CFG["lam"], flags=rs.RS_REFINE_X)
+        torch.cuda.synchronize()
+        ctx.check_device_status()
+        print(json.dumps({"profile_gram": args.profile_gram}), flush=True)
+        ctx.close()
+        return 0
     if args.only_lovo:
         flush = torch.empty(32 * 1024 * 1024, dtype=torch.int64, device=dev)
         print(json.dumps({"lovo_form": run_lovo(rs, ctx, dev, stream, flush, args, args.only_lovo)}), flush=True)

@@ -1186,7 +1186,7 @@ solve_large_kernel(const SolveArgs a) {
 // with the candidate rows spread over the lanes.  Every loop that shuffles runs to the warp's
 // largest n, so the groups of a warp (equal n except at bucket boundaries) stay converged.
 #ifndef RS_WIDE_LANES
-#define RS_WIDE_LANES 8
+#define RS_WIDE_LANES 16
 #endif
 constexpr int kWideLanes = RS_WIDE_LANES;                  // lanes per fit: 4, 8 or 16
 static_assert(kWideLanes == 4 || kWideLanes == 8 || kWideLanes == 16, "lanes per fit");
@@ -1222,8 +1222,11 @@ __device__ __forceinline__ void tri_step(int& i, int& j) {
 __global__ void __launch_bounds__(kWideWarps * 32)
 solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
     __shared__ long long start[kHist], cstart[kHist];
+    __shared__ uint16_t tri_rc[tri(RS_MAXPAIRS - 1)];         // packed-triangle entry -> row, column
     extern __shared__ __align__(16) double wsm[];
-    bucket_tables(a.hist, start, cstart);
+    for (int i = threadIdx.x >> 5; i < RS_MAXPAIRS - 1; i += kWideWarps)
+        for (int j = threadIdx.x & 31; j <= i; j += 32) tri_rc[tri(i) + j] = (uint16_t)(i << 8 | j);
+    bucket_tables(a.hist, start, cstart);                      // (ends with a barrier)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane / kWideLanes, l = lane % kWideLanes;
     const int gb = warp * kWideGroups + g;                  // fit group of the block
@@ -1317,11 +1320,11 @@ solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
                 }
                 o = (o + m - 1) & (kWideLanes - 1);
                 {                                            // rows and columns > k+1
-                    const int e0 = (l - o) & (kWideLanes - 1);
-                    int i, jj;
-                    tri_pos(e0, i, jj);
-                    for (int e = e0; e < tri(m - 1); e += kWideLanes, tri_step(i, jj)) {
-                        const int ri = k + 2 + i, cj = k + 2 + jj;
+                    const int T = tri(m - 1);
+#pragma unroll 4
+                    for (int e = (l - o) & (kWideLanes - 1); e < T; e += kWideLanes) {
+                        const int ij = tri_rc[e];            // row << 8 | column of entry e
+                        const int ri = k + 2 + (ij >> 8), cj = k + 2 + (ij & 255);
                         A[tri(ri) + cj] = fma(-A[tri(ri) + k], Ck[cj], A[tri(ri) + cj]);
                     }
                 }
