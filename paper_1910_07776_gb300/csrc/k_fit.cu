@@ -258,15 +258,6 @@ struct PredTarget {
     int64_t room;         // rows left in the buffer from dst (guards a wrong size hint)
 };
 
-__device__ __forceinline__ void mark_failed(const PredTarget& pt) {
-    const double fail = __longlong_as_double(kFailBits);
-    for (uint64_t cm = pt.cand; cm; cm &= cm - 1) {
-        const int t = __ffsll((long long)cm) - 1;
-        const int r = __popcll(pt.test & ((1ull << t) - 1ull));
-        if (r < pt.room) pt.dst[r] = fail;
-    }
-}
-
 // One fit of n = N pairs in registers.  M = K_TT + lambda I = L D L^T (unit lower L, no
 // square roots; reciprocal pivots by rcp_newton).  With t_y = L^-1 y and t_1 = L^-1 1:
 //   1^T M^-1 y = t_1^T D^-1 t_y,  1^T M^-1 1 = t_1^T D^-1 t_1,  b = their ratio,
@@ -438,6 +429,7 @@ struct SolveArgs {
     const int32_t* feat_width;
     int max_feat;
     int order;            // 0: largest fits first; 1: alternate ranges from both ends
+    unsigned long long* row_info;   // [R] the rank pass's row records (with predictions)
 };
 
 __device__ __forceinline__ bool pred_target_v(const SolveArgs& a, int64_t s, int j, int p, int V, PredTarget& pt) {
@@ -453,6 +445,18 @@ __device__ __forceinline__ bool pred_target_v(const SolveArgs& a, int64_t s, int
 }
 __device__ __forceinline__ bool pred_target(const SolveArgs& a, int64_t s, int j, int p, PredTarget& pt) {
     return pred_target_v(a, s, j, p, (int)(a.row_off[p + 1] - a.row_off[p]), pt);
+}
+
+// A fit (s, j) that failed sets bit 36 + j in the row records of its candidate rows, beside the
+// fits without a training pair: the rank pass leaves optimization j out of those rows and reads
+// no fit status.
+__device__ __forceinline__ void mark_failed(const SolveArgs& a, int64_t s, int j, const PredTarget& pt) {
+    unsigned long long* info = a.row_info + a.rec_offsets[s];
+    for (uint64_t cm = pt.cand; cm; cm &= cm - 1) {
+        const int t = __ffsll((long long)cm) - 1;
+        const int r = __popcll(pt.test & ((1ull << t) - 1ull));
+        if (r < pt.room) atomicOr(info + r, 1ull << (36 + j));
+    }
 }
 
 __device__ __forceinline__ void finish_record(const SolveArgs& a, int64_t f, int n, int st, double* out) {
@@ -634,7 +638,7 @@ solve_small_kernel(const SolveArgs a, unsigned long long* work) {
             const PredTarget* pt = pred_target_v(a, s, j, p, (int)rec.w, ptv) ? &ptv : nullptr;
             st = solve_dispatch<NLO, NHI>(n, Kp, a.pb + pbase, a.ylab + pbase, rec.z,
                                           a.dlam + (int64_t)p * RS_MAXV, out, pt);
-            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            if (st != RS_FIT_OK && pt) mark_failed(a, s, j, *pt);
             finish_record(a, f, n, st, out);
         }
         count_status(a, st, active);
@@ -841,7 +845,7 @@ solve_mid_kernel(const SolveArgs a, int nmax, unsigned long long* work) {
             const PredTarget* pt = pred_target(a, s, j, p, ptv) ? &ptv : nullptr;
             st = solve_var(n, nmax, Kp, a.pb + pbase, a.ylab + pbase, rec.z,
                            a.dlam + (int64_t)p * RS_MAXV, out, pt, W, VB);
-            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            if (st != RS_FIT_OK && pt) mark_failed(a, s, j, *pt);
             finish_record(a, f, n, st, out);
         }
         count_status(a, st, active);
@@ -1164,7 +1168,7 @@ solve_large_kernel(const SolveArgs a) {
                               : fit_warp_ldl(n, rec.z, a.pb + base, a.ylab + base, Kp,
                                              a.dlam + (int64_t)p * RS_MAXV, Lsh, Ush, out, pt);
         if (lane == 0) {
-            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            if (st != RS_FIT_OK && pt) mark_failed(a, s, j, *pt);
             finish_record(a, f, n, st, out);
         }
         if (a.counters && lane == 0) atomicAdd(a.counters + (st == RS_FIT_OK ? 9 : st == RS_FIT_NOTPD ? 11 : 12), 1ull);
@@ -1188,8 +1192,8 @@ solve_large_kernel(const SolveArgs a) {
 #ifndef RS_WIDE_LANES
 #define RS_WIDE_LANES 16
 #endif
-constexpr int kWideLanes = RS_WIDE_LANES;                  // lanes per fit: 4, 8 or 16
-static_assert(kWideLanes == 4 || kWideLanes == 8 || kWideLanes == 16, "lanes per fit");
+constexpr int kWideLanes = RS_WIDE_LANES;                  // lanes per fit: 4, 8, 16 or 32
+static_assert(kWideLanes == 4 || kWideLanes == 8 || kWideLanes == 16 || kWideLanes == 32, "lanes per fit");
 constexpr int kWideGroups = 32 / kWideLanes;
 constexpr int kWideWarps = 2;
 constexpr int kWideTri = tri(RS_MAXPAIRS);                 // packed lower triangle with diagonal
@@ -1363,7 +1367,7 @@ solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
         bool bad = ok && !finite_bits(b);
         if (ok)
             for (int i = l; i < n; i += kWideLanes) bad = bad || !finite_bits(Ty[i]);
-        const unsigned gm = ((1u << kWideLanes) - 1u) << (g * kWideLanes);
+        const unsigned gm = kWideLanes == 32 ? 0xffffffffu : ((1u << (kWideLanes & 31)) - 1u) << (g * kWideLanes);
         const unsigned badm = __ballot_sync(0xffffffffu, bad);
         if (ok && (badm & gm)) st = RS_FIT_NONFINITE;
         if (out && st == RS_FIT_OK) {
@@ -1385,7 +1389,7 @@ solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
             }
         }
         if (active && l == 0) {
-            if (st != RS_FIT_OK && pt) mark_failed(*pt);
+            if (st != RS_FIT_OK && pt) mark_failed(a, s, j, *pt);
             finish_record(a, f, n, st, out);
         }
         count_status(a, st, active && l == 0);
@@ -1396,96 +1400,126 @@ solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
 // ====================================================================== rank pass
 // One thread per test row: its row record and its six predictions (written by the solve
 // kernels) go through rank_row; no FP64 arithmetic.
-constexpr int kRankTile = 256;               // rows per tile = threads per block
+#ifndef RS_RANK_TILE
+#define RS_RANK_TILE 256
+#endif
+#ifndef RS_RANK_RPT
+#define RS_RANK_RPT 1
+#endif
+#ifndef RS_RANK_MINB
+#define RS_RANK_MINB 3
+#endif
+constexpr int kRankTile = RS_RANK_TILE;      // rows per tile (one ring stage)
+constexpr int kRankRpt = RS_RANK_RPT;        // rows of a tile per consumer thread
+constexpr int kRankCons = kRankTile / kRankRpt;                    // consumer threads
+constexpr int kRankWarps = kRankCons / 32;   // consumer warps
+constexpr int kRankThreads = kRankCons + 32; // and one producer warp
 constexpr int kRankStages = 3;
 constexpr int kRankPlanes = 1 + RS_NOPT;     // the row records, then the six prediction planes
 constexpr size_t kRankStageBytes = (size_t)kRankPlanes * kRankTile * 8;
-constexpr size_t kRankSmem = kRankStages * kRankStageBytes + kRankStages * 8;
+constexpr size_t kRankSmem = kRankStages * kRankStageBytes + 2 * kRankStages * 8;
+static_assert(kRankCons % 32 == 0 && kRankCons * kRankRpt == kRankTile, "whole warps of rows");
 
-// Persistent blocks over tiles of 256 rows.  Thread 0 streams each tile -- the row records
-// and the six prediction planes, seven 1-D TMA bulk copies -- into a 3-stage shared-memory
-// ring (one mbarrier per stage); the threads read their row from shared memory, the stage
-// is refilled with the tile three ahead, and the row is ranked while those copies fly.
-// Bounded waits: on a timeout RS_ETIMEOUT is set, the copies still in flight are waited
-// for (bounded) and the block returns.
+// Persistent blocks over tiles of kRankTile rows, a producer warp and kRankWarps consumer
+// warps that never wait for one another.  The producer's lane 0 streams each tile -- the row
+// records and the six prediction planes, seven 1-D TMA bulk copies -- into a 3-stage
+// shared-memory ring: a stage is refilled once every consumer warp has arrived on its "empty"
+// mbarrier, and its copies complete on its "full" mbarrier.  A consumer warp waits for the
+// stage, reads its rows into registers (kRankRpt per thread, kRankCons rows apart), arrives on
+// "empty" and ranks the rows while the copies of the tiles ahead fly.  Bounded waits: on a
+// timeout RS_ETIMEOUT is set and the warp leaves; the producer waits (bounded) for the copies
+// it has in flight before it leaves.
 template <bool PACK>
-__global__ void __launch_bounds__(kRankTile, 2)
+__global__ void __launch_bounds__(kRankThreads, RS_RANK_MINB)
 rank_pass_kernel(const RankPassArgs a) {
     extern __shared__ __align__(128) unsigned char rsm[];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t total = a.rec_offsets[a.S];
     const int64_t nrows = total < a.R ? total : a.R;
     if (total > a.R && blockIdx.x == 0 && tid == 0) rs_dev_flag(a.dstatus, RS_EDATA, -3);
     const int64_t ntiles = (nrows + kRankTile - 1) / kRankTile;
     const uint32_t sbase = tc::smem_u32(rsm);
-    const uint32_t bar0 = sbase + (uint32_t)(kRankStages * kRankStageBytes);
+    const uint32_t full0 = sbase + (uint32_t)(kRankStages * kRankStageBytes);
+    const uint32_t empty0 = full0 + 8 * kRankStages;
     if (tid == 0) {
-        for (int st = 0; st < kRankStages; ++st) tc::mbar_init(bar0 + 8 * st, 1);
+        for (int st = 0; st < kRankStages; ++st) {
+            tc::mbar_init(full0 + 8 * st, 1);
+            tc::mbar_init(empty0 + 8 * st, kRankWarps);
+        }
         tc::fence_barrier_init();
     }
     __syncthreads();
-    auto issue = [&](int64_t tile, int st) {   // thread 0
-        const int64_t row0 = tile * kRankTile;
-        int64_t rows = nrows - row0 < kRankTile ? nrows - row0 : kRankTile;
-        rows = (rows + 1) & ~(int64_t)1;       // even: 16-byte multiple (stays inside the buffers)
-        const uint32_t bytes = (uint32_t)rows * 8;
-        const uint32_t bar = bar0 + 8 * st;
-        const uint32_t dst = sbase + (uint32_t)(st * kRankStageBytes);
-        tc::mbar_expect_tx(bar, bytes * kRankPlanes);
-        tc::bulk_load(dst, a.row_info + row0, bytes, bar);
-        for (int j = 0; j < RS_NOPT; ++j)
-            tc::bulk_load(dst + (uint32_t)((1 + j) * kRankTile * 8), a.predbuf + (int64_t)j * a.PS + row0, bytes, bar);
-    };
-    if (tid == 0)
-        for (int st = 0; st < kRankStages; ++st) {
-            const int64_t tile = blockIdx.x + (int64_t)st * gridDim.x;
-            if (tile < ntiles) issue(tile, st);
-        }
-    RankTally c;
-    int64_t i = 0;
-    bool failed = false;
-    for (;; ++i) {
-        const int64_t tile = blockIdx.x + i * gridDim.x;
-        if (tile >= ntiles) break;
-        const int st = (int)(i % kRankStages);
-        const uint32_t par = (uint32_t)((i / kRankStages) & 1);
-        const bool ok = tc::mbar_wait(bar0 + 8 * st, par, a.dstatus, -20);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        const unsigned char* stage = rsm + st * kRankStageBytes;
-        const unsigned long long info = reinterpret_cast<const unsigned long long*>(stage)[tid];
-        double pred[RS_NOPT];
+    if (warp == kRankWarps) {                  // producer
+        if (lane != 0) return;
+        int64_t q = 0;                         // tiles issued
+        int st = 0;
+        uint32_t eph = 0;                      // parity of the next "empty" phase to wait for
+        bool failed = false;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++q) {
+            if (q >= kRankStages &&            // every consumer warp has read the stage's last tile
+                !tc::mbar_wait(empty0 + 8 * st, eph, a.dstatus, -22)) {
+                failed = true;
+                break;
+            }
+            tc::fence_proxy_async_smem();
+            const int64_t row0 = tile * kRankTile;
+            const int64_t rows = nrows - row0 < kRankTile ? nrows - row0 : kRankTile;
+            // even: a 16-byte multiple (stays inside the buffers: PS and the record array are even)
+            const uint32_t bytes = (uint32_t)((rows + 1) & ~(int64_t)1) * 8;
+            const uint32_t bar = full0 + 8 * st;
+            const uint32_t dst = sbase + (uint32_t)(st * kRankStageBytes);
+            tc::mbar_expect_tx(bar, bytes * kRankPlanes);
+            tc::bulk_load(dst, a.row_info + row0, bytes, bar);
 #pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j)
-            pred[j] = reinterpret_cast<const double*>(stage + (1 + j) * kRankTile * 8)[tid];
-        __syncthreads();                       // the stage has been read: refill it
-        if (tid == 0) {
-            const int64_t next = tile + (int64_t)kRankStages * gridDim.x;
-            if (next < ntiles) {
-                tc::fence_proxy_async_smem();
-                issue(next, st);
+            for (int j = 0; j < RS_NOPT; ++j)
+                tc::bulk_load(dst + (uint32_t)((1 + j) * kRankTile * 8), a.predbuf + (int64_t)j * a.PS + row0, bytes, bar);
+            if (++st == kRankStages) {
+                st = 0;
+                if (q >= kRankStages) eph ^= 1u;
             }
         }
-        const int64_t row = tile * kRankTile + tid;
-        if constexpr (PACK) {                  // the tile's recommendations, for the packed output
-            const int nrec = row < nrows ? rank_row<true>(a, row, info, pred, c) : 0;
-            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)nrec);
-            if ((tid & 31) == 0 && v) atomicAdd(a.tile_sum + tile, (unsigned long long)v);
-        } else {
-            if (row < nrows) rank_row(a, row, info, pred, c);
-        }
-    }
-    if (failed) {                              // drain this block's copies still in flight
-        if (tid == 0)
-            for (int64_t q = i; q < i + kRankStages; ++q) {   // tiles i .. i + 2 were issued
-                const int64_t tile = blockIdx.x + q * gridDim.x;
-                if (tile >= ntiles) break;
-                tc::mbar_wait(bar0 + 8 * (int)(q % kRankStages), (uint32_t)((q / kRankStages) & 1), a.dstatus, -21);
-            }
-        __syncthreads();
+        if (failed)                            // the copies of tiles q - 3 .. q - 1 were issued
+            for (int64_t x = q - 1; x >= 0 && x >= q - kRankStages; --x)
+                tc::mbar_wait(full0 + 8 * (int)(x % kRankStages), (uint32_t)((x / kRankStages) & 1), a.dstatus, -23);
         return;
+    }
+    RankTally c;
+    int st = 0;
+    uint32_t par = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool ok = tc::mbar_wait(full0 + 8 * st, par, a.dstatus, -20);
+        if (!__all_sync(0xffffffffu, ok)) return;
+        const unsigned char* stage = rsm + st * kRankStageBytes;
+        const int64_t row0 = tile * kRankTile + tid;
+        unsigned long long info[kRankRpt];
+        double pred[kRankRpt][RS_NOPT];
+#pragma unroll
+        for (int h = 0; h < kRankRpt; ++h) {
+            const int r = h * kRankCons + tid;
+            const bool in = row0 + h * kRankCons < nrows;
+            info[h] = in ? reinterpret_cast<const unsigned long long*>(stage)[r] : 0ull;
+#pragma unroll
+            for (int j = 0; j < RS_NOPT; ++j)
+                pred[h][j] = in ? reinterpret_cast<const double*>(stage + (1 + j) * kRankTile * 8)[r] : 0.0;
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(empty0 + 8 * st);   // this warp has read the stage
+        if (++st == kRankStages) {
+            st = 0;
+            par ^= 1u;
+        }
+        if constexpr (PACK) {                  // the tile's recommendations, for the packed output
+            int nrec = 0;
+#pragma unroll
+            for (int h = 0; h < kRankRpt; ++h)
+                if (row0 + h * kRankCons < nrows) nrec += rank_row<true>(a, row0 + h * kRankCons, info[h], pred[h], c);
+            const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)nrec);
+            if (lane == 0 && v) atomicAdd(a.tile_sum + tile, (unsigned long long)v);
+        } else {
+#pragma unroll
+            for (int h = 0; h < kRankRpt; ++h)
+                if (row0 + h * kRankCons < nrows) rank_row(a, row0 + h * kRankCons, info[h], pred[h], c);
+        }
     }
     if (a.counters) {
         const uint32_t vals[10] = {c.rows, c.pred, c.scored, c.sign, c.rec, c.reck, c.rech, c.t1, c.t1h, c.inv};
@@ -1493,7 +1527,7 @@ rank_pass_kernel(const RankPassArgs a) {
 #pragma unroll
         for (int q = 0; q < 10; ++q) {
             const uint32_t v = __reduce_add_sync(0xffffffffu, vals[q]);
-            if ((tid & 31) == 0 && v) atomicAdd(a.counters + slot[q], (unsigned long long)v);
+            if (lane == 0 && v) atomicAdd(a.counters + slot[q], (unsigned long long)v);
         }
     }
 }
@@ -2051,7 +2085,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                  a.counters,
                  a.row_offsets, a.train_masks, a.rec_offsets, w.cand, rank ? w.predbuf : nullptr,
                  a.rows_cap, plane_stride(a.rows_cap), a.flags, a.dstatus, a.Z, a.x_offsets,
-                 a.feat_width, a.max_feat, a.tune_order};
+                 a.feat_width, a.max_feat, a.tune_order, rank ? w.row_info : nullptr};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -2147,7 +2181,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         e = cudaFuncSetAttribute(rank_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_kern, kRankTile, kRankSmem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_kern, kRankThreads, kRankSmem);
         if (e != cudaSuccess) return e;
         // persistent: tune_rank_waves (8, 16, 32) scales the resident blocks per SM by 1/4, 1/2, 1
         int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
@@ -2156,7 +2190,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         const int64_t tiles = (a.rows_cap + kRankTile - 1) / kRankTile;
         if (blocks > tiles) blocks = tiles;
         if (blocks < 1) blocks = 1;
-        rank_kern<<<(unsigned)blocks, kRankTile, kRankSmem, st>>>(ra);
+        rank_kern<<<(unsigned)blocks, kRankThreads, kRankSmem, st>>>(ra);
         if (packed && tiles_cap > 0) {
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;

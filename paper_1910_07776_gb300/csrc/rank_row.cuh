@@ -1,8 +1,8 @@
 // rank_row.cuh -- device pieces shared by the batched predict/rank path (k_fit.cu) and the
 // transfer path (k_transfer.cu): order keys of doubles, FP64 reciprocals with few FP64
-// instructions, the failure pattern of a fit, the scoring summary of a version, and the
-// ranking, threshold, top-k and scoring of one test row (Sec. 2 tier 3, Sec. 5, Sec. 6), plus
-// the neighbour list of the instance-based learner.
+// instructions, the scoring summary of a version, and the ranking, threshold, top-k and
+// scoring of one test row (Sec. 2 tier 3, Sec. 5, Sec. 6), plus the neighbour list of the
+// instance-based learner.
 #pragma once
 #include <string.h>
 
@@ -22,11 +22,13 @@ __device__ __forceinline__ bool pos_finite(double x) {
 __device__ __forceinline__ bool finite_bits(double x) {
     return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
 }
-// Order-preserving integer key of a non-NaN double; -0.0 and +0.0 share key 0.
+// Order-preserving integer key of a non-NaN double: the bit pattern for a positive sign, minus
+// the magnitude bits for a negative one (so -0.0 and +0.0 share key 0, and every key is above
+// INT64_MIN).
 __device__ __forceinline__ long long okey(double x) {
-    long long b = __double_as_longlong(x);
-    if (b == (long long)0x8000000000000000ull) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+    const long long b = __double_as_longlong(x);
+    const long long s = b >> 63;                       // all ones for a negative sign
+    return ((b & 0x7fffffffffffffffll) ^ s) - s;
 }
 
 // float <-> double for values inside the float normal range, by re-packing the IEEE-754
@@ -81,8 +83,8 @@ __device__ __forceinline__ double rcp_newton(double d) {
 inline long long okey_host(double x) {
     long long b;
     memcpy(&b, &x, sizeof(b));
-    if (b == (long long)0x8000000000000000ull) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+    const long long m = b & 0x7fffffffffffffffll;
+    return b < 0 ? -m : m;
 }
 
 // Scoring summary of version t of a program (its masks msk, log times lt, and the slot of each
@@ -115,12 +117,6 @@ __device__ __forceinline__ uint32_t row_summary(int t, int V, const uint8_t* msk
     }
     return (uint32_t)kn | ((uint32_t)apos << 6) | (ord << 12);
 }
-
-// A fit that failed writes this signalling-NaN pattern to its candidate rows instead of
-// predictions.  Arithmetic never produces a signalling NaN, so the rank pass tells failed
-// fits from predictions by the value alone, without reading the fit status of each row's
-// split (fits without a training pair are marked in the row records instead).
-constexpr long long kFailBits = 0x7ff4000000000001ll;
 
 constexpr int kIbkK = RS_IBK_NEIGHBORS;   // neighbours of the instance-based learner
 
@@ -158,18 +154,15 @@ struct RankTally {
 // for each candidate j, the set of candidates that rank before it; its place is the
 // popcount of that set restricted to the candidates at or above the threshold.
 // info64: the row's scoring summary (row_summary) | version mask << 30 | mask of the
-// optimizations whose fit has no training pair << 36.
+// optimizations whose fit has no training pair or failed << 36.
 template <bool PACK = false>
 __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
                                         const double (&pred)[RS_NOPT], RankTally& c) {
     const uint32_t info = (uint32_t)info64;
     const int mt = (int)(info64 >> 30) & 63;
     const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
-    // a candidate counts when its fit had a training pair (row record) and did not fail
-    // (the failure pattern in the prediction plane)
-    int okm = ~(int)(info64 >> 36) & 63;
-#pragma unroll
-    for (int j = 0; j < RS_NOPT; ++j) okm &= ~((int)(__double_as_longlong(pred[j]) == kFailBits) << j);
+    // a candidate counts when its fit had a training pair and did not fail (row record)
+    const int okm = ~(int)(info64 >> 36) & 63;
     const int validm = candm & okm;
     long long key[RS_NOPT];
     int above = 0, spos = 0;
@@ -213,9 +206,7 @@ __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsi
 #pragma unroll
         for (int j = 0; j < RS_NOPT; ++j)
             if ((rk >> j) & 1) o[pos[j]] = pred[j];
-#pragma unroll
-        for (int x = 0; x < RS_NOPT; ++x)
-            if (x >= nrec && x < a.k) o[x] = nan_d();
+        for (int x = nrec; x < a.k; ++x) o[x] = nan_d();
     }
     if (a.pred_all)
 #pragma unroll
@@ -232,18 +223,22 @@ __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsi
     c.rech += __popc(rk & scored & apos);
     c.inv += __popc(candm & ~okm);
     if (scored) {
-        int bp = 0;
+        // ba: the scored optimization first in the actual order -- the order's first entry
+        // when every known optimization is scored (unknown ones are ordered last)
+        int ba = (info >> 12) & 7;
+        if (scored != known) {
 #pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j)
-            if (((scored >> j) & 1) && !(bm[j] & scored)) bp = j;
-        int ba = -1;
-#pragma unroll
-        for (int x = 0; x < RS_NOPT; ++x) {
-            const int j = (info >> (12 + 3 * x)) & 7;
-            if (ba < 0 && ((scored >> j) & 1)) ba = j;
+            for (int x = RS_NOPT - 1; x >= 0; --x) {
+                const int j = (info >> (12 + 3 * x)) & 7;
+                if ((scored >> j) & 1) ba = j;
+            }
         }
+        // a top-1 hit: no scored optimization is ranked before ba by the predictions
+        int bmba = bm[0];
+#pragma unroll
+        for (int j = 1; j < RS_NOPT; ++j) bmba = ba == j ? bm[j] : bmba;
         c.t1 += 1;
-        c.t1h += (bp == ba);
+        c.t1h += !(bmba & scored);
     }
     return nrec;
 }

@@ -110,10 +110,6 @@ struct Layout {
     static constexpr int kBytes = STAGES * kStage + kBars + 1024;   // + alignment slack
 };
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 constexpr int kEpiWarps = 8;                          // two per TMEM lane quarter
 constexpr int kGemmThreads = (2 + kEpiWarps) * 32;    // producer, MMA issuer, epilogue
 
