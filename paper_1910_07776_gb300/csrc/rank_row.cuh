@@ -24,11 +24,12 @@ __device__ __forceinline__ bool finite_bits(double x) {
 }
 // Order-preserving integer key of a non-NaN double: the bit pattern for a positive sign, minus
 // the magnitude bits for a negative one (so -0.0 and +0.0 share key 0, and every key is above
-// INT64_MIN).
+// INT64_MIN).  For a negative sign b - INT64_MIN is the magnitude, so the key is INT64_MIN - b
+// in wrapping arithmetic; no mask of the sign bit appears, which a compiler may turn into an
+// FP64 absolute value (an instruction of the slow FP64 pipe).
 __device__ __forceinline__ long long okey(double x) {
     const long long b = __double_as_longlong(x);
-    const long long s = b >> 63;                       // all ones for a negative sign
-    return ((b & 0x7fffffffffffffffll) ^ s) - s;
+    return b < 0 ? (long long)(0x8000000000000000ull - (unsigned long long)b) : b;
 }
 
 // float <-> double for values inside the float normal range, by re-packing the IEEE-754
