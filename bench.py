@@ -440,11 +440,17 @@ def main():
     flush = torch.empty(32 * 1024 * 1024, dtype=torch.int64, device=dev)
     cws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    ctx.profile_enable(True)
+    # the whole step (rs_cv_step: the planning on the context's second stream beside the
+    # standardization and the Gram) captured once as a CUDA graph, one launch per step
+    graph = ctx.cv_graph(db, ds, cws, out.rec_offsets, out.rec_code, lam=CFG["lam"], k=CFG["k"],
+                         tau=CFG["tau"], rec_pred=out.rec_pred, counters=out.counters)
 
     def step():
-        # the whole step in one call (rs_cv_step): the planning runs on the context's second
-        # stream beside the standardization and the Gram
+        ev[0].record(stream)
+        graph.launch()
+        ev[1].record(stream)
+
+    def eager_step():
         ev[0].record(stream)
         ctx.cv_step(db, ds, cws, out.rec_offsets, out.rec_code, lam=CFG["lam"], k=CFG["k"],
                     tau=CFG["tau"], rec_pred=out.rec_pred, counters=out.counters)
@@ -465,15 +471,12 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     t_clk = time.perf_counter()
-    stages = {}
     tot = 0.0
     for _ in range(args.steps):
         between()
         step()
         torch.cuda.synchronize()
         tot += ev[0].elapsed_time(ev[1])
-        for k_, v_ in ctx.profile_read().items():
-            stages[k_] = stages.get(k_, 0.0) + v_
     torch.cuda.synchronize()
     clocks.mark("timed_end")
     # the same step keeps running until the clock record spans at least one second (a short
@@ -485,8 +488,8 @@ def main():
         torch.cuda.synchronize()
         sus_ms += ev[0].elapsed_time(ev[1])
         sus_n += 1
-        ctx.profile_read()
     clk = clocks.stop()
+    graph.close()
     clk["after_timed_region"] = {"steps": sus_n, "ms_per_step": sus_ms / sus_n if sus_n else None}
     tot, R_total = aggregate_over_ranks(tot, R, world, dev)
     ctx.check_device_status()
@@ -498,6 +501,25 @@ def main():
     cnt = out.counters.cpu().numpy().view(np.uint64).astype(np.float64)
     acc = {"sign_accuracy": cnt[3] / max(cnt[2], 1), "top1_hit_rate": cnt[8] / max(cnt[7], 1),
            "rec_precision": cnt[6] / max(cnt[5], 1), "recs_per_row": cnt[4] / max(cnt[0], 1)}
+
+    # the stage breakdown (not part of the value): the same step as an eager rs_cv_step call
+    # with the library's stage events on
+    ctx.profile_enable(True)
+    between()
+    eager_step()
+    torch.cuda.synchronize()
+    ctx.profile_read()
+    stages = {}
+    eager_tot = 0.0
+    for _ in range(args.steps):
+        between()
+        eager_step()
+        torch.cuda.synchronize()
+        eager_tot += ev[0].elapsed_time(ev[1])
+        for k_, v_ in ctx.profile_read().items():
+            stages[k_] = stages.get(k_, 0.0) + v_
+    ctx.profile_enable(False)
+    ctx.check_device_status()
 
     # the stages before the solvers, each alone (not part of the value): in the step the
     # planning overlaps the standardization and the Gram
@@ -630,13 +652,16 @@ def main():
                    "parallelism": (f"{world} GPUs, a job of {world} x 64 programs split by the longest-"
                                    "processing-time rule, no data-path collective, counters summed at the end"
                                    if world > 1 else "1 GPU")},
-        "kernels_ms": {"step": ms_step, **{k_ + "_alone": v_ for k_, v_ in alone.items()},
+        "kernels_ms": {"step": ms_step, "eager_step": eager_tot / args.steps,
+                       **{k_ + "_alone": v_ for k_, v_ in alone.items()},
                        "solve_and_rank": fit_ms,
                        **{"fit." + k_: v_ for k_, v_ in stage_ms.items()},
-                       "note": "one rs_cv_step call per step; the planning (fit.pairs, fit.plan_fits, "
-                               "fit.bucket_fits) runs on a second stream beside the standardization and "
-                               "the Gram, so fit.bucket_fits spans the bucketing and the wait for the "
-                               "Gram; *_alone: those stages timed on their own"},
+                       "note": "step: one CUDA-graph launch of the whole rs_cv_step per step (the value); "
+                               "eager_step and the fit.* stages: the same step as an eager rs_cv_step "
+                               "call with the library's stage events; the planning (fit.pairs, "
+                               "fit.plan_fits, fit.bucket_fits) runs on a second stream beside the "
+                               "standardization and the Gram, so fit.bucket_fits spans the bucketing and "
+                               "the wait for the Gram; *_alone: those stages timed on their own"},
         "roofline": roof,
         "accuracy": acc,
         "plain_form": plain,

@@ -123,6 +123,7 @@ dlam_kernel(const int64_t* __restrict__ row_off, const double* __restrict__ K, d
 }
 
 // ====================================================================== plan
+constexpr int kPlanProgs = 8;                // programs whose pair tables a plan block stages
 // One thread per split: the six pair masks of its fits (the pair loops run over one
 // program's pair tables, uniform across a warp whose splits share the program), their sort
 // keys n * kCntBins + c (c = the predictions the fit makes when predictions are wanted, else
@@ -138,40 +139,71 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                  const uint32_t* __restrict__ rowinfo, const uint64_t* __restrict__ cand, int cand_all,
                  int count_preds, int* dstatus) {
     __shared__ unsigned h[kHist];
+    // the tables of the block's first kPlanProgs programs (its splits' programs are
+    // consecutive): pair slots [program][before / after][optimization][32], pair counts,
+    // candidate masks, scoring summaries and version masks of the program's slots
+    __shared__ __align__(16) uint8_t tab[kPlanProgs][2][RS_NOPT][RS_MAXPAIRS];
+    __shared__ int snp[kPlanProgs][RS_NOPT];
+    __shared__ uint64_t scand[kPlanProgs][RS_NOPT];
+    __shared__ uint32_t sri[kPlanProgs][RS_MAXV];
+    __shared__ uint8_t smk[kPlanProgs][RS_MAXV];
+    __shared__ int p_first;
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
-    __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = s < S ? rs_find_segment(split_off, P, s) : 0;
+    if (threadIdx.x == 0) p_first = p;
+    __syncthreads();
+    {
+        const int p0 = p_first, np_tab = P - p0 < kPlanProgs ? P - p0 : kPlanProgs;
+        const int words = np_tab * RS_NOPT * RS_MAXPAIRS / 16;       // 16-byte words per table
+        for (int w = threadIdx.x; w < 2 * words; w += blockDim.x) {
+            const int t = w / words, r = w - t * words;               // table (before / after), word
+            const int q = r / (RS_NOPT * RS_MAXPAIRS / 16), k = r - q * (RS_NOPT * RS_MAXPAIRS / 16);
+            const uint8_t* src = (t ? pa : pb) + (int64_t)(p0 + q) * RS_NOPT * RS_MAXPAIRS;
+            reinterpret_cast<uint4*>(&tab[q][t][0][0])[k] = __ldg(reinterpret_cast<const uint4*>(src) + k);
+        }
+        for (int i = threadIdx.x; i < np_tab * RS_MAXV; i += blockDim.x) {
+            const int q = i / RS_MAXV, t = i - q * RS_MAXV, pq = p0 + q;
+            const int64_t r0 = row_off[pq];
+            sri[q][t] = rowinfo[(int64_t)pq * RS_MAXV + t];
+            smk[q][t] = t < row_off[pq + 1] - r0 ? masks[r0 + t] : 0;
+            if (t < RS_NOPT) {
+                snp[q][t] = npair[pq * RS_NOPT + t];
+                scand[q][t] = cand ? cand[pq * RS_NOPT + t] : 0ull;
+            }
+        }
+    }
+    __syncthreads();
     if (s < S) {
-        const int p = rs_find_segment(split_off, P, s);
         const int V = (int)(row_off[p + 1] - row_off[p]);
         const bool okV = V >= 1 && V <= RS_MAXV;
         split_prog[s] = p;
         const uint64_t full = okV ? rs_full_mask(V) : 0ull;
         const uint64_t T = tm[s] & full;
         int emptym = 0;
-        // the program's pair tables (32 before / 32 after slots per optimization) come in as
-        // 16-byte vectors, all issued before the first is used
-        ulonglong2 vb[RS_NOPT][2], va[RS_NOPT][2];
-        int np[RS_NOPT];
-#pragma unroll
+        // the program's pair tables: from shared memory, else (a block spanning more than
+        // kPlanProgs programs) from global memory, as 16-byte vectors
+        const int q = p - p_first;
+        const bool st = q < kPlanProgs;
+        const uint8_t* tb = st ? &tab[q][0][0][0] : pb + (int64_t)p * RS_NOPT * RS_MAXPAIRS;
+        const uint8_t* ta = st ? &tab[q][1][0][0] : pa + (int64_t)p * RS_NOPT * RS_MAXPAIRS;
+        const int* npp = st ? snp[q] : npair + p * RS_NOPT;
+        const uint64_t* cp = st ? scand[q] : cand + p * RS_NOPT;
+        const uint32_t* rip = st ? sri[q] : rowinfo + (int64_t)p * RS_MAXV;
+        const uint8_t* mkp = st ? smk[q] : masks + row_off[p];
+#pragma unroll 2
         for (int j = 0; j < RS_NOPT; ++j) {
-            const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
-            const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(pb + base);
-            const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(pa + base);
-            vb[j][0] = __ldg(b2);
-            vb[j][1] = __ldg(b2 + 1);
-            va[j][0] = __ldg(a2);
-            va[j][1] = __ldg(a2 + 1);
-            np[j] = okV ? npair[p * RS_NOPT + j] : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < RS_NOPT; ++j) {
+            const int npj = okV ? npp[j] : 0;
+            const ulonglong2 vb[2] = {reinterpret_cast<const ulonglong2*>(tb + j * RS_MAXPAIRS)[0],
+                                      reinterpret_cast<const ulonglong2*>(tb + j * RS_MAXPAIRS)[1]};
+            const ulonglong2 va[2] = {reinterpret_cast<const ulonglong2*>(ta + j * RS_MAXPAIRS)[0],
+                                      reinterpret_cast<const ulonglong2*>(ta + j * RS_MAXPAIRS)[1]};
             uint32_t pm = 0;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
-                if (8 * w >= np[j]) break;
-                const unsigned long long wb = (w & 1) ? vb[j][w >> 1].y : vb[j][w >> 1].x;
-                const unsigned long long wa = (w & 1) ? va[j][w >> 1].y : va[j][w >> 1].x;
+                if (8 * w >= npj) break;
+                const unsigned long long wb = (w & 1) ? vb[w >> 1].y : vb[w >> 1].x;
+                const unsigned long long wa = (w & 1) ? va[w >> 1].y : va[w >> 1].x;
                 uint32_t part = 0;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -179,7 +211,7 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                     const unsigned sa = (unsigned)(wa >> (8 * e)) & 63u;
                     part |= (uint32_t)((T >> sb) & (T >> sa) & 1ull) << e;
                 }
-                const int keep = np[j] - 8 * w;           // pairs of this word that exist
+                const int keep = npj - 8 * w;             // pairs of this word that exist
                 if (keep < 8) part &= (1u << keep) - 1u;
                 pm |= part << (8 * w);
             }
@@ -191,7 +223,7 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
             }
             // c = the predictions the fit makes: its split's test rows that are candidates
             int c = 0;
-            if (count_preds && n > 0) c = __popcll(~T & full & (cand_all ? full : __ldg(cand + p * RS_NOPT + j)));
+            if (count_preds && n > 0) c = __popcll(~T & full & (cand_all ? full : cp[j]));
             const int key = n * kCntBins + c;
             fit_pm[s * RS_NOPT + j] = pm;
             fit_key[s * RS_NOPT + j] = (uint16_t)key;
@@ -201,12 +233,10 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         }
         if (row_info && okV) {
             const uint64_t test = ~tm[s] & rs_full_mask(V);
-            const int64_t rv = row_off[p];
             int64_t r = rec_offsets[s];
             for (uint64_t x = test; x && r < rows_cap; x &= x - 1, ++r) {
                 const int t = __ffsll((long long)x) - 1;
-                row_info[r] = (unsigned long long)rowinfo[(int64_t)p * RS_MAXV + t] |
-                              ((unsigned long long)(masks[rv + t] & 63) << 30) |
+                row_info[r] = (unsigned long long)rip[t] | ((unsigned long long)(mkp[t] & 63) << 30) |
                               ((unsigned long long)emptym << 36);
             }
         }
@@ -484,7 +514,7 @@ __device__ __forceinline__ double* coef_out(const SolveArgs& a, int64_t f) {
 // to the results: every result goes to its fit's own place.
 // A fit without a training pair (n = 0) is finished here (status RS_FIT_EMPTY); the rank
 // pass knows it from the row records.
-__global__ void __launch_bounds__(kBucketThreads)
+__global__ void __launch_bounds__(kBucketThreads, 2)
 bucket_fits_kernel(int64_t S6, const uint16_t* __restrict__ fit_key, const unsigned* __restrict__ hist,
                    unsigned* cursor, uint4* recs, int64_t* fit_off, uint8_t* status, double* coef_user,
                    unsigned long long* counters, const uint32_t* __restrict__ fit_pm,
@@ -497,11 +527,19 @@ bucket_fits_kernel(int64_t S6, const uint16_t* __restrict__ fit_key, const unsig
     const int64_t f0 = (int64_t)blockIdx.x * (kBucketThreads * kBucketPer) + threadIdx.x;
     int key[kBucketPer];
     unsigned local[kBucketPer];
+    uint4 rec[kBucketPer];                   // each fit's record, loaded before the block's scan
 #pragma unroll
     for (int q = 0; q < kBucketPer; ++q) {
         const int64_t f = f0 + (int64_t)q * kBucketThreads;
         key[q] = f < S6 ? fit_key[f] : 0;
         local[q] = key[q] >= kCntBins ? atomicAdd(&lcount[key[q]], 1u) : 0u;
+        rec[q] = make_uint4((unsigned)f, 0u, 0u, 0u);
+        if (key[q] >= kCntBins) {
+            const int p = split_prog[f / RS_NOPT];
+            rec[q].y = (unsigned)p;
+            rec[q].z = fit_pm[f];
+            rec[q].w = (unsigned)(row_off[p + 1] - row_off[p]);
+        }
     }
     __syncthreads();
     // warp w scans the counts of n = w + 1 and n = w + 17: exclusive offsets over c, and the
@@ -552,9 +590,7 @@ bucket_fits_kernel(int64_t S6, const uint16_t* __restrict__ fit_key, const unsig
             }
         } else {
             const long long pos = start[n] + lbase[n] + lcount[key[q]] + local[q];
-            // the solver's whole first round trip in one 16-byte record
-            const int p = split_prog[f / RS_NOPT];
-            recs[pos] = make_uint4((unsigned)f, (unsigned)p, fit_pm[f], (unsigned)(row_off[p + 1] - row_off[p]));
+            recs[pos] = rec[q];              // the solver's whole first round trip in 16 bytes
             if (fit_off) fit_off[f] = cstart[n] + (pos - start[n]) * (n + 1);
         }
     }
