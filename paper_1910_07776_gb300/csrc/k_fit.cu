@@ -1453,7 +1453,8 @@ constexpr int kRankThreads = kRankCons + 32; // and one producer warp
 constexpr int kRankStages = 3;
 constexpr int kRankPlanes = 1 + RS_NOPT;     // the row records, then the six prediction planes
 constexpr size_t kRankStageBytes = (size_t)kRankPlanes * kRankTile * 8;
-constexpr size_t kRankSmem = kRankStages * kRankStageBytes + 2 * kRankStages * 8;
+constexpr size_t kRankOutBytes = (size_t)kRankCons * RS_NOPT * 8;   // reported values, per warp
+constexpr size_t kRankSmem = kRankStages * kRankStageBytes + 2 * kRankStages * 8 + kRankOutBytes;
 static_assert(kRankCons % 32 == 0 && kRankCons * kRankRpt == kRankTile, "whole warps of rows");
 
 // Persistent blocks over tiles of kRankTile rows, a producer warp and kRankWarps consumer
@@ -1462,9 +1463,11 @@ static_assert(kRankCons % 32 == 0 && kRankCons * kRankRpt == kRankTile, "whole w
 // shared-memory ring: a stage is refilled once every consumer warp has arrived on its "empty"
 // mbarrier, and its copies complete on its "full" mbarrier.  A consumer warp waits for the
 // stage, reads its rows into registers (kRankRpt per thread, kRankCons rows apart), arrives on
-// "empty" and ranks the rows while the copies of the tiles ahead fly.  Bounded waits: on a
-// timeout RS_ETIMEOUT is set and the warp leaves; the producer waits (bounded) for the copies
-// it has in flight before it leaves.
+// "empty" and ranks the rows while the copies of the tiles ahead fly.  The reported values of a
+// warp's 32 rows (32 k doubles, contiguous in rec_pred) are gathered in shared memory and
+// written as 16-byte stores, instead of each lane's k scattered 8-byte stores.  Bounded waits:
+// on a timeout RS_ETIMEOUT is set and the warp leaves; the producer waits (bounded) for the
+// copies it has in flight before it leaves.
 template <bool PACK>
 __global__ void __launch_bounds__(kRankThreads, RS_RANK_MINB)
 rank_pass_kernel(const RankPassArgs a) {
@@ -1522,6 +1525,11 @@ rank_pass_kernel(const RankPassArgs a) {
     RankTally c;
     int st = 0;
     uint32_t par = 0;
+    // this warp's slots for the reported values: [32 kRankRpt rows][k]
+    double* wout = reinterpret_cast<double*>(rsm + kRankStages * kRankStageBytes + 2 * kRankStages * 8) +
+                   (size_t)warp * 32 * kRankRpt * RS_NOPT;
+    // k = 3 (the method's top-3) with a 16-byte aligned rec_pred; other k store per lane
+    const bool stage_out = !PACK && a.rec_pred && a.k == 3 && (reinterpret_cast<uintptr_t>(a.rec_pred) & 15) == 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const bool ok = tc::mbar_wait(full0 + 8 * st, par, a.dstatus, -20);
         if (!__all_sync(0xffffffffu, ok)) return;
@@ -1551,6 +1559,28 @@ rank_pass_kernel(const RankPassArgs a) {
                 if (row0 + h * kRankCons < nrows) nrec += rank_row<true>(a, row0 + h * kRankCons, info[h], pred[h], c);
             const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)nrec);
             if (lane == 0 && v) atomicAdd(a.tile_sum + tile, (unsigned long long)v);
+        } else if (stage_out) {
+#pragma unroll
+            for (int h = 0; h < kRankRpt; ++h) {
+                if (row0 + h * kRankCons < nrows)
+                    rank_row<false, true, 3>(a, row0 + h * kRankCons, info[h], pred[h], c,
+                                             wout + (h * 32 + lane) * 3);
+                __syncwarp();
+                // the warp's rows h kRankCons + 32 warp ... + 31: 96 contiguous doubles of rec_pred
+                const int64_t wrow = tile * kRankTile + h * kRankCons + warp * 32;
+                const double2* src = reinterpret_cast<const double2*>(wout + h * 32 * 3);
+                double2* dst = reinterpret_cast<double2*>(a.rec_pred + wrow * 3);
+                if (wrow + 32 <= nrows) {              // a whole warp of rows: 48 pairs
+                    dst[lane] = src[lane];
+                    if (lane < 16) dst[32 + lane] = src[32 + lane];
+                } else {
+                    const int64_t nv = (nrows - wrow) * 3;           // doubles (none past the end)
+                    const double* s1 = reinterpret_cast<const double*>(src);
+                    double* d1 = reinterpret_cast<double*>(dst);
+                    for (int64_t q = lane; q < nv; q += 32) d1[q] = s1[q];
+                }
+                __syncwarp();
+            }
         } else {
 #pragma unroll
             for (int h = 0; h < kRankRpt; ++h)

@@ -155,10 +155,13 @@ struct RankTally {
 // for each candidate j, the set of candidates that rank before it; its place is the
 // popcount of that set restricted to the candidates at or above the threshold.
 // info64: the row's scoring summary (row_summary) | version mask << 30 | mask of the
-// optimizations whose fit has no training pair or failed << 36.
-template <bool PACK = false>
+// optimizations whose fit has no training pair or failed << 36.  STAGE (k = STAGE_K): the
+// reported values go to so[0 .. k-1] (the caller's shared-memory slots of the row) instead of
+// rec_pred.
+template <bool PACK = false, bool STAGE = false, int STAGE_K = 3>
 __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsigned long long info64,
-                                        const double (&pred)[RS_NOPT], RankTally& c) {
+                                        const double (&pred)[RS_NOPT], RankTally& c,
+                                        double* so = nullptr) {
     const uint32_t info = (uint32_t)info64;
     const int mt = (int)(info64 >> 30) & 63;
     const int candm = (a.flags & RS_RANK_ALL) ? 63 : (~mt & 63);
@@ -202,6 +205,12 @@ __device__ __forceinline__ int rank_row(const RankPassArgs& a, int64_t row, unsi
 #pragma unroll
         for (int j = 0; j < RS_NOPT; ++j)
             if ((rk >> j) & 1) a.pack_dst[pos[j] * a.PS + row] = pred[j];
+    } else if constexpr (STAGE) {              // every slot, then each chosen candidate's
+#pragma unroll
+        for (int x = 0; x < STAGE_K; ++x) so[x] = nan_d();
+#pragma unroll
+        for (int j = 0; j < RS_NOPT; ++j)
+            if ((rk >> j) & 1) so[pos[j]] = pred[j];
     } else if (a.rec_pred) {                   // each chosen candidate writes its own slot
         double* o = a.rec_pred + row * a.k;
 #pragma unroll
