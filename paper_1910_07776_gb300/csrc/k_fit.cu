@@ -87,28 +87,36 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
     __syncthreads();
     if (tid < V) slot_of[msk[tid]] = (int8_t)tid;
     __syncthreads();
-    if (tid < RS_NOPT) {
-        const int j = tid;
+    // warp w takes optimizations w, w + 2, w + 4; its lanes take 32 slots at a time, and a
+    // ballot places each pair after those of the lower slots
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int j = warp; j < RS_NOPT; j += 2) {
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
         int np = 0;
         uint64_t cm = 0;
-        for (int v = 0; v < V; ++v) {
-            const int m = msk[v];
-            if ((m >> j) & 1) continue;
-            cm |= 1ull << v;
-            const int w = slot_of[m | (1 << j)];
-            if (w < 0) continue;
-            if (np == RS_MAXPAIRS) {      // only possible with repeated masks
-                rs_dev_flag(dstatus, RS_EDATA, p);
-                continue;
+        for (int v0 = 0; v0 < V; v0 += 32) {
+            const int v = v0 + lane;
+            const int m = v < V ? msk[v] : (1 << j);
+            const bool c = !((m >> j) & 1);                  // slot v lacks j
+            const int w = c ? slot_of[m | (1 << j)] : -1;
+            const unsigned cb = __ballot_sync(0xffffffffu, c), pm = __ballot_sync(0xffffffffu, w >= 0);
+            cm |= (uint64_t)cb << v0;
+            const int at = np + __popc(pm & ((1u << lane) - 1u));
+            if (w >= 0) {
+                if (at < RS_MAXPAIRS) {
+                    pb[base + at] = (uint8_t)v;
+                    pa[base + at] = (uint8_t)w;
+                    ylab[base + at] = lt[v] - lt[w];
+                } else {
+                    rs_dev_flag(dstatus, RS_EDATA, p);       // only possible with repeated masks
+                }
             }
-            pb[base + np] = (uint8_t)v;
-            pa[base + np] = (uint8_t)w;
-            ylab[base + np] = lt[v] - lt[w];
-            ++np;
+            np += __popc(pm);
         }
-        npair[p * RS_NOPT + j] = np;
-        cand[p * RS_NOPT + j] = cm;
+        if (lane == 0) {
+            npair[p * RS_NOPT + j] = np < RS_MAXPAIRS ? np : RS_MAXPAIRS;
+            cand[p * RS_NOPT + j] = cm;
+        }
     }
     rowinfo[(int64_t)p * RS_MAXV + tid] = row_summary(tid, V, msk, lt, slot_of);
 }

@@ -11,14 +11,6 @@ constexpr int kItems = 4;                       // splits per thread
 constexpr int kPerBlock = kScanThreads * kItems;
 constexpr int kMaxBlocks = kPerBlock;           // one block scans the block sums
 
-__device__ __forceinline__ int64_t rows_of_split(const int64_t* row_off, const int64_t* split_off,
-                                                 const uint64_t* tm, int P, int64_t i) {
-    const int p = rs_find_segment(split_off, P, i);
-    const int V = (int)(row_off[p + 1] - row_off[p]);
-    if (V < 1 || V > RS_MAXV) return 0;
-    return V - __popcll(tm[i] & rs_full_mask(V));
-}
-
 // Block-wide exclusive scan of one int64 per thread; returns the block total in *total.
 __device__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
     __shared__ int64_t warp_sums[kScanThreads / 32];
@@ -52,11 +44,16 @@ count_kernel(int P, const int64_t* row_off, const int64_t* split_off, const uint
              int64_t S, int64_t* out, int64_t* block_sums) {
     const int64_t base = (int64_t)blockIdx.x * kPerBlock + (int64_t)threadIdx.x * kItems;
     int64_t local = 0;
+    // one search for the thread's first split; its next splits are in the same program or
+    // one of the programs after it
+    int p = base < S ? rs_find_segment(split_off, P, base) : 0;
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
         const int64_t i = base + q;
         if (i < S) {
-            const int64_t c = rows_of_split(row_off, split_off, tm, P, i);
+            while (p + 1 < P && split_off[p + 1] <= i) ++p;
+            const int V = (int)(row_off[p + 1] - row_off[p]);
+            const int64_t c = (V < 1 || V > RS_MAXV) ? 0 : V - __popcll(tm[i] & rs_full_mask(V));
             out[i] = c;
             local += c;
         }
