@@ -291,3 +291,48 @@ def test_packed_predictions_equal_the_dense_lists(rs, ctx, flags):
     assert total == want.size
     np.testing.assert_array_equal(got[:total], want)
     assert np.all(got[total:] == 7.0)           # nothing written past the packed lists
+
+
+# ------------------------------------------------------------------------------ failed fits
+@pytest.mark.parametrize("kind", ["half", "frac"])
+def test_failed_fits_leave_their_optimization_out(rs, ctx, kind):
+    """A version with an infinite log time gives its pairs infinite labels: every fit with one
+    of them in training is non-finite (RS_FIT_NONFINITE), in each solver's size range (the
+    frac splits make fits of 1 to 32 pairs).  The failed fit's optimization leaves its split's
+    rows (the row records carry the failure); rankings and counters equal the oracle's."""
+    batch = synth.make_batch(6, versions=(24, 64), feat=24, dtype=np.float64, seed=77)
+    lt = batch.log_time.copy()
+    for p in (1, 4):
+        lt[int(batch.row_offsets[p]) + 3] = np.inf
+    batch.log_time = lt
+    splits = synth.make_splits(batch, kind, 40, seed=78)
+    g, r = _run_both(rs, ctx, batch, splits)
+    assert r.counter("fit_nonfinite") > 0
+    _check_cv(g, r, 3, 1.05)
+
+
+def test_rank_outputs_with_unaligned_rec_pred(rs, ctx):
+    """rec_pred 16-byte aligned (a warp's values go through shared memory as 16-byte stores)
+    and only 8-byte aligned (each lane stores its own values): the same outputs, and nothing
+    written outside the view."""
+    batch = synth.make_batch(7, versions=(20, 64), feat=32, dtype=np.float64, seed=91)
+    splits = synth.make_splits(batch, "half", 50, seed=91)
+    db = rs.DeviceBatch.from_host(batch)
+    ds = rs.DeviceSplits.from_host(splits, batch=batch)
+    zb = db.with_X(ctx.standardize(db))
+    K = ctx.gram(zb, rs.RS_GRAM_F64)
+    ro = ctx.rec_offsets(zb, ds)
+    R = int(ro[-1].item())
+    got = []
+    for off in (0, 1):
+        buf = torch.full((R * 3 + 2,), 7.0, dtype=torch.float64, device="cuda")
+        rp = buf[off:off + R * 3]
+        code = torch.empty(R, dtype=torch.int32, device="cuda")
+        ctx.predict_rank(zb, K, ds, ro, code, lam=1e-3, k=3, tau=1.05, rec_pred=rp)
+        torch.cuda.synchronize()
+        ctx.check_device_status()
+        got.append((code.cpu().numpy(), rp.cpu().numpy(), buf.cpu().numpy()))
+    np.testing.assert_array_equal(got[0][0], got[1][0])
+    np.testing.assert_array_equal(got[0][1], got[1][1])
+    assert got[0][2][-2] == 7.0 and got[0][2][-1] == 7.0
+    assert got[1][2][0] == 7.0 and got[1][2][-1] == 7.0
