@@ -186,9 +186,14 @@ cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch*
     return cudaGetLastError();
 }
 
+#ifndef RS_GRAM_MAXB
+#define RS_GRAM_MAXB 4
+#endif
 cudaError_t rs_launch_gram_f64(const rs_batch* b, double* K, int* dstatus, cudaStream_t st) {
     dim3 grid((unsigned)b->n_programs, kGramChunks);
-    gram_f64_kernel<false><<<grid, kGramThreads, 0, st>>>(b->n_programs, b->row_offsets, b->feat_width,
+    const size_t pad = rs_residency_pad(RS_GRAM_MAXB, sizeof(double) * 2 * RS_MAXV * kGramLd);
+    if (pad) cudaFuncSetAttribute(gram_f64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
+    gram_f64_kernel<false><<<grid, kGramThreads, pad, st>>>(b->n_programs, b->row_offsets, b->feat_width,
                                             b->x_offsets, (const double*)b->X, K, dstatus);
     return cudaGetLastError();
 }

@@ -120,6 +120,7 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     if (active)
         for (int r = g; r < V; r += kGroups) {
             const double d = lv[r][fl] - m;
+            lv[r][fl] = d;                     // kept for the output
             q2 += d * d;
         }
     part[g][fl] = q2;
@@ -135,7 +136,7 @@ standardize_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __
     const bool ok = sd > 1e-12;
     const double rs = ok ? 1.0 / sd : 0.0;
     for (int r = g; r < V; r += kGroups)
-        Z[base + (int64_t)r * F + f] = ok ? (lv[r][fl] - m) * rs : 0.0;
+        Z[base + (int64_t)r * F + f] = ok ? lv[r][fl] * rs : 0.0;
     if (g == 0) {
         if (mu) mu[fo[p] + f] = m;
         if (sigma) sigma[fo[p] + f] = sd;
@@ -209,6 +210,7 @@ group_standardize_kernel(const int64_t* __restrict__ group_off, int max_runs, in
     if (active)
         for (int u = g; u < N; u += kGroups) {
             const double d = lv[u][fl] - m;
+            lv[u][fl] = d;                     // kept for the output
             q2 += d * d;
         }
     part[g][fl] = q2;
@@ -223,7 +225,7 @@ group_standardize_kernel(const int64_t* __restrict__ group_off, int max_runs, in
     const double sd = stat[1][fl];
     const bool ok = sd > 1e-12;
     const double rs = ok ? 1.0 / sd : 0.0;
-    for (int u = g; u < N; u += kGroups) Z[rowx[u] + f] = ok ? (lv[u][fl] - m) * rs : 0.0;
+    for (int u = g; u < N; u += kGroups) Z[rowx[u] + f] = ok ? lv[u][fl] * rs : 0.0;
     if (g == 0) {
         mu[(int64_t)q * stat_stride + f] = m;
         sigma[(int64_t)q * stat_stride + f] = sd;
@@ -298,16 +300,24 @@ cudaError_t rs_launch_transfer_standardize(const rs_batch* train, const rs_batch
     return cudaGetLastError();
 }
 
+#ifndef RS_STD_MAXB
+#define RS_STD_MAXB 0
+#endif
 cudaError_t rs_launch_standardize(const rs_batch* b, double* Z, double* mu, double* sigma,
                                   int* dstatus, cudaStream_t st) {
     dim3 grid((unsigned)b->n_programs, (unsigned)((b->max_feat + kFeat - 1) / kFeat));
-    if (b->dtype == RS_F32)
-        standardize_kernel<float><<<grid, kThreads, 0, st>>>(
+    const size_t pad = rs_residency_pad(RS_STD_MAXB, sizeof(double) * (RS_MAXV * kFeat + kGroups * kFeat + 2 * kFeat +
+                                                                      RS_MAXV + 512));
+    if (b->dtype == RS_F32) {
+        if (pad) cudaFuncSetAttribute(standardize_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
+        standardize_kernel<float><<<grid, kThreads, pad, st>>>(
             b->n_programs, b->row_offsets, b->feat_width, b->x_offsets, b->feat_offsets,
             (const float*)b->X, b->cycles, Z, mu, sigma, dstatus);
-    else
-        standardize_kernel<double><<<grid, kThreads, 0, st>>>(
+    } else {
+        if (pad) cudaFuncSetAttribute(standardize_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
+        standardize_kernel<double><<<grid, kThreads, pad, st>>>(
             b->n_programs, b->row_offsets, b->feat_width, b->x_offsets, b->feat_offsets,
             (const double*)b->X, b->cycles, Z, mu, sigma, dstatus);
+    }
     return cudaGetLastError();
 }

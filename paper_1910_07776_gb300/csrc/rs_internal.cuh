@@ -31,6 +31,16 @@ __device__ __forceinline__ int rs_find_segment(const int64_t* offs, int P, int64
     return lo;
 }
 
+// Dynamic shared memory that caps a kernel at maxb resident blocks per SM (0: no cap): with
+// fewer blocks than the SMs can hold at once, the block scheduler may stack them on some SMs
+// and leave others idle; a cap spreads them.  static_bytes: the kernel's own shared memory.
+inline size_t rs_residency_pad(int maxb, size_t static_bytes) {
+    if (maxb <= 0) return 0;
+    const size_t per = (size_t)228 * 1024 / (size_t)maxb;        // shared memory per SM / cap
+    const size_t own = static_bytes + 1024;                      // + the block's reserved 1 KB
+    return per > own ? per - own : 0;
+}
+
 // Host-side argument rules shared by every entry point that takes a batch or a set of splits:
 // nullptr when the arguments are acceptable, else the reason.
 inline const char* rs_batch_problem(const rs_batch* b, bool need_raw) {
