@@ -1447,30 +1447,25 @@ solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
 #ifndef RS_RANK_TILE
 #define RS_RANK_TILE 256
 #endif
-#ifndef RS_RANK_RPT
-#define RS_RANK_RPT 1
-#endif
 #ifndef RS_RANK_MINB
 #define RS_RANK_MINB 3
 #endif
-constexpr int kRankTile = RS_RANK_TILE;      // rows per tile (one ring stage)
-constexpr int kRankRpt = RS_RANK_RPT;        // rows of a tile per consumer thread
-constexpr int kRankCons = kRankTile / kRankRpt;                    // consumer threads
-constexpr int kRankWarps = kRankCons / 32;   // consumer warps
-constexpr int kRankThreads = kRankCons + 32; // and one producer warp
+constexpr int kRankTile = RS_RANK_TILE;      // rows per tile (one ring stage) = consumer threads
+constexpr int kRankWarps = kRankTile / 32;   // consumer warps
+constexpr int kRankThreads = kRankTile + 32; // and one producer warp
 constexpr int kRankStages = 3;
 constexpr int kRankPlanes = 1 + RS_NOPT;     // the row records, then the six prediction planes
 constexpr size_t kRankStageBytes = (size_t)kRankPlanes * kRankTile * 8;
-constexpr size_t kRankOutBytes = (size_t)kRankCons * RS_NOPT * 8;   // reported values, per warp
+constexpr size_t kRankOutBytes = (size_t)kRankTile * 3 * 8;   // a warp's top-3 values, per warp
 constexpr size_t kRankSmem = kRankStages * kRankStageBytes + 2 * kRankStages * 8 + kRankOutBytes;
-static_assert(kRankCons % 32 == 0 && kRankCons * kRankRpt == kRankTile, "whole warps of rows");
+static_assert(kRankTile % 32 == 0, "whole warps of rows");
 
 // Persistent blocks over tiles of kRankTile rows, a producer warp and kRankWarps consumer
 // warps that never wait for one another.  The producer's lane 0 streams each tile -- the row
 // records and the six prediction planes, seven 1-D TMA bulk copies -- into a 3-stage
 // shared-memory ring: a stage is refilled once every consumer warp has arrived on its "empty"
 // mbarrier, and its copies complete on its "full" mbarrier.  A consumer warp waits for the
-// stage, reads its rows into registers (kRankRpt per thread, kRankCons rows apart), arrives on
+// stage, reads its 32 rows into registers (one per lane), arrives on
 // "empty" and ranks the rows while the copies of the tiles ahead fly.  The reported values of a
 // warp's 32 rows (32 k doubles, contiguous in rec_pred) are gathered in shared memory and
 // written as 16-byte stores, instead of each lane's k scattered 8-byte stores.  Bounded waits:
@@ -1533,27 +1528,22 @@ rank_pass_kernel(const RankPassArgs a) {
     RankTally c;
     int st = 0;
     uint32_t par = 0;
-    // this warp's slots for the reported values: [32 kRankRpt rows][k]
+    // this warp's slots for the reported values: [32 rows][3]
     double* wout = reinterpret_cast<double*>(rsm + kRankStages * kRankStageBytes + 2 * kRankStages * 8) +
-                   (size_t)warp * 32 * kRankRpt * RS_NOPT;
+                   (size_t)warp * 32 * 3;
     // k = 3 (the method's top-3) with a 16-byte aligned rec_pred; other k store per lane
     const bool stage_out = !PACK && a.rec_pred && a.k == 3 && (reinterpret_cast<uintptr_t>(a.rec_pred) & 15) == 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const bool ok = tc::mbar_wait(full0 + 8 * st, par, a.dstatus, -20);
         if (!__all_sync(0xffffffffu, ok)) return;
         const unsigned char* stage = rsm + st * kRankStageBytes;
-        const int64_t row0 = tile * kRankTile + tid;
-        unsigned long long info[kRankRpt];
-        double pred[kRankRpt][RS_NOPT];
+        const int64_t row = tile * kRankTile + tid;
+        const bool in = row < nrows;
+        const unsigned long long info = in ? reinterpret_cast<const unsigned long long*>(stage)[tid] : 0ull;
+        double pred[RS_NOPT];
 #pragma unroll
-        for (int h = 0; h < kRankRpt; ++h) {
-            const int r = h * kRankCons + tid;
-            const bool in = row0 + h * kRankCons < nrows;
-            info[h] = in ? reinterpret_cast<const unsigned long long*>(stage)[r] : 0ull;
-#pragma unroll
-            for (int j = 0; j < RS_NOPT; ++j)
-                pred[h][j] = in ? reinterpret_cast<const double*>(stage + (1 + j) * kRankTile * 8)[r] : 0.0;
-        }
+        for (int j = 0; j < RS_NOPT; ++j)
+            pred[j] = in ? reinterpret_cast<const double*>(stage + (1 + j) * kRankTile * 8)[tid] : 0.0;
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(empty0 + 8 * st);   // this warp has read the stage
         if (++st == kRankStages) {
@@ -1561,38 +1551,28 @@ rank_pass_kernel(const RankPassArgs a) {
             par ^= 1u;
         }
         if constexpr (PACK) {                  // the tile's recommendations, for the packed output
-            int nrec = 0;
-#pragma unroll
-            for (int h = 0; h < kRankRpt; ++h)
-                if (row0 + h * kRankCons < nrows) nrec += rank_row<true>(a, row0 + h * kRankCons, info[h], pred[h], c);
+            const int nrec = in ? rank_row<true>(a, row, info, pred, c) : 0;
             const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)nrec);
             if (lane == 0 && v) atomicAdd(a.tile_sum + tile, (unsigned long long)v);
         } else if (stage_out) {
-#pragma unroll
-            for (int h = 0; h < kRankRpt; ++h) {
-                if (row0 + h * kRankCons < nrows)
-                    rank_row<false, true, 3>(a, row0 + h * kRankCons, info[h], pred[h], c,
-                                             wout + (h * 32 + lane) * 3);
-                __syncwarp();
-                // the warp's rows h kRankCons + 32 warp ... + 31: 96 contiguous doubles of rec_pred
-                const int64_t wrow = tile * kRankTile + h * kRankCons + warp * 32;
-                const double2* src = reinterpret_cast<const double2*>(wout + h * 32 * 3);
-                double2* dst = reinterpret_cast<double2*>(a.rec_pred + wrow * 3);
-                if (wrow + 32 <= nrows) {              // a whole warp of rows: 48 pairs
-                    dst[lane] = src[lane];
-                    if (lane < 16) dst[32 + lane] = src[32 + lane];
-                } else {
-                    const int64_t nv = (nrows - wrow) * 3;           // doubles (none past the end)
-                    const double* s1 = reinterpret_cast<const double*>(src);
-                    double* d1 = reinterpret_cast<double*>(dst);
-                    for (int64_t q = lane; q < nv; q += 32) d1[q] = s1[q];
-                }
-                __syncwarp();
+            if (in) rank_row<false, true, 3>(a, row, info, pred, c, wout + lane * 3);
+            __syncwarp();
+            // the warp's 32 rows: 96 contiguous doubles of rec_pred
+            const int64_t wrow = tile * kRankTile + warp * 32;
+            const double2* src = reinterpret_cast<const double2*>(wout);
+            double2* dst = reinterpret_cast<double2*>(a.rec_pred + wrow * 3);
+            if (wrow + 32 <= nrows) {                  // a whole warp of rows: 48 pairs
+                dst[lane] = src[lane];
+                if (lane < 16) dst[32 + lane] = src[32 + lane];
+            } else {
+                const int64_t nv = (nrows - wrow) * 3;               // doubles (none past the end)
+                const double* s1 = reinterpret_cast<const double*>(src);
+                double* d1 = reinterpret_cast<double*>(dst);
+                for (int64_t q = lane; q < nv; q += 32) d1[q] = s1[q];
             }
+            __syncwarp();
         } else {
-#pragma unroll
-            for (int h = 0; h < kRankRpt; ++h)
-                if (row0 + h * kRankCons < nrows) rank_row(a, row0 + h * kRankCons, info[h], pred[h], c);
+            if (in) rank_row(a, row, info, pred, c);
         }
     }
     if (a.counters) {
