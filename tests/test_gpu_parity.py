@@ -264,8 +264,8 @@ def test_argument_errors(rs, ctx):
         assert e.value.status == rs.RS_EINVAL
 
 
-@pytest.mark.parametrize("flags", [0, 4])
-def test_packed_predictions_equal_the_dense_lists(rs, ctx, flags):
+@pytest.mark.parametrize("flags,k", [(0, 3), (4, 3), (4, 6), (0, 1)])
+def test_packed_predictions_equal_the_dense_lists(rs, ctx, flags, k):
     # RS_PACK_PRED: the reported predictions back to back in row order, no padding; the same
     # values as the dense rec_pred without its NaN slots, and as many as counter 4 says
     batch = synth.make_batch(12, versions=(1, 64), feat=48, dtype=np.float32, seed=321)
@@ -274,17 +274,17 @@ def test_packed_predictions_equal_the_dense_lists(rs, ctx, flags):
     ds = rs.DeviceSplits.from_host(splits, batch=batch)
     R = ds.n_test_rows
     ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
-    dense = rs.alloc_outputs(R, ds.n_splits, 3, "cuda")
-    ctx.cv_step(db, ds, ws, dense.rec_offsets, dense.rec_code, flags=flags, rec_pred=dense.rec_pred,
+    dense = rs.alloc_outputs(R, ds.n_splits, k, "cuda")
+    ctx.cv_step(db, ds, ws, dense.rec_offsets, dense.rec_code, k=k, flags=flags, rec_pred=dense.rec_pred,
                 counters=dense.counters)
-    packed = rs.alloc_outputs(R, ds.n_splits, 3, "cuda")
+    packed = rs.alloc_outputs(R, ds.n_splits, k, "cuda")
     packed.rec_pred.fill_(7.0)
-    ctx.cv_step(db, ds, ws, packed.rec_offsets, packed.rec_code, flags=flags | rs.RS_PACK_PRED,
+    ctx.cv_step(db, ds, ws, packed.rec_offsets, packed.rec_code, k=k, flags=flags | rs.RS_PACK_PRED,
                 rec_pred=packed.rec_pred, counters=packed.counters)
     torch.cuda.synchronize()
     ctx.check_device_status()
     assert torch.equal(dense.rec_code, packed.rec_code) and torch.equal(dense.counters, packed.counters)
-    d = dense.rec_pred.cpu().numpy().reshape(R, 3)
+    d = dense.rec_pred.cpu().numpy().reshape(R, k)
     want = d[~np.isnan(d)]                      # row order, then list order
     total = int(packed.counters[4].item())
     got = packed.rec_pred.cpu().numpy()
