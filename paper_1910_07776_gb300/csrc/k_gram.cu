@@ -97,7 +97,8 @@ gram_f64_kernel(int P, const int64_t* __restrict__ row_off, const int32_t* __res
     }
 }
 
-// Blocks of a transfer problem q (Table 2).  Its training runs form one list of N versions
+// Blocks of a transfer problem q (Table 2), one thread per entry (kept for the IBK distance
+// block, where the tiled form below measured slower).  Its training runs form one list of N versions
 // (rs_group_layout); the rows are the list itself (CROSS false: the lower triangle u <= i of
 // the group's Gram KA[q][i][u], ld x ld -- all that the fits read) or the versions of the
 // test program q (CROSS true: Kx[q][t][u], 64 x ld).  Entry =
@@ -157,6 +158,106 @@ transfer_block_kernel(const int64_t* __restrict__ group_off, int max_runs, int64
     out[((int64_t)q * rows_ld + i) * ld + u] = acc;
 }
 
+// Blocks of a transfer problem q (Table 2).  Its training runs form one list of N versions
+// (rs_group_layout); the rows are the list itself (CROSS false: the lower triangle u <= i of
+// the group's Gram KA[q][i][u], ld x ld -- all that the fits read) or the versions of the
+// test program q (CROSS true: Kx[q][t][u], 64 x ld).  Entry = sum_f z_i[f] z_u[f] (FMA
+// chain), or with DIST sum_f (z_t[f] - z_u[f])^2 with unfused operations (the plain
+// definition's arithmetic), ascending f.  Problems that fail the layout checks (reported by
+// the standardization) are skipped.  A block computes a 32 x 32 tile of entries (rows i0..,
+// columns u0..; for the group's Gram only tiles with u0 <= i0, and entries u <= i), 16 x 16
+// threads of 2 x 2 entries each.  The tile's rows come through shared memory in slices of 32
+// features, one row per warp-row of lanes (coalesced); each entry sums its features in
+// ascending order, one slice after another.
+constexpr int kTT = 32;                      // tile edge
+constexpr int kTS = 32;                      // features per slice
+template <bool CROSS, bool DIST>
+__global__ void __launch_bounds__(256)
+transfer_tile_kernel(const int64_t* __restrict__ group_off, int max_runs, int64_t n_runs, int stat_stride,
+                     const int64_t* __restrict__ a_row, const int32_t* __restrict__ a_fw,
+                     const int64_t* __restrict__ a_xo, const double* __restrict__ ZA,
+                     const int64_t* __restrict__ b_row, const int32_t* __restrict__ b_fw,
+                     const int64_t* __restrict__ b_xo, const double* __restrict__ ZB, int ld,
+                     double* __restrict__ out) {
+    __shared__ double Si[kTT][kTS + 1], Su[kTT][kTS + 1];
+    __shared__ int64_t xi[kTT], xu[kTT];
+    const int q = blockIdx.x;
+    int start[RS_MAXRUNS + 1], F = 0;
+    const int N = rs_group_layout(q, group_off, max_runs, n_runs, a_row, a_fw, b_fw, stat_stride, start, F);
+    if (N < 0 || N > ld) return;
+    const int VB = (int)(b_row[q + 1] - b_row[q]);
+    if (CROSS && (VB < 1 || VB > RS_MAXV)) return;
+    const int rows = CROSS ? VB : N;
+    const int tu_n = (N + kTT - 1) / kTT;
+    int ti, tu;
+    if constexpr (CROSS) {
+        ti = (int)blockIdx.y / tu_n;
+        tu = (int)blockIdx.y - ti * tu_n;
+    } else {                                   // tile t = ti (ti + 1) / 2 + tu, tu <= ti
+        ti = 0;
+        while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.y) ++ti;
+        tu = (int)blockIdx.y - ti * (ti + 1) / 2;
+    }
+    const int i0 = ti * kTT, u0 = tu * kTT;
+    if (i0 >= rows || u0 >= N) return;
+    const int64_t g0 = group_off[q];
+    const int tid = threadIdx.x;
+    if (tid < 2 * kTT) {                       // element offsets of the tile's rows
+        const int k = tid & (kTT - 1);
+        const int v = (tid < kTT ? i0 : u0) + k;
+        int64_t x = -1;
+        if (tid < kTT && CROSS) {
+            if (v < rows) x = b_xo[q] + (int64_t)v * F;
+        } else if (v < N) {
+            int r = 0;
+            while (v >= start[r + 1]) ++r;
+            x = a_xo[g0 + r] + (int64_t)(v - start[r]) * F;
+        }
+        (tid < kTT ? xi : xu)[k] = x;
+    }
+    __syncthreads();
+    const double* Zi = CROSS ? ZB : ZA;
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int f0 = 0; f0 < F; f0 += kTS) {
+        const int w = F - f0 < kTS ? F - f0 : kTS;
+        for (int e = tid; e < 2 * kTT * kTS; e += 256) {   // lane c of warp-row r: feature f0 + c
+            const int r = e / kTS, c = e - r * kTS;
+            const bool isu = r >= kTT;
+            const int rr = isu ? r - kTT : r;
+            const int64_t x = isu ? xu[rr] : xi[rr];
+            const double v = (x >= 0 && c < w) ? __ldg((isu ? ZA : Zi) + x + f0 + c) : 0.0;
+            (isu ? Su : Si)[rr][c] = v;
+        }
+        __syncthreads();
+        for (int c = 0; c < w; ++c) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const double zi = Si[ty + 16 * a][c];
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const double zu = Su[tx + 16 * b][c];
+                    if constexpr (DIST) {
+                        const double d = __dsub_rn(zi, zu);
+                        acc[a][b] = __dadd_rn(acc[a][b], __dmul_rn(d, d));
+                    } else {
+                        acc[a][b] = fma(zi, zu, acc[a][b]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t rows_ld = CROSS ? RS_MAXV : ld;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int i = i0 + ty + 16 * a, u = u0 + tx + 16 * b;
+            if (i < rows && u < N && (CROSS || u <= i)) out[((int64_t)q * rows_ld + i) * ld + u] = acc[a][b];
+        }
+}
+
 }  // namespace
 
 cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch* test_std, const int64_t* group_off,
@@ -166,21 +267,23 @@ cudaError_t rs_launch_transfer_blocks(const rs_batch* train_std, const rs_batch*
     const int n = RS_MAXV * max_runs;
     const double* ZA = (const double*)train_std->X;
     const double* ZB = (const double*)test_std->X;
+    const int nt = (n + kTT - 1) / kTT;        // tiles along the group's versions
     if (KA) {
-        dim3 grid(Q, (unsigned)(((int64_t)n * (n + 1) / 2 + 127) / 128));
-        transfer_block_kernel<false, false><<<grid, 128, 0, st>>>(
+        dim3 grid(Q, (unsigned)(nt * (nt + 1) / 2));
+        transfer_tile_kernel<false, false><<<grid, 256, 0, st>>>(
             group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
             ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, KA);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    dim3 grid(Q, (unsigned)(((int64_t)RS_MAXV * n + 127) / 128));
-    if (dist)
-        transfer_block_kernel<true, true><<<grid, 128, 0, st>>>(
+    dim3 grid(Q, (unsigned)((RS_MAXV / kTT) * nt));
+    if (dist) {
+        dim3 g1(Q, (unsigned)(((int64_t)RS_MAXV * n + 127) / 128));
+        transfer_block_kernel<true, true><<<g1, 128, 0, st>>>(
             group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
             ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, Kx);
-    else
-        transfer_block_kernel<true, false><<<grid, 128, 0, st>>>(
+    } else
+        transfer_tile_kernel<true, false><<<grid, 256, 0, st>>>(
             group_off, max_runs, train_std->n_programs, stat_stride, train_std->row_offsets, train_std->feat_width, train_std->x_offsets,
             ZA, test_std->row_offsets, test_std->feat_width, test_std->x_offsets, ZB, ld, Kx);
     return cudaGetLastError();
