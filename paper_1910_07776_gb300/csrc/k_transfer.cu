@@ -258,10 +258,16 @@ struct M5Tree {
 };
 
 struct M5Smem {
-    uint8_t sorted[kM5MaxFeat][kM5MaxN];          // per attribute: instances in (value, index) order
-    uint8_t scratch[kM5Threads][kM5MaxN];
-    double G[kM5MaxTerms * kM5Ld];                // centred normal equations of the node's candidates
-    double H[kM5MaxTerms * kM5Ld];                // inverse of the current subset's system
+    union {                                       // the growing pass, then the models' pass
+        struct {
+            uint8_t sorted[kM5MaxFeat][kM5MaxN];  // per attribute: instances in (value, index) order
+            uint8_t scratch[kM5Threads][kM5MaxN];
+        } gr;
+        struct {
+            double G[kM5MaxTerms * kM5Ld];        // centred normal equations of the node's candidates
+            double H[kM5MaxTerms * kM5Ld];        // inverse of the current subset's system
+        } mo;
+    };
     double colk[kM5MaxTerms], rowk[kM5MaxTerms];
     double zbar[kM5MaxTerms], r[kM5MaxTerms], w[kM5MaxTerms], cand_err[kM5MaxTerms];
     double res[kM5MaxN];
@@ -371,7 +377,7 @@ m5p_fit_kernel(const TransferArgs a) {
     __syncthreads();
     // presort: attribute f's instances by (value, index)
     for (int f = tid; f < F; f += kM5Threads) {
-        uint8_t* o = S.sorted[f];
+        uint8_t* o = S.gr.sorted[f];
         for (int i = 0; i < n; ++i) {
             const double v = __ldg(S.zp[i] + f);
             int p = i;
@@ -439,7 +445,7 @@ m5p_fit_kernel(const TransferArgs a) {
         double best = 0.0, bthr = 0.0;
         int battr = -1;
         for (int f = tid; f < F; f += kM5Threads) {
-            const uint8_t* o = S.sorted[f];
+            const uint8_t* o = S.gr.sorted[f];
             double l1 = 0.0, l2 = 0.0;
             for (int c = 1; c < m; ++c) {
                 const int ia = o[lo + c - 1], ib = o[lo + c];
@@ -506,8 +512,8 @@ m5p_fit_kernel(const TransferArgs a) {
         // stable partition of the node's instance list and of every attribute's sorted list
         int nl = 0;
         for (int f = tid; f < F + 1; f += kM5Threads) {
-            uint8_t* o = f < F ? S.sorted[f] : S.ids;
-            uint8_t* sc = S.scratch[tid];
+            uint8_t* o = f < F ? S.gr.sorted[f] : S.ids;
+            uint8_t* sc = S.gr.scratch[tid];
             int k = 0;
             for (int a2 = lo; a2 < hi; ++a2)
                 if (S.side[o[a2]] == 0) sc[k++] = o[a2];
@@ -582,8 +588,8 @@ m5p_fit_kernel(const TransferArgs a) {
                     const double* z = S.zp[S.ids[lo + a2]];
                     s += (__ldg(z + S.cand[f]) - S.zbar[f]) * (__ldg(z + S.cand[g]) - S.zbar[g]);
                 }
-                S.G[f * kM5Ld + g] = s + (f == g ? kM5Ridge : 0.0);
-                S.G[g * kM5Ld + f] = s + (f == g ? kM5Ridge : 0.0);
+                S.mo.G[f * kM5Ld + g] = s + (f == g ? kM5Ridge : 0.0);
+                S.mo.G[g * kM5Ld + f] = s + (f == g ? kM5Ridge : 0.0);
             } else {
                 for (int a2 = 0; a2 < m; ++a2) {
                     const int i = S.ids[lo + a2];
@@ -598,13 +604,13 @@ m5p_fit_kernel(const TransferArgs a) {
             const int ns = S.nsel;
             for (int e = tid; e < ns * ns; e += kM5Threads) {
                 const int i = e / ns, k = e - i * ns;
-                S.H[i * kM5Ld + k] = S.G[S.sel[i] * kM5Ld + S.sel[k]];
+                S.mo.H[i * kM5Ld + k] = S.mo.G[S.sel[i] * kM5Ld + S.sel[k]];
             }
             __syncthreads();
-            m5_invert(S, S.H, ns);
+            m5_invert(S, S.mo.H, ns);
             for (int i = tid; i < ns; i += kM5Threads) {
                 double s = 0.0;
-                for (int k = 0; k < ns; ++k) s = fma(S.H[i * kM5Ld + k], S.r[S.sel[k]], s);
+                for (int k = 0; k < ns; ++k) s = fma(S.mo.H[i * kM5Ld + k], S.r[S.sel[k]], s);
                 S.w[i] = s;
             }
             __syncthreads();
@@ -620,11 +626,11 @@ m5p_fit_kernel(const TransferArgs a) {
             }
             // drop-one candidates: w' = w - H[:, d] w_d / H_dd, one warp each
             for (int d = warp; d < ns; d += nwarps) {
-                const double fac = S.w[d] / S.H[d * kM5Ld + d];
+                const double fac = S.w[d] / S.mo.H[d * kM5Ld + d];
                 double wd[kM5MaxTerms];
                 double b = ybar;
                 for (int i = 0; i < ns; ++i) {
-                    wd[i] = i == d ? 0.0 : fma(-S.H[i * kM5Ld + d], fac, S.w[i]);
+                    wd[i] = i == d ? 0.0 : fma(-S.mo.H[i * kM5Ld + d], fac, S.w[i]);
                     if (i != d) b -= wd[i] * S.zbar[S.sel[i]];
                 }
                 const double ed = m5_warp_err(S, lo, m, wd, b, ns, S.sel, d);
