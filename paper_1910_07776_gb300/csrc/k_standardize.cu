@@ -300,24 +300,16 @@ cudaError_t rs_launch_transfer_standardize(const rs_batch* train, const rs_batch
     return cudaGetLastError();
 }
 
-#ifndef RS_STD_MAXB
-#define RS_STD_MAXB 0
-#endif
 cudaError_t rs_launch_standardize(const rs_batch* b, double* Z, double* mu, double* sigma,
                                   int* dstatus, cudaStream_t st) {
     dim3 grid((unsigned)b->n_programs, (unsigned)((b->max_feat + kFeat - 1) / kFeat));
-    const size_t pad = rs_residency_pad(RS_STD_MAXB, sizeof(double) * (RS_MAXV * kFeat + kGroups * kFeat + 2 * kFeat +
-                                                                      RS_MAXV + 512));
-    if (b->dtype == RS_F32) {
-        if (pad) cudaFuncSetAttribute(standardize_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
-        standardize_kernel<float><<<grid, kThreads, pad, st>>>(
+    if (b->dtype == RS_F32)
+        standardize_kernel<float><<<grid, kThreads, 0, st>>>(
             b->n_programs, b->row_offsets, b->feat_width, b->x_offsets, b->feat_offsets,
             (const float*)b->X, b->cycles, Z, mu, sigma, dstatus);
-    } else {
-        if (pad) cudaFuncSetAttribute(standardize_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
-        standardize_kernel<double><<<grid, kThreads, pad, st>>>(
+    else
+        standardize_kernel<double><<<grid, kThreads, 0, st>>>(
             b->n_programs, b->row_offsets, b->feat_width, b->x_offsets, b->feat_offsets,
             (const double*)b->X, b->cycles, Z, mu, sigma, dstatus);
-    }
     return cudaGetLastError();
 }
