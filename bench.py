@@ -801,7 +801,9 @@ def run_lovo(rs, ctx, dev, stream, flush, args, programs=256):
     98,304 ridge fits of 31 pairs each, every stage in FP64 through the one-call step.  The
     fits of more than 16 pairs run in solve_wide_kernel; its stage time (from the end of the
     planning to the join of the solver streams) against its FP64 flops gives its roofline
-    fraction, and the Gram (1.07 GFLOP) is timed alone beside it."""
+    fraction, and the Gram (1.07 GFLOP) is timed alone beside it.  The same step with
+    RS_LOO_CLOSED (one inverse per program and optimization, every fit from it in O(n)) is
+    timed beside it, with its largest prediction difference from the direct solves."""
     import torch
     from paper_1910_07776_gb300 import synth
     b = synth.make_batch_fast(programs, versions=64, feat=1024, dtype=np.float64, seed=43)
@@ -810,27 +812,34 @@ def run_lovo(rs, ctx, dev, stream, flush, args, programs=256):
     ds = rs.DeviceSplits.from_host(sp, dev, b)
     R = ds.n_test_rows
     ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
-    o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
-                               tau=CFG["tau"], rec_pred=o.rec_pred, counters=o.counters)
-    for _ in range(3):
-        step()
-    torch.cuda.synchronize()
-    o.counters.zero_()
-    ctx.profile_enable(True)
-    reps, tot, stages = 10, 0.0, {}
-    for _ in range(reps):
-        flush.fill_(1)
-        e0.record(stream)
-        step()
-        e1.record(stream)
+
+    def timed(flags):
+        o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev)
+        step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
+                                   tau=CFG["tau"], flags=flags, rec_pred=o.rec_pred, pred_all=o.pred_all,
+                                   counters=o.counters)
+        for _ in range(3):
+            step()
         torch.cuda.synchronize()
-        tot += e0.elapsed_time(e1)
-        for k_, v_ in ctx.profile_read().items():
-            stages[k_] = stages.get(k_, 0.0) + v_ / reps
-    ctx.profile_enable(False)
-    ctx.check_device_status()
+        o.counters.zero_()
+        ctx.profile_enable(True)
+        reps, tot, stages = 10, 0.0, {}
+        for _ in range(reps):
+            flush.fill_(1)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+            for k_, v_ in ctx.profile_read().items():
+                stages[k_] = stages.get(k_, 0.0) + v_ / reps
+        ctx.profile_enable(False)
+        ctx.check_device_status()
+        return tot / reps, stages, o
+
+    ms, stages, o = timed(0)
+    ms_c, stages_c, oc = timed(rs.RS_LOO_CLOSED)
     Z = torch.empty(db.x_elems, dtype=torch.float64, device=dev)
     K = torch.zeros(db.n_programs * 64 * 64, dtype=torch.float64, device=dev)
     ctx.standardize(db, Z)
@@ -847,7 +856,19 @@ def run_lovo(rs, ctx, dev, stream, flush, args, programs=256):
     solve_ms = stages.get("solve", 0.0) + stages.get("solve_join", 0.0)
     flops = work["solve_small"] + work["solve_large"]
     c = o.counters.cpu().numpy().view(np.uint64).astype(np.float64)
-    ms = tot / reps
+    cc = oc.counters.cpu().numpy().view(np.uint64).astype(np.float64)
+    pa, pc = o.pred_all.cpu().numpy(), oc.pred_all.cpu().numpy()
+    fin = ~np.isnan(pa)
+    same_nan = bool(np.array_equal(np.isnan(pa), np.isnan(pc)))
+    diff = np.abs(pa[fin] - pc[fin])
+    closed = {"ms_per_step": ms_c, "value": R / (ms_c * 1e-3), "unit": UNIT, "stages_ms": stages_c,
+              "fit_ms": stages_c.get("solve", 0.0) + stages_c.get("solve_join", 0.0),
+              "sign_accuracy": cc[3] / max(cc[2], 1), "top1_hit_rate": cc[8] / max(cc[7], 1),
+              "fits_ok": int(cc[9]),
+              "max_abs_pred_diff_vs_direct": float(diff.max()) if diff.size else 0.0,
+              "max_rel_pred_diff_vs_direct": float((diff / np.maximum(np.abs(pa[fin]), 1e-300)).max()) if diff.size else 0.0,
+              "nan_pattern_equal": same_nan,
+              "rec_code_rows_differing": int((o.rec_code != oc.rec_code).sum().item())}
     return {"workload": f"{programs} programs x 64 versions (all masks) x 1024 f64 features, "
                         f"leave-one-version-out ({64 * programs:,} splits, {384 * programs:,} fits of 31 pairs)",
             "ms_per_step": ms, "value": R / (ms * 1e-3), "unit": UNIT, "recs_per_step": R,
@@ -858,6 +879,7 @@ def run_lovo(rs, ctx, dev, stream, flush, args, programs=256):
                          "frac": flops / (solve_ms * 1e-3) / 1e12 / fp64_peak, "flops_per_launch": flops,
                          "ms": solve_ms,
                          "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FMA/clk x 2.07 GHz)"},
+            "closed_form": closed,
             "gram_alone": {"ms": g_ms, "flops": work["gram_flops"],
                            "frac_fp64": work["gram_flops"] / (g_ms * 1e-3) / 1e12 / fp64_peak}}
 

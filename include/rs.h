@@ -62,7 +62,9 @@ enum {
     RS_MODEL_IBK = 4,     /* the instance-based learner (IBK, k nearest neighbours)
                              instead of ridge regression; K is the distance block    */
     RS_MODEL_M5P = 8,     /* the M5P model tree instead of ridge regression (rs_transfer) */
-    RS_PACK_PRED = 16     /* rec_pred packed: the reported lists back to back (rs_predict_rank) */
+    RS_PACK_PRED = 16,    /* rec_pred packed: the reported lists back to back (rs_predict_rank) */
+    RS_LOO_CLOSED = 32    /* leave-one-version-out splits: every fit from one inverse of its
+                             program's full system (rs_predict_rank, rs_cv_step)      */
 };
 #define RS_IBK_NEIGHBORS 10  /* k of the instance-based learner (Sec. 3.4: k = 10)        */
 
@@ -185,7 +187,8 @@ rs_status rs_rec_offsets(rs_ctx* ctx, const rs_batch* batch, const rs_splits* sp
  * 10 pairs, lanes sharing the larger fits) or RS_FORM_PLAIN (one warp per fit, per chunk);
  * with the batched form, form | RS_REFINE_X takes one step of iterative refinement of every
  * fit through the standardized features of `std` (for a K from RS_GRAM_BF16X3), as the
- * flag does in rs_predict_rank.
+ * flag does in rs_predict_rank; form | RS_LOO_CLOSED (batched, not with RS_REFINE_X) takes
+ * the fits of leave-one-version-out splits in closed form, as in rs_predict_rank.
  * workspace: caller-owned device scratch of at least rs_fit_workspace_bytes(std, splits)
  * bytes, 256-byte aligned, required by the batched form (may be NULL for the plain form);
  * its contents are undefined after the call.  RS_ENOMEM if it is too small.  A fit with
@@ -221,7 +224,18 @@ rs_status rs_fit_batched(rs_ctx* ctx, const rs_batch* std, const double* K,
  * regression -- a fit is OK when it has a training pair; the prediction for test row t is
  * the mean label of the RS_IBK_NEIGHBORS training pairs whose before versions are nearest
  * to t (distance K[t][v_a]; equal distances take the lower pair first; all pairs when there
- * are fewer), summed in ascending pair order.  lambda is ignored.  tau > 0.           */
+ * are fewer), summed in ascending pair order.  lambda is ignored.  RS_LOO_CLOSED (batched
+ * form, coef == NULL, not with RS_REFINE_X or RS_MODEL_IBK): for splits that each hold out
+ * one version (the leave-one-version-out protocol of Sec. 5), optimization j's training
+ * pairs are the program's pairs for j minus at most the one that contains the held-out
+ * version, so every fit is the program's full system M = K_PP + lambda I without one row and
+ * column.  With M^-1, w_y = M^-1 y and w_1 = M^-1 1 formed once per (program, j), the
+ * reduced system's M_r^-1 y = (w_y - u w_y[i] / u_i) without entry i (u = column i of M^-1)
+ * and likewise for 1, so b and alpha cost O(n) per fit instead of a factorization.  The same
+ * fits to rounding (the inverse adds an error of order cond(M) times the unit roundoff) and the
+ * same statuses.  A fit whose split leaves out more than one of its program's pairs for j
+ * (a split that holds out two or more versions, in general) has no such form: RS_EDATA
+ * (detail: the program), and the fit is reported failed (RS_FIT_NOTPD).  tau > 0.     */
 rs_status rs_predict_rank(rs_ctx* ctx, const rs_batch* std, const double* K,
                           const rs_splits* splits, double lambda, const double* coef,
                           int k, double tau, int flags, int form, void* workspace,

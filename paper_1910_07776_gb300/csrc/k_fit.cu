@@ -1441,6 +1441,229 @@ solve_wide_kernel(const SolveArgs a, unsigned long long* work) {
     }
 }
 
+// ====================================================================== closed-form leave-one-out
+// RS_LOO_CLOSED.  A split that holds out one version removes, for optimization j, at most the
+// one pair of the program's pairs for j that contains that version (a version is the before
+// or the after side of at most one pair per j).  The fit's system is then the program's full
+// M = K_PP + lambda I for j without row and column i, and with w_y = M^-1 y, w_1 = M^-1 1 and
+// u = row i of the symmetric M^-1, deleting index i from a linear system gives, for q != i,
+//   (M_r^-1 y)_q = w_y[q] - u_q w_y[i] / u_i,     (M_r^-1 1)_q = w_1[q] - u_q w_1[i] / u_i.
+// b and alpha then follow as in every solver (Sec. 3.4): b = sum t_y / sum t_1 and
+// alpha = t_y - b t_1.  One inverse per (program, j) replaces a factorization per fit.
+// the table of one (program, optimization): M^-1 (32 x 32, row-major), w_y, w_1, then the
+// sums 1^T w_y and 1^T w_1 (padded to a 32-byte multiple)
+constexpr int kLooWy = RS_MAXPAIRS * RS_MAXPAIRS;
+constexpr int kLooW1 = kLooWy + RS_MAXPAIRS;
+constexpr int kLooSum = kLooW1 + RS_MAXPAIRS;
+constexpr int kLooTab = kLooSum + 4;                                   // doubles per (p, j)
+constexpr int kLooFitThreads = 256;
+
+// One warp per (program, optimization): Gauss-Jordan elimination of [M | y | 1] without
+// pivoting (M is symmetric positive definite), lane i holding row i in registers, padded
+// with the identity past n (inert: a padded row or column meets only zeros), so that every
+// index is static.  Step k: every row i != k subtracts A_ik / p_k times row k (p_k = A_kk,
+// the pivot; row k reaches the others through shared memory) and stores -A_ik / p_k in
+// column k, the right block's column that column k's elimination has made; row k stays and
+// stores 1 there.  The left block ends diagonal, diag(p), so M^-1 is each row of the right
+// block divided by its pivot.  Row k needs no scaling inside the loop, so every lane runs the
+// same instructions.  Writes the symmetrized inverse, w_y, w_1 and their sums to tab, and
+// ok = 1 when every pivot was positive and finite.  A non-finite label enters y as 0 and sets
+// its pair's bit in bad: a fit that trains on that pair is non-finite, and one that leaves it
+// out does not depend on its label (the deletion formula above holds for any value in
+// position i).
+__global__ void __launch_bounds__(32)
+loo_inv_kernel(const int64_t* __restrict__ row_off, const double* __restrict__ K,
+               const uint8_t* __restrict__ pb, const double* __restrict__ ylab,
+               const int* __restrict__ npair, const double* __restrict__ dlam, double* tab, uint8_t* ok,
+               uint32_t* bad) {
+    __shared__ __align__(16) double rowk[RS_MAXPAIRS + 2];     // the pivot row and its right-hand sides
+    __shared__ double S[RS_MAXPAIRS][RS_MAXPAIRS + 1];          // the inverse, for the symmetrized store
+    __shared__ int vs[RS_MAXPAIRS];
+    const int pj = blockIdx.x, p = pj / RS_NOPT, i = threadIdx.x;
+    const int V = (int)(row_off[p + 1] - row_off[p]);
+    const int n = V >= 1 && V <= RS_MAXV ? npair[pj] : 0;
+    if (n < 1 || n > RS_MAXPAIRS) {
+        if (i == 0) {
+            ok[pj] = 0;
+            bad[pj] = 0;
+        }
+        return;
+    }
+    const double* Kp = K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+    const bool row = i < n;
+    if (row) vs[i] = pb[(int64_t)pj * RS_MAXPAIRS + i];
+    __syncwarp();
+    double A[RS_MAXPAIRS], y = 0.0, one = 0.0;
+    const int vi = row ? vs[i] : 0;
+#pragma unroll
+    for (int c = 0; c < RS_MAXPAIRS; ++c) {
+        double v = c == i ? 1.0 : 0.0;
+        if (row && c < n) v = c == i ? dlam[(int64_t)p * RS_MAXV + vi] : __ldg(Kp + vi * RS_GRAM_LD + vs[c]);
+        A[c] = v;
+    }
+    if (row) {
+        y = ylab[(int64_t)pj * RS_MAXPAIRS + i];
+        one = 1.0;
+    }
+    const bool yb = row && !finite_bits(y);
+    const unsigned badm = __ballot_sync(0xffffffffu, yb);
+    if (yb) y = 0.0;
+    double piv = 1.0;                                           // this row's pivot
+    bool good = true;
+#pragma unroll
+    for (int k = 0; k < RS_MAXPAIRS; ++k) {
+        if (i == k) {
+#pragma unroll
+            for (int c = 0; c < RS_MAXPAIRS; c += 2)
+                *reinterpret_cast<double2*>(rowk + c) = make_double2(A[c], A[c + 1]);
+            rowk[RS_MAXPAIRS] = y;
+            rowk[RS_MAXPAIRS + 1] = one;
+        }
+        __syncwarp();
+        const double d = rowk[k];                               // the same value in every lane
+        good = good && pos_finite(d);
+        const double r = rcp_newton(good ? d : 1.0);
+        const double fr = i == k ? 0.0 : A[k] * r;
+        if (i == k) piv = d;
+#pragma unroll
+        for (int c = 0; c < RS_MAXPAIRS; c += 2) {
+            const double2 rk = *reinterpret_cast<const double2*>(rowk + c);
+            if (c != k) A[c] = fma(-fr, rk.x, A[c]);
+            if (c + 1 != k) A[c + 1] = fma(-fr, rk.y, A[c + 1]);
+        }
+        y = fma(-fr, rowk[RS_MAXPAIRS], y);
+        one = fma(-fr, rowk[RS_MAXPAIRS + 1], one);
+        A[k] = i == k ? 1.0 : -fr;
+        __syncwarp();                                           // before the next pivot row
+    }
+    if (good) {
+        const double rp = rcp_newton(piv);
+#pragma unroll
+        for (int c = 0; c < RS_MAXPAIRS; ++c) S[i][c] = A[c] * rp;
+        y *= rp;
+        one *= rp;
+        __syncwarp();
+        double* T = tab + (int64_t)pj * kLooTab;
+        for (int rr = 0; rr < n; ++rr)
+            if (row) T[rr * RS_MAXPAIRS + i] = 0.5 * (S[rr][i] + S[i][rr]);
+        if (row) {
+            T[kLooWy + i] = y;
+            T[kLooW1 + i] = one;
+        }
+        const double sy = warp_sum(y), s1 = warp_sum(one);    // lanes past n hold 0
+        if (i == 0) {
+            T[kLooSum] = sy;
+            T[kLooSum + 1] = s1;
+        }
+    }
+    if (i == 0) {
+        ok[pj] = good ? 1 : 0;
+        bad[pj] = badm;
+    }
+}
+
+// One thread per fit.  With u_i = (M^-1)_ii and 1^T u = w_1[i] (M^-1 is symmetric), deleting
+// pair i turns the sums that give b into one-term downdates,
+//   1^T t_y = 1^T w_y - w_1[i] w_y[i] / u_i,     1^T t_1 = 1^T w_1 - w_1[i]^2 / u_i,
+// so b = 1^T t_y / 1^T t_1 costs O(1), and alpha_q = (w_y[q] - b w_1[q]) - u_q e for q != i,
+// e = (w_y[i] - b w_1[i]) / u_i.  The prediction at pair i's own before version v_i -- the
+// held-out version whenever it lacks j -- needs no sum either: with K_PP = M - lambda I,
+//   b + sum_{q != i} alpha_q K[v_i][v_q] = y_i - e
+// (the leave-one-out residual of kernel ridge, with the intercept refitted; y_i the value that
+// entered the inverse).  Other candidate rows (a version without a partner for j, or the
+// after versions that RS_RANK_ALL ranks) take the sum over the fit's pairs in pair order, as
+// the direct solvers do.  A fit whose training pairs lack more than one of its program's pairs
+// for j has no closed form here: RS_EDATA (detail: the program), and the fit is reported
+// failed.  Non-finite b or e: RS_FIT_NONFINITE.  Fits without a pair were finished by the
+// bucket pass.
+__global__ void __launch_bounds__(kLooFitThreads)
+loo_fit_kernel(const SolveArgs a, int64_t S6, const int* __restrict__ npair,
+               const double* __restrict__ tab, const uint8_t* __restrict__ tab_ok,
+               const uint32_t* __restrict__ tab_bad) {
+    const int64_t f = (int64_t)blockIdx.x * kLooFitThreads + threadIdx.x;
+    const int n = f < S6 ? a.fit_key[f] / kCntBins : 0;
+    const bool active = n > 0;
+    int st = RS_FIT_EMPTY;
+    if (active) {
+        const int64_t s = f / RS_NOPT;
+        const int j = (int)(f - s * RS_NOPT);
+        const int p = a.split_prog[s];
+        const int pj = p * RS_NOPT + j;
+        const int N = npair[pj];
+        const uint32_t pm = a.fit_pm[f];
+        const uint32_t full = N >= 32 ? 0xffffffffu : (1u << N) - 1u;
+        const uint32_t removed = full & ~pm;
+        const double* T = tab + (int64_t)pj * kLooTab;
+        st = RS_FIT_OK;
+        if (__popc(removed) > 1 || (pm & ~full)) {
+            st = RS_FIT_NOTPD;
+            rs_dev_flag(a.dstatus, RS_EDATA, p);
+        } else if (!tab_ok[pj]) {
+            st = RS_FIT_NOTPD;
+        } else if (pm & tab_bad[pj]) {
+            st = RS_FIT_NONFINITE;           // a label of the fit's pairs is not finite
+        }
+        const int i = removed ? __ffs(removed) - 1 : -1;
+        double b = 0.0, e = 0.0;
+        if (st == RS_FIT_OK) {
+            double num = T[kLooSum], den = T[kLooSum + 1], cy = 0.0, c1 = 0.0;
+            if (i >= 0) {
+                const double ui = T[i * RS_MAXPAIRS + i];
+                if (!pos_finite(ui)) {
+                    st = RS_FIT_NOTPD;
+                } else {
+                    const double ri = rcp_newton(ui), wyi = T[kLooWy + i], w1i = T[kLooW1 + i];
+                    cy = wyi * ri;
+                    c1 = w1i * ri;
+                    num = fma(-w1i, cy, num);
+                    den = fma(-w1i, c1, den);
+                }
+            }
+            if (st == RS_FIT_OK) {
+                b = num * rcp_newton(den);
+                e = fma(-b, c1, cy);
+                if (!finite_bits(b) || !finite_bits(e)) st = RS_FIT_NONFINITE;
+            }
+        }
+        const uint8_t* pbj = a.pb + (int64_t)pj * RS_MAXPAIRS;
+        auto alpha = [&](int q) {
+            const double al = fma(-b, T[kLooW1 + q], T[kLooWy + q]);
+            return i >= 0 ? fma(-T[i * RS_MAXPAIRS + q], e, al) : al;
+        };
+        double* out = coef_out(a, f);
+        if (out && st == RS_FIT_OK) {
+            out[0] = b;
+            int c = 1;
+            for (uint32_t m = pm; m; m &= m - 1) out[c++] = alpha(__ffs(m) - 1);
+        }
+        PredTarget pt;
+        const bool has = pred_target_v(a, s, j, p, (int)(a.row_off[p + 1] - a.row_off[p]), pt);
+        if (has && st == RS_FIT_OK) {
+            const int vi = i >= 0 ? pbj[i] : -1;
+            const double* Kp = a.K + (int64_t)p * RS_GRAM_LD * RS_GRAM_LD;
+            for (uint64_t cm = pt.cand; cm; cm &= cm - 1) {
+                const int t = __ffsll((long long)cm) - 1;
+                double yh;
+                if (t == vi) {
+                    const double yi = a.ylab[(int64_t)pj * RS_MAXPAIRS + i];
+                    yh = (finite_bits(yi) ? yi : 0.0) - e;
+                } else {
+                    yh = b;
+                    for (uint32_t m = pm; m; m &= m - 1) {
+                        const int q = __ffs(m) - 1;
+                        yh = fma(alpha(q), __ldg(Kp + t * RS_GRAM_LD + pbj[q]), yh);
+                    }
+                }
+                const int r = __popcll(pt.test & ((1ull << t) - 1ull));
+                if (r < pt.room) pt.dst[r] = yh;
+            }
+        }
+        if (st != RS_FIT_OK && has) mark_failed(a, s, j, pt);
+        finish_record(a, f, n, st, out);
+    }
+    count_status(a, st, active);
+}
+
 // ====================================================================== rank pass
 // One thread per test row: its row record and its six predictions (written by the solve
 // kernels) go through rank_row; no FP64 arithmetic.
@@ -2002,6 +2225,9 @@ struct FitWs {
     double* predbuf;     // [6][Rcap]
     unsigned long long* tile_sum;   // [ceil(Rcap / 256)] recommendations per rank tile (packed output)
     unsigned long long* tile_off;   // [ceil(Rcap / 256)] their exclusive scan
+    double* loo_tab;     // [P][6][kLooTab] M^-1, w_y, w_1 per (program, optimization) (RS_LOO_CLOSED)
+    uint8_t* loo_ok;     // [P][6] 1 when that inverse exists
+    uint32_t* loo_bad;   // [P][6] pairs whose label is not finite
     size_t bytes;
 };
 
@@ -2042,6 +2268,9 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     const size_t ntiles = (size_t)((Rcap + kRankTile - 1) / kRankTile);
     w.tile_sum = (unsigned long long*)take(ntiles * sizeof(unsigned long long));
     w.tile_off = (unsigned long long*)take(ntiles * sizeof(unsigned long long));
+    w.loo_tab = (double*)take(P * RS_NOPT * kLooTab * sizeof(double));
+    w.loo_ok = (uint8_t*)take(P * RS_NOPT);
+    w.loo_bad = (uint32_t*)take(P * RS_NOPT * sizeof(uint32_t));
     w.bytes = o;
     return w;
 }
@@ -2153,6 +2382,17 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         ibk_kernel<<<(unsigned)grid, 128, 0, st>>>(sa, nmax, w.work + 3);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        mark(4);
+    } else if (a.flags & RS_LOO_CLOSED) {
+        // one inverse per (program, optimization), then every fit in closed form
+        loo_inv_kernel<<<(unsigned)(a.P * RS_NOPT), 32, 0, st>>>(a.row_offsets, a.K, w.pb, w.ylab, w.npair,
+                                                                 w.dlam, w.loo_tab, w.loo_ok, w.loo_bad);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t grid = (S6 + kLooFitThreads - 1) / kLooFitThreads;
+        loo_fit_kernel<<<(unsigned)grid, kLooFitThreads, 0, st>>>(sa, S6, w.npair, w.loo_tab, w.loo_ok, w.loo_bad);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         mark(4);

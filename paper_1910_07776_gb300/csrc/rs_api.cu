@@ -308,18 +308,20 @@ rs_status rs_fit_batched(rs_ctx* c, const rs_batch* b, const double* K, const rs
                          double lambda, int form, void* workspace, size_t workspace_bytes,
                          double* coef, uint8_t* fit_status) {
     if (!c) return RS_EINVAL;
-    const int refine = form & RS_REFINE_X;
-    form &= ~RS_REFINE_X;
+    const int refine = form & RS_REFINE_X, loo = form & RS_LOO_CLOSED;
+    form &= ~(RS_REFINE_X | RS_LOO_CLOSED);
     rs_fit_args a;
     rs_status s = fit_common(c, b, K, sp, lambda, form, a);
     if (s != RS_OK) return s;
     if (refine && form != RS_FORM_BATCHED) return fail(c, RS_EINVAL, "RS_REFINE_X needs the batched form");
+    if (loo && (form != RS_FORM_BATCHED || refine))
+        return fail(c, RS_EINVAL, "RS_LOO_CLOSED needs the batched form without RS_REFINE_X");
     if (refine && b->max_feat > 4096) return fail(c, RS_EINVAL, "RS_REFINE_X: max_feat <= 4096");
     if (form == RS_FORM_BATCHED) {
         s = check_ws(c, b, sp, workspace, workspace_bytes, a);
         if (s != RS_OK) return s;
     }
-    a.flags |= refine;
+    a.flags |= refine | loo;
     a.coef_out = coef;
     a.status_out = fit_status;
     a.k = 1;
@@ -343,7 +345,10 @@ static rs_status predict_args(rs_ctx* c, const rs_batch* b, const double* K, con
     }
     if (k < 1 || k > RS_NOPT) return fail(c, RS_EINVAL, "k must be in 1..6");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(c, RS_EINVAL, "tau must be finite and > 0");
-    if (flags & ~(RS_RANK_ALL | RS_REFINE_X | RS_MODEL_IBK | RS_PACK_PRED)) return fail(c, RS_EINVAL, "unknown flag bits");
+    if (flags & ~(RS_RANK_ALL | RS_REFINE_X | RS_MODEL_IBK | RS_PACK_PRED | RS_LOO_CLOSED))
+        return fail(c, RS_EINVAL, "unknown flag bits");
+    if ((flags & RS_LOO_CLOSED) && (form != RS_FORM_BATCHED || coef || (flags & (RS_REFINE_X | RS_MODEL_IBK))))
+        return fail(c, RS_EINVAL, "RS_LOO_CLOSED needs the batched form, coef = NULL, no RS_REFINE_X or RS_MODEL_IBK");
     if ((flags & RS_PACK_PRED) && (form != RS_FORM_BATCHED || coef))
         return fail(c, RS_EINVAL, "RS_PACK_PRED needs the batched form with the fits computed in the call (coef = NULL)");
     if ((flags & RS_MODEL_IBK) && (form != RS_FORM_BATCHED || coef || (flags & RS_REFINE_X)))

@@ -21,7 +21,7 @@ RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EUNSUPPORTED, RS_EDATA = 
 RS_F32, RS_F64 = 0, 1
 RS_GRAM_F64, RS_GRAM_BF16X3, RS_GRAM_DIST2 = 0, 1, 2
 RS_FORM_BATCHED, RS_FORM_PLAIN = 0, 1
-RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK, RS_MODEL_M5P, RS_PACK_PRED = 1, 2, 4, 8, 16
+RS_RANK_ALL, RS_REFINE_X, RS_MODEL_IBK, RS_MODEL_M5P, RS_PACK_PRED, RS_LOO_CLOSED = 1, 2, 4, 8, 16, 32
 IBK_NEIGHBORS = 10
 NOPT = 6
 COEF_STRIDE = 33
@@ -400,8 +400,9 @@ class Context:
     def fit_batched(self, zb: DeviceBatch, K, s: DeviceSplits, lam: float = 1e-3,
                     form: int = RS_FORM_BATCHED, coef=None, fit_status=None, workspace=None):
         """form: RS_FORM_BATCHED or RS_FORM_PLAIN; RS_FORM_BATCHED | RS_REFINE_X refines each fit
-        once through the standardized features of zb."""
-        if workspace is None and (form & ~RS_REFINE_X) == RS_FORM_BATCHED:
+        once through the standardized features of zb; RS_FORM_BATCHED | RS_LOO_CLOSED takes the
+        fits of leave-one-version-out splits in closed form."""
+        if workspace is None and (form & ~(RS_REFINE_X | RS_LOO_CLOSED)) == RS_FORM_BATCHED:
             workspace = self.workspace(self.fit_workspace_bytes(zb, s))
         bc, sc = zb.c(), s.c()
         wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
