@@ -750,18 +750,22 @@ def run_ibk(rs, ctx, batch, splits, dev, stream, flush, args):
     """The instance-based learner (Sec. 3.4, IBK k = 10) beside ridge, through the one-call
     step on the same inputs: the batched-CV workload (where most fits have at most 10 pairs,
     so the mean of all labels is the prediction) and a leave-one-version-out workload over all
-    64 masks (31 pairs per fit: the 10-nearest selection decides every prediction)."""
+    64 masks (31 pairs per fit: the 10-nearest selection decides every prediction), where ridge
+    is also timed with its fits in closed form (RS_LOO_CLOSED)."""
     import torch
     from paper_1910_07776_gb300 import synth
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def measure(b, sp, reps):
+    def measure(b, sp, reps, loo=False):
         db = rs.DeviceBatch.from_host(b, dev)
         ds = rs.DeviceSplits.from_host(sp, dev, b)
         R = ds.n_test_rows
         ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
         res = {}
-        for name, flags in (("ridge", 0), ("ibk", rs.RS_MODEL_IBK)):
+        forms = [("ridge", 0), ("ibk", rs.RS_MODEL_IBK)]
+        if loo:
+            forms.append(("ridge_closed_form", rs.RS_LOO_CLOSED))
+        for name, flags in forms:
             o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev, pred_all=False)
             step = lambda: ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"],
                                        tau=CFG["tau"], flags=flags, rec_pred=o.rec_pred, counters=o.counters)
@@ -791,7 +795,7 @@ def run_ibk(rs, ctx, batch, splits, dev, stream, flush, args):
     b = synth.make_batch_fast(256, versions=64, feat=256, dtype=np.float32, seed=41)
     sp = synth.make_splits(b, "lovo")
     out["lovo"] = {"workload": "256 programs x 64 versions (all masks) x 256 f32 features, leave-one-"
-                               "version-out (16,384 splits, 98,304 fits of 31 pairs)", **measure(b, sp, 20)}
+                               "version-out (16,384 splits, 98,304 fits of 31 pairs)", **measure(b, sp, 20, loo=True)}
     return out
 
 
