@@ -202,3 +202,29 @@ def test_rank_all_predicts_the_after_versions_too(rs, ctx):
     close(g["pred_all"], r.pred_all)
     _, nnear = compare_rankings(g["rec_code"], r.rec_code, r.pred_all, math.log(1.05))
     compare_counters(g["counters"], r.counters, slack=nnear)
+
+
+def test_graph_of_the_closed_form_step_equals_the_call(rs, ctx):
+    # rs_cv_graph_create captures the step with RS_LOO_CLOSED; two launches give the one-call
+    # step's outputs bit for bit (the counters accumulate over launches)
+    batch, splits = _case("tiny")
+    db = rs.DeviceBatch.from_host(batch)
+    ds = rs.DeviceSplits.from_host(splits, batch=batch)
+    R = ds.n_test_rows
+    ws = ctx.workspace(ctx.cv_workspace_bytes(db, ds))
+    a = rs.alloc_outputs(R, ds.n_splits, 3, "cuda")
+    ctx.cv_step(db, ds, ws, a.rec_offsets, a.rec_code, flags=rs.RS_LOO_CLOSED, rec_pred=a.rec_pred,
+                pred_all=a.pred_all, counters=a.counters)
+    b = rs.alloc_outputs(R, ds.n_splits, 3, "cuda")
+    g = ctx.cv_graph(db, ds, ws, b.rec_offsets, b.rec_code, flags=rs.RS_LOO_CLOSED, rec_pred=b.rec_pred,
+                     pred_all=b.pred_all, counters=b.counters)
+    b.counters.zero_()
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    g.close()
+    ctx.check_device_status()
+    assert torch.equal(a.rec_code, b.rec_code)
+    np.testing.assert_array_equal(a.pred_all.cpu().numpy(), b.pred_all.cpu().numpy())
+    np.testing.assert_array_equal(a.rec_pred.cpu().numpy(), b.rec_pred.cpu().numpy())
+    assert torch.equal(2 * a.counters, b.counters)
