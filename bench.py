@@ -588,7 +588,7 @@ def main():
     roof["stages"]["standardize_alone"] = {
         "ms": alone["standardize"], "bytes": work["std_bytes"],
         "frac_hbm": work["std_bytes"] / (alone["standardize"] * 1e-3) / 1e9 / hbm_peak,
-        "note": "bound by the FP64 logarithm (12 FP64 instructions per element), not by HBM"}
+        "note": "bound by the FP64 logarithm (9 FP64 instructions per element), not by HBM"}
     roof["stages"]["step"] = {"ms": ms_step, "bound_ms": sum(bounds.values()),
                               "frac": sum(bounds.values()) / ms_step,
                               "bound_ms_parts": bounds,

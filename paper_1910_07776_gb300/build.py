@@ -42,8 +42,7 @@ def write_log_table(path: str) -> None:
     """Constants of the table-driven logarithm of the standardization kernel, correctly
     rounded to FP64 from exact decimal arithmetic (the same values on every build machine):
     log F_i and 1 / F_i for the centres F_i = 1 + (2 i + 1) / 512 of the 256 intervals of
-    width 1/256 that split the mantissa range [1, 2); ln 2 as hi + lo with hi rounded to 42
-    significant bits (e * hi is exact for |e| < 2^11); and log(1e-30), the clamp value."""
+    width 1/256 that split the mantissa range [1, 2); ln 2; and log(1e-30), the clamp value."""
     from decimal import Decimal, getcontext
     getcontext().prec = 60
     lines = ["// generated by build.py (write_log_table): do not edit", "#pragma once", ""]
@@ -53,15 +52,10 @@ def write_log_table(path: str) -> None:
         logs.append(float(F.ln()).hex())
         invs.append(float(Decimal(1) / F).hex())
     ln2 = Decimal(2).ln()
-    # 42 significant bits: round ln 2 * 2^41 to an integer
-    hi_int = int((ln2 * (Decimal(2) ** 41)).to_integral_value())
-    hi = Decimal(hi_int) / (Decimal(2) ** 41)
-    lo = float(ln2 - hi)
     eps = Decimal(1e-30)                 # the FP64 value nearest 1e-30, exactly
     lines.append("__device__ const double kLogTabF[256] = {" + ", ".join(logs) + "};")
     lines.append("__device__ const double kLogTabInv[256] = {" + ", ".join(invs) + "};")
-    lines.append(f"constexpr double kLn2Hi = {float(hi).hex()};")
-    lines.append(f"constexpr double kLn2Lo = {lo.hex()};")
+    lines.append(f"constexpr double kLn2 = {float(ln2).hex()};")
     lines.append(f"constexpr double kLogClamp = {float(eps.ln()).hex()};   // log(1e-30)")
     txt = "\n".join(lines) + "\n"
     if not os.path.exists(path) or open(path).read() != txt:
