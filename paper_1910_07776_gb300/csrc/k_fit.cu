@@ -55,6 +55,44 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
     return __ffsll((long long)x) - 1;
 }
 
+// Gathering the bits of a 64-bit word at the positions of a fixed set into its low bits, in
+// ascending order (a compress), in six rounds of shifts: round i moves each bit that still has
+// to travel an odd multiple of 2^i places by 2^i.  compress_moves stores the set and its six
+// move masks (the positions moved in each round, derived from the running count of the set's
+// zeros below each bit -- the parallel-suffix construction of Hacker's Delight, Sec. 7-4);
+// compress applies them.  A pair's training bit is T[b] & T[a] for its before and after
+// slots; when both kinds of slot ascend with the pair index, compress(T, before set) &
+// compress(T, after set) gives every pair's bit at once.
+constexpr int kSetWords = 14;                // per (program, optimization): 2 x (set + 6 moves)
+
+__device__ __forceinline__ void compress_moves(uint64_t m, uint64_t* out) {
+    out[0] = m;
+    uint64_t mk = ~m << 1;                   // bit k: a zero of the set lies below k
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        uint64_t mp = mk ^ (mk << 1);        // parity of the zeros below each bit
+        mp ^= mp << 2;
+        mp ^= mp << 4;
+        mp ^= mp << 8;
+        mp ^= mp << 16;
+        mp ^= mp << 32;
+        const uint64_t mv = mp & m;          // set bits that move in this round
+        out[1 + i] = mv;
+        m = (m ^ mv) | (mv >> (1 << i));
+        mk &= ~mp;
+    }
+}
+
+__device__ __forceinline__ uint64_t compress(uint64_t x, const uint64_t* c) {
+    x &= c[0];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint64_t t = x & c[1 + i];
+        x = (x ^ t) | (t >> (1 << i));
+    }
+    return x;
+}
+
 // ====================================================================== pair tables
 // One block per program: the before/after pairs of each optimization in ascending order of
 // the before slot, and their labels.  Tables: [P][6][32] (u8, u8, double), counts [P][6].
@@ -64,7 +102,8 @@ __device__ __forceinline__ int select_bit(uint64_t x, int a) {
 __global__ void __launch_bounds__(64)
 pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restrict__ masks,
              const double* __restrict__ log_time, uint8_t* pb, uint8_t* pa, double* ylab,
-             int* npair, uint64_t* cand, uint32_t* rowinfo, int* dstatus) {
+             int* npair, uint64_t* cand, uint32_t* rowinfo, uint64_t* pset, uint8_t* psorted,
+             int* dstatus) {
     __shared__ int8_t slot_of[RS_MAXV];
     __shared__ uint8_t msk[RS_MAXV];
     __shared__ double lt[RS_MAXV];
@@ -76,7 +115,10 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
             npair[p * RS_NOPT + tid] = 0;
             cand[p * RS_NOPT + tid] = 0;
         }
-        if (tid == 0) rs_dev_flag(dstatus, RS_EDATA, p);
+        if (tid == 0) {
+            psorted[p] = 0;
+            rs_dev_flag(dstatus, RS_EDATA, p);
+        }
         return;
     }
     slot_of[tid] = -1;
@@ -86,14 +128,17 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
     }
     __syncthreads();
     if (tid < V) slot_of[msk[tid]] = (int8_t)tid;
-    __syncthreads();
+    // masks strictly ascending over the slots: then the after slots of a j's pairs ascend with
+    // their before slots, and plan_fits may gather a split's pair bits set by set
+    const int sorted = __syncthreads_and(tid == 0 || tid >= V || msk[tid] > msk[tid - 1]);
+    if (tid == 0) psorted[p] = (uint8_t)sorted;
     // warp w takes optimizations w, w + 2, w + 4; its lanes take 32 slots at a time, and a
     // ballot places each pair after those of the lower slots
     const int warp = tid >> 5, lane = tid & 31;
     for (int j = warp; j < RS_NOPT; j += 2) {
         const int64_t base = ((int64_t)p * RS_NOPT + j) * RS_MAXPAIRS;
         int np = 0;
-        uint64_t cm = 0;
+        uint64_t cm = 0, bset = 0, aset = 0;
         for (int v0 = 0; v0 < V; v0 += 32) {
             const int v = v0 + lane;
             const int m = v < V ? msk[v] : (1 << j);
@@ -112,10 +157,17 @@ pairs_kernel(int P, const int64_t* __restrict__ row_off, const uint8_t* __restri
                 }
             }
             np += __popc(pm);
+            bset |= (uint64_t)pm << v0;
+            const unsigned alo = __reduce_or_sync(0xffffffffu, w >= 0 && w < 32 ? 1u << w : 0u);
+            const unsigned ahi = __reduce_or_sync(0xffffffffu, w >= 32 ? 1u << (w - 32) : 0u);
+            aset |= (uint64_t)ahi << 32 | alo;
         }
         if (lane == 0) {
             npair[p * RS_NOPT + j] = np < RS_MAXPAIRS ? np : RS_MAXPAIRS;
             cand[p * RS_NOPT + j] = cm;
+            uint64_t* ps = pset + ((int64_t)p * RS_NOPT + j) * kSetWords;
+            compress_moves(bset, ps);
+            compress_moves(aset, ps + kSetWords / 2);
         }
     }
     rowinfo[(int64_t)p * RS_MAXV + tid] = row_summary(tid, V, msk, lt, slot_of);
@@ -145,7 +197,8 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                  const int64_t* __restrict__ rec_offsets, int64_t rows_cap,
                  unsigned long long* row_info, const uint8_t* __restrict__ masks,
                  const uint32_t* __restrict__ rowinfo, const uint64_t* __restrict__ cand, int cand_all,
-                 int count_preds, int* dstatus) {
+                 int count_preds, const uint64_t* __restrict__ pset, const uint8_t* __restrict__ psorted,
+                 int* dstatus) {
     __shared__ unsigned h[kHist];
     // the tables of the block's first kPlanProgs programs (its splits' programs are
     // consecutive): pair slots [program][before / after][optimization][32], pair counts,
@@ -155,6 +208,8 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
     __shared__ uint64_t scand[kPlanProgs][RS_NOPT];
     __shared__ uint32_t sri[kPlanProgs][RS_MAXV];
     __shared__ uint8_t smk[kPlanProgs][RS_MAXV];
+    __shared__ uint64_t sset[kPlanProgs][RS_NOPT][kSetWords];
+    __shared__ uint8_t ssorted[kPlanProgs];
     __shared__ int p_first;
     if (threadIdx.x < kHist) h[threadIdx.x] = 0;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,7 +234,10 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
                 snp[q][t] = npair[pq * RS_NOPT + t];
                 scand[q][t] = cand ? cand[pq * RS_NOPT + t] : 0ull;
             }
+            if (t == 0) ssorted[q] = psorted[pq];
         }
+        for (int i = threadIdx.x; i < np_tab * RS_NOPT * kSetWords; i += blockDim.x)
+            (&sset[0][0][0])[i] = pset[(int64_t)p0 * RS_NOPT * kSetWords + i];
     }
     __syncthreads();
     if (s < S) {
@@ -199,29 +257,37 @@ plan_fits_kernel(int P, const int64_t* __restrict__ row_off, const int64_t* __re
         const uint64_t* cp = st ? scand[q] : cand + p * RS_NOPT;
         const uint32_t* rip = st ? sri[q] : rowinfo + (int64_t)p * RS_MAXV;
         const uint8_t* mkp = st ? smk[q] : masks + row_off[p];
+        const uint64_t* psp = st ? sset[q][0] : pset + (int64_t)p * RS_NOPT * kSetWords;
+        const bool srt = okV && (st ? ssorted[q] : psorted[p]) != 0;
 #pragma unroll 2
         for (int j = 0; j < RS_NOPT; ++j) {
             const int npj = okV ? npp[j] : 0;
-            const ulonglong2 vb[2] = {reinterpret_cast<const ulonglong2*>(tb + j * RS_MAXPAIRS)[0],
-                                      reinterpret_cast<const ulonglong2*>(tb + j * RS_MAXPAIRS)[1]};
-            const ulonglong2 va[2] = {reinterpret_cast<const ulonglong2*>(ta + j * RS_MAXPAIRS)[0],
-                                      reinterpret_cast<const ulonglong2*>(ta + j * RS_MAXPAIRS)[1]};
             uint32_t pm = 0;
+            if (srt) {
+                // sorted masks: every pair's bit at once from the before and after slot sets
+                const uint64_t* c = psp + j * kSetWords;
+                pm = (uint32_t)(compress(T, c) & compress(T, c + kSetWords / 2));
+            } else {
+                const ulonglong2 vb[2] = {reinterpret_cast<const ulonglong2*>(tb + j * RS_MAXPAIRS)[0],
+                                          reinterpret_cast<const ulonglong2*>(tb + j * RS_MAXPAIRS)[1]};
+                const ulonglong2 va[2] = {reinterpret_cast<const ulonglong2*>(ta + j * RS_MAXPAIRS)[0],
+                                          reinterpret_cast<const ulonglong2*>(ta + j * RS_MAXPAIRS)[1]};
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                if (8 * w >= npj) break;
-                const unsigned long long wb = (w & 1) ? vb[w >> 1].y : vb[w >> 1].x;
-                const unsigned long long wa = (w & 1) ? va[w >> 1].y : va[w >> 1].x;
-                uint32_t part = 0;
+                for (int w = 0; w < 4; ++w) {
+                    if (8 * w >= npj) break;
+                    const unsigned long long wb = (w & 1) ? vb[w >> 1].y : vb[w >> 1].x;
+                    const unsigned long long wa = (w & 1) ? va[w >> 1].y : va[w >> 1].x;
+                    uint32_t part = 0;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const unsigned sb = (unsigned)(wb >> (8 * e)) & 63u;
-                    const unsigned sa = (unsigned)(wa >> (8 * e)) & 63u;
-                    part |= (uint32_t)((T >> sb) & (T >> sa) & 1ull) << e;
+                    for (int e = 0; e < 8; ++e) {
+                        const unsigned sb = (unsigned)(wb >> (8 * e)) & 63u;
+                        const unsigned sa = (unsigned)(wa >> (8 * e)) & 63u;
+                        part |= (uint32_t)((T >> sb) & (T >> sa) & 1ull) << e;
+                    }
+                    const int keep = npj - 8 * w;             // pairs of this word that exist
+                    if (keep < 8) part &= (1u << keep) - 1u;
+                    pm |= part << (8 * w);
                 }
-                const int keep = npj - 8 * w;             // pairs of this word that exist
-                if (keep < 8) part &= (1u << keep) - 1u;
-                pm |= part << (8 * w);
             }
             int n = __popc(pm);
             if (n > nmax) {        // more pairs than the workspace was sized for
@@ -2213,6 +2279,8 @@ struct FitWs {
     int* npair;          // [P][6]
     uint64_t* cand;      // [P][6]
     uint32_t* rowinfo;   // [P][64]
+    uint64_t* pset;      // [P][6][kSetWords] the pairs' before and after slot sets, with their move masks
+    uint8_t* psorted;    // [P] 1 when the program's masks ascend over its slots
     double* dlam;        // [P][64] K[t][t] + lambda
     unsigned long long* row_info;   // [Rcap] scoring summary | mask << 30
     int* split_prog;     // [S]
@@ -2255,6 +2323,8 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.npair = (int*)take(P * RS_NOPT * sizeof(int));
     w.cand = (uint64_t*)take(P * RS_NOPT * sizeof(uint64_t));
     w.rowinfo = (uint32_t*)take(P * RS_MAXV * sizeof(uint32_t));
+    w.pset = (uint64_t*)take(P * RS_NOPT * kSetWords * sizeof(uint64_t));
+    w.psorted = (uint8_t*)take(P);
     w.dlam = (double*)take(P * RS_MAXV * sizeof(double));
     w.row_info = (unsigned long long*)take((size_t)Rcap * sizeof(unsigned long long));
     w.split_prog = (int*)take(S * sizeof(int));
@@ -2344,7 +2414,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         mark(0);
         pairs_kernel<<<a.P, 64, 0, st>>>(a.P, a.row_offsets, a.masks, a.log_time, w.pb, w.pa, w.ylab,
-                                         w.npair, w.cand, w.rowinfo, a.dstatus);
+                                         w.npair, w.cand, w.rowinfo, w.pset, w.psorted, a.dstatus);
         mark(1);
         plan_fits_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a.P, a.row_offsets, a.split_offsets, a.train_masks,
                                                     a.S, w.pb, w.pa, w.npair, w.fit_pm, w.fit_key, w.hist,
@@ -2352,7 +2422,7 @@ cudaError_t rs_launch_fit_predict(const rs_fit_args& a, cudaStream_t st) {
                                                     a.rec_code ? a.rows_cap : 0,
                                                     a.rec_code ? w.row_info : nullptr,
                                                     a.masks, w.rowinfo, w.cand, (a.flags & RS_RANK_ALL) ? 1 : 0,
-                                                    a.rec_code ? 1 : 0, a.dstatus);
+                                                    a.rec_code ? 1 : 0, w.pset, w.psorted, a.dstatus);
         mark(2);
         bucket_fits_kernel<<<bucket_blocks, kBucketThreads, 0, st>>>(S6, w.fit_key, w.hist, w.cursor, w.recs,
                                                       need_off ? w.fit_off : nullptr,

@@ -46,9 +46,10 @@ def test_workspace_query_needs_no_gpu():
     # coefficient doubles;
     # per test row (bound: S x max_versions when no row count is given): six predictions
     # and the row's scoring record; per (program, optimization) the closed-form leave-one-out
-    # tables: a 32 x 32 inverse, two 32-vectors, a flag and a 32-bit label mask
+    # tables (a 32 x 32 inverse, two 32-vectors and their sums, a flag, a 32-bit label mask)
+    # and the pairs' slot sets with their move masks (14 words); per program a flag
     need_fit = (S * 6 * (4 + 1 + 16 + 8 + 1 + 17 * 8) + S * 64 * (6 * 8 + 8)
-                + b.n_programs * 6 * ((32 * 32 + 64) * 8 + 1 + 4))
+                + b.n_programs * 6 * ((32 * 32 + 68) * 8 + 1 + 4 + 14 * 8) + b.n_programs)
     assert need_fit <= fit <= need_fit + 64 * 1024
     cs.n_test_rows = 1000
     fit2 = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
