@@ -1883,37 +1883,71 @@ rank_pass_kernel(const RankPassArgs a) {
 // of each tile's rows (from rec_code) and writes the lists in place.
 constexpr int kScanThreads = 1024;
 
+constexpr int kScanItems = 8;                // tiles per thread and round (64 contiguous bytes)
+
+// Exclusive scan of the tiles' recommendation counts, one block: rounds of 8192 tiles, each
+// thread loading its 8 consecutive counts as 16-byte vectors, a block scan of the threads'
+// sums, and the running total of the earlier rounds carried along.
 __global__ void __launch_bounds__(kScanThreads)
 tile_scan_kernel(const unsigned long long* __restrict__ tile_sum, unsigned long long* __restrict__ tile_off,
                  int64_t ntiles) {
     __shared__ unsigned long long wsum[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t chunk = (ntiles + kScanThreads - 1) / kScanThreads;
-    const int64_t c0 = tid * chunk, c1 = c0 + chunk < ntiles ? c0 + chunk : ntiles;
-    unsigned long long s = 0;
-    for (int64_t t = c0; t < c1; ++t) s += tile_sum[t];
-    unsigned long long incl = s;
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < ntiles; base += (int64_t)kScanThreads * kScanItems) {
+        const int64_t i0 = base + (int64_t)tid * kScanItems;
+        const bool whole = i0 + kScanItems <= ntiles;
+        unsigned long long v[kScanItems];
+        if (whole) {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = wsum[lane];
+            for (int q = 0; q < kScanItems / 2; ++q) {
+                const ulonglong2 x = reinterpret_cast<const ulonglong2*>(tile_sum + i0)[q];
+                v[2 * q] = x.x;
+                v[2 * q + 1] = x.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k) v[k] = i0 + k < ntiles ? tile_sum[i0 + k] : 0ull;
+        }
+        unsigned long long s = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) s += v[k];
+        unsigned long long incl = s;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long v = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += v;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
         }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    unsigned long long off = incl - s + (warp > 0 ? wsum[warp - 1] : 0ull);
-    for (int64_t t = c0; t < c1; ++t) {
-        tile_off[t] = off;
-        off += tile_sum[t];
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = wsum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        unsigned long long off = carry + incl - s + (warp > 0 ? wsum[warp - 1] : 0ull);
+        unsigned long long o[kScanItems];
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            o[k] = off;
+            off += v[k];
+        }
+        if (whole) {
+#pragma unroll
+            for (int q = 0; q < kScanItems / 2; ++q)
+                reinterpret_cast<ulonglong2*>(tile_off + i0)[q] = make_ulonglong2(o[2 * q], o[2 * q + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k)
+                if (i0 + k < ntiles) tile_off[i0 + k] = o[k];
+        }
+        carry += wsum[kScanThreads / 32 - 1];
+        __syncthreads();                     // wsum is written again in the next round
     }
 }
 
@@ -1929,6 +1963,12 @@ pack_pred_kernel(const int64_t* __restrict__ rec_offsets, int64_t S, int64_t R, 
     if (tile * kRankTile >= nrows) return;
     const int64_t row = tile * kRankTile + tid;
     const unsigned c = row < nrows ? (rec_code[row] & 0xFu) : 0u;
+    // the row's parked values and the tile's offset are loaded before the block's scan, so
+    // their latency overlaps it
+    const unsigned long long toff = tile_off[tile];
+    double val[RS_NOPT];
+#pragma unroll
+    for (int pos = 0; pos < RS_NOPT; ++pos) val[pos] = pos < (int)c ? planes[pos * PS + row] : 0.0;
     unsigned incl = c;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -1939,8 +1979,10 @@ pack_pred_kernel(const int64_t* __restrict__ rec_offsets, int64_t S, int64_t R, 
     __syncthreads();
     unsigned before = 0;
     for (int w = 0; w < warp; ++w) before += wsum[w];
-    const unsigned long long off = tile_off[tile] + before + (incl - c);
-    for (unsigned pos = 0; pos < c && pos < (unsigned)RS_NOPT; ++pos) out[off + pos] = planes[pos * PS + row];
+    const unsigned long long off = toff + before + (incl - c);
+#pragma unroll
+    for (int pos = 0; pos < RS_NOPT; ++pos)
+        if (pos < (int)c) out[off + pos] = val[pos];
 }
 
 // ====================================================================== predict / rank (chunked)
