@@ -336,3 +336,36 @@ def test_rank_outputs_with_unaligned_rec_pred(rs, ctx):
     np.testing.assert_array_equal(got[0][1], got[1][1])
     assert got[0][2][-2] == 7.0 and got[0][2][-1] == 7.0
     assert got[1][2][0] == 7.0 and got[1][2][-1] == 7.0
+
+
+# ------------------------------------------------------------------------------ slot order
+def _shuffled(batch, seed):
+    """The batch with each program's versions in a random slot order, so that its masks no
+    longer ascend over the slots (the pair masks then take the bit-by-bit path)."""
+    rng = np.random.default_rng(seed)
+    X, masks, lt = batch.X.copy(), batch.masks.copy(), batch.log_time.copy()
+    cyc = None if batch.cycles is None else batch.cycles.copy()
+    for p in range(batch.n_programs):
+        r0, V = int(batch.row_offsets[p]), batch.versions(p)
+        F, xo = int(batch.feat_width[p]), int(batch.x_offsets[p])
+        perm = rng.permutation(V)
+        masks[r0:r0 + V] = batch.masks[r0:r0 + V][perm]
+        lt[r0:r0 + V] = batch.log_time[r0:r0 + V][perm]
+        if cyc is not None:
+            cyc[r0:r0 + V] = batch.cycles[r0:r0 + V][perm]
+        X[xo:xo + V * F] = batch.X[xo:xo + V * F].reshape(V, F)[perm].reshape(-1)
+    return synth.ProgramBatch(X=X, x_offsets=batch.x_offsets.copy(), row_offsets=batch.row_offsets.copy(),
+                              feat_width=batch.feat_width.copy(), masks=masks, log_time=lt, cycles=cyc)
+
+
+@pytest.mark.parametrize("kind", ["half", "frac", "lovo"])
+def test_versions_in_any_slot_order(rs, ctx, kind):
+    # programs whose masks do not ascend over their slots, beside the sorted layout of every
+    # other test: the same parity with the oracle
+    batch = _shuffled(synth.make_batch(8, versions=(12, 64), feat=40, dtype=np.float32, seed=93), 93)
+    unsorted = sum(not np.all(np.diff(batch.masks[batch.program_rows(p)].astype(int)) > 0)
+                   for p in range(batch.n_programs))
+    assert unsorted >= 7
+    splits = synth.make_splits(batch, kind, 60, seed=94)
+    g, r = _run_both(rs, ctx, batch, splits)
+    _check_cv(g, r, 3, 1.05)
