@@ -1696,7 +1696,7 @@ loo_fit_kernel(const SolveArgs a, int64_t S6, const int* __restrict__ npair,
             const double al = fma(-b, T[kLooW1 + q], T[kLooWy + q]);
             return i >= 0 ? fma(-T[i * RS_MAXPAIRS + q], e, al) : al;
         };
-        double* out = coef_out(a, f);
+        double* out = a.coef_user ? a.coef + f * RS_COEF_STRIDE : nullptr;   // no compact records
         if (out && st == RS_FIT_OK) {
             out[0] = b;
             int c = 1;
@@ -2335,7 +2335,7 @@ struct FitWs {
     double* predbuf;     // [6][Rcap]
     unsigned long long* tile_sum;   // [ceil(Rcap / 256)] recommendations per rank tile (packed output)
     unsigned long long* tile_off;   // [ceil(Rcap / 256)] their exclusive scan
-    double* loo_tab;     // [P][6][kLooTab] M^-1, w_y, w_1 per (program, optimization) (RS_LOO_CLOSED)
+    double* loo_tab;     // [P][6][kLooTab] M^-1, w_y, w_1, sums (RS_LOO_CLOSED; aliases coef)
     uint8_t* loo_ok;     // [P][6] 1 when that inverse exists
     uint32_t* loo_bad;   // [P][6] pairs whose label is not finite
     size_t bytes;
@@ -2375,12 +2375,16 @@ FitWs carve(void* base, int64_t P, int64_t S, int nmax, int64_t Rcap) {
     w.recs = (uint4*)take(S6 * sizeof(uint4));
     w.fit_off = (int64_t*)take(S6 * sizeof(int64_t));
     w.status = (uint8_t*)take(S6);
-    w.coef = (double*)take(S6 * (size_t)(nmax + 1) * sizeof(double));
+    // compact records, or with RS_LOO_CLOSED (which keeps fits only in a caller's array) the
+    // tables of the inverses: one region serves both
+    const size_t coef_bytes = S6 * (size_t)(nmax + 1) * sizeof(double);
+    const size_t loo_bytes = (size_t)P * RS_NOPT * kLooTab * sizeof(double);
+    w.coef = (double*)take(coef_bytes > loo_bytes ? coef_bytes : loo_bytes);
+    w.loo_tab = w.coef;
     w.predbuf = (double*)take((size_t)RS_NOPT * plane_stride(Rcap) * sizeof(double));
     const size_t ntiles = (size_t)((Rcap + kRankTile - 1) / kRankTile);
     w.tile_sum = (unsigned long long*)take(ntiles * sizeof(unsigned long long));
     w.tile_off = (unsigned long long*)take(ntiles * sizeof(unsigned long long));
-    w.loo_tab = (double*)take(P * RS_NOPT * kLooTab * sizeof(double));
     w.loo_ok = (uint8_t*)take(P * RS_NOPT);
     w.loo_bad = (uint32_t*)take(P * RS_NOPT * sizeof(uint32_t));
     w.bytes = o;

@@ -45,11 +45,13 @@ def test_workspace_query_needs_no_gpu():
     # per fit: pair mask, size, 16-byte record in bucket order, offset, status, and up to 17
     # coefficient doubles;
     # per test row (bound: S x max_versions when no row count is given): six predictions
-    # and the row's scoring record; per (program, optimization) the closed-form leave-one-out
-    # tables (a 32 x 32 inverse, two 32-vectors and their sums, a flag, a 32-bit label mask)
-    # and the pairs' slot sets with their move masks (14 words); per program a flag
-    need_fit = (S * 6 * (4 + 1 + 16 + 8 + 1 + 17 * 8) + S * 64 * (6 * 8 + 8)
-                + b.n_programs * 6 * ((32 * 32 + 68) * 8 + 1 + 4 + 14 * 8) + b.n_programs)
+    # and the row's scoring record; per (program, optimization) the pairs' slot sets with their
+    # move masks (14 words), and a flag and a 32-bit label mask of the closed-form
+    # leave-one-out fits, whose tables (a 32 x 32 inverse, two 32-vectors and their sums) share
+    # the coefficient records' region; per program a flag
+    coef_region = max(S * 6 * 17 * 8, b.n_programs * 6 * (32 * 32 + 68) * 8)
+    need_fit = (S * 6 * (4 + 1 + 16 + 8 + 1) + coef_region + S * 64 * (6 * 8 + 8)
+                + b.n_programs * 6 * (1 + 4 + 14 * 8) + b.n_programs)
     assert need_fit <= fit <= need_fit + 64 * 1024
     cs.n_test_rows = 1000
     fit2 = lib.rs_fit_workspace_bytes(ctypes.byref(cb), ctypes.byref(cs))
