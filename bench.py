@@ -1187,7 +1187,7 @@ def run_precision(rs, ctx, dev, stream, flush, args):
     a condition-number sweep by random mixing; BF16-split tensor-core Gram + FP64 factorisation
     + one refinement step through Z, against the FP64 path (itself within 1e-9 of the CPU
     reference).  Reports errors of the raw and refined forms per kappa and their timings, and
-    those of the FP64 path with its fits in closed form (RS_LOO_CLOSED)."""
+    those of the FP64 and the tensor-core paths with their fits in closed form (RS_LOO_CLOSED)."""
     import torch
     from paper_1910_07776_gb300 import synth
     base = synth.make_batch_fast(256, versions=64, feat=1024, dtype=np.float64, seed=21)
@@ -1207,7 +1207,8 @@ def run_precision(rs, ctx, dev, stream, flush, args):
         times = {}
         for name, prec, flags in (("f64", rs.RS_GRAM_F64, 0), ("bf16x3", rs.RS_GRAM_BF16X3, 0),
                                   ("bf16x3_refined", rs.RS_GRAM_BF16X3, rs.RS_REFINE_X),
-                                  ("f64_closed_form", rs.RS_GRAM_F64, rs.RS_LOO_CLOSED)):
+                                  ("f64_closed_form", rs.RS_GRAM_F64, rs.RS_LOO_CLOSED),
+                                  ("bf16x3_closed_form", rs.RS_GRAM_BF16X3, rs.RS_LOO_CLOSED)):
             o = rs.alloc_outputs(R, ds.n_splits, CFG["k"], dev)
             ctx.cv_step(db, ds, ws, o.rec_offsets, o.rec_code, lam=CFG["lam"], k=CFG["k"], tau=CFG["tau"],
                         flags=flags, precision=prec, rec_pred=o.rec_pred, pred_all=o.pred_all)
@@ -1224,7 +1225,7 @@ def run_precision(rs, ctx, dev, stream, flush, args):
         ok = ~np.isnan(ref)
         sc = float(np.abs(ref[ok]).max())
         ent = {}
-        for name in ("bf16x3", "bf16x3_refined", "f64_closed_form"):
+        for name in ("bf16x3", "bf16x3_refined", "f64_closed_form", "bf16x3_closed_form"):
             pa, code = outs[name]
             d = np.abs(pa[ok] - ref[ok])
             ent[name] = {"max_rel_err_pred": float(d.max() / sc), "median_rel_err_pred": float(np.median(d) / sc),

@@ -228,3 +228,17 @@ def test_graph_of_the_closed_form_step_equals_the_call(rs, ctx):
     np.testing.assert_array_equal(a.pred_all.cpu().numpy(), b.pred_all.cpu().numpy())
     np.testing.assert_array_equal(a.rec_pred.cpu().numpy(), b.rec_pred.cpu().numpy())
     assert torch.equal(2 * a.counters, b.counters)
+
+
+def test_closed_form_on_the_tensor_core_gram(rs, ctx):
+    # the precision form's BF16 hi/lo tensor-core Gram with the fits in closed form: the same
+    # system as the direct solves on that Gram, so the two agree to FP64 rounding
+    batch = synth.make_batch(4, versions=64, feat=256, dtype=np.float64, seed=82, mixing_kappa=1e4)
+    splits = synth.make_splits(batch, "lovo")
+    db = rs.DeviceBatch.from_host(batch)
+    ds = rs.DeviceSplits.from_host(splits, batch=batch)
+    d = rs.cv_run(ctx, db, ds, precision=rs.RS_GRAM_BF16X3)
+    c = rs.cv_run(ctx, db, ds, precision=rs.RS_GRAM_BF16X3, flags=rs.RS_LOO_CLOSED)
+    close(c["pred_all"], d["pred_all"])
+    _, nnear = compare_rankings(c["rec_code"], d["rec_code"], d["pred_all"], math.log(1.05))
+    compare_counters(c["counters"], d["counters"], slack=nnear)
