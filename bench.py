@@ -572,7 +572,11 @@ def main():
                         "note": "n <= split on the call's stream; n > 10 (shared memory) then "
                                 "split < n <= 10 on a second stream; joined before the rank pass"},
         "rank": {"ms": stage_ms.get("rank"), "bytes": work["rank_bytes"],
-                 "frac_hbm": work["rank_bytes"] / (stage_ms["rank"] * 1e-3) / 1e9 / hbm_peak},
+                 "frac_hbm": work["rank_bytes"] / (stage_ms["rank"] * 1e-3) / 1e9 / hbm_peak,
+                 "traffic": profiled_traffic("rank"),
+                 "note": "bound by the integer ALU pipe (75 % busy in profiles/batched_cv_kernels.md: "
+                         "64-bit order-preserving keys, 15 comparisons, threshold, top-k and scoring "
+                         "per row), not by HBM"},
         "fit_predict_path": {"ms": fit_ms, "fp64_flops": path_flops,
                              "frac_fp64": path_flops / (fit_ms * 1e-3) / 1e12 / fp64_peak}}
     # the whole step against the sum of its stages' roofline times (HBM bytes at the measured
