@@ -434,11 +434,12 @@ rs_status rs_gemm_bf16(rs_ctx* ctx, const void* A, int64_t lda, const void* B, i
  * 1 b1 [512], 2 W2 [512][512], 3 b2 [512], 4 W3 [16][512] (rows 6..15 must be zero),
  * 5 b3 [16], 6 Adam m, 7 Adam v, 8 last gradients (each laid out like 0..5), 9 feature
  * mean [256] then std [256] of the training rows, 10 counters.  The caller writes the
- * initial weights and zeros m and v.
+ * initial weights and zeros the rest of the blob (m, v and the counters).
  * rs_surrogate_train: rows (double, [n][256] standardized features; labels [n][6] double,
  * NaN = no label, trained as 0) are taken in order in minibatches of cfg->batch_rows,
  * wrapping around; cfg->steps optimizer steps (0: only the feature statistics and the BF16
- * weight copies are prepared).  use_graph = 1 captures one step in a CUDA graph and replays
+ * weight copies are prepared).  A call continues from the blob's counters: AdamW's step
+ * count, and the minibatch position (wrapped into this call's rows).  use_graph = 1 captures one step in a CUDA graph and replays
  * it.  loss_curve (nullable, float [steps]) gets each minibatch's loss.
  * rs_surrogate_infer: X 16-byte aligned (RS_EINVAL otherwise; it is read with 16-byte
  * loads); pred [n][6] (float, nullable); ood_score [n] (nullable) = mean over
@@ -469,6 +470,22 @@ rs_status rs_surrogate_infer(rs_ctx* ctx, const float* blob, const double* X, in
                              uint8_t* used_fallback, const uint8_t* masks, int k, double tau,
                              int flags, uint32_t* rec_code, double* rec_pred, void* workspace,
                              size_t workspace_bytes, int chunk_rows);
+
+/* ---- surrogate checkpoints ---------------------------------------------------------------
+ * A checkpoint is a host byte buffer of rs_surrogate_checkpoint_bytes() bytes: a 64-byte
+ * header (the magic "RSSURR01", format version 1, the layer widths 256, 512, 512 and 6, the
+ * element type 0 = FP32, the optimizer steps taken so far (AdamW's t) and the blob's size in
+ * bytes) followed by the whole blob: weights, Adam moments, last gradients, BF16 copies,
+ * feature statistics and counters.  rs_surrogate_save copies the device blob into `host`
+ * (host_bytes >= rs_surrogate_checkpoint_bytes(); ordered on the context's stream, and it
+ * returns once the copy is complete).  rs_surrogate_restore checks the header (RS_EINVAL for a
+ * wrong magic, version, width, type or size) and copies the blob back, returning once the
+ * copy is complete.  rs_surrogate_train continues from the blob's counters, so s steps, a
+ * save, a restore and t more steps on the same rows give the weights of s + t steps in one
+ * run.  (The paper has no surrogate, so it has no checkpoint format either.)            */
+size_t rs_surrogate_checkpoint_bytes(void);
+rs_status rs_surrogate_save(rs_ctx* ctx, const float* blob, void* host, size_t host_bytes);
+rs_status rs_surrogate_restore(rs_ctx* ctx, float* blob, const void* host, size_t host_bytes);
 
 /* ---- the whole step, allocating nothing -------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of rs_cv_step for callers that

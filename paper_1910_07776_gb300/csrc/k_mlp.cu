@@ -438,6 +438,14 @@ adamw_kernel(float* blob, float lr, float b1, float b2, float eps, float wd, int
     }
 }
 
+// A call continues from the blob's counters (a restored checkpoint resumes the same sequence
+// of minibatches and Adam steps); the minibatch position wraps into this call's rows.
+__global__ void wrap_counters_kernel(int* counters, int64_t steps_per_epoch) {
+    int64_t q = counters[0] % steps_per_epoch;
+    if (q < 0) q += steps_per_epoch;                         // (a blob not zeroed by its owner)
+    counters[0] = (int)q;
+    if (counters[1] < 0) counters[1] = 0;
+}
 __global__ void bump_counters_kernel(int* counters, int64_t steps_per_epoch) {
     counters[1] += 1;                                        // Adam t
     counters[0] = (int)((counters[0] + 1) % steps_per_epoch); // minibatch index
@@ -643,13 +651,14 @@ cudaError_t rs_launch_surrogate_train(float* blob, const double* X, const double
     if (e == cudaSuccess) e = all_attrs();
     if (e != cudaSuccess) return e;
     const int64_t spe = n / B > 0 ? n / B : 1;
-    // statistics for the OOD score, BF16 copies of the initial weights, counters
+    // statistics for the OOD score, BF16 copies of the initial weights, the counters' position
     e = cudaMemsetAsync(w.stats_acc, 0, 2 * kIn * sizeof(double), st);
     if (e != cudaSuccess) return e;
     feature_stats_kernel<<<(unsigned)(n < 1024 ? n : 1024), kIn, 0, st>>>(X, n, w.stats_acc);
     feature_stats_finish<<<1, kIn, 0, st>>>(w.stats_acc, n, blob + Blob::oStats, blob + Blob::oStats + kIn);
     sync_bf16_kernel<<<(unsigned)((Blob::nW2 + 255) / 256), 256, 0, st>>>(blob, bf);
-    e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+    wrap_counters_kernel<<<1, 1, 0, st>>>(counters, spe);
+    e = cudaGetLastError();
     if (e == cudaSuccess && loss_curve) e = cudaMemsetAsync(loss_curve, 0, steps * sizeof(float), st);
     if (e != cudaSuccess) return e;
     // one step; the loss goes to loss_curve[t - 1] through a device-side pointer bump

@@ -450,6 +450,71 @@ rs_status rs_surrogate_infer(rs_ctx* c, const float* blob, const double* X, int6
     return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_surrogate_infer");
 }
 
+// ---- surrogate checkpoints: a 64-byte header, then the blob as it is on the device
+namespace {
+struct CkptHeader {
+    char magic[8];                // "RSSURR01"
+    uint32_t version;             // 1
+    uint32_t width[4];            // 256, 512, 512, 6
+    uint32_t dtype;               // 0: FP32
+    int64_t step;                 // optimizer steps taken (AdamW's t)
+    uint64_t blob_bytes;
+    unsigned char pad[16];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+constexpr char kCkptMagic[8] = {'R', 'S', 'S', 'U', 'R', 'R', '0', '1'};
+constexpr uint32_t kCkptWidth[4] = {256, 512, 512, 6};
+}  // namespace
+
+size_t rs_surrogate_checkpoint_bytes(void) { return sizeof(CkptHeader) + rs_surrogate_blob_bytes(); }
+
+rs_status rs_surrogate_save(rs_ctx* c, const float* blob, void* host, size_t host_bytes) {
+    if (!c) return RS_EINVAL;
+    if (!blob || !host) return fail(c, RS_EINVAL, "blob and host are required");
+    if (host_bytes < rs_surrogate_checkpoint_bytes())
+        return fail(c, RS_EINVAL, "host buffer has %zu bytes, needs %zu", host_bytes, rs_surrogate_checkpoint_bytes());
+    cudaSetDevice(c->device);
+    unsigned char* out = static_cast<unsigned char*>(host);
+    const size_t nb = rs_surrogate_blob_bytes();
+    cudaError_t e = cudaMemcpyAsync(out + sizeof(CkptHeader), blob, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rs_surrogate_save");
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+    h.version = 1;
+    memcpy(h.width, kCkptWidth, sizeof(h.width));
+    h.dtype = 0;
+    int32_t t = 0;                // counters: [0] minibatch position, [1] AdamW's t
+    memcpy(&t, out + sizeof(CkptHeader) + (size_t)rs_surrogate_blob_offset(10) * sizeof(float) + sizeof(int32_t),
+           sizeof(t));
+    h.step = t;
+    h.blob_bytes = nb;
+    memcpy(out, &h, sizeof(h));
+    return RS_OK;
+}
+
+rs_status rs_surrogate_restore(rs_ctx* c, float* blob, const void* host, size_t host_bytes) {
+    if (!c) return RS_EINVAL;
+    if (!blob || !host) return fail(c, RS_EINVAL, "blob and host are required");
+    if ((uintptr_t)blob % 256) return fail(c, RS_EINVAL, "blob must be 256-byte aligned");
+    if (host_bytes < sizeof(CkptHeader)) return fail(c, RS_EINVAL, "not a surrogate checkpoint (too short)");
+    CkptHeader h;
+    memcpy(&h, host, sizeof(h));
+    if (memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0) return fail(c, RS_EINVAL, "not a surrogate checkpoint");
+    if (h.version != 1) return fail(c, RS_EINVAL, "checkpoint format version %u, expected 1", h.version);
+    if (memcmp(h.width, kCkptWidth, sizeof(h.width)) != 0 || h.dtype != 0)
+        return fail(c, RS_EINVAL, "checkpoint of another network shape or element type");
+    const size_t nb = rs_surrogate_blob_bytes();
+    if (h.blob_bytes != nb || host_bytes < sizeof(CkptHeader) + nb)
+        return fail(c, RS_EINVAL, "checkpoint blob of %llu bytes, expected %zu", (unsigned long long)h.blob_bytes, nb);
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpyAsync(blob, static_cast<const unsigned char*>(host) + sizeof(CkptHeader), nb,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? RS_OK : cuda_fail(c, e, "rs_surrogate_restore");
+}
+
 }  // extern "C"
 
 namespace {

@@ -40,6 +40,7 @@ EXPORTS = [
     "rs_check_reciprocals", "rs_check_wait_timeout", "rs_fallback_workspace_bytes", "rs_surrogate_fallback",
     "rs_pooled_workspace_bytes", "rs_fit_pooled", "rs_predict_pooled",
     "rs_autotune_gram", "rs_get_gram_tuning", "rs_set_gram_tuning",
+    "rs_surrogate_checkpoint_bytes", "rs_surrogate_save", "rs_surrogate_restore",
 ]
 
 
@@ -138,6 +139,10 @@ def load(path: str = SO):
     L.rs_surrogate_workspace_bytes.restype = C.c_size_t
     L.rs_surrogate_train.argtypes = [P, P, P, P, i64, P, P, P, C.c_size_t]
     L.rs_surrogate_infer.argtypes = [P, P, P, i64, C.c_float, P, P, P, P, i, d, i, P, P, P, C.c_size_t, i]
+    L.rs_surrogate_checkpoint_bytes.argtypes = []
+    L.rs_surrogate_checkpoint_bytes.restype = C.c_size_t
+    L.rs_surrogate_save.argtypes = [P, P, P, C.c_size_t]
+    L.rs_surrogate_restore.argtypes = [P, P, P, C.c_size_t]
     L.rs_profile_enable.argtypes = [P, i]
     L.rs_profile_read.argtypes = [P, C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     L.rs_transfer_workspace_bytes.argtypes = [P, P, P, i]
@@ -146,7 +151,8 @@ def load(path: str = SO):
     for name in EXPORTS:
         if name not in ("rs_last_error", "rs_cv_workspace_bytes", "rs_fit_workspace_bytes", "rs_gram_workspace_bytes",
                         "rs_fallback_workspace_bytes", "rs_pooled_workspace_bytes",
-                        "rs_transfer_workspace_bytes", "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes"):
+                        "rs_transfer_workspace_bytes", "rs_surrogate_blob_bytes", "rs_surrogate_offset", "rs_surrogate_workspace_bytes",
+                        "rs_surrogate_checkpoint_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -545,6 +551,25 @@ class Surrogate:
                 dst[:t.shape[0]].copy_(t)
             else:
                 dst.copy_(t)
+
+    def save(self, path: str) -> int:
+        """Write a checkpoint of the whole state (rs_surrogate_save) to `path`; returns the
+        optimizer steps taken so far."""
+        n = int(self.ctx.L.rs_surrogate_checkpoint_bytes())
+        buf = (C.c_ubyte * n)()
+        self.ctx._check(self.ctx.L.rs_surrogate_save(self.ctx.h, _ptr(self.blob), buf, n))
+        data = bytes(buf)
+        with open(path, "wb") as f:
+            f.write(data)
+        return int.from_bytes(data[32:40], "little", signed=True)
+
+    def restore(self, path: str) -> None:
+        """Load a checkpoint written by save (rs_surrogate_restore checks its header); training
+        then continues where the saved run stopped."""
+        with open(path, "rb") as f:
+            data = f.read()
+        buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+        self.ctx._check(self.ctx.L.rs_surrogate_restore(self.ctx.h, _ptr(self.blob), buf, len(data)))
 
     def train(self, X, Y, steps: int, lr: float = 1e-3, weight_decay: float = 0.0, use_graph: bool = True,
               loss_curve=None):

@@ -164,3 +164,34 @@ def test_inference_ranking_matches_reference_ranking(env):
         want = list(oracle.rank(P[r], valid, 3, lt))
         assert got[r] == want, (r, got[r], want, P[r])
         np.testing.assert_array_equal(rp.cpu().numpy().reshape(700, 3)[r, :len(want)], P[r, want])
+
+
+def test_checkpoint_resume_continues_the_run(env, tmp_path):
+    # 3 steps, a checkpoint, a restore into a fresh state and 7 more steps give the weights and
+    # Adam moments of 10 steps in one run (4 minibatches of 256 rows: the run wraps around)
+    rs, ctx = env
+    X, Y, Xd, Yd = data(1024, 6)
+    p = mlp.init_params(6)
+    a = rs.Surrogate(ctx, 256)
+    a.load(p)
+    a.train(Xd, Yd, steps=10, lr=1e-3)
+    b = rs.Surrogate(ctx, 256)
+    b.load(p)
+    b.train(Xd, Yd, steps=3, lr=1e-3)
+    path = str(tmp_path / "surrogate.ckpt")
+    assert b.save(path) == 3
+    c = rs.Surrogate(ctx, 256)
+    c.restore(path)
+    c.train(Xd, Yd, steps=7, lr=1e-3)
+    torch.cuda.synchronize()
+    for k in mlp.NAMES:
+        assert torch.equal(a.view(k), c.view(k)), k
+        assert torch.equal(a.view(k, "m"), c.view(k, "m")) and torch.equal(a.view(k, "v"), c.view(k, "v")), k
+    # a damaged or truncated checkpoint is refused
+    raw = bytearray(open(path, "rb").read())
+    for bad in (bytes([raw[0] ^ 1]) + bytes(raw[1:]), bytes(raw[:1000])):
+        f = tmp_path / "bad.ckpt"
+        f.write_bytes(bad)
+        with pytest.raises(rs.RsError) as e:
+            c.restore(str(f))
+        assert e.value.status == rs.RS_EINVAL
