@@ -869,8 +869,19 @@ def run_lovo(rs, ctx, dev, stream, flush, args, programs=256):
     fin = ~np.isnan(pa)
     same_nan = bool(np.array_equal(np.isnan(pa), np.isnan(pc)))
     diff = np.abs(pa[fin] - pc[fin])
+    # the closed form's FP64 work: one Gauss-Jordan inverse per (program, optimization) with at
+    # least one pair, padded to 32 x 32 with two right-hand sides (2 flops per FMA)
+    n_inv = 0
+    for p_ in range(b.n_programs):
+        m_ = set(int(x) for x in b.masks[b.program_rows(p_)])
+        n_inv += sum(1 for j in range(6) if any(not (x >> j) & 1 and (x | 1 << j) in m_ for x in m_))
+    inv_flops = n_inv * 2.0 * 32 * 32 * (32 + 2)
+    fit_ms_c = stages_c.get("solve", 0.0) + stages_c.get("solve_join", 0.0)
     closed = {"ms_per_step": ms_c, "value": R / (ms_c * 1e-3), "unit": UNIT, "stages_ms": stages_c,
-              "fit_ms": stages_c.get("solve", 0.0) + stages_c.get("solve_join", 0.0),
+              "fit_ms": fit_ms_c, "inverses": n_inv, "inverse_flops": inv_flops,
+              "fit_stage_frac_fp64": inv_flops / (fit_ms_c * 1e-3) / 1e12 / fp64_peak if fit_ms_c > 0 else None,
+              "fit_stage_note": "the inverses' FMAs (1,536 x 32 x 32 x 34 at 256 programs) over the stage time, "
+                                "which also holds the diagonal kernel and the O(1) per-fit kernel",
               "sign_accuracy": cc[3] / max(cc[2], 1), "top1_hit_rate": cc[8] / max(cc[7], 1),
               "fits_ok": int(cc[9]),
               "max_abs_pred_diff_vs_direct": float(diff.max()) if diff.size else 0.0,
