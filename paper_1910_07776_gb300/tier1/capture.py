@@ -13,7 +13,7 @@ was profiled three times per input):
 Inputs with the same body count share their profiled time step within a run.
 
 Run on the GPU machine from the repository root:
-    python -m paper_1910_07776_gb300.tier1.capture gpurun_out/nb_gb300.npz
+    python -m paper_1910_07776_gb300.tier1.capture out/nb_gb300.npz
 and copy the file next to this script as nb_gb300.npz.  Needs nvcc and ncu on PATH."""
 from __future__ import annotations
 
