@@ -114,6 +114,8 @@ def main(out_path):
                 feats[r, i, mask] = [prof[n][m] / c for m in COUNTERS]
     gpu = subprocess.check_output(["nvidia-smi", "--query-gpu=name,driver_version", "--format=csv,noheader"],
                                   text=True).strip()
+    if os.path.dirname(out_path):
+        os.makedirs(os.path.dirname(out_path), exist_ok=True)
     np.savez_compressed(out_path, features=feats, cycles=cycles, time_ms=times,
                         inputs=np.array(INPUTS), counters=np.array(COUNTERS), cycles_metric=CYCLES,
                         gpu=gpu, seconds=time.time() - t0,
